@@ -1,0 +1,288 @@
+"""FP64 CPU oracle of the coupled colour-gradient LBM / DEM method (arXiv 2505.10171).
+
+TEST INFRASTRUCTURE.  This package is the plain, slow reference the CUDA library
+is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import it.
+Nothing in ``paper_2505_10171_gb300`` imports it, and it imports nothing from
+there.
+
+``lbm_oracle.c`` holds the method (each step cites its section/equation of the
+paper); ``mlp_oracle.py`` holds the NumPy FP64 reference of the learned force
+surrogate.  This module only builds the C file with gcc and marshals NumPy
+arrays through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+Q = 19
+MAXP = 61
+
+
+class OrParams(ct.Structure):
+    _fields_ = [
+        ("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+        ("wall_z0", ct.c_int),
+        ("wall_velocity", ct.c_double * 3),
+        ("theta_wall_deg", ct.c_double),
+        ("rho0", ct.c_double),
+        ("nu_a", ct.c_double), ("nu_b", ct.c_double),
+        ("sigma", ct.c_double), ("beta", ct.c_double), ("cap_norm", ct.c_double),
+        ("body_force_a", ct.c_double * 3), ("body_force_b", ct.c_double * 3),
+        ("kn", ct.c_double), ("kt", ct.c_double), ("kr", ct.c_double),
+        ("gn", ct.c_double), ("gt", ct.c_double), ("gr", ct.c_double),
+        ("mu_s", ct.c_double), ("mu_r", ct.c_double), ("delta_R", ct.c_double),
+        ("g_particle", ct.c_double * 3),
+        ("grad_eps", ct.c_double), ("wet_phi_max", ct.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile lbm_oracle.c into a shared library (gcc, OpenMP, no FMA contraction)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "lbm_oracle.h"))
+        ):
+            return _LIB
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE", "-fopenmp", "-ffp-contract=off",
+               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ct.CDLL(_LIB)
+        P = ct.POINTER
+        d, i = ct.c_double, ct.c_int
+        L.or_create.restype = ct.c_void_p
+        L.or_create.argtypes = [P(OrParams)]
+        L.or_destroy.argtypes = [ct.c_void_p]
+        L.or_set_static_solid.argtypes = [ct.c_void_p, P(ct.c_ubyte)]
+        L.or_init_fields.argtypes = [ct.c_void_p, P(d), P(d), P(d)]
+        L.or_set_pops.argtypes = [ct.c_void_p, P(d), P(d)]
+        L.or_add_particle.argtypes = [ct.c_void_p, P(d), P(d), P(d), d, d, d, i]
+        L.or_step.argtypes = [ct.c_void_p, i]
+        L.or_dem_only_step.argtypes = [ct.c_void_p, i, P(d)]
+        L.or_get_pops.argtypes = [ct.c_void_p, P(d), P(d)]
+        L.or_get_fields.argtypes = [ct.c_void_p, P(d), P(d), P(d), P(d)]
+        L.or_get_grad.argtypes = [ct.c_void_p, P(d)]
+        L.or_get_owner.argtypes = [ct.c_void_p, P(ct.c_ubyte)]
+        L.or_num_particles.argtypes = [ct.c_void_p]
+        L.or_num_particles.restype = i
+        L.or_get_particles.argtypes = [ct.c_void_p, P(d)]
+        L.or_get_diag.argtypes = [ct.c_void_p, P(d)]
+        L.or_lattice.argtypes = [P(i), P(d), P(i)]
+        L.or_mrt_matrices.argtypes = [P(d), P(d), P(d)]
+        L.or_collide_node.argtypes = [P(d), P(d), P(d), P(d), d, d, d, P(d), P(d), P(d)]
+        L.or_omega_of_phi.argtypes = [P(OrParams), d, d]
+        L.or_omega_of_phi.restype = d
+        L.or_wetting_rotate.argtypes = [P(d), P(d), d]
+        L.or_capillary.argtypes = [ct.c_void_p, i, P(d), P(d)]
+        L.or_capillary.restype = i
+        L.or_eval_interface.argtypes = [ct.c_void_p]
+        L.or_get_phi.argtypes = [ct.c_void_p, P(d)]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+DEFAULTS = dict(
+    wall_z0=0, wall_velocity=(0.0, 0.0, 0.0), theta_wall_deg=90.0, rho0=1.0,
+    nu_a=1.0 / 6.0, nu_b=1.0 / 6.0, sigma=0.01, beta=0.7,
+    cap_norm=4.5 * (1.0 + 2.0 ** 0.5) / 18.0 * 0.7,
+    body_force_a=(0.0, 0.0, 0.0), body_force_b=(0.0, 0.0, 0.0),
+    kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0,
+    g_particle=(0.0, 0.0, 0.0), grad_eps=1e-10, wet_phi_max=0.99,
+)
+
+
+def make_params(nx, ny, nz, **kw) -> OrParams:
+    """OrParams from keyword arguments; unspecified values take DEFAULTS.
+
+    ``cap_norm`` defaults to the paper's (9/2) k beta with k = (1+sqrt 2)/18
+    and the given beta, unless passed explicitly.
+    """
+    v = dict(DEFAULTS)
+    v.update(kw)
+    if "cap_norm" not in kw:
+        v["cap_norm"] = 4.5 * (1.0 + 2.0 ** 0.5) / 18.0 * v["beta"]
+    p = OrParams()
+    p.nx, p.ny, p.nz = nx, ny, nz
+    for name, _ in OrParams._fields_:
+        if name in ("nx", "ny", "nz"):
+            continue
+        val = v[name]
+        if isinstance(val, (tuple, list, np.ndarray)):
+            arr = getattr(p, name)
+            for k in range(3):
+                arr[k] = float(val[k])
+        else:
+            setattr(p, name, type(getattr(p, name))(val))
+    return p
+
+
+class OracleSim:
+    """One FP64 oracle simulation (Sec. III-V of the paper)."""
+
+    def __init__(self, nx, ny, nz, **kw):
+        self.L = lib()
+        self.params = make_params(nx, ny, nz, **kw)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.N = nx * ny * nz
+        self.h = self.L.or_create(ct.byref(self.params))
+        if not self.h:
+            raise MemoryError("or_create failed")
+
+    def close(self):
+        if self.h:
+            self.L.or_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_static_solid(self, mask):
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        assert m.size == self.N
+        self.L.or_set_static_solid(self.h, m.ctypes.data_as(ct.POINTER(ct.c_ubyte)))
+
+    def init_fields(self, phi, rho=None, u=None):
+        phi = _f64(phi).reshape(-1)
+        rho = _f64(rho).reshape(-1) if rho is not None else np.full(self.N, self.params.rho0)
+        u = _f64(u).reshape(-1) if u is not None else np.zeros(3 * self.N)
+        self.L.or_init_fields(self.h, _dp(phi), _dp(rho), _dp(u))
+
+    def set_pops(self, fa, fb):
+        fa, fb = _f64(fa).reshape(-1), _f64(fb).reshape(-1)
+        self.L.or_set_pops(self.h, _dp(fa), _dp(fb))
+
+    def add_particle(self, x, R, rho_p=0.125, theta_deg=90.0, v=(0, 0, 0), w=(0, 0, 0), kinematic=False):
+        x, v, w = _f64(x), _f64(v), _f64(w)
+        r = self.L.or_add_particle(self.h, _dp(x), _dp(v), _dp(w), float(R), float(rho_p), float(theta_deg),
+                                   int(kinematic))
+        if r != 0:
+            raise ValueError("too many particles")
+
+    def step(self, n=1):
+        self.L.or_step(self.h, int(n))
+
+    def dem_only(self, n):
+        np_ = self.num_particles
+        traj = np.zeros((n, np_, 13))
+        self.L.or_dem_only_step(self.h, int(n), _dp(traj))
+        return traj
+
+    @property
+    def num_particles(self):
+        return self.L.or_num_particles(self.h)
+
+    def pops(self):
+        fa = np.zeros((Q, self.N))
+        fb = np.zeros((Q, self.N))
+        self.L.or_get_pops(self.h, _dp(fa), _dp(fb))
+        return fa, fb
+
+    def fields(self):
+        ra, rb, ph = np.zeros(self.N), np.zeros(self.N), np.zeros(self.N)
+        u = np.zeros(3 * self.N)
+        self.L.or_get_fields(self.h, _dp(ra), _dp(rb), _dp(ph), _dp(u))
+        return dict(rho_a=ra, rho_b=rb, phi=ph, u=u.reshape(3, self.N))
+
+    def grad(self):
+        g = np.zeros(3 * self.N)
+        self.L.or_get_grad(self.h, _dp(g))
+        return g.reshape(3, self.N)
+
+    def owner(self):
+        o = np.zeros(self.N, dtype=np.uint8)
+        self.L.or_get_owner(self.h, o.ctypes.data_as(ct.POINTER(ct.c_ubyte)))
+        return o
+
+    def particles(self):
+        n = self.num_particles
+        out = np.zeros((max(n, 1), 32))
+        self.L.or_get_particles(self.h, _dp(out))
+        return out[:n]
+
+    def diag(self):
+        out = np.zeros(8)
+        self.L.or_get_diag(self.h, _dp(out))
+        return out
+
+    def eval_interface(self):
+        """phi, corrected grad(phi) from the current state (no streaming)."""
+        self.L.or_eval_interface(self.h)
+        ph = np.zeros(self.N)
+        self.L.or_get_phi(self.h, _dp(ph))
+        return ph, self.grad()
+
+    def capillary(self, p):
+        F, T = np.zeros(3), np.zeros(3)
+        used = self.L.or_capillary(self.h, int(p), _dp(F), _dp(T))
+        return F, T, used
+
+
+def lattice():
+    L = lib()
+    c = np.zeros(Q * 3, dtype=np.int32)
+    w = np.zeros(Q)
+    opp = np.zeros(Q, dtype=np.int32)
+    L.or_lattice(c.ctypes.data_as(ct.POINTER(ct.c_int)), _dp(w), opp.ctypes.data_as(ct.POINTER(ct.c_int)))
+    return c.reshape(Q, 3), w, opp
+
+
+def mrt_matrices():
+    L = lib()
+    M, Mi, S = np.zeros(Q * Q), np.zeros(Q * Q), np.zeros(Q)
+    L.or_mrt_matrices(_dp(M), _dp(Mi), _dp(S))
+    return M.reshape(Q, Q), Mi.reshape(Q, Q), S
+
+
+def collide_node(fa, fb, F, nhat, omega, omega_p, beta):
+    L = lib()
+    fa, fb, F, nhat = _f64(fa), _f64(fb), _f64(F), _f64(nhat)
+    fao, fbo, u = np.zeros(Q), np.zeros(Q), np.zeros(3)
+    L.or_collide_node(_dp(fa), _dp(fb), _dp(F), _dp(nhat), float(omega), float(omega_p), float(beta),
+                      _dp(fao), _dp(fbo), _dp(u))
+    return fao, fbo, u
+
+
+def wetting_rotate(g, ns, theta_rad):
+    L = lib()
+    g = _f64(g).copy()
+    ns = _f64(ns)
+    L.or_wetting_rotate(_dp(g), _dp(ns), float(theta_rad))
+    return g
+
+
+def omega_of_phi(phi, rho, **kw):
+    p = make_params(1, 1, 1, **kw)
+    return lib().or_omega_of_phi(ct.byref(p), float(phi), float(rho))

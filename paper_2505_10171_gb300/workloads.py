@@ -1,0 +1,146 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module holds no arithmetic of the method: it only draws initial fields
+(order parameter, density, velocity), static solid masks and particle lists.
+Both the CUDA path and the CPU oracle are fed from it.  Every array is
+z-major (index = (z*ny + y)*nx + x) and FP64.
+
+The shapes follow the paper's own set-ups (Sec. VI A: a hemispherical drop on
+a flat substrate with a sphere in front of it, periodic in x, y, z; Table I
+parameter ranges; Sec. V F: Segre-Silberberg tube), with the sizes of the
+configurations this library is measured on:
+
+* ``cfg1`` - 48x32x32, drop R=10, one sphere R_p=4, 200 steps (parity case).
+* ``cfg2`` - 256x128x128, drop R=40, eight spheres R_p=8, 20000 steps.
+* ``cfg3`` - 64x64x1024 tube R_t=31, single phase, one sphere R_p=6.
+* ``cfg4`` - 96 independent drop/sphere instances of uneven size.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+# Table I (simulation units) and the common defaults of the configurations.
+COMMON = dict(
+    rho0=1.0, beta=0.7, sigma=0.01, delta_R=1.0,
+    kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0,
+)
+INTERFACE_WIDTH = 2.5
+
+
+def grid(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return x.astype(np.float64), y.astype(np.float64), z.astype(np.float64)
+
+
+def periodic_delta(d, n):
+    """Minimum-image displacement on a periodic axis of n nodes."""
+    return d - n * np.floor(d / n + 0.5)
+
+
+def drop_phi(nx, ny, nz, centre, R, width=INTERFACE_WIDTH):
+    """Order parameter of a spherical drop: +1 inside, -1 outside, tanh edge."""
+    x, y, z = grid(nx, ny, nz)
+    dx = periodic_delta(x - centre[0], nx)
+    dy = periodic_delta(y - centre[1], ny)
+    dz = periodic_delta(z - centre[2], nz)
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    return np.tanh(2.0 * (R - r) / width).reshape(-1)
+
+
+def cfg1():
+    """48x32x32 parity case: drop R=10 on a wall sliding at 1e-3, sphere R_p=4."""
+    nx, ny, nz = 48, 32, 32
+    params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, wall_velocity=(1e-3, 0.0, 0.0),
+                  theta_wall_deg=90.0, nu_a=1.0 / 6.0, nu_b=1.0 / 6.0, mu_s=0.3, mu_r=0.05,
+                  g_particle=(0.0, 0.0, 0.0))
+    phi = drop_phi(nx, ny, nz, (16.0, 16.0, 0.5), 10.0)
+    particles = [dict(x=(33.0, 16.0, 5.5), R=4.0, rho_p=0.125, theta_deg=60.0)]
+    return dict(name="drop-sphere 48x32x32, 1 sphere R=4, FP64 parity", params=params, phi=phi,
+                particles=particles, steps=200)
+
+
+def place_spheres(rng, n, R, Rc, x_range, y_range, z, min_spacing, max_tries=100000):
+    """Rejection-sample n non-overlapping sphere centres at height z."""
+    out = []
+    tries = 0
+    while len(out) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place spheres")
+        x = rng.uniform(*x_range)
+        y = rng.uniform(*y_range)
+        if all((x - a) ** 2 + (y - b) ** 2 >= min_spacing ** 2 for a, b, _ in out):
+            out.append((x, y, z))
+    return out
+
+
+def cfg2(seed=20251, n_spheres=8):
+    """256x128x128 resolved run: drop R=40 driven along x over a 150 deg wall,
+    eight spheres R_p=8 with contact angles uniform in [30, 90] deg,
+    drop:ambient kinematic viscosities 1/6 : 1/60."""
+    nx, ny, nz = 256, 128, 128
+    R_p, Rc = 8.0, 9.0
+    rng = np.random.default_rng(seed)
+    centres = place_spheres(rng, n_spheres, R_p, Rc, (96 + Rc + 4, nx - Rc - 4), (Rc, ny - Rc),
+                            9.5, 2 * Rc + 1)
+    thetas = rng.uniform(30.0, 90.0, size=n_spheres)
+    sigma = COMMON["sigma"]
+    params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, wall_velocity=(0.0, 0.0, 0.0),
+                  theta_wall_deg=150.0, nu_a=1.0 / 6.0, nu_b=1.0 / 60.0, mu_s=0.3, mu_r=0.05,
+                  body_force_a=(2.0e-6, 0.0, 0.0), g_particle=(0.0, 0.0, -10.0 * sigma * R_p))
+    phi = drop_phi(nx, ny, nz, (48.0, 64.0, 0.5), 40.0)
+    particles = [dict(x=c, R=R_p, rho_p=0.125, theta_deg=float(t)) for c, t in zip(centres, thetas)]
+    return dict(name="drop-sphere 256x128x128, 8 spheres R=8", params=params, phi=phi,
+                particles=particles, steps=20000)
+
+
+def cfg3(nz=1024):
+    """64x64xnz tube of radius 31 (periodic along z), single phase, body-force
+    driven Poiseuille flow at centreline speed 0.02, one neutrally buoyant
+    sphere R_p=6 released at r = 0.3 R_t."""
+    nx = ny = 64
+    Rt, uc, nu = 31.0, 0.02, 1.0 / 6.0
+    x, y, z = grid(nx, ny, nz)
+    r = np.sqrt((x - 31.5) ** 2 + (y - 31.5) ** 2).reshape(-1)
+    mask = (r > Rt).astype(np.uint8)
+    g = 4.0 * nu * uc / Rt ** 2
+    u = np.zeros((3, nx * ny * nz))
+    u[2] = np.where(r <= Rt, uc * (1.0 - (r / Rt) ** 2), 0.0)
+    l = 0.3 * Rt
+    params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=0, nu_a=nu, nu_b=nu, sigma=0.0,
+                  body_force_a=(0.0, 0.0, g), mu_s=0.0, mu_r=0.0)
+    up = uc * (1.0 - (l / Rt) ** 2)
+    particles = [dict(x=(31.5 + l, 31.5, nz / 2), R=6.0, rho_p=1.0, theta_deg=90.0, v=(0.0, 0.0, up))]
+    return dict(name=f"tube 64x64x{nz}, sphere R=6", params=params, phi=np.ones(nx * ny * nz), u=u,
+                mask=mask, particles=particles, steps=50000)
+
+
+def ceil8(v):
+    return int(math.ceil(v / 8.0) * 8)
+
+
+def cfg4(seed=4242, n_instances=96):
+    """Batched sweep: drop radius uniform in [16, 40], domain 5.5R x 3.2R x 3.2R
+    rounded up to multiples of 8 (at least 96x64x64), one sphere R/5, drop speed
+    uniform in [1e-3, 1e-2], mu_s in [0, 0.6], mu_r in [0, 0.1]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_instances):
+        Rd = rng.uniform(16.0, 40.0)
+        U = rng.uniform(1e-3, 1e-2)
+        mu_s = rng.uniform(0.0, 0.6)
+        mu_r = rng.uniform(0.0, 0.1)
+        nx, ny, nz = max(96, ceil8(5.5 * Rd)), max(64, ceil8(3.2 * Rd)), max(64, ceil8(3.2 * Rd))
+        R_p = Rd / 5.0
+        sigma = COMMON["sigma"]
+        params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=90.0,
+                      nu_a=1.0 / 6.0, nu_b=1.0 / 60.0, mu_s=mu_s, mu_r=mu_r,
+                      body_force_a=(U * 4e-4, 0.0, 0.0), g_particle=(0.0, 0.0, -10.0 * sigma * R_p))
+        xd = 1.2 * Rd
+        phi = drop_phi(nx, ny, nz, (xd, ny / 2.0, 0.5), Rd)
+        xp = xd + Rd + R_p + 3.0
+        particles = [dict(x=(xp, ny / 2.0, R_p + 1.5), R=R_p, rho_p=0.125, theta_deg=90.0)]
+        out.append(dict(params=params, phi=phi, particles=particles, drop_speed=U))
+    return out
