@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled LBM-DEM time step on GB300.
+
+One "step" is one coupled time step of the whole hot path (streaming with
+bounce-back, order parameter, gradient with wetting, curvature and CSF force,
+MRT collision with Guo forcing, recolouring, momentum exchange, capillary
+force, DEM, geometry update and refill) over the 256x128x128 drop + 8 spheres
+workload (FP32 offset storage).  The metric is MLUPS (all nodes x steps /
+time).  Inputs are synthetic (seeded), see paper_2505_10171_gb300/workloads.py.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Under torchrun each rank steps its own copy
+of the workload (independent problems, weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM roofline at 1 GB300 (FP32 vs FP16-storage vs batched) at stated error"
+UNIT = "MLUPS"
+WORKLOAD = "drop R=40 sliding over a 150 deg wall + 8 spheres R_p=8, 256x128x128 (4.19M nodes), coupled LBM-DEM step"
+# algorithmic bytes per lattice update of the fluid update: read + write of
+# 2 x 19 populations
+ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}
+
+
+def algorithmic_bytes_per_node(stage, prec):
+    e = ELEM[prec]
+    r = 8 if prec == "fp64" else 4
+    return {"collide": 76 * e, "phi": 38 * e + r}.get(stage, 0)
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def oracle_sample(budget_s=15.0, steps_cap=None):
+    """Time the FP64 CPU oracle on a sub-box of the workload (host cores)."""
+    import oracle as O
+    from paper_2505_10171_gb300 import workloads as W
+    for dims in ((128, 128, 48), (96, 96, 40), (64, 64, 32)):
+        w = W.cfg2_crop(*dims)
+        s = O.from_workload(w)
+        t0 = time.perf_counter()
+        s.step(1)
+        t1 = time.perf_counter() - t0
+        if t1 * 3 <= budget_s or dims == (64, 64, 32):
+            break
+    n = max(1, int(budget_s / max(t1, 1e-3)))
+    if steps_cap:
+        n = min(n, steps_cap)
+    t0 = time.perf_counter()
+    s.step(n)
+    dt = time.perf_counter() - t0
+    N = dims[0] * dims[1] * dims[2]
+    cores = os.cpu_count()
+    return dict(value=N * n / dt / 1e6, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{n} steps of a {dims[0]}x{dims[1]}x{dims[2]} sub-box of the workload "
+                       f"({len(w['particles'])} spheres), FP64 C oracle, OpenMP on {cores} threads",
+                seconds=dt)
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2505_10171_gb300 import workloads as W
+    budget = 150.0
+    chosen = None
+    for dims in ((128, 128, 48), (96, 96, 40), (64, 64, 32), (48, 48, 24)):
+        w = W.cfg2_crop(*dims)
+        s = O.from_workload(w)
+        t0 = time.perf_counter()
+        s.step(1)
+        t1 = time.perf_counter() - t0
+        chosen = (dims, w, s)
+        if t1 * (args.steps + args.warmup) <= budget:
+            break
+    dims, w, s = chosen
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    N = dims[0] * dims[1] * dims[2]
+    value = N * args.steps / dt / 1e6
+    cores = os.cpu_count()
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=dt / args.steps * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, sample=f"{dims[0]}x{dims[1]}x{dims[2]} sub-box per step"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=cores, kind="oracle",
+                                  sample=f"each step = one FP64 oracle time step of a {dims[0]}x{dims[1]}x{dims[2]} "
+                                         f"sub-box of the workload ({len(w['particles'])} spheres)"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def build_context(lbm, w, precision, stream_handle, store_velocity=0):
+    p = dict(w["params"], store_velocity=store_velocity, diag_interval=0)
+    ctx = lbm.Context(p, precision, stream=stream_handle)
+    if w.get("mask") is not None:
+        ctx.lbm_set_solid_mask(w["mask"])
+    if w.get("particles"):
+        ctx.lbm_add_particles(w["particles"])
+    return ctx
+
+
+def timed_steps(torch, ctx, stream, K, profile):
+    """K steps between CUDA events on the context's stream."""
+    ctx.lbm_profile(1 if profile else 0)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.lbm_step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.lbm_profile_read() if profile else None
+    launches = ctx.lbm_last_launch_count()
+    ctx.lbm_profile(0)
+    return ms, prof, launches
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "fp64"], default="fp32")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit and batched extra measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    # CPU baseline first (no process forked after the GPU is touched)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample()
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2505_10171_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2505_10171_gb300 import lbm
+    from paper_2505_10171_gb300 import workloads as W
+
+    stream = torch.cuda.Stream()
+    w = W.cfg2()
+    N = 256 * 128 * 128
+    ctx = build_context(lbm, w, args.precision, stream.cuda_stream)
+    ctx.lbm_init_fields(w["phi"])
+    ctx.lbm_step(args.warmup)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    ms, prof, launches = timed_steps(torch, ctx, stream, args.steps, profile=True)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    # the same K steps replayed from the captured graph (no per-kernel events)
+    ms_graph, _, launches_graph = timed_steps(torch, ctx, stream, args.steps, profile=False)
+    diag = ctx.lbm_diagnostics()
+    ctx.close()
+
+    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    peaks = measured_peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    dom_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
+    dom_bytes = algorithmic_bytes_per_node(dom, args.precision) * N
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
+    step_bytes = 76 * ELEM[args.precision] * N
+    roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=hbm, unit="GB/s",
+                    frac=(achieved / hbm) if achieved else None, traffic=None, peak_source=peak_src,
+                    algorithmic_bytes_per_launch=dom_bytes, avg_launch_ms=dom_ms)
+    stage_ms = {k: round(v["ms"] / max(1, v["launches"]), 5) for k, v in prof.items() if v["launches"]}
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype=DTYPE[args.precision], data="synthetic",
+                config=dict(workload=WORKLOAD, nodes=N, precision=f"{args.precision} offset population storage",
+                            parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                            l2="inputs larger than L2 (populations %.0f MB)" % (2 * step_bytes / 2 / 1e6)),
+                roofline=roofline,
+                step_roofline_frac=(value * 1e6 * step_bytes / N) / (hbm * 1e9),
+                stage_ms_per_launch=stage_ms,
+                value_graph_replay=world * N * args.steps / (ms_graph * 1e-3) / 1e6,
+                gpu_launches=launches, clocks=clk, mass=dict(rho_a=diag[0], rho_b=diag[1]))
+    if cpu:
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line["e2e"] = e2e_measure(torch, lbm, W, args, stream)
+        if not args.no_extra and world == 1:
+            line["extra"] = extra_measure(torch, lbm, W, args, stream, N)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def e2e_measure(torch, lbm, W, args, stream):
+    """The same metric through the C ABI with host buffers: pinned-host upload of
+    the initial order parameter, K steps each followed by a device-to-host read of
+    the per-particle force records, and a final host read of phi."""
+    w = W.cfg2()
+    N = 256 * 128 * 128
+    phi_h = torch.from_numpy(w["phi"]).pin_memory().numpy()
+    out_h = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    ctx = build_context(lbm, w, args.precision, stream.cuda_stream)
+    ctx.lbm_init_fields(phi_h)
+    ctx.lbm_step(args.warmup)
+    torch.cuda.synchronize()
+    K = args.steps
+    t0 = time.perf_counter()
+    ctx.lbm_init_fields(phi_h)
+    for _ in range(K):
+        ctx.lbm_step(1)
+        ctx.lbm_particle_forces()
+    ctx.lbm_read_fields(lbm.FIELD_PHI, out=out_h)
+    dt = time.perf_counter() - t0
+    nparts = len(w["particles"])
+    ctx.close()
+    return dict(value=N * K / dt / 1e6, unit=UNIT, h2d_bytes_per_step=8 * N / K,
+                d2h_bytes_per_step=8 * lbm.PARTICLE_RECORD * nparts + 8 * N / K)
+
+
+def extra_measure(torch, lbm, W, args, stream, N):
+    """FP16/BF16 offset storage on the same workload, and the batched sweep."""
+    out = {}
+    K = max(50, args.steps // 4)
+    for prec in ("fp16", "bf16"):
+        w = W.cfg2()
+        ctx = build_context(lbm, w, prec, stream.cuda_stream)
+        ctx.lbm_init_fields(w["phi"])
+        ctx.lbm_step(args.warmup)
+        ms, prof, _ = timed_steps(torch, ctx, stream, K, profile=True)
+        ms_g, _, _ = timed_steps(torch, ctx, stream, K, profile=False)
+        ctx.close()
+        col = prof["collide"]
+        cms = col["ms"] / max(1, col["launches"])
+        out[prec] = dict(value=N * K / (ms * 1e-3) / 1e6, value_graph_replay=N * K / (ms_g * 1e-3) / 1e6,
+                         collide_ms=cms, collide_gbs=76 * 2 * N / (cms * 1e-3) / 1e9, steps=K)
+    ws = W.cfg4()
+    params = [dict(w["params"], store_velocity=0) for w in ws]
+    ctx = lbm.Context(params, "fp16", stream=stream.cuda_stream)
+    nodes = 0
+    for k, w in enumerate(ws):
+        ctx.lbm_add_particles(w["particles"], inst=k)
+        ctx.lbm_init_fields(w["phi"], inst=k)
+        nodes += ctx.num_nodes(k)
+    ctx.lbm_step(args.warmup)
+    Kb = max(20, args.steps // 20)
+    ms_g, _, _ = timed_steps(torch, ctx, stream, Kb, profile=False)
+    ctx.close()
+    out["batched_fp16"] = dict(value=nodes * Kb / (ms_g * 1e-3) / 1e6, unit=UNIT, instances=len(ws), nodes=nodes,
+                               steps=Kb)
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,226 @@
+/*
+ * lbm.h - C ABI of the GB300 (sm_103a) hot path of the coupled colour-gradient
+ * lattice Boltzmann / discrete element method for droplet-particle
+ * interactions on solid surfaces (Naga, Zhang, Yang, Kusumaatmaja,
+ * arXiv 2505.10171).
+ *
+ * One context holds one or more independent simulation instances (a batch of
+ * uneven domains is stepped together).  Each instance is a periodic
+ * nx x ny x nz D3Q19 lattice with two fluid components a (phi = +1) and b
+ * (phi = -1), an optional solid substrate at the node plane z = 0, optional
+ * static solid nodes, and up to LBM_MAX_PARTICLES rigid spheres.
+ *
+ * Conventions shared by every entry point:
+ *  - Fields are z-major: node (x, y, z) sits at index (z*ny + y)*nx + x, and a
+ *    vector field is three such blocks (x, y, z components).  Every value that
+ *    crosses this boundary is IEEE double, whatever the storage precision.
+ *  - Populations crossing the boundary are f^a_i then f^b_i, each [19][N], in
+ *    the velocity order LBM_C below.
+ *  - The caller owns every host buffer and every device buffer it passes; the
+ *    library owns all device memory it allocates (released by lbm_destroy).
+ *  - No C++ exception crosses this boundary.  Every call returns an
+ *    lbm_status; lbm_last_error() gives a one-line description of the last
+ *    failure on a context.  A device-side instability (non-finite or
+ *    non-positive density) or an illegal particle displacement sets a sticky
+ *    status reported by the next synchronising call.
+ *  - lbm_step is asynchronous on the context's stream; the read functions
+ *    synchronise that stream.
+ *  - A context is not thread-safe: calls on one context must not overlap.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_Q 19
+#define LBM_MAX_PARTICLES 61
+
+/* D3Q19 velocity order of every population array at this boundary
+ * (Sec. IV: D3Q19 after Krueger et al.): rest, +-x, +-y, +-z, then the twelve
+ * face diagonals in opposite pairs. */
+#define LBM_C                                                                  \
+    {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1},       \
+     {0, 0, -1}, {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},    \
+     {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1},  \
+     {0, -1, 1}}
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,         /* invalid argument or physically invalid parameter */
+    LBM_ERR_OOM = 2,         /* device allocation failed                        */
+    LBM_ERR_CUDA = 3,        /* CUDA runtime error                              */
+    LBM_ERR_STATE = 4,       /* call not valid in the current state             */
+    LBM_ERR_UNSTABLE = 5,    /* non-finite/non-positive density seen on device  */
+    LBM_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                   */
+    LBM_ERR_UNSUPPORTED = 7  /* feature or precision not available              */
+} lbm_status;
+
+/* Population storage.  FP64 and FP32 store f_i/(w_i rho0) - 1 and
+ * (f^a_i - f^b_i)/(w_i rho0); the 16-bit forms store the same offsets in
+ * half or bfloat16 with FP32 collision arithmetic.  Particle sums, the DEM and
+ * mass sums are FP64 in every form. */
+typedef enum {
+    LBM_FP64 = 0,
+    LBM_FP32 = 1,
+    LBM_FP16_OFFSET = 2,
+    LBM_BF16_OFFSET = 3
+} lbm_precision;
+
+/* Physical parameters of one instance (lattice units, dt = dx = 1).
+ * Table I of the paper gives the ranges used there. */
+typedef struct {
+    int nx, ny, nz;            /* lattice size, periodic in x, y and z (Sec. VI A)       */
+    int wall_z0;               /* 1: node plane z = 0 is the substrate; its halfway wall  */
+                               /*    sits at z = 0.5 (and z = nz - 0.5 through periodicity) */
+    double wall_velocity[3];   /* substrate velocity (moving-wall bounce-back, Sec. V A)  */
+    double theta_wall_deg;     /* substrate contact angle, measured in phase a (Sec. V D) */
+    double rho0;               /* reference density                                       */
+    double nu_a, nu_b;         /* kinematic viscosities; eta = rho0 nu, harmonic mean     */
+                               /*    in phi (Sec. IV); must be > 0                         */
+    double sigma;              /* interfacial tension (CSF force, Sec. IV)                */
+    double beta;               /* recolouring segregation parameter in [0, 1] (Sec. IV)   */
+    double cap_norm;           /* capillary prefactor C of Sec. V E; 0 selects (9/2) k beta */
+                               /*    with k = (1 + sqrt 2)/18                               */
+    double body_force_a[3];    /* force density on phase a, weighted by (1 + phi)/2       */
+    double body_force_b[3];    /* force density on phase b, weighted by (1 - phi)/2       */
+    double kn, kt, kr;         /* DEM normal / sliding / rolling stiffness (Sec. III)     */
+    double gn, gt, gr;         /* DEM damping constants                                   */
+    double mu_s, mu_r;         /* sliding and rolling friction coefficients               */
+    double delta_R;            /* mechanical minus hydrodynamic radius (Sec. V G)         */
+    double g_particle[3];      /* external force on every particle (gravity, Sec. VI A)   */
+    double grad_eps;           /* |grad phi| below which the interface normal is zero;     */
+                               /*    0 selects 1e-10 (FP64) or 1e-6 (other precisions)     */
+    double wet_phi_max;        /* wetting applied at nodes with |phi| < this; 0 -> 0.99   */
+    int store_velocity;        /* 1: keep the collision velocity for lbm_read_fields(U)   */
+    int diag_interval;         /* > 0: FP64 mass sums every that many steps               */
+} lbm_params;
+
+/* One rigid sphere (Sec. III, V).  R_c = R_p + delta_R; m = rho_p 4/3 pi R_p^3;
+ * I = 2/5 m R_p^2.  kinematic = 1 prescribes the motion (v, w kept constant). */
+typedef struct {
+    double x[3], v[3], w[3];
+    double R_p, rho_p, theta_deg;
+    int kinematic;
+} lbm_particle;
+
+/* lbm_read_fields mask bits; the output holds the selected fields one after
+ * another in this bit order. */
+enum {
+    LBM_FIELD_RHO_A = 1,   /* sum_i f^a_i of the current state          [N]    */
+    LBM_FIELD_RHO_B = 2,   /* sum_i f^b_i                                [N]    */
+    LBM_FIELD_PHI = 4,     /* (rho^a - rho^b)/(rho^a + rho^b)            [N]    */
+    LBM_FIELD_U = 8,       /* velocity of the last collision (Sec. IV)   [3][N] */
+    LBM_FIELD_POPS = 16,   /* f^a then f^b, LBM_C order                  [38][N]*/
+    LBM_FIELD_OWNER = 32   /* 0 fluid, 1 static solid, 2+p particle p    [N]    */
+};
+
+/* Number of doubles lbm_particle_forces writes per particle:
+ * F_eta[3] T_eta[3] (momentum exchange, Sec. V B), F_sigma[3] T_sigma[3]
+ * (capillary, Sec. V E), F_c[3] T_c[3] (contact, Sec. III), x[3] v[3] w[3],
+ * orientation quaternion q[4] (w, x, y, z), m. */
+#define LBM_PARTICLE_RECORD 32
+
+/* Create a context of n_instances instances; params points to n_instances
+ * records (uneven sizes allowed).  stream is a cudaStream_t (NULL: the
+ * library creates its own).  Validates every parameter (nu > 0, beta in
+ * [0, 1], sizes > 0, finite values) -> LBM_ERR_ARG; allocates all lattice
+ * memory -> LBM_ERR_OOM.  Populations start at rest with phi = -1 everywhere
+ * until lbm_init_fields. */
+lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision prec,
+                      void *stream, lbm_ctx **out);
+
+/* Release all device memory of the context (NULL is ignored). */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* One-line description of the last error on ctx (never NULL). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Mark static solid nodes of an instance (mask [N] host bytes, nonzero =
+ * solid, e.g. a tube wall), in addition to the substrate plane.  Must come
+ * before lbm_add_particles. */
+lbm_status lbm_set_solid_mask(lbm_ctx *ctx, int inst, const uint8_t *mask);
+
+/* Initialise the populations of an instance to the equilibrium (Sec. V C
+ * form) of the given host fields: phi [N], rho [N] (NULL: rho0), u [3][N]
+ * (NULL: at rest); rho^{a,b} = rho (1 +- phi)/2.  When pops is non-NULL it
+ * holds f^a then f^b ([38][N], LBM_C order) and is stored instead (resume).
+ * Host buffers; synchronous. */
+lbm_status lbm_init_fields(lbm_ctx *ctx, int inst, const double *phi, const double *rho,
+                           const double *u, const double *pops);
+
+/* As lbm_init_fields with device pointers (FP64), enqueued on the context's
+ * stream; the buffers must stay valid until the stream reaches the call. */
+lbm_status lbm_init_fields_device(lbm_ctx *ctx, int inst, const double *phi, const double *rho,
+                                  const double *u);
+
+/* Add n spheres to an instance (Sec. III, V).  Checks (-> LBM_ERR_ARG):
+ * R_p > 0, rho_p > 0, 0 < theta < 180, hydrodynamic spheres clear of each
+ * other and of the substrate, gamma_n < 2 sqrt(k_n m) and a collision time
+ * t_c >= 10 (Sec. V G), at most LBM_MAX_PARTICLES per instance.  Only before
+ * the first lbm_step (-> LBM_ERR_STATE). */
+lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *parts);
+
+/* Advance every instance by nsteps coupled time steps (Sec. IV-V and Fig. 5
+ * order: streaming with bounce-back, momentum exchange, order parameter,
+ * gradient with wetting, curvature and CSF force, MRT collision with Guo
+ * forcing, recolouring, capillary force, DEM, geometry update and refill).
+ * Asynchronous on the context's stream; replays a captured CUDA graph. */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* Per-particle record (LBM_PARTICLE_RECORD doubles each) of an instance after
+ * the last step; out holds n_particles records.  Synchronises. */
+lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out);
+
+/* Read the fields selected by mask (LBM_FIELD_*) of an instance into host
+ * memory, FP64.  Solid nodes read 0 for the density, phi and population
+ * fields.  LBM_FIELD_U requires store_velocity (-> LBM_ERR_STATE).
+ * Synchronises. */
+lbm_status lbm_read_fields(lbm_ctx *ctx, int inst, unsigned mask, double *out);
+
+/* As lbm_read_fields into a device buffer; enqueued on the stream, no sync. */
+lbm_status lbm_read_fields_device(lbm_ctx *ctx, int inst, unsigned mask, double *out);
+
+/* Number of particles of an instance, or -1 for a bad instance index. */
+int lbm_num_particles(const lbm_ctx *ctx, int inst);
+
+/* Nodes (nx*ny*nz) of an instance, or -1. */
+long long lbm_num_nodes(const lbm_ctx *ctx, int inst);
+
+/* FP64 diagnostics of an instance, from the last time they were taken
+ * (every diag_interval steps, or now when diag_interval is 0):
+ * out[0] = sum rho^a, out[1] = sum rho^b over fluid nodes, out[2] = steps
+ * taken so far, out[3] = sticky device status bits.  Synchronises. */
+lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
+
+/* Launch-shape override of the fluid kernels (block size in threads, a
+ * multiple of 32 in [64, 1024]); 0 restores the default.  Invalidates the
+ * captured step graph. */
+lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads);
+
+/* Count of kernel launches the last lbm_step call enqueued (graph nodes
+ * included); for accounting in benchmarks. */
+long long lbm_last_launch_count(const lbm_ctx *ctx);
+
+/* Per-kernel timing.  With enable = 1, later lbm_step calls launch eagerly
+ * (no graph replay) and bracket every kernel with CUDA events on the
+ * context's stream; enabling again clears the record.  Synchronises. */
+lbm_status lbm_profile(lbm_ctx *ctx, int enable);
+
+/* Read the per-kernel record since lbm_profile(ctx, 1): for stage k (launch
+ * order within a step: order parameter, solid phi, gradient+wetting,
+ * collision, momentum exchange, capillary force, DEM, geometry owner,
+ * geometry boundary, refill) out[2k] = launches, out[2k+1] = total device
+ * milliseconds; at most max_stages stages are written.  Synchronises. */
+lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

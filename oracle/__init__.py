@@ -286,3 +286,22 @@ def wetting_rotate(g, ns, theta_rad):
 def omega_of_phi(phi, rho, **kw):
     p = make_params(1, 1, 1, **kw)
     return lib().or_omega_of_phi(ct.byref(p), float(phi), float(rho))
+
+
+SIM_KEYS = ("wall_z0", "wall_velocity", "theta_wall_deg", "rho0", "nu_a", "nu_b", "sigma", "beta",
+            "body_force_a", "body_force_b", "kn", "kt", "kr", "gn", "gt", "gr", "mu_s", "mu_r", "delta_R",
+            "g_particle")
+
+
+def from_workload(w) -> OracleSim:
+    """OracleSim initialised from a workload dict (params, phi, optional rho, u,
+    mask, particles) as drawn by the seeded input generators."""
+    p = w["params"]
+    s = OracleSim(p["nx"], p["ny"], p["nz"], **{k: p[k] for k in SIM_KEYS if k in p})
+    if w.get("mask") is not None:
+        s.set_static_solid(w["mask"])
+    for q in w.get("particles", []):
+        s.add_particle(q["x"], q["R"], rho_p=q.get("rho_p", 0.125), theta_deg=q.get("theta_deg", 90.0),
+                       v=q.get("v", (0, 0, 0)), w=q.get("w", (0, 0, 0)), kinematic=q.get("kinematic", False))
+    s.init_fields(w["phi"], w.get("rho"), w.get("u"))
+    return s

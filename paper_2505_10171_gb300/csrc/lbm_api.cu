@@ -1,0 +1,947 @@
+// Host runtime and C ABI (include/lbm.h) of the sm_103a LBM-DEM library:
+// context and device memory, parameter validation, the per-step launch
+// sequence (captured once into a CUDA graph of two steps and replayed), field
+// initialisation / read-out kernels and FP64 diagnostics.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.cuh"
+
+using namespace lbmg;
+
+struct lbm_ctx {
+    lbm_precision prec;
+    int n_inst;
+    std::vector<lbm_params> P;
+    std::vector<InstDev> inst_h;
+    InstDev *inst_d = nullptr;
+    long long Ntot = 0, n_blocks = 0;
+    int bt = 256;
+    size_t elem = 8, real_sz = 8;
+    uint8_t *flags = nullptr;
+    void *pop[2] = {nullptr, nullptr};
+    void *phi = nullptr, *grad = nullptr, *u = nullptr;
+    std::vector<PartDev> parts_h;
+    PartDev *parts_d = nullptr;
+    double *mem_part = nullptr, *cap_part = nullptr, *hist = nullptr;
+    unsigned *status = nullptr;
+    int mem_blocks = 1, geom_blocks = 1, geom_side = 1;
+    int cur = 0;
+    long long steps = 0;
+    bool stepped = false;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_launches = 0;
+    long long last_launches = 0;
+    double *scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double *diag_d = nullptr;       // [n_inst][2]
+    double *diag_part = nullptr;    // [DIAG_BLOCKS][2]
+    std::vector<long long> diag_step;
+    std::string err = "no error";
+    // profile mode: eager launches bracketed by CUDA events on the stream
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
+    cudaEvent_t ev_open[N_STAGES] = {};
+};
+
+static const int DIAG_BLOCKS = 512;
+
+static lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m)
+{
+    if (c) c->err = m;
+    return s;
+}
+
+#define CU(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess)                                                                         \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,             \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+    } while (0)
+
+static Lattice make_lattice(const lbm_ctx *c)
+{
+    Lattice L;
+    L.inst = c->inst_d;
+    L.n_inst = c->n_inst;
+    L.n_blocks = c->n_blocks;
+    L.bt = c->bt;
+    L.flags = c->flags;
+    L.pop[0] = c->pop[0];
+    L.pop[1] = c->pop[1];
+    L.phi = c->phi;
+    L.grad = c->grad;
+    L.u = c->u;
+    L.Ntot = c->Ntot;
+    L.parts = c->parts_d;
+    L.n_parts = (int)c->parts_h.size();
+    L.mem_blocks = c->mem_blocks;
+    L.geom_blocks = c->geom_blocks;
+    L.geom_side = c->geom_side;
+    L.mem_part = c->mem_part;
+    L.cap_part = c->cap_part;
+    L.hist = c->hist;
+    L.status = c->status;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// init / read-out / diagnostics kernels
+// ---------------------------------------------------------------------------
+struct AbiMap {
+    int dev[Q];  // device index of ABI velocity a
+};
+
+static AbiMap abi_map()
+{
+    static const int C[Q][3] = LBM_C;
+    AbiMap m;
+    for (int a = 0; a < Q; a++)
+        for (int i = 0; i < Q; i++)
+            if (cx(i) == C[a][0] && cy(i) == C[a][1] && cz(i) == C[a][2]) m.dev[a] = i;
+    return m;
+}
+
+template <class S>
+__global__ void k_init(Lattice L, int cur, int inst, const double *phi, const double *rho, const double *u,
+                       const double *pops, AbiMap map)
+{
+    using R = typename Store<S>::real;
+    const InstDev &I = L.inst[inst];
+    const long long N = I.N;
+    S *pop = (S *)L.pop[cur] + NPOP * I.node_off;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        if (pops) {
+            for (int a = 0; a < Q; a++) {
+                int i = map.dev[a];
+                double w = wgt<double>(i) * I.rho0;
+                double fa = pops[(long long)a * N + n], fb = pops[(long long)(Q + a) * N + n];
+                Store<S>::st(pop + (long long)i * N + n, (R)((fa + fb) / w - 1.0));
+                Store<S>::st(pop + (long long)(Q + i) * N + n, (R)((fa - fb) / w));
+            }
+            continue;
+        }
+        double ph = phi[n];
+        double r = rho ? rho[n] : I.rho0;
+        double uu[3] = {u ? u[n] : 0.0, u ? u[N + n] : 0.0, u ? u[2 * N + n] : 0.0};
+        double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+        double rr = r / I.rho0;
+        for (int i = 0; i < Q; i++) {
+            double cu = cx(i) * uu[0] + cy(i) * uu[1] + cz(i) * uu[2];
+            double e = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
+            // f^{a,b} = feq(rho (1 +- phi)/2, u): total rho e w, colour rho phi e w
+            Store<S>::st(pop + (long long)i * N + n, (R)(rr * e - 1.0));
+            Store<S>::st(pop + (long long)(Q + i) * N + n, (R)(rr * ph * e));
+        }
+        if (I.store_u) {
+            R *U = (R *)L.u;
+            bool fl = (L.flags[I.node_off + n] & OWNER_MASK) == OWN_FLUID;
+            for (int a = 0; a < 3; a++) U[a * L.Ntot + I.node_off + n] = fl ? (R)uu[a] : (R)0;
+        }
+    }
+}
+
+template <class S>
+__global__ void k_read(Lattice L, int cur, int inst, unsigned mask, double *out, AbiMap map)
+{
+    using R = typename Store<S>::real;
+    const InstDev &I = L.inst[inst];
+    const long long N = I.N;
+    const S *pop = (const S *)L.pop[cur] + NPOP * I.node_off;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        const uint8_t f = L.flags[I.node_off + n];
+        const bool fluid = (f & OWNER_MASK) == OWN_FLUID;
+        double ra = 0.0, rb = 0.0;
+        if (fluid)
+            for (int i = 0; i < Q; i++) {
+                double w = wgt<double>(i) * I.rho0;
+                double Fv = (double)Store<S>::ld(pop + (long long)i * N + n);
+                double Gv = (double)Store<S>::ld(pop + (long long)(Q + i) * N + n);
+                ra += 0.5 * w * (1.0 + Fv + Gv);
+                rb += 0.5 * w * (1.0 + Fv - Gv);
+            }
+        long long off = 0;
+        if (mask & LBM_FIELD_RHO_A) { out[off + n] = ra; off += N; }
+        if (mask & LBM_FIELD_RHO_B) { out[off + n] = rb; off += N; }
+        if (mask & LBM_FIELD_PHI) { out[off + n] = fluid ? (ra - rb) / (ra + rb) : 0.0; off += N; }
+        if (mask & LBM_FIELD_U) {
+            const R *U = (const R *)L.u;
+            for (int a = 0; a < 3; a++) out[off + a * N + n] = (double)U[a * L.Ntot + I.node_off + n];
+            off += 3 * N;
+        }
+        if (mask & LBM_FIELD_POPS) {
+            for (int a = 0; a < Q; a++) {
+                int i = map.dev[a];
+                double w = wgt<double>(i) * I.rho0;
+                double Fv = fluid ? (double)Store<S>::ld(pop + (long long)i * N + n) : 0.0;
+                double Gv = fluid ? (double)Store<S>::ld(pop + (long long)(Q + i) * N + n) : 0.0;
+                out[off + (long long)a * N + n] = fluid ? 0.5 * w * (1.0 + Fv + Gv) : 0.0;
+                out[off + (long long)(Q + a) * N + n] = fluid ? 0.5 * w * (1.0 + Fv - Gv) : 0.0;
+            }
+            off += (long long)NPOP * N;
+        }
+        if (mask & LBM_FIELD_OWNER) { out[off + n] = (double)(f & OWNER_MASK); off += N; }
+    }
+}
+
+// FP64 component masses over fluid nodes: fixed grid of partial sums, then a
+// fixed-order single-block sum (deterministic)
+template <class S>
+__global__ void k_mass_partial(Lattice L, int cur, int inst, double *part)
+{
+    const InstDev &I = L.inst[inst];
+    const long long N = I.N;
+    const S *pop = (const S *)L.pop[cur] + NPOP * I.node_off;
+    double sa = 0.0, sb = 0.0;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
+        for (int i = 0; i < Q; i++) {
+            double w = wgt<double>(i) * I.rho0;
+            double Fv = (double)Store<S>::ld(pop + (long long)i * N + n);
+            double Gv = (double)Store<S>::ld(pop + (long long)(Q + i) * N + n);
+            sa += 0.5 * w * (1.0 + Fv + Gv);
+            sb += 0.5 * w * (1.0 + Fv - Gv);
+        }
+    }
+    __shared__ double sh[2][256];
+    sh[0][threadIdx.x] = sa;
+    sh[1][threadIdx.x] = sb;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sh[0][0];
+        part[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
+__global__ void k_mass_final(const double *part, int nblk, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < nblk; i++) { a += part[2 * i]; b += part[2 * i + 1]; }
+        out[0] = a;
+        out[1] = b;
+    }
+}
+
+namespace lbmg {
+template <class S>
+void launch_init_fields(const Lattice &L, int cur, int inst, long long N, const double *phi, const double *rho,
+                        const double *u, const double *pops, cudaStream_t st)
+{
+    long long blocks = (N + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_init<S><<<(unsigned)blocks, 256, 0, st>>>(L, cur, inst, phi, rho, u, pops, abi_map());
+}
+template <class S>
+void launch_read_fields(const Lattice &L, int cur, int inst, long long N, unsigned mask, double *out,
+                        cudaStream_t st)
+{
+    long long blocks = (N + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    k_read<S><<<(unsigned)blocks, 256, 0, st>>>(L, cur, inst, mask, out, abi_map());
+}
+template <class S>
+void launch_mass_sums(const Lattice &L, int cur, int inst, long long N, double *partial, int nblk, double *out,
+                      cudaStream_t st)
+{
+    (void)N;
+    k_mass_partial<S><<<nblk, 256, 0, st>>>(L, cur, inst, partial);
+    k_mass_final<<<1, 32, 0, st>>>(partial, nblk, out);
+}
+}  // namespace lbmg
+
+// ---------------------------------------------------------------------------
+// precision dispatch
+// ---------------------------------------------------------------------------
+template <class F>
+static void dispatch(lbm_precision p, F &&f)
+{
+    switch (p) {
+    case LBM_FP64: f((double *)nullptr); break;
+    case LBM_FP32: f((float *)nullptr); break;
+    case LBM_FP16_OFFSET: f((__half *)nullptr); break;
+    case LBM_BF16_OFFSET: f((__nv_bfloat16 *)nullptr); break;
+    }
+}
+
+static cudaEvent_t next_event(lbm_ctx *c)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+static void profile_mark(void *self, int stage, int after)
+{
+    lbm_ctx *c = (lbm_ctx *)self;
+    cudaEvent_t e = next_event(c);
+    cudaEventRecord(e, c->stream);
+    if (!after) c->ev_open[stage] = e;
+    else c->ev_pairs.push_back({stage, {c->ev_open[stage], e}});
+}
+
+static void enqueue_step(lbm_ctx *c, long long *launches)
+{
+    Lattice L = make_lattice(c);
+    const int cur = c->cur;
+    Marker mk;
+    if (c->profile) {
+        mk.fn = profile_mark;
+        mk.self = c;
+    }
+    dispatch(c->prec, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        launch_fluid_step<S>(L, cur, c->stream, launches, mk);
+        launch_particle_forces<S>(L, cur, c->stream, launches, mk);
+        launch_dem(L, c->stream, launches, mk);
+        launch_geometry<S>(L, cur ^ 1, c->stream, launches, mk);
+    });
+    c->cur ^= 1;
+}
+
+static lbm_status take_diag(lbm_ctx *ctx)
+{
+    Lattice L = make_lattice(ctx);
+    for (int k = 0; k < ctx->n_inst; k++) {
+        dispatch(ctx->prec, [&](auto *tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            launch_mass_sums<S>(L, ctx->cur, k, ctx->inst_h[k].N, ctx->diag_part, DIAG_BLOCKS, ctx->diag_d + 2 * k,
+                                ctx->stream);
+        });
+        ctx->diag_step[k] = ctx->steps;
+    }
+    CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+static bool finite3(const double *v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+static lbm_status validate(lbm_ctx *ctx, const lbm_params &p, int k)
+{
+    char b[160];
+    auto bad = [&](const char *what) {
+        snprintf(b, sizeof b, "instance %d: %s", k, what);
+        return fail(ctx, LBM_ERR_ARG, b);
+    };
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return bad("nx, ny, nz must be >= 1");
+    if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return bad("lattice too large");
+    if (p.wall_z0 && p.nz < 3) return bad("a substrate needs nz >= 3");
+    if (!(p.nu_a > 0.0) || !(p.nu_b > 0.0) || !std::isfinite(p.nu_a) || !std::isfinite(p.nu_b))
+        return bad("viscosities must be finite and > 0 (tau > 1/2)");
+    if (!(p.rho0 > 0.0) || !std::isfinite(p.rho0)) return bad("rho0 must be > 0");
+    if (!(p.beta >= 0.0 && p.beta <= 1.0)) return bad("beta must be in [0, 1]");
+    if (!(p.sigma >= 0.0) || !std::isfinite(p.sigma)) return bad("sigma must be finite and >= 0");
+    if (!(p.theta_wall_deg > 0.0 && p.theta_wall_deg < 180.0)) return bad("theta_wall must be in (0, 180)");
+    if (!finite3(p.wall_velocity) || !finite3(p.body_force_a) || !finite3(p.body_force_b) || !finite3(p.g_particle))
+        return bad("non-finite vector parameter");
+    if (!(p.kn >= 0 && p.kt >= 0 && p.kr >= 0 && p.gn >= 0 && p.gt >= 0 && p.gr >= 0 && p.mu_s >= 0 &&
+          p.mu_r >= 0 && p.delta_R >= 0))
+        return bad("DEM constants must be >= 0");
+    if (p.grad_eps < 0 || p.wet_phi_max < 0 || p.cap_norm < 0 || p.diag_interval < 0)
+        return bad("negative grad_eps / wet_phi_max / cap_norm / diag_interval");
+    return LBM_OK;
+}
+
+static const char *status_text(unsigned s)
+{
+    if (s & ST_UNSTABLE) return "device: non-finite or non-positive density (unstable run)";
+    if (s & ST_DISPLACEMENT) return "device: a particle moved more than 2 lattice units in one step";
+    return "device status";
+}
+
+static lbm_status check_status(lbm_ctx *ctx)
+{
+    unsigned s = 0;
+    CU(cudaMemcpyAsync(&s, ctx->status, sizeof s, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (s) return fail(ctx, LBM_ERR_UNSTABLE, status_text(s));
+    return LBM_OK;
+}
+
+static void drop_graph(lbm_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void lbm_destroy(lbm_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+    cudaFree(ctx->inst_d);
+    cudaFree(ctx->flags);
+    cudaFree(ctx->pop[0]);
+    cudaFree(ctx->pop[1]);
+    cudaFree(ctx->phi);
+    cudaFree(ctx->grad);
+    cudaFree(ctx->u);
+    cudaFree(ctx->parts_d);
+    cudaFree(ctx->mem_part);
+    cudaFree(ctx->cap_part);
+    cudaFree(ctx->hist);
+    cudaFree(ctx->status);
+    cudaFree(ctx->scratch);
+    cudaFree(ctx->diag_d);
+    cudaFree(ctx->diag_part);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision prec, void *stream, lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!params || n_instances < 1) return LBM_ERR_ARG;
+    if (prec < LBM_FP64 || prec > LBM_BF16_OFFSET) return LBM_ERR_UNSUPPORTED;
+    lbm_ctx *ctx = new lbm_ctx();
+    ctx->prec = prec;
+    ctx->n_inst = n_instances;
+    ctx->P.assign(params, params + n_instances);
+    ctx->elem = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2);
+    ctx->real_sz = prec == LBM_FP64 ? 8 : 4;
+    ctx->diag_step.assign(n_instances, -1);
+    lbm_status st;
+    long long node_off = 0, blk = 0;
+    bool any_u = false;
+    for (int k = 0; k < n_instances; k++) {
+        const lbm_params &p = params[k];
+        if ((st = validate(ctx, p, k)) != LBM_OK) {
+            std::string m = ctx->err;
+            delete ctx;
+            (void)m;
+            return st;
+        }
+        InstDev I;
+        memset(&I, 0, sizeof I);
+        I.nx = p.nx; I.ny = p.ny; I.nz = p.nz;
+        I.N = (long long)p.nx * p.ny * p.nz;
+        I.node_off = node_off;
+        I.blk_start = blk;
+        I.wall_z0 = p.wall_z0;
+        I.store_u = p.store_velocity ? 1 : 0;
+        any_u |= I.store_u != 0;
+        I.rho0 = p.rho0;
+        I.sigma = p.sigma;
+        I.beta = p.beta;
+        I.cap_norm = p.cap_norm > 0.0 ? p.cap_norm : 4.5 * (1.0 + std::sqrt(2.0)) / 18.0 * p.beta;
+        I.eta_a = p.rho0 * p.nu_a;
+        I.eta_b = p.rho0 * p.nu_b;
+        for (int a = 0; a < 3; a++) {
+            I.body_a[a] = p.body_force_a[a];
+            I.body_b[a] = p.body_force_b[a];
+            I.wall_u[a] = p.wall_velocity[a];
+            I.g_part[a] = p.g_particle[a];
+        }
+        double th = p.theta_wall_deg * M_PI / 180.0;
+        I.cos_tw = std::cos(th);
+        I.sin_tw = std::sin(th);
+        I.grad_eps = p.grad_eps > 0.0 ? p.grad_eps : (prec == LBM_FP64 ? 1e-10 : 1e-6);
+        I.wet_max = p.wet_phi_max > 0.0 ? p.wet_phi_max : 0.99;
+        I.kn = p.kn; I.kt = p.kt; I.kr = p.kr;
+        I.gn = p.gn; I.gt = p.gt; I.gr = p.gr;
+        I.mu_s = p.mu_s; I.mu_r = p.mu_r; I.dR = p.delta_R;
+        ctx->inst_h.push_back(I);
+        node_off += I.N;
+        blk += (I.N + ctx->bt - 1) / ctx->bt;
+    }
+    ctx->Ntot = node_off;
+    ctx->n_blocks = blk;
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return LBM_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    auto alloc = [&](void **p, size_t bytes) -> lbm_status {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                        std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        return LBM_OK;
+    };
+    const size_t Nt = (size_t)ctx->Ntot;
+    if ((st = alloc((void **)&ctx->inst_d, sizeof(InstDev) * n_instances)) ||
+        (st = alloc((void **)&ctx->flags, Nt)) || (st = alloc(&ctx->pop[0], NPOP * Nt * ctx->elem)) ||
+        (st = alloc(&ctx->pop[1], NPOP * Nt * ctx->elem)) || (st = alloc(&ctx->phi, Nt * ctx->real_sz)) ||
+        (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
+        (st = alloc((void **)&ctx->diag_d, sizeof(double) * 2 * n_instances)) ||
+        (st = alloc((void **)&ctx->diag_part, sizeof(double) * 2 * DIAG_BLOCKS)) ||
+        (any_u && (st = alloc(&ctx->u, 3 * Nt * ctx->real_sz)))) {
+        std::string m = ctx->err;
+        lbm_destroy(ctx);
+        return st;
+    }
+    cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * n_instances, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream);
+    cudaMemsetAsync(ctx->phi, 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->grad, 0, 3 * Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->diag_d, 0, sizeof(double) * 2 * n_instances, ctx->stream);
+    if (ctx->u) cudaMemsetAsync(ctx->u, 0, 3 * Nt * ctx->real_sz, ctx->stream);
+    // flags: substrate plane, then boundary bits
+    std::vector<uint8_t> fl;
+    for (int k = 0; k < n_instances; k++) {
+        const InstDev &I = ctx->inst_h[k];
+        fl.assign((size_t)I.N, OWN_FLUID);
+        if (I.wall_z0)
+            for (long long n = 0; n < (long long)I.nx * I.ny; n++) fl[(size_t)n] = OWN_WALL;
+        cudaMemcpyAsync(ctx->flags + I.node_off, fl.data(), (size_t)I.N, cudaMemcpyHostToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+    }
+    Lattice L = make_lattice(ctx);
+    for (int k = 0; k < n_instances; k++) launch_boundary_full(L, k, ctx->inst_h[k].N, ctx->stream);
+    // populations at rest, phi = -1 (phase b) until lbm_init_fields
+    for (int k = 0; k < n_instances; k++) {
+        std::vector<double> ph((size_t)ctx->inst_h[k].N, -1.0);
+        double *d = nullptr;
+        if (cudaMalloc(&d, ph.size() * sizeof(double)) != cudaSuccess) {
+            lbm_destroy(ctx);
+            return LBM_ERR_OOM;
+        }
+        cudaMemcpyAsync(d, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream);
+        dispatch(prec, [&](auto *tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            launch_init_fields<S>(L, 0, k, ctx->inst_h[k].N, d, nullptr, nullptr, nullptr, ctx->stream);
+        });
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(d);
+    }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        lbm_destroy(ctx);
+        return LBM_ERR_CUDA;
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_solid_mask(lbm_ctx *ctx, int inst, const uint8_t *mask)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !mask) return fail(ctx, LBM_ERR_ARG, "bad instance or mask");
+    if (ctx->stepped || ctx->inst_h[inst].np > 0)
+        return fail(ctx, LBM_ERR_STATE, "solid mask must be set before particles and steps");
+    const InstDev &I = ctx->inst_h[inst];
+    std::vector<uint8_t> fl((size_t)I.N);
+    for (long long n = 0; n < I.N; n++) {
+        bool wall = I.wall_z0 && n < (long long)I.nx * I.ny;
+        fl[(size_t)n] = (wall || mask[n]) ? OWN_WALL : OWN_FLUID;
+    }
+    CU(cudaMemcpyAsync(ctx->flags + I.node_off, fl.data(), (size_t)I.N, cudaMemcpyHostToDevice, ctx->stream));
+    Lattice L = make_lattice(ctx);
+    launch_boundary_full(L, inst, I.N, ctx->stream);
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+static lbm_status ensure_scratch(lbm_ctx *ctx, size_t bytes)
+{
+    if (ctx->scratch_bytes >= bytes) return LBM_OK;
+    CU(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->scratch);
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    CU(cudaMalloc(&ctx->scratch, bytes));
+    ctx->scratch_bytes = bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields(lbm_ctx *ctx, int inst, const double *phi, const double *rho, const double *u,
+                           const double *pops)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || (!phi && !pops)) return fail(ctx, LBM_ERR_ARG, "bad instance or fields");
+    const long long N = ctx->inst_h[inst].N;
+    size_t need = (size_t)N * (pops ? NPOP : (1 + (rho ? 1 : 0) + (u ? 3 : 0))) * sizeof(double);
+    lbm_status s = ensure_scratch(ctx, need);
+    if (s) return s;
+    double *d = ctx->scratch, *dphi = nullptr, *drho = nullptr, *du = nullptr, *dpops = nullptr;
+    if (pops) {
+        dpops = d;
+        CU(cudaMemcpyAsync(dpops, pops, sizeof(double) * NPOP * N, cudaMemcpyHostToDevice, ctx->stream));
+    } else {
+        dphi = d;
+        d += N;
+        CU(cudaMemcpyAsync(dphi, phi, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+        if (rho) {
+            drho = d;
+            d += N;
+            CU(cudaMemcpyAsync(drho, rho, sizeof(double) * N, cudaMemcpyHostToDevice, ctx->stream));
+        }
+        if (u) {
+            du = d;
+            CU(cudaMemcpyAsync(du, u, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, ctx->stream));
+        }
+    }
+    Lattice L = make_lattice(ctx);
+    dispatch(ctx->prec, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        launch_init_fields<S>(L, ctx->cur, inst, N, dphi, drho, du, dpops, ctx->stream);
+    });
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_init_fields_device(lbm_ctx *ctx, int inst, const double *phi, const double *rho, const double *u)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !phi) return fail(ctx, LBM_ERR_ARG, "bad instance or fields");
+    Lattice L = make_lattice(ctx);
+    dispatch(ctx->prec, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        launch_init_fields<S>(L, ctx->cur, inst, ctx->inst_h[inst].N, phi, rho, u, nullptr, ctx->stream);
+    });
+    CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *parts)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || n < 0 || (n > 0 && !parts))
+        return fail(ctx, LBM_ERR_ARG, "bad instance or particle array");
+    if (ctx->stepped) return fail(ctx, LBM_ERR_STATE, "particles must be added before the first step");
+    InstDev &I = ctx->inst_h[inst];
+    if (I.np + n > LBM_MAX_PARTICLES) return fail(ctx, LBM_ERR_ARG, "too many particles in one instance");
+    const lbm_params &p = ctx->P[inst];
+    // existing particles of this instance (host copies)
+    std::vector<PartDev> mine;
+    for (auto &q : ctx->parts_h)
+        if (q.inst == inst) mine.push_back(q);
+    std::vector<PartDev> add;
+    char b[200];
+    for (int k = 0; k < n; k++) {
+        const lbm_particle &q = parts[k];
+        if (!(q.R_p > 0.0) || !(q.rho_p > 0.0) || !(q.theta_deg > 0.0 && q.theta_deg < 180.0) || !finite3(q.x) ||
+            !finite3(q.v) || !finite3(q.w))
+            return fail(ctx, LBM_ERR_ARG, "particle needs R_p > 0, rho_p > 0, 0 < theta < 180, finite state");
+        if (q.x[0] < 0 || q.x[0] >= p.nx || q.x[1] < 0 || q.x[1] >= p.ny || q.x[2] < 0 || q.x[2] >= p.nz)
+            return fail(ctx, LBM_ERR_ARG, "particle centre outside the domain");
+        if (2.0 * q.R_p + 2.0 >= std::min(p.nx, std::min(p.ny, p.nz)) && (p.nx > 1 && p.ny > 1 && p.nz > 1))
+            return fail(ctx, LBM_ERR_ARG, "particle larger than the domain");
+        if (p.wall_z0 && q.x[2] - q.R_p <= 0.5)
+            return fail(ctx, LBM_ERR_ARG, "particle intersects the substrate");
+        PartDev d;
+        memset(&d, 0, sizeof d);
+        for (int a = 0; a < 3; a++) {
+            d.x[a] = q.x[a]; d.v[a] = q.v[a]; d.w[a] = q.w[a]; d.x_old[a] = q.x[a];
+            d.Fp[a] = p.g_particle[a];
+        }
+        d.q[0] = 1.0;
+        d.R = q.R_p;
+        d.Rc = q.R_p + p.delta_R;
+        d.m = q.rho_p * 4.0 / 3.0 * M_PI * q.R_p * q.R_p * q.R_p;
+        d.I = 0.4 * d.m * q.R_p * q.R_p;
+        double th = q.theta_deg * M_PI / 180.0;
+        d.cos_t = std::cos(th);
+        d.sin_t = std::sin(th);
+        d.kin = q.kinematic ? 1 : 0;
+        d.inst = inst;
+        d.local = I.np + k;
+        // Sec. V G: gamma_n < 2 sqrt(k_n m) and a resolved collision time
+        if (!d.kin) {
+            if (!(p.gn < 2.0 * std::sqrt(p.kn * d.m)))
+                return fail(ctx, LBM_ERR_ARG, "gamma_n >= 2 sqrt(k_n m): no real collision time");
+            if (p.kn > 0.0) {
+                double wc = std::sqrt(p.kn / d.m - (p.gn / (2 * d.m)) * (p.gn / (2 * d.m)));
+                double tc = M_PI / wc;
+                if (tc < 10.0) {
+                    snprintf(b, sizeof b, "collision time t_c = %.3g < 10 steps (Sec. V G)", tc);
+                    return fail(ctx, LBM_ERR_ARG, b);
+                }
+            }
+        }
+        for (auto &o : mine) {
+            double dd[3] = {min_image(d.x[0] - o.x[0], p.nx), min_image(d.x[1] - o.x[1], p.ny),
+                            min_image(d.x[2] - o.x[2], p.nz)};
+            if (std::sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]) < d.R + o.R)
+                return fail(ctx, LBM_ERR_ARG, "particles overlap");
+        }
+        mine.push_back(d);
+        add.push_back(d);
+    }
+    // rebuild the global particle array grouped by instance
+    std::vector<PartDev> all;
+    for (int k = 0; k < ctx->n_inst; k++) {
+        int cnt = 0;
+        ctx->inst_h[k].part_off = (int)all.size();
+        for (auto &q : ctx->parts_h)
+            if (q.inst == k) { all.push_back(q); cnt++; }
+        if (k == inst)
+            for (auto &q : add) { all.push_back(q); cnt++; }
+        ctx->inst_h[k].np = cnt;
+    }
+    int hist = 0;
+    for (int k = 0; k < ctx->n_inst; k++) {
+        ctx->inst_h[k].hist_off = hist;
+        hist += ctx->inst_h[k].np * (ctx->inst_h[k].np + 1);
+    }
+    double Rmax = 0.0;
+    for (auto &q : all) Rmax = std::max(Rmax, q.R);
+    int mem_side = 2 * (int)std::ceil(Rmax) + 5;
+    for (auto &q : all) q.mem_side = mem_side;
+    ctx->parts_h = all;
+    ctx->mem_blocks = (int)(((long long)mem_side * mem_side * mem_side + PART_THREADS - 1) / PART_THREADS);
+    ctx->geom_side = 2 * (int)std::ceil(Rmax) + 4 * GEOM_MARGIN + 3;
+    long long gs3 = (long long)(ctx->geom_side + 2) * (ctx->geom_side + 2) * (ctx->geom_side + 2);
+    ctx->geom_blocks = (int)std::min<long long>((gs3 + PART_THREADS - 1) / PART_THREADS, 256);
+    const size_t np = all.size();
+    CU(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->parts_d);
+    cudaFree(ctx->mem_part);
+    cudaFree(ctx->cap_part);
+    cudaFree(ctx->hist);
+    ctx->parts_d = nullptr;
+    ctx->mem_part = ctx->cap_part = ctx->hist = nullptr;
+    CU(cudaMalloc((void **)&ctx->parts_d, sizeof(PartDev) * np));
+    CU(cudaMalloc((void **)&ctx->mem_part, sizeof(double) * 6 * np * ctx->mem_blocks));
+    CU(cudaMalloc((void **)&ctx->cap_part, sizeof(double) * 6 * np * CAP_BLOCKS));
+    CU(cudaMalloc((void **)&ctx->hist, sizeof(double) * 6 * std::max(hist, 1)));
+    CU(cudaMemsetAsync(ctx->hist, 0, sizeof(double) * 6 * std::max(hist, 1), ctx->stream));
+    CU(cudaMemsetAsync(ctx->mem_part, 0, sizeof(double) * 6 * np * ctx->mem_blocks, ctx->stream));
+    CU(cudaMemsetAsync(ctx->cap_part, 0, sizeof(double) * 6 * np * CAP_BLOCKS, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->parts_d, all.data(), sizeof(PartDev) * np, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    Lattice L = make_lattice(ctx);
+    launch_mark_particles(L, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
+    ctx->stepped = true;
+    long long launches = 0;
+    while (nsteps > 0) {
+        int interval = 0;
+        for (auto &p : ctx->P) interval = std::max(interval, p.diag_interval);
+        if (ctx->cur == 0 && nsteps >= 2 && !ctx->profile) {
+            if (!ctx->graph) {
+                cudaGraph_t g;
+                CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                long long l = 0;
+                enqueue_step(ctx, &l);
+                enqueue_step(ctx, &l);
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+                if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+                e = cudaGraphInstantiate(&ctx->graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+                ctx->graph_launches = l;
+            }
+            CU(cudaGraphLaunch(ctx->graph, ctx->stream));
+            launches += ctx->graph_launches;
+            nsteps -= 2;
+            ctx->steps += 2;
+            if (interval > 0 && (ctx->steps % interval == 0 || ctx->steps % interval == 1)) {
+                lbm_status s = take_diag(ctx);
+                if (s) return s;
+                launches += 2 * ctx->n_inst;
+            }
+        } else {
+            enqueue_step(ctx, &launches);
+            nsteps -= 1;
+            ctx->steps += 1;
+            if (interval > 0 && ctx->steps % interval == 0) {
+                lbm_status s = take_diag(ctx);
+                if (s) return s;
+                launches += 2 * ctx->n_inst;
+            }
+        }
+    }
+    ctx->last_launches = launches;
+    CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !out) return fail(ctx, LBM_ERR_ARG, "bad instance or output");
+    const InstDev &I = ctx->inst_h[inst];
+    if (I.np == 0) return LBM_OK;
+    std::vector<PartDev> h((size_t)I.np);
+    CU(cudaMemcpyAsync(h.data(), ctx->parts_d + I.part_off, sizeof(PartDev) * I.np, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    lbm_status s = check_status(ctx);
+    for (int p = 0; p < I.np; p++) {
+        double *o = out + (size_t)LBM_PARTICLE_RECORD * p;
+        const PartDev &q = h[(size_t)p];
+        for (int a = 0; a < 3; a++) {
+            o[a] = q.Feta[a]; o[3 + a] = q.Teta[a];
+            o[6 + a] = q.Fsig[a]; o[9 + a] = q.Tsig[a];
+            o[12 + a] = q.Fc[a]; o[15 + a] = q.Tc[a];
+            o[18 + a] = q.x[a]; o[21 + a] = q.v[a]; o[24 + a] = q.w[a];
+        }
+        for (int a = 0; a < 4; a++) o[27 + a] = q.q[a];
+        o[31] = q.m;
+    }
+    return s;
+}
+
+static size_t field_count(unsigned mask)
+{
+    size_t c = 0;
+    if (mask & LBM_FIELD_RHO_A) c += 1;
+    if (mask & LBM_FIELD_RHO_B) c += 1;
+    if (mask & LBM_FIELD_PHI) c += 1;
+    if (mask & LBM_FIELD_U) c += 3;
+    if (mask & LBM_FIELD_POPS) c += NPOP;
+    if (mask & LBM_FIELD_OWNER) c += 1;
+    return c;
+}
+
+lbm_status lbm_read_fields_device(lbm_ctx *ctx, int inst, unsigned mask, double *out)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !out || mask == 0 || (mask & ~63u))
+        return fail(ctx, LBM_ERR_ARG, "bad instance, mask or output");
+    if ((mask & LBM_FIELD_U) && !ctx->inst_h[inst].store_u)
+        return fail(ctx, LBM_ERR_STATE, "velocity read needs store_velocity = 1");
+    Lattice L = make_lattice(ctx);
+    dispatch(ctx->prec, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        launch_read_fields<S>(L, ctx->cur, inst, ctx->inst_h[inst].N, mask, out, ctx->stream);
+    });
+    CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_read_fields(lbm_ctx *ctx, int inst, unsigned mask, double *out)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !out) return fail(ctx, LBM_ERR_ARG, "bad instance or output");
+    const long long N = ctx->inst_h[inst].N;
+    size_t bytes = field_count(mask) * (size_t)N * sizeof(double);
+    lbm_status s = ensure_scratch(ctx, bytes);
+    if (s) return s;
+    s = lbm_read_fields_device(ctx, inst, mask, ctx->scratch);
+    if (s) return s;
+    CU(cudaMemcpyAsync(out, ctx->scratch, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return check_status(ctx);
+}
+
+int lbm_num_particles(const lbm_ctx *ctx, int inst)
+{
+    if (!ctx || inst < 0 || inst >= ctx->n_inst) return -1;
+    return ctx->inst_h[inst].np;
+}
+
+long long lbm_num_nodes(const lbm_ctx *ctx, int inst)
+{
+    if (!ctx || inst < 0 || inst >= ctx->n_inst) return -1;
+    return ctx->inst_h[inst].N;
+}
+
+lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !out) return fail(ctx, LBM_ERR_ARG, "bad instance or output");
+    int interval = ctx->P[inst].diag_interval;
+    if (interval == 0 || ctx->diag_step[inst] < 0) {
+        lbm_status s = take_diag(ctx);
+        if (s) return s;
+    }
+    double m[2];
+    unsigned st = 0;
+    CU(cudaMemcpyAsync(m, ctx->diag_d + 2 * inst, sizeof m, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&st, ctx->status, sizeof st, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    out[0] = m[0];
+    out[1] = m[1];
+    out[2] = (double)ctx->steps;
+    out[3] = (double)st;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    int bt = block_threads == 0 ? 256 : block_threads;
+    if (bt < 64 || bt > 1024 || bt % 32) return fail(ctx, LBM_ERR_ARG, "block_threads must be a multiple of 32 in [64, 1024]");
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->bt = bt;
+    long long blk = 0;
+    for (auto &I : ctx->inst_h) {
+        I.blk_start = blk;
+        blk += (I.N + bt - 1) / bt;
+    }
+    ctx->n_blocks = blk;
+    CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
+long long lbm_last_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->last_launches : -1; }
+
+lbm_status lbm_profile(lbm_ctx *ctx, int enable)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->profile = enable != 0;
+    ctx->ev_used = 0;
+    ctx->ev_pairs.clear();
+    return LBM_OK;
+}
+
+lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages)
+{
+    if (!ctx || !out || max_stages < 1) return fail(ctx, LBM_ERR_ARG, "bad output");
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> ms(N_STAGES, 0.0), cnt(N_STAGES, 0.0);
+    for (auto &pr : ctx->ev_pairs) {
+        float t = 0.0f;
+        CU(cudaEventElapsedTime(&t, pr.second.first, pr.second.second));
+        ms[pr.first] += t;
+        cnt[pr.first] += 1.0;
+    }
+    for (int k = 0; k < max_stages && k < N_STAGES; k++) {
+        out[2 * k] = cnt[k];
+        out[2 * k + 1] = ms[k];
+    }
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -144,3 +144,27 @@ def cfg4(seed=4242, n_instances=96):
         particles = [dict(x=(xp, ny / 2.0, R_p + 1.5), R=R_p, rho_p=0.125, theta_deg=90.0)]
         out.append(dict(params=params, phi=phi, particles=particles, drop_speed=U))
     return out
+
+
+def cfg2_crop(nx=64, ny=64, nz=32, seed=20251, sphere=5):
+    """A sub-box of the 256x128x128 resolved run (same parameters and fields,
+    cut out around one of its spheres, the one nearest the drop by default),
+    for bounded CPU samples of that workload."""
+    full = cfg2(seed)
+    N0 = (256, 128, 128)
+    p0 = full["particles"][sphere]["x"]
+    x0 = int(p0[0]) - nx // 2
+    y0 = int(p0[1]) - ny // 2
+    params = dict(full["params"], nx=nx, ny=ny, nz=nz)
+    x, y, z = grid(nx, ny, nz)
+    dx = periodic_delta(x + x0 - 48.0, N0[0])
+    dy = periodic_delta(y + y0 - 64.0, N0[1])
+    dz = z - 0.5
+    phi = np.tanh(2.0 * (40.0 - np.sqrt(dx * dx + dy * dy + dz * dz)) / INTERFACE_WIDTH).reshape(-1)
+    parts = []
+    for q in full["particles"]:
+        xx, yy, zz = q["x"][0] - x0, q["x"][1] - y0, q["x"][2]
+        R = q["R"] + 2.0
+        if R <= xx < nx - R and R <= yy < ny - R and zz + R < nz - 1:
+            parts.append(dict(q, x=(xx, yy, zz)))
+    return dict(name=f"sub-box {nx}x{ny}x{nz} of the 256x128x128 run", params=params, phi=phi, particles=parts)

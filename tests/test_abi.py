@@ -1,0 +1,83 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, exports
+every entry point include/lbm.h declares, and the ctypes structs match the C
+layout.  No compute call is made (no GPU here)."""
+import ctypes as ct
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2505_10171_gb300 import build as B
+from paper_2505_10171_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbm.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return B.build()
+
+
+def test_library_exports_every_declared_entry_point(libpath):
+    L = ct.CDLL(libpath)
+    names = declared_functions()
+    assert "lbm_step" in names and "lbm_create" in names and len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(lbm.EXPORTS)
+
+
+def test_binding_loads(libpath):
+    L = lbm.load()
+    assert L.lbm_last_error(None) == b"null context"
+    assert L.lbm_num_nodes(None, 0) == -1
+
+
+def test_struct_layout_matches_header(libpath):
+    prog = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "lbm.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, g_particle),
+         offsetof(lbm_params, store_velocity), offsetof(lbm_params, diag_interval), sizeof(lbm_particle),
+         offsetof(lbm_particle, theta_deg), offsetof(lbm_particle, kinematic));
+  return 0; }
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        open(c, "w").write(prog)
+        exe = os.path.join(d, "t")
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    P, Pa = lbm.lbm_params, lbm.lbm_particle
+    assert vals == [ct.sizeof(P), P.g_particle.offset, P.store_velocity.offset, P.diag_interval.offset,
+                    ct.sizeof(Pa), Pa.theta_deg.offset, Pa.kinematic.offset]
+
+
+def test_abi_velocity_order_matches_header():
+    src = open(HEADER).read()
+    m = re.search(r"#define LBM_C\s*\\\s*(.*?)\n\n", src, flags=re.S)
+    nums = [int(v) for v in re.findall(r"-?\d+", m.group(1).replace("\\", ""))]
+    assert nums == lbm.LBM_C.reshape(-1).tolist()
+
+
+def test_create_without_gpu_fails_cleanly(libpath):
+    """With no device, lbm_create reports an error status instead of crashing."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except Exception:
+        pass
+    with pytest.raises(lbm.LbmError):
+        lbm.Context(dict(nx=4, ny=4, nz=4), "fp64")

@@ -1,0 +1,236 @@
+"""GPU-vs-oracle parity through the C ABI (needs a GB300).
+
+Bars: FP64 storage max-abs population error <= 1e-12 after the run; FP32
+storage rel-L2 <= 1e-4 on rho, phi, u and the per-particle force; 16-bit offset
+storage rel-L2 <= 2e-3.  Inputs come from paper_2505_10171_gb300.workloads,
+shared by both sides; expected values come only from the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import gpu_ctx, oracle_sim, rel_l2
+from paper_2505_10171_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_POP_TOL = 1e-12
+FP32_TOL = 1e-4
+HALF_TOL = 2e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2505_10171_gb300 import build
+    build.build()
+
+
+def run_oracle(w, steps):
+    s = oracle_sim(w)
+    s.step(steps)
+    fa, fb = s.pops()
+    return dict(fields=s.fields(), fa=fa, fb=fb, parts=s.particles(), owner=s.owner())
+
+
+def run_gpu(w, steps, precision="fp64"):
+    c = gpu_ctx(w, precision)
+    c.lbm_step(steps)
+    fa, fb = c.pops()
+    out = dict(fields=c.fields(), fa=fa, fb=fb, parts=c.lbm_particle_forces(), owner=c.owner())
+    c.close()
+    return out
+
+
+def assert_fp64_parity(g, o, tol=FP64_POP_TOL):
+    assert (g["owner"] == o["owner"]).all()
+    fl = o["owner"] == 0
+    err = max(np.abs(g["fa"][:, fl] - o["fa"][:, fl]).max(), np.abs(g["fb"][:, fl] - o["fb"][:, fl]).max())
+    assert err <= tol, err
+    assert np.abs(g["fields"]["u"] - o["fields"]["u"]).max() <= tol
+    if len(o["parts"]):
+        # forces, torques, state: absolute 1e-12 scaled by the magnitudes involved
+        scale = max(1.0, np.abs(o["parts"]).max())
+        assert np.abs(g["parts"] - o["parts"]).max() <= 1e-12 * scale
+
+
+def assert_reduced_parity(g, o, tol):
+    fl = o["owner"] == 0
+    assert (g["owner"] == o["owner"]).all()
+    rg = g["fields"]["rho_a"] + g["fields"]["rho_b"]
+    ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
+    assert rel_l2(rg[fl], ro[fl]) <= tol
+    # the density deviation rho - rho0 is small, so its relative error is only reported
+    print("rel-L2(rho - rho0) =", rel_l2(rg[fl] - 1.0, ro[fl] - 1.0))
+    assert rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]) <= tol
+    assert rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= tol
+    if len(o["parts"]):
+        Fo = o["parts"][:, 0:3] + o["parts"][:, 6:9]
+        Fg = g["parts"][:, 0:3] + g["parts"][:, 6:9]
+        assert rel_l2(Fg, Fo) <= tol
+
+
+@pytest.fixture(scope="module")
+def cfg1_oracle():
+    w = W.cfg1()
+    return w, run_oracle(w, w["steps"])
+
+
+def test_fp64_cfg1_drop_and_sphere(cfg1_oracle):
+    w, o = cfg1_oracle
+    g = run_gpu(w, w["steps"], "fp64")
+    assert_fp64_parity(g, o)
+    # the drop actually moved and the sphere felt the fluid
+    assert np.abs(o["parts"][0, 0:3]).max() > 0
+
+
+def test_fp32_cfg1(cfg1_oracle):
+    w, o = cfg1_oracle
+    assert_reduced_parity(run_gpu(w, w["steps"], "fp32"), o, FP32_TOL)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_16bit_offset_cfg1(cfg1_oracle, prec):
+    w, o = cfg1_oracle
+    g = run_gpu(w, w["steps"], prec)
+    fl = o["owner"] == 0
+    rg = g["fields"]["rho_a"] + g["fields"]["rho_b"]
+    ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
+    errs = dict(rho=rel_l2(rg[fl], ro[fl]), phi=rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]),
+                u=rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]))
+    print(prec, errs)
+    assert errs["rho"] <= HALF_TOL and errs["phi"] <= HALF_TOL
+    if prec == "fp16":
+        assert errs["u"] <= HALF_TOL
+
+
+def test_fp64_fluid_only_sliding_wall():
+    w = W.cfg1()
+    w["particles"] = []
+    o = run_oracle(w, 120)
+    assert_fp64_parity(run_gpu(w, 120, "fp64"), o)
+
+
+def test_fp64_ragged_domain_two_spheres_contact():
+    """Odd sizes (ragged last block), two spheres pressed together and onto the
+    wall by gravity (pair + substrate contacts, friction springs)."""
+    nx, ny, nz = 37, 23, 19
+    p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, wall_velocity=(2e-3, 0, 0), theta_wall_deg=110.0,
+             nu_a=1 / 6, nu_b=1 / 20, mu_s=0.4, mu_r=0.05, gn=0.05, gt=0.1, gr=0.05,
+             g_particle=(0.3, 0.0, -0.5), sigma=0.02)
+    phi = W.drop_phi(nx, ny, nz, (10.0, 11.0, 0.5), 7.0)
+    parts = [dict(x=(22.0, 11.3, 5.5), R=4.0, theta_deg=70.0, rho_p=1.0),
+             dict(x=(30.6, 11.0, 5.5), R=4.0, theta_deg=120.0, rho_p=1.0)]
+    w = dict(params=p, phi=phi, particles=parts)
+    o = run_oracle(w, 60)
+    assert np.abs(o["parts"][:, 12:15]).max() > 0  # contacts active
+    assert_fp64_parity(run_gpu(w, 60, "fp64"), o)
+
+
+def test_fp64_kinematic_sphere_refill():
+    """A prescribed moving sphere uncovers and covers nodes every few steps."""
+    nx, ny, nz = 32, 24, 24
+    p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=0, nu_a=1 / 6, nu_b=1 / 6)
+    phi = W.drop_phi(nx, ny, nz, (16.0, 12.0, 12.0), 6.0)
+    parts = [dict(x=(9.3, 12.2, 11.7), R=4.5, theta_deg=80.0, v=(0.09, 0.03, -0.02), w=(0.0, 0.01, 0.02),
+                  kinematic=1)]
+    w = dict(params=p, phi=phi, particles=parts)
+    o = run_oracle(w, 50)
+    assert_fp64_parity(run_gpu(w, 50, "fp64"), o)
+
+
+def test_fp64_static_tube_mask():
+    w = W.cfg3(nz=40)
+    w["particles"][0]["x"] = (31.5 + 9.3, 31.5, 20.0)
+    o = run_oracle(w, 20)
+    assert_fp64_parity(run_gpu(w, 20, "fp64"), o)
+
+
+def test_batched_instances_match_single_runs():
+    """Three uneven instances stepped in one context equal three separate runs
+    bit for bit, and the oracle within the FP64 bar."""
+    from paper_2505_10171_gb300 import lbm
+    ws = []
+    for k, (nx, ny, nz, R) in enumerate(((40, 24, 20, 7.0), (33, 29, 17, 6.0), (24, 24, 24, 5.0))):
+        p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=80.0 + 15 * k, nu_a=1 / 6,
+                 nu_b=1 / 30, mu_s=0.2, store_velocity=1)
+        phi = W.drop_phi(nx, ny, nz, (nx / 3, ny / 2, 0.5), R)
+        parts = [dict(x=(nx / 3 + R + 6.0, ny / 2, 4.5), R=3.0, theta_deg=90.0)]
+        ws.append(dict(params=p, phi=phi, particles=parts))
+    c = lbm.Context([w["params"] for w in ws], "fp64")
+    for k, w in enumerate(ws):
+        c.lbm_add_particles(w["particles"], inst=k)
+        c.lbm_init_fields(w["phi"], inst=k)
+    c.lbm_step(30)
+    for k, w in enumerate(ws):
+        single = run_gpu(w, 30, "fp64")
+        fa, fb = c.pops(k)
+        assert np.array_equal(fa, single["fa"]) and np.array_equal(fb, single["fb"])
+        assert np.array_equal(c.lbm_particle_forces(k), single["parts"])
+        o = run_oracle(w, 30)
+        assert_fp64_parity(single, o)
+
+
+def test_fp32_deterministic():
+    w = W.cfg1()
+    a = run_gpu(w, 40, "fp32")
+    b = run_gpu(w, 40, "fp32")
+    assert np.array_equal(a["fa"], b["fa"]) and np.array_equal(a["parts"], b["parts"])
+
+
+def test_full_size_cfg2_one_step_fp32():
+    """The 256x128x128 workload of the benchmark, in its launch configuration:
+    one coupled step in FP32 against the oracle at full size."""
+    w = W.cfg2()
+    o = run_oracle(w, 1)
+    g = run_gpu(w, 1, "fp32")
+    assert_reduced_parity(g, o, FP32_TOL)
+
+
+def test_unstable_state_is_reported():
+    """A NaN planted in the host-side initial field is caught by the device
+    status word and reported as LBM_ERR_UNSTABLE by the next read."""
+    from paper_2505_10171_gb300 import lbm
+    w = W.cfg1()
+    w["particles"] = []
+    w["phi"] = w["phi"].copy()
+    w["phi"][1000] = np.nan
+    c = gpu_ctx(w, "fp32")
+    c.lbm_step(2)
+    with pytest.raises(lbm.LbmError) as e:
+        c.fields()
+    assert e.value.status == lbm.LBM_ERR_UNSTABLE
+
+
+def test_particle_limits_and_state_errors():
+    from paper_2505_10171_gb300 import lbm
+    p = dict(W.COMMON, nx=64, ny=64, nz=64, wall_z0=1)
+    c = lbm.Context(p, "fp32")
+    with pytest.raises(lbm.LbmError) as e:
+        c.lbm_add_particles([dict(x=(10, 10, 2.0), R=3.0)])  # intersects the substrate
+    assert e.value.status == lbm.LBM_ERR_ARG
+    with pytest.raises(lbm.LbmError):
+        c.lbm_add_particles([dict(x=(10, 10, 10), R=3.0), dict(x=(14, 10, 10), R=3.0)])  # overlap
+    many = [dict(x=(4 + 8 * (k % 8), 4 + 8 * (k // 8), 30.0), R=2.0, rho_p=40.0) for k in range(62)]
+    with pytest.raises(lbm.LbmError):
+        c.lbm_add_particles(many)
+    c.lbm_add_particles(many[:61])
+    c.lbm_init_fields(np.full(64 ** 3, -1.0))
+    c.lbm_step(0)
+    c.lbm_step(3)
+    with pytest.raises(lbm.LbmError) as e:
+        c.lbm_add_particles([dict(x=(30, 30, 50), R=2.0)])
+    assert e.value.status == lbm.LBM_ERR_STATE
+    d = c.lbm_diagnostics()
+    assert d[2] == 3 and abs(d[1] - (c.owner() == 0).sum()) < 1e-6 * d[1]
+
+
+def test_2d_slab_domain_matches_oracle():
+    """Degenerate one-node-thick domain (ny = 1): sessile drop, FP64."""
+    nx, nz, R = 48, 20, 8
+    X, Z = np.meshgrid(np.arange(nx), np.arange(nz), indexing="xy")
+    phi = np.tanh(2 * (R - np.sqrt((X - 24) ** 2 + (Z - 0.5) ** 2)) / 2.5).reshape(-1)
+    p = dict(W.COMMON, nx=nx, ny=1, nz=nz, wall_z0=1, theta_wall_deg=60.0, nu_a=1 / 6, nu_b=1 / 6)
+    w = dict(params=p, phi=phi, particles=[])
+    o = run_oracle(w, 100)
+    assert_fp64_parity(run_gpu(w, 100, "fp64"), o)
