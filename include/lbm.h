@@ -95,8 +95,8 @@ typedef struct {
     double mu_s, mu_r;         /* sliding and rolling friction coefficients               */
     double delta_R;            /* mechanical minus hydrodynamic radius (Sec. V G)         */
     double g_particle[3];      /* external force on every particle (gravity, Sec. VI A)   */
-    double grad_eps;           /* |grad phi| below which the interface normal is zero;     */
-                               /*    0 selects 1e-10 (FP64) or 1e-6 (other precisions)     */
+    double grad_eps;           /* eps of the interface normal g/sqrt(|g|^2 + eps^2),       */
+                               /*    g = grad phi; 0 selects 1e-6                          */
     double wet_phi_max;        /* wetting applied at nodes with |phi| < this; 0 -> 0.99   */
     int store_velocity;        /* 1: keep the collision velocity for lbm_read_fields(U)   */
     int diag_interval;         /* > 0: FP64 mass sums every that many steps               */

@@ -548,11 +548,13 @@ int or_capillary(const or_sim *s, int p, double *F, double *T)
             ph /= ws;
             for (int a = 0; a < 3; a++) g[a] /= ws;
             if (fabs(ph) >= 1.0) continue; /* outside the diffuse interface */
-            double gm = sqrt(dot3(g, g));
-            if (gm < s->p.grad_eps) continue;
-            double n[3] = {g[0] / gm, g[1] / gm, g[2] / gm};
-            double nn = dot3(n, ns);
-            double mvec[3] = {ns[0] - nn * n[0], ns[1] - nn * n[1], ns[2] - nn * n[2]};
+            /* READING c6: interface normal n = g/sqrt(|g|^2 + eps^2); m is the
+             * paper's (n x n_s) x n = (n.n) n_s - (n.n_s) n */
+            double gr = sqrt(dot3(g, g) + s->p.grad_eps * s->p.grad_eps);
+            double n[3] = {g[0] / gr, g[1] / gr, g[2] / gr};
+            double nxs[3], mvec[3];
+            cross3(n, ns, nxs);
+            cross3(nxs, n, mvec);
             double coef = s->p.cap_norm * s->p.sigma * (1.0 - ph * ph) * dA;
             double dF[3] = {coef * mvec[0], coef * mvec[1], coef * mvec[2]};
             double r[3] = {P->R * ns[0], P->R * ns[1], P->R * ns[2]}, t[3];
@@ -877,12 +879,15 @@ static void step_once(or_sim *s)
                     if (solid_normal(s, x, y, z, ns, &th)) or_wetting_rotate(g, ns, th);
                 }
                 for (int a = 0; a < 3; a++) s->grad[a * N + id] = g[a];
-                double gm = sqrt(dot3(g, g));
-                for (int a = 0; a < 3; a++) s->nrm[a * N + id] = gm >= pp->grad_eps ? g[a] / gm : 0.0;
+                double gr = sqrt(dot3(g, g) + pp->grad_eps * pp->grad_eps);
+                for (int a = 0; a < 3; a++) s->nrm[a * N + id] = g[a] / gr;
             }
     /* (6) curvature, force, collision, recolouring.
-     * READING c6: kappa = div(n), n = grad(phi)/|grad(phi)|, with the same
-     * stencil; READING c7: a solid neighbour contributes the node's own n.
+     * READING c6: kappa = div(n) with the same stencil, n the interface normal
+     * grad(phi)/|grad(phi)| taken in the regularised form
+     * grad(phi)/sqrt(|grad(phi)|^2 + eps^2), continuous where grad(phi) vanishes
+     * inside the diffuse interface; READING c7: a solid neighbour contributes
+     * the node's own n.
      * Sec. IV CSF: F = -1/2 sigma kappa grad(phi); body forces weighted by the
      * local phase fractions (1 +- phi)/2 (Sec. II, Sec. VI A). */
 #pragma omp parallel for collapse(2) schedule(static)
@@ -1035,10 +1040,10 @@ int or_eval_interface(or_sim *s)
                         if (solid_normal(s, x, y, z, ns, &th)) or_wetting_rotate(g, ns, th);
                     }
                 }
-                double gm = sqrt(dot3(g, g));
+                double gr = sqrt(dot3(g, g) + s->p.grad_eps * s->p.grad_eps);
                 for (int a = 0; a < 3; a++) {
                     s->grad[a * N + id] = g[a];
-                    s->nrm[a * N + id] = gm >= s->p.grad_eps ? g[a] / gm : 0.0;
+                    s->nrm[a * N + id] = g[a] / gr;
                 }
             }
     return 0;

@@ -37,7 +37,7 @@ typedef struct {
     double mu_s, mu_r;           /* sliding / rolling friction coeffs      */
     double delta_R;              /* R_c - R_p                              */
     double g_particle[3];        /* external force on every particle       */
-    double grad_eps;             /* |grad phi| below which n is zero       */
+    double grad_eps;             /* eps of the normal g/sqrt(|g|^2+eps^2) */
     double wet_phi_max;          /* wetting applied where |phi| < this     */
 } or_params;
 

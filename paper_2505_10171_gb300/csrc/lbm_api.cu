@@ -463,7 +463,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         double th = p.theta_wall_deg * M_PI / 180.0;
         I.cos_tw = std::cos(th);
         I.sin_tw = std::sin(th);
-        I.grad_eps = p.grad_eps > 0.0 ? p.grad_eps : (prec == LBM_FP64 ? 1e-10 : 1e-6);
+        I.grad_eps = p.grad_eps > 0.0 ? p.grad_eps : 1e-6;
         I.wet_max = p.wet_phi_max > 0.0 ? p.wet_phi_max : 0.99;
         I.kn = p.kn; I.kt = p.kt; I.kr = p.kr;
         I.gn = p.gn; I.gt = p.gt; I.gr = p.gr;

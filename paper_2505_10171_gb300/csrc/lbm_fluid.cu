@@ -180,15 +180,14 @@ __global__ void k_collide(Lattice L, int cur)
     const R phi = sG / rr;
     if (!(rr > R(0)) || !(phi == phi)) atomicOr(L.status, ST_UNSTABLE);
 
-    // interface normal and curvature (div of the unit normal, solid
+    // interface normal n = g/sqrt(|g|^2 + eps^2) and curvature (div n; solid
     // neighbours contribute this node's own normal)
     const R *GR = (const R *)L.grad;
     const long long Nt = L.Ntot;
-    const R eps = (R)I.grad_eps;
-    R g0 = GR[g], g1 = GR[Nt + g], g2 = GR[2 * Nt + g];
-    R gm = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
-    R n0 = 0, n1 = 0, n2 = 0;
-    if (gm >= eps) { n0 = g0 / gm; n1 = g1 / gm; n2 = g2 / gm; }
+    const R eps2 = (R)(I.grad_eps * I.grad_eps);
+    const R g0 = GR[g], g1 = GR[Nt + g], g2 = GR[2 * Nt + g];
+    const R ig = R(1) / sqrt(g0 * g0 + g1 * g1 + g2 * g2 + eps2);
+    const R n0 = g0 * ig, n1 = g1 * ig, n2 = g2 * ig;
     R kap = 0;
     const uint8_t *fli = L.flags + I.node_off;
 #pragma unroll
@@ -198,9 +197,8 @@ __global__ void k_collide(Lattice L, int cur)
         if (!(fl & BOUND_BIT) || (fli[m] & OWNER_MASK) == OWN_FLUID) {
             long long gmn = I.node_off + m;
             R h0 = GR[gmn], h1 = GR[Nt + gmn], h2 = GR[2 * Nt + gmn];
-            R hm = sqrt(h0 * h0 + h1 * h1 + h2 * h2);
-            if (hm >= eps) { a0 = h0 / hm; a1 = h1 / hm; a2 = h2 / hm; }
-            else { a0 = a1 = a2 = 0; }
+            R ih = R(1) / sqrt(h0 * h0 + h1 * h1 + h2 * h2 + eps2);
+            a0 = h0 * ih; a1 = h1 * ih; a2 = h2 * ih;
         }
         kap += wgt<R>(i) * (cx(i) * a0 + cy(i) * a1 + cz(i) * a2);
     }

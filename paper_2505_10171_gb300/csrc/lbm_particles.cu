@@ -166,13 +166,16 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
         if (ws > 0.0) {
             const double phv = phs / ws;
             const double g0 = gs[0] / ws, g1 = gs[1] / ws, g2 = gs[2] / ws;
-            const double gm = sqrt(g0 * g0 + g1 * g1 + g2 * g2);
-            if (fabs(phv) < 1.0 && gm >= I.grad_eps) {
-                const double nn[3] = {g0 / gm, g1 / gm, g2 / gm};
-                const double d = nn[0] * ns[0] + nn[1] * ns[1] + nn[2] * ns[2];
+            if (fabs(phv) < 1.0) {
+                // regularised normal n = g/sqrt(|g|^2 + eps^2), m = (n x n_s) x n
+                const double gr = sqrt(g0 * g0 + g1 * g1 + g2 * g2 + I.grad_eps * I.grad_eps);
+                const double nn[3] = {g0 / gr, g1 / gr, g2 / gr};
+                const double c0 = nn[1] * ns[2] - nn[2] * ns[1], c1 = nn[2] * ns[0] - nn[0] * ns[2],
+                             c2 = nn[0] * ns[1] - nn[1] * ns[0];
+                const double mv[3] = {c1 * nn[2] - c2 * nn[1], c2 * nn[0] - c0 * nn[2], c0 * nn[1] - c1 * nn[0]};
                 const double coef = I.cap_norm * I.sigma * (1.0 - phv * phv) * dA;
                 double dF[3];
-                for (int a = 0; a < 3; a++) dF[a] = coef * (ns[a] - d * nn[a]);
+                for (int a = 0; a < 3; a++) dF[a] = coef * mv[a];
                 const double r[3] = {P.R * ns[0], P.R * ns[1], P.R * ns[2]};
                 acc[0] = dF[0];
                 acc[1] = dF[1];

@@ -27,6 +27,9 @@ COMMON = dict(
     kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0,
 )
 INTERFACE_WIDTH = 2.5
+# Table I: particle density 0.125 against fluid density 0.05, i.e. a particle
+# 2.5 times denser than the fluid; with rho0 = 1 the particle density is 2.5.
+PARTICLE_DENSITY = 2.5
 
 
 def grid(nx, ny, nz):
@@ -56,7 +59,7 @@ def cfg1():
                   theta_wall_deg=90.0, nu_a=1.0 / 6.0, nu_b=1.0 / 6.0, mu_s=0.3, mu_r=0.05,
                   g_particle=(0.0, 0.0, 0.0))
     phi = drop_phi(nx, ny, nz, (16.0, 16.0, 0.5), 10.0)
-    particles = [dict(x=(33.0, 16.0, 5.5), R=4.0, rho_p=0.125, theta_deg=60.0)]
+    particles = [dict(x=(33.0, 16.0, 5.5), R=4.0, rho_p=PARTICLE_DENSITY, theta_deg=60.0)]
     return dict(name="drop-sphere 48x32x32, 1 sphere R=4, FP64 parity", params=params, phi=phi,
                 particles=particles, steps=200)
 
@@ -91,7 +94,7 @@ def cfg2(seed=20251, n_spheres=8):
                   theta_wall_deg=150.0, nu_a=1.0 / 6.0, nu_b=1.0 / 60.0, mu_s=0.3, mu_r=0.05,
                   body_force_a=(2.0e-6, 0.0, 0.0), g_particle=(0.0, 0.0, -10.0 * sigma * R_p))
     phi = drop_phi(nx, ny, nz, (48.0, 64.0, 0.5), 40.0)
-    particles = [dict(x=c, R=R_p, rho_p=0.125, theta_deg=float(t)) for c, t in zip(centres, thetas)]
+    particles = [dict(x=c, R=R_p, rho_p=PARTICLE_DENSITY, theta_deg=float(t)) for c, t in zip(centres, thetas)]
     return dict(name="drop-sphere 256x128x128, 8 spheres R=8", params=params, phi=phi,
                 particles=particles, steps=20000)
 
@@ -141,7 +144,7 @@ def cfg4(seed=4242, n_instances=96):
         xd = 1.2 * Rd
         phi = drop_phi(nx, ny, nz, (xd, ny / 2.0, 0.5), Rd)
         xp = xd + Rd + R_p + 3.0
-        particles = [dict(x=(xp, ny / 2.0, R_p + 1.5), R=R_p, rho_p=0.125, theta_deg=90.0)]
+        particles = [dict(x=(xp, ny / 2.0, R_p + 1.5), R=R_p, rho_p=PARTICLE_DENSITY, theta_deg=90.0)]
         out.append(dict(params=params, phi=phi, particles=particles, drop_speed=U))
     return out
 

@@ -49,9 +49,9 @@ def assert_fp64_parity(g, o, tol=FP64_POP_TOL):
     assert err <= tol, err
     assert np.abs(g["fields"]["u"] - o["fields"]["u"]).max() <= tol
     if len(o["parts"]):
-        # forces, torques, state: absolute 1e-12 scaled by the magnitudes involved
-        scale = max(1.0, np.abs(o["parts"]).max())
-        assert np.abs(g["parts"] - o["parts"]).max() <= 1e-12 * scale
+        # forces, torques, state: 1e-12 absolute, relative for entries above 1
+        d = np.abs(g["parts"] - o["parts"]) / np.maximum(1.0, np.abs(o["parts"]))
+        assert d.max() <= 1e-12, d.max(axis=0)
 
 
 def assert_reduced_parity(g, o, tol):
@@ -65,9 +65,11 @@ def assert_reduced_parity(g, o, tol):
     assert rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]) <= tol
     assert rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= tol
     if len(o["parts"]):
+        # relative to the force scale sigma R_p when the forces themselves are ~0
         Fo = o["parts"][:, 0:3] + o["parts"][:, 6:9]
         Fg = g["parts"][:, 0:3] + g["parts"][:, 6:9]
-        assert rel_l2(Fg, Fo) <= tol
+        scale = max(np.linalg.norm(Fo), 1e-3 * np.sqrt(len(Fo)))
+        assert np.linalg.norm(Fg - Fo) / scale <= tol
 
 
 @pytest.fixture(scope="module")
@@ -119,8 +121,8 @@ def test_fp64_ragged_domain_two_spheres_contact():
              nu_a=1 / 6, nu_b=1 / 20, mu_s=0.4, mu_r=0.05, gn=0.05, gt=0.1, gr=0.05,
              g_particle=(0.3, 0.0, -0.5), sigma=0.02)
     phi = W.drop_phi(nx, ny, nz, (10.0, 11.0, 0.5), 7.0)
-    parts = [dict(x=(22.0, 11.3, 5.5), R=4.0, theta_deg=70.0, rho_p=1.0),
-             dict(x=(30.6, 11.0, 5.5), R=4.0, theta_deg=120.0, rho_p=1.0)]
+    parts = [dict(x=(22.0, 11.3, 5.5), R=4.0, theta_deg=70.0, rho_p=W.PARTICLE_DENSITY),
+             dict(x=(30.6, 11.0, 5.5), R=4.0, theta_deg=120.0, rho_p=W.PARTICLE_DENSITY)]
     w = dict(params=p, phi=phi, particles=parts)
     o = run_oracle(w, 60)
     assert np.abs(o["parts"][:, 12:15]).max() > 0  # contacts active
@@ -155,7 +157,7 @@ def test_batched_instances_match_single_runs():
         p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=80.0 + 15 * k, nu_a=1 / 6,
                  nu_b=1 / 30, mu_s=0.2, store_velocity=1)
         phi = W.drop_phi(nx, ny, nz, (nx / 3, ny / 2, 0.5), R)
-        parts = [dict(x=(nx / 3 + R + 6.0, ny / 2, 4.5), R=3.0, theta_deg=90.0)]
+        parts = [dict(x=(nx / 3 + R + 6.0, ny / 2, 4.5), R=3.0, theta_deg=90.0, rho_p=W.PARTICLE_DENSITY)]
         ws.append(dict(params=p, phi=phi, particles=parts))
     c = lbm.Context([w["params"] for w in ws], "fp64")
     for k, w in enumerate(ws):
@@ -194,7 +196,7 @@ def test_unstable_state_is_reported():
     w = W.cfg1()
     w["particles"] = []
     w["phi"] = w["phi"].copy()
-    w["phi"][1000] = np.nan
+    w["phi"][(10 * 32 + 16) * 48 + 16] = np.nan  # a fluid node inside the drop
     c = gpu_ctx(w, "fp32")
     c.lbm_step(2)
     with pytest.raises(lbm.LbmError) as e:

@@ -14,7 +14,7 @@ K = (1 + math.sqrt(2)) / 18
 def planar(beta, steps=4000, nx=64):
     x = np.arange(nx)
     phi = np.where((x >= nx // 4) & (x < 3 * nx // 4), 1.0, -1.0)
-    s = O.OracleSim(nx, 1, 1, beta=beta, sigma=0.0)
+    s = O.OracleSim(nx, 1, 1, beta=beta, sigma=0.0, grad_eps=1e-14)  # unregularised limit
     s.init_fields(phi)
     s.step(steps)
     return s.fields()["phi"]
