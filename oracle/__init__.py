@@ -117,7 +117,7 @@ DEFAULTS = dict(
     cap_norm=4.5 * (1.0 + 2.0 ** 0.5) / 18.0 * 0.7,
     body_force_a=(0.0, 0.0, 0.0), body_force_b=(0.0, 0.0, 0.0),
     kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0,
-    g_particle=(0.0, 0.0, 0.0), grad_eps=1e-6, wet_phi_max=0.99,
+    g_particle=(0.0, 0.0, 0.0), grad_eps=1e-4, wet_phi_max=1.0,
 )
 
 

@@ -859,7 +859,9 @@ static void step_once(or_sim *s)
             }
     /* (5) READING c5: grad phi = (1/cs2) sum_i w_i c_i phi(x + c_i); then the
      * Sec. V D wetting rotation at fluid nodes next to a solid inside the
-     * interface (READING c10: |phi| < wet_phi_max). */
+     * diffuse interface (READING c10: |phi| < wet_phi_max, by default 1, the
+     * region -1 < phi < 1 the capillary model of Sec. V E calls the diffuse
+     * interface). */
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; z++)
         for (int y = 0; y < ny; y++)
