@@ -97,8 +97,7 @@ typedef struct {
     double g_particle[3];      /* external force on every particle (gravity, Sec. VI A)   */
     double grad_eps;           /* eps of the interface normal g/sqrt(|g|^2 + eps^2),       */
                                /*    g = grad phi; 0 selects 1e-4                          */
-    double wet_phi_max;        /* wetting applied at nodes with |phi| < this; 0 -> 1      */
-                               /*    (the diffuse interface -1 < phi < 1, Sec. V E)        */
+    double wet_phi_max;        /* wetting applied at nodes with |phi| < this; 0 -> 0.99   */
     int store_velocity;        /* 1: keep the collision velocity for lbm_read_fields(U)   */
     int diag_interval;         /* > 0: FP64 mass sums every that many steps               */
 } lbm_params;

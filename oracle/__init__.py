@@ -117,7 +117,7 @@ DEFAULTS = dict(
     cap_norm=4.5 * (1.0 + 2.0 ** 0.5) / 18.0 * 0.7,
     body_force_a=(0.0, 0.0, 0.0), body_force_b=(0.0, 0.0, 0.0),
     kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0,
-    g_particle=(0.0, 0.0, 0.0), grad_eps=1e-4, wet_phi_max=1.0,
+    g_particle=(0.0, 0.0, 0.0), grad_eps=1e-4, wet_phi_max=0.99,
 )
 
 
@@ -290,7 +290,7 @@ def omega_of_phi(phi, rho, **kw):
 
 SIM_KEYS = ("wall_z0", "wall_velocity", "theta_wall_deg", "rho0", "nu_a", "nu_b", "sigma", "beta",
             "body_force_a", "body_force_b", "kn", "kt", "kr", "gn", "gt", "gr", "mu_s", "mu_r", "delta_R",
-            "g_particle")
+            "g_particle", "grad_eps", "wet_phi_max")
 
 
 def from_workload(w) -> OracleSim:

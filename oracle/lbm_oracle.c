@@ -444,7 +444,11 @@ void or_wetting_rotate(double *g, const double *ns, double theta)
     if (ca < -1.0) ca = -1.0;
     double alpha = acos(ca);
     double sa = sin(alpha), cal = cos(alpha);
-    if (sa < 1e-12) return; /* n* parallel to n_s: direction undefined */
+    /* READING c11: where n* is parallel to n_s (sin alpha* -> 0) the plane of
+     * rotation, i.e. the contact-line direction, is undefined and the formula
+     * divides rounding noise by sin alpha*; below 1e-4 (0.006 deg) the gradient
+     * is left as it is. */
+    if (sa < 1e-4) return;
     double best[3], bestdot = -2.0;
     for (int sg = 0; sg < 2; sg++) {
         double th = sg == 0 ? theta : -theta;
@@ -859,9 +863,7 @@ static void step_once(or_sim *s)
             }
     /* (5) READING c5: grad phi = (1/cs2) sum_i w_i c_i phi(x + c_i); then the
      * Sec. V D wetting rotation at fluid nodes next to a solid inside the
-     * diffuse interface (READING c10: |phi| < wet_phi_max, by default 1, the
-     * region -1 < phi < 1 the capillary model of Sec. V E calls the diffuse
-     * interface). */
+     * diffuse interface (READING c10: |phi| < wet_phi_max = 0.99). */
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; z++)
         for (int y = 0; y < ny; y++)

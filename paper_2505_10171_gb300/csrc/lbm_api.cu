@@ -464,7 +464,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.cos_tw = std::cos(th);
         I.sin_tw = std::sin(th);
         I.grad_eps = p.grad_eps > 0.0 ? p.grad_eps : 1e-4;
-        I.wet_max = p.wet_phi_max > 0.0 ? p.wet_phi_max : 1.0;
+        I.wet_max = p.wet_phi_max > 0.0 ? p.wet_phi_max : 0.99;
         I.kn = p.kn; I.kt = p.kt; I.kr = p.kr;
         I.gn = p.gn; I.gt = p.gt; I.gr = p.gr;
         I.mu_s = p.mu_s; I.mu_r = p.mu_r; I.dR = p.delta_R;

@@ -249,7 +249,7 @@ __device__ __forceinline__ void wetting_rotate(R *g, const R *ns, R cth, R sth)
     ca = ca > R(1) ? R(1) : (ca < R(-1) ? R(-1) : ca);
     R al = acos(ca);
     R sa = sin(al), cal = cos(al);
-    if (sa < R(1e-12)) return;
+    if (sa < R(1e-4)) return;  // contact-line direction undefined (n* parallel to n_s)
     R ap1 = cth - sth * cal / sa, ap2 = sth / sa;
     R am1 = cth + sth * cal / sa, am2 = -sth / sa;
     R np_[3], nm_[3];
