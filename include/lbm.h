@@ -220,6 +220,24 @@ lbm_status lbm_profile(lbm_ctx *ctx, int enable);
  * milliseconds; at most max_stages stages are written.  Synchronises. */
 lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages);
 
+/* Allocation-free FP64 component masses, for callers that cannot call
+ * cudaMalloc (code running while a CUDA graph is captured, frameworks that own
+ * all device memory through their own pool, loops where an allocation would
+ * synchronise the device).  The paper has no counterpart; it is a variant of
+ * the reduction behind lbm_diagnostics that needs no context.
+ * pops: device pointer to FP64 populations, f^a then f^b, [38][n_nodes]
+ * (the LBM_FIELD_POPS layout of lbm_read_fields_device; solid nodes 0);
+ * masses: device pointer to 2 doubles, receives sum f^a, sum f^b.
+ * stream: cudaStream_t the two kernels are enqueued on (NULL: legacy stream).
+ * Allocates nothing: its scratch is a static device array of 4096 x 2 doubles
+ * (64 KiB) that every GPU which loads the library keeps until the process
+ * exits.  n_nodes must be in [1, 2^28] (-> LBM_ERR_ARG otherwise).  The first
+ * call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call shares
+ * the one array, so calls that overlap on the GPU race.  Asynchronous; returns
+ * LBM_ERR_CUDA if the lookup or a launch fails. */
+lbm_status lbm_component_masses_noalloc(const double *pops, long long n_nodes, double *masses, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

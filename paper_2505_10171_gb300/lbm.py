@@ -68,7 +68,7 @@ _lib = None
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", "lbm_init_fields",
            "lbm_init_fields_device", "lbm_add_particles", "lbm_step", "lbm_particle_forces", "lbm_read_fields",
            "lbm_read_fields_device", "lbm_num_particles", "lbm_num_nodes", "lbm_diagnostics", "lbm_set_launch",
-           "lbm_last_launch_count", "lbm_profile", "lbm_profile_read"]
+           "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc"]
 STAGES = ["phi", "solid_phi", "grad_wetting", "collide", "momentum_exchange", "capillary", "dem", "geom_owner",
           "geom_boundary", "refill"]
 
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.lbm_last_launch_count.restype = ct.c_longlong
     L.lbm_profile.argtypes = [vp, i]
     L.lbm_profile_read.argtypes = [vp, d, i]
+    L.lbm_component_masses_noalloc.argtypes = [vp, ct.c_longlong, vp, vp]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
                         "lbm_last_launch_count"):
@@ -135,6 +136,15 @@ def make_params(**kw) -> lbm_params:
         else:
             setattr(p, name, int(val) if typ is ct.c_int else float(val))
     return p
+
+
+def lbm_component_masses_noalloc(pops_ptr, n_nodes, masses_ptr, stream=0):
+    """FP64 sums of f^a and f^b of a device population array ([38][n_nodes],
+    ABI layout) into a device buffer of 2 doubles, without any allocation."""
+    st = load().lbm_component_masses_noalloc(ct.c_void_p(pops_ptr), int(n_nodes), ct.c_void_p(masses_ptr),
+                                             ct.c_void_p(stream or 0))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_component_masses_noalloc failed")
 
 
 def _dp(a):
