@@ -76,7 +76,8 @@ typedef enum {
 /* Physical parameters of one instance (lattice units, dt = dx = 1).
  * Table I of the paper gives the ranges used there. */
 typedef struct {
-    int nx, ny, nz;            /* lattice size, periodic in x, y and z (Sec. VI A)       */
+    int nx, ny, nz;            /* lattice size, periodic in x, y and z (Sec. VI A);      */
+                               /*    38 nx ny nz < 2^31 per instance                       */
     int wall_z0;               /* 1: node plane z = 0 is the substrate; its halfway wall  */
                                /*    sits at z = 0.5 (and z = nz - 0.5 through periodicity) */
     double wall_velocity[3];   /* substrate velocity (moving-wall bounce-back, Sec. V A)  */
@@ -199,10 +200,17 @@ long long lbm_num_nodes(const lbm_ctx *ctx, int inst);
  * taken so far, out[3] = sticky device status bits.  Synchronises. */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
 
-/* Launch-shape override of the fluid kernels (block size in threads, a
- * multiple of 32 in [64, 1024]); 0 restores the default.  Invalidates the
+/* Launch-shape override of the four-kernel fluid form (block size in threads,
+ * a multiple of 32 in [64, 256]); 0 restores the default.  Invalidates the
  * captured step graph. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads);
+
+/* Fluid-update launch form.  fused = 1 (default): one z-marching kernel per
+ * step; tile selects its column tile (0: 32x8, 1: 64x4, 2: 16x16); zchunk is
+ * the number of z-planes per work item (0: automatic, 32).  fused = 0: the
+ * four-kernel form (order parameter, solid phi, gradient, collision), kept as
+ * a reference.  Both give identical results.  Invalidates the step graph. */
+lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int fused, int tile, int zchunk);
 
 /* Count of kernel launches the last lbm_step call enqueued (graph nodes
  * included); for accounting in benchmarks. */
@@ -213,11 +221,12 @@ long long lbm_last_launch_count(const lbm_ctx *ctx);
  * context's stream; enabling again clears the record.  Synchronises. */
 lbm_status lbm_profile(lbm_ctx *ctx, int enable);
 
-/* Read the per-kernel record since lbm_profile(ctx, 1): for stage k (launch
- * order within a step: order parameter, solid phi, gradient+wetting,
- * collision, momentum exchange, capillary force, DEM, geometry owner,
- * geometry boundary, refill) out[2k] = launches, out[2k+1] = total device
- * milliseconds; at most max_stages stages are written.  Synchronises. */
+/* Read the per-kernel record since lbm_profile(ctx, 1): for stage k
+ * (order parameter, solid phi, gradient+wetting, collision [four-kernel
+ * form], momentum exchange, capillary force, DEM, geometry owner, geometry
+ * boundary, refill, fused fluid kernel, particle-region phi/gradient)
+ * out[2k] = launches, out[2k+1] = total device milliseconds; at most
+ * max_stages stages are written.  Synchronises. */
 lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages);
 
 /* Allocation-free FP64 component masses, for callers that cannot call

@@ -24,12 +24,14 @@ struct lbm_ctx {
     size_t elem = 8, real_sz = 8;
     uint8_t *flags = nullptr;
     void *pop[2] = {nullptr, nullptr};
-    void *phi = nullptr, *grad = nullptr, *u = nullptr;
+    void *phi = nullptr, *grad = nullptr, *gmag = nullptr, *u = nullptr;
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
     double *mem_part = nullptr, *cap_part = nullptr, *hist = nullptr;
+    double *cap_pts = nullptr;  // Lagrangian surface-point table
+    double *crec = nullptr;     // DEM contact records
     unsigned *status = nullptr;
-    int mem_blocks = 1, geom_blocks = 1, geom_side = 1;
+    int mem_blocks = 1, geom_blocks = 1, geom_side = 1, cap_side = 1, cap_blocks = 1;
     int cur = 0;
     long long steps = 0;
     bool stepped = false;
@@ -50,7 +52,28 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
+    // fluid launch form: fused z-marching kernel (default) or four kernels
+    FluidLaunch fz = {1, 0, 0};
+    int zc_request = 0;  // z-planes per fused work item, 0: automatic
 };
+
+// work items of the fused kernel: column tiles x z-chunks, per instance
+static void plan_fused(lbm_ctx *c)
+{
+    const int TX = fused_tile_x(c->fz.tile), TY = fused_tile_y(c->fz.tile);
+    long long items = 0;
+    for (auto &I : c->inst_h) {
+        I.tiles_x = (I.nx + TX - 1) / TX;
+        I.tiles_y = (I.ny + TY - 1) / TY;
+        int zc = c->zc_request > 0 ? c->zc_request : 32;
+        if (zc > I.nz) zc = I.nz;
+        I.nchunks = (I.nz + zc - 1) / zc;
+        I.zc = (I.nz + I.nchunks - 1) / I.nchunks;
+        I.item_start = items;
+        items += (long long)I.tiles_x * I.tiles_y * I.nchunks;
+    }
+    c->fz.items = items;
+}
 
 static const int DIAG_BLOCKS = 512;
 
@@ -80,6 +103,7 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.pop[1] = c->pop[1];
     L.phi = c->phi;
     L.grad = c->grad;
+    L.gmag = c->gmag;
     L.u = c->u;
     L.Ntot = c->Ntot;
     L.parts = c->parts_d;
@@ -87,9 +111,13 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.mem_blocks = c->mem_blocks;
     L.geom_blocks = c->geom_blocks;
     L.geom_side = c->geom_side;
+    L.cap_side = c->cap_side;
+    L.cap_blocks = c->cap_blocks;
     L.mem_part = c->mem_part;
     L.cap_part = c->cap_part;
+    L.cap_pts = c->cap_pts;
     L.hist = c->hist;
+    L.crec = c->crec;
     L.status = c->status;
     return L;
 }
@@ -310,7 +338,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
     }
     dispatch(c->prec, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        launch_fluid_step<S>(L, cur, c->stream, launches, mk);
+        launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz);
         launch_particle_forces<S>(L, cur, c->stream, launches, mk);
         launch_dem(L, c->stream, launches, mk);
         launch_geometry<S>(L, cur ^ 1, c->stream, launches, mk);
@@ -343,7 +371,7 @@ static lbm_status validate(lbm_ctx *ctx, const lbm_params &p, int k)
         return fail(ctx, LBM_ERR_ARG, b);
     };
     if (p.nx < 1 || p.ny < 1 || p.nz < 1) return bad("nx, ny, nz must be >= 1");
-    if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return bad("lattice too large");
+    if ((long long)p.nx * p.ny * p.nz * NPOP >= (1LL << 31)) return bad("instance too large (38 x nodes must be < 2^31)");
     if (p.wall_z0 && p.nz < 3) return bad("a substrate needs nz >= 3");
     if (!(p.nu_a > 0.0) || !(p.nu_b > 0.0) || !std::isfinite(p.nu_a) || !std::isfinite(p.nu_b))
         return bad("viscosities must be finite and > 0 (tau > 1/2)");
@@ -402,11 +430,14 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->pop[1]);
     cudaFree(ctx->phi);
     cudaFree(ctx->grad);
+    cudaFree(ctx->gmag);
     cudaFree(ctx->u);
     cudaFree(ctx->parts_d);
     cudaFree(ctx->mem_part);
     cudaFree(ctx->cap_part);
+    cudaFree(ctx->cap_pts);
     cudaFree(ctx->hist);
+    cudaFree(ctx->crec);
     cudaFree(ctx->status);
     cudaFree(ctx->scratch);
     cudaFree(ctx->diag_d);
@@ -468,12 +499,20 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.kn = p.kn; I.kt = p.kt; I.kr = p.kr;
         I.gn = p.gn; I.gt = p.gt; I.gr = p.gr;
         I.mu_s = p.mu_s; I.mu_r = p.mu_r; I.dR = p.delta_R;
+        I.f_rho0 = (float)I.rho0; I.f_sigma = (float)I.sigma; I.f_beta = (float)I.beta;
+        I.f_eta_a = (float)I.eta_a; I.f_eta_b = (float)I.eta_b;
+        I.f_eps2 = (float)(I.grad_eps * I.grad_eps); I.f_wet_max = (float)I.wet_max;
+        for (int a = 0; a < 3; a++) { I.f_body_a[a] = (float)I.body_a[a]; I.f_body_b[a] = (float)I.body_b[a]; }
+        I.f_ir0 = (float)(1.0 / I.rho0);
+        I.f_h_ia = (float)(0.5 / I.eta_a);
+        I.f_h_ib = (float)(0.5 / I.eta_b);
         ctx->inst_h.push_back(I);
         node_off += I.N;
         blk += (I.N + ctx->bt - 1) / ctx->bt;
     }
     ctx->Ntot = node_off;
     ctx->n_blocks = blk;
+    plan_fused(ctx);
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
     } else {
@@ -496,7 +535,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     if ((st = alloc((void **)&ctx->inst_d, sizeof(InstDev) * n_instances)) ||
         (st = alloc((void **)&ctx->flags, Nt)) || (st = alloc(&ctx->pop[0], NPOP * Nt * ctx->elem)) ||
         (st = alloc(&ctx->pop[1], NPOP * Nt * ctx->elem)) || (st = alloc(&ctx->phi, Nt * ctx->real_sz)) ||
-        (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
+        (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc(&ctx->gmag, Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
         (st = alloc((void **)&ctx->diag_d, sizeof(double) * 2 * n_instances)) ||
         (st = alloc((void **)&ctx->diag_part, sizeof(double) * 2 * DIAG_BLOCKS)) ||
         (any_u && (st = alloc(&ctx->u, 3 * Nt * ctx->real_sz)))) {
@@ -504,10 +543,31 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         lbm_destroy(ctx);
         return st;
     }
+    // Sec. V E surface points alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg:
+    // unit normal and sin(alpha), evaluated once on the host
+    {
+        std::vector<double> tab(4 * (size_t)CAP_POINTS);
+        const double da = 2.0 * M_PI / 180.0;
+        for (int j = 0; j < 90; j++)
+            for (int k = 0; k < 180; k++) {
+                const double al = (j + 0.5) * da, vp = k * da;
+                double *t = &tab[4 * (size_t)(j * 180 + k)];
+                t[0] = std::sin(al) * std::cos(vp);
+                t[1] = std::sin(al) * std::sin(vp);
+                t[2] = std::cos(al);
+                t[3] = std::sin(al);
+            }
+        if ((st = alloc((void **)&ctx->cap_pts, sizeof(double) * tab.size()))) {
+            lbm_destroy(ctx);
+            return st;
+        }
+        cudaMemcpy(ctx->cap_pts, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice);
+    }
     cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * n_instances, cudaMemcpyHostToDevice, ctx->stream);
     cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream);
     cudaMemsetAsync(ctx->phi, 0, Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->grad, 0, 3 * Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->gmag, 0, Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->diag_d, 0, sizeof(double) * 2 * n_instances, ctx->stream);
     if (ctx->u) cudaMemsetAsync(ctx->u, 0, 3 * Nt * ctx->real_sz, ctx->stream);
     // flags: substrate plane, then boundary bits
@@ -672,6 +732,11 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
         d.sin_t = std::sin(th);
         d.kin = q.kinematic ? 1 : 0;
         d.inst = inst;
+        for (int a = 0; a < 3; a++) d.xf[a] = d.xfo[a] = (float)q.x[a];
+        // margin of the single-precision inside/outside decision: the float copy of
+        // the centre is within 2^-24 |x| of it, far below 0.05 in |x - x_p|^2
+        d.R2lo = (float)(q.R_p * q.R_p - 0.05);
+        d.R2hi = (float)(q.R_p * q.R_p + 0.05);
         d.local = I.np + k;
         // Sec. V G: gamma_n < 2 sqrt(k_n m) and a resolved collision time
         if (!d.kin) {
@@ -706,10 +771,13 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
             for (auto &q : add) { all.push_back(q); cnt++; }
         ctx->inst_h[k].np = cnt;
     }
-    int hist = 0;
+    int hist = 0, crec = 0;
     for (int k = 0; k < ctx->n_inst; k++) {
+        const int npk = ctx->inst_h[k].np;
         ctx->inst_h[k].hist_off = hist;
-        hist += ctx->inst_h[k].np * (ctx->inst_h[k].np + 1);
+        hist += npk * (npk + 1);
+        ctx->inst_h[k].crec_off = crec;
+        crec += npk + npk * (npk - 1) / 2;
     }
     double Rmax = 0.0;
     for (auto &q : all) Rmax = std::max(Rmax, q.R);
@@ -718,6 +786,8 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     ctx->parts_h = all;
     ctx->mem_blocks = (int)(((long long)mem_side * mem_side * mem_side + PART_THREADS - 1) / PART_THREADS);
     ctx->geom_side = 2 * (int)std::ceil(Rmax) + 4 * GEOM_MARGIN + 3;
+    ctx->cap_side = 2 * (int)std::ceil(Rmax) + 11;
+    ctx->cap_blocks = (int)(((long long)ctx->cap_side * ctx->cap_side * ctx->cap_side + PART_THREADS - 1) / PART_THREADS);
     long long gs3 = (long long)(ctx->geom_side + 2) * (ctx->geom_side + 2) * (ctx->geom_side + 2);
     ctx->geom_blocks = (int)std::min<long long>((gs3 + PART_THREADS - 1) / PART_THREADS, 256);
     const size_t np = all.size();
@@ -726,12 +796,14 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     cudaFree(ctx->mem_part);
     cudaFree(ctx->cap_part);
     cudaFree(ctx->hist);
+    cudaFree(ctx->crec);
     ctx->parts_d = nullptr;
-    ctx->mem_part = ctx->cap_part = ctx->hist = nullptr;
+    ctx->mem_part = ctx->cap_part = ctx->hist = ctx->crec = nullptr;
     CU(cudaMalloc((void **)&ctx->parts_d, sizeof(PartDev) * np));
     CU(cudaMalloc((void **)&ctx->mem_part, sizeof(double) * 6 * np * ctx->mem_blocks));
     CU(cudaMalloc((void **)&ctx->cap_part, sizeof(double) * 6 * np * CAP_BLOCKS));
     CU(cudaMalloc((void **)&ctx->hist, sizeof(double) * 6 * std::max(hist, 1)));
+    CU(cudaMalloc((void **)&ctx->crec, sizeof(double) * 12 * std::max(crec, 1)));
     CU(cudaMemsetAsync(ctx->hist, 0, sizeof(double) * 6 * std::max(hist, 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->mem_part, 0, sizeof(double) * 6 * np * ctx->mem_blocks, ctx->stream));
     CU(cudaMemsetAsync(ctx->cap_part, 0, sizeof(double) * 6 * np * CAP_BLOCKS, ctx->stream));
@@ -898,7 +970,7 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads)
 {
     if (!ctx) return LBM_ERR_ARG;
     int bt = block_threads == 0 ? 256 : block_threads;
-    if (bt < 64 || bt > 1024 || bt % 32) return fail(ctx, LBM_ERR_ARG, "block_threads must be a multiple of 32 in [64, 1024]");
+    if (bt < 64 || bt > 256 || bt % 32) return fail(ctx, LBM_ERR_ARG, "block_threads must be a multiple of 32 in [64, 256]");
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->bt = bt;
     long long blk = 0;
@@ -915,6 +987,23 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads)
 }
 
 long long lbm_last_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->last_launches : -1; }
+
+lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int fused, int tile, int zchunk)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if ((fused != 0 && fused != 1) || tile < 0 || tile > 2 || zchunk < 0)
+        return fail(ctx, LBM_ERR_ARG, "fused must be 0/1, tile 0..2, zchunk >= 0");
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->fz.fused = fused;
+    ctx->fz.tile = tile;
+    ctx->zc_request = zchunk;
+    plan_fused(ctx);
+    CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    drop_graph(ctx);
+    return LBM_OK;
+}
 
 lbm_status lbm_profile(lbm_ctx *ctx, int enable)
 {

@@ -60,6 +60,7 @@ struct InstDev {
     long long blk_start; // first fluid block of the instance
     int part_off;        // first particle of the instance
     int hist_off;        // first pair-history record of the instance
+    int crec_off;        // first DEM contact record of the instance
     int wall_z0, store_u;
     double rho0, sigma, beta, cap_norm, eta_a, eta_b;
     double body_a[3], body_b[3], wall_u[3];
@@ -67,7 +68,36 @@ struct InstDev {
     double grad_eps, wet_max;
     double kn, kt, kr, gn, gt, gr, mu_s, mu_r, dR;
     double g_part[3];
+    // single-precision copies of the fluid parameters (no FP64 conversions in
+    // the FP32 and 16-bit kernels)
+    float f_rho0, f_sigma, f_beta, f_eta_a, f_eta_b, f_eps2, f_wet_max;
+    float f_body_a[3], f_body_b[3];
+    float f_ir0, f_h_ia, f_h_ib;
+    // fused-kernel work items: tiles_x * tiles_y column tiles x nchunks z-chunks
+    long long item_start;
+    int tiles_x, tiles_y, nchunks, zc;
 };
+
+// fluid parameters in the arithmetic precision R
+template <class R>
+struct FluidPar {
+    R rho0, sigma, beta, eta_a, eta_b, eps2, wet_max, ba[3], bb[3];
+    R ir0, h_ia, h_ib;  // 1/rho0, 1/(2 eta_a), 1/(2 eta_b)
+};
+__device__ __forceinline__ void load_par(const InstDev &I, FluidPar<double> &p)
+{
+    p.rho0 = I.rho0; p.sigma = I.sigma; p.beta = I.beta; p.eta_a = I.eta_a; p.eta_b = I.eta_b;
+    p.eps2 = I.grad_eps * I.grad_eps; p.wet_max = I.wet_max;
+    for (int a = 0; a < 3; a++) { p.ba[a] = I.body_a[a]; p.bb[a] = I.body_b[a]; }
+    p.ir0 = 1.0 / I.rho0; p.h_ia = 0.5 / I.eta_a; p.h_ib = 0.5 / I.eta_b;
+}
+__device__ __forceinline__ void load_par(const InstDev &I, FluidPar<float> &p)
+{
+    p.rho0 = I.f_rho0; p.sigma = I.f_sigma; p.beta = I.f_beta; p.eta_a = I.f_eta_a; p.eta_b = I.f_eta_b;
+    p.eps2 = I.f_eps2; p.wet_max = I.f_wet_max;
+    for (int a = 0; a < 3; a++) { p.ba[a] = I.f_body_a[a]; p.bb[a] = I.f_body_b[a]; }
+    p.ir0 = I.f_ir0; p.h_ia = I.f_h_ia; p.h_ib = I.f_h_ib;
+}
 
 struct PartDev {
     double x[3], v[3], w[3], q[4];
@@ -75,6 +105,8 @@ struct PartDev {
     double R, Rc, m, I, cos_t, sin_t;
     double Fp[3], Tp[3];
     double Feta[3], Teta[3], Fsig[3], Tsig[3], Fc[3], Tc[3];
+    float xf[3], xfo[3];  // single-precision copies of x and x_old
+    float R2lo, R2hi;     // |x - x_p|^2 below / above these is inside / outside for sure
     int kin, inst, local, mem_side;
 };
 
@@ -86,7 +118,8 @@ struct Lattice {
     uint8_t *flags;
     void *pop[2];
     void *phi;           // [Ntot] real
-    void *grad;          // [3][Ntot] real
+    void *grad;          // [3][Ntot] real: regularised interface normal n
+    void *gmag;          // [Ntot] real: sqrt(|grad phi|^2 + eps^2), so grad phi = n gmag
     void *u;             // [3][Ntot] real (store_velocity)
     long long Ntot;
     PartDev *parts;
@@ -94,9 +127,13 @@ struct Lattice {
     int mem_blocks;      // blocks per particle of the momentum-exchange kernel
     int geom_blocks;     // blocks per particle of the geometry kernels
     int geom_side;       // side of the cube the geometry kernels cover
+    int cap_side;        // side of the cube of phi around a particle for the capillary force
+    int cap_blocks;      // blocks per particle covering that cube
     double *mem_part;    // [n_parts][mem_blocks][6]
     double *cap_part;    // [n_parts][CAP_BLOCKS][6]
+    const double *cap_pts;  // [CAP_POINTS][4]: unit normal (3) and sin(alpha) of each surface point
     double *hist;        // contact springs: per instance np*(np+1) records of 6
+    double *crec;        // DEM contact forces: per instance np + np(np-1)/2 records of 12
     unsigned *status;
 };
 
@@ -138,29 +175,35 @@ __device__ __forceinline__ int find_inst(const InstDev *I, int n, long long blk)
     return lo;
 }
 
+// minimum-image displacement on a periodic axis of n nodes (|d| < 3n/2): the
+// same value as d - n floor(d/n + 1/2) without a double-precision division
 __host__ __device__ __forceinline__ double min_image(double d, int n)
 {
-    return d - n * floor(d / n + 0.5);
+    const double h = 0.5 * n;
+    return d >= h ? d - n : (d < -h ? d + n : d);
 }
 
-// periodic neighbourhood of one node
+// periodic neighbourhood of one node: x coordinates and row/plane offsets of
+// x-1..x+1, y-1..y+1, z-1..z+1 (instance-local 32-bit node indices; every
+// instance has fewer than 2^31/38 nodes)
 struct Nbr {
-    int X[3], Y[3], Z[3];
-    int nx;
-    long long nxy;
+    int X[3], YO[3], ZO[3];
     __device__ __forceinline__ void init(int x, int y, int z, int nx_, int ny_, int nz_)
     {
-        nx = nx_;
-        nxy = (long long)nx_ * ny_;
+        const int nxy = nx_ * ny_;
         X[0] = x == 0 ? nx_ - 1 : x - 1; X[1] = x; X[2] = x == nx_ - 1 ? 0 : x + 1;
-        Y[0] = y == 0 ? ny_ - 1 : y - 1; Y[1] = y; Y[2] = y == ny_ - 1 ? 0 : y + 1;
-        Z[0] = z == 0 ? nz_ - 1 : z - 1; Z[1] = z; Z[2] = z == nz_ - 1 ? 0 : z + 1;
+        YO[0] = (y == 0 ? ny_ - 1 : y - 1) * nx_; YO[1] = y * nx_; YO[2] = (y == ny_ - 1 ? 0 : y + 1) * nx_;
+        ZO[0] = (z == 0 ? nz_ - 1 : z - 1) * nxy; ZO[1] = z * nxy; ZO[2] = (z == nz_ - 1 ? 0 : z + 1) * nxy;
     }
-    __device__ __forceinline__ long long at(int dx, int dy, int dz) const
-    {
-        return (long long)Z[dz + 1] * nxy + (long long)Y[dy + 1] * nx + X[dx + 1];
-    }
+    __device__ __forceinline__ int at(int dx, int dy, int dz) const { return ZO[dz + 1] + YO[dy + 1] + X[dx + 1]; }
 };
+
+// reciprocal and inverse square root: IEEE for double, the fast single-precision
+// forms otherwise (the FP32 and 16-bit paths are held to 1e-4 / 2e-3)
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double frsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 
 // velocity of the solid owning a node at the point xw (Sec. V A)
 __device__ __forceinline__ void surface_velocity(const InstDev &I, const PartDev *parts, int owner,
@@ -181,56 +224,117 @@ __device__ __forceinline__ void surface_velocity(const InstDev &I, const PartDev
     lev[0] = d0; lev[1] = d1; lev[2] = d2;
 }
 
+// cube of side `side` (clamped to the domain) centred on a particle's node
+struct Region {
+    int lo[3], sz[3];
+    __device__ __forceinline__ void init(const double *xc, int side, int nx, int ny, int nz)
+    {
+        const int n[3] = {nx, ny, nz};
+        for (int a = 0; a < 3; a++) {
+            int s = side < n[a] ? side : n[a];
+            sz[a] = s;
+            int lo_ = (int)floor(xc[a]) - (s - 1) / 2;
+            lo[a] = s == n[a] ? 0 : lo_;
+        }
+    }
+    __device__ __forceinline__ long long count() const { return (long long)sz[0] * sz[1] * sz[2]; }
+    __device__ __forceinline__ void coord(long long t, int nx, int ny, int nz, int *x, int *y, int *z) const
+    {
+        int i = (int)(t % sz[0]);
+        int j = (int)((t / sz[0]) % sz[1]);
+        int k = (int)(t / ((long long)sz[0] * sz[1]));
+        *x = ((lo[0] + i) % nx + nx) % nx;
+        *y = ((lo[1] + j) % ny + ny) % ny;
+        *z = ((lo[2] + k) % nz + nz) % nz;
+    }
+};
+
+// neighbourhood of a node in global memory: node index and owner of the node
+// at offset (dx, dy, dz), periodic
+struct GlobalNbr {
+    Nbr nb;
+    const uint8_t *fli;  // flags of the instance
+    __device__ __forceinline__ int idx(int dx, int dy, int dz) const { return nb.at(dx, dy, dz); }
+    __device__ __forceinline__ int own(int dx, int dy, int dz) const { return fli[nb.at(dx, dy, dz)] & OWNER_MASK; }
+};
+
 // Pull streaming of both components into node n (Sec. IV streaming), with the
 // Sec. V A halfway bounce-back where the source node is solid:
 //   f_i(x) = f*_ibar(x) + 6 w_i rho^{a,b}(x) c_i.u_w,  rho^{a,b}(x) taken from
 // the node's own pre-streaming populations, u_w at the link midpoint.
-template <class S>
-__device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, const uint8_t *flags,
-                                       const S *__restrict__ in, long long N, long long n, const Nbr &nb,
-                                       uint8_t fl, typename Store<S>::real *F, typename Store<S>::real *G,
-                                       int x, int y, int z)
+// A is the neighbourhood accessor (global flags, or a shared-memory copy).
+template <class S, class A>
+__device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, const A &nbr,
+                                       const S *__restrict__ in, int N, int n, uint8_t fl,
+                                       typename Store<S>::real *F, typename Store<S>::real *G, int x, int y, int z)
 {
     using R = typename Store<S>::real;
-    const uint8_t *fli = flags + I.node_off;
     if (!(fl & BOUND_BIT)) {
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            long long s = nb.at(-cx(i), -cy(i), -cz(i));
-            F[i] = Store<S>::ld(in + (long long)i * N + s);
-            G[i] = Store<S>::ld(in + (long long)(Q + i) * N + s);
+            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
+            F[i] = Store<S>::ld(in + i * N + s);
+            G[i] = Store<S>::ld(in + (Q + i) * N + s);
         }
         return;
     }
     bool have_rho = false;
-    double rr = 0.0, rd = 0.0;  // rho/rho0 and (rho^a - rho^b)/rho0 of this node
+    R rr = 0, rd = 0;  // rho/rho0 and (rho^a - rho^b)/rho0 of this node
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        long long s = nb.at(-cx(i), -cy(i), -cz(i));
-        int own = fli[s] & OWNER_MASK;
+        const int own = nbr.own(-cx(i), -cy(i), -cz(i));
         if (own == OWN_FLUID) {
-            F[i] = Store<S>::ld(in + (long long)i * N + s);
-            G[i] = Store<S>::ld(in + (long long)(Q + i) * N + s);
+            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
+            F[i] = Store<S>::ld(in + i * N + s);
+            G[i] = Store<S>::ld(in + (Q + i) * N + s);
             continue;
         }
         if (!have_rho) {
-            double sF = 0.0, sG = 0.0;
+            R sF = 0, sG = 0;
 #pragma unroll
             for (int j = 0; j < Q; j++) {
-                sF += wgt<double>(j) * (double)Store<S>::ld(in + (long long)j * N + n);
-                sG += wgt<double>(j) * (double)Store<S>::ld(in + (long long)(Q + j) * N + n);
+                sF += wgt<R>(j) * Store<S>::ld(in + j * N + n);
+                sG += wgt<R>(j) * Store<S>::ld(in + (Q + j) * N + n);
             }
-            rr = 1.0 + sF;
+            rr = R(1) + sF;
             rd = sG;
             have_rho = true;
         }
         double uw[3], lev[3];
         surface_velocity(I, parts, own, x - 0.5 * cx(i), y - 0.5 * cy(i), z - 0.5 * cz(i), uw, lev);
-        double cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
+        const R cu = (R)(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
         const int ib = opp(i);
-        F[i] = (R)((double)Store<S>::ld(in + (long long)ib * N + n) + 6.0 * rr * cu);
-        G[i] = (R)((double)Store<S>::ld(in + (long long)(Q + ib) * N + n) + 6.0 * rd * cu);
+        F[i] = Store<S>::ld(in + ib * N + n) + R(6) * rr * cu;
+        G[i] = Store<S>::ld(in + (Q + ib) * N + n) + R(6) * rd * cu;
     }
+}
+
+// order parameter of a fluid node after streaming: the same sums as the
+// collision's, without keeping the 38 values
+template <class S, class A>
+__device__ __forceinline__ typename Store<S>::real node_phi(const InstDev &I, const PartDev *parts, const A &nbr,
+                                                            const S *__restrict__ in, int N, int n, uint8_t fl,
+                                                            int x, int y, int z)
+{
+    using R = typename Store<S>::real;
+    R sF = 0, sG = 0;
+    if (!(fl & BOUND_BIT)) {
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
+            sF += wgt<R>(i) * Store<S>::ld(in + i * N + s);
+            sG += wgt<R>(i) * Store<S>::ld(in + (Q + i) * N + s);
+        }
+        return sG / (R(1) + sF);
+    }
+    R F[Q], G[Q];
+    gather<S>(I, parts, nbr, in, N, n, fl, F, G, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        sF += wgt<R>(i) * F[i];
+        sG += wgt<R>(i) * G[i];
+    }
+    return sG / (R(1) + sF);
 }
 
 template <class R>
@@ -266,7 +370,7 @@ __device__ __forceinline__ void wetting_rotate(R *g, const R *ns, R cth, R sth)
 // kernel stages, in launch order within a step (for per-kernel timing)
 enum Stage {
     STAGE_PHI = 0, STAGE_SOLIDPHI, STAGE_GRAD, STAGE_COLLIDE, STAGE_MEM, STAGE_CAPILLARY, STAGE_DEM,
-    STAGE_GEOM_OWNER, STAGE_GEOM_BOUND, STAGE_REFILL, N_STAGES
+    STAGE_GEOM_OWNER, STAGE_GEOM_BOUND, STAGE_REFILL, STAGE_FUSED, STAGE_REGION, N_STAGES
 };
 
 // optional per-kernel marker: called right before and right after each launch
@@ -280,8 +384,16 @@ struct Marker {
 };
 
 // host-side kernel launchers (defined in the .cu files)
+struct FluidLaunch {
+    int fused;       // 1: one fused kernel per step, 0: the four-kernel form
+    int tile;        // fused tile shape index (see lbm_fluid.cu)
+    long long items; // fused work items (all instances)
+};
 template <class S>
-void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk);
+void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
+                       const FluidLaunch &fz);
+int fused_tile_x(int tile);
+int fused_tile_y(int tile);
 template <class S>
 void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk);
 template <class S>

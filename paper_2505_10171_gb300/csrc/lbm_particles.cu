@@ -1,41 +1,21 @@
 // Particle kernels of one coupled time step (Sec. III and V of arXiv 2505.10171):
-//   k_mem       momentum-exchange force and torque per particle (Sec. V B)
-//   k_capillary capillary force and torque from the Lagrangian surface points
-//               (Sec. V E)
-//   k_dem       contacts (normal spring-dashpot, Luding sliding and rolling
-//               friction) and velocity-Verlet update, FP64 (Sec. III)
-//   k_geom_*    solid map update and refilling of uncovered nodes (Sec. V C)
-// Per-particle sums are reduced in FP64 with a fixed order (warp shuffle,
-// block tree, then a fixed-order sum over blocks inside k_dem), so results are
-// reproducible run to run.
+//   k_mem        momentum-exchange force and torque per particle (Sec. V B)
+//   k_capillary  capillary force and torque from the Lagrangian surface points
+//                (Sec. V E)
+//   k_part_sums  fixed-order sums of the per-block partials of both
+//   k_dem        contacts (normal spring-dashpot, Luding sliding and rolling
+//                friction) and velocity-Verlet update, FP64 (Sec. III): one
+//                thread per contact, then one per particle
+//   k_geom_*     solid map update and refilling of uncovered nodes (Sec. V C)
+// Per-link and per-point arithmetic runs in the storage precision's arithmetic
+// type (double for FP64 storage, float otherwise); every sum over links,
+// points or contacts is FP64 with a fixed order (warp shuffle, block tree,
+// fixed block order), so results are reproducible run to run.  GB300 executes
+// double precision at a small fraction of the single-precision rate, so the
+// FP64 work is kept to the sums and the DEM.
 #include "lbm_internal.cuh"
 
 namespace lbmg {
-
-// cube of side `side` (clamped to the domain) centred on a particle's node
-struct Region {
-    int lo[3], sz[3];
-    __device__ __forceinline__ void init(const double *xc, int side, int nx, int ny, int nz)
-    {
-        const int n[3] = {nx, ny, nz};
-        for (int a = 0; a < 3; a++) {
-            int s = side < n[a] ? side : n[a];
-            sz[a] = s;
-            int lo_ = (int)floor(xc[a]) - (s - 1) / 2;
-            lo[a] = s == n[a] ? 0 : lo_;
-        }
-    }
-    __device__ __forceinline__ long long count() const { return (long long)sz[0] * sz[1] * sz[2]; }
-    __device__ __forceinline__ void coord(long long t, int nx, int ny, int nz, int *x, int *y, int *z) const
-    {
-        int i = (int)(t % sz[0]);
-        int j = (int)((t / sz[0]) % sz[1]);
-        int k = (int)(t / ((long long)sz[0] * sz[1]));
-        *x = ((lo[0] + i) % nx + nx) % nx;
-        *y = ((lo[1] + j) % ny + ny) % ny;
-        *z = ((lo[2] + k) % nz + nz) % nz;
-    }
-};
 
 // deterministic block sum of 6 doubles; thread 0 writes them to out
 __device__ __forceinline__ void block_sum6(double *v, double *out)
@@ -57,6 +37,17 @@ __device__ __forceinline__ void block_sum6(double *v, double *out)
     }
 }
 
+// particle centre in the arithmetic type R (single-precision copy for float)
+__device__ __forceinline__ void centre(const PartDev &P, double *c) { c[0] = P.x[0]; c[1] = P.x[1]; c[2] = P.x[2]; }
+__device__ __forceinline__ void centre(const PartDev &P, float *c) { c[0] = P.xf[0]; c[1] = P.xf[1]; c[2] = P.xf[2]; }
+
+template <class R>
+__device__ __forceinline__ R min_image_r(R d, int n)
+{
+    const R h = R(0.5) * n;
+    return d >= h ? d - n : (d < -h ? d + n : d);
+}
+
 // Sec. V B momentum exchange (Wen 2014, Galilean invariant): per link from a
 // fluid node x into particle p, force on p = (c_out - u_w) f_out - (c_in - u_w) f_in
 // with f_out = f*_ibar(x) leaving towards the solid and f_in = f_i(x) bounced
@@ -64,10 +55,11 @@ __device__ __forceinline__ void block_sum6(double *v, double *out)
 template <class S>
 __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
 {
+    using R = typename Store<S>::real;
     const int p = blockIdx.y;
     const PartDev &P = L.parts[p];
     const InstDev &I = L.inst[P.inst];
-    const long long N = I.N;
+    const int N = (int)I.N;
     Region reg;
     reg.init(P.x, P.mem_side, I.nx, I.ny, I.nz);
     double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -75,7 +67,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
     if (t < reg.count()) {
         int x, y, z;
         reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
-        const long long n = ((long long)z * I.ny + y) * I.nx + x;
+        const int n = (z * I.ny + y) * I.nx + x;
         const uint8_t *fli = L.flags + I.node_off;
         const uint8_t fl = fli[n];
         if ((fl & OWNER_MASK) == OWN_FLUID && (fl & BOUND_BIT)) {
@@ -83,42 +75,48 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
             Nbr nb;
             nb.init(x, y, z, I.nx, I.ny, I.nz);
             const int mine = 2 + P.local;
-            double rr = -1.0;
-            const double wr0 = I.rho0;
+            R rr = -1;
+            R c[3], v[3], w[3];
+            centre(P, c);
+            for (int a = 0; a < 3; a++) { v[a] = (R)P.v[a]; w[a] = (R)P.w[a]; }
+            const R wr0 = (R)I.rho0;
             for (int i = 1; i < Q; i++) {
-                long long s = nb.at(-cx(i), -cy(i), -cz(i));
-                if ((fli[s] & OWNER_MASK) != mine) continue;
-                if (rr < 0.0) {
-                    double sF = 0.0;
-                    for (int j = 0; j < Q; j++) sF += wgt<double>(j) * (double)Store<S>::ld(in + (long long)j * N + n);
-                    rr = 1.0 + sF;
+                if ((fli[nb.at(-cx(i), -cy(i), -cz(i))] & OWNER_MASK) != mine) continue;
+                if (rr < R(0)) {
+                    R sF = 0;
+                    for (int j = 0; j < Q; j++) sF += wgt<R>(j) * Store<S>::ld(in + j * N + n);
+                    rr = R(1) + sF;
                 }
-                double uw[3], lev[3];
-                surface_velocity(I, L.parts, mine, x - 0.5 * cx(i), y - 0.5 * cy(i), z - 0.5 * cz(i), uw, lev);
+                const R lev[3] = {min_image_r<R>(x - R(0.5) * cx(i) - c[0], I.nx),
+                                  min_image_r<R>(y - R(0.5) * cy(i) - c[1], I.ny),
+                                  min_image_r<R>(z - R(0.5) * cz(i) - c[2], I.nz)};
+                const R uw[3] = {v[0] + (w[1] * lev[2] - w[2] * lev[1]), v[1] + (w[2] * lev[0] - w[0] * lev[2]),
+                                 v[2] + (w[0] * lev[1] - w[1] * lev[0])};
                 const int ib = opp(i);
-                const double w = wgt<double>(i) * wr0;
-                const double Fo = (double)Store<S>::ld(in + (long long)ib * N + n);
-                const double cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
-                const double fout = w * (1.0 + Fo);
-                const double fin = w * (1.0 + Fo + 6.0 * rr * cu);
-                const double ci[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
-                double dp[3];
+                const R wt = wgt<R>(i) * wr0;
+                const R Fo = Store<S>::ld(in + ib * N + n);
+                const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
+                const R fout = wt * (R(1) + Fo);
+                const R fin = wt * (R(1) + Fo + R(6) * rr * cu);
+                const R ci[3] = {(R)cx(i), (R)cy(i), (R)cz(i)};
+                R dp[3];
                 for (int a = 0; a < 3; a++) dp[a] = (-ci[a] - uw[a]) * fout - (ci[a] - uw[a]) * fin;
-                acc[0] += dp[0];
-                acc[1] += dp[1];
-                acc[2] += dp[2];
-                acc[3] += lev[1] * dp[2] - lev[2] * dp[1];
-                acc[4] += lev[2] * dp[0] - lev[0] * dp[2];
-                acc[5] += lev[0] * dp[1] - lev[1] * dp[0];
+                acc[0] += (double)dp[0];
+                acc[1] += (double)dp[1];
+                acc[2] += (double)dp[2];
+                acc[3] += (double)(lev[1] * dp[2] - lev[2] * dp[1]);
+                acc[4] += (double)(lev[2] * dp[0] - lev[0] * dp[2]);
+                acc[5] += (double)(lev[0] * dp[1] - lev[1] * dp[0]);
             }
         }
     }
     block_sum6(acc, L.mem_part + ((long long)p * L.mem_blocks + blockIdx.x) * 6);
 }
 
-// Sec. V E: dF = C sigma (1 - phi^2) dA [n_s - (n.n_s) n] at the points
-// alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg on r = R_p; phi and grad(phi)
-// trilinearly interpolated over fluid corners only; torque R_p n_s x dF.
+// Sec. V E: dF = C sigma (1 - phi^2) dA (n x n_s) x n at the points
+// alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg on r = R_p, n the regularised
+// normal of the trilinearly interpolated grad(phi) (fluid corners only);
+// torque R_p n_s x dF.
 template <class R>
 __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
 {
@@ -128,69 +126,98 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const int pt = blockIdx.x * blockDim.x + threadIdx.x;
     if (pt < CAP_POINTS) {
-        const int j = pt / 180, k = pt % 180;
-        const double da = 2.0 * M_PI / 180.0;
-        const double al = (j + 0.5) * da, vp = k * da;
-        const double sa = sin(al), ca = cos(al), sv = sin(vp), cv = cos(vp);
-        const double ns[3] = {sa * cv, sa * sv, ca};
-        const double xi[3] = {P.x[0] + P.R * ns[0], P.x[1] + P.R * ns[1], P.x[2] + P.R * ns[2]};
-        const double dA = P.R * P.R * sa * da * da;
+        const double *tp = L.cap_pts + 4 * pt;
+        const R ns[3] = {(R)tp[0], (R)tp[1], (R)tp[2]};
+        const R sa = (R)tp[3];
+        const R da = R(2.0 * M_PI / 180.0);
+        R c[3];
+        centre(P, c);
+        const R Rp = (R)P.R;
+        const R xi[3] = {c[0] + Rp * ns[0], c[1] + Rp * ns[1], c[2] + Rp * ns[2]};
+        const R dA = Rp * Rp * sa * da * da;
         int b[3];
-        double fr[3];
+        R fr[3];
         for (int a = 0; a < 3; a++) {
-            double fl = floor(xi[a]);
+            const R fl = floor(xi[a]);
             b[a] = (int)fl;
             fr[a] = xi[a] - fl;
         }
         const int n3[3] = {I.nx, I.ny, I.nz};
         const uint8_t *fli = L.flags + I.node_off;
         const R *ph = (const R *)L.phi + I.node_off;
-        const R *G = (const R *)L.grad + I.node_off;
-        double ws = 0.0, phs = 0.0, gs[3] = {0, 0, 0};
+        const R *Gn = (const R *)L.grad + I.node_off;   // regularised normal
+        const R *Gm = (const R *)L.gmag + I.node_off;   // its norm: grad phi = n gmag
+        R ws = 0, phs = 0, gs[3] = {0, 0, 0};
         for (int cz_ = 0; cz_ < 2; cz_++)
             for (int cy_ = 0; cy_ < 2; cy_++)
                 for (int cx_ = 0; cx_ < 2; cx_++) {
-                    int X = ((b[0] + cx_) % n3[0] + n3[0]) % n3[0];
-                    int Y = ((b[1] + cy_) % n3[1] + n3[1]) % n3[1];
-                    int Z = ((b[2] + cz_) % n3[2] + n3[2]) % n3[2];
-                    long long m = ((long long)Z * I.ny + Y) * I.nx + X;
+                    int X = b[0] + cx_, Y = b[1] + cy_, Z = b[2] + cz_;
+                    X = X < 0 ? X + n3[0] : (X >= n3[0] ? X - n3[0] : X);
+                    Y = Y < 0 ? Y + n3[1] : (Y >= n3[1] ? Y - n3[1] : Y);
+                    Z = Z < 0 ? Z + n3[2] : (Z >= n3[2] ? Z - n3[2] : Z);
+                    const long long m = ((long long)Z * I.ny + Y) * I.nx + X;
                     if ((fli[m] & OWNER_MASK) != OWN_FLUID) continue;
-                    double wgt_ = (cx_ ? fr[0] : 1.0 - fr[0]) * (cy_ ? fr[1] : 1.0 - fr[1]) *
-                                  (cz_ ? fr[2] : 1.0 - fr[2]);
+                    const R wgt_ = (cx_ ? fr[0] : R(1) - fr[0]) * (cy_ ? fr[1] : R(1) - fr[1]) *
+                                   (cz_ ? fr[2] : R(1) - fr[2]);
+                    const R mg = Gm[m];
                     ws += wgt_;
-                    phs += wgt_ * (double)ph[m];
-                    gs[0] += wgt_ * (double)G[m];
-                    gs[1] += wgt_ * (double)G[L.Ntot + m];
-                    gs[2] += wgt_ * (double)G[2 * L.Ntot + m];
+                    phs += wgt_ * ph[m];
+                    gs[0] += wgt_ * (Gn[m] * mg);
+                    gs[1] += wgt_ * (Gn[L.Ntot + m] * mg);
+                    gs[2] += wgt_ * (Gn[2 * L.Ntot + m] * mg);
                 }
-        if (ws > 0.0) {
-            const double phv = phs / ws;
-            const double g0 = gs[0] / ws, g1 = gs[1] / ws, g2 = gs[2] / ws;
-            if (fabs(phv) < 1.0) {
-                // regularised normal n = g/sqrt(|g|^2 + eps^2), m = (n x n_s) x n
-                const double gr = sqrt(g0 * g0 + g1 * g1 + g2 * g2 + I.grad_eps * I.grad_eps);
-                const double nn[3] = {g0 / gr, g1 / gr, g2 / gr};
-                const double c0 = nn[1] * ns[2] - nn[2] * ns[1], c1 = nn[2] * ns[0] - nn[0] * ns[2],
-                             c2 = nn[0] * ns[1] - nn[1] * ns[0];
-                const double mv[3] = {c1 * nn[2] - c2 * nn[1], c2 * nn[0] - c0 * nn[2], c0 * nn[1] - c1 * nn[0]};
-                const double coef = I.cap_norm * I.sigma * (1.0 - phv * phv) * dA;
-                double dF[3];
+        if (ws > R(0)) {
+            const R phv = phs / ws;
+            const R g0 = gs[0] / ws, g1 = gs[1] / ws, g2 = gs[2] / ws;
+            if (fabs(phv) < R(1)) {
+                const R eps2 = (R)(I.grad_eps * I.grad_eps);
+                const R gr = sqrt(g0 * g0 + g1 * g1 + g2 * g2 + eps2);
+                const R nn[3] = {g0 / gr, g1 / gr, g2 / gr};
+                const R c0 = nn[1] * ns[2] - nn[2] * ns[1], c1 = nn[2] * ns[0] - nn[0] * ns[2],
+                        c2 = nn[0] * ns[1] - nn[1] * ns[0];
+                const R mv[3] = {c1 * nn[2] - c2 * nn[1], c2 * nn[0] - c0 * nn[2], c0 * nn[1] - c1 * nn[0]};
+                const R coef = (R)(I.cap_norm * I.sigma) * (R(1) - phv * phv) * dA;
+                R dF[3];
                 for (int a = 0; a < 3; a++) dF[a] = coef * mv[a];
-                const double r[3] = {P.R * ns[0], P.R * ns[1], P.R * ns[2]};
-                acc[0] = dF[0];
-                acc[1] = dF[1];
-                acc[2] = dF[2];
-                acc[3] = r[1] * dF[2] - r[2] * dF[1];
-                acc[4] = r[2] * dF[0] - r[0] * dF[2];
-                acc[5] = r[0] * dF[1] - r[1] * dF[0];
+                const R r[3] = {Rp * ns[0], Rp * ns[1], Rp * ns[2]};
+                acc[0] = (double)dF[0];
+                acc[1] = (double)dF[1];
+                acc[2] = (double)dF[2];
+                acc[3] = (double)(r[1] * dF[2] - r[2] * dF[1]);
+                acc[4] = (double)(r[2] * dF[0] - r[0] * dF[2]);
+                acc[5] = (double)(r[0] * dF[1] - r[1] * dF[0]);
             }
         }
     }
     block_sum6(acc, L.cap_part + ((long long)p * CAP_BLOCKS + blockIdx.x) * 6);
 }
 
+// fluid forces of this step: each particle's block partials of the momentum
+// exchange and capillary kernels summed by one warp, lanes over a fixed
+// block stride and then a fixed shuffle tree (deterministic)
+__global__ void k_part_sums(Lattice L)
+{
+    const int p = blockIdx.x;
+    const int lane = threadIdx.x;
+    double s[12];
+    for (int a = 0; a < 12; a++) s[a] = 0.0;
+    for (int b = lane; b < L.mem_blocks; b += 32)
+        for (int a = 0; a < 6; a++) s[a] += L.mem_part[((long long)p * L.mem_blocks + b) * 6 + a];
+    for (int b = lane; b < CAP_BLOCKS; b += 32)
+        for (int a = 0; a < 6; a++) s[6 + a] += L.cap_part[((long long)p * CAP_BLOCKS + b) * 6 + a];
+    for (int o = 16; o > 0; o >>= 1)
+        for (int a = 0; a < 12; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
+    if (lane == 0) {
+        PartDev &P = L.parts[p];
+        for (int a = 0; a < 3; a++) {
+            P.Feta[a] = s[a]; P.Teta[a] = s[3 + a];
+            P.Fsig[a] = s[6 + a]; P.Tsig[a] = s[9 + a];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
-// DEM (Sec. III), one thread per instance, FP64.
+// DEM (Sec. III), FP64.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 __device__ __forceinline__ void cross3(const double *a, const double *b, double *r)
@@ -219,9 +246,10 @@ __device__ void dem_spring(double *xi, const double *n, const double *v, double 
 // contact of particle i with partner j (j < 0: substrate); n from partner to
 // i, delta > 0 the overlap.  Contact point X_i - (R_c,i - delta/2) n;
 // F_n = [k_n delta - g_n v_rel.n] n; rolling velocity -a'(w_i - w_j) x n with
-// torque -a' n x F_r on i (+a' n x F_r on j).
-__device__ void dem_contact(const InstDev &I, PartDev *P, int i, int j, const double *vp, const double *wp,
-                            const double *n, double delta, double *xi, double *xir)
+// torque -a' n x F_r on i (+a' n x F_r on j).  rec receives the force and
+// torque on i, then on j.
+__device__ void dem_contact(const InstDev &I, const PartDev *P, int i, int j, const double *vp, const double *wp,
+                            const double *n, double delta, double *xi, double *xir, double *rec)
 {
     double bi[3], bj[3] = {0, 0, 0}, t[3], vi[3], vj[3];
     for (int a = 0; a < 3; a++) bi[a] = -(P[i].Rc - 0.5 * delta) * n[a];
@@ -254,17 +282,13 @@ __device__ void dem_contact(const InstDev &I, PartDev *P, int i, int j, const do
     double Tt[3], Tr[3];
     cross3(bi, Ft, Tt);
     cross3(n, Fr, Tr);
+    double mFt[3] = {-Ft[0], -Ft[1], -Ft[2]}, Ttj[3];
+    cross3(bj, mFt, Ttj);
     for (int a = 0; a < 3; a++) {
-        P[i].Fc[a] += Fnm * n[a] + Ft[a];
-        P[i].Tc[a] += Tt[a] - ap * Tr[a];
-    }
-    if (j >= 0) {
-        double mFt[3] = {-Ft[0], -Ft[1], -Ft[2]}, Ttj[3];
-        cross3(bj, mFt, Ttj);
-        for (int a = 0; a < 3; a++) {
-            P[j].Fc[a] -= Fnm * n[a] + Ft[a];
-            P[j].Tc[a] += Ttj[a] + ap * Tr[a];
-        }
+        rec[a] = Fnm * n[a] + Ft[a];
+        rec[3 + a] = Tt[a] - ap * Tr[a];
+        rec[6 + a] = -(Fnm * n[a] + Ft[a]);
+        rec[9 + a] = Ttj[a] + ap * Tr[a];
     }
 }
 
@@ -283,95 +307,117 @@ __device__ void quat_rotate(double *q, const double *w)
 }
 
 constexpr int DEM_MAXP = 61;
+constexpr int DEM_THREADS = 64;
 
-__global__ void k_dem(Lattice L, int mem_blocks)
+// pair index c in [0, np(np-1)/2) -> (i, j), i < j, lexicographic
+__device__ __forceinline__ void pair_of(int c, int np, int *i, int *j)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L.n_inst) return;
-    const InstDev &I = L.inst[k];
-    if (I.np == 0) return;
-    PartDev *P = L.parts + I.part_off;
-    const int np = I.np;
-    double *hist = L.hist + (long long)I.hist_off * 6;
-    // fluid forces of this step: fixed-order sums of the block partials
-    for (int p = 0; p < np; p++) {
-        const long long gp = I.part_off + p;
-        double s[6] = {0, 0, 0, 0, 0, 0}, c[6] = {0, 0, 0, 0, 0, 0};
-        for (int b = 0; b < mem_blocks; b++)
-            for (int a = 0; a < 6; a++) s[a] += L.mem_part[(gp * mem_blocks + b) * 6 + a];
-        for (int b = 0; b < CAP_BLOCKS; b++)
-            for (int a = 0; a < 6; a++) c[a] += L.cap_part[(gp * CAP_BLOCKS + b) * 6 + a];
-        for (int a = 0; a < 3; a++) {
-            P[p].Feta[a] = s[a]; P[p].Teta[a] = s[3 + a];
-            P[p].Fsig[a] = c[a]; P[p].Tsig[a] = c[3 + a];
-        }
+    int a = 0;
+    while (c >= np - 1 - a) {
+        c -= np - 1 - a;
+        a++;
     }
-    // velocity Verlet predictor (dt = 1)
-    double vp[3 * DEM_MAXP], wp[3 * DEM_MAXP], xn[3 * DEM_MAXP];
-    for (int p = 0; p < np; p++) {
+    *i = a;
+    *j = a + 1 + c;
+}
+
+__device__ __forceinline__ int pair_index(int i, int j, int np) { return i * np - i * (i + 1) / 2 + (j - i - 1); }
+
+// one block per instance.  Velocity-Verlet predictor per particle; contact
+// forces one thread per contact (substrate contacts, then pairs), kept per
+// contact; corrector per particle, adding its contacts in a fixed order
+// (substrate, then partners in increasing index).
+__global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
+{
+    const InstDev &I = L.inst[blockIdx.x];
+    const int np = I.np;
+    if (np == 0) return;
+    PartDev *P = L.parts + I.part_off;
+    double *hist = L.hist + (long long)I.hist_off * 6;
+    double *rec = L.crec + (long long)I.crec_off * 12;
+    __shared__ double xn[3 * DEM_MAXP], vp[3 * DEM_MAXP], wp[3 * DEM_MAXP];
+    const int tid = threadIdx.x;
+    for (int p = tid; p < np; p += blockDim.x)
         for (int a = 0; a < 3; a++) {
-            P[p].x_old[a] = P[p].x[a];
             if (P[p].kin) {
                 xn[3 * p + a] = P[p].x[a] + P[p].v[a];
                 vp[3 * p + a] = P[p].v[a];
                 wp[3 * p + a] = P[p].w[a];
             } else {
-                double acc = P[p].Fp[a] / P[p].m, alp = P[p].Tp[a] / P[p].I;
+                const double acc = P[p].Fp[a] / P[p].m, alp = P[p].Tp[a] / P[p].I;
                 xn[3 * p + a] = P[p].x[a] + P[p].v[a] + 0.5 * acc;
                 vp[3 * p + a] = P[p].v[a] + acc;
                 wp[3 * p + a] = P[p].w[a] + alp;
             }
-            P[p].Fc[a] = 0.0;
-            P[p].Tc[a] = 0.0;
         }
-    }
-    // substrate contacts, delta = R_c - (z_p - 0.5); history record p
-    for (int p = 0; p < np; p++) {
-        double *xi = hist + 6 * p, *xir = xi + 3;
-        double delta = P[p].Rc - (xn[3 * p + 2] - 0.5);
-        if (I.wall_z0 && delta > 0.0) {
-            const double n[3] = {0.0, 0.0, 1.0};
-            dem_contact(I, P, p, -1, vp, wp, n, delta, xi, xir);
+    __syncthreads();
+    const int npair = np * (np - 1) / 2;
+    for (int c = tid; c < np + npair; c += blockDim.x) {
+        double *r = rec + 12 * c;
+        for (int a = 0; a < 12; a++) r[a] = 0.0;
+        if (c < np) {
+            // particle-substrate contact, delta = R_c - (z_p - 0.5); history record c
+            const int p = c;
+            double *xi = hist + 6 * p, *xir = xi + 3;
+            const double delta = P[p].Rc - (xn[3 * p + 2] - 0.5);
+            if (I.wall_z0 && delta > 0.0) {
+                const double n[3] = {0.0, 0.0, 1.0};
+                dem_contact(I, P, p, -1, vp, wp, n, delta, xi, xir, r);
+            } else {
+                for (int a = 0; a < 6; a++) xi[a] = 0.0;
+            }
         } else {
-            for (int a = 0; a < 6; a++) xi[a] = 0.0;
-        }
-    }
-    // pair contacts, delta_ij = R_c,i + R_c,j - |X_i - X_j|; history record
-    // np + i*np + j
-    for (int i = 0; i < np; i++)
-        for (int j = i + 1; j < np; j++) {
+            // particle pair, delta_ij = R_c,i + R_c,j - |X_i - X_j|; history record np + i*np + j
+            int i, j;
+            pair_of(c - np, np, &i, &j);
             double *xi = hist + 6 * (np + i * np + j), *xir = xi + 3;
-            double d[3] = {min_image(xn[3 * i] - xn[3 * j], I.nx), min_image(xn[3 * i + 1] - xn[3 * j + 1], I.ny),
-                           min_image(xn[3 * i + 2] - xn[3 * j + 2], I.nz)};
-            double dl = sqrt(dot3(d, d));
-            double delta = P[i].Rc + P[j].Rc - dl;
+            const double d[3] = {min_image(xn[3 * i] - xn[3 * j], I.nx), min_image(xn[3 * i + 1] - xn[3 * j + 1], I.ny),
+                                 min_image(xn[3 * i + 2] - xn[3 * j + 2], I.nz)};
+            const double dl = sqrt(dot3(d, d));
+            const double delta = P[i].Rc + P[j].Rc - dl;
             if (delta > 0.0 && dl > 0.0) {
                 const double n[3] = {d[0] / dl, d[1] / dl, d[2] / dl};
-                dem_contact(I, P, i, j, vp, wp, n, delta, xi, xir);
+                dem_contact(I, P, i, j, vp, wp, n, delta, xi, xir, r);
             } else {
                 for (int a = 0; a < 6; a++) xi[a] = 0.0;
             }
         }
-    // corrector
-    for (int p = 0; p < np; p++) {
+    }
+    __syncthreads();
+    for (int p = tid; p < np; p += blockDim.x) {
+        double Fc[3] = {0, 0, 0}, Tc[3] = {0, 0, 0};
+        const double *r = rec + 12 * p;
+        for (int a = 0; a < 3; a++) { Fc[a] += r[a]; Tc[a] += r[3 + a]; }
+        for (int q = 0; q < np; q++) {
+            if (q == p) continue;
+            const double *rp = rec + 12 * (np + (q < p ? pair_index(q, p, np) : pair_index(p, q, np)));
+            const int off = q < p ? 6 : 0;  // p is the second member of (q, p)
+            for (int a = 0; a < 3; a++) { Fc[a] += rp[off + a]; Tc[a] += rp[off + 3 + a]; }
+        }
+        PartDev &Q_ = P[p];
         double F[3], T[3], wold[3];
         for (int a = 0; a < 3; a++) {
-            F[a] = P[p].Fc[a] + I.g_part[a] + P[p].Feta[a] + P[p].Fsig[a];
-            T[a] = P[p].Tc[a] + P[p].Teta[a] + P[p].Tsig[a];
-            wold[a] = P[p].w[a];
+            Q_.Fc[a] = Fc[a];
+            Q_.Tc[a] = Tc[a];
+            F[a] = Fc[a] + I.g_part[a] + Q_.Feta[a] + Q_.Fsig[a];
+            T[a] = Tc[a] + Q_.Teta[a] + Q_.Tsig[a];
+            wold[a] = Q_.w[a];
+            Q_.x_old[a] = Q_.x[a];
+            Q_.xfo[a] = Q_.xf[a];
         }
-        if (!P[p].kin)
+        if (!Q_.kin)
             for (int a = 0; a < 3; a++) {
-                P[p].v[a] += 0.5 * (P[p].Fp[a] + F[a]) / P[p].m;
-                P[p].w[a] += 0.5 * (P[p].Tp[a] + T[a]) / P[p].I;
+                Q_.v[a] += 0.5 * (Q_.Fp[a] + F[a]) / Q_.m;
+                Q_.w[a] += 0.5 * (Q_.Tp[a] + T[a]) / Q_.I;
             }
-        double wm[3] = {0.5 * (wold[0] + P[p].w[0]), 0.5 * (wold[1] + P[p].w[1]), 0.5 * (wold[2] + P[p].w[2])};
-        quat_rotate(P[p].q, wm);
+        double wm[3] = {0.5 * (wold[0] + Q_.w[0]), 0.5 * (wold[1] + Q_.w[1]), 0.5 * (wold[2] + Q_.w[2])};
+        quat_rotate(Q_.q, wm);
         for (int a = 0; a < 3; a++) {
-            if (fabs(xn[3 * p + a] - P[p].x[a]) >= GEOM_MARGIN - 1) atomicOr(L.status, ST_DISPLACEMENT);
-            P[p].x[a] = xn[3 * p + a];
-            P[p].Fp[a] = F[a];
-            P[p].Tp[a] = T[a];
+            if (fabs(xn[3 * p + a] - Q_.x[a]) >= GEOM_MARGIN - 1) atomicOr(L.status, ST_DISPLACEMENT);
+            Q_.x[a] = xn[3 * p + a];
+            Q_.xf[a] = (float)Q_.x[a];
+            Q_.Fp[a] = F[a];
+            Q_.Tp[a] = T[a];
         }
     }
 }
@@ -379,14 +425,23 @@ __global__ void k_dem(Lattice L, int mem_blocks)
 // ---------------------------------------------------------------------------
 // Geometry update and refilling (Sec. V C)
 // ---------------------------------------------------------------------------
-// owner of node (x,y,z) for particle positions `which` (0: current, 1: previous)
+// owner of node (x,y,z) for the particle positions `which` (0: current, 1:
+// previous): |x - x_p|^2 < R_p^2, decided in single precision when clear of
+// the sphere surface by a margin and in double precision otherwise
 __device__ __forceinline__ int particle_owner(const InstDev &I, const PartDev *parts, int x, int y, int z, int which)
 {
     for (int p = 0; p < I.np; p++) {
         const PartDev &P = parts[I.part_off + p];
+        const float *cf = which ? P.xfo : P.xf;
+        const float e0 = min_image_r<float>((float)x - cf[0], I.nx);
+        const float e1 = min_image_r<float>((float)y - cf[1], I.ny);
+        const float e2 = min_image_r<float>((float)z - cf[2], I.nz);
+        const float d2 = e0 * e0 + e1 * e1 + e2 * e2;
+        if (d2 > P.R2hi) continue;
+        if (d2 < P.R2lo) return 2 + p;
         const double *c = which ? P.x_old : P.x;
-        double d0 = min_image(x - c[0], I.nx), d1 = min_image(y - c[1], I.ny), d2 = min_image(z - c[2], I.nz);
-        if (d0 * d0 + d1 * d1 + d2 * d2 < P.R * P.R) return 2 + p;
+        const double d0 = min_image(x - c[0], I.nx), d1 = min_image(y - c[1], I.ny), dd = min_image(z - c[2], I.nz);
+        if (d0 * d0 + d1 * d1 + dd * dd < P.R * P.R) return 2 + p;
     }
     return OWN_FLUID;
 }
@@ -418,7 +473,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_geom_owner(Lattice L, int side
 __device__ __forceinline__ void set_boundary(const Lattice &L, const InstDev &I, int x, int y, int z)
 {
     const uint8_t *fli = L.flags + I.node_off;
-    const long long n = ((long long)z * I.ny + y) * I.nx + x;
+    const int n = (z * I.ny + y) * I.nx + x;
     const uint8_t f = fli[n];
     const bool fluid = (f & OWNER_MASK) == OWN_FLUID;
     Nbr nb;
@@ -463,50 +518,55 @@ __global__ void k_boundary_full(Lattice L, int inst)
 template <class S>
 __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int side)
 {
+    using R = typename Store<S>::real;
     const PartDev &P0 = L.parts[blockIdx.y];
     const InstDev &I = L.inst[P0.inst];
     Region reg;
     reg.init(P0.x, side, I.nx, I.ny, I.nz);
-    const long long N = I.N;
+    const int N = (int)I.N;
     S *pop = (S *)L.pop[nxt] + NPOP * I.node_off;
     const uint8_t *fli = L.flags + I.node_off;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < reg.count();
          t += (long long)gridDim.x * blockDim.x) {
         int x, y, z;
         reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
-        const long long n = ((long long)z * I.ny + y) * I.nx + x;
+        const int n = (z * I.ny + y) * I.nx + x;
         if (!(fli[n] & FRESH_BIT)) continue;
-        double sF = 0.0, sG = 0.0;
+        R sF = 0, sG = 0;
         int nf = 0;
         for (int hop = 1; hop <= 2 && nf == 0; hop++)
             for (int i = 1; i < Q; i++) {
                 int X = ((x + hop * cx(i)) % I.nx + I.nx) % I.nx;
                 int Y = ((y + hop * cy(i)) % I.ny + I.ny) % I.ny;
                 int Z = ((z + hop * cz(i)) % I.nz + I.nz) % I.nz;
-                long long m = ((long long)Z * I.ny + Y) * I.nx + X;
+                const int m = (Z * I.ny + Y) * I.nx + X;
                 uint8_t fm = fli[m];
                 if ((fm & OWNER_MASK) != OWN_FLUID || (fm & FRESH_BIT)) continue;
                 for (int j = 0; j < Q; j++) {
-                    sF += wgt<double>(j) * (1.0 + (double)Store<S>::ld(pop + (long long)j * N + m));
-                    sG += wgt<double>(j) * (double)Store<S>::ld(pop + (long long)(Q + j) * N + m);
+                    sF += wgt<R>(j) * (R(1) + Store<S>::ld(pop + j * N + m));
+                    sG += wgt<R>(j) * Store<S>::ld(pop + (Q + j) * N + m);
                 }
                 nf++;
             }
         // mean rho/rho0 and (rho^a - rho^b)/rho0 of the neighbours
-        double rr, rd;
+        R rr, rd;
         if (nf > 0) { rr = sF / nf; rd = sG / nf; }
-        else { rr = 1.0; rd = -1.0; }
+        else { rr = R(1); rd = R(-1); }
         const int prev = particle_owner(I, L.parts, x, y, z, 1);
         const PartDev &P = L.parts[I.part_off + (prev >= 2 ? prev - 2 : 0)];
-        double d0 = min_image(x - P.x[0], I.nx), d1 = min_image(y - P.x[1], I.ny), d2 = min_image(z - P.x[2], I.nz);
-        double u[3] = {P.v[0] + P.w[1] * d2 - P.w[2] * d1, P.v[1] + P.w[2] * d0 - P.w[0] * d2,
-                       P.v[2] + P.w[0] * d1 - P.w[1] * d0};
-        double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        R c[3];
+        centre(P, c);
+        const R d0 = min_image_r<R>(x - c[0], I.nx), d1 = min_image_r<R>(y - c[1], I.ny),
+                d2 = min_image_r<R>(z - c[2], I.nz);
+        const R w[3] = {(R)P.w[0], (R)P.w[1], (R)P.w[2]};
+        const R u[3] = {(R)P.v[0] + w[1] * d2 - w[2] * d1, (R)P.v[1] + w[2] * d0 - w[0] * d2,
+                        (R)P.v[2] + w[0] * d1 - w[1] * d0};
+        const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         for (int i = 0; i < Q; i++) {
-            double cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-            double e = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu;
-            Store<S>::st(pop + (long long)i * N + n, (typename Store<S>::real)(rr * e - 1.0));
-            Store<S>::st(pop + (long long)(Q + i) * N + n, (typename Store<S>::real)(rd * e));
+            const R cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+            const R e = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+            Store<S>::st(pop + i * N + n, rr * e - R(1));
+            Store<S>::st(pop + (Q + i) * N + n, rd * e);
         }
     }
 }
@@ -548,9 +608,10 @@ void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Ma
 {
     if (L.n_parts == 0) return;
     mk(STAGE_DEM, 0);
-    k_dem<<<(L.n_inst + 31) / 32, 32, 0, st>>>(L, L.mem_blocks);
+    k_part_sums<<<L.n_parts, 32, 0, st>>>(L);
+    k_dem<<<L.n_inst, DEM_THREADS, 0, st>>>(L);
     mk(STAGE_DEM, 1);
-    *launches += 1;
+    *launches += 2;
 }
 
 template <class S>

@@ -68,9 +68,10 @@ _lib = None
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", "lbm_init_fields",
            "lbm_init_fields_device", "lbm_add_particles", "lbm_step", "lbm_particle_forces", "lbm_read_fields",
            "lbm_read_fields_device", "lbm_num_particles", "lbm_num_nodes", "lbm_diagnostics", "lbm_set_launch",
-           "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc"]
+           "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
+           "lbm_set_fluid_kernel"]
 STAGES = ["phi", "solid_phi", "grad_wetting", "collide", "momentum_exchange", "capillary", "dem", "geom_owner",
-          "geom_boundary", "refill"]
+          "geom_boundary", "refill", "fused", "particle_region"]
 
 
 def load(path: str = LIB_PATH):
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH):
     L.lbm_profile.argtypes = [vp, i]
     L.lbm_profile_read.argtypes = [vp, d, i]
     L.lbm_component_masses_noalloc.argtypes = [vp, ct.c_longlong, vp, vp]
+    L.lbm_set_fluid_kernel.argtypes = [vp, i, i, i]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
                         "lbm_last_launch_count"):
@@ -245,6 +247,9 @@ class Context:
 
     def lbm_set_launch(self, block_threads):
         self._check(self.L.lbm_set_launch(self.h, int(block_threads)))
+
+    def lbm_set_fluid_kernel(self, fused=1, tile=0, zchunk=0):
+        self._check(self.L.lbm_set_fluid_kernel(self.h, int(fused), int(tile), int(zchunk)))
 
     def lbm_last_launch_count(self):
         return int(self.L.lbm_last_launch_count(self.h))
