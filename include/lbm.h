@@ -205,11 +205,12 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
  * captured step graph. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads);
 
-/* Fluid-update launch form.  fused = 1 (default): one z-marching kernel per
- * step; tile selects its column tile (0: 32x8, 1: 64x4, 2: 16x16); zchunk is
- * the number of z-planes per work item (0: automatic, 32).  fused = 0: the
- * four-kernel form (order parameter, solid phi, gradient, collision), kept as
- * a reference.  Both give identical results.  Invalidates the step graph. */
+/* Fluid-update launch form.  fused = 0 (default): four kernels per step
+ * (order parameter, solid phi, gradient, collision).  fused = 1: one
+ * z-marching kernel per step; tile selects its column tile (0: 32x8, 1: 64x4,
+ * 2: 16x16); zchunk is the number of z-planes per work item (0: automatic,
+ * 32).  The two forms agree bit for bit in FP32 and to rounding (FMA
+ * contraction) in FP64.  Invalidates the step graph. */
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int fused, int tile, int zchunk);
 
 /* Count of kernel launches the last lbm_step call enqueued (graph nodes

@@ -52,8 +52,8 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
-    // fluid launch form: fused z-marching kernel (default) or four kernels
-    FluidLaunch fz = {1, 0, 0};
+    // fluid launch form: four kernels (default) or the fused z-marching kernel
+    FluidLaunch fz = {0, 0, 0};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
 };
 

@@ -283,4 +283,7 @@ def test_fused_kernel_equals_four_kernel_form(prec):
     for tile, zc in ((0, 0), (1, 5), (2, 7), (0, 27), (0, 1)):
         got = run(1, tile, zc)
         for a, b in zip(ref, got):
-            assert np.array_equal(a, b), (tile, zc)
+            if prec == "fp32":
+                assert np.array_equal(a, b), (tile, zc)
+            else:  # FMA contraction may differ between the two kernels
+                assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(a).max()), (tile, zc)
