@@ -58,7 +58,7 @@ typedef enum {
     LBM_ERR_CUDA = 3,        /* CUDA runtime error                              */
     LBM_ERR_STATE = 4,       /* call not valid in the current state             */
     LBM_ERR_UNSTABLE = 5,    /* non-finite/non-positive density seen on device  */
-    LBM_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                   */
+    LBM_ERR_TIMEOUT = 6,     /* a bounded device wait gave up (staged copies)   */
     LBM_ERR_UNSUPPORTED = 7  /* feature or precision not available              */
 } lbm_status;
 
@@ -205,13 +205,26 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
  * captured step graph. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads);
 
-/* Fluid-update launch form.  fused = 0 (default): four kernels per step
- * (order parameter, solid phi, gradient, collision).  fused = 1: one
- * z-marching kernel per step; tile selects its column tile (0: 32x8, 1: 64x4,
- * 2: 16x16); zchunk is the number of z-planes per work item (0: automatic,
- * 32).  The two forms agree bit for bit in FP32 and to rounding (FMA
- * contraction) in FP64.  Invalidates the step graph. */
-lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int fused, int tile, int zchunk);
+/* Fluid-update launch form (all forms compute the same update).
+ * form = 0 (default), staged: five kernels per step (order parameter, solid
+ *   phi, gradient, curvature, collision); the two kernels that stream the
+ *   populations are persistent and bring each strip of x-rows into shared
+ *   memory with bulk asynchronous copies.  Needs nx * (bytes per stored
+ *   population) to be a multiple of 16 in every instance; otherwise the plain
+ *   form runs.
+ * form = 1, fused: one z-marching kernel per step; tile selects its column
+ *   tile (0: 16x16, 1: 32x8); zchunk is the number of z-planes per work item
+ *   (0: automatic, 32).
+ * form = 2, plain: the five kernels with one thread per node and direct loads.
+ * Staged and plain agree bit for bit; fused agrees bit for bit in FP32 and to
+ * rounding (FMA contraction) in FP64.  Invalid form, tile or zchunk -> LBM_ERR_ARG.
+ * Invalidates the step graph. */
+lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk);
+
+/* The fluid-update form the next step runs: 0 staged, 1 fused, 2 plain (the
+ * staged form falls back to plain when an instance's rows are not whole
+ * 16-byte units); -1 for a null context. */
+int lbm_fluid_form_in_use(const lbm_ctx *ctx);
 
 /* Count of kernel launches the last lbm_step call enqueued (graph nodes
  * included); for accounting in benchmarks. */

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lbm.h"
@@ -24,7 +25,7 @@ struct lbm_ctx {
     size_t elem = 8, real_sz = 8;
     uint8_t *flags = nullptr;
     void *pop[2] = {nullptr, nullptr};
-    void *phi = nullptr, *grad = nullptr, *gmag = nullptr, *u = nullptr;
+    void *phi = nullptr, *grad = nullptr, *gmag = nullptr, *kap = nullptr, *u = nullptr;
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
     double *mem_part = nullptr, *cap_part = nullptr, *hist = nullptr;
@@ -52,10 +53,12 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
-    // fluid launch form: four kernels (default) or the fused z-marching kernel
-    FluidLaunch fz = {0, 0, 0};
+    // fluid launch form: staged (default), fused z-marching or plain
+    FluidLaunch fz = {FORM_STAGED, 0, 0, 0, {0, 0}, {0, 0}};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
 };
+
+static void dispatch_grids(lbm_ctx *c);
 
 // work items of the fused kernel: column tiles x z-chunks, per instance
 static void plan_fused(lbm_ctx *c)
@@ -75,7 +78,17 @@ static void plan_fused(lbm_ctx *c)
     c->fz.items = items;
 }
 
+// work items and persistent grids of the staged kernels
+static void plan_launch(lbm_ctx *c)
+{
+    plan_fused(c);
+    plan_staged(c->inst_h, c->elem, &c->fz.st_items);
+    dispatch_grids(c);
+}
+
 static const int DIAG_BLOCKS = 512;
+// bytes after the last flag: the staged kernels copy flags in whole 16-byte units
+static const size_t FLAG_PAD = 64;
 
 static lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m)
 {
@@ -104,6 +117,7 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.phi = c->phi;
     L.grad = c->grad;
     L.gmag = c->gmag;
+    L.kap = c->kap;
     L.u = c->u;
     L.Ntot = c->Ntot;
     L.parts = c->parts_d;
@@ -308,6 +322,14 @@ static void dispatch(lbm_precision p, F &&f)
     }
 }
 
+static void dispatch_grids(lbm_ctx *c)
+{
+    dispatch(c->prec, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        staged_grids<S>(c->fz.st_grid_phi, c->fz.st_grid_collide);
+    });
+}
+
 static cudaEvent_t next_event(lbm_ctx *c)
 {
     if (c->ev_used == c->ev_pool.size()) {
@@ -393,6 +415,7 @@ static const char *status_text(unsigned s)
 {
     if (s & ST_UNSTABLE) return "device: non-finite or non-positive density (unstable run)";
     if (s & ST_DISPLACEMENT) return "device: a particle moved more than 2 lattice units in one step";
+    if (s & ST_TIMEOUT) return "device: a bounded wait for an asynchronous copy gave up";
     return "device status";
 }
 
@@ -401,7 +424,8 @@ static lbm_status check_status(lbm_ctx *ctx)
     unsigned s = 0;
     CU(cudaMemcpyAsync(&s, ctx->status, sizeof s, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    if (s) return fail(ctx, LBM_ERR_UNSTABLE, status_text(s));
+    if (s) return fail(ctx, (s & ST_TIMEOUT) && !(s & ST_UNSTABLE) ? LBM_ERR_TIMEOUT : LBM_ERR_UNSTABLE,
+                       status_text(s));
     return LBM_OK;
 }
 
@@ -431,6 +455,7 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->phi);
     cudaFree(ctx->grad);
     cudaFree(ctx->gmag);
+    cudaFree(ctx->kap);
     cudaFree(ctx->u);
     cudaFree(ctx->parts_d);
     cudaFree(ctx->mem_part);
@@ -512,7 +537,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     }
     ctx->Ntot = node_off;
     ctx->n_blocks = blk;
-    plan_fused(ctx);
+    plan_launch(ctx);
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
     } else {
@@ -533,9 +558,9 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     };
     const size_t Nt = (size_t)ctx->Ntot;
     if ((st = alloc((void **)&ctx->inst_d, sizeof(InstDev) * n_instances)) ||
-        (st = alloc((void **)&ctx->flags, Nt)) || (st = alloc(&ctx->pop[0], NPOP * Nt * ctx->elem)) ||
+        (st = alloc((void **)&ctx->flags, Nt + FLAG_PAD)) || (st = alloc(&ctx->pop[0], NPOP * Nt * ctx->elem)) ||
         (st = alloc(&ctx->pop[1], NPOP * Nt * ctx->elem)) || (st = alloc(&ctx->phi, Nt * ctx->real_sz)) ||
-        (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc(&ctx->gmag, Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
+        (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc(&ctx->gmag, Nt * ctx->real_sz)) || (st = alloc(&ctx->kap, Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
         (st = alloc((void **)&ctx->diag_d, sizeof(double) * 2 * n_instances)) ||
         (st = alloc((void **)&ctx->diag_part, sizeof(double) * 2 * DIAG_BLOCKS)) ||
         (any_u && (st = alloc(&ctx->u, 3 * Nt * ctx->real_sz)))) {
@@ -568,6 +593,8 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     cudaMemsetAsync(ctx->phi, 0, Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->grad, 0, 3 * Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->gmag, 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->kap, 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->flags + Nt, 0, FLAG_PAD, ctx->stream);
     cudaMemsetAsync(ctx->diag_d, 0, sizeof(double) * 2 * n_instances, ctx->stream);
     if (ctx->u) cudaMemsetAsync(ctx->u, 0, 3 * Nt * ctx->real_sz, ctx->stream);
     // flags: substrate plane, then boundary bits
@@ -988,21 +1015,28 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads)
 
 long long lbm_last_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->last_launches : -1; }
 
-lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int fused, int tile, int zchunk)
+lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
 {
     if (!ctx) return LBM_ERR_ARG;
-    if ((fused != 0 && fused != 1) || tile < 0 || tile > 2 || zchunk < 0)
-        return fail(ctx, LBM_ERR_ARG, "fused must be 0/1, tile 0..2, zchunk >= 0");
+    if (form < FORM_STAGED || form > FORM_PLAIN || tile < 0 || tile > 1 || zchunk < 0)
+        return fail(ctx, LBM_ERR_ARG, "form must be 0 (staged), 1 (fused) or 2 (plain), tile 0..1, zchunk >= 0");
     CU(cudaStreamSynchronize(ctx->stream));
-    ctx->fz.fused = fused;
+    ctx->fz.form = form;
     ctx->fz.tile = tile;
     ctx->zc_request = zchunk;
-    plan_fused(ctx);
+    plan_launch(ctx);
     CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,
                        ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     drop_graph(ctx);
     return LBM_OK;
+}
+
+int lbm_fluid_form_in_use(const lbm_ctx *ctx)
+{
+    if (!ctx) return -1;
+    if (ctx->fz.form == FORM_STAGED && ctx->fz.st_items == 0) return FORM_PLAIN;
+    return ctx->fz.form;
 }
 
 lbm_status lbm_profile(lbm_ctx *ctx, int enable)

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace lbmg {
 
 constexpr int Q = 19;
@@ -46,6 +48,7 @@ constexpr uint8_t OWN_WALL = 1;
 // sticky status bits
 constexpr unsigned ST_UNSTABLE = 1u;
 constexpr unsigned ST_DISPLACEMENT = 2u;
+constexpr unsigned ST_TIMEOUT = 4u;  // a bounded wait for an asynchronous copy gave up
 
 constexpr int CAP_POINTS = 90 * 180;  // Sec. V E: 2 deg x 2 deg Lagrangian points
 constexpr int CAP_THREADS = 256;
@@ -76,6 +79,11 @@ struct InstDev {
     // fused-kernel work items: tiles_x * tiles_y column tiles x nchunks z-chunks
     long long item_start;
     int tiles_x, tiles_y, nchunks, zc;
+    // staged-kernel work items: st_rows whole x-rows of one z-plane per item
+    // (st_nseg = 1, st_seg = nx), or one row cut into st_nseg segments of at
+    // most st_seg nodes; st_ygroups items cover the y rows of a plane
+    long long st_item_start;
+    int st_rows, st_seg, st_nseg, st_ygroups;
 };
 
 // fluid parameters in the arithmetic precision R
@@ -120,6 +128,7 @@ struct Lattice {
     void *phi;           // [Ntot] real
     void *grad;          // [3][Ntot] real: regularised interface normal n
     void *gmag;          // [Ntot] real: sqrt(|grad phi|^2 + eps^2), so grad phi = n gmag
+    void *kap;           // [Ntot] real: curvature div(n) of fluid nodes
     void *u;             // [3][Ntot] real (store_velocity)
     long long Ntot;
     PartDev *parts;
@@ -143,24 +152,28 @@ template <>
 struct Store<double> {
     using real = double;
     static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ double lds(const double *p) { return *p; }  // shared memory
     static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 };
 template <>
 struct Store<float> {
     using real = float;
     static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float lds(const float *p) { return *p; }  // shared memory
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <>
 struct Store<__half> {
     using real = float;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }  // shared memory
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <>
 struct Store<__nv_bfloat16> {
     using real = float;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }  // shared memory
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
@@ -370,7 +383,7 @@ __device__ __forceinline__ void wetting_rotate(R *g, const R *ns, R cth, R sth)
 // kernel stages, in launch order within a step (for per-kernel timing)
 enum Stage {
     STAGE_PHI = 0, STAGE_SOLIDPHI, STAGE_GRAD, STAGE_COLLIDE, STAGE_MEM, STAGE_CAPILLARY, STAGE_DEM,
-    STAGE_GEOM_OWNER, STAGE_GEOM_BOUND, STAGE_REFILL, STAGE_FUSED, STAGE_REGION, N_STAGES
+    STAGE_GEOM_OWNER, STAGE_GEOM_BOUND, STAGE_REFILL, STAGE_FUSED, STAGE_REGION, STAGE_CURV, N_STAGES
 };
 
 // optional per-kernel marker: called right before and right after each launch
@@ -384,11 +397,34 @@ struct Marker {
 };
 
 // host-side kernel launchers (defined in the .cu files)
+enum { FORM_STAGED = 0, FORM_FUSED = 1, FORM_PLAIN = 2 };
 struct FluidLaunch {
-    int fused;       // 1: one fused kernel per step, 0: the four-kernel form
-    int tile;        // fused tile shape index (see lbm_fluid.cu)
-    long long items; // fused work items (all instances)
+    int form;           // FORM_STAGED, FORM_FUSED or FORM_PLAIN
+    int tile;           // fused tile shape index (see lbm_fluid.cu)
+    long long items;    // fused work items (all instances)
+    long long st_items; // staged work items (all instances); 0: staged form unavailable
+    // persistent grids of the staged kernels, per variant (0: two CTAs per SM,
+    // 1: one CTA per SM with a deeper copy ring)
+    int st_grid_phi[2], st_grid_collide[2];
 };
+// staged kernels: threads per CTA and nodes per work item at most
+constexpr int ST_THREADS = 256;
+constexpr int ST_SEGMAX = 256;
+template <class S>
+struct StagedCfg {
+    static constexpr int A = 16 / (int)sizeof(S);  // elements per 16 bytes
+};
+// plan the staged work items of every instance (false if an instance's nx is
+// not a multiple of 16 bytes of storage, which the bulk copies need)
+bool plan_staged(std::vector<InstDev> &inst, size_t elem, long long *items);
+template <class S>
+void staged_grids(int *grid_phi, int *grid_collide);  // arrays of 2 (variants)
+template <class S>
+void launch_staged_phi(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
+template <class S>
+void launch_staged_collide(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
+template <class S>
+void launch_fused_form(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
 template <class S>
 void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
                        const FluidLaunch &fz);

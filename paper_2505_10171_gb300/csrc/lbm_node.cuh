@@ -1,0 +1,226 @@
+// Per-node device functions of the fluid update (Sec. IV, V D of arXiv
+// 2505.10171), shared by every launch form so that all forms run the same
+// arithmetic: solid-node phi, wetting normal, grad(phi), collision + recolouring
+// + write, curvature and the regularised normal.
+#pragma once
+#include "lbm_internal.cuh"
+
+namespace lbmg {
+
+// ---------------------------------------------------------------------------
+// per-node device functions
+// ---------------------------------------------------------------------------
+
+// phi of a solid node: w-weighted mean over its fluid neighbours; phi_of(dx,
+// dy, dz) returns the order parameter of the neighbour
+template <class R, class A, class PhiF>
+__device__ __forceinline__ R solid_fill(const A &nbr, const PhiF &phi_of)
+{
+    R sw = 0, sp = 0;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        if (nbr.own(cx(i), cy(i), cz(i)) != OWN_FLUID) continue;
+        sw += wgt<R>(i);
+        sp += wgt<R>(i) * phi_of(cx(i), cy(i), cz(i));
+    }
+    return sw > R(0) ? sp / sw : R(0);
+}
+
+// outward solid normal and contact angle at a fluid node next to solid: the
+// nearest particle surface if a neighbour belongs to a particle, otherwise the
+// normalised -sum w_i c_i over substrate neighbours.
+template <class R, class A>
+__device__ __forceinline__ bool solid_normal(const InstDev &I, const PartDev *parts, const A &nbr, int x, int y,
+                                             int z, R *ns, R *cth, R *sth)
+{
+    int best = -1;
+    double bestd = 0.0;
+    double ws[3] = {0.0, 0.0, 0.0};
+    bool any = false;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        int own = nbr.own(cx(i), cy(i), cz(i));
+        if (own == OWN_FLUID) continue;
+        any = true;
+        if (own == OWN_WALL) {
+            ws[0] -= wgt<double>(i) * cx(i);
+            ws[1] -= wgt<double>(i) * cy(i);
+            ws[2] -= wgt<double>(i) * cz(i);
+        } else {
+            const PartDev &P = parts[I.part_off + own - 2];
+            double d0 = min_image(x - P.x[0], I.nx), d1 = min_image(y - P.x[1], I.ny),
+                   d2 = min_image(z - P.x[2], I.nz);
+            double dist = sqrt(d0 * d0 + d1 * d1 + d2 * d2) - P.R;
+            int p = own - 2;
+            if (best < 0 || dist < bestd || (dist == bestd && p < best)) {
+                best = p;
+                bestd = dist;
+            }
+        }
+    }
+    if (!any) return false;
+    if (best >= 0) {
+        const PartDev &P = parts[I.part_off + best];
+        double d0 = min_image(x - P.x[0], I.nx), d1 = min_image(y - P.x[1], I.ny), d2 = min_image(z - P.x[2], I.nz);
+        double dl = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        ns[0] = (R)(d0 / dl); ns[1] = (R)(d1 / dl); ns[2] = (R)(d2 / dl);
+        *cth = (R)P.cos_t;
+        *sth = (R)P.sin_t;
+        return true;
+    }
+    double wl = sqrt(ws[0] * ws[0] + ws[1] * ws[1] + ws[2] * ws[2]);
+    if (wl == 0.0) return false;
+    ns[0] = (R)(ws[0] / wl); ns[1] = (R)(ws[1] / wl); ns[2] = (R)(ws[2] / wl);
+    *cth = (R)I.cos_tw;
+    *sth = (R)I.sin_tw;
+    return true;
+}
+
+// grad(phi) = 3 sum_i w_i c_i phi(x + c_i) with the wetting rotation at
+// boundary nodes inside the interface
+template <class R, class A, class PhiF>
+__device__ __forceinline__ void grad_node(const InstDev &I, const PartDev *parts, const A &nbr, const PhiF &phi_of,
+                                          R phi_here, uint8_t fl, R wet_max, int x, int y, int z, R *gr)
+{
+    gr[0] = gr[1] = gr[2] = 0;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        R p = phi_of(cx(i), cy(i), cz(i));
+        R wc = R(3) * wgt<R>(i);
+        gr[0] += wc * cx(i) * p;
+        gr[1] += wc * cy(i) * p;
+        gr[2] += wc * cz(i) * p;
+    }
+    if ((fl & BOUND_BIT) && fabs(phi_here) < wet_max) {
+        R ns[3], cth, sth;
+        if (solid_normal<R>(I, parts, nbr, x, y, z, ns, &cth, &sth)) wetting_rotate<R>(gr, ns, cth, sth);
+    }
+}
+
+// force, velocity, MRT (two-relaxation-time form) with Guo forcing,
+// recolouring and the write of node n.  F, G: streamed offsets; g: corrected
+// grad(phi) of the node; nn: its regularised normal; kap: curvature.
+template <class S>
+__device__ __forceinline__ void collide_store_sg(const FluidPar<typename Store<S>::real> &P,
+                                                 const typename Store<S>::real *F, typename Store<S>::real sG,
+                                                 const typename Store<S>::real *g, const typename Store<S>::real *nn,
+                                                 typename Store<S>::real kap, S *__restrict__ out, int N, int n,
+                                                 typename Store<S>::real *U, long long Ustride, unsigned *status)
+{
+    using R = typename Store<S>::real;
+    R sF = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const R w = wgt<R>(i);
+        sF += w * F[i];
+        if (cx(i)) jx += w * cx(i) * F[i];
+        if (cy(i)) jy += w * cy(i) * F[i];
+        if (cz(i)) jz += w * cz(i) * F[i];
+    }
+    const R rr = R(1) + sF;  // rho / rho0
+    const R phi = sG * frcp(rr);
+    if (!(rr > R(0)) || !(phi == phi)) atomicOr(status, ST_UNSTABLE);
+    // force density: CSF -1/2 sigma kappa grad(phi) plus phase-weighted body forces
+    const R hs = R(-0.5) * P.sigma * kap;
+    const R pa = R(0.5) * (R(1) + phi), pb = R(0.5) * (R(1) - phi);
+    const R Fx = hs * g[0] + pa * P.ba[0] + pb * P.bb[0];
+    const R Fy = hs * g[1] + pa * P.ba[1] + pb * P.bb[1];
+    const R Fz = hs * g[2] + pa * P.ba[2] + pb * P.bb[2];
+    // velocity: rho u = sum c f + F/2
+    const R rho = P.rho0 * rr;
+    const R irho = frcp(rho);
+    const R ux = (P.rho0 * jx + R(0.5) * Fx) * irho;
+    const R uy = (P.rho0 * jy + R(0.5) * Fy) * irho;
+    const R uz = (P.rho0 * jz + R(0.5) * Fz) * irho;
+    if (U) { U[n] = ux; U[Ustride + n] = uy; U[2 * Ustride + n] = uz; }
+    // relaxation rates: harmonic-mean viscosity, tau = eta/(rho cs2) + 1/2
+    const R inv_eta = (R(1) + phi) * P.h_ia + (R(1) - phi) * P.h_ib;
+    const R tau = R(3) * frcp(inv_eta * rho) + R(0.5);
+    const R om = frcp(tau);
+    const R omp = R(8) * (R(2) - om) * frcp(R(8) - om);
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R uF = ux * Fx + uy * Fy + uz * Fz;
+    const R cpe = R(1) - R(0.5) * om, cpo = R(1) - R(0.5) * omp;
+    const R bq = R(0.5) * P.beta * rr * (R(1) - phi * phi);
+    {
+        const R feq0 = sF + rr * (R(-1.5) * uu);
+        const R fb0 = R(-3) * uF * P.ir0;
+        const R Fs = F[0] - om * (F[0] - feq0) + cpe * fb0;
+        Store<S>::st(out + n, Fs);
+        Store<S>::st(out + Q * N + n, phi * (R(1) + Fs));
+    }
+    // opposite pairs (i, i+9): the paper's S relaxes every even non-conserved
+    // moment with omega and every odd one with omega', i.e. the MRT operator is
+    // exactly the two-relaxation-time operator on the pair's even/odd parts
+#pragma unroll
+    for (int i = 1; i <= 9; i++) {
+        const int ib = i + 9;
+        const R cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+        const R cF = cx(i) * Fx + cy(i) * Fy + cz(i) * Fz;
+        const R eqp = sF + rr * (R(4.5) * cu * cu - R(1.5) * uu);
+        const R eqm = rr * R(3) * cu;
+        const R fbp = (R(9) * cu * cF - R(3) * uF) * P.ir0;
+        const R fbm = R(3) * cF * P.ir0;
+        const R fp = R(0.5) * (F[i] + F[ib]);
+        const R fm = R(0.5) * (F[i] - F[ib]);
+        const R dp = -om * (fp - eqp) + cpe * fbp;
+        const R dm = -omp * (fm - eqm) + cpo * fbm;
+        const R Fi = F[i] + dp + dm;
+        const R Fib = F[ib] + dp - dm;
+        // recolouring: G* = phi (1 + F*) + beta/2 (rho/rho0)(1 - phi^2) c.n/|c|
+        const R inv_len = csq(i) == 1 ? R(1) : R(0.70710678118654752440);
+        const R cn = (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]) * inv_len;
+        const R rec = bq * cn;
+        Store<S>::st(out + i * N + n, Fi);
+        Store<S>::st(out + ib * N + n, Fib);
+        Store<S>::st(out + (Q + i) * N + n, phi * (R(1) + Fi) + rec);
+        Store<S>::st(out + (Q + ib) * N + n, phi * (R(1) + Fib) - rec);
+    }
+}
+
+// the same with the streamed colour offsets G; only their weighted sum
+// sG = sum_i w_i G_i (summed in i order) enters the update
+template <class S>
+__device__ __forceinline__ void collide_store(const FluidPar<typename Store<S>::real> &P, const typename Store<S>::real *F,
+                                              const typename Store<S>::real *G, const typename Store<S>::real *g,
+                                              const typename Store<S>::real *nn, typename Store<S>::real kap,
+                                              S *__restrict__ out, int N, int n, typename Store<S>::real *U,
+                                              long long Ustride, unsigned *status)
+{
+    using R = typename Store<S>::real;
+    R sG = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) sG += wgt<R>(i) * G[i];
+    collide_store_sg<S>(P, F, sG, g, nn, kap, out, N, n, U, Ustride, status);
+}
+
+// curvature kappa = 3 sum_i w_i c_i . n(x + c_i), taken over opposite pairs as
+// w_i c_i . (n(x + c_i) - n(x - c_i)) so that only the components along c_i
+// are read; nf(dx, dy, dz, a) is component a of the neighbour's normal (the
+// node's own normal for a solid neighbour)
+template <class R, class NF>
+__device__ __forceinline__ R curvature(const NF &nf)
+{
+    R k = 0;
+#pragma unroll
+    for (int i = 1; i <= 9; i++) {
+        R t = 0;
+        if (cx(i)) t += cx(i) * (nf(cx(i), cy(i), cz(i), 0) - nf(-cx(i), -cy(i), -cz(i), 0));
+        if (cy(i)) t += cy(i) * (nf(cx(i), cy(i), cz(i), 1) - nf(-cx(i), -cy(i), -cz(i), 1));
+        if (cz(i)) t += cz(i) * (nf(cx(i), cy(i), cz(i), 2) - nf(-cx(i), -cy(i), -cz(i), 2));
+        k += wgt<R>(i) * t;
+    }
+    return R(3) * k;
+}
+
+// regularised interface normal n = g / sqrt(|g|^2 + eps^2); returns the norm
+template <class R>
+__device__ __forceinline__ R reg_normal(const R *g, R eps2, R *nn)
+{
+    const R m2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + eps2;
+    const R im = frsqrt(m2);
+    nn[0] = g[0] * im; nn[1] = g[1] * im; nn[2] = g[2] * im;
+    return m2 * im;
+}
+
+}  // namespace lbmg

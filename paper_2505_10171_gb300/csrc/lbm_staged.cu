@@ -1,0 +1,497 @@
+// Row-staged order-parameter and collision kernels (Sec. IV of arXiv
+// 2505.10171): the same per-node arithmetic as the plain kernels, with the
+// populations brought into shared memory by bulk asynchronous copies.
+//
+// A work item is a strip of one z-plane: st_rows whole x-rows (packed up to
+// ST_SEGMAX nodes), or one segment of a longer row.  Pull streaming reads, for
+// population q with velocity c, the strip shifted by -c; for a strip that is a
+// run of whole rows that source is again a run of whole rows of plane z - c_z
+// (two runs where it wraps in y), so each population of an item arrives with
+// one or two cp.async.bulk copies and the x-shift (with its periodic wrap) is
+// applied when reading shared memory.  A segment of a long row is copied with
+// 16 bytes of halo on both sides; its two end nodes of the row, and every
+// node next to a solid (bounce-back), take the plain global-memory gather.
+//
+// Each CTA is persistent: it walks items blockIdx.x, blockIdx.x + gridDim.x,
+// ... through an NST-deep ring of shared-memory stages.  Warp 0 issues the
+// copies of item k + NST while the CTA computes item k; each stage completes on
+// an mbarrier that counts the bytes.  The HBM stream therefore stays busy
+// independently of how many registers the collision needs.  Every wait is
+// bounded: after about a second the kernel sets ST_TIMEOUT, waits (bounded)
+// for its own copies in flight and returns.
+#include "lbm_node.cuh"
+
+namespace lbmg {
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second at 2 GHz
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+
+// global -> shared bulk copy completing on mbarrier `bar` (addresses and size
+// multiples of 16 bytes)
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// shared-memory stage: NPOP population strips of BUFW elements, then (EXT) the
+// normal n (3), |grad phi|_eps and curvature of the strip's nodes, then its
+// flags (from the 16-byte boundary below the first node)
+// MINB CTAs share an SM; the ring is as deep as their share of the 228 KB of
+// shared memory allows (2..8 stages)
+template <class S, bool EXT, int MINB>
+struct StLayout {
+    using R = typename Store<S>::real;
+    static constexpr int A = StagedCfg<S>::A;
+    static constexpr int BUFW = ST_SEGMAX + 2 * A;
+    static constexpr size_t POP = (size_t)NPOP * BUFW * sizeof(S);
+    static constexpr size_t EXTB = EXT ? (size_t)5 * ST_SEGMAX * sizeof(R) : 0;
+    static constexpr size_t FLB = ST_SEGMAX + 32;
+    static constexpr size_t STAGE = (POP + EXTB + FLB + 127) / 128 * 128;
+    static constexpr size_t HEAD = 128;  // the NST mbarriers
+    static constexpr size_t BUDGET = (size_t)228 * 1024 / MINB - 1024 - HEAD;
+    static constexpr int NST_FIT = (int)(BUDGET / STAGE);
+    static constexpr int NST = NST_FIT > 8 ? 8 : NST_FIT;
+    static_assert(NST >= 2, "two stages must fit");
+    static constexpr size_t bytes() { return HEAD + NST * STAGE; }
+};
+
+struct StItem {
+    int k;       // instance
+    int z, y0;   // plane and first row
+    int nrows;   // rows (whole-row items)
+    int x0, cnt; // first x and number of nodes
+    bool whole;
+};
+
+__device__ __forceinline__ void st_item(const Lattice &L, long long item, StItem &it)
+{
+    int lo = 0, hi = L.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.inst[mid].st_item_start <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const InstDev &I = L.inst[lo];
+    const long long loc = item - I.st_item_start;
+    const int per_plane = I.st_ygroups * I.st_nseg;
+    it.k = lo;
+    it.z = (int)(loc / per_plane);
+    const int r = (int)(loc - (long long)it.z * per_plane);
+    const int yg = r / I.st_nseg, sg = r - yg * I.st_nseg;
+    it.y0 = yg * I.st_rows;
+    it.whole = I.st_nseg == 1;
+    it.nrows = min(I.st_rows, I.ny - it.y0);
+    it.x0 = sg * I.st_seg;
+    it.cnt = it.whole ? it.nrows * I.nx : min(I.st_seg, I.nx - it.x0);
+}
+
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// first node of the item in the per-node arrays and the 16-byte-aligned start
+// of its flag copy
+__device__ __forceinline__ long long item_node0(const InstDev &I, const StItem &it)
+{
+    return I.node_off + ((long long)it.z * I.ny + it.y0) * I.nx + it.x0;
+}
+
+// issue the copies of one item into a stage (all 32 lanes of warp 0)
+template <class S, bool EXT, int MINB>
+__device__ void st_issue(const Lattice &L, const void *pop_in, const StItem &it, unsigned char *stage, uint32_t bar,
+                         int lane)
+{
+    using Ly = StLayout<S, EXT, MINB>;
+    using R = typename Store<S>::real;
+    constexpr int A = Ly::A;
+    const InstDev &I = L.inst[it.k];
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N;
+    const S *in = (const S *)pop_in + NPOP * I.node_off;
+    const int lo = it.whole ? 0 : max(it.x0 - A, 0);
+    const int hi = it.whole ? nx : min(it.x0 + it.cnt + A, nx);
+    const unsigned popb = (unsigned)(it.whole ? it.nrows * nx : hi - lo) * (unsigned)sizeof(S);
+    const long long g0 = item_node0(I, it);
+    const long long fst = g0 & ~15ll, fen = (g0 + it.cnt + 15) & ~15ll;
+    const unsigned flb = (unsigned)(fen - fst);
+    const unsigned extb = EXT ? (unsigned)it.cnt * (unsigned)sizeof(R) : 0u;
+    if (lane == 0) mbar_arrive_expect_tx(bar, NPOP * popb + 5 * extb + flb);
+    __syncwarp();
+    constexpr int NC = NPOP + (EXT ? 5 : 0) + 1;
+    for (int c = lane; c < NC; c += 32) {
+        if (c < NPOP) {
+            const int d = c < Q ? c : c - Q;
+            const int zs = wrap1(it.z - cz(d), nz);
+            const S *src = in + (long long)c * N + (long long)zs * ny * nx;
+            unsigned char *dst = stage + (size_t)c * Ly::BUFW * sizeof(S);
+            if (it.whole) {
+                const int ys = wrap1(it.y0 - cy(d), ny);
+                const int len1 = min(it.nrows, ny - ys);
+                bulk_g2s(smem_addr(dst), src + (long long)ys * nx, (unsigned)(len1 * nx * sizeof(S)), bar);
+                if (it.nrows > len1)
+                    bulk_g2s(smem_addr(dst + (size_t)len1 * nx * sizeof(S)), src,
+                             (unsigned)((it.nrows - len1) * nx * sizeof(S)), bar);
+            } else {
+                const int ys = wrap1(it.y0 - cy(d), ny);
+                bulk_g2s(smem_addr(dst + (size_t)(lo - (it.x0 - A)) * sizeof(S)), src + (long long)ys * nx + lo,
+                         popb, bar);
+            }
+        } else if (EXT && c < NPOP + 5) {
+            const int e = c - NPOP;
+            const R *base = e < 3 ? (const R *)L.grad + (long long)e * L.Ntot
+                                  : (e == 3 ? (const R *)L.gmag : (const R *)L.kap);
+            bulk_g2s(smem_addr(stage + Ly::POP + (size_t)e * ST_SEGMAX * sizeof(R)), base + g0, extb, bar);
+        } else {
+            bulk_g2s(smem_addr(stage + Ly::POP + Ly::EXTB), L.flags + fst, flb, bar);
+        }
+    }
+}
+
+// shared-memory indices of the sources x-1, x, x+1 of node (x, row r) in a
+// stage strip; `edge` marks the end nodes of a cut row, whose wrapped source
+// is not in the strip
+struct StSrc {
+    int bm, b0, bp;
+    bool edge;
+};
+template <int A>
+__device__ __forceinline__ StSrc st_src(const StItem &it, int nx, int r, int x)
+{
+    StSrc s;
+    if (it.whole) {
+        const int rb = r * nx;
+        s.bm = rb + (x == 0 ? nx - 1 : x - 1);
+        s.b0 = rb + x;
+        s.bp = rb + (x == nx - 1 ? 0 : x + 1);
+        s.edge = false;
+    } else {
+        const int o = it.x0 - A;
+        s.bm = x - 1 - o;
+        s.b0 = x - o;
+        s.bp = x + 1 - o;
+        s.edge = x == 0 || x == nx - 1;
+    }
+    return s;
+}
+
+// the persistent pipeline shared by both kernels; body(it, stage) computes one
+// item from a landed stage
+template <class S, bool EXT, int MINB, class Body>
+__device__ __forceinline__ void st_pipeline(const Lattice &L, const void *pop_in, long long n_items, Body &&body)
+{
+    using Ly = StLayout<S, EXT, MINB>;
+    constexpr int NST = Ly::NST;
+    extern __shared__ __align__(128) unsigned char st_smem[];
+    const uint32_t bar0 = smem_addr(st_smem);
+    auto bar = [&](int s) { return bar0 + 8u * (unsigned)s; };
+    auto stage = [&](int s) { return st_smem + Ly::HEAD + (size_t)s * Ly::STAGE; };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; s++) mbar_init(bar(s), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const bool producer = threadIdx.x < 32;
+    if (producer)
+        for (int s = 0; s < NST; s++) {
+            const long long item = blockIdx.x + (long long)s * gridDim.x;
+            if (item >= n_items) break;
+            StItem it;
+            st_item(L, item, it);
+            st_issue<S, EXT, MINB>(L, pop_in, it, stage(s), bar(s), lane);
+        }
+    for (long long k = 0;; k++) {
+        const long long item = blockIdx.x + k * gridDim.x;
+        if (item >= n_items) break;
+        const int s = (int)(k % NST);
+        const bool ok = mbar_wait_bounded(bar(s), (unsigned)((k / NST) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(L.status, ST_TIMEOUT);
+                // let this CTA's copies in flight land before it exits
+                for (long long j = k; j < k + NST; j++) {
+                    if (blockIdx.x + j * gridDim.x >= n_items) break;
+                    mbar_wait_bounded(bar((int)(j % NST)), (unsigned)((j / NST) & 1));
+                }
+            }
+            return;
+        }
+        StItem it;
+        st_item(L, item, it);
+        body(it, (const unsigned char *)stage(s));
+        __syncthreads();  // every thread is done with stage s
+        const long long nxt = item + (long long)NST * gridDim.x;
+        if (producer && nxt < n_items) {
+            StItem it2;
+            st_item(L, nxt, it2);
+            st_issue<S, EXT, MINB>(L, pop_in, it2, stage(s), bar(s), lane);
+        }
+    }
+}
+
+// nodes next to a solid and the end nodes of a cut row take the global-memory
+// path; kept out of line so that their registers do not weigh on the hot loop
+template <class S>
+__device__ __noinline__ typename Store<S>::real phi_node_cold(const InstDev *Ip, const PartDev *parts,
+                                                              const uint8_t *fli, const S *in, int n, uint8_t fl,
+                                                              int x, int y, int z)
+{
+    const InstDev &I = *Ip;
+    GlobalNbr nb;
+    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
+    nb.fli = fli;
+    return node_phi<S>(I, parts, nb, in, (int)I.N, n, fl, x, y, z);
+}
+
+template <class S>
+__device__ __noinline__ void collide_node_cold(const InstDev *Ip, const PartDev *parts, const uint8_t *fli,
+                                               const S *in, S *out, int n, uint8_t fl, int x, int y, int z,
+                                               typename Store<S>::real n0, typename Store<S>::real n1,
+                                               typename Store<S>::real n2, typename Store<S>::real m,
+                                               typename Store<S>::real kap, typename Store<S>::real *U,
+                                               long long Ntot, unsigned *status)
+{
+    using R = typename Store<S>::real;
+    const InstDev &I = *Ip;
+    GlobalNbr nb;
+    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
+    nb.fli = fli;
+    FluidPar<R> P;
+    load_par(I, P);
+    const R nn[3] = {n0, n1, n2};
+    const R gr[3] = {n0 * m, n1 * m, n2 * m};
+    R F[Q], G[Q];
+    gather<S>(I, parts, nb, in, (int)I.N, n, fl, F, G, x, y, z);
+    collide_store<S>(P, F, G, gr, nn, kap, out, (int)I.N, n, U, Ntot, status);
+}
+
+}  // namespace
+
+// order parameter after streaming (same sums as node_phi)
+template <class S, int MINB>
+__global__ void __launch_bounds__(ST_THREADS, MINB) k_phi_staged(Lattice L, int cur, long long n_items)
+{
+    using R = typename Store<S>::real;
+    using Ly = StLayout<S, false, MINB>;
+    const void *pop_in = L.pop[cur];
+    st_pipeline<S, false, MINB>(L, pop_in, n_items, [&](const StItem &it, const unsigned char *stg) {
+        const InstDev &I = L.inst[it.k];
+        const int nx = I.nx, ny = I.ny, nz = I.nz, N = (int)I.N;
+        const S *in = (const S *)pop_in + NPOP * I.node_off;
+        const S *sp = (const S *)stg;
+        const long long g0 = item_node0(I, it);
+        const uint8_t *sf = stg + Ly::POP + (g0 & 15);
+        R *phi = (R *)L.phi;
+        for (int j = threadIdx.x; j < it.cnt; j += ST_THREADS) {
+            const uint8_t fl = sf[j];
+            if ((fl & OWNER_MASK) != OWN_FLUID) continue;
+            const int r = it.whole ? j / nx : 0;
+            const int x = it.whole ? j - r * nx : it.x0 + j;
+            const int y = it.y0 + r, z = it.z;
+            const int n = (z * ny + y) * nx + x;
+            const StSrc b = st_src<Ly::A>(it, nx, r, x);
+            R v;
+            if ((fl & BOUND_BIT) || b.edge) {
+                v = phi_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, n, fl, x, y, z);
+            } else {
+                R sF = 0, sG = 0;
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    const int o = cx(i) == 1 ? b.bm : (cx(i) == -1 ? b.bp : b.b0);
+                    sF += wgt<R>(i) * Store<S>::lds(sp + i * Ly::BUFW + o);
+                    sG += wgt<R>(i) * Store<S>::lds(sp + (Q + i) * Ly::BUFW + o);
+                }
+                v = sG / (R(1) + sF);
+            }
+            phi[I.node_off + n] = v;
+        }
+    });
+}
+
+// force, collision, recolouring and write (same arithmetic as k_collide)
+template <class S, int MINB>
+__global__ void __launch_bounds__(ST_THREADS, MINB) k_collide_staged(Lattice L, int cur, long long n_items)
+{
+    using R = typename Store<S>::real;
+    using Ly = StLayout<S, true, MINB>;
+    const void *pop_in = L.pop[cur];
+    st_pipeline<S, true, MINB>(L, pop_in, n_items, [&](const StItem &it, const unsigned char *stg) {
+        const InstDev &I = L.inst[it.k];
+        const int nx = I.nx, ny = I.ny, nz = I.nz, N = (int)I.N;
+        const S *in = (const S *)pop_in + NPOP * I.node_off;
+        S *out = (S *)L.pop[cur ^ 1] + NPOP * I.node_off;
+        const S *sp = (const S *)stg;
+        const R *se = (const R *)(stg + Ly::POP);
+        const long long g0 = item_node0(I, it);
+        const uint8_t *sf = stg + Ly::POP + Ly::EXTB + (g0 & 15);
+        R *U = I.store_u ? (R *)L.u + I.node_off : nullptr;
+        FluidPar<R> P;
+        load_par(I, P);
+        for (int j = threadIdx.x; j < it.cnt; j += ST_THREADS) {
+            const uint8_t fl = sf[j];
+            const int r = it.whole ? j / nx : 0;
+            const int x = it.whole ? j - r * nx : it.x0 + j;
+            const int y = it.y0 + r, z = it.z;
+            const int n = (z * ny + y) * nx + x;
+            if ((fl & OWNER_MASK) != OWN_FLUID) {
+                if (U) { U[n] = 0; U[L.Ntot + n] = 0; U[2 * L.Ntot + n] = 0; }
+                continue;
+            }
+            const R nn[3] = {se[j], se[ST_SEGMAX + j], se[2 * ST_SEGMAX + j]};
+            const R m = se[3 * ST_SEGMAX + j];
+            const R kap = se[4 * ST_SEGMAX + j];
+            const StSrc b = st_src<Ly::A>(it, nx, r, x);
+            if ((fl & BOUND_BIT) || b.edge) {
+                collide_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, out, n, fl, x, y, z, nn[0], nn[1], nn[2],
+                                     m, kap, U, L.Ntot, L.status);
+                continue;
+            }
+            const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
+            R F[Q], sG = 0;
+#pragma unroll
+            for (int i = 0; i < Q; i++) {
+                const int o = cx(i) == 1 ? b.bm : (cx(i) == -1 ? b.bp : b.b0);
+                F[i] = Store<S>::lds(sp + i * Ly::BUFW + o);
+                sG += wgt<R>(i) * Store<S>::lds(sp + (Q + i) * Ly::BUFW + o);
+            }
+            collide_store_sg<S>(P, F, sG, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+        }
+    });
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+bool plan_staged(std::vector<InstDev> &inst, size_t elem, long long *items)
+{
+    const int A = 16 / (int)elem;
+    long long total = 0;
+    bool ok = true;
+    for (auto &I : inst) {
+        if (I.nx % A) ok = false;
+        if (I.nx <= ST_SEGMAX) {
+            I.st_rows = std::min(I.ny, ST_SEGMAX / I.nx);
+            I.st_seg = I.nx;
+            I.st_nseg = 1;
+        } else {
+            const int nseg = (I.nx + ST_SEGMAX - 1) / ST_SEGMAX;
+            int seg = (I.nx + nseg - 1) / nseg;
+            seg = (seg + A - 1) / A * A;
+            I.st_rows = 1;
+            I.st_seg = seg;
+            I.st_nseg = (I.nx + seg - 1) / seg;
+        }
+        I.st_ygroups = (I.ny + I.st_rows - 1) / I.st_rows;
+        I.st_item_start = total;
+        total += (long long)I.nz * I.st_ygroups * I.st_nseg;
+    }
+    *items = ok ? total : 0;
+    return ok;
+}
+
+template <class S, class K>
+static int persistent_grid(K kernel, size_t smem)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ST_THREADS, smem);
+    return std::max(1, sms * std::max(per_sm, 1));
+}
+
+// FP64 keeps one CTA per SM in both variants (its collision needs the full
+// register file)
+template <class S>
+constexpr int minb_of(int variant)
+{
+    return sizeof(S) == 8 ? 1 : (variant == 1 ? 1 : 2);
+}
+
+template <class S>
+void staged_grids(int *grid_phi, int *grid_collide)
+{
+    grid_phi[0] = persistent_grid<S>(k_phi_staged<S, minb_of<S>(0)>, StLayout<S, false, minb_of<S>(0)>::bytes());
+    grid_phi[1] = persistent_grid<S>(k_phi_staged<S, 1>, StLayout<S, false, 1>::bytes());
+    grid_collide[0] =
+        persistent_grid<S>(k_collide_staged<S, minb_of<S>(0)>, StLayout<S, true, minb_of<S>(0)>::bytes());
+    grid_collide[1] = persistent_grid<S>(k_collide_staged<S, 1>, StLayout<S, true, 1>::bytes());
+}
+
+template <class S, int MINB>
+static void staged_phi_v(const Lattice &L, int cur, const FluidLaunch &fz, int v, cudaStream_t st)
+{
+    const int grid = (int)std::min<long long>(fz.st_grid_phi[v], fz.st_items);
+    k_phi_staged<S, MINB><<<grid, ST_THREADS, StLayout<S, false, MINB>::bytes(), st>>>(L, cur, fz.st_items);
+}
+
+template <class S, int MINB>
+static void staged_collide_v(const Lattice &L, int cur, const FluidLaunch &fz, int v, cudaStream_t st)
+{
+    const int grid = (int)std::min<long long>(fz.st_grid_collide[v], fz.st_items);
+    k_collide_staged<S, MINB><<<grid, ST_THREADS, StLayout<S, true, MINB>::bytes(), st>>>(L, cur, fz.st_items);
+}
+
+// variant fz.tile (0 or 1)
+template <class S>
+void launch_staged_phi(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st)
+{
+    if (fz.tile == 1) staged_phi_v<S, 1>(L, cur, fz, 1, st);
+    else staged_phi_v<S, minb_of<S>(0)>(L, cur, fz, 0, st);
+}
+
+template <class S>
+void launch_staged_collide(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st)
+{
+    if (fz.tile == 1) staged_collide_v<S, 1>(L, cur, fz, 1, st);
+    else staged_collide_v<S, minb_of<S>(0)>(L, cur, fz, 0, st);
+}
+
+#define INST(S)                                                                                   \
+    template void staged_grids<S>(int *, int *);                                                  \
+    template void launch_staged_phi<S>(const Lattice &, int, const FluidLaunch &, cudaStream_t); \
+    template void launch_staged_collide<S>(const Lattice &, int, const FluidLaunch &, cudaStream_t);
+INST(double)
+INST(float)
+INST(__half)
+INST(__nv_bfloat16)
+#undef INST
+
+}  // namespace lbmg

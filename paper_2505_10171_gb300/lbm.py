@@ -69,9 +69,11 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_init_fields_device", "lbm_add_particles", "lbm_step", "lbm_particle_forces", "lbm_read_fields",
            "lbm_read_fields_device", "lbm_num_particles", "lbm_num_nodes", "lbm_diagnostics", "lbm_set_launch",
            "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
-           "lbm_set_fluid_kernel"]
+           "lbm_set_fluid_kernel", "lbm_fluid_form_in_use"]
 STAGES = ["phi", "solid_phi", "grad_wetting", "collide", "momentum_exchange", "capillary", "dem", "geom_owner",
-          "geom_boundary", "refill", "fused", "particle_region"]
+          "geom_boundary", "refill", "fused", "particle_region", "curvature"]
+# fluid launch forms of lbm_set_fluid_kernel
+FORM_STAGED, FORM_FUSED, FORM_PLAIN = 0, 1, 2
 
 
 def load(path: str = LIB_PATH):
@@ -102,6 +104,8 @@ def load(path: str = LIB_PATH):
     L.lbm_num_nodes.restype = ct.c_longlong
     L.lbm_diagnostics.argtypes = [vp, i, d]
     L.lbm_set_launch.argtypes = [vp, i]
+    L.lbm_fluid_form_in_use.argtypes = [vp]
+    L.lbm_fluid_form_in_use.restype = i
     L.lbm_last_launch_count.argtypes = [vp]
     L.lbm_last_launch_count.restype = ct.c_longlong
     L.lbm_profile.argtypes = [vp, i]
@@ -248,8 +252,11 @@ class Context:
     def lbm_set_launch(self, block_threads):
         self._check(self.L.lbm_set_launch(self.h, int(block_threads)))
 
-    def lbm_set_fluid_kernel(self, fused=1, tile=0, zchunk=0):
-        self._check(self.L.lbm_set_fluid_kernel(self.h, int(fused), int(tile), int(zchunk)))
+    def lbm_set_fluid_kernel(self, form=FORM_STAGED, tile=0, zchunk=0):
+        self._check(self.L.lbm_set_fluid_kernel(self.h, int(form), int(tile), int(zchunk)))
+
+    def lbm_fluid_form_in_use(self):
+        return int(self.L.lbm_fluid_form_in_use(self.h))
 
     def lbm_last_launch_count(self):
         return int(self.L.lbm_last_launch_count(self.h))

@@ -168,18 +168,23 @@ def test_fp64_static_tube_mask():
     assert_fp64_parity(run_gpu(w, 20, "fp64"), o)
 
 
-def test_batched_instances_match_single_runs():
+@pytest.mark.parametrize("sizes,form", [
+    (((40, 24, 20, 7.0), (33, 29, 17, 6.0), (24, 24, 24, 5.0)), 2),  # nx = 33: plain form
+    (((48, 24, 20, 7.0), (40, 29, 17, 6.0), (24, 24, 24, 5.0)), 0),  # all staged, 5/6/10 rows per item
+])
+def test_batched_instances_match_single_runs(sizes, form):
     """Three uneven instances stepped in one context equal three separate runs
     bit for bit, and the oracle within the FP64 bar."""
     from paper_2505_10171_gb300 import lbm
     ws = []
-    for k, (nx, ny, nz, R) in enumerate(((40, 24, 20, 7.0), (33, 29, 17, 6.0), (24, 24, 24, 5.0))):
+    for k, (nx, ny, nz, R) in enumerate(sizes):
         p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=80.0 + 15 * k, nu_a=1 / 6,
                  nu_b=1 / 30, mu_s=0.2, store_velocity=1)
         phi = W.drop_phi(nx, ny, nz, (nx / 3, ny / 2, 0.5), R)
         parts = [dict(x=(nx / 3 + R + 6.0, ny / 2, 4.5), R=3.0, theta_deg=90.0, rho_p=W.PARTICLE_DENSITY)]
         ws.append(dict(params=p, phi=phi, particles=parts))
     c = lbm.Context([w["params"] for w in ws], "fp64")
+    assert c.lbm_fluid_form_in_use() == form
     for k, w in enumerate(ws):
         c.lbm_add_particles(w["particles"], inst=k)
         c.lbm_init_fields(w["phi"], inst=k)
@@ -258,32 +263,54 @@ def test_2d_slab_domain_matches_oracle():
     assert_fp64_parity(run_gpu(w, 100, "fp64"), o)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_fused_kernel_equals_four_kernel_form(prec):
-    """The z-marching fused kernel (every tile shape, several z-chunk sizes,
-    ragged tiles and chunks) gives the same bits as the four-kernel form."""
-    nx, ny, nz = 45, 21, 27
+# 45: rows not whole 16-byte units (plain form only); 48: five whole rows per
+# staged item with y-wrapped sources; 264: rows cut into two staged segments
+FORM_SHAPES = [(45, 21, 27), (48, 21, 27), (264, 16, 13)]
+
+
+def _forms_workload(nx, ny, nz):
     p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, wall_velocity=(1e-3, 0, 0), theta_wall_deg=70.0,
              nu_a=1 / 6, nu_b=1 / 30, mu_s=0.3, mu_r=0.05, g_particle=(0.0, 0.0, -0.05))
-    phi = W.drop_phi(nx, ny, nz, (14.0, 10.0, 0.5), 8.0)
-    parts = [dict(x=(29.0, 10.5, 5.5), R=4.0, theta_deg=60.0, rho_p=W.PARTICLE_DENSITY),
-             dict(x=(39.0, 4.2, 6.5), R=3.5, theta_deg=120.0, rho_p=W.PARTICLE_DENSITY)]
-    w = dict(params=p, phi=phi, particles=parts)
+    phi = W.drop_phi(nx, ny, nz, (0.3 * nx, ny / 2, 0.5), min(8.0, ny / 2 - 2))
+    parts = [dict(x=(0.65 * nx, ny / 2 + 0.5, 5.5), R=4.0, theta_deg=60.0, rho_p=W.PARTICLE_DENSITY),
+             dict(x=(0.87 * nx, 0.2 * ny, 6.5), R=3.5, theta_deg=120.0, rho_p=W.PARTICLE_DENSITY)]
+    return dict(params=p, phi=phi, particles=parts)
 
-    def run(fused, tile=0, zc=0):
+
+@pytest.mark.parametrize("shape", FORM_SHAPES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_launch_forms_agree(prec, shape):
+    """The staged form (both variants) gives the bits of the plain form; the
+    z-marching fused form (both tiles, several z-chunk sizes, ragged tiles and
+    chunks) the same bits in FP32 and agrees to rounding in FP64."""
+    from paper_2505_10171_gb300 import lbm
+    w = _forms_workload(*shape)
+    aligned = shape[0] % (16 // {"fp64": 8, "fp32": 4, "fp16": 2}[prec]) == 0
+
+    def run(form, tile=0, zc=0):
         c = gpu_ctx(w, prec)
-        c.lbm_set_fluid_kernel(fused, tile, zc)
+        c.lbm_set_fluid_kernel(form, tile, zc)
+        used = c.lbm_fluid_form_in_use()
         c.lbm_step(25)
         fa, fb = c.pops()
         out = (fa, fb, c.lbm_particle_forces(), c.fields()["u"])
         c.close()
-        return out
+        return used, out
 
-    ref = run(0)
-    for tile, zc in ((0, 0), (1, 5), (2, 7), (0, 27), (0, 1)):
-        got = run(1, tile, zc)
+    used, ref = run(lbm.FORM_PLAIN)
+    assert used == lbm.FORM_PLAIN
+    for tile in (0, 1):
+        used, got = run(lbm.FORM_STAGED, tile)
+        assert used == (lbm.FORM_STAGED if aligned else lbm.FORM_PLAIN)
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b), ("staged", tile)
+    if prec == "fp16":
+        return
+    for tile, zc in ((0, 0), (1, 5), (0, 7), (1, 27), (0, 1)):
+        used, got = run(lbm.FORM_FUSED, tile, zc)
+        assert used == lbm.FORM_FUSED
         for a, b in zip(ref, got):
             if prec == "fp32":
-                assert np.array_equal(a, b), (tile, zc)
+                assert np.array_equal(a, b), ("fused", tile, zc)
             else:  # FMA contraction may differ between the two kernels
-                assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(a).max()), (tile, zc)
+                assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(a).max()), ("fused", tile, zc)
