@@ -208,14 +208,17 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads);
 /* Fluid-update launch form (all forms compute the same update).
  * form = 0 (default), staged: five kernels per step (order parameter, solid
  *   phi, gradient, curvature, collision); the two kernels that stream the
- *   populations are persistent and bring each strip of x-rows into shared
- *   memory with bulk asynchronous copies.  Needs nx * (bytes per stored
- *   population) to be a multiple of 16 in every instance; otherwise the plain
- *   form runs.
+ *   populations are persistent and bring each strip of x-rows into a ring of
+ *   shared-memory stages with asynchronous copies.  tile selects the variant:
+ *   0 16-byte cp.async copies by all threads, two CTAs per SM; 1 bulk copies
+ *   (cp.async.bulk) completing on mbarriers, two CTAs per SM; 2 as 0 with one
+ *   CTA per SM and a deeper ring.  Needs nx * (bytes per stored population)
+ *   to be a multiple of 16 in every instance; otherwise the plain form runs.
  * form = 1, fused: one z-marching kernel per step; tile selects its column
  *   tile (0: 16x16, 1: 32x8); zchunk is the number of z-planes per work item
  *   (0: automatic, 32).
- * form = 2, plain: the five kernels with one thread per node and direct loads.
+ * form = 2, plain: the five kernels with one thread per node and direct loads
+ *   (tile must be 0).
  * Staged and plain agree bit for bit; fused agrees bit for bit in FP32 and to
  * rounding (FMA contraction) in FP64.  Invalid form, tile or zchunk -> LBM_ERR_ARG.
  * Invalidates the step graph. */

@@ -54,7 +54,7 @@ struct lbm_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
     // fluid launch form: staged (default), fused z-marching or plain
-    FluidLaunch fz = {FORM_STAGED, 0, 0, 0, {0, 0}, {0, 0}};
+    FluidLaunch fz = {FORM_STAGED, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
 };
 
@@ -1018,8 +1018,10 @@ long long lbm_last_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->last_lau
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
 {
     if (!ctx) return LBM_ERR_ARG;
-    if (form < FORM_STAGED || form > FORM_PLAIN || tile < 0 || tile > 1 || zchunk < 0)
-        return fail(ctx, LBM_ERR_ARG, "form must be 0 (staged), 1 (fused) or 2 (plain), tile 0..1, zchunk >= 0");
+    const int max_tile = form == FORM_STAGED ? 2 : (form == FORM_FUSED ? 1 : 0);
+    if (form < FORM_STAGED || form > FORM_PLAIN || tile < 0 || tile > max_tile || zchunk < 0)
+        return fail(ctx, LBM_ERR_ARG,
+                    "form must be 0 (staged, tile 0..2), 1 (fused, tile 0..1) or 2 (plain, tile 0); zchunk >= 0");
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->fz.form = form;
     ctx->fz.tile = tile;

@@ -403,9 +403,8 @@ struct FluidLaunch {
     int tile;           // fused tile shape index (see lbm_fluid.cu)
     long long items;    // fused work items (all instances)
     long long st_items; // staged work items (all instances); 0: staged form unavailable
-    // persistent grids of the staged kernels, per variant (0: two CTAs per SM,
-    // 1: one CTA per SM with a deeper copy ring)
-    int st_grid_phi[2], st_grid_collide[2];
+    // persistent grids of the staged kernels, per variant (see lbm_staged.cu)
+    int st_grid_phi[3], st_grid_collide[3];
 };
 // staged kernels: threads per CTA and nodes per work item at most
 constexpr int ST_THREADS = 256;
@@ -418,7 +417,7 @@ struct StagedCfg {
 // not a multiple of 16 bytes of storage, which the bulk copies need)
 bool plan_staged(std::vector<InstDev> &inst, size_t elem, long long *items);
 template <class S>
-void staged_grids(int *grid_phi, int *grid_collide);  // arrays of 2 (variants)
+void staged_grids(int *grid_phi, int *grid_collide);  // arrays of 3 (variants)
 template <class S>
 void launch_staged_phi(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
 template <class S>

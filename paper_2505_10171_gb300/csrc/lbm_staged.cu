@@ -72,6 +72,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, unsigned
                  : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only), and its group fences
+__device__ __forceinline__ void cp16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // shared-memory stage: NPOP population strips of BUFW elements, then (EXT) the
 // normal n (3), |grad phi|_eps and curvature of the strip's nodes, then its
 // flags (from the 16-byte boundary below the first node)
@@ -184,6 +193,56 @@ __device__ void st_issue(const Lattice &L, const void *pop_in, const StItem &it,
     }
 }
 
+// the same copies as st_issue, spread over all threads as 16-byte cp.async:
+// warp w takes populations w, w + 8, ..., its lanes the 16-byte chunks of each
+// source row; then the five per-node arrays and the flags
+template <class S, bool EXT, int MINB>
+__device__ __forceinline__ void st_issue_async(const Lattice &L, const void *pop_in, const StItem &it,
+                                               unsigned char *stage)
+{
+    using Ly = StLayout<S, EXT, MINB>;
+    using R = typename Store<S>::real;
+    constexpr int A = Ly::A;
+    constexpr int NW = ST_THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const InstDev &I = L.inst[it.k];
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long N = I.N;
+    const S *in = (const S *)pop_in + NPOP * I.node_off;
+    const int lo = it.whole ? 0 : max(it.x0 - A, 0);
+    const int hi = it.whole ? nx : min(it.x0 + it.cnt + A, nx);
+    const int nrows = it.whole ? it.nrows : 1;
+    const int rowch = (hi - lo) * (int)sizeof(S) / 16;  // 16-byte chunks per copied row
+    const int dst0 = it.whole ? 0 : (lo - (it.x0 - A)) * (int)sizeof(S);
+    const int rowb = nx * (int)sizeof(S);
+    for (int q = warp; q < NPOP; q += NW) {
+        const int d = q < Q ? q : q - Q;
+        const int zs = wrap1(it.z - cz(d), nz);
+        const char *src = (const char *)(in + (long long)q * N + (long long)zs * ny * nx + lo);
+        const uint32_t dst = smem_addr(stage + (size_t)q * Ly::BUFW * sizeof(S)) + dst0;
+        for (int r = 0; r < nrows; r++) {
+            const int ys = wrap1(it.y0 + r - cy(d), ny);
+            const char *sr = src + (long long)ys * rowb;
+            for (int ch = lane; ch < rowch; ch += 32) cp16(dst + r * rowb + 16 * ch, sr + 16 * ch);
+        }
+    }
+    const long long g0 = item_node0(I, it);
+    if (EXT && warp < 5) {
+        const R *base = warp < 3 ? (const R *)L.grad + (long long)warp * L.Ntot
+                                 : (warp == 3 ? (const R *)L.gmag : (const R *)L.kap);
+        const char *src = (const char *)(base + g0);
+        const uint32_t dst = smem_addr(stage + Ly::POP + (size_t)warp * ST_SEGMAX * sizeof(R));
+        const int nch = it.cnt * (int)sizeof(R) / 16;
+        for (int ch = lane; ch < nch; ch += 32) cp16(dst + 16 * ch, src + 16 * ch);
+    }
+    if (warp == NW - 1) {
+        const long long fst = g0 & ~15ll, fen = (g0 + it.cnt + 15) & ~15ll;
+        const int nch = (int)(fen - fst) / 16;
+        const uint32_t dst = smem_addr(stage + Ly::POP + Ly::EXTB);
+        for (int ch = lane; ch < nch; ch += 32) cp16(dst + 16 * ch, L.flags + fst + 16 * ch);
+    }
+}
+
 // shared-memory indices of the sources x-1, x, x+1 of node (x, row r) in a
 // stage strip; `edge` marks the end nodes of a cut row, whose wrapped source
 // is not in the strip
@@ -266,6 +325,45 @@ __device__ __forceinline__ void st_pipeline(const Lattice &L, const void *pop_in
     }
 }
 
+// the pipeline with cp.async staging: NST - 1 items in flight per thread; the
+// barrier at the top of each iteration both publishes item k's copies and
+// frees the stage of item k - 1 for item k + NST - 1 (no spin-waits)
+template <class S, bool EXT, int MINB, class Body>
+__device__ __forceinline__ void st_pipeline_async(const Lattice &L, const void *pop_in, long long n_items,
+                                                  Body &&body)
+{
+    using Ly = StLayout<S, EXT, MINB>;
+    constexpr int NST = Ly::NST;
+    extern __shared__ __align__(128) unsigned char st_smem[];
+    auto stage = [&](int s) { return st_smem + Ly::HEAD + (size_t)s * Ly::STAGE; };
+    for (int s = 0; s < NST - 1; s++) {
+        const long long item = blockIdx.x + (long long)s * gridDim.x;
+        if (item < n_items) {
+            StItem it;
+            st_item(L, item, it);
+            st_issue_async<S, EXT, MINB>(L, pop_in, it, stage(s));
+        }
+        cp_commit();
+    }
+    for (long long k = 0;; k++) {
+        const long long item = blockIdx.x + k * gridDim.x;
+        if (item >= n_items) break;
+        cp_wait<NST - 2>();
+        __syncthreads();
+        const long long nxt = item + (long long)(NST - 1) * gridDim.x;
+        if (nxt < n_items) {
+            StItem it2;
+            st_item(L, nxt, it2);
+            st_issue_async<S, EXT, MINB>(L, pop_in, it2, stage((int)((k + NST - 1) % NST)));
+        }
+        cp_commit();
+        StItem it;
+        st_item(L, item, it);
+        body(it, (const unsigned char *)stage((int)(k % NST)));
+    }
+    cp_wait<0>();
+}
+
 // nodes next to a solid and the end nodes of a cut row take the global-memory
 // path; kept out of line so that their registers do not weigh on the hot loop
 template <class S>
@@ -305,13 +403,13 @@ __device__ __noinline__ void collide_node_cold(const InstDev *Ip, const PartDev 
 }  // namespace
 
 // order parameter after streaming (same sums as node_phi)
-template <class S, int MINB>
+template <class S, int MINB, bool ASYNC>
 __global__ void __launch_bounds__(ST_THREADS, MINB) k_phi_staged(Lattice L, int cur, long long n_items)
 {
     using R = typename Store<S>::real;
     using Ly = StLayout<S, false, MINB>;
     const void *pop_in = L.pop[cur];
-    st_pipeline<S, false, MINB>(L, pop_in, n_items, [&](const StItem &it, const unsigned char *stg) {
+    auto body = [&](const StItem &it, const unsigned char *stg) {
         const InstDev &I = L.inst[it.k];
         const int nx = I.nx, ny = I.ny, nz = I.nz, N = (int)I.N;
         const S *in = (const S *)pop_in + NPOP * I.node_off;
@@ -342,17 +440,19 @@ __global__ void __launch_bounds__(ST_THREADS, MINB) k_phi_staged(Lattice L, int 
             }
             phi[I.node_off + n] = v;
         }
-    });
+    };
+    if constexpr (ASYNC) st_pipeline_async<S, false, MINB>(L, pop_in, n_items, body);
+    else st_pipeline<S, false, MINB>(L, pop_in, n_items, body);
 }
 
 // force, collision, recolouring and write (same arithmetic as k_collide)
-template <class S, int MINB>
+template <class S, int MINB, bool ASYNC>
 __global__ void __launch_bounds__(ST_THREADS, MINB) k_collide_staged(Lattice L, int cur, long long n_items)
 {
     using R = typename Store<S>::real;
     using Ly = StLayout<S, true, MINB>;
     const void *pop_in = L.pop[cur];
-    st_pipeline<S, true, MINB>(L, pop_in, n_items, [&](const StItem &it, const unsigned char *stg) {
+    auto body = [&](const StItem &it, const unsigned char *stg) {
         const InstDev &I = L.inst[it.k];
         const int nx = I.nx, ny = I.ny, nz = I.nz, N = (int)I.N;
         const S *in = (const S *)pop_in + NPOP * I.node_off;
@@ -393,7 +493,9 @@ __global__ void __launch_bounds__(ST_THREADS, MINB) k_collide_staged(Lattice L, 
             }
             collide_store_sg<S>(P, F, sG, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
         }
-    });
+    };
+    if constexpr (ASYNC) st_pipeline_async<S, true, MINB>(L, pop_in, n_items, body);
+    else st_pipeline<S, true, MINB>(L, pop_in, n_items, body);
 }
 
 // ---------------------------------------------------------------------------
@@ -437,51 +539,71 @@ static int persistent_grid(K kernel, size_t smem)
     return std::max(1, sms * std::max(per_sm, 1));
 }
 
-// FP64 keeps one CTA per SM in both variants (its collision needs the full
-// register file)
+// staged variants: 0 cp.async copies, two CTAs per SM; 1 bulk copies, two
+// CTAs per SM; 2 cp.async copies, one CTA per SM with a deeper ring.  FP64
+// keeps one CTA per SM throughout (its collision needs the full register file).
 template <class S>
 constexpr int minb_of(int variant)
 {
-    return sizeof(S) == 8 ? 1 : (variant == 1 ? 1 : 2);
+    return sizeof(S) == 8 ? 1 : (variant == 2 ? 1 : 2);
+}
+
+template <class S, int V>
+struct StVariant {
+    static constexpr int MINB = minb_of<S>(V);
+    static constexpr bool ASYNC = V != 1;
+};
+
+template <class S, int V>
+static void grids_v(int *grid_phi, int *grid_collide)
+{
+    using Vt = StVariant<S, V>;
+    grid_phi[V] = persistent_grid<S>(k_phi_staged<S, Vt::MINB, Vt::ASYNC>, StLayout<S, false, Vt::MINB>::bytes());
+    grid_collide[V] =
+        persistent_grid<S>(k_collide_staged<S, Vt::MINB, Vt::ASYNC>, StLayout<S, true, Vt::MINB>::bytes());
 }
 
 template <class S>
 void staged_grids(int *grid_phi, int *grid_collide)
 {
-    grid_phi[0] = persistent_grid<S>(k_phi_staged<S, minb_of<S>(0)>, StLayout<S, false, minb_of<S>(0)>::bytes());
-    grid_phi[1] = persistent_grid<S>(k_phi_staged<S, 1>, StLayout<S, false, 1>::bytes());
-    grid_collide[0] =
-        persistent_grid<S>(k_collide_staged<S, minb_of<S>(0)>, StLayout<S, true, minb_of<S>(0)>::bytes());
-    grid_collide[1] = persistent_grid<S>(k_collide_staged<S, 1>, StLayout<S, true, 1>::bytes());
+    grids_v<S, 0>(grid_phi, grid_collide);
+    grids_v<S, 1>(grid_phi, grid_collide);
+    grids_v<S, 2>(grid_phi, grid_collide);
 }
 
-template <class S, int MINB>
-static void staged_phi_v(const Lattice &L, int cur, const FluidLaunch &fz, int v, cudaStream_t st)
+template <class S, int V>
+static void staged_phi_v(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st)
 {
-    const int grid = (int)std::min<long long>(fz.st_grid_phi[v], fz.st_items);
-    k_phi_staged<S, MINB><<<grid, ST_THREADS, StLayout<S, false, MINB>::bytes(), st>>>(L, cur, fz.st_items);
+    using Vt = StVariant<S, V>;
+    const int grid = (int)std::min<long long>(fz.st_grid_phi[V], fz.st_items);
+    k_phi_staged<S, Vt::MINB, Vt::ASYNC>
+        <<<grid, ST_THREADS, StLayout<S, false, Vt::MINB>::bytes(), st>>>(L, cur, fz.st_items);
 }
 
-template <class S, int MINB>
-static void staged_collide_v(const Lattice &L, int cur, const FluidLaunch &fz, int v, cudaStream_t st)
+template <class S, int V>
+static void staged_collide_v(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st)
 {
-    const int grid = (int)std::min<long long>(fz.st_grid_collide[v], fz.st_items);
-    k_collide_staged<S, MINB><<<grid, ST_THREADS, StLayout<S, true, MINB>::bytes(), st>>>(L, cur, fz.st_items);
+    using Vt = StVariant<S, V>;
+    const int grid = (int)std::min<long long>(fz.st_grid_collide[V], fz.st_items);
+    k_collide_staged<S, Vt::MINB, Vt::ASYNC>
+        <<<grid, ST_THREADS, StLayout<S, true, Vt::MINB>::bytes(), st>>>(L, cur, fz.st_items);
 }
 
-// variant fz.tile (0 or 1)
+// variant fz.tile (0, 1 or 2)
 template <class S>
 void launch_staged_phi(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st)
 {
-    if (fz.tile == 1) staged_phi_v<S, 1>(L, cur, fz, 1, st);
-    else staged_phi_v<S, minb_of<S>(0)>(L, cur, fz, 0, st);
+    if (fz.tile == 1) staged_phi_v<S, 1>(L, cur, fz, st);
+    else if (fz.tile == 2) staged_phi_v<S, 2>(L, cur, fz, st);
+    else staged_phi_v<S, 0>(L, cur, fz, st);
 }
 
 template <class S>
 void launch_staged_collide(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st)
 {
-    if (fz.tile == 1) staged_collide_v<S, 1>(L, cur, fz, 1, st);
-    else staged_collide_v<S, minb_of<S>(0)>(L, cur, fz, 0, st);
+    if (fz.tile == 1) staged_collide_v<S, 1>(L, cur, fz, st);
+    else if (fz.tile == 2) staged_collide_v<S, 2>(L, cur, fz, st);
+    else staged_collide_v<S, 0>(L, cur, fz, st);
 }
 
 #define INST(S)                                                                                   \

@@ -280,7 +280,7 @@ def _forms_workload(nx, ny, nz):
 @pytest.mark.parametrize("shape", FORM_SHAPES)
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
 def test_launch_forms_agree(prec, shape):
-    """The staged form (both variants) gives the bits of the plain form; the
+    """The staged form (all three variants) gives the bits of the plain form; the
     z-marching fused form (both tiles, several z-chunk sizes, ragged tiles and
     chunks) the same bits in FP32 and agrees to rounding in FP64."""
     from paper_2505_10171_gb300 import lbm
@@ -299,7 +299,7 @@ def test_launch_forms_agree(prec, shape):
 
     used, ref = run(lbm.FORM_PLAIN)
     assert used == lbm.FORM_PLAIN
-    for tile in (0, 1):
+    for tile in (0, 1, 2):
         used, got = run(lbm.FORM_STAGED, tile)
         assert used == (lbm.FORM_STAGED if aligned else lbm.FORM_PLAIN)
         for a, b in zip(ref, got):
