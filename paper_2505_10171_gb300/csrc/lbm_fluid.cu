@@ -25,6 +25,15 @@
 // double for S = double and float otherwise.
 #include "lbm_node.cuh"
 
+// CTAs of 256 threads per SM the single-precision order-parameter and
+// collision kernels are compiled for (register budget 65536 / (256 x this))
+#ifndef LBM_PHI_MINB
+#define LBM_PHI_MINB 2
+#endif
+#ifndef LBM_COLLIDE_MINB
+#define LBM_COLLIDE_MINB 2
+#endif
+
 namespace lbmg {
 
 // ---------------------------------------------------------------------------
@@ -60,11 +69,17 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID) return;
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = L.flags + I.node_off;
     const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
-    ((R *)L.phi)[g] = node_phi<S>(I, L.parts, nb, in, (int)I.N, n, fl, x, y, z);
+    R v;
+    if (fl & BOUND_BIT) {
+        v = phi_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, n, fl, x, y, z);
+    } else {
+        GlobalNbr nb;
+        nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
+        nb.fli = L.flags + I.node_off;
+        v = phi_fluid<S>(nb, in, (int)I.N);
+    }
+    ((R *)L.phi)[g] = v;
 }
 
 template <class R>
@@ -105,7 +120,7 @@ __device__ __forceinline__ void grad_body(const Lattice &L, const InstDev &I, in
 }
 
 template <class S>
-__global__ void k_phi(Lattice L, int cur)
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
 {
     LBM_NODE_PROLOGUE
     phi_body<S>(L, I, cur, n, x, y, z);
@@ -169,7 +184,7 @@ __global__ void k_curv(Lattice L)
 }
 
 template <class S>
-__global__ void __launch_bounds__(256, sizeof(typename Store<S>::real) == 8 ? 1 : 2) k_collide(Lattice L, int cur)
+__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_collide(Lattice L, int cur)
 {
     using R = typename Store<S>::real;
     LBM_NODE_PROLOGUE
@@ -183,20 +198,26 @@ __global__ void __launch_bounds__(256, sizeof(typename Store<S>::real) == 8 ? 1 
     }
     const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
     S *out = (S *)L.pop[cur ^ 1] + NPOP * I.node_off;
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = L.flags + I.node_off;
-    FluidPar<R> P;
-    load_par(I, P);
     const R *Nn = (const R *)L.grad + I.node_off;
     const long long Nt = L.Ntot;
     const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
     const R m = ((const R *)L.gmag)[g];
-    const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
     const R kap = ((const R *)L.kap)[g];
-    R F[Q], G[Q];
-    gather<S>(I, L.parts, nb, in, N, n, fl, F, G, x, y, z);
-    collide_store<S>(P, F, G, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+    const R phi = ((const R *)L.phi)[g];
+    if (fl & BOUND_BIT) {
+        collide_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, out, n, fl, x, y, z, phi, nn[0], nn[1], nn[2], m,
+                             kap, U, L.Ntot, L.status);
+        return;
+    }
+    Nbr nb;
+    nb.init(x, y, z, I.nx, I.ny, I.nz);
+    R F[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) F[i] = Store<S>::ld(in + i * N + nb.at(-cx(i), -cy(i), -cz(i)));
+    FluidPar<R> P;
+    load_par(I, P);
+    const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
 }
 
 // tile shapes of the fused kernel: 0 -> 16 x 16, 1 -> 32 x 8

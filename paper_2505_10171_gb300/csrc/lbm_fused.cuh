@@ -189,9 +189,9 @@ __global__ void __launch_bounds__(TX *TY, 2) k_fused(Lattice L, int cur)
                     return nS[(nsl[dz + 1] * 3 + a) * R1N + r1 + dy * W1 + dx];
                 };
                 const R kap = curvature<R>(nf);
-                R F[Q], G[Q];
-                gather<S>(I, L.parts, nb, in, N, n, fl, F, G, gx, gy, Z);
-                collide_store<S>(P, F, G, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+                R F[Q];
+                gather_F<S>(I, L.parts, nb, in, N, n, fl, F, gx, gy, Z);
+                collide_store_phi<S>(P, F, phiS[s0 * RN + r], gr, nn, kap, out, N, n, U, L.Ntot, L.status);
             }
         }
         __syncthreads();

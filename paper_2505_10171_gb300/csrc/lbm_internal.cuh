@@ -322,6 +322,58 @@ __device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, c
     }
 }
 
+// pull streaming of the total populations only (F), with the same
+// bounce-back as gather(); the collision needs the colour offsets only through
+// the order parameter, which the order-parameter kernel has already stored
+template <class S, class A>
+__device__ __forceinline__ void gather_F(const InstDev &I, const PartDev *parts, const A &nbr,
+                                         const S *__restrict__ in, int N, int n, uint8_t fl,
+                                         typename Store<S>::real *F, int x, int y, int z)
+{
+    using R = typename Store<S>::real;
+    if (!(fl & BOUND_BIT)) {
+#pragma unroll
+        for (int i = 0; i < Q; i++) F[i] = Store<S>::ld(in + i * N + nbr.idx(-cx(i), -cy(i), -cz(i)));
+        return;
+    }
+    bool have_rho = false;
+    R rr = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int own = nbr.own(-cx(i), -cy(i), -cz(i));
+        if (own == OWN_FLUID) {
+            F[i] = Store<S>::ld(in + i * N + nbr.idx(-cx(i), -cy(i), -cz(i)));
+            continue;
+        }
+        if (!have_rho) {
+            R sF = 0;
+#pragma unroll
+            for (int j = 0; j < Q; j++) sF += wgt<R>(j) * Store<S>::ld(in + j * N + n);
+            rr = R(1) + sF;
+            have_rho = true;
+        }
+        double uw[3], lev[3];
+        surface_velocity(I, parts, own, x - 0.5 * cx(i), y - 0.5 * cy(i), z - 0.5 * cz(i), uw, lev);
+        const R cu = (R)(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
+        F[i] = Store<S>::ld(in + opp(i) * N + n) + R(6) * rr * cu;
+    }
+}
+
+// order parameter of a fluid node none of whose neighbours is solid
+template <class S, class A>
+__device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const S *__restrict__ in, int N)
+{
+    using R = typename Store<S>::real;
+    R sF = 0, sG = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
+        sF += wgt<R>(i) * Store<S>::ld(in + i * N + s);
+        sG += wgt<R>(i) * Store<S>::ld(in + (Q + i) * N + s);
+    }
+    return sG / (R(1) + sF);
+}
+
 // order parameter of a fluid node after streaming: the same sums as the
 // collision's, without keeping the 38 values
 template <class S, class A>
@@ -330,16 +382,8 @@ __device__ __forceinline__ typename Store<S>::real node_phi(const InstDev &I, co
                                                             int x, int y, int z)
 {
     using R = typename Store<S>::real;
+    if (!(fl & BOUND_BIT)) return phi_fluid<S>(nbr, in, N);
     R sF = 0, sG = 0;
-    if (!(fl & BOUND_BIT)) {
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-            sF += wgt<R>(i) * Store<S>::ld(in + i * N + s);
-            sG += wgt<R>(i) * Store<S>::ld(in + (Q + i) * N + s);
-        }
-        return sG / (R(1) + sF);
-    }
     R F[Q], G[Q];
     gather<S>(I, parts, nbr, in, N, n, fl, F, G, x, y, z);
 #pragma unroll

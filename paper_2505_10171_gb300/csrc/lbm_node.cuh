@@ -98,14 +98,16 @@ __device__ __forceinline__ void grad_node(const InstDev &I, const PartDev *parts
 }
 
 // force, velocity, MRT (two-relaxation-time form) with Guo forcing,
-// recolouring and the write of node n.  F, G: streamed offsets; g: corrected
-// grad(phi) of the node; nn: its regularised normal; kap: curvature.
+// recolouring and the write of node n.  F: streamed total offsets; phi: the
+// order parameter after streaming (stored by the order-parameter pass: the
+// colour offsets enter the update only through it); g: corrected grad(phi) of
+// the node; nn: its regularised normal; kap: curvature.
 template <class S>
-__device__ __forceinline__ void collide_store_sg(const FluidPar<typename Store<S>::real> &P,
-                                                 const typename Store<S>::real *F, typename Store<S>::real sG,
-                                                 const typename Store<S>::real *g, const typename Store<S>::real *nn,
-                                                 typename Store<S>::real kap, S *__restrict__ out, int N, int n,
-                                                 typename Store<S>::real *U, long long Ustride, unsigned *status)
+__device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<S>::real> &P,
+                                                  const typename Store<S>::real *F, typename Store<S>::real phi,
+                                                  const typename Store<S>::real *g, const typename Store<S>::real *nn,
+                                                  typename Store<S>::real kap, S *__restrict__ out, int N, int n,
+                                                  typename Store<S>::real *U, long long Ustride, unsigned *status)
 {
     using R = typename Store<S>::real;
     R sF = 0, jx = 0, jy = 0, jz = 0;
@@ -118,7 +120,6 @@ __device__ __forceinline__ void collide_store_sg(const FluidPar<typename Store<S
         if (cz(i)) jz += w * cz(i) * F[i];
     }
     const R rr = R(1) + sF;  // rho / rho0
-    const R phi = sG * frcp(rr);
     if (!(rr > R(0)) || !(phi == phi)) atomicOr(status, ST_UNSTABLE);
     // force density: CSF -1/2 sigma kappa grad(phi) plus phase-weighted body forces
     const R hs = R(-0.5) * P.sigma * kap;
@@ -178,21 +179,6 @@ __device__ __forceinline__ void collide_store_sg(const FluidPar<typename Store<S
     }
 }
 
-// the same with the streamed colour offsets G; only their weighted sum
-// sG = sum_i w_i G_i (summed in i order) enters the update
-template <class S>
-__device__ __forceinline__ void collide_store(const FluidPar<typename Store<S>::real> &P, const typename Store<S>::real *F,
-                                              const typename Store<S>::real *G, const typename Store<S>::real *g,
-                                              const typename Store<S>::real *nn, typename Store<S>::real kap,
-                                              S *__restrict__ out, int N, int n, typename Store<S>::real *U,
-                                              long long Ustride, unsigned *status)
-{
-    using R = typename Store<S>::real;
-    R sG = 0;
-#pragma unroll
-    for (int i = 0; i < Q; i++) sG += wgt<R>(i) * G[i];
-    collide_store_sg<S>(P, F, sG, g, nn, kap, out, N, n, U, Ustride, status);
-}
 
 // curvature kappa = 3 sum_i w_i c_i . n(x + c_i), taken over opposite pairs as
 // w_i c_i . (n(x + c_i) - n(x - c_i)) so that only the components along c_i
@@ -221,6 +207,43 @@ __device__ __forceinline__ R reg_normal(const R *g, R eps2, R *nn)
     const R im = frsqrt(m2);
     nn[0] = g[0] * im; nn[1] = g[1] * im; nn[2] = g[2] * im;
     return m2 * im;
+}
+
+// nodes next to a solid (bounce-back) and other rare nodes take these
+// out-of-line global-memory paths, so that their registers do not weigh on the
+// kernels' hot loops
+template <class S>
+__device__ __noinline__ typename Store<S>::real phi_node_cold(const InstDev *Ip, const PartDev *parts,
+                                                              const uint8_t *fli, const S *in, int n, uint8_t fl,
+                                                              int x, int y, int z)
+{
+    const InstDev &I = *Ip;
+    GlobalNbr nb;
+    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
+    nb.fli = fli;
+    return node_phi<S>(I, parts, nb, in, (int)I.N, n, fl, x, y, z);
+}
+
+template <class S>
+__device__ __noinline__ void collide_node_cold(const InstDev *Ip, const PartDev *parts, const uint8_t *fli,
+                                               const S *in, S *out, int n, uint8_t fl, int x, int y, int z,
+                                               typename Store<S>::real phi, typename Store<S>::real n0,
+                                               typename Store<S>::real n1, typename Store<S>::real n2,
+                                               typename Store<S>::real m, typename Store<S>::real kap,
+                                               typename Store<S>::real *U, long long Ntot, unsigned *status)
+{
+    using R = typename Store<S>::real;
+    const InstDev &I = *Ip;
+    GlobalNbr nb;
+    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
+    nb.fli = fli;
+    FluidPar<R> P;
+    load_par(I, P);
+    const R nn[3] = {n0, n1, n2};
+    const R gr[3] = {n0 * m, n1 * m, n2 * m};
+    R F[Q];
+    gather_F<S>(I, parts, nb, in, (int)I.N, n, fl, F, x, y, z);
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, (int)I.N, n, U, Ntot, status);
 }
 
 }  // namespace lbmg

@@ -81,9 +81,10 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// shared-memory stage: NPOP population strips of BUFW elements, then (EXT) the
-// normal n (3), |grad phi|_eps and curvature of the strip's nodes, then its
-// flags (from the 16-byte boundary below the first node)
+// shared-memory stage: NROWS population strips of BUFW elements (all 38 for
+// the order parameter, the 19 total offsets F for the collision), then (EXT)
+// the normal n (3), |grad phi|_eps, curvature and order parameter of the
+// strip's nodes, then its flags (from the 16-byte boundary below the first node)
 // MINB CTAs share an SM; the ring is as deep as their share of the 228 KB of
 // shared memory allows (2..8 stages)
 template <class S, bool EXT, int MINB>
@@ -91,8 +92,10 @@ struct StLayout {
     using R = typename Store<S>::real;
     static constexpr int A = StagedCfg<S>::A;
     static constexpr int BUFW = ST_SEGMAX + 2 * A;
-    static constexpr size_t POP = (size_t)NPOP * BUFW * sizeof(S);
-    static constexpr size_t EXTB = EXT ? (size_t)5 * ST_SEGMAX * sizeof(R) : 0;
+    static constexpr int NROWS = EXT ? Q : NPOP;
+    static constexpr int NEXT = EXT ? 6 : 0;
+    static constexpr size_t POP = (size_t)NROWS * BUFW * sizeof(S);
+    static constexpr size_t EXTB = (size_t)NEXT * ST_SEGMAX * sizeof(R);
     static constexpr size_t FLB = ST_SEGMAX + 32;
     static constexpr size_t STAGE = (POP + EXTB + FLB + 127) / 128 * 128;
     static constexpr size_t HEAD = 128;  // the NST mbarriers
@@ -102,6 +105,15 @@ struct StLayout {
     static_assert(NST >= 2, "two stages must fit");
     static constexpr size_t bytes() { return HEAD + NST * STAGE; }
 };
+
+// per-node arrays staged for the collision: n (3 components), |grad phi|_eps,
+// curvature, order parameter
+template <class R>
+__device__ __forceinline__ const R *ext_array(const Lattice &L, int e)
+{
+    if (e < 3) return (const R *)L.grad + (long long)e * L.Ntot;
+    return e == 3 ? (const R *)L.gmag : (e == 4 ? (const R *)L.kap : (const R *)L.phi);
+}
 
 struct StItem {
     int k;       // instance
@@ -161,11 +173,11 @@ __device__ void st_issue(const Lattice &L, const void *pop_in, const StItem &it,
     const long long fst = g0 & ~15ll, fen = (g0 + it.cnt + 15) & ~15ll;
     const unsigned flb = (unsigned)(fen - fst);
     const unsigned extb = EXT ? (unsigned)it.cnt * (unsigned)sizeof(R) : 0u;
-    if (lane == 0) mbar_arrive_expect_tx(bar, NPOP * popb + 5 * extb + flb);
+    if (lane == 0) mbar_arrive_expect_tx(bar, Ly::NROWS * popb + Ly::NEXT * extb + flb);
     __syncwarp();
-    constexpr int NC = NPOP + (EXT ? 5 : 0) + 1;
+    constexpr int NC = Ly::NROWS + Ly::NEXT + 1;
     for (int c = lane; c < NC; c += 32) {
-        if (c < NPOP) {
+        if (c < Ly::NROWS) {
             const int d = c < Q ? c : c - Q;
             const int zs = wrap1(it.z - cz(d), nz);
             const S *src = in + (long long)c * N + (long long)zs * ny * nx;
@@ -182,11 +194,10 @@ __device__ void st_issue(const Lattice &L, const void *pop_in, const StItem &it,
                 bulk_g2s(smem_addr(dst + (size_t)(lo - (it.x0 - A)) * sizeof(S)), src + (long long)ys * nx + lo,
                          popb, bar);
             }
-        } else if (EXT && c < NPOP + 5) {
-            const int e = c - NPOP;
-            const R *base = e < 3 ? (const R *)L.grad + (long long)e * L.Ntot
-                                  : (e == 3 ? (const R *)L.gmag : (const R *)L.kap);
-            bulk_g2s(smem_addr(stage + Ly::POP + (size_t)e * ST_SEGMAX * sizeof(R)), base + g0, extb, bar);
+        } else if (EXT && c < Ly::NROWS + Ly::NEXT) {
+            const int e = c - Ly::NROWS;
+            bulk_g2s(smem_addr(stage + Ly::POP + (size_t)e * ST_SEGMAX * sizeof(R)), ext_array<R>(L, e) + g0, extb,
+                     bar);
         } else {
             bulk_g2s(smem_addr(stage + Ly::POP + Ly::EXTB), L.flags + fst, flb, bar);
         }
@@ -215,7 +226,7 @@ __device__ __forceinline__ void st_issue_async(const Lattice &L, const void *pop
     const int rowch = (hi - lo) * (int)sizeof(S) / 16;  // 16-byte chunks per copied row
     const int dst0 = it.whole ? 0 : (lo - (it.x0 - A)) * (int)sizeof(S);
     const int rowb = nx * (int)sizeof(S);
-    for (int q = warp; q < NPOP; q += NW) {
+    for (int q = warp; q < Ly::NROWS; q += NW) {
         const int d = q < Q ? q : q - Q;
         const int zs = wrap1(it.z - cz(d), nz);
         const char *src = (const char *)(in + (long long)q * N + (long long)zs * ny * nx + lo);
@@ -227,9 +238,8 @@ __device__ __forceinline__ void st_issue_async(const Lattice &L, const void *pop
         }
     }
     const long long g0 = item_node0(I, it);
-    if (EXT && warp < 5) {
-        const R *base = warp < 3 ? (const R *)L.grad + (long long)warp * L.Ntot
-                                 : (warp == 3 ? (const R *)L.gmag : (const R *)L.kap);
+    if (EXT && warp < Ly::NEXT) {
+        const R *base = ext_array<R>(L, warp);
         const char *src = (const char *)(base + g0);
         const uint32_t dst = smem_addr(stage + Ly::POP + (size_t)warp * ST_SEGMAX * sizeof(R));
         const int nch = it.cnt * (int)sizeof(R) / 16;
@@ -364,42 +374,6 @@ __device__ __forceinline__ void st_pipeline_async(const Lattice &L, const void *
     cp_wait<0>();
 }
 
-// nodes next to a solid and the end nodes of a cut row take the global-memory
-// path; kept out of line so that their registers do not weigh on the hot loop
-template <class S>
-__device__ __noinline__ typename Store<S>::real phi_node_cold(const InstDev *Ip, const PartDev *parts,
-                                                              const uint8_t *fli, const S *in, int n, uint8_t fl,
-                                                              int x, int y, int z)
-{
-    const InstDev &I = *Ip;
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = fli;
-    return node_phi<S>(I, parts, nb, in, (int)I.N, n, fl, x, y, z);
-}
-
-template <class S>
-__device__ __noinline__ void collide_node_cold(const InstDev *Ip, const PartDev *parts, const uint8_t *fli,
-                                               const S *in, S *out, int n, uint8_t fl, int x, int y, int z,
-                                               typename Store<S>::real n0, typename Store<S>::real n1,
-                                               typename Store<S>::real n2, typename Store<S>::real m,
-                                               typename Store<S>::real kap, typename Store<S>::real *U,
-                                               long long Ntot, unsigned *status)
-{
-    using R = typename Store<S>::real;
-    const InstDev &I = *Ip;
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = fli;
-    FluidPar<R> P;
-    load_par(I, P);
-    const R nn[3] = {n0, n1, n2};
-    const R gr[3] = {n0 * m, n1 * m, n2 * m};
-    R F[Q], G[Q];
-    gather<S>(I, parts, nb, in, (int)I.N, n, fl, F, G, x, y, z);
-    collide_store<S>(P, F, G, gr, nn, kap, out, (int)I.N, n, U, Ntot, status);
-}
-
 }  // namespace
 
 // order parameter after streaming (same sums as node_phi)
@@ -477,21 +451,21 @@ __global__ void __launch_bounds__(ST_THREADS, MINB) k_collide_staged(Lattice L, 
             const R nn[3] = {se[j], se[ST_SEGMAX + j], se[2 * ST_SEGMAX + j]};
             const R m = se[3 * ST_SEGMAX + j];
             const R kap = se[4 * ST_SEGMAX + j];
+            const R phi = se[5 * ST_SEGMAX + j];
             const StSrc b = st_src<Ly::A>(it, nx, r, x);
             if ((fl & BOUND_BIT) || b.edge) {
-                collide_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, out, n, fl, x, y, z, nn[0], nn[1], nn[2],
-                                     m, kap, U, L.Ntot, L.status);
+                collide_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, out, n, fl, x, y, z, phi, nn[0], nn[1],
+                                     nn[2], m, kap, U, L.Ntot, L.status);
                 continue;
             }
             const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-            R F[Q], sG = 0;
+            R F[Q];
 #pragma unroll
             for (int i = 0; i < Q; i++) {
                 const int o = cx(i) == 1 ? b.bm : (cx(i) == -1 ? b.bp : b.b0);
                 F[i] = Store<S>::lds(sp + i * Ly::BUFW + o);
-                sG += wgt<R>(i) * Store<S>::lds(sp + (Q + i) * Ly::BUFW + o);
             }
-            collide_store_sg<S>(P, F, sG, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+            collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
         }
     };
     if constexpr (ASYNC) st_pipeline_async<S, true, MINB>(L, pop_in, n_items, body);
