@@ -200,14 +200,17 @@ long long lbm_num_nodes(const lbm_ctx *ctx, int inst);
  * taken so far, out[3] = sticky device status bits.  Synchronises. */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
 
-/* Launch-shape override of the four-kernel fluid form (block size in threads,
- * a multiple of 32 in [64, 256]); 0 restores the default.  Invalidates the
+/* Launch-shape override of the persistent fluid kernels: at most ctas_per_sm
+ * CTAs (of 256 threads) per SM, in [1, 8]; 0 (default) fills every SM to the
+ * occupancy each kernel allows.  Out of range -> LBM_ERR_ARG.  Invalidates the
  * captured step graph. */
-lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads);
+lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
 
 /* Fluid-update launch form (all forms compute the same update).
- * form = 0 (default), staged: five kernels per step (order parameter, solid
- *   phi, gradient, curvature, collision); the two kernels that stream the
+ * form = 2 (default), plain: five kernels per step (order parameter, solid
+ *   phi, gradient + wetting + normal, curvature, collision), one thread per
+ *   node with direct loads; tile must be 0.
+ * form = 0, staged: the same five kernels, but the two that stream the
  *   populations are persistent and bring each strip of x-rows into a ring of
  *   shared-memory stages with asynchronous copies.  tile selects the variant:
  *   0 16-byte cp.async copies by all threads, two CTAs per SM; 1 bulk copies
@@ -217,8 +220,6 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads);
  * form = 1, fused: one z-marching kernel per step; tile selects its column
  *   tile (0: 16x16, 1: 32x8); zchunk is the number of z-planes per work item
  *   (0: automatic, 32).
- * form = 2, plain: the five kernels with one thread per node and direct loads
- *   (tile must be 0).
  * Staged and plain agree bit for bit; fused agrees bit for bit in FP32 and to
  * rounding (FMA contraction) in FP64.  Invalid form, tile or zchunk -> LBM_ERR_ARG.
  * Invalidates the step graph. */

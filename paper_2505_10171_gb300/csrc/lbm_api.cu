@@ -20,8 +20,8 @@ struct lbm_ctx {
     std::vector<lbm_params> P;
     std::vector<InstDev> inst_h;
     InstDev *inst_d = nullptr;
-    long long Ntot = 0, n_blocks = 0;
-    int bt = 256;
+    long long Ntot = 0;
+    int cta_cap = 0;  // CTAs per SM of the persistent fluid kernels at most (0: occupancy)
     size_t elem = 8, real_sz = 8;
     uint8_t *flags = nullptr;
     void *pop[2] = {nullptr, nullptr};
@@ -53,8 +53,8 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
-    // fluid launch form: staged (default), fused z-marching or plain
-    FluidLaunch fz = {FORM_STAGED, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
+    // fluid launch form: plain (default), staged or fused z-marching
+    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, {0, 0, 0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
 };
 
@@ -82,7 +82,8 @@ static void plan_fused(lbm_ctx *c)
 static void plan_launch(lbm_ctx *c)
 {
     plan_fused(c);
-    plan_staged(c->inst_h, c->elem, &c->fz.st_items);
+    const bool aligned = plan_rows(c->inst_h, c->elem, &c->fz.rows);
+    c->fz.st_items = aligned ? c->fz.rows : 0;
     dispatch_grids(c);
 }
 
@@ -109,8 +110,7 @@ static Lattice make_lattice(const lbm_ctx *c)
     Lattice L;
     L.inst = c->inst_d;
     L.n_inst = c->n_inst;
-    L.n_blocks = c->n_blocks;
-    L.bt = c->bt;
+    L.n_items = c->fz.rows;
     L.flags = c->flags;
     L.pop[0] = c->pop[0];
     L.pop[1] = c->pop[1];
@@ -326,7 +326,8 @@ static void dispatch_grids(lbm_ctx *c)
 {
     dispatch(c->prec, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        staged_grids<S>(c->fz.st_grid_phi, c->fz.st_grid_collide);
+        plain_grids<S>(c->fz.grid_plain, c->cta_cap);
+        staged_grids<S>(c->fz.st_grid_phi, c->fz.st_grid_collide, c->cta_cap);
     });
 }
 
@@ -485,7 +486,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     ctx->real_sz = prec == LBM_FP64 ? 8 : 4;
     ctx->diag_step.assign(n_instances, -1);
     lbm_status st;
-    long long node_off = 0, blk = 0;
+    long long node_off = 0;
     bool any_u = false;
     for (int k = 0; k < n_instances; k++) {
         const lbm_params &p = params[k];
@@ -500,7 +501,6 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.nx = p.nx; I.ny = p.ny; I.nz = p.nz;
         I.N = (long long)p.nx * p.ny * p.nz;
         I.node_off = node_off;
-        I.blk_start = blk;
         I.wall_z0 = p.wall_z0;
         I.store_u = p.store_velocity ? 1 : 0;
         any_u |= I.store_u != 0;
@@ -533,10 +533,8 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.f_h_ib = (float)(0.5 / I.eta_b);
         ctx->inst_h.push_back(I);
         node_off += I.N;
-        blk += (I.N + ctx->bt - 1) / ctx->bt;
     }
     ctx->Ntot = node_off;
-    ctx->n_blocks = blk;
     plan_launch(ctx);
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
@@ -993,22 +991,13 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch(lbm_ctx *ctx, int block_threads)
+lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm)
 {
     if (!ctx) return LBM_ERR_ARG;
-    int bt = block_threads == 0 ? 256 : block_threads;
-    if (bt < 64 || bt > 256 || bt % 32) return fail(ctx, LBM_ERR_ARG, "block_threads must be a multiple of 32 in [64, 256]");
+    if (ctas_per_sm < 0 || ctas_per_sm > 8) return fail(ctx, LBM_ERR_ARG, "ctas_per_sm must be in [0, 8]");
     CU(cudaStreamSynchronize(ctx->stream));
-    ctx->bt = bt;
-    long long blk = 0;
-    for (auto &I : ctx->inst_h) {
-        I.blk_start = blk;
-        blk += (I.N + bt - 1) / bt;
-    }
-    ctx->n_blocks = blk;
-    CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,
-                       ctx->stream));
-    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->cta_cap = ctas_per_sm;
+    dispatch_grids(ctx);
     drop_graph(ctx);
     return LBM_OK;
 }

@@ -7,11 +7,13 @@
 // in its two-relaxation-time form -> recolouring -> write.
 //
 // Three launch forms run the per-node device functions of lbm_node.cuh:
-//  * staged (default): k_phi_staged, k_solidphi, k_grad, k_curv,
-//    k_collide_staged; the two population-streaming kernels bring their
-//    inputs into shared memory with bulk asynchronous copies (lbm_staged.cu).
-//  * plain: the same five kernels with one thread per node and direct global
-//    loads; used where an instance's x-rows are not whole 16-byte units.
+//  * plain (default): k_phi, k_solidphi, k_grad, k_curv, k_collide, one thread
+//    per node with direct global loads.  The collision pulls only the 19 total
+//    offsets F: the colour offsets enter it only through phi, which k_phi
+//    stores.
+//  * staged: the same kernels, with k_phi and k_collide replaced by persistent
+//    kernels that bring their inputs into shared memory with asynchronous
+//    copies (lbm_staged.cu).
 //  * k_fused: one kernel per step.  A block owns a TX x TY column tile and a
 //    chunk of z-planes and marches z: the order parameter of plane z+3 is
 //    gathered into a shared-memory ring (with a 3-node halo, enough for the
@@ -28,10 +30,10 @@
 // CTAs of 256 threads per SM the single-precision order-parameter and
 // collision kernels are compiled for (register budget 65536 / (256 x this))
 #ifndef LBM_PHI_MINB
-#define LBM_PHI_MINB 2
+#define LBM_PHI_MINB 4
 #endif
 #ifndef LBM_COLLIDE_MINB
-#define LBM_COLLIDE_MINB 2
+#define LBM_COLLIDE_MINB 4
 #endif
 
 namespace lbmg {
@@ -39,17 +41,6 @@ namespace lbmg {
 // ---------------------------------------------------------------------------
 // four-kernel form over all nodes (and the same bodies over particle regions)
 // ---------------------------------------------------------------------------
-#define LBM_NODE_PROLOGUE                                                                   \
-    const long long blk = blockIdx.x;                                                        \
-    const int k_inst = find_inst(L.inst, L.n_inst, blk);                                     \
-    const InstDev &I = L.inst[k_inst];                                                       \
-    const long long n_ = (blk - I.blk_start) * (long long)blockDim.x + threadIdx.x;          \
-    if (n_ >= I.N) return;                                                                   \
-    const int n = (int)n_;                                                                   \
-    const int x = n % I.nx;                                                                  \
-    const int y = (n / I.nx) % I.ny;                                                         \
-    const int z = n / (I.nx * I.ny);
-
 // region of particle blockIdx.y: nodes of a cube of side `side` around it
 #define LBM_REGION_PROLOGUE                                                                  \
     const PartDev &P0 = L.parts[blockIdx.y];                                                 \
@@ -120,24 +111,21 @@ __device__ __forceinline__ void grad_body(const Lattice &L, const InstDev &I, in
 }
 
 template <class S>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
+__global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
 {
-    LBM_NODE_PROLOGUE
-    phi_body<S>(L, I, cur, n, x, y, z);
+    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
 }
 
 template <class R>
-__global__ void k_solidphi(Lattice L)
+__global__ void __launch_bounds__(ROW_NODES) k_solidphi(Lattice L)
 {
-    LBM_NODE_PROLOGUE
-    solidphi_body<R>(L, I, n, x, y, z);
+    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { solidphi_body<R>(L, I, n, x, y, z); });
 }
 
 template <class R>
-__global__ void k_grad(Lattice L)
+__global__ void __launch_bounds__(ROW_NODES) k_grad(Lattice L)
 {
-    LBM_NODE_PROLOGUE
-    grad_body<R>(L, I, n, x, y, z);
+    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { grad_body<R>(L, I, n, x, y, z); });
 }
 
 template <class S>
@@ -164,9 +152,8 @@ __global__ void __launch_bounds__(PART_THREADS) k_grad_region(Lattice L, int sid
 // curvature of every fluid node from the stored normals (a solid neighbour
 // contributes the node's own normal)
 template <class R>
-__global__ void k_curv(Lattice L)
+__device__ __forceinline__ void curv_body(const Lattice &L, const InstDev &I, int n, int x, int y, int z)
 {
-    LBM_NODE_PROLOGUE
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID) return;
@@ -183,11 +170,16 @@ __global__ void k_curv(Lattice L)
     ((R *)L.kap)[g] = curvature<R>(nf);
 }
 
+template <class R>
+__global__ void __launch_bounds__(ROW_NODES) k_curv(Lattice L)
+{
+    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { curv_body<R>(L, I, n, x, y, z); });
+}
+
 template <class S>
-__global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_collide(Lattice L, int cur)
+__device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
 {
     using R = typename Store<S>::real;
-    LBM_NODE_PROLOGUE
     const int N = (int)I.N;
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
@@ -218,6 +210,12 @@ __global__ void __launch_bounds__(256, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
     collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+}
+
+template <class S>
+__global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_collide(Lattice L, int cur)
+{
+    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { collide_body<S>(L, I, cur, n, x, y, z); });
 }
 
 // tile shapes of the fused kernel: 0 -> 16 x 16, 1 -> 32 x 8
@@ -251,28 +249,40 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     }
     // staged form where every instance's rows are whole 16-byte units, plain otherwise
     const bool staged = fz.form == FORM_STAGED && fz.st_items > 0;
-    dim3 grid((unsigned)L.n_blocks), block(L.bt);
+    auto grid = [&](int k) { return (unsigned)std::min<long long>(fz.grid_plain[k], fz.rows); };
     mk(STAGE_PHI, 0);
     if (staged) launch_staged_phi<S>(L, cur, fz, st);
-    else k_phi<S><<<grid, block, 0, st>>>(L, cur);
+    else k_phi<S><<<grid(0), ROW_NODES, 0, st>>>(L, cur);
     mk(STAGE_PHI, 1);
     mk(STAGE_SOLIDPHI, 0);
-    k_solidphi<R><<<grid, block, 0, st>>>(L);
+    k_solidphi<R><<<grid(1), ROW_NODES, 0, st>>>(L);
     mk(STAGE_SOLIDPHI, 1);
     mk(STAGE_GRAD, 0);
-    k_grad<R><<<grid, block, 0, st>>>(L);
+    k_grad<R><<<grid(2), ROW_NODES, 0, st>>>(L);
     mk(STAGE_GRAD, 1);
     mk(STAGE_CURV, 0);
-    k_curv<R><<<grid, block, 0, st>>>(L);
+    k_curv<R><<<grid(3), ROW_NODES, 0, st>>>(L);
     mk(STAGE_CURV, 1);
     mk(STAGE_COLLIDE, 0);
     if (staged) launch_staged_collide<S>(L, cur, fz, st);
-    else k_collide<S><<<grid, block, 0, st>>>(L, cur);
+    else k_collide<S><<<grid(4), ROW_NODES, 0, st>>>(L, cur);
     mk(STAGE_COLLIDE, 1);
     *launches += 5;
 }
 
+template <class S>
+void plain_grids(int *g, int cap)
+{
+    using R = typename Store<S>::real;
+    g[0] = persistent_grid(k_phi<S>, 0, cap);
+    g[1] = persistent_grid(k_solidphi<R>, 0, cap);
+    g[2] = persistent_grid(k_grad<R>, 0, cap);
+    g[3] = persistent_grid(k_curv<R>, 0, cap);
+    g[4] = persistent_grid(k_collide<S>, 0, cap);
+}
+
 #define INST(S)                                                                                                   \
+    template void plain_grids<S>(int *, int);                                                                     \
     template void launch_fluid_step<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &,            \
                                        const FluidLaunch &);
 INST(double)

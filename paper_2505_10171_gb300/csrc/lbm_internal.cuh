@@ -60,7 +60,6 @@ struct InstDev {
     int nx, ny, nz, np;
     long long N;         // nodes of the instance
     long long node_off;  // first node in the per-node arrays
-    long long blk_start; // first fluid block of the instance
     int part_off;        // first particle of the instance
     int hist_off;        // first pair-history record of the instance
     int crec_off;        // first DEM contact record of the instance
@@ -121,8 +120,7 @@ struct PartDev {
 struct Lattice {
     const InstDev *inst;
     int n_inst;
-    long long n_blocks;
-    int bt;              // fluid block threads
+    long long n_items;   // row-strip work items of all instances
     uint8_t *flags;
     void *pop[2];
     void *phi;           // [Ntot] real
@@ -176,17 +174,6 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }  // shared memory
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
-
-__device__ __forceinline__ int find_inst(const InstDev *I, int n, long long blk)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (I[mid].blk_start <= blk) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 // minimum-image displacement on a periodic axis of n nodes (|d| < 3n/2): the
 // same value as d - n floor(d/n + 1/2) without a double-precision division
@@ -424,6 +411,94 @@ __device__ __forceinline__ void wetting_rotate(R *g, const R *ns, R cth, R sth)
     for (int a = 0; a < 3; a++) g[a] = -gm * nc[a];
 }
 
+// ---------------------------------------------------------------------------
+// row-strip work items (all per-node kernels): a strip of one z-plane made of
+// st_rows whole x-rows (at most ROW_NODES nodes), or one segment of a longer row
+// ---------------------------------------------------------------------------
+constexpr int ROW_NODES = 256;  // nodes per work item at most = threads per CTA
+
+struct StItem {
+    int k;       // instance
+    int z, y0;   // plane and first row
+    int nrows;   // rows (whole-row items)
+    int x0, cnt; // first x and number of nodes
+    bool whole;
+};
+
+__device__ __forceinline__ void st_item(const Lattice &L, long long item, StItem &it)
+{
+    int lo = 0, hi = L.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.inst[mid].st_item_start <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const InstDev &I = L.inst[lo];
+    const int loc = (int)(item - I.st_item_start);  // < 2^31: rows of one instance
+    const int per_plane = I.st_ygroups * I.st_nseg;
+    it.k = lo;
+    it.z = loc / per_plane;
+    const int r = loc - it.z * per_plane;
+    const int yg = r / I.st_nseg, sg = r - yg * I.st_nseg;
+    it.y0 = yg * I.st_rows;
+    it.whole = I.st_nseg == 1;
+    it.nrows = min(I.st_rows, I.ny - it.y0);
+    it.x0 = sg * I.st_seg;
+    it.cnt = it.whole ? it.nrows * I.nx : min(I.st_seg, I.nx - it.x0);
+}
+
+__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// first node of the item in the per-node arrays and the 16-byte-aligned start
+// of its flag copy
+__device__ __forceinline__ long long item_node0(const InstDev &I, const StItem &it)
+{
+    return I.node_off + ((long long)it.z * I.ny + it.y0) * I.nx + it.x0;
+}
+
+// node j of a work item
+__device__ __forceinline__ void item_node(const StItem &it, int nx, int j, int *x, int *y)
+{
+    int r = 0, xx = it.x0 + j;
+    if (it.nrows > 1) {
+        r = j / nx;
+        xx = j - r * nx;
+    }
+    *x = xx;
+    *y = it.y0 + r;
+}
+
+// persistent loop over the work items: f(I, n, x, y, z) for every node
+template <class F>
+__device__ __forceinline__ void for_each_node(const Lattice &L, F &&f)
+{
+    for (long long item = blockIdx.x; item < L.n_items; item += gridDim.x) {
+        StItem it;
+        st_item(L, item, it);
+        const int j = threadIdx.x;
+        if (j >= it.cnt) continue;
+        const InstDev &I = L.inst[it.k];
+        int x, y;
+        item_node(it, I.nx, j, &x, &y);
+        f(I, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
+    }
+}
+
+// grid of a persistent kernel of ROW_NODES threads: every SM filled to the
+// occupancy the kernel allows, capped at cap CTAs per SM when cap > 0
+template <class K>
+int persistent_grid(K kernel, size_t smem, int cap)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ROW_NODES, smem);
+    if (per_sm < 1) per_sm = 1;
+    if (cap > 0 && per_sm > cap) per_sm = cap;
+    return sms * per_sm;
+}
+
 // kernel stages, in launch order within a step (for per-kernel timing)
 enum Stage {
     STAGE_PHI = 0, STAGE_SOLIDPHI, STAGE_GRAD, STAGE_COLLIDE, STAGE_MEM, STAGE_CAPILLARY, STAGE_DEM,
@@ -446,22 +521,28 @@ struct FluidLaunch {
     int form;           // FORM_STAGED, FORM_FUSED or FORM_PLAIN
     int tile;           // fused tile shape index (see lbm_fluid.cu)
     long long items;    // fused work items (all instances)
-    long long st_items; // staged work items (all instances); 0: staged form unavailable
+    long long rows;     // row-strip work items (all instances)
+    long long st_items; // the same when the staged form is available, else 0
+    int grid_plain[5];  // persistent grids: phi, solid phi, grad, curvature, collision
     // persistent grids of the staged kernels, per variant (see lbm_staged.cu)
     int st_grid_phi[3], st_grid_collide[3];
 };
 // staged kernels: threads per CTA and nodes per work item at most
 constexpr int ST_THREADS = 256;
 constexpr int ST_SEGMAX = 256;
+static_assert(ST_SEGMAX == ROW_NODES && ST_THREADS == ROW_NODES, "one node per thread per item");
 template <class S>
 struct StagedCfg {
     static constexpr int A = 16 / (int)sizeof(S);  // elements per 16 bytes
 };
-// plan the staged work items of every instance (false if an instance's nx is
-// not a multiple of 16 bytes of storage, which the bulk copies need)
-bool plan_staged(std::vector<InstDev> &inst, size_t elem, long long *items);
+// plan the row-strip work items of every instance; *items = their number,
+// returns false if an instance's rows are not whole 16-byte units of storage
+// (which the staged copies need)
+bool plan_rows(std::vector<InstDev> &inst, size_t elem, long long *items);
 template <class S>
-void staged_grids(int *grid_phi, int *grid_collide);  // arrays of 3 (variants)
+void plain_grids(int *grid, int cap);  // [5], see FluidLaunch::grid_plain
+template <class S>
+void staged_grids(int *grid_phi, int *grid_collide, int cap);  // arrays of 3 (variants)
 template <class S>
 void launch_staged_phi(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
 template <class S>

@@ -115,45 +115,6 @@ __device__ __forceinline__ const R *ext_array(const Lattice &L, int e)
     return e == 3 ? (const R *)L.gmag : (e == 4 ? (const R *)L.kap : (const R *)L.phi);
 }
 
-struct StItem {
-    int k;       // instance
-    int z, y0;   // plane and first row
-    int nrows;   // rows (whole-row items)
-    int x0, cnt; // first x and number of nodes
-    bool whole;
-};
-
-__device__ __forceinline__ void st_item(const Lattice &L, long long item, StItem &it)
-{
-    int lo = 0, hi = L.n_inst - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (L.inst[mid].st_item_start <= item) lo = mid;
-        else hi = mid - 1;
-    }
-    const InstDev &I = L.inst[lo];
-    const long long loc = item - I.st_item_start;
-    const int per_plane = I.st_ygroups * I.st_nseg;
-    it.k = lo;
-    it.z = (int)(loc / per_plane);
-    const int r = (int)(loc - (long long)it.z * per_plane);
-    const int yg = r / I.st_nseg, sg = r - yg * I.st_nseg;
-    it.y0 = yg * I.st_rows;
-    it.whole = I.st_nseg == 1;
-    it.nrows = min(I.st_rows, I.ny - it.y0);
-    it.x0 = sg * I.st_seg;
-    it.cnt = it.whole ? it.nrows * I.nx : min(I.st_seg, I.nx - it.x0);
-}
-
-__device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
-
-// first node of the item in the per-node arrays and the 16-byte-aligned start
-// of its flag copy
-__device__ __forceinline__ long long item_node0(const InstDev &I, const StItem &it)
-{
-    return I.node_off + ((long long)it.z * I.ny + it.y0) * I.nx + it.x0;
-}
-
 // issue the copies of one item into a stage (all 32 lanes of warp 0)
 template <class S, bool EXT, int MINB>
 __device__ void st_issue(const Lattice &L, const void *pop_in, const StItem &it, unsigned char *stage, uint32_t bar,
@@ -475,7 +436,7 @@ __global__ void __launch_bounds__(ST_THREADS, MINB) k_collide_staged(Lattice L, 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-bool plan_staged(std::vector<InstDev> &inst, size_t elem, long long *items)
+bool plan_rows(std::vector<InstDev> &inst, size_t elem, long long *items)
 {
     const int A = 16 / (int)elem;
     long long total = 0;
@@ -498,20 +459,10 @@ bool plan_staged(std::vector<InstDev> &inst, size_t elem, long long *items)
         I.st_item_start = total;
         total += (long long)I.nz * I.st_ygroups * I.st_nseg;
     }
-    *items = ok ? total : 0;
+    *items = total;
     return ok;
 }
 
-template <class S, class K>
-static int persistent_grid(K kernel, size_t smem)
-{
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ST_THREADS, smem);
-    return std::max(1, sms * std::max(per_sm, 1));
-}
 
 // staged variants: 0 cp.async copies, two CTAs per SM; 1 bulk copies, two
 // CTAs per SM; 2 cp.async copies, one CTA per SM with a deeper ring.  FP64
@@ -529,20 +480,21 @@ struct StVariant {
 };
 
 template <class S, int V>
-static void grids_v(int *grid_phi, int *grid_collide)
+static void grids_v(int *grid_phi, int *grid_collide, int cap)
 {
     using Vt = StVariant<S, V>;
-    grid_phi[V] = persistent_grid<S>(k_phi_staged<S, Vt::MINB, Vt::ASYNC>, StLayout<S, false, Vt::MINB>::bytes());
+    grid_phi[V] =
+        persistent_grid(k_phi_staged<S, Vt::MINB, Vt::ASYNC>, StLayout<S, false, Vt::MINB>::bytes(), cap);
     grid_collide[V] =
-        persistent_grid<S>(k_collide_staged<S, Vt::MINB, Vt::ASYNC>, StLayout<S, true, Vt::MINB>::bytes());
+        persistent_grid(k_collide_staged<S, Vt::MINB, Vt::ASYNC>, StLayout<S, true, Vt::MINB>::bytes(), cap);
 }
 
 template <class S>
-void staged_grids(int *grid_phi, int *grid_collide)
+void staged_grids(int *grid_phi, int *grid_collide, int cap)
 {
-    grids_v<S, 0>(grid_phi, grid_collide);
-    grids_v<S, 1>(grid_phi, grid_collide);
-    grids_v<S, 2>(grid_phi, grid_collide);
+    grids_v<S, 0>(grid_phi, grid_collide, cap);
+    grids_v<S, 1>(grid_phi, grid_collide, cap);
+    grids_v<S, 2>(grid_phi, grid_collide, cap);
 }
 
 template <class S, int V>
@@ -581,7 +533,7 @@ void launch_staged_collide(const Lattice &L, int cur, const FluidLaunch &fz, cud
 }
 
 #define INST(S)                                                                                   \
-    template void staged_grids<S>(int *, int *);                                                  \
+    template void staged_grids<S>(int *, int *, int);                                             \
     template void launch_staged_phi<S>(const Lattice &, int, const FluidLaunch &, cudaStream_t); \
     template void launch_staged_collide<S>(const Lattice &, int, const FluidLaunch &, cudaStream_t);
 INST(double)

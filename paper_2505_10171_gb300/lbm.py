@@ -249,10 +249,10 @@ class Context:
         self._check(self.L.lbm_diagnostics(self.h, inst, _dp(out)))
         return out
 
-    def lbm_set_launch(self, block_threads):
-        self._check(self.L.lbm_set_launch(self.h, int(block_threads)))
+    def lbm_set_launch(self, ctas_per_sm=0):
+        self._check(self.L.lbm_set_launch(self.h, int(ctas_per_sm)))
 
-    def lbm_set_fluid_kernel(self, form=FORM_STAGED, tile=0, zchunk=0):
+    def lbm_set_fluid_kernel(self, form=FORM_PLAIN, tile=0, zchunk=0):
         self._check(self.L.lbm_set_fluid_kernel(self.h, int(form), int(tile), int(zchunk)))
 
     def lbm_fluid_form_in_use(self):
