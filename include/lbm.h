@@ -200,10 +200,10 @@ long long lbm_num_nodes(const lbm_ctx *ctx, int inst);
  * taken so far, out[3] = sticky device status bits.  Synchronises. */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
 
-/* Launch-shape override of the persistent fluid kernels: at most ctas_per_sm
- * CTAs (of 256 threads) per SM, in [1, 8]; 0 (default) fills every SM to the
- * occupancy each kernel allows.  Out of range -> LBM_ERR_ARG.  Invalidates the
- * captured step graph. */
+/* Launch-shape override of the persistent kernels of the staged form: at most
+ * ctas_per_sm CTAs (of 256 threads) per SM, in [1, 8]; 0 (default) fills every
+ * SM to the occupancy each kernel allows.  Out of range -> LBM_ERR_ARG.
+ * Invalidates the captured step graph. */
 lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
 
 /* Fluid-update launch form (all forms compute the same update).

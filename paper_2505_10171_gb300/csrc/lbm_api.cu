@@ -21,7 +21,7 @@ struct lbm_ctx {
     std::vector<InstDev> inst_h;
     InstDev *inst_d = nullptr;
     long long Ntot = 0;
-    int cta_cap = 0;  // CTAs per SM of the persistent fluid kernels at most (0: occupancy)
+    int cta_cap = 0;  // CTAs per SM of the persistent staged kernels at most (0: occupancy)
     size_t elem = 8, real_sz = 8;
     uint8_t *flags = nullptr;
     void *pop[2] = {nullptr, nullptr};
@@ -54,7 +54,7 @@ struct lbm_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
     // fluid launch form: plain (default), staged or fused z-marching
-    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, {0, 0, 0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
 };
 
@@ -326,7 +326,6 @@ static void dispatch_grids(lbm_ctx *c)
 {
     dispatch(c->prec, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        plain_grids<S>(c->fz.grid_plain, c->cta_cap);
         staged_grids<S>(c->fz.st_grid_phi, c->fz.st_grid_collide, c->cta_cap);
     });
 }

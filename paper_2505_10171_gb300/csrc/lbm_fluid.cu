@@ -113,19 +113,19 @@ __device__ __forceinline__ void grad_body(const Lattice &L, const InstDev &I, in
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
 {
-    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
 }
 
 template <class R>
 __global__ void __launch_bounds__(ROW_NODES) k_solidphi(Lattice L)
 {
-    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { solidphi_body<R>(L, I, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { solidphi_body<R>(L, I, n, x, y, z); });
 }
 
 template <class R>
 __global__ void __launch_bounds__(ROW_NODES) k_grad(Lattice L)
 {
-    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { grad_body<R>(L, I, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { grad_body<R>(L, I, n, x, y, z); });
 }
 
 template <class S>
@@ -173,7 +173,7 @@ __device__ __forceinline__ void curv_body(const Lattice &L, const InstDev &I, in
 template <class R>
 __global__ void __launch_bounds__(ROW_NODES) k_curv(Lattice L)
 {
-    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { curv_body<R>(L, I, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { curv_body<R>(L, I, n, x, y, z); });
 }
 
 template <class S>
@@ -215,7 +215,7 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_collide(Lattice L, int cur)
 {
-    for_each_node(L, [&](const InstDev &I, int n, int x, int y, int z) { collide_body<S>(L, I, cur, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { collide_body<S>(L, I, cur, n, x, y, z); });
 }
 
 // tile shapes of the fused kernel: 0 -> 16 x 16, 1 -> 32 x 8
@@ -249,40 +249,29 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     }
     // staged form where every instance's rows are whole 16-byte units, plain otherwise
     const bool staged = fz.form == FORM_STAGED && fz.st_items > 0;
-    auto grid = [&](int k) { return (unsigned)std::min<long long>(fz.grid_plain[k], fz.rows); };
+    const dim3 grid((unsigned)fz.rows);  // one CTA per row-strip work item
     mk(STAGE_PHI, 0);
     if (staged) launch_staged_phi<S>(L, cur, fz, st);
-    else k_phi<S><<<grid(0), ROW_NODES, 0, st>>>(L, cur);
+    else k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
     mk(STAGE_PHI, 1);
     mk(STAGE_SOLIDPHI, 0);
-    k_solidphi<R><<<grid(1), ROW_NODES, 0, st>>>(L);
+    k_solidphi<R><<<grid, ROW_NODES, 0, st>>>(L);
     mk(STAGE_SOLIDPHI, 1);
     mk(STAGE_GRAD, 0);
-    k_grad<R><<<grid(2), ROW_NODES, 0, st>>>(L);
+    k_grad<R><<<grid, ROW_NODES, 0, st>>>(L);
     mk(STAGE_GRAD, 1);
     mk(STAGE_CURV, 0);
-    k_curv<R><<<grid(3), ROW_NODES, 0, st>>>(L);
+    k_curv<R><<<grid, ROW_NODES, 0, st>>>(L);
     mk(STAGE_CURV, 1);
     mk(STAGE_COLLIDE, 0);
     if (staged) launch_staged_collide<S>(L, cur, fz, st);
-    else k_collide<S><<<grid(4), ROW_NODES, 0, st>>>(L, cur);
+    else k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
     mk(STAGE_COLLIDE, 1);
     *launches += 5;
 }
 
-template <class S>
-void plain_grids(int *g, int cap)
-{
-    using R = typename Store<S>::real;
-    g[0] = persistent_grid(k_phi<S>, 0, cap);
-    g[1] = persistent_grid(k_solidphi<R>, 0, cap);
-    g[2] = persistent_grid(k_grad<R>, 0, cap);
-    g[3] = persistent_grid(k_curv<R>, 0, cap);
-    g[4] = persistent_grid(k_collide<S>, 0, cap);
-}
 
 #define INST(S)                                                                                                   \
-    template void plain_grids<S>(int *, int);                                                                     \
     template void launch_fluid_step<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &,            \
                                        const FluidLaunch &);
 INST(double)

@@ -468,20 +468,20 @@ __device__ __forceinline__ void item_node(const StItem &it, int nx, int j, int *
     *y = it.y0 + r;
 }
 
-// persistent loop over the work items: f(I, n, x, y, z) for every node
+// one CTA per work item, launched in item order (so that the CTAs in flight
+// cover a contiguous band of rows and the neighbour rows they share stay in
+// L2): f(I, n, x, y, z) for the CTA's nodes
 template <class F>
-__device__ __forceinline__ void for_each_node(const Lattice &L, F &&f)
+__device__ __forceinline__ void for_item_nodes(const Lattice &L, F &&f)
 {
-    for (long long item = blockIdx.x; item < L.n_items; item += gridDim.x) {
-        StItem it;
-        st_item(L, item, it);
-        const int j = threadIdx.x;
-        if (j >= it.cnt) continue;
-        const InstDev &I = L.inst[it.k];
-        int x, y;
-        item_node(it, I.nx, j, &x, &y);
-        f(I, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
-    }
+    StItem it;
+    st_item(L, blockIdx.x, it);
+    const int j = threadIdx.x;
+    if (j >= it.cnt) return;
+    const InstDev &I = L.inst[it.k];
+    int x, y;
+    item_node(it, I.nx, j, &x, &y);
+    f(I, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
 }
 
 // grid of a persistent kernel of ROW_NODES threads: every SM filled to the
@@ -521,9 +521,8 @@ struct FluidLaunch {
     int form;           // FORM_STAGED, FORM_FUSED or FORM_PLAIN
     int tile;           // fused tile shape index (see lbm_fluid.cu)
     long long items;    // fused work items (all instances)
-    long long rows;     // row-strip work items (all instances)
+    long long rows;     // row-strip work items (all instances): CTAs of each plain kernel
     long long st_items; // the same when the staged form is available, else 0
-    int grid_plain[5];  // persistent grids: phi, solid phi, grad, curvature, collision
     // persistent grids of the staged kernels, per variant (see lbm_staged.cu)
     int st_grid_phi[3], st_grid_collide[3];
 };
@@ -539,8 +538,6 @@ struct StagedCfg {
 // returns false if an instance's rows are not whole 16-byte units of storage
 // (which the staged copies need)
 bool plan_rows(std::vector<InstDev> &inst, size_t elem, long long *items);
-template <class S>
-void plain_grids(int *grid, int cap);  // [5], see FluidLaunch::grid_plain
 template <class S>
 void staged_grids(int *grid_phi, int *grid_collide, int cap);  // arrays of 3 (variants)
 template <class S>
