@@ -59,17 +59,15 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     using R = typename Store<S>::real;
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
-    if ((fl & OWNER_MASK) != OWN_FLUID) return;
     const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
-    R v;
-    if (fl & BOUND_BIT) {
-        v = phi_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, n, fl, x, y, z);
-    } else {
-        GlobalNbr nb;
-        nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-        nb.fli = L.flags + I.node_off;
-        v = phi_fluid<S>(nb, in, (int)I.N);
-    }
+    // the sums of a node without solid neighbours are formed before the flag
+    // is tested (every neighbour address is valid), so that the 38 loads travel
+    // with the flag load instead of after it
+    Nbr nb;
+    nb.init(x, y, z, I.nx, I.ny, I.nz);
+    R v = phi_fluid<S>(nb, in, (int)I.N);
+    if ((fl & OWNER_MASK) != OWN_FLUID) return;
+    if (fl & BOUND_BIT) v = phi_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, n, fl, x, y, z);
     ((R *)L.phi)[g] = v;
 }
 
@@ -92,16 +90,17 @@ __device__ __forceinline__ void grad_body(const Lattice &L, const InstDev &I, in
 {
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
-    if ((fl & OWNER_MASK) != OWN_FLUID) return;
     GlobalNbr nb;
     nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
     nb.fli = L.flags + I.node_off;
-    FluidPar<R> P;
-    load_par(I, P);
     const R *ph = (const R *)L.phi + I.node_off;
     auto phi_of = [&](int dx, int dy, int dz) { return ph[nb.idx(dx, dy, dz)]; };
     R gr[3], nn[3];
-    grad_node<R>(I, L.parts, nb, phi_of, ph[n], fl, P.wet_max, x, y, z, gr);
+    grad_sum<R>(phi_of, gr);  // loads issued before the flag is tested
+    if ((fl & OWNER_MASK) != OWN_FLUID) return;
+    FluidPar<R> P;
+    load_par(I, P);
+    grad_wet<R>(I, L.parts, nb, ph[n], fl, P.wet_max, x, y, z, gr);
     const R m = reg_normal(gr, P.eps2, nn);
     R *Nn = (R *)L.grad;
     Nn[g] = nn[0];
@@ -156,18 +155,20 @@ __device__ __forceinline__ void curv_body(const Lattice &L, const InstDev &I, in
 {
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
-    if ((fl & OWNER_MASK) != OWN_FLUID) return;
     GlobalNbr nb;
     nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
     nb.fli = L.flags + I.node_off;
     const R *Nn = (const R *)L.grad + I.node_off;
     const long long Nt = L.Ntot;
-    const bool bnd = fl & BOUND_BIT;
-    auto nf = [&](int dx, int dy, int dz, int a) {
-        if (bnd && nb.own(dx, dy, dz) != OWN_FLUID) return Nn[a * Nt + n];
-        return Nn[a * Nt + nb.idx(dx, dy, dz)];
-    };
-    ((R *)L.kap)[g] = curvature<R>(nf);
+    // all-fluid neighbourhood first (loads issued with the flag load)
+    R kap = curvature<R>([&](int dx, int dy, int dz, int a) { return Nn[a * Nt + nb.idx(dx, dy, dz)]; });
+    if ((fl & OWNER_MASK) != OWN_FLUID) return;
+    if (fl & BOUND_BIT)
+        kap = curvature<R>([&](int dx, int dy, int dz, int a) {
+            if (nb.own(dx, dy, dz) != OWN_FLUID) return Nn[a * Nt + n];
+            return Nn[a * Nt + nb.idx(dx, dy, dz)];
+        });
+    ((R *)L.kap)[g] = kap;
 }
 
 template <class R>
@@ -182,30 +183,31 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     using R = typename Store<S>::real;
     const int N = (int)I.N;
     const long long g = I.node_off + n;
-    const uint8_t fl = L.flags[g];
-    R *U = I.store_u ? (R *)L.u + I.node_off : nullptr;
-    if ((fl & OWNER_MASK) != OWN_FLUID) {
-        if (U) { U[n] = 0; U[L.Ntot + n] = 0; U[2 * L.Ntot + n] = 0; }
-        return;
-    }
     const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
     S *out = (S *)L.pop[cur ^ 1] + NPOP * I.node_off;
+    // every load of an interior fluid node is issued before the flag is tested
+    const uint8_t fl = L.flags[g];
     const R *Nn = (const R *)L.grad + I.node_off;
     const long long Nt = L.Ntot;
     const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
     const R m = ((const R *)L.gmag)[g];
     const R kap = ((const R *)L.kap)[g];
     const R phi = ((const R *)L.phi)[g];
-    if (fl & BOUND_BIT) {
-        collide_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, out, n, fl, x, y, z, phi, nn[0], nn[1], nn[2], m,
-                             kap, U, L.Ntot, L.status);
-        return;
-    }
     Nbr nb;
     nb.init(x, y, z, I.nx, I.ny, I.nz);
     R F[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) F[i] = Store<S>::ld(in + i * N + nb.at(-cx(i), -cy(i), -cz(i)));
+    R *U = I.store_u ? (R *)L.u + I.node_off : nullptr;
+    if ((fl & OWNER_MASK) != OWN_FLUID) {
+        if (U) { U[n] = 0; U[L.Ntot + n] = 0; U[2 * L.Ntot + n] = 0; }
+        return;
+    }
+    if (fl & BOUND_BIT) {
+        collide_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, out, n, fl, x, y, z, phi, nn[0], nn[1], nn[2], m,
+                             kap, U, L.Ntot, L.status);
+        return;
+    }
     FluidPar<R> P;
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};

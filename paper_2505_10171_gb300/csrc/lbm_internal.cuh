@@ -196,6 +196,7 @@ struct Nbr {
         ZO[0] = (z == 0 ? nz_ - 1 : z - 1) * nxy; ZO[1] = z * nxy; ZO[2] = (z == nz_ - 1 ? 0 : z + 1) * nxy;
     }
     __device__ __forceinline__ int at(int dx, int dy, int dz) const { return ZO[dz + 1] + YO[dy + 1] + X[dx + 1]; }
+    __device__ __forceinline__ int idx(int dx, int dy, int dz) const { return at(dx, dy, dz); }
 };
 
 // reciprocal and inverse square root: IEEE for double, the fast single-precision

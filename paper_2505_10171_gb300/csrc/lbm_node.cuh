@@ -76,11 +76,9 @@ __device__ __forceinline__ bool solid_normal(const InstDev &I, const PartDev *pa
     return true;
 }
 
-// grad(phi) = 3 sum_i w_i c_i phi(x + c_i) with the wetting rotation at
-// boundary nodes inside the interface
-template <class R, class A, class PhiF>
-__device__ __forceinline__ void grad_node(const InstDev &I, const PartDev *parts, const A &nbr, const PhiF &phi_of,
-                                          R phi_here, uint8_t fl, R wet_max, int x, int y, int z, R *gr)
+// grad(phi) = 3 sum_i w_i c_i phi(x + c_i)
+template <class R, class PhiF>
+__device__ __forceinline__ void grad_sum(const PhiF &phi_of, R *gr)
 {
     gr[0] = gr[1] = gr[2] = 0;
 #pragma unroll
@@ -91,10 +89,26 @@ __device__ __forceinline__ void grad_node(const InstDev &I, const PartDev *parts
         gr[1] += wc * cy(i) * p;
         gr[2] += wc * cz(i) * p;
     }
+}
+
+// the wetting rotation of grad(phi) at boundary nodes inside the interface
+template <class R, class A>
+__device__ __forceinline__ void grad_wet(const InstDev &I, const PartDev *parts, const A &nbr, R phi_here,
+                                         uint8_t fl, R wet_max, int x, int y, int z, R *gr)
+{
     if ((fl & BOUND_BIT) && fabs(phi_here) < wet_max) {
         R ns[3], cth, sth;
         if (solid_normal<R>(I, parts, nbr, x, y, z, ns, &cth, &sth)) wetting_rotate<R>(gr, ns, cth, sth);
     }
+}
+
+// both
+template <class R, class A, class PhiF>
+__device__ __forceinline__ void grad_node(const InstDev &I, const PartDev *parts, const A &nbr, const PhiF &phi_of,
+                                          R phi_here, uint8_t fl, R wet_max, int x, int y, int z, R *gr)
+{
+    grad_sum<R>(phi_of, gr);
+    grad_wet<R>(I, parts, nbr, phi_here, fl, wet_max, x, y, z, gr);
 }
 
 // force, velocity, MRT (two-relaxation-time form) with Guo forcing,
