@@ -36,9 +36,12 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "
 
 
 def algorithmic_bytes_per_node(stage, prec):
+    """Bytes a kernel must move per node: the order-parameter pass reads the 38
+    streamed populations and writes phi; the collision reads the 19 streamed
+    total populations and phi and writes all 38 populations."""
     e = ELEM[prec]
     r = 8 if prec == "fp64" else 4
-    return {"collide": 76 * e, "phi": 38 * e + r}.get(stage, 0)
+    return {"collide": 57 * e + r, "phi": 38 * e + r}.get(stage, 0)
 
 
 def measured_peaks():
@@ -332,7 +335,7 @@ def extra_measure(torch, lbm, W, args, stream, N):
         col = prof["collide"]
         cms = col["ms"] / max(1, col["launches"])
         out[prec] = dict(value=N * K / (ms * 1e-3) / 1e6, value_graph_replay=N * K / (ms_g * 1e-3) / 1e6,
-                         collide_ms=cms, collide_gbs=76 * 2 * N / (cms * 1e-3) / 1e9, steps=K)
+                         collide_ms=cms, collide_gbs=(57 * 2 + 4) * N / (cms * 1e-3) / 1e9, steps=K)
     ws = W.cfg4()
     params = [dict(w["params"], store_velocity=0) for w in ws]
     ctx = lbm.Context(params, "fp16", stream=stream.cuda_stream)
