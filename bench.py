@@ -44,6 +44,12 @@ def algorithmic_bytes_per_node(stage, prec):
     return {"collide": 57 * e + r, "phi": 38 * e + r}.get(stage, 0)
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of this workload (profiles/step_launches_fp32_256x128x128.md); valid
+# while the kernel is unchanged since that capture
+NCU_TRAFFIC = {("collide", "fp32"): 1035.67e6}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -268,7 +274,8 @@ def main():
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
     step_bytes = 76 * ELEM[args.precision] * N
     roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=hbm, unit="GB/s",
-                    frac=(achieved / hbm) if achieved else None, traffic=None, peak_source=peak_src,
+                    frac=(achieved / hbm) if achieved else None,
+                    traffic=NCU_TRAFFIC.get((dom, args.precision)), peak_source=peak_src,
                     algorithmic_bytes_per_launch=dom_bytes, avg_launch_ms=dom_ms)
     stage_ms = {k: round(v["ms"] / max(1, v["launches"]), 5) for k, v in prof.items() if v["launches"]}
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
