@@ -101,6 +101,9 @@ typedef struct {
     double wet_phi_max;        /* wetting applied at nodes with |phi| < this; 0 -> 0.99   */
     int store_velocity;        /* 1: keep the collision velocity for lbm_read_fields(U)   */
     int diag_interval;         /* > 0: FP64 mass sums every that many steps               */
+    double surrogate_u_ref;    /* surrogate inputs: velocity scale; 0 -> 1e-3             */
+    double surrogate_r_ref;    /* surrogate inputs: radius scale; 0 -> 8                  */
+    double surrogate_shell_gap;/* shell radius R_p + this; 0 -> 2                         */
 } lbm_params;
 
 /* One rigid sphere (Sec. III, V).  R_c = R_p + delta_R; m = rho_p 4/3 pi R_p^3;
@@ -264,6 +267,69 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages);
  * the one array, so calls that overlap on the GPU race.  Asynchronous; returns
  * LBM_ERR_CUDA if the lookup or a launch fails. */
 lbm_status lbm_component_masses_noalloc(const double *pops, long long n_nodes, double *masses, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned force surrogate (an extension of the method; the paper has none).
+ * On a coarse grid the momentum-exchange and capillary forces (Sec. V B, V E)
+ * can be replaced by a network evaluated on samples of the flow around each
+ * sphere:
+ *   inputs (LBM_MLP_INPUTS = 387): at the 96 points of a Fibonacci sphere of
+ *     radius R_p + surrogate_shell_gap around the centre (z_k = 1 - (2k+1)/96,
+ *     azimuth k times the golden angle pi (3 - sqrt 5)), the order parameter
+ *     and the velocity relative to the particle's rigid motion divided by
+ *     surrogate_u_ref (phi, ux, uy, uz per point; trilinear over the fluid
+ *     corners of the cell, zeros when none is fluid), then cos theta_p,
+ *     sin theta_p, R_p / surrogate_r_ref;
+ *   network: 400 (inputs zero-padded) -> 128 -> 128 -> 6, tanh hidden layers;
+ *   outputs: F / (sigma R_p) (3) and T / (sigma R_p^2) (3), which replace
+ *     F_eta + F_sigma and T_eta + T_sigma in the DEM.
+ * Weights (LBM_MLP_PARAMS floats): W1 (128 x 400 row-major), b1 (128), W2
+ * (128 x 128), b2 (128), W3 (6 x 128), b3 (6).  Products run on the tensor
+ * cores with BF16 operands and FP32 accumulation; the master weights and Adam
+ * state are FP32.  Training loss: mean over samples and the 6 outputs of the
+ * squared error; Adam with beta1 = 0.9, beta2 = 0.999, eps = 1e-8; each epoch
+ * visits the samples in the order of a Fisher-Yates shuffle driven by
+ * SplitMix64 seeded once per call.
+ * ------------------------------------------------------------------------- */
+#define LBM_MLP_INPUTS 387
+#define LBM_MLP_OUTPUTS 6
+#define LBM_MLP_PARAMS 68614
+#define LBM_MLP_MAX_BATCH 4096
+
+typedef enum { LBM_FORCE_RESOLVED = 0, LBM_FORCE_SURROGATE = 1 } lbm_force_model;
+
+/* Select how the fluid forces on the particles are computed from the next
+ * step on.  LBM_FORCE_SURROGATE needs loaded weights and store_velocity in
+ * every instance (-> LBM_ERR_STATE).  Invalidates the step graph. */
+lbm_status lbm_set_force_model(lbm_ctx *ctx, int model);
+
+/* Copy n = LBM_MLP_PARAMS host floats in as the master weights (the BF16
+ * copies follow) and reset the Adam state.  Wrong n -> LBM_ERR_ARG. */
+lbm_status lbm_surrogate_load(lbm_ctx *ctx, const float *weights, size_t n);
+
+/* Copy the FP32 master weights out (n = LBM_MLP_PARAMS).  Synchronises. */
+lbm_status lbm_surrogate_save(lbm_ctx *ctx, float *weights, size_t n);
+
+/* Network outputs Y [n][6] for host inputs X [n][387].  Synchronises. */
+lbm_status lbm_surrogate_predict(lbm_ctx *ctx, const float *X, size_t n, float *Y);
+
+/* Loss of one batch (X [n][387], targets Y [n][6], 1 <= n <=
+ * LBM_MLP_MAX_BATCH) and its gradient with respect to the weights (grad
+ * [LBM_MLP_PARAMS], same layout); no update.  Synchronises. */
+lbm_status lbm_surrogate_gradient(lbm_ctx *ctx, const float *X, const float *Y, size_t n, float *grad,
+                                  double *loss);
+
+/* Mini-batch Adam over n samples for `epochs` epochs (batch in
+ * [1, LBM_MLP_MAX_BATCH], lr > 0); *loss_out = mean batch loss of the last
+ * epoch.  The Adam state carries over between calls until the next load.
+ * Synchronises. */
+lbm_status lbm_surrogate_train(lbm_ctx *ctx, const float *X, const float *Y, size_t n, int epochs, int batch,
+                               double lr, uint64_t seed, double *loss_out);
+
+/* Surrogate inputs of every particle of an instance for the current state,
+ * out [n_particles][387].  Needs store_velocity (-> LBM_ERR_STATE).
+ * Synchronises. */
+lbm_status lbm_surrogate_features(lbm_ctx *ctx, int inst, float *out);
 
 #ifdef __cplusplus
 }

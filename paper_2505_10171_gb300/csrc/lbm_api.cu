@@ -56,6 +56,14 @@ struct lbm_ctx {
     // fluid launch form: plain (default), staged or fused z-marching
     FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
+    // learned force surrogate
+    Mlp mlp;
+    bool mlp_loaded = false;
+    int force_model = LBM_FORCE_RESOLVED;
+    float *feat = nullptr;                // [MLP_CAP][387] shell features of the step
+    float *trX = nullptr, *trY = nullptr;  // training set on the device
+    long long *perm = nullptr;            // batch order of an epoch
+    size_t tr_cap = 0;
 };
 
 static void dispatch_grids(lbm_ctx *c);
@@ -361,8 +369,10 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
     dispatch(c->prec, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz);
-        launch_particle_forces<S>(L, cur, c->stream, launches, mk);
-        launch_dem(L, c->stream, launches, mk);
+        const bool sur = c->force_model == LBM_FORCE_SURROGATE;
+        if (sur) launch_surrogate_forces<S>(L, c->mlp, c->feat, c->stream, launches, mk);
+        else launch_particle_forces<S>(L, cur, c->stream, launches, mk);
+        launch_dem(L, c->stream, launches, mk, !sur);
         launch_geometry<S>(L, cur ^ 1, c->stream, launches, mk);
     });
     c->cur ^= 1;
@@ -408,6 +418,8 @@ static lbm_status validate(lbm_ctx *ctx, const lbm_params &p, int k)
         return bad("DEM constants must be >= 0");
     if (p.grad_eps < 0 || p.wet_phi_max < 0 || p.cap_norm < 0 || p.diag_interval < 0)
         return bad("negative grad_eps / wet_phi_max / cap_norm / diag_interval");
+    if (!(p.surrogate_u_ref >= 0) || !(p.surrogate_r_ref >= 0) || !(p.surrogate_shell_gap >= 0))
+        return bad("negative surrogate_u_ref / surrogate_r_ref / surrogate_shell_gap");
     return LBM_OK;
 }
 
@@ -456,6 +468,11 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->grad);
     cudaFree(ctx->gmag);
     cudaFree(ctx->kap);
+    mlp_free(ctx->mlp);
+    cudaFree(ctx->feat);
+    cudaFree(ctx->trX);
+    cudaFree(ctx->trY);
+    cudaFree(ctx->perm);
     cudaFree(ctx->u);
     cudaFree(ctx->parts_d);
     cudaFree(ctx->mem_part);
@@ -520,6 +537,9 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.sin_tw = std::sin(th);
         I.grad_eps = p.grad_eps > 0.0 ? p.grad_eps : 1e-4;
         I.wet_max = p.wet_phi_max > 0.0 ? p.wet_phi_max : 0.99;
+        I.sh_gap = p.surrogate_shell_gap > 0.0 ? p.surrogate_shell_gap : 2.0;
+        I.sh_uref = p.surrogate_u_ref > 0.0 ? p.surrogate_u_ref : 1e-3;
+        I.sh_rref = p.surrogate_r_ref > 0.0 ? p.surrogate_r_ref : 8.0;
         I.kn = p.kn; I.kt = p.kt; I.kr = p.kr;
         I.gn = p.gn; I.gt = p.gt; I.gr = p.gr;
         I.mu_s = p.mu_s; I.mu_r = p.mu_r; I.dR = p.delta_R;
@@ -1055,6 +1075,215 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages)
         out[2 * k + 1] = ms[k];
     }
     return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned force surrogate
+// ---------------------------------------------------------------------------
+static lbm_status ensure_mlp(lbm_ctx *ctx)
+{
+    if (ctx->mlp.cap) return LBM_OK;
+    CU(cudaStreamSynchronize(ctx->stream));
+    cudaError_t e = mlp_alloc(ctx->mlp, MLP_CAP);
+    if (e == cudaSuccess && !ctx->feat) e = cudaMalloc((void **)&ctx->feat, sizeof(float) * MLP_CAP * MLP_NIN);
+    if (e != cudaSuccess) {
+        mlp_free(ctx->mlp);
+        cudaGetLastError();
+        return fail(ctx, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+                    std::string("surrogate buffers: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+static bool all_finite(const float *v, size_t n)
+{
+    for (size_t i = 0; i < n; i++)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+// host inputs [n][387] and targets [n][6] onto the device (scratch)
+static lbm_status upload_xy(lbm_ctx *ctx, const float *X, const float *Y, size_t n, float **Xd, float **Yd)
+{
+    const size_t bx = sizeof(float) * n * MLP_NIN, by = Y ? sizeof(float) * n * MLP_NOUT : 0;
+    lbm_status s = ensure_scratch(ctx, ((bx + 255) / 256) * 256 + by + 256);
+    if (s != LBM_OK) return s;
+    *Xd = (float *)ctx->scratch;
+    CU(cudaMemcpyAsync(*Xd, X, bx, cudaMemcpyHostToDevice, ctx->stream));
+    if (Y) {
+        *Yd = (float *)((char *)ctx->scratch + ((bx + 255) / 256) * 256);
+        CU(cudaMemcpyAsync(*Yd, Y, by, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_force_model(lbm_ctx *ctx, int model)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (model != LBM_FORCE_RESOLVED && model != LBM_FORCE_SURROGATE)
+        return fail(ctx, LBM_ERR_ARG, "model must be LBM_FORCE_RESOLVED or LBM_FORCE_SURROGATE");
+    if (model == LBM_FORCE_SURROGATE) {
+        if (!ctx->mlp_loaded) return fail(ctx, LBM_ERR_STATE, "no surrogate weights loaded");
+        for (auto &I : ctx->inst_h)
+            if (!I.store_u) return fail(ctx, LBM_ERR_STATE, "the surrogate needs store_velocity in every instance");
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->force_model = model;
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_load(lbm_ctx *ctx, const float *weights, size_t n)
+{
+    if (!ctx || !weights) return fail(ctx, LBM_ERR_ARG, "null weights");
+    if (n != (size_t)MLP_NPARAM) return fail(ctx, LBM_ERR_ARG, "expected LBM_MLP_PARAMS weights");
+    if (!all_finite(weights, n)) return fail(ctx, LBM_ERR_ARG, "non-finite weight");
+    lbm_status s = ensure_mlp(ctx);
+    if (s != LBM_OK) return s;
+    CU(cudaMemcpyAsync(ctx->mlp.theta, weights, sizeof(float) * n, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp.adam_m, 0, sizeof(float) * n, ctx->stream));
+    CU(cudaMemsetAsync(ctx->mlp.adam_v, 0, sizeof(float) * n, ctx->stream));
+    ctx->mlp.t = 0;
+    mlp_refresh(ctx->mlp, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->mlp_loaded = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_save(lbm_ctx *ctx, float *weights, size_t n)
+{
+    if (!ctx || !weights) return fail(ctx, LBM_ERR_ARG, "null weights");
+    if (n != (size_t)MLP_NPARAM) return fail(ctx, LBM_ERR_ARG, "expected LBM_MLP_PARAMS weights");
+    if (!ctx->mlp_loaded) return fail(ctx, LBM_ERR_STATE, "no surrogate weights loaded");
+    CU(cudaMemcpyAsync(weights, ctx->mlp.theta, sizeof(float) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_surrogate_predict(lbm_ctx *ctx, const float *X, size_t n, float *Y)
+{
+    if (!ctx || !X || !Y || n < 1) return fail(ctx, LBM_ERR_ARG, "bad surrogate_predict arguments");
+    if (!ctx->mlp_loaded) return fail(ctx, LBM_ERR_STATE, "no surrogate weights loaded");
+    for (size_t r0 = 0; r0 < n; r0 += MLP_CAP) {
+        const int nb = (int)std::min<size_t>(MLP_CAP, n - r0);
+        float *Xd = nullptr, *Yd = nullptr;
+        lbm_status s = upload_xy(ctx, X + r0 * MLP_NIN, nullptr, nb, &Xd, &Yd);
+        if (s != LBM_OK) return s;
+        mlp_stage(ctx->mlp, Xd, nullptr, nullptr, 0, nb, ctx->stream);
+        mlp_forward(ctx->mlp, nb, ctx->status, ctx->stream);
+        CU(cudaGetLastError());
+        CU(cudaMemcpy2DAsync(Y + r0 * MLP_NOUT, sizeof(float) * MLP_NOUT, ctx->mlp.Y, sizeof(float) * 16,
+                             sizeof(float) * MLP_NOUT, nb, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return check_status(ctx);
+}
+
+lbm_status lbm_surrogate_gradient(lbm_ctx *ctx, const float *X, const float *Y, size_t n, float *grad,
+                                  double *loss)
+{
+    if (!ctx || !X || !Y || !grad || n < 1 || n > (size_t)MLP_CAP)
+        return fail(ctx, LBM_ERR_ARG, "bad surrogate_gradient arguments (1 <= n <= LBM_MLP_MAX_BATCH)");
+    if (!ctx->mlp_loaded) return fail(ctx, LBM_ERR_STATE, "no surrogate weights loaded");
+    float *Xd = nullptr, *Yd = nullptr;
+    lbm_status s = upload_xy(ctx, X, Y, n, &Xd, &Yd);
+    if (s != LBM_OK) return s;
+    mlp_stage(ctx->mlp, Xd, Yd, nullptr, 0, (int)n, ctx->stream);
+    mlp_forward(ctx->mlp, (int)n, ctx->status, ctx->stream);
+    mlp_backward(ctx->mlp, (int)n, nullptr, ctx->status, ctx->stream);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(grad, ctx->mlp.grad, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, ctx->stream));
+    double l = 0.0;
+    CU(cudaMemcpyAsync(&l, ctx->mlp.loss, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (loss) *loss = l;
+    return check_status(ctx);
+}
+
+// SplitMix64 (Steele, Lea and Flood 2014) and the Fisher-Yates order of an epoch
+static uint64_t splitmix64(uint64_t &s)
+{
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+lbm_status lbm_surrogate_train(lbm_ctx *ctx, const float *X, const float *Y, size_t n, int epochs, int batch,
+                               double lr, uint64_t seed, double *loss_out)
+{
+    if (!ctx || !X || !Y || n < 1 || epochs < 1 || batch < 1 || batch > MLP_CAP || !(lr > 0.0))
+        return fail(ctx, LBM_ERR_ARG, "bad surrogate_train arguments");
+    if (!ctx->mlp_loaded) return fail(ctx, LBM_ERR_STATE, "no surrogate weights loaded");
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->tr_cap < n) {
+        cudaFree(ctx->trX);
+        cudaFree(ctx->trY);
+        cudaFree(ctx->perm);
+        ctx->trX = ctx->trY = nullptr;
+        ctx->perm = nullptr;
+        ctx->tr_cap = 0;
+        CU(cudaMalloc((void **)&ctx->trX, sizeof(float) * n * MLP_NIN));
+        CU(cudaMalloc((void **)&ctx->trY, sizeof(float) * n * MLP_NOUT));
+        CU(cudaMalloc((void **)&ctx->perm, sizeof(long long) * n));
+        ctx->tr_cap = n;
+    }
+    CU(cudaMemcpyAsync(ctx->trX, X, sizeof(float) * n * MLP_NIN, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(ctx->trY, Y, sizeof(float) * n * MLP_NOUT, cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<long long> perm(n);
+    uint64_t st = seed;
+    const size_t nb = (n + batch - 1) / batch;
+    double last = 0.0;
+    for (int ep = 0; ep < epochs; ep++) {
+        for (size_t i = 0; i < n; i++) perm[i] = (long long)i;
+        for (size_t i = n - 1; i >= 1; i--) {
+            const size_t j = (size_t)(splitmix64(st) % (uint64_t)(i + 1));
+            std::swap(perm[i], perm[j]);
+        }
+        CU(cudaStreamSynchronize(ctx->stream));  // the previous epoch has finished with ctx->perm
+        CU(cudaMemcpyAsync(ctx->perm, perm.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaMemsetAsync(ctx->mlp.loss + 1, 0, sizeof(double), ctx->stream));
+        for (size_t b = 0; b < nb; b++) {
+            const long long r0 = (long long)(b * batch);
+            const int sz = (int)std::min<size_t>(batch, n - r0);
+            mlp_stage(ctx->mlp, ctx->trX, ctx->trY, ctx->perm, r0, sz, ctx->stream);
+            mlp_forward(ctx->mlp, sz, ctx->status, ctx->stream);
+            mlp_backward(ctx->mlp, sz, ctx->mlp.loss + 1, ctx->status, ctx->stream);
+            mlp_adam(ctx->mlp, lr, ctx->stream);
+        }
+        CU(cudaGetLastError());
+        double acc = 0.0;
+        CU(cudaMemcpyAsync(&acc, ctx->mlp.loss + 1, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        last = acc / (double)nb;
+    }
+    if (loss_out) *loss_out = last;
+    return check_status(ctx);
+}
+
+lbm_status lbm_surrogate_features(lbm_ctx *ctx, int inst, float *out)
+{
+    if (!ctx || !out || inst < 0 || inst >= ctx->n_inst) return fail(ctx, LBM_ERR_ARG, "bad instance or output");
+    const InstDev &I = ctx->inst_h[inst];
+    if (!I.store_u) return fail(ctx, LBM_ERR_STATE, "the surrogate inputs need store_velocity");
+    if (I.np == 0) return LBM_OK;
+    lbm_status s = ensure_mlp(ctx);
+    if (s != LBM_OK) return s;
+    Lattice L = make_lattice(ctx);
+    for (int p0 = 0; p0 < I.np; p0 += MLP_CAP) {
+        const int np = std::min(MLP_CAP, I.np - p0);
+        dispatch(ctx->prec, [&](auto *tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            launch_shell_features<S>(L, I.part_off + p0, np, ctx->feat, ctx->stream);
+        });
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(out + (size_t)p0 * MLP_NIN, ctx->feat, sizeof(float) * np * MLP_NIN,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return check_status(ctx);
 }
 
 }  // extern "C"

@@ -83,6 +83,8 @@ struct InstDev {
     // most st_seg nodes; st_ygroups items cover the y rows of a plane
     long long st_item_start;
     int st_rows, st_seg, st_nseg, st_ygroups;
+    // surrogate inputs: shell gap, velocity and radius scales
+    double sh_gap, sh_uref, sh_rref;
 };
 
 // fluid parameters in the arithmetic precision R
@@ -503,7 +505,8 @@ int persistent_grid(K kernel, size_t smem, int cap)
 // kernel stages, in launch order within a step (for per-kernel timing)
 enum Stage {
     STAGE_PHI = 0, STAGE_SOLIDPHI, STAGE_GRAD, STAGE_COLLIDE, STAGE_MEM, STAGE_CAPILLARY, STAGE_DEM,
-    STAGE_GEOM_OWNER, STAGE_GEOM_BOUND, STAGE_REFILL, STAGE_FUSED, STAGE_REGION, STAGE_CURV, N_STAGES
+    STAGE_GEOM_OWNER, STAGE_GEOM_BOUND, STAGE_REFILL, STAGE_FUSED, STAGE_REGION, STAGE_CURV, STAGE_SURROGATE,
+    N_STAGES
 };
 
 // optional per-kernel marker: called right before and right after each launch
@@ -556,7 +559,46 @@ template <class S>
 void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk);
 template <class S>
 void launch_geometry(const Lattice &L, int nxt, cudaStream_t st, long long *launches, const Marker &mk);
-void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk);
+// sum_fluid: gather the momentum-exchange and capillary partial sums first
+// (false when the surrogate has written the fluid forces)
+void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk, bool sum_fluid);
+
+// ---------------------------------------------------------------------------
+// learned force surrogate (lbm_mlp.cu)
+// ---------------------------------------------------------------------------
+constexpr int MLP_NIN = 387, MLP_KIN = 400, MLP_HIDDEN = 128, MLP_NOUT = 6, MLP_SHELL = 96;
+constexpr int MLP_OFF_W1 = 0;
+constexpr int MLP_OFF_B1 = MLP_OFF_W1 + MLP_HIDDEN * MLP_KIN;
+constexpr int MLP_OFF_W2 = MLP_OFF_B1 + MLP_HIDDEN;
+constexpr int MLP_OFF_B2 = MLP_OFF_W2 + MLP_HIDDEN * MLP_HIDDEN;
+constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_HIDDEN;
+constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_NOUT * MLP_HIDDEN;
+constexpr int MLP_NPARAM = MLP_OFF_B3 + MLP_NOUT;
+constexpr int MLP_CAP = 4096;  // batch rows at most
+
+struct Mlp {
+    float *theta = nullptr, *grad = nullptr, *adam_m = nullptr, *adam_v = nullptr;  // [MLP_NPARAM]
+    __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W3b = nullptr;                   // BF16 operand copies
+    __nv_bfloat16 *X = nullptr, *H1 = nullptr, *H2 = nullptr, *dZ1 = nullptr, *dZ2 = nullptr, *dYb = nullptr;
+    float *Y = nullptr, *dY = nullptr, *T = nullptr;  // [cap][16], [cap][16], [cap][6]
+    double *loss_part = nullptr, *loss = nullptr;     // loss[0]: last batch, loss[1]: accumulator
+    int cap = 0;
+    long long t = 0;  // Adam steps taken
+};
+cudaError_t mlp_alloc(Mlp &m, int cap);
+void mlp_free(Mlp &m);
+void mlp_refresh(const Mlp &m, cudaStream_t st);
+// rows idx[row0 + r] (or row0 + r) of fp32 features [*][387] (and targets [*][6]) into the batch buffers
+void mlp_stage(const Mlp &m, const float *X, const float *Y, const long long *idx, long long row0, int n,
+               cudaStream_t st);
+void mlp_forward(const Mlp &m, int n, unsigned *status, cudaStream_t st);
+void mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cudaStream_t st);
+void mlp_adam(Mlp &m, double lr, cudaStream_t st);
+template <class S>
+void launch_shell_features(const Lattice &L, int p0, int np, float *feat, cudaStream_t st);
+template <class S>
+void launch_surrogate_forces(const Lattice &L, const Mlp &m, float *feat, cudaStream_t st, long long *launches,
+                             const Marker &mk);
 template <class S>
 void launch_init_fields(const Lattice &L, int cur, int inst, long long N, const double *phi, const double *rho,
                         const double *u, const double *pops, cudaStream_t st);

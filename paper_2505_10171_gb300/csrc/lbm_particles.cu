@@ -604,14 +604,17 @@ void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long lon
     *launches += 2;
 }
 
-void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk)
+void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk, bool sum_fluid)
 {
     if (L.n_parts == 0) return;
     mk(STAGE_DEM, 0);
-    k_part_sums<<<L.n_parts, 32, 0, st>>>(L);
+    if (sum_fluid) {
+        k_part_sums<<<L.n_parts, 32, 0, st>>>(L);
+        *launches += 1;
+    }
     k_dem<<<L.n_inst, DEM_THREADS, 0, st>>>(L);
     mk(STAGE_DEM, 1);
-    *launches += 2;
+    *launches += 1;
 }
 
 template <class S>

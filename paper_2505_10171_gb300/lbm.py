@@ -53,6 +53,7 @@ class lbm_params(ct.Structure):
         ("g_particle", ct.c_double * 3),
         ("grad_eps", ct.c_double), ("wet_phi_max", ct.c_double),
         ("store_velocity", ct.c_int), ("diag_interval", ct.c_int),
+        ("surrogate_u_ref", ct.c_double), ("surrogate_r_ref", ct.c_double), ("surrogate_shell_gap", ct.c_double),
     ]
 
 
@@ -69,9 +70,14 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_init_fields_device", "lbm_add_particles", "lbm_step", "lbm_particle_forces", "lbm_read_fields",
            "lbm_read_fields_device", "lbm_num_particles", "lbm_num_nodes", "lbm_diagnostics", "lbm_set_launch",
            "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
-           "lbm_set_fluid_kernel", "lbm_fluid_form_in_use"]
+           "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
+           "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
+           "lbm_surrogate_features"]
+# learned force surrogate (include/lbm.h)
+MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
+FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
 STAGES = ["phi", "solid_phi", "grad_wetting", "collide", "momentum_exchange", "capillary", "dem", "geom_owner",
-          "geom_boundary", "refill", "fused", "particle_region", "curvature"]
+          "geom_boundary", "refill", "fused", "particle_region", "curvature", "surrogate"]
 # fluid launch forms of lbm_set_fluid_kernel
 FORM_STAGED, FORM_FUSED, FORM_PLAIN = 0, 1, 2
 
@@ -112,6 +118,15 @@ def load(path: str = LIB_PATH):
     L.lbm_profile_read.argtypes = [vp, d, i]
     L.lbm_component_masses_noalloc.argtypes = [vp, ct.c_longlong, vp, vp]
     L.lbm_set_fluid_kernel.argtypes = [vp, i, i, i]
+    fp = ct.POINTER(ct.c_float)
+    sz = ct.c_size_t
+    L.lbm_set_force_model.argtypes = [vp, i]
+    L.lbm_surrogate_load.argtypes = [vp, fp, sz]
+    L.lbm_surrogate_save.argtypes = [vp, fp, sz]
+    L.lbm_surrogate_predict.argtypes = [vp, fp, sz, fp]
+    L.lbm_surrogate_gradient.argtypes = [vp, fp, fp, sz, fp, d]
+    L.lbm_surrogate_train.argtypes = [vp, fp, fp, sz, i, i, ct.c_double, ct.c_uint64, d]
+    L.lbm_surrogate_features.argtypes = [vp, i, fp]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
                         "lbm_last_launch_count"):
@@ -125,6 +140,7 @@ PARAM_DEFAULTS = dict(
     sigma=0.01, beta=0.7, cap_norm=0.0, body_force_a=(0.0, 0.0, 0.0), body_force_b=(0.0, 0.0, 0.0), kn=2.5,
     kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0, g_particle=(0.0, 0.0, 0.0),
     grad_eps=0.0, wet_phi_max=0.0, store_velocity=0, diag_interval=0,
+    surrogate_u_ref=0.0, surrogate_r_ref=0.0, surrogate_shell_gap=0.0,
 )
 
 
@@ -159,6 +175,14 @@ def _dp(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fp(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_float))
 
 
 class Context:
@@ -268,6 +292,47 @@ class Context:
         out = np.zeros(2 * len(STAGES))
         self._check(self.L.lbm_profile_read(self.h, _dp(out), len(STAGES)))
         return {name: dict(launches=int(out[2 * k]), ms=float(out[2 * k + 1])) for k, name in enumerate(STAGES)}
+
+    # --- learned force surrogate --------------------------------------------
+    def lbm_set_force_model(self, model):
+        self._check(self.L.lbm_set_force_model(self.h, int(model)))
+
+    def lbm_surrogate_load(self, weights):
+        w = _f32(weights)
+        self._check(self.L.lbm_surrogate_load(self.h, _fp(w), w.size))
+
+    def lbm_surrogate_save(self):
+        w = np.zeros(MLP_PARAMS, dtype=np.float32)
+        self._check(self.L.lbm_surrogate_save(self.h, _fp(w), w.size))
+        return w
+
+    def lbm_surrogate_predict(self, X):
+        X = _f32(X).reshape(-1, MLP_INPUTS)
+        Y = np.zeros((X.shape[0], MLP_OUTPUTS), dtype=np.float32)
+        self._check(self.L.lbm_surrogate_predict(self.h, _fp(X), X.shape[0], _fp(Y)))
+        return Y
+
+    def lbm_surrogate_gradient(self, X, Y):
+        X = _f32(X).reshape(-1, MLP_INPUTS)
+        Y = _f32(Y).reshape(-1, MLP_OUTPUTS)
+        g = np.zeros(MLP_PARAMS, dtype=np.float32)
+        loss = np.zeros(1)
+        self._check(self.L.lbm_surrogate_gradient(self.h, _fp(X), _fp(Y), X.shape[0], _fp(g), _dp(loss)))
+        return g, float(loss[0])
+
+    def lbm_surrogate_train(self, X, Y, epochs, batch, lr, seed):
+        X = _f32(X).reshape(-1, MLP_INPUTS)
+        Y = _f32(Y).reshape(-1, MLP_OUTPUTS)
+        loss = np.zeros(1)
+        self._check(self.L.lbm_surrogate_train(self.h, _fp(X), _fp(Y), X.shape[0], int(epochs), int(batch),
+                                               float(lr), ct.c_uint64(int(seed) & (2 ** 64 - 1)), _dp(loss)))
+        return float(loss[0])
+
+    def lbm_surrogate_features(self, inst=0):
+        n = self.num_particles(inst)
+        out = np.zeros((max(n, 1), MLP_INPUTS), dtype=np.float32)
+        self._check(self.L.lbm_surrogate_features(self.h, inst, _fp(out)))
+        return out[:n]
 
     # --- conveniences built only from the entry points above ----------------
     def fields(self, inst=0):
