@@ -54,8 +54,12 @@ struct lbm_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
     // fluid launch form: plain (default), staged or fused z-marching
-    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
+    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
+    // static solid nodes next to non-static ones (built before the first step)
+    long long *static_list = nullptr;
+    long long n_static = 0;
+    bool static_ready = false;
     // learned force surrogate
     Mlp mlp;
     bool mlp_loaded = false;
@@ -90,6 +94,7 @@ static void plan_fused(lbm_ctx *c)
 static void plan_launch(lbm_ctx *c)
 {
     plan_fused(c);
+    c->fz.gc_items = plan_gradcurv(c->inst_h);
     const bool aligned = plan_rows(c->inst_h, c->elem, &c->fz.rows);
     c->fz.st_items = aligned ? c->fz.rows : 0;
     dispatch_grids(c);
@@ -119,6 +124,8 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.inst = c->inst_d;
     L.n_inst = c->n_inst;
     L.n_items = c->fz.rows;
+    L.static_list = c->static_list;
+    L.n_static = c->n_static;
     L.flags = c->flags;
     L.pop[0] = c->pop[0];
     L.pop[1] = c->pop[1];
@@ -468,6 +475,7 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->grad);
     cudaFree(ctx->gmag);
     cudaFree(ctx->kap);
+    cudaFree(ctx->static_list);
     mlp_free(ctx->mlp);
     cudaFree(ctx->feat);
     cudaFree(ctx->trX);
@@ -866,6 +874,28 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
 {
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
+    if (!ctx->static_ready) {
+        // the static solid boundary list: count, allocate, fill
+        Lattice L = make_lattice(ctx);
+        unsigned long long *cnt = nullptr, h = 0;
+        CU(cudaMalloc((void **)&cnt, sizeof(unsigned long long)));
+        CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream));
+        launch_static_bound(L, nullptr, cnt, ctx->stream);
+        CU(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+        if (h > 0) {
+            CU(cudaMalloc((void **)&ctx->static_list, sizeof(long long) * h));
+            CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream));
+            L.static_list = ctx->static_list;
+            launch_static_bound(L, ctx->static_list, cnt, ctx->stream);
+            CU(cudaStreamSynchronize(ctx->stream));
+        }
+        CU(cudaGetLastError());
+        cudaFree(cnt);
+        ctx->n_static = (long long)h;
+        ctx->static_ready = true;
+        drop_graph(ctx);
+    }
     ctx->stepped = true;
     long long launches = 0;
     while (nsteps > 0) {

@@ -7,13 +7,14 @@
 // in its two-relaxation-time form -> recolouring -> write.
 //
 // Three launch forms run the per-node device functions of lbm_node.cuh:
-//  * plain (default): k_phi, k_solidphi, k_grad, k_curv, k_collide, one thread
-//    per node with direct global loads.  The collision pulls only the 19 total
+//  * plain (default): k_phi (one thread per node, stores phi); the solid-phi
+//    fill over the listed static solid nodes and the particle cubes;
+//    k_gradcurv (z-marching tiles: gradient, wetting, normal, curvature);
+//    k_collide (one thread per node).  The collision pulls only the 19 total
 //    offsets F: the colour offsets enter it only through phi, which k_phi
 //    stores.
-//  * staged: the same kernels, with k_phi and k_collide replaced by persistent
-//    kernels that bring their inputs into shared memory with asynchronous
-//    copies (lbm_staged.cu).
+//  * staged: k_phi and k_collide replaced by persistent kernels that bring
+//    their inputs into shared memory with asynchronous copies (lbm_staged.cu).
 //  * k_fused: one kernel per step.  A block owns a TX x TY column tile and a
 //    chunk of z-planes and marches z: the order parameter of plane z+3 is
 //    gathered into a shared-memory ring (with a 3-node halo, enough for the
@@ -115,17 +116,57 @@ __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) 
     for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
 }
 
-template <class R>
-__global__ void __launch_bounds__(ROW_NODES) k_solidphi(Lattice L)
+// instance of global node g (binary search over the node offsets)
+__device__ __forceinline__ int inst_of_node(const Lattice &L, long long g)
 {
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { solidphi_body<R>(L, I, n, x, y, z); });
+    int lo = 0, hi = L.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.inst[mid].node_off <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-template <class R>
-__global__ void __launch_bounds__(ROW_NODES) k_grad(Lattice L)
+// static solid nodes with a neighbour that is not static solid: the only
+// static nodes the solid-phi fill can reach.  count pass (list == null) or
+// fill pass; the order of the list does not matter.
+__global__ void k_static_bound(Lattice L, long long *list, unsigned long long *count)
 {
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { grad_body<R>(L, I, n, x, y, z); });
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= L.Ntot || (L.flags[g] & OWNER_MASK) != OWN_WALL) return;
+    const InstDev &I = L.inst[inst_of_node(L, g)];
+    const int n = (int)(g - I.node_off);
+    const int x = n % I.nx, y = (n / I.nx) % I.ny, z = n / (I.nx * I.ny);
+    Nbr nb;
+    nb.init(x, y, z, I.nx, I.ny, I.nz);
+    const uint8_t *fli = L.flags + I.node_off;
+    bool hit = false;
+#pragma unroll
+    for (int i = 1; i < Q; i++) hit |= (fli[nb.at(cx(i), cy(i), cz(i))] & OWNER_MASK) != OWN_WALL;
+    if (!hit) return;
+    const unsigned long long k = atomicAdd(count, 1ull);
+    if (list) list[k] = g;
 }
+
+// solid-phi fill of the listed static nodes
+template <class R>
+__global__ void k_solidphi_list(Lattice L)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.n_static) return;
+    const long long g = L.static_list[i];
+    const InstDev &I = L.inst[inst_of_node(L, g)];
+    const int n = (int)(g - I.node_off);
+    const int x = n % I.nx, y = (n / I.nx) % I.ny, z = n / (I.nx * I.ny);
+    solidphi_body<R>(L, I, n, x, y, z);
+}
+
+void launch_static_bound(const Lattice &L, long long *list, unsigned long long *count, cudaStream_t st)
+{
+    k_static_bound<<<(unsigned)((L.Ntot + 255) / 256), 256, 0, st>>>(L, list, count);
+}
+
 
 template <class S>
 __global__ void __launch_bounds__(PART_THREADS) k_phi_region(Lattice L, int cur, int side)
@@ -146,35 +187,6 @@ __global__ void __launch_bounds__(PART_THREADS) k_grad_region(Lattice L, int sid
 {
     LBM_REGION_PROLOGUE
     grad_body<R>(L, I, n, x, y, z);
-}
-
-// curvature of every fluid node from the stored normals (a solid neighbour
-// contributes the node's own normal)
-template <class R>
-__device__ __forceinline__ void curv_body(const Lattice &L, const InstDev &I, int n, int x, int y, int z)
-{
-    const long long g = I.node_off + n;
-    const uint8_t fl = L.flags[g];
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = L.flags + I.node_off;
-    const R *Nn = (const R *)L.grad + I.node_off;
-    const long long Nt = L.Ntot;
-    // all-fluid neighbourhood first (loads issued with the flag load)
-    R kap = curvature<R>([&](int dx, int dy, int dz, int a) { return Nn[a * Nt + nb.idx(dx, dy, dz)]; });
-    if ((fl & OWNER_MASK) != OWN_FLUID) return;
-    if (fl & BOUND_BIT)
-        kap = curvature<R>([&](int dx, int dy, int dz, int a) {
-            if (nb.own(dx, dy, dz) != OWN_FLUID) return Nn[a * Nt + n];
-            return Nn[a * Nt + nb.idx(dx, dy, dz)];
-        });
-    ((R *)L.kap)[g] = kap;
-}
-
-template <class R>
-__global__ void __launch_bounds__(ROW_NODES) k_curv(Lattice L)
-{
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { curv_body<R>(L, I, n, x, y, z); });
 }
 
 template <class S>
@@ -220,6 +232,156 @@ __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MI
     for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { collide_body<S>(L, I, cur, n, x, y, z); });
 }
 
+// ---------------------------------------------------------------------------
+// gradient, wetting, normal and curvature in one z-marching pass
+// ---------------------------------------------------------------------------
+// A CTA owns a GC_TX x GC_TY column tile and a chunk of z-planes.  Step j loads
+// phi of plane z0-2+j (2-node halo) into a 3-plane ring, forms the normals of
+// plane z0-3+j on the 1-halo tile into a second 3-plane ring (and writes
+// those of its own planes), and the curvature of plane z0-4+j from the normal
+// ring.  Each phi value is read from L2/HBM about 1.7 times, the normal once
+// per CTA; the per-node arithmetic is that of grad_body and the curvature
+// of the fused kernel.
+constexpr int GC_TX = 32, GC_TY = 8, GC_ZC = 16;
+
+__device__ __forceinline__ int wrap_any(int a, int n)
+{
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+template <class R>
+__global__ void __launch_bounds__(GC_TX *GC_TY) k_gradcurv(Lattice L)
+{
+    constexpr int NT = GC_TX * GC_TY;
+    constexpr int PW = GC_TX + 4, PH = GC_TY + 4, PN = PW * PH;  // phi region
+    constexpr int NW = GC_TX + 2, NH = GC_TY + 2, NN = NW * NH;  // normal region
+    __shared__ R phS[3][PN];
+    __shared__ R nS[3][3][NN];
+
+    const long long item = blockIdx.x;
+    int k = 0;
+    {
+        int lo = 0, hi = L.n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.inst[mid].gc_item_start <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        k = lo;
+    }
+    const InstDev &I = L.inst[k];
+    const int loc = (int)(item - I.gc_item_start);
+    const int chunk = loc % I.gc_nchunks;
+    const int t2 = loc / I.gc_nchunks;
+    const int x0 = (t2 % I.gc_tiles_x) * GC_TX, y0 = (t2 / I.gc_tiles_x) * GC_TY;
+    const int z0 = chunk * I.gc_zc, z1 = min(z0 + I.gc_zc, I.nz);
+    const int nx = I.nx, ny = I.ny, nz = I.nz;
+    const long long off = I.node_off, Nt = L.Ntot;
+    const uint8_t *fli = L.flags + off;
+    const R *ph = (const R *)L.phi + off;
+    R *Nn = (R *)L.grad + off;
+    R *Gm = (R *)L.gmag + off;
+    R *Kp = (R *)L.kap + off;
+    FluidPar<R> P;
+    load_par(I, P);
+    const int tid = threadIdx.x, lx = tid % GC_TX, ly = tid / GC_TX;
+    const int gx = x0 + lx, gy = y0 + ly;
+    const bool active = gx < nx && gy < ny;
+    const int niter = (z1 - z0) + 4;
+
+    for (int j = 0; j < niter; j++) {
+        // (1) phi of plane z0-2+j
+        {
+            const int Z = wrap_any(z0 - 2 + j, nz);
+            R *dst = phS[j % 3];
+            for (int r = tid; r < PN; r += NT) {
+                const int X = wrap_any(x0 - 2 + r % PW, nx), Y = wrap_any(y0 - 2 + r / PW, ny);
+                dst[r] = ph[(Z * ny + Y) * nx + X];
+            }
+        }
+        __syncthreads();
+        // (2) normals of plane zz = z0-3+j on the 1-halo tile
+        if (j >= 2) {
+            const int zz = z0 - 3 + j;
+            const int Z = wrap_any(zz, nz);
+            const R *pm = phS[(j - 2) % 3], *p0 = phS[(j - 1) % 3], *pp = phS[j % 3];
+            const bool own_plane = zz >= z0 && zz < z1;
+            for (int r1 = tid; r1 < NN; r1 += NT) {
+                const int ax = r1 % NW, ay = r1 / NW;
+                const int X = wrap_any(x0 - 1 + ax, nx), Y = wrap_any(y0 - 1 + ay, ny);
+                const int n = (Z * ny + Y) * nx + X;
+                const uint8_t fl = fli[n];
+                R nn[3] = {0, 0, 0};
+                if ((fl & OWNER_MASK) == OWN_FLUID) {
+                    const int c = (ay + 1) * PW + (ax + 1);
+                    auto phi_of = [&](int dx, int dy, int dz) {
+                        const R *pl = dz < 0 ? pm : (dz > 0 ? pp : p0);
+                        return pl[c + dy * PW + dx];
+                    };
+                    R gr[3];
+                    grad_sum<R>(phi_of, gr);
+                    if (fl & BOUND_BIT) {
+                        GlobalNbr nb;
+                        nb.nb.init(X, Y, Z, nx, ny, nz);
+                        nb.fli = fli;
+                        grad_wet<R>(I, L.parts, nb, p0[c], fl, P.wet_max, X, Y, Z, gr);
+                    }
+                    const R m = reg_normal(gr, P.eps2, nn);
+                    if (own_plane && ax >= 1 && ax <= GC_TX && ay >= 1 && ay <= GC_TY && x0 - 1 + ax < nx &&
+                        y0 - 1 + ay < ny) {
+                        Nn[n] = nn[0];
+                        Nn[Nt + n] = nn[1];
+                        Nn[2 * Nt + n] = nn[2];
+                        Gm[n] = m;
+                    }
+                }
+                nS[j % 3][0][r1] = nn[0];
+                nS[j % 3][1][r1] = nn[1];
+                nS[j % 3][2][r1] = nn[2];
+            }
+        }
+        __syncthreads();
+        // (3) curvature of plane z = z0-4+j
+        if (j >= 4 && active) {
+            const int z = z0 - 4 + j;
+            const int n = (z * ny + gy) * nx + gx;
+            const uint8_t fl = fli[n];
+            if ((fl & OWNER_MASK) == OWN_FLUID) {
+                const int c = (ly + 1) * NW + (lx + 1);
+                const int sl[3] = {(j - 2) % 3, (j - 1) % 3, j % 3};
+                R kap = curvature<R>([&](int dx, int dy, int dz, int a) { return nS[sl[dz + 1]][a][c + dy * NW + dx]; });
+                if (fl & BOUND_BIT) {
+                    GlobalNbr nb;
+                    nb.nb.init(gx, gy, z, nx, ny, nz);
+                    nb.fli = fli;
+                    kap = curvature<R>([&](int dx, int dy, int dz, int a) {
+                        if (nb.own(dx, dy, dz) != OWN_FLUID) return nS[sl[1]][a][c];
+                        return nS[sl[dz + 1]][a][c + dy * NW + dx];
+                    });
+                }
+                Kp[n] = kap;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+long long plan_gradcurv(std::vector<InstDev> &inst)
+{
+    long long items = 0;
+    for (auto &I : inst) {
+        I.gc_tiles_x = (I.nx + GC_TX - 1) / GC_TX;
+        I.gc_tiles_y = (I.ny + GC_TY - 1) / GC_TY;
+        const int zc = std::min(GC_ZC, I.nz);
+        I.gc_nchunks = (I.nz + zc - 1) / zc;
+        I.gc_zc = (I.nz + I.gc_nchunks - 1) / I.gc_nchunks;
+        I.gc_item_start = items;
+        items += (long long)I.gc_tiles_x * I.gc_tiles_y * I.gc_nchunks;
+    }
+    return items;
+}
+
 // tile shapes of the fused kernel: 0 -> 16 x 16, 1 -> 32 x 8
 int fused_tile_x(int tile) { return tile == 1 ? 32 : 16; }
 int fused_tile_y(int tile) { return tile == 1 ? 8 : 16; }
@@ -256,20 +418,26 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     if (staged) launch_staged_phi<S>(L, cur, fz, st);
     else k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
     mk(STAGE_PHI, 1);
+    // phi of solid nodes next to fluid: the listed static nodes and the
+    // particle cubes (every particle node lies within R_p + 1 of its centre)
     mk(STAGE_SOLIDPHI, 0);
-    k_solidphi<R><<<grid, ROW_NODES, 0, st>>>(L);
+    if (L.n_static > 0) {
+        k_solidphi_list<R><<<(unsigned)((L.n_static + 255) / 256), 256, 0, st>>>(L);
+        *launches += 1;
+    }
+    if (L.n_parts > 0) {
+        k_solidphi_region<R><<<dim3(L.cap_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, L.cap_side - 2);
+        *launches += 1;
+    }
     mk(STAGE_SOLIDPHI, 1);
     mk(STAGE_GRAD, 0);
-    k_grad<R><<<grid, ROW_NODES, 0, st>>>(L);
+    k_gradcurv<R><<<(unsigned)fz.gc_items, GC_TX * GC_TY, 0, st>>>(L);
     mk(STAGE_GRAD, 1);
-    mk(STAGE_CURV, 0);
-    k_curv<R><<<grid, ROW_NODES, 0, st>>>(L);
-    mk(STAGE_CURV, 1);
     mk(STAGE_COLLIDE, 0);
     if (staged) launch_staged_collide<S>(L, cur, fz, st);
     else k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
     mk(STAGE_COLLIDE, 1);
-    *launches += 5;
+    *launches += 3;
 }
 
 

@@ -85,6 +85,10 @@ struct InstDev {
     int st_rows, st_seg, st_nseg, st_ygroups;
     // surrogate inputs: shell gap, velocity and radius scales
     double sh_gap, sh_uref, sh_rref;
+    // gradient + curvature work items: gc_tiles_x * gc_tiles_y column tiles x
+    // gc_nchunks z-chunks of gc_zc planes
+    long long gc_item_start;
+    int gc_tiles_x, gc_tiles_y, gc_nchunks, gc_zc;
 };
 
 // fluid parameters in the arithmetic precision R
@@ -123,6 +127,8 @@ struct Lattice {
     const InstDev *inst;
     int n_inst;
     long long n_items;   // row-strip work items of all instances
+    const long long *static_list;  // static solid nodes next to non-static ones (global node index)
+    long long n_static;
     uint8_t *flags;
     void *pop[2];
     void *phi;           // [Ntot] real
@@ -526,6 +532,7 @@ struct FluidLaunch {
     int tile;           // fused tile shape index (see lbm_fluid.cu)
     long long items;    // fused work items (all instances)
     long long rows;     // row-strip work items (all instances): CTAs of each plain kernel
+    long long gc_items; // gradient + curvature work items (all instances)
     long long st_items; // the same when the staged form is available, else 0
     // persistent grids of the staged kernels, per variant (see lbm_staged.cu)
     int st_grid_phi[3], st_grid_collide[3];
@@ -538,6 +545,8 @@ template <class S>
 struct StagedCfg {
     static constexpr int A = 16 / (int)sizeof(S);  // elements per 16 bytes
 };
+// plan the work items of the gradient + curvature kernel
+long long plan_gradcurv(std::vector<InstDev> &inst);
 // plan the row-strip work items of every instance; *items = their number,
 // returns false if an instance's rows are not whole 16-byte units of storage
 // (which the staged copies need)
@@ -609,6 +618,8 @@ template <class S>
 void launch_mass_sums(const Lattice &L, int cur, int inst, long long N, double *partial, int nblk, double *out,
                       cudaStream_t st);
 void launch_boundary_full(const Lattice &L, int inst, long long N, cudaStream_t st);
+// count (list == null) or fill the static solid boundary list
+void launch_static_bound(const Lattice &L, long long *list, unsigned long long *count, cudaStream_t st);
 void launch_mark_particles(const Lattice &L, cudaStream_t st);
 
 }  // namespace lbmg
