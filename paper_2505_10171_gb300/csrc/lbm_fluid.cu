@@ -250,13 +250,26 @@ __device__ __forceinline__ int wrap_any(int a, int n)
     return a < 0 ? a + n : a;
 }
 
+// owners of the neighbours of a node from the shared-memory flag ring
+template <int PW>
+struct GcNbr {
+    const uint8_t *fl[3];  // flag planes z-1, z, z+1
+    int c;                 // index of the node in the plane region
+    __device__ __forceinline__ int own(int dx, int dy, int dz) const
+    {
+        return fl[dz + 1][c + dy * PW + dx] & OWNER_MASK;
+    }
+};
+
 template <class R>
-__global__ void __launch_bounds__(GC_TX *GC_TY) k_gradcurv(Lattice L)
+__global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : 4) k_gradcurv(Lattice L)
 {
     constexpr int NT = GC_TX * GC_TY;
-    constexpr int PW = GC_TX + 4, PH = GC_TY + 4, PN = PW * PH;  // phi region
-    constexpr int NW = GC_TX + 2, NH = GC_TY + 2, NN = NW * NH;  // normal region
+    constexpr int PW = GC_TX + 4, PH = GC_TY + 4, PN = PW * PH;  // phi / flag region (2-node halo)
+    constexpr int NW = GC_TX + 2, NH = GC_TY + 2, NN = NW * NH;  // normal region (1-node halo)
+    constexpr int PER = (PN + NT - 1) / NT;                       // region values per thread
     __shared__ R phS[3][PN];
+    __shared__ uint8_t flS[4][PN];
     __shared__ R nS[3][3][NN];
 
     const long long item = blockIdx.x;
@@ -290,46 +303,69 @@ __global__ void __launch_bounds__(GC_TX *GC_TY) k_gradcurv(Lattice L)
     const bool active = gx < nx && gy < ny;
     const int niter = (z1 - z0) + 4;
 
+    // this thread's share of a plane region, prefetched one step ahead
+    int roff[PER];
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+        const int r = tid + q * NT;
+        roff[q] = r < PN ? wrap_any(y0 - 2 + r / PW, ny) * nx + wrap_any(x0 - 2 + r % PW, nx) : -1;
+    }
+    R pv[PER];
+    uint8_t fv[PER];
+    auto fetch = [&](int j) {
+        const int zo = wrap_any(z0 - 2 + j, nz) * ny * nx;
+#pragma unroll
+        for (int q = 0; q < PER; q++)
+            if (roff[q] >= 0) {
+                pv[q] = ph[zo + roff[q]];
+                fv[q] = fli[zo + roff[q]];
+            }
+    };
+    fetch(0);
+
     for (int j = 0; j < niter; j++) {
-        // (1) phi of plane z0-2+j
-        {
-            const int Z = wrap_any(z0 - 2 + j, nz);
-            R *dst = phS[j % 3];
-            for (int r = tid; r < PN; r += NT) {
-                const int X = wrap_any(x0 - 2 + r % PW, nx), Y = wrap_any(y0 - 2 + r / PW, ny);
-                dst[r] = ph[(Z * ny + Y) * nx + X];
+        // (1) plane z0-2+j into the rings, then fetch the next one
+#pragma unroll
+        for (int q = 0; q < PER; q++) {
+            const int r = tid + q * NT;
+            if (r < PN) {
+                phS[j % 3][r] = pv[q];
+                flS[j % 4][r] = fv[q];
             }
         }
+        if (j + 1 < niter) fetch(j + 1);
         __syncthreads();
-        // (2) normals of plane zz = z0-3+j on the 1-halo tile
+        // (2) normals of plane zz = z0-3+j (phi planes of steps j-2..j) on the 1-halo tile
         if (j >= 2) {
             const int zz = z0 - 3 + j;
             const int Z = wrap_any(zz, nz);
             const R *pm = phS[(j - 2) % 3], *p0 = phS[(j - 1) % 3], *pp = phS[j % 3];
             const bool own_plane = zz >= z0 && zz < z1;
+            GcNbr<PW> nb;
+            nb.fl[0] = flS[(j - 2) % 4];
+            nb.fl[1] = flS[(j - 1) % 4];
+            nb.fl[2] = flS[j % 4];
             for (int r1 = tid; r1 < NN; r1 += NT) {
                 const int ax = r1 % NW, ay = r1 / NW;
-                const int X = wrap_any(x0 - 1 + ax, nx), Y = wrap_any(y0 - 1 + ay, ny);
-                const int n = (Z * ny + Y) * nx + X;
-                const uint8_t fl = fli[n];
+                const int c = (ay + 1) * PW + (ax + 1);
+                const uint8_t fl = nb.fl[1][c];
                 R nn[3] = {0, 0, 0};
                 if ((fl & OWNER_MASK) == OWN_FLUID) {
-                    const int c = (ay + 1) * PW + (ax + 1);
                     auto phi_of = [&](int dx, int dy, int dz) {
                         const R *pl = dz < 0 ? pm : (dz > 0 ? pp : p0);
                         return pl[c + dy * PW + dx];
                     };
                     R gr[3];
                     grad_sum<R>(phi_of, gr);
+                    const int X = wrap_any(x0 - 1 + ax, nx), Y = wrap_any(y0 - 1 + ay, ny);
                     if (fl & BOUND_BIT) {
-                        GlobalNbr nb;
-                        nb.nb.init(X, Y, Z, nx, ny, nz);
-                        nb.fli = fli;
+                        nb.c = c;
                         grad_wet<R>(I, L.parts, nb, p0[c], fl, P.wet_max, X, Y, Z, gr);
                     }
                     const R m = reg_normal(gr, P.eps2, nn);
                     if (own_plane && ax >= 1 && ax <= GC_TX && ay >= 1 && ay <= GC_TY && x0 - 1 + ax < nx &&
                         y0 - 1 + ay < ny) {
+                        const int n = (Z * ny + Y) * nx + X;
                         Nn[n] = nn[0];
                         Nn[Nt + n] = nn[1];
                         Nn[2 * Nt + n] = nn[2];
@@ -342,25 +378,27 @@ __global__ void __launch_bounds__(GC_TX *GC_TY) k_gradcurv(Lattice L)
             }
         }
         __syncthreads();
-        // (3) curvature of plane z = z0-4+j
+        // (3) curvature of plane z = z0-4+j (normals of steps j-2..j, flags of steps j-3..j-1)
         if (j >= 4 && active) {
             const int z = z0 - 4 + j;
-            const int n = (z * ny + gy) * nx + gx;
-            const uint8_t fl = fli[n];
+            const int cp = (ly + 2) * PW + (lx + 2);
+            const uint8_t fl = flS[(j - 2) % 4][cp];
             if ((fl & OWNER_MASK) == OWN_FLUID) {
                 const int c = (ly + 1) * NW + (lx + 1);
                 const int sl[3] = {(j - 2) % 3, (j - 1) % 3, j % 3};
                 R kap = curvature<R>([&](int dx, int dy, int dz, int a) { return nS[sl[dz + 1]][a][c + dy * NW + dx]; });
                 if (fl & BOUND_BIT) {
-                    GlobalNbr nb;
-                    nb.nb.init(gx, gy, z, nx, ny, nz);
-                    nb.fli = fli;
+                    GcNbr<PW> fb;
+                    fb.fl[0] = flS[(j - 3) % 4];
+                    fb.fl[1] = flS[(j - 2) % 4];
+                    fb.fl[2] = flS[(j - 1) % 4];
+                    fb.c = cp;
                     kap = curvature<R>([&](int dx, int dy, int dz, int a) {
-                        if (nb.own(dx, dy, dz) != OWN_FLUID) return nS[sl[1]][a][c];
+                        if (fb.own(dx, dy, dz) != OWN_FLUID) return nS[sl[1]][a][c];
                         return nS[sl[dz + 1]][a][c + dy * NW + dx];
                     });
                 }
-                Kp[n] = kap;
+                Kp[(z * ny + gy) * nx + gx] = kap;
             }
         }
         __syncthreads();
