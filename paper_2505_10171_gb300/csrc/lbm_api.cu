@@ -379,7 +379,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
         const bool sur = c->force_model == LBM_FORCE_SURROGATE;
         if (sur) launch_surrogate_forces<S>(L, c->mlp, c->feat, c->stream, launches, mk);
         else launch_particle_forces<S>(L, cur, c->stream, launches, mk);
-        launch_dem(L, c->stream, launches, mk, !sur);
+        launch_dem<S>(L, c->stream, launches, mk, !sur);
         launch_geometry<S>(L, cur ^ 1, c->stream, launches, mk);
     });
     c->cur ^= 1;

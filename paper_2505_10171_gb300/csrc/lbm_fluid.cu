@@ -303,6 +303,17 @@ __global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : 4) k_gradcu
     const bool active = gx < nx && gy < ny;
     const int niter = (z1 - z0) + 4;
 
+    // this thread's columns of the 1-halo normal region (fixed for all planes)
+    constexpr int PER1 = (NN + NT - 1) / NT;
+    int nX[PER1], nY[PER1];
+    bool nOwn[PER1];
+#pragma unroll
+    for (int q = 0; q < PER1; q++) {
+        const int r1 = tid + q * NT, ax = r1 % NW, ay = r1 / NW;
+        nX[q] = wrap_any(x0 - 1 + ax, nx);
+        nY[q] = wrap_any(y0 - 1 + ay, ny);
+        nOwn[q] = r1 < NN && ax >= 1 && ax <= GC_TX && ay >= 1 && ay <= GC_TY && x0 - 1 + ax < nx && y0 - 1 + ay < ny;
+    }
     // this thread's share of a plane region, prefetched one step ahead
     int roff[PER];
 #pragma unroll
@@ -345,7 +356,10 @@ __global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : 4) k_gradcu
             nb.fl[0] = flS[(j - 2) % 4];
             nb.fl[1] = flS[(j - 1) % 4];
             nb.fl[2] = flS[j % 4];
-            for (int r1 = tid; r1 < NN; r1 += NT) {
+#pragma unroll
+            for (int q = 0; q < PER1; q++) {
+                const int r1 = tid + q * NT;
+                if (r1 >= NN) break;
                 const int ax = r1 % NW, ay = r1 / NW;
                 const int c = (ay + 1) * PW + (ax + 1);
                 const uint8_t fl = nb.fl[1][c];
@@ -357,14 +371,13 @@ __global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : 4) k_gradcu
                     };
                     R gr[3];
                     grad_sum<R>(phi_of, gr);
-                    const int X = wrap_any(x0 - 1 + ax, nx), Y = wrap_any(y0 - 1 + ay, ny);
+                    const int X = nX[q], Y = nY[q];
                     if (fl & BOUND_BIT) {
                         nb.c = c;
                         grad_wet<R>(I, L.parts, nb, p0[c], fl, P.wet_max, X, Y, Z, gr);
                     }
                     const R m = reg_normal(gr, P.eps2, nn);
-                    if (own_plane && ax >= 1 && ax <= GC_TX && ay >= 1 && ay <= GC_TY && x0 - 1 + ax < nx &&
-                        y0 - 1 + ay < ny) {
+                    if (own_plane && nOwn[q]) {
                         const int n = (Z * ny + Y) * nx + X;
                         Nn[n] = nn[0];
                         Nn[Nt + n] = nn[1];

@@ -247,14 +247,22 @@ struct Region {
         }
     }
     __device__ __forceinline__ long long count() const { return (long long)sz[0] * sz[1] * sz[2]; }
+    // node t of the cube (t < count < 2^31); lo + i lies in (-n, 2n), so one
+    // conditional wrap per axis suffices
     __device__ __forceinline__ void coord(long long t, int nx, int ny, int nz, int *x, int *y, int *z) const
     {
-        int i = (int)(t % sz[0]);
-        int j = (int)((t / sz[0]) % sz[1]);
-        int k = (int)(t / ((long long)sz[0] * sz[1]));
-        *x = ((lo[0] + i) % nx + nx) % nx;
-        *y = ((lo[1] + j) % ny + ny) % ny;
-        *z = ((lo[2] + k) % nz + nz) % nz;
+        const int tt = (int)t;
+        const int ij = tt / sz[0];
+        const int i = tt - ij * sz[0];
+        const int k = ij / sz[1];
+        const int j = ij - k * sz[1];
+        int a = lo[0] + i, b = lo[1] + j, c = lo[2] + k;
+        a += a < 0 ? nx : (a >= nx ? -nx : 0);
+        b += b < 0 ? ny : (b >= ny ? -ny : 0);
+        c += c < 0 ? nz : (c >= nz ? -nz : 0);
+        *x = a;
+        *y = b;
+        *z = c;
     }
 };
 
@@ -570,6 +578,7 @@ template <class S>
 void launch_geometry(const Lattice &L, int nxt, cudaStream_t st, long long *launches, const Marker &mk);
 // sum_fluid: gather the momentum-exchange and capillary partial sums first
 // (false when the surrogate has written the fluid forces)
+template <class S>
 void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk, bool sum_fluid);
 
 // ---------------------------------------------------------------------------

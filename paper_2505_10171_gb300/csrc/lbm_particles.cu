@@ -217,29 +217,35 @@ __global__ void k_part_sums(Lattice L)
 }
 
 // ---------------------------------------------------------------------------
-// DEM (Sec. III), FP64.
+// DEM (Sec. III).  Positions, velocities, spring histories and the Verlet
+// sums are FP64; the contact arithmetic runs in T: double in the FP64 mode,
+// float otherwise (FP64 issues at a small fraction of the FP32 rate here and
+// the DEM is one serial chain of dependent operations).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
-__device__ __forceinline__ void cross3(const double *a, const double *b, double *r)
+template <class T>
+__device__ __forceinline__ T dot3(const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <class T>
+__device__ __forceinline__ void cross3(const T *a, const T *b, T *r)
 {
-    double t0 = a[1] * b[2] - a[2] * b[1], t1 = a[2] * b[0] - a[0] * b[2], t2 = a[0] * b[1] - a[1] * b[0];
+    T t0 = a[1] * b[2] - a[2] * b[1], t1 = a[2] * b[0] - a[0] * b[2], t2 = a[0] * b[1] - a[1] * b[0];
     r[0] = t0; r[1] = t1; r[2] = t2;
 }
 
 // Luding spring: project on the tangent plane, trial force, Coulomb cap,
 // spring update (static: xi += v dt; sliding: xi = -(F + gamma v)/k).
-__device__ void dem_spring(double *xi, const double *n, const double *v, double k, double gam, double FC, double *F)
+template <class T>
+__device__ void dem_spring(T *xi, const T *n, const T *v, T k, T gam, T FC, T *F)
 {
-    double xn = dot3(xi, n);
+    T xn = dot3(xi, n);
     for (int a = 0; a < 3; a++) xi[a] -= xn * n[a];
-    double F0[3];
+    T F0[3];
     for (int a = 0; a < 3; a++) F0[a] = -k * xi[a] - gam * v[a];
-    double m = sqrt(dot3(F0, F0));
+    T m = sqrt(dot3(F0, F0));
     if (m <= FC) {
         for (int a = 0; a < 3; a++) { F[a] = F0[a]; xi[a] += v[a]; }
     } else {
         for (int a = 0; a < 3; a++) F[a] = FC * F0[a] / m;
-        for (int a = 0; a < 3; a++) xi[a] = k > 0.0 ? -(F[a] + gam * v[a]) / k : 0.0;
+        for (int a = 0; a < 3; a++) xi[a] = k > T(0) ? -(F[a] + gam * v[a]) / k : T(0);
     }
 }
 
@@ -248,41 +254,44 @@ __device__ void dem_spring(double *xi, const double *n, const double *v, double 
 // F_n = [k_n delta - g_n v_rel.n] n; rolling velocity -a'(w_i - w_j) x n with
 // torque -a' n x F_r on i (+a' n x F_r on j).  rec receives the force and
 // torque on i, then on j.
-__device__ void dem_contact(const InstDev &I, const PartDev *P, int i, int j, const double *vp, const double *wp,
-                            const double *n, double delta, double *xi, double *xir, double *rec)
+template <class T>
+__device__ void dem_contact(const InstDev &I, const PartDev *P, int i, int j, const T *vp, const T *wp, const T *n,
+                            T delta, T *xi, T *xir, T *rec)
 {
-    double bi[3], bj[3] = {0, 0, 0}, t[3], vi[3], vj[3];
-    for (int a = 0; a < 3; a++) bi[a] = -(P[i].Rc - 0.5 * delta) * n[a];
+    const T Rci = (T)P[i].Rc;
+    T bi[3], bj[3] = {0, 0, 0}, t[3], vi[3], vj[3];
+    for (int a = 0; a < 3; a++) bi[a] = -(Rci - T(0.5) * delta) * n[a];
     cross3(wp + 3 * i, bi, t);
     for (int a = 0; a < 3; a++) vi[a] = vp[3 * i + a] + t[a];
-    double ap;
+    T ap;
     if (j >= 0) {
-        for (int a = 0; a < 3; a++) bj[a] = (P[j].Rc - 0.5 * delta) * n[a];
+        const T Rcj = (T)P[j].Rc;
+        for (int a = 0; a < 3; a++) bj[a] = (Rcj - T(0.5) * delta) * n[a];
         cross3(wp + 3 * j, bj, t);
         for (int a = 0; a < 3; a++) vj[a] = vp[3 * j + a] + t[a];
-        ap = P[i].Rc * P[j].Rc / (P[i].Rc + P[j].Rc);
+        ap = Rci * Rcj / (Rci + Rcj);
     } else {
-        for (int a = 0; a < 3; a++) vj[a] = I.wall_u[a];
-        ap = P[i].Rc;
+        for (int a = 0; a < 3; a++) vj[a] = (T)I.wall_u[a];
+        ap = Rci;
     }
-    double vr[3];
+    T vr[3];
     for (int a = 0; a < 3; a++) vr[a] = vi[a] - vj[a];
-    const double vn = dot3(vr, n);
-    const double Fnm = I.kn * delta - I.gn * vn;
-    double vt[3];
+    const T vn = dot3(vr, n);
+    const T Fnm = (T)I.kn * delta - (T)I.gn * vn;
+    T vt[3];
     for (int a = 0; a < 3; a++) vt[a] = vr[a] - vn * n[a];
-    double Ft[3];
-    dem_spring(xi, n, vt, I.kt, I.gt, I.mu_s * fabs(Fnm), Ft);
-    double wrel[3], vrl[3];
-    for (int a = 0; a < 3; a++) wrel[a] = wp[3 * i + a] - (j >= 0 ? wp[3 * j + a] : 0.0);
+    T Ft[3];
+    dem_spring(xi, n, vt, (T)I.kt, (T)I.gt, (T)I.mu_s * fabs(Fnm), Ft);
+    T wrel[3], vrl[3];
+    for (int a = 0; a < 3; a++) wrel[a] = wp[3 * i + a] - (j >= 0 ? wp[3 * j + a] : T(0));
     cross3(wrel, n, vrl);
     for (int a = 0; a < 3; a++) vrl[a] *= -ap;
-    double Fr[3];
-    dem_spring(xir, n, vrl, I.kr, I.gr, I.mu_r * fabs(Fnm), Fr);
-    double Tt[3], Tr[3];
+    T Fr[3];
+    dem_spring(xir, n, vrl, (T)I.kr, (T)I.gr, (T)I.mu_r * fabs(Fnm), Fr);
+    T Tt[3], Tr[3];
     cross3(bi, Ft, Tt);
     cross3(n, Fr, Tr);
-    double mFt[3] = {-Ft[0], -Ft[1], -Ft[2]}, Ttj[3];
+    T mFt[3] = {-Ft[0], -Ft[1], -Ft[2]}, Ttj[3];
     cross3(bj, mFt, Ttj);
     for (int a = 0; a < 3; a++) {
         rec[a] = Fnm * n[a] + Ft[a];
@@ -292,17 +301,20 @@ __device__ void dem_contact(const InstDev &I, const PartDev *P, int i, int j, co
     }
 }
 
-__device__ void quat_rotate(double *q, const double *w)
+// orientation: exact rotation by |w| about w (unit quaternion, FP64 storage)
+template <class T>
+__device__ void quat_rotate(double *q, const T *w)
 {
-    double wm = sqrt(dot3(w, w));
-    if (wm == 0.0) return;
-    double h = 0.5 * wm, s = sin(h) / wm;
-    double d0 = cos(h), d1 = s * w[0], d2 = s * w[1], d3 = s * w[2];
-    double r0 = d0 * q[0] - d1 * q[1] - d2 * q[2] - d3 * q[3];
-    double r1 = d0 * q[1] + d1 * q[0] + d2 * q[3] - d3 * q[2];
-    double r2 = d0 * q[2] - d1 * q[3] + d2 * q[0] + d3 * q[1];
-    double r3 = d0 * q[3] + d1 * q[2] - d2 * q[1] + d3 * q[0];
-    double l = sqrt(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    T wm = sqrt(dot3(w, w));
+    if (wm == T(0)) return;
+    T h = T(0.5) * wm, s = sin(h) / wm;
+    T d0 = cos(h), d1 = s * w[0], d2 = s * w[1], d3 = s * w[2];
+    T q0 = (T)q[0], q1 = (T)q[1], q2 = (T)q[2], q3 = (T)q[3];
+    T r0 = d0 * q0 - d1 * q1 - d2 * q2 - d3 * q3;
+    T r1 = d0 * q1 + d1 * q0 + d2 * q3 - d3 * q2;
+    T r2 = d0 * q2 - d1 * q3 + d2 * q0 + d3 * q1;
+    T r3 = d0 * q3 + d1 * q2 - d2 * q1 + d3 * q0;
+    T l = sqrt(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
     q[0] = r0 / l; q[1] = r1 / l; q[2] = r2 / l; q[3] = r3 / l;
 }
 
@@ -327,6 +339,7 @@ __device__ __forceinline__ int pair_index(int i, int j, int np) { return i * np 
 // forces one thread per contact (substrate contacts, then pairs), kept per
 // contact; corrector per particle, adding its contacts in a fixed order
 // (substrate, then partners in increasing index).
+template <class T>
 __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
 {
     const InstDev &I = L.inst[blockIdx.x];
@@ -335,53 +348,60 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
     PartDev *P = L.parts + I.part_off;
     double *hist = L.hist + (long long)I.hist_off * 6;
     double *rec = L.crec + (long long)I.crec_off * 12;
-    __shared__ double xn[3 * DEM_MAXP], vp[3 * DEM_MAXP], wp[3 * DEM_MAXP];
+    __shared__ double xn[3 * DEM_MAXP];
+    __shared__ T vp[3 * DEM_MAXP], wp[3 * DEM_MAXP];
     const int tid = threadIdx.x;
     for (int p = tid; p < np; p += blockDim.x)
         for (int a = 0; a < 3; a++) {
             if (P[p].kin) {
                 xn[3 * p + a] = P[p].x[a] + P[p].v[a];
-                vp[3 * p + a] = P[p].v[a];
-                wp[3 * p + a] = P[p].w[a];
+                vp[3 * p + a] = (T)P[p].v[a];
+                wp[3 * p + a] = (T)P[p].w[a];
             } else {
                 const double acc = P[p].Fp[a] / P[p].m, alp = P[p].Tp[a] / P[p].I;
                 xn[3 * p + a] = P[p].x[a] + P[p].v[a] + 0.5 * acc;
-                vp[3 * p + a] = P[p].v[a] + acc;
-                wp[3 * p + a] = P[p].w[a] + alp;
+                vp[3 * p + a] = (T)(P[p].v[a] + acc);
+                wp[3 * p + a] = (T)(P[p].w[a] + alp);
             }
         }
     __syncthreads();
     const int npair = np * (np - 1) / 2;
     for (int c = tid; c < np + npair; c += blockDim.x) {
         double *r = rec + 12 * c;
-        for (int a = 0; a < 12; a++) r[a] = 0.0;
+        T rt[12];
+        for (int a = 0; a < 12; a++) rt[a] = T(0);
+        double *hs;
+        T xi[6];
+        bool touch = false;
         if (c < np) {
             // particle-substrate contact, delta = R_c - (z_p - 0.5); history record c
             const int p = c;
-            double *xi = hist + 6 * p, *xir = xi + 3;
+            hs = hist + 6 * p;
+            for (int a = 0; a < 6; a++) xi[a] = (T)hs[a];
             const double delta = P[p].Rc - (xn[3 * p + 2] - 0.5);
             if (I.wall_z0 && delta > 0.0) {
-                const double n[3] = {0.0, 0.0, 1.0};
-                dem_contact(I, P, p, -1, vp, wp, n, delta, xi, xir, r);
-            } else {
-                for (int a = 0; a < 6; a++) xi[a] = 0.0;
+                const T n[3] = {T(0), T(0), T(1)};
+                dem_contact<T>(I, P, p, -1, vp, wp, n, (T)delta, xi, xi + 3, rt);
+                touch = true;
             }
         } else {
             // particle pair, delta_ij = R_c,i + R_c,j - |X_i - X_j|; history record np + i*np + j
             int i, j;
             pair_of(c - np, np, &i, &j);
-            double *xi = hist + 6 * (np + i * np + j), *xir = xi + 3;
+            hs = hist + 6 * (np + i * np + j);
+            for (int a = 0; a < 6; a++) xi[a] = (T)hs[a];
             const double d[3] = {min_image(xn[3 * i] - xn[3 * j], I.nx), min_image(xn[3 * i + 1] - xn[3 * j + 1], I.ny),
                                  min_image(xn[3 * i + 2] - xn[3 * j + 2], I.nz)};
-            const double dl = sqrt(dot3(d, d));
+            const double dl = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
             const double delta = P[i].Rc + P[j].Rc - dl;
             if (delta > 0.0 && dl > 0.0) {
-                const double n[3] = {d[0] / dl, d[1] / dl, d[2] / dl};
-                dem_contact(I, P, i, j, vp, wp, n, delta, xi, xir, r);
-            } else {
-                for (int a = 0; a < 6; a++) xi[a] = 0.0;
+                const T n[3] = {(T)(d[0] / dl), (T)(d[1] / dl), (T)(d[2] / dl)};
+                dem_contact<T>(I, P, i, j, vp, wp, n, (T)delta, xi, xi + 3, rt);
+                touch = true;
             }
         }
+        for (int a = 0; a < 6; a++) hs[a] = touch ? (double)xi[a] : 0.0;
+        for (int a = 0; a < 12; a++) r[a] = (double)rt[a];
     }
     __syncthreads();
     for (int p = tid; p < np; p += blockDim.x) {
@@ -395,12 +415,12 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
             for (int a = 0; a < 3; a++) { Fc[a] += rp[off + a]; Tc[a] += rp[off + 3 + a]; }
         }
         PartDev &Q_ = P[p];
-        double F[3], T[3], wold[3];
+        double F[3], Tq[3], wold[3];
         for (int a = 0; a < 3; a++) {
             Q_.Fc[a] = Fc[a];
             Q_.Tc[a] = Tc[a];
             F[a] = Fc[a] + I.g_part[a] + Q_.Feta[a] + Q_.Fsig[a];
-            T[a] = Tc[a] + Q_.Teta[a] + Q_.Tsig[a];
+            Tq[a] = Tc[a] + Q_.Teta[a] + Q_.Tsig[a];
             wold[a] = Q_.w[a];
             Q_.x_old[a] = Q_.x[a];
             Q_.xfo[a] = Q_.xf[a];
@@ -408,16 +428,17 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
         if (!Q_.kin)
             for (int a = 0; a < 3; a++) {
                 Q_.v[a] += 0.5 * (Q_.Fp[a] + F[a]) / Q_.m;
-                Q_.w[a] += 0.5 * (Q_.Tp[a] + T[a]) / Q_.I;
+                Q_.w[a] += 0.5 * (Q_.Tp[a] + Tq[a]) / Q_.I;
             }
-        double wm[3] = {0.5 * (wold[0] + Q_.w[0]), 0.5 * (wold[1] + Q_.w[1]), 0.5 * (wold[2] + Q_.w[2])};
-        quat_rotate(Q_.q, wm);
+        const T wm[3] = {(T)(0.5 * (wold[0] + Q_.w[0])), (T)(0.5 * (wold[1] + Q_.w[1])),
+                         (T)(0.5 * (wold[2] + Q_.w[2]))};
+        quat_rotate<T>(Q_.q, wm);
         for (int a = 0; a < 3; a++) {
             if (fabs(xn[3 * p + a] - Q_.x[a]) >= GEOM_MARGIN - 1) atomicOr(L.status, ST_DISPLACEMENT);
             Q_.x[a] = xn[3 * p + a];
             Q_.xf[a] = (float)Q_.x[a];
             Q_.Fp[a] = F[a];
-            Q_.Tp[a] = T[a];
+            Q_.Tp[a] = Tq[a];
         }
     }
 }
@@ -604,15 +625,17 @@ void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long lon
     *launches += 2;
 }
 
+template <class S>
 void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk, bool sum_fluid)
 {
+    using R = typename Store<S>::real;
     if (L.n_parts == 0) return;
     mk(STAGE_DEM, 0);
     if (sum_fluid) {
         k_part_sums<<<L.n_parts, 32, 0, st>>>(L);
         *launches += 1;
     }
-    k_dem<<<L.n_inst, DEM_THREADS, 0, st>>>(L);
+    k_dem<R><<<L.n_inst, DEM_THREADS, 0, st>>>(L);
     mk(STAGE_DEM, 1);
     *launches += 1;
 }
@@ -653,7 +676,8 @@ void launch_boundary_full(const Lattice &L, int inst, long long N, cudaStream_t 
 
 #define INST(S)                                                                                             \
     template void launch_particle_forces<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &); \
-    template void launch_geometry<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &);
+    template void launch_geometry<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &);     \
+    template void launch_dem<S>(const Lattice &, cudaStream_t, long long *, const Marker &, bool);
 INST(double)
 INST(float)
 INST(__half)
