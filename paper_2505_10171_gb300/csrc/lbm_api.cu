@@ -38,6 +38,9 @@ struct lbm_ctx {
     bool stepped = false;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // side stream of the step: particle forces run beside the fluid kernels
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_grad = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph = nullptr;
     long long graph_launches = 0;
     long long last_launches = 0;
@@ -375,10 +378,38 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
     }
     dispatch(c->prec, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz);
         const bool sur = c->force_model == LBM_FORCE_SURROGATE;
-        if (sur) launch_surrogate_forces<S>(L, c->mlp, c->feat, c->stream, launches, mk);
-        else launch_particle_forces<S>(L, cur, c->stream, launches, mk);
+        // resolved forces beside the fluid kernels: the momentum exchange reads
+        // only the step's input populations (the fluid kernels write the other
+        // buffer), the capillary force only phi, n and |grad phi| once the
+        // gradient pass is done.  Profiling keeps one stream (per-kernel events).
+        const bool fork = !sur && !c->profile && L.n_parts > 0 && c->fz.form != FORM_FUSED;
+        if (fork) {
+            cudaEventRecord(c->ev_fork, c->stream);
+            cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+            launch_momentum_exchange<S>(L, cur, c->side, launches, mk);
+            struct Ctx2 {
+                lbm_ctx *c;
+                const Lattice *L;
+                long long *launches;
+                const Marker *mk;
+            } h2 = {c, &L, launches, &mk};
+            Hook hook;
+            hook.self = &h2;
+            hook.fn = [](void *p) {
+                Ctx2 *q = (Ctx2 *)p;
+                cudaEventRecord(q->c->ev_grad, q->c->stream);
+                cudaStreamWaitEvent(q->c->side, q->c->ev_grad, 0);
+                launch_capillary<S>(*q->L, q->c->side, q->launches, *q->mk);
+                cudaEventRecord(q->c->ev_join, q->c->side);
+            };
+            launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz, hook);
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+        } else {
+            launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz);
+            if (sur) launch_surrogate_forces<S>(L, c->mlp, c->feat, c->stream, launches, mk);
+            else launch_particle_forces<S>(L, cur, c->stream, launches, mk);
+        }
         launch_dem<S>(L, c->stream, launches, mk, !sur);
         launch_geometry<S>(L, cur ^ 1, c->stream, launches, mk);
     });
@@ -493,6 +524,10 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->diag_d);
     cudaFree(ctx->diag_part);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_grad) cudaEventDestroy(ctx->ev_grad);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     delete ctx;
 }
 
@@ -571,6 +606,13 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
             return LBM_ERR_CUDA;
         }
         ctx->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        lbm_destroy(ctx);
+        return LBM_ERR_CUDA;
     }
     auto alloc = [&](void **p, size_t bytes) -> lbm_status {
         cudaError_t e = cudaMalloc(p, bytes);

@@ -439,7 +439,7 @@ int fused_tile_y(int tile) { return tile == 1 ? 8 : 16; }
 
 template <class S>
 void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
-                       const FluidLaunch &fz)
+                       const FluidLaunch &fz, const Hook &after_grad)
 {
     using R = typename Store<S>::real;
     if (fz.form == FORM_FUSED) {
@@ -484,6 +484,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     mk(STAGE_GRAD, 0);
     k_gradcurv<R><<<(unsigned)fz.gc_items, GC_TX * GC_TY, 0, st>>>(L);
     mk(STAGE_GRAD, 1);
+    after_grad();
     mk(STAGE_COLLIDE, 0);
     if (staged) launch_staged_collide<S>(L, cur, fz, st);
     else k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
@@ -494,7 +495,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
 
 #define INST(S)                                                                                                   \
     template void launch_fluid_step<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &,            \
-                                       const FluidLaunch &);
+                                       const FluidLaunch &, const Hook &);
 INST(double)
 INST(float)
 INST(__half)

@@ -533,6 +533,17 @@ struct Marker {
     }
 };
 
+// host-side hook run by the fluid launcher once grad(phi), the normals and
+// the curvature of the step are final (plain and staged forms)
+struct Hook {
+    void (*fn)(void *self) = nullptr;
+    void *self = nullptr;
+    void operator()() const
+    {
+        if (fn) fn(self);
+    }
+};
+
 // host-side kernel launchers (defined in the .cu files)
 enum { FORM_STAGED = 0, FORM_FUSED = 1, FORM_PLAIN = 2 };
 struct FluidLaunch {
@@ -569,11 +580,17 @@ template <class S>
 void launch_fused_form(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
 template <class S>
 void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
-                       const FluidLaunch &fz);
+                       const FluidLaunch &fz, const Hook &after_grad = Hook());
 int fused_tile_x(int tile);
 int fused_tile_y(int tile);
 template <class S>
 void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk);
+// the two halves of it: momentum exchange (needs only the step's input
+// populations) and capillary force (needs the step's phi and normals)
+template <class S>
+void launch_momentum_exchange(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk);
+template <class S>
+void launch_capillary(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk);
 template <class S>
 void launch_geometry(const Lattice &L, int nxt, cudaStream_t st, long long *launches, const Marker &mk);
 // sum_fluid: gather the momentum-exchange and capillary partial sums first

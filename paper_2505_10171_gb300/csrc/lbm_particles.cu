@@ -612,17 +612,31 @@ __global__ void __launch_bounds__(PART_THREADS) k_mark(Lattice L, int side)
 
 // ---------------------------------------------------------------------------
 template <class S>
-void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk)
+void launch_momentum_exchange(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk)
 {
-    using R = typename Store<S>::real;
     if (L.n_parts == 0) return;
     mk(STAGE_MEM, 0);
     k_mem<S><<<dim3(L.mem_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, cur);
     mk(STAGE_MEM, 1);
+    *launches += 1;
+}
+
+template <class S>
+void launch_capillary(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk)
+{
+    using R = typename Store<S>::real;
+    if (L.n_parts == 0) return;
     mk(STAGE_CAPILLARY, 0);
     k_capillary<R><<<dim3(CAP_BLOCKS, L.n_parts), CAP_THREADS, 0, st>>>(L);
     mk(STAGE_CAPILLARY, 1);
-    *launches += 2;
+    *launches += 1;
+}
+
+template <class S>
+void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk)
+{
+    launch_momentum_exchange<S>(L, cur, st, launches, mk);
+    launch_capillary<S>(L, st, launches, mk);
 }
 
 template <class S>
@@ -676,6 +690,8 @@ void launch_boundary_full(const Lattice &L, int inst, long long N, cudaStream_t 
 
 #define INST(S)                                                                                             \
     template void launch_particle_forces<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &); \
+    template void launch_momentum_exchange<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &); \
+    template void launch_capillary<S>(const Lattice &, cudaStream_t, long long *, const Marker &);           \
     template void launch_geometry<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &);     \
     template void launch_dem<S>(const Lattice &, cudaStream_t, long long *, const Marker &, bool);
 INST(double)
