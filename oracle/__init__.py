@@ -46,6 +46,8 @@ class OrParams(ct.Structure):
         ("mu_s", ct.c_double), ("mu_r", ct.c_double), ("delta_R", ct.c_double),
         ("g_particle", ct.c_double * 3),
         ("grad_eps", ct.c_double), ("wet_phi_max", ct.c_double),
+        ("drop_speed_control", ct.c_int), ("drop_speed_target", ct.c_double * 3),
+        ("drop_speed_kp", ct.c_double), ("drop_speed_ki", ct.c_double), ("drop_speed_interval", ct.c_int),
     ]
 
 
@@ -88,6 +90,7 @@ def lib():
         L.or_num_particles.argtypes = [ct.c_void_p]
         L.or_num_particles.restype = i
         L.or_get_particles.argtypes = [ct.c_void_p, P(d)]
+        L.or_get_speed_control.argtypes = [ct.c_void_p, P(d)]
         L.or_get_diag.argtypes = [ct.c_void_p, P(d)]
         L.or_lattice.argtypes = [P(i), P(d), P(i)]
         L.or_mrt_matrices.argtypes = [P(d), P(d), P(d)]
@@ -118,6 +121,8 @@ DEFAULTS = dict(
     body_force_a=(0.0, 0.0, 0.0), body_force_b=(0.0, 0.0, 0.0),
     kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0,
     g_particle=(0.0, 0.0, 0.0), grad_eps=1e-4, wet_phi_max=0.99,
+    drop_speed_control=0, drop_speed_target=(0.0, 0.0, 0.0), drop_speed_kp=0.0, drop_speed_ki=0.0,
+    drop_speed_interval=0,
 )
 
 
@@ -226,6 +231,12 @@ class OracleSim:
         self.L.or_get_owner(self.h, o.ctypes.data_as(ct.POINTER(ct.c_ubyte)))
         return o
 
+    def speed_control(self):
+        """(body force on phase a now, phase-a velocity at the last controller update)."""
+        out = np.zeros(6)
+        self.L.or_get_speed_control(self.h, _dp(out))
+        return out[:3], out[3:]
+
     def particles(self):
         n = self.num_particles
         out = np.zeros((max(n, 1), 32))
@@ -290,7 +301,8 @@ def omega_of_phi(phi, rho, **kw):
 
 SIM_KEYS = ("wall_z0", "wall_velocity", "theta_wall_deg", "rho0", "nu_a", "nu_b", "sigma", "beta",
             "body_force_a", "body_force_b", "kn", "kt", "kr", "gn", "gt", "gr", "mu_s", "mu_r", "delta_R",
-            "g_particle", "grad_eps", "wet_phi_max")
+            "g_particle", "grad_eps", "wet_phi_max", "drop_speed_control", "drop_speed_target", "drop_speed_kp",
+            "drop_speed_ki", "drop_speed_interval")
 
 
 def from_workload(w) -> OracleSim:

@@ -174,6 +174,10 @@ struct or_sim {
     double xi_w[OR_MAXP][3], xir_w[OR_MAXP][3];
     double (*xi_p)[OR_MAXP][3], (*xir_p)[OR_MAXP][3];
     double diag[8];
+    long steps;              /* time steps taken                            */
+    double sp_f0[3];         /* body_force_a at creation (controller base)  */
+    double sp_int[3];        /* controller integral of the velocity error   */
+    double sp_u[3];          /* phase-a velocity at the last update          */
 };
 
 static inline int wrapi(int a, int n)
@@ -223,6 +227,7 @@ or_sim *or_create(const or_params *p)
     or_sim *s = (or_sim *)calloc(1, sizeof(or_sim));
     if (!s) return NULL;
     s->p = *p;
+    for (int a = 0; a < 3; a++) s->sp_f0[a] = p->body_force_a[a];
     s->nx = p->nx; s->ny = p->ny; s->nz = p->nz;
     s->N = (long)p->nx * p->ny * p->nz;
     long N = s->N;
@@ -1058,10 +1063,61 @@ void or_get_phi(const or_sim *s, double *phi)
     memcpy(phi, s->phi, sizeof(double) * s->N);
 }
 
+/* SURVEY c27 reading: the drop is driven by the body force on phase a.
+   Every `interval` steps the mass-weighted velocity of phase a over the fluid
+   nodes of the current (post-collision) state,
+       U_a = sum_x (rho^a / rho) j / sum_x rho^a,  j = sum_i c_i (f^a_i + f^b_i),
+   is compared with the target, e = U_target - U_a, and each controlled
+   component follows the PI law f_a = f0 + kp e + ki sum_k (e_k interval). */
+static void speed_control(or_sim *s)
+{
+    const or_params *p = &s->p;
+    double sa = 0.0, su[3] = {0.0, 0.0, 0.0};
+    for (long id = 0; id < s->N; id++) {
+        if (s->owner[id] != FLUID) continue;
+        double ra = 0.0, rb = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < OR_Q; i++) {
+            const double fa = s->fa[i * s->N + id], fb = s->fb[i * s->N + id];
+            ra += fa;
+            rb += fb;
+            for (int a = 0; a < 3; a++) j[a] += OR_C[i][a] * (fa + fb);
+        }
+        const double w = ra / (ra + rb);
+        for (int a = 0; a < 3; a++) su[a] += w * j[a];
+        sa += ra;
+    }
+    double kp = p->drop_speed_kp, ki = p->drop_speed_ki;
+    if (kp == 0.0 && ki == 0.0) {
+        kp = p->rho0 / 1000.0;
+        ki = kp / 5000.0;
+    }
+    const int iv = p->drop_speed_interval > 0 ? p->drop_speed_interval : 100;
+    for (int a = 0; a < 3; a++) {
+        s->sp_u[a] = sa > 0.0 ? su[a] / sa : 0.0;
+        if (!(p->drop_speed_control & (1 << a))) continue;
+        const double e = p->drop_speed_target[a] - s->sp_u[a];
+        s->sp_int[a] += e * iv;
+        s->p.body_force_a[a] = s->sp_f0[a] + kp * e + ki * s->sp_int[a];
+    }
+}
+
 int or_step(or_sim *s, int n)
 {
-    for (int t = 0; t < n; t++) step_once(s);
+    for (int t = 0; t < n; t++) {
+        step_once(s);
+        s->steps++;
+        const int iv = s->p.drop_speed_interval > 0 ? s->p.drop_speed_interval : 100;
+        if (s->p.drop_speed_control && s->steps % iv == 0) speed_control(s);
+    }
     return 0;
+}
+
+void or_get_speed_control(const or_sim *s, double *out)
+{
+    for (int a = 0; a < 3; a++) {
+        out[a] = s->p.body_force_a[a];
+        out[3 + a] = s->sp_u[a];
+    }
 }
 
 void or_get_pops(const or_sim *s, double *fa, double *fb)

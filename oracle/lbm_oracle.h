@@ -39,6 +39,10 @@ typedef struct {
     double g_particle[3];        /* external force on every particle       */
     double grad_eps;             /* eps of the normal g/sqrt(|g|^2+eps^2) */
     double wet_phi_max;          /* wetting applied where |phi| < this     */
+    int drop_speed_control;      /* bit a set: PI control of body_force_a[a] */
+    double drop_speed_target[3]; /* target mean velocity of phase a        */
+    double drop_speed_kp, drop_speed_ki;  /* PI gains; both 0: rho0/1000, rho0/(1000*5000) */
+    int drop_speed_interval;     /* steps between updates; 0: 100          */
 } or_params;
 
 typedef struct or_sim or_sim;
@@ -58,6 +62,8 @@ void    or_get_fields(const or_sim *s, double *rho_a, double *rho_b, double *phi
 void    or_get_grad(const or_sim *s, double *grad /* [3][N] */);
 void    or_get_owner(const or_sim *s, unsigned char *owner);
 int     or_num_particles(const or_sim *s);
+/* body force on phase a now and the phase-a velocity of the last controller update */
+void    or_get_speed_control(const or_sim *s, double *out /* [6] */);
 /* per particle 32 doubles: F_eta[3] T_eta[3] F_sig[3] T_sig[3] F_c[3] T_c[3]
    x[3] v[3] w[3] q[4] m */
 void    or_get_particles(const or_sim *s, double *out);

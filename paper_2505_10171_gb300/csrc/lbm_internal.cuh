@@ -152,33 +152,41 @@ struct Lattice {
     unsigned *status;
 };
 
+// streamed populations are read through the read-only path (measured on this
+// GPU: as fast as plain loads, faster than evict-first streaming loads)
+template <class T>
+__device__ __forceinline__ T pop_load(const T *p)
+{
+    return __ldg(p);
+}
+
 template <class S>
 struct Store;
 template <>
 struct Store<double> {
     using real = double;
-    static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ double ld(const double *p) { return pop_load(p); }
     static __device__ __forceinline__ double lds(const double *p) { return *p; }  // shared memory
     static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
 };
 template <>
 struct Store<float> {
     using real = float;
-    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld(const float *p) { return pop_load(p); }
     static __device__ __forceinline__ float lds(const float *p) { return *p; }  // shared memory
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
 };
 template <>
 struct Store<__half> {
     using real = float;
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(pop_load(p)); }
     static __device__ __forceinline__ float lds(const __half *p) { return __half2float(*p); }  // shared memory
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
 };
 template <>
 struct Store<__nv_bfloat16> {
     using real = float;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(pop_load(p)); }
     static __device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(*p); }  // shared memory
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };

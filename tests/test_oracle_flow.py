@@ -53,3 +53,36 @@ def test_component_mass_conserved_drop_on_sliding_wall():
     assert abs(f1["rho_a"].sum() - ma0) / ma0 < 1e-13
     assert abs(f1["rho_b"].sum() - mb0) / mb0 < 1e-13
     assert np.isfinite(f1["u"]).all()
+
+
+def test_drop_speed_controller_follows_the_pi_recurrence():
+    """SURVEY c27 reading: PI control of the phase-a body force.  In a uniform
+    single-phase periodic box Guo forcing adds exactly f to the momentum per
+    node and step, so the measured velocity after step t is U(t) = U(t-1) +
+    f(t)/rho0 and the force follows the PI law updated every `iv` steps; the
+    oracle must reproduce that scalar recurrence."""
+    n, iv, kp, ki, target, f0 = 6, 10, 2e-2, 1e-4, 1e-3, 2e-6
+    # run the oracle in pieces that straddle update points
+    s2 = O.OracleSim(n, n, n, body_force_a=(f0, 0.0, 0.0), drop_speed_control=1,
+                     drop_speed_target=(target, 0.0, 0.0), drop_speed_kp=kp, drop_speed_ki=ki,
+                     drop_speed_interval=iv)
+    s2.init_fields(np.ones(n ** 3))
+    U, f, integ, t, Ulast = 0.0, f0, 0.0, 0, 0.0
+    for chunk in (7, 3, 45, 145):
+        s2.step(chunk)
+        for _ in range(chunk):
+            t += 1
+            U += f
+            if t % iv == 0:
+                Ulast = U
+                e = target - U
+                integ += e * iv
+                f = f0 + kp * e + ki * integ
+        force, uref = s2.speed_control()
+        # the measured velocity is a momentum formed from O(0.1) populations:
+        # compare to absolute round-off
+        assert abs(uref[0] - Ulast) <= 1e-13
+        assert abs(force[0] - f) <= 1e-15
+        assert force[1] == 0.0 and force[2] == 0.0
+    # the controlled run approaches the target
+    assert abs(U - target) < 0.5 * target
