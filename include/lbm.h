@@ -104,6 +104,17 @@ typedef struct {
     double surrogate_u_ref;    /* surrogate inputs: velocity scale; 0 -> 1e-3             */
     double surrogate_r_ref;    /* surrogate inputs: radius scale; 0 -> 8                  */
     double surrogate_shell_gap;/* shell radius R_p + this; 0 -> 2                         */
+    /* drop-speed control (driving of the drop by body_force_a): bit a of
+     * drop_speed_control set -> every drop_speed_interval steps (0 -> 100) the
+     * mass-weighted velocity of phase a over the fluid nodes,
+     * U_a = sum (rho^a / rho) j / sum rho^a, j = sum_i c_i f_i, is compared with
+     * drop_speed_target and body_force_a[a] = f0 + kp e + ki sum(e interval),
+     * e = target - U_a, f0 = the body_force_a given here; kp = ki = 0 selects
+     * kp = rho0/1000, ki = kp/5000 */
+    int drop_speed_control;
+    double drop_speed_target[3];
+    double drop_speed_kp, drop_speed_ki;
+    int drop_speed_interval;
 } lbm_params;
 
 /* One rigid sphere (Sec. III, V).  R_c = R_p + delta_R; m = rho_p 4/3 pi R_p^3;
@@ -267,6 +278,11 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages);
  * the one array, so calls that overlap on the GPU race.  Asynchronous; returns
  * LBM_ERR_CUDA if the lookup or a launch fails. */
 lbm_status lbm_component_masses_noalloc(const double *pops, long long n_nodes, double *masses, void *stream);
+
+/* Drop-speed control state of an instance: out[0..2] the body force on phase
+ * a now, out[3..5] U_a at the last update (zeros before the first).
+ * Synchronises. */
+lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out);
 
 /* ---------------------------------------------------------------------------
  * Learned force surrogate (an extension of the method; the paper has none).

@@ -59,6 +59,9 @@ struct lbm_ctx {
     // fluid launch form: plain (default), staged or fused z-marching
     FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
+    // drop-speed control: per instance integral (3) and last U_a (3); block partials
+    double *speed_d = nullptr;
+    double *speed_part = nullptr;
     // static solid nodes next to non-static ones (built before the first step)
     long long *static_list = nullptr;
     long long n_static = 0;
@@ -299,6 +302,65 @@ __global__ void k_mass_final(const double *part, int nblk, double *out)
     }
 }
 
+// drop-speed control: FP64 sums over the fluid nodes of sum (rho^a/rho) j and
+// sum rho^a (per block), then one thread per instance applies the PI law to
+// the body force on phase a in the device instance table
+template <class S>
+__global__ void k_speed_partial(Lattice L, int cur, int inst, double *part)
+{
+    const InstDev &I = L.inst[inst];
+    const long long N = I.N;
+    const S *pop = (const S *)L.pop[cur] + NPOP * I.node_off;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+        if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
+        double sF = 0.0, sG = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < Q; i++) {
+            const double w = wgt<double>(i);
+            const double Fv = (double)Store<S>::ld(pop + (long long)i * N + n);
+            sF += w * Fv;
+            sG += w * (double)Store<S>::ld(pop + (long long)(Q + i) * N + n);
+            j[0] += w * cx(i) * Fv;
+            j[1] += w * cy(i) * Fv;
+            j[2] += w * cz(i) * Fv;
+        }
+        const double rr = 1.0 + sF;             // rho / rho0
+        const double ra = 0.5 * (rr + sG);      // rho^a / rho0
+        for (int a = 0; a < 3; a++) s[a] += ra / rr * I.rho0 * j[a];
+        s[3] += ra * I.rho0;
+    }
+    __shared__ double sh[4][256];
+    for (int a = 0; a < 4; a++) sh[a][threadIdx.x] = s[a];
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k)
+            for (int a = 0; a < 4; a++) sh[a][threadIdx.x] += sh[a][threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int a = 0; a < 4; a++) part[4 * blockIdx.x + a] = sh[a][0];
+}
+
+// state[0..2]: integral of the error, state[3..5]: U_a at the last update
+__global__ void k_speed_update(Lattice L, int inst, const double *part, int nblk, double *state)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < nblk; b++)
+        for (int a = 0; a < 4; a++) s[a] += part[4 * b + a];
+    InstDev &I = ((InstDev *)L.inst)[inst];
+    for (int a = 0; a < 3; a++) {
+        const double U = s[3] > 0.0 ? s[a] / s[3] : 0.0;
+        state[3 + a] = U;
+        if (!(I.sp_mask & (1 << a))) continue;
+        const double e = I.sp_target[a] - U;
+        state[a] += e * I.sp_interval;
+        const double f = I.sp_f0[a] + I.sp_kp * e + I.sp_ki * state[a];
+        I.body_a[a] = f;
+        I.f_body_a[a] = (float)f;
+    }
+}
+
 namespace lbmg {
 template <class S>
 void launch_init_fields(const Lattice &L, int cur, int inst, long long N, const double *phi, const double *rho,
@@ -416,6 +478,34 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
     c->cur ^= 1;
 }
 
+// the next step count (> steps) after which some instance updates its
+// drop-speed control; -1 if none does
+static long long next_speed_update(const lbm_ctx *ctx, long long steps)
+{
+    long long best = -1;
+    for (const auto &I : ctx->inst_h) {
+        if (!I.sp_mask) continue;
+        const long long t = (steps / I.sp_interval + 1) * I.sp_interval;
+        if (best < 0 || t < best) best = t;
+    }
+    return best;
+}
+
+static void take_speed(lbm_ctx *ctx, long long *launches)
+{
+    Lattice L = make_lattice(ctx);
+    for (int k = 0; k < ctx->n_inst; k++) {
+        const InstDev &I = ctx->inst_h[k];
+        if (!I.sp_mask || ctx->steps % I.sp_interval != 0) continue;
+        dispatch(ctx->prec, [&](auto *tag) {
+            using S = std::remove_pointer_t<decltype(tag)>;
+            k_speed_partial<S><<<DIAG_BLOCKS, 256, 0, ctx->stream>>>(L, ctx->cur, k, ctx->speed_part);
+        });
+        k_speed_update<<<1, 32, 0, ctx->stream>>>(L, k, ctx->speed_part, DIAG_BLOCKS, ctx->speed_d + 6 * k);
+        *launches += 2;
+    }
+}
+
 static lbm_status take_diag(lbm_ctx *ctx)
 {
     Lattice L = make_lattice(ctx);
@@ -458,6 +548,9 @@ static lbm_status validate(lbm_ctx *ctx, const lbm_params &p, int k)
         return bad("negative grad_eps / wet_phi_max / cap_norm / diag_interval");
     if (!(p.surrogate_u_ref >= 0) || !(p.surrogate_r_ref >= 0) || !(p.surrogate_shell_gap >= 0))
         return bad("negative surrogate_u_ref / surrogate_r_ref / surrogate_shell_gap");
+    if (p.drop_speed_control < 0 || p.drop_speed_control > 7 || p.drop_speed_interval < 0 ||
+        !finite3(p.drop_speed_target) || !std::isfinite(p.drop_speed_kp) || !std::isfinite(p.drop_speed_ki))
+        return bad("drop_speed_control must be a mask in [0, 7], drop_speed_interval >= 0, finite gains and target");
     return LBM_OK;
 }
 
@@ -507,6 +600,8 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->gmag);
     cudaFree(ctx->kap);
     cudaFree(ctx->static_list);
+    cudaFree(ctx->speed_d);
+    cudaFree(ctx->speed_part);
     mlp_free(ctx->mlp);
     cudaFree(ctx->feat);
     cudaFree(ctx->trX);
@@ -583,6 +678,18 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.sh_gap = p.surrogate_shell_gap > 0.0 ? p.surrogate_shell_gap : 2.0;
         I.sh_uref = p.surrogate_u_ref > 0.0 ? p.surrogate_u_ref : 1e-3;
         I.sh_rref = p.surrogate_r_ref > 0.0 ? p.surrogate_r_ref : 8.0;
+        I.sp_mask = p.drop_speed_control & 7;
+        I.sp_interval = p.drop_speed_interval > 0 ? p.drop_speed_interval : 100;
+        I.sp_kp = p.drop_speed_kp;
+        I.sp_ki = p.drop_speed_ki;
+        if (I.sp_kp == 0.0 && I.sp_ki == 0.0) {
+            I.sp_kp = p.rho0 / 1000.0;
+            I.sp_ki = I.sp_kp / 5000.0;
+        }
+        for (int a = 0; a < 3; a++) {
+            I.sp_target[a] = p.drop_speed_target[a];
+            I.sp_f0[a] = p.body_force_a[a];
+        }
         I.kn = p.kn; I.kt = p.kt; I.kr = p.kr;
         I.gn = p.gn; I.gt = p.gt; I.gr = p.gr;
         I.mu_s = p.mu_s; I.mu_r = p.mu_r; I.dR = p.delta_R;
@@ -630,6 +737,8 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc(&ctx->gmag, Nt * ctx->real_sz)) || (st = alloc(&ctx->kap, Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
         (st = alloc((void **)&ctx->diag_d, sizeof(double) * 2 * n_instances)) ||
         (st = alloc((void **)&ctx->diag_part, sizeof(double) * 2 * DIAG_BLOCKS)) ||
+        (st = alloc((void **)&ctx->speed_d, sizeof(double) * 6 * n_instances)) ||
+        (st = alloc((void **)&ctx->speed_part, sizeof(double) * 4 * DIAG_BLOCKS)) ||
         (any_u && (st = alloc(&ctx->u, 3 * Nt * ctx->real_sz)))) {
         std::string m = ctx->err;
         lbm_destroy(ctx);
@@ -663,6 +772,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     cudaMemsetAsync(ctx->kap, 0, Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->flags + Nt, 0, FLAG_PAD, ctx->stream);
     cudaMemsetAsync(ctx->diag_d, 0, sizeof(double) * 2 * n_instances, ctx->stream);
+    cudaMemsetAsync(ctx->speed_d, 0, sizeof(double) * 6 * n_instances, ctx->stream);
     if (ctx->u) cudaMemsetAsync(ctx->u, 0, 3 * Nt * ctx->real_sz, ctx->stream);
     // flags: substrate plane, then boundary bits
     std::vector<uint8_t> fl;
@@ -943,7 +1053,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     while (nsteps > 0) {
         int interval = 0;
         for (auto &p : ctx->P) interval = std::max(interval, p.diag_interval);
-        if (ctx->cur == 0 && nsteps >= 2 && !ctx->profile) {
+        // a controller update falls after the next step: take that step alone
+        const bool ctrl_next = next_speed_update(ctx, ctx->steps) == ctx->steps + 1;
+        if (ctx->cur == 0 && nsteps >= 2 && !ctx->profile && !ctrl_next) {
             if (!ctx->graph) {
                 cudaGraph_t g;
                 CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -961,6 +1073,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
             launches += ctx->graph_launches;
             nsteps -= 2;
             ctx->steps += 2;
+            take_speed(ctx, &launches);
             if (interval > 0 && (ctx->steps % interval == 0 || ctx->steps % interval == 1)) {
                 lbm_status s = take_diag(ctx);
                 if (s) return s;
@@ -970,6 +1083,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
             enqueue_step(ctx, &launches);
             nsteps -= 1;
             ctx->steps += 1;
+            take_speed(ctx, &launches);
             if (interval > 0 && ctx->steps % interval == 0) {
                 lbm_status s = take_diag(ctx);
                 if (s) return s;
@@ -1103,6 +1217,8 @@ lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
         return fail(ctx, LBM_ERR_ARG,
                     "form must be 0 (staged, tile 0..2), 1 (fused, tile 0..1) or 2 (plain, tile 0); zchunk >= 0");
     CU(cudaStreamSynchronize(ctx->stream));
+    // the device table is authoritative (the drop-speed control writes it)
+    CU(cudaMemcpy(ctx->inst_h.data(), ctx->inst_d, sizeof(InstDev) * ctx->n_inst, cudaMemcpyDeviceToHost));
     ctx->fz.form = form;
     ctx->fz.tile = tile;
     ctx->zc_request = zchunk;
@@ -1356,6 +1472,21 @@ lbm_status lbm_surrogate_features(lbm_ctx *ctx, int inst, float *out)
         CU(cudaStreamSynchronize(ctx->stream));
     }
     return check_status(ctx);
+}
+
+lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out)
+{
+    if (!ctx || !out || inst < 0 || inst >= ctx->n_inst) return fail(ctx, LBM_ERR_ARG, "bad instance or output");
+    CU(cudaStreamSynchronize(ctx->stream));
+    InstDev I;
+    CU(cudaMemcpy(&I, ctx->inst_d + inst, sizeof I, cudaMemcpyDeviceToHost));
+    double st[6];
+    CU(cudaMemcpy(st, ctx->speed_d + 6 * inst, sizeof st, cudaMemcpyDeviceToHost));
+    for (int a = 0; a < 3; a++) {
+        out[a] = I.body_a[a];
+        out[3 + a] = st[3 + a];
+    }
+    return LBM_OK;
 }
 
 }  // extern "C"

@@ -89,6 +89,10 @@ struct InstDev {
     // gc_nchunks z-chunks of gc_zc planes
     long long gc_item_start;
     int gc_tiles_x, gc_tiles_y, gc_nchunks, gc_zc;
+    // drop-speed control (body force on phase a): component mask, interval,
+    // target velocity, PI gains, base force
+    int sp_mask, sp_interval;
+    double sp_target[3], sp_kp, sp_ki, sp_f0[3];
 };
 
 // fluid parameters in the arithmetic precision R

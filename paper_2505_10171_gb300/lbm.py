@@ -54,6 +54,8 @@ class lbm_params(ct.Structure):
         ("grad_eps", ct.c_double), ("wet_phi_max", ct.c_double),
         ("store_velocity", ct.c_int), ("diag_interval", ct.c_int),
         ("surrogate_u_ref", ct.c_double), ("surrogate_r_ref", ct.c_double), ("surrogate_shell_gap", ct.c_double),
+        ("drop_speed_control", ct.c_int), ("drop_speed_target", ct.c_double * 3),
+        ("drop_speed_kp", ct.c_double), ("drop_speed_ki", ct.c_double), ("drop_speed_interval", ct.c_int),
     ]
 
 
@@ -72,7 +74,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
            "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
-           "lbm_surrogate_features"]
+           "lbm_surrogate_features", "lbm_drop_speed_state"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -127,6 +129,7 @@ def load(path: str = LIB_PATH):
     L.lbm_surrogate_gradient.argtypes = [vp, fp, fp, sz, fp, d]
     L.lbm_surrogate_train.argtypes = [vp, fp, fp, sz, i, i, ct.c_double, ct.c_uint64, d]
     L.lbm_surrogate_features.argtypes = [vp, i, fp]
+    L.lbm_drop_speed_state.argtypes = [vp, i, d]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
                         "lbm_last_launch_count"):
@@ -141,6 +144,8 @@ PARAM_DEFAULTS = dict(
     kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0, g_particle=(0.0, 0.0, 0.0),
     grad_eps=0.0, wet_phi_max=0.0, store_velocity=0, diag_interval=0,
     surrogate_u_ref=0.0, surrogate_r_ref=0.0, surrogate_shell_gap=0.0,
+    drop_speed_control=0, drop_speed_target=(0.0, 0.0, 0.0), drop_speed_kp=0.0, drop_speed_ki=0.0,
+    drop_speed_interval=0,
 )
 
 
@@ -292,6 +297,11 @@ class Context:
         out = np.zeros(2 * len(STAGES))
         self._check(self.L.lbm_profile_read(self.h, _dp(out), len(STAGES)))
         return {name: dict(launches=int(out[2 * k]), ms=float(out[2 * k + 1])) for k, name in enumerate(STAGES)}
+
+    def lbm_drop_speed_state(self, inst=0):
+        out = np.zeros(6)
+        self._check(self.L.lbm_drop_speed_state(self.h, inst, _dp(out)))
+        return out[:3], out[3:]
 
     # --- learned force surrogate --------------------------------------------
     def lbm_set_force_model(self, model):

@@ -315,3 +315,26 @@ def test_launch_forms_agree(prec, shape):
                 assert np.array_equal(a, b), ("fused", tile, zc)
             else:  # FMA contraction may differ between the two kernels
                 assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(a).max()), ("fused", tile, zc)
+
+def test_fp64_drop_speed_control_matches_oracle():
+    """Drop-speed control (PI on the phase-a body force, x component, every 10
+    steps) on a sessile drop: the controlled force, the measured phase-a
+    velocity and the populations after 65 steps (6 updates, one between the
+    two steps of a captured pair) against the oracle."""
+    nx, ny, nz = 40, 24, 20
+    p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=100.0, nu_a=1 / 6, nu_b=1 / 30,
+             body_force_a=(1e-6, 0.0, 0.0), drop_speed_control=1, drop_speed_target=(2e-3, 0.0, 0.0),
+             drop_speed_kp=1e-2, drop_speed_ki=5e-5, drop_speed_interval=10)
+    w = dict(params=p, phi=W.drop_phi(nx, ny, nz, (14.0, 12.0, 0.5), 7.0), particles=[])
+    o = run_oracle(w, 65)
+    sim = oracle_sim(w)
+    sim.step(65)
+    fo, uo = sim.speed_control()
+    c = gpu_ctx(w, "fp64")
+    c.lbm_step(65)
+    fg, ug = c.lbm_drop_speed_state()
+    c.close()
+    assert abs(fg[0] - fo[0]) <= 1e-12 * abs(fo[0]) and fg[1] == 0.0 and fg[2] == 0.0
+    assert np.all(np.abs(ug - uo) <= 1e-13)
+    assert fo[0] != 1e-6  # the controller acted
+    assert_fp64_parity(run_gpu(w, 65, "fp64"), o)
