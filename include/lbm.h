@@ -239,6 +239,15 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
  * Invalidates the step graph. */
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk);
 
+/* Autotuner: steps the simulation `steps` times (>= 2) in each available
+ * launch form and variant -- plain; staged tiles 0, 1, 2 (when available);
+ * fused tiles 0, 1 -- timing each with CUDA events on the context stream,
+ * and keeps the fastest.  The simulation advances by all the trial steps (every
+ * form computes the same update).  *form and *tile receive the choice;
+ * ms_per_step (may be NULL) receives 6 times in the order above, -1 for a
+ * form that is not available.  Synchronises. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step);
+
 /* The fluid-update form the next step runs: 0 staged, 1 fused, 2 plain (the
  * staged form falls back to plain when an instance's rows are not whole
  * 16-byte units); -1 for a null context. */

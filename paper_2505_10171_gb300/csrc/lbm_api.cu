@@ -1489,4 +1489,47 @@ lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out)
     return LBM_OK;
 }
 
+lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step)
+{
+    if (!ctx || !form || !tile || steps < 2) return fail(ctx, LBM_ERR_ARG, "autotune needs steps >= 2 and outputs");
+    const int cand[6][2] = {{FORM_PLAIN, 0}, {FORM_STAGED, 0}, {FORM_STAGED, 1}, {FORM_STAGED, 2}, {FORM_FUSED, 0},
+                            {FORM_FUSED, 1}};
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    double best = -1.0;
+    int bf = FORM_PLAIN, bt = 0;
+    lbm_status st = LBM_OK;
+    for (int k = 0; k < 6 && st == LBM_OK; k++) {
+        if (ms_per_step) ms_per_step[k] = -1.0;
+        if ((st = lbm_set_fluid_kernel(ctx, cand[k][0], cand[k][1], 0)) != LBM_OK) break;
+        if (lbm_fluid_form_in_use(ctx) != cand[k][0]) continue;  // staged form not available here
+        if ((st = lbm_step(ctx, 2)) != LBM_OK) break;            // capture and warm up
+        cudaEventRecord(e0, ctx->stream);
+        if ((st = lbm_step(ctx, steps)) != LBM_OK) break;
+        cudaEventRecord(e1, ctx->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(ctx, LBM_ERR_CUDA, "autotune: event");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / steps;
+        if (ms_per_step) ms_per_step[k] = per;
+        if (best < 0.0 || per < best) {
+            best = per;
+            bf = cand[k][0];
+            bt = cand[k][1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBM_OK) return st;
+    *form = bf;
+    *tile = bt;
+    st = lbm_set_fluid_kernel(ctx, bf, bt, 0);
+    if (st != LBM_OK) return st;
+    return check_status(ctx);
+}
+
 }  // extern "C"

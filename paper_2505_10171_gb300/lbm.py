@@ -74,7 +74,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
            "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
-           "lbm_surrogate_features", "lbm_drop_speed_state"]
+           "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH):
     L.lbm_surrogate_train.argtypes = [vp, fp, fp, sz, i, i, ct.c_double, ct.c_uint64, d]
     L.lbm_surrogate_features.argtypes = [vp, i, fp]
     L.lbm_drop_speed_state.argtypes = [vp, i, d]
+    L.lbm_autotune.argtypes = [vp, i, P(ct.c_int), P(ct.c_int), d]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
                         "lbm_last_launch_count"):
@@ -297,6 +298,13 @@ class Context:
         out = np.zeros(2 * len(STAGES))
         self._check(self.L.lbm_profile_read(self.h, _dp(out), len(STAGES)))
         return {name: dict(launches=int(out[2 * k]), ms=float(out[2 * k + 1])) for k, name in enumerate(STAGES)}
+
+    def lbm_autotune(self, steps=20):
+        """(form, tile) chosen and the per-candidate ms/step (plain, staged 0-2, fused 0-1; -1 unavailable)."""
+        f, t = ct.c_int(), ct.c_int()
+        ms = np.zeros(6)
+        self._check(self.L.lbm_autotune(self.h, int(steps), ct.byref(f), ct.byref(t), _dp(ms)))
+        return (f.value, t.value), ms
 
     def lbm_drop_speed_state(self, inst=0):
         out = np.zeros(6)

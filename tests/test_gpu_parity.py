@@ -338,3 +338,26 @@ def test_fp64_drop_speed_control_matches_oracle():
     assert np.all(np.abs(ug - uo) <= 1e-13)
     assert fo[0] != 1e-6  # the controller acted
     assert_fp64_parity(run_gpu(w, 65, "fp64"), o)
+
+
+def test_autotune_picks_a_form_and_keeps_the_trajectory():
+    """The autotuner times all six launch forms/variants (8 steps each here)
+    and keeps the fastest; since every form gives the same FP32 bits, the state
+    afterwards equals 48 plain steps."""
+    from paper_2505_10171_gb300 import lbm
+    w = _forms_workload(48, 24, 20)
+    c = gpu_ctx(w, "fp32")
+    (form, tile), ms = c.lbm_autotune(6)
+    assert np.all(ms > 0.0), ms
+    assert c.lbm_fluid_form_in_use() == form and ms[[0, 1, 2, 3, 4, 5].index(
+        {(2, 0): 0, (0, 0): 1, (0, 1): 2, (0, 2): 3, (1, 0): 4, (1, 1): 5}[(form, tile)])] == ms.min()
+    fa, fb = c.pops()
+    parts = c.lbm_particle_forces()
+    c.close()
+    c = gpu_ctx(w, "fp32")
+    c.lbm_set_fluid_kernel(lbm.FORM_PLAIN)
+    c.lbm_step(48)
+    ra, rb = c.pops()
+    assert np.array_equal(fa, ra) and np.array_equal(fb, rb)
+    assert np.array_equal(parts, c.lbm_particle_forces())
+    c.close()
