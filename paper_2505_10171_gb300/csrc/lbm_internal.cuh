@@ -203,6 +203,13 @@ __host__ __device__ __forceinline__ double min_image(double d, int n)
     return d >= h ? d - n : (d < -h ? d + n : d);
 }
 
+// the same in single precision (|d| < 3n/2)
+__device__ __forceinline__ float min_image_f(float d, int n)
+{
+    const float h = 0.5f * n;
+    return d >= h ? d - n : (d < -h ? d + n : d);
+}
+
 // periodic neighbourhood of one node: x coordinates and row/plane offsets of
 // x-1..x+1, y-1..y+1, z-1..z+1 (instance-local 32-bit node indices; every
 // instance has fewer than 2^31/38 nodes)
@@ -424,8 +431,18 @@ __device__ __forceinline__ void wetting_rotate(R *g, const R *ns, R cth, R sth)
     R st[3] = {-g[0] / gm, -g[1] / gm, -g[2] / gm};
     R ca = ns[0] * st[0] + ns[1] * st[1] + ns[2] * st[2];
     ca = ca > R(1) ? R(1) : (ca < R(-1) ? R(-1) : ca);
-    R al = acos(ca);
-    R sa = sin(al), cal = cos(al);
+    // cos and sin of the angle alpha* between n* and n_s: the FP64 path takes
+    // acos / sin / cos as the oracle does; single precision uses cos alpha* and
+    // sqrt(1 - cos^2) (alpha* in [0, pi]), which needs no transcendental calls
+    R sa, cal;
+    if (sizeof(R) == 8) {
+        const R al = acos(ca);
+        sa = sin(al);
+        cal = cos(al);
+    } else {
+        cal = ca;
+        sa = sqrt(R(1) - ca * ca);
+    }
     if (sa < R(1e-4)) return;  // contact-line direction undefined (n* parallel to n_s)
     R ap1 = cth - sth * cal / sa, ap2 = sth / sa;
     R am1 = cth + sth * cal / sa, am2 = -sth / sa;

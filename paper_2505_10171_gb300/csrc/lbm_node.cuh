@@ -33,9 +33,11 @@ template <class R, class A>
 __device__ __forceinline__ bool solid_normal(const InstDev &I, const PartDev *parts, const A &nbr, int x, int y,
                                              int z, R *ns, R *cth, R *sth)
 {
+    // arithmetic in R: FP64 in the FP64 mode, FP32 (with the float copies of
+    // the particle centres) otherwise
     int best = -1;
-    double bestd = 0.0;
-    double ws[3] = {0.0, 0.0, 0.0};
+    R bestd = 0;
+    R ws[3] = {0, 0, 0};
     bool any = false;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
@@ -43,15 +45,21 @@ __device__ __forceinline__ bool solid_normal(const InstDev &I, const PartDev *pa
         if (own == OWN_FLUID) continue;
         any = true;
         if (own == OWN_WALL) {
-            ws[0] -= wgt<double>(i) * cx(i);
-            ws[1] -= wgt<double>(i) * cy(i);
-            ws[2] -= wgt<double>(i) * cz(i);
+            ws[0] -= wgt<R>(i) * cx(i);
+            ws[1] -= wgt<R>(i) * cy(i);
+            ws[2] -= wgt<R>(i) * cz(i);
         } else {
             const PartDev &P = parts[I.part_off + own - 2];
-            double d0 = min_image(x - P.x[0], I.nx), d1 = min_image(y - P.x[1], I.ny),
-                   d2 = min_image(z - P.x[2], I.nz);
-            double dist = sqrt(d0 * d0 + d1 * d1 + d2 * d2) - P.R;
-            int p = own - 2;
+            R d0, d1, d2;
+            if (sizeof(R) == 8) {
+                d0 = (R)min_image(x - P.x[0], I.nx); d1 = (R)min_image(y - P.x[1], I.ny);
+                d2 = (R)min_image(z - P.x[2], I.nz);
+            } else {
+                d0 = (R)min_image_f((float)x - P.xf[0], I.nx); d1 = (R)min_image_f((float)y - P.xf[1], I.ny);
+                d2 = (R)min_image_f((float)z - P.xf[2], I.nz);
+            }
+            const R dist = sqrt(d0 * d0 + d1 * d1 + d2 * d2) - (R)P.R;
+            const int p = own - 2;
             if (best < 0 || dist < bestd || (dist == bestd && p < best)) {
                 best = p;
                 bestd = dist;
@@ -61,16 +69,23 @@ __device__ __forceinline__ bool solid_normal(const InstDev &I, const PartDev *pa
     if (!any) return false;
     if (best >= 0) {
         const PartDev &P = parts[I.part_off + best];
-        double d0 = min_image(x - P.x[0], I.nx), d1 = min_image(y - P.x[1], I.ny), d2 = min_image(z - P.x[2], I.nz);
-        double dl = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-        ns[0] = (R)(d0 / dl); ns[1] = (R)(d1 / dl); ns[2] = (R)(d2 / dl);
+        R d0, d1, d2;
+        if (sizeof(R) == 8) {
+            d0 = (R)min_image(x - P.x[0], I.nx); d1 = (R)min_image(y - P.x[1], I.ny);
+            d2 = (R)min_image(z - P.x[2], I.nz);
+        } else {
+            d0 = (R)min_image_f((float)x - P.xf[0], I.nx); d1 = (R)min_image_f((float)y - P.xf[1], I.ny);
+            d2 = (R)min_image_f((float)z - P.xf[2], I.nz);
+        }
+        const R dl = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+        ns[0] = d0 / dl; ns[1] = d1 / dl; ns[2] = d2 / dl;
         *cth = (R)P.cos_t;
         *sth = (R)P.sin_t;
         return true;
     }
-    double wl = sqrt(ws[0] * ws[0] + ws[1] * ws[1] + ws[2] * ws[2]);
-    if (wl == 0.0) return false;
-    ns[0] = (R)(ws[0] / wl); ns[1] = (R)(ws[1] / wl); ns[2] = (R)(ws[2] / wl);
+    const R wl = sqrt(ws[0] * ws[0] + ws[1] * ws[1] + ws[2] * ws[2]);
+    if (wl == R(0)) return false;
+    ns[0] = ws[0] / wl; ns[1] = ws[1] / wl; ns[2] = ws[2] / wl;
     *cth = (R)I.cos_tw;
     *sth = (R)I.sin_tw;
     return true;
