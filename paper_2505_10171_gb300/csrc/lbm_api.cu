@@ -473,7 +473,19 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
             else launch_particle_forces<S>(L, cur, c->stream, launches, mk);
         }
         launch_dem<S>(L, c->stream, launches, mk, !sur);
-        launch_geometry<S>(L, cur ^ 1, c->stream, launches, mk);
+        // geometry: owners first; then boundary bits (side stream) beside the
+        // refill of uncovered nodes (they touch disjoint data)
+        if (!c->profile && L.n_parts > 0) {
+            launch_geom_owner(L, c->stream, launches, mk);
+            cudaEventRecord(c->ev_fork, c->stream);
+            cudaStreamWaitEvent(c->side, c->ev_fork, 0);
+            launch_geom_bound(L, c->side, launches, mk);
+            cudaEventRecord(c->ev_join, c->side);
+            launch_refill<S>(L, cur ^ 1, c->stream, launches, mk);
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+        } else {
+            launch_geometry<S>(L, cur ^ 1, c->stream, launches, mk);
+        }
     });
     c->cur ^= 1;
 }
@@ -931,6 +943,8 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
         d.Rc = q.R_p + p.delta_R;
         d.m = q.rho_p * 4.0 / 3.0 * M_PI * q.R_p * q.R_p * q.R_p;
         d.I = 0.4 * d.m * q.R_p * q.R_p;
+        d.inv_m = 1.0 / d.m;
+        d.inv_I = 1.0 / d.I;
         double th = q.theta_deg * M_PI / 180.0;
         d.cos_t = std::cos(th);
         d.sin_t = std::sin(th);

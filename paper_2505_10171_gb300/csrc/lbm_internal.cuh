@@ -120,6 +120,7 @@ struct PartDev {
     double x[3], v[3], w[3], q[4];
     double x_old[3];
     double R, Rc, m, I, cos_t, sin_t;
+    double inv_m, inv_I;  // 1/m, 1/I
     double Fp[3], Tp[3];
     double Feta[3], Teta[3], Fsig[3], Tsig[3], Fc[3], Tc[3];
     float xf[3], xfo[3];  // single-precision copies of x and x_old
@@ -622,6 +623,12 @@ template <class S>
 void launch_capillary(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk);
 template <class S>
 void launch_geometry(const Lattice &L, int nxt, cudaStream_t st, long long *launches, const Marker &mk);
+// its three parts: owners and fresh bits (first), then boundary bits and the
+// refill of fresh nodes, which touch disjoint data and may run concurrently
+void launch_geom_owner(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk);
+void launch_geom_bound(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk);
+template <class S>
+void launch_refill(const Lattice &L, int nxt, cudaStream_t st, long long *launches, const Marker &mk);
 // sum_fluid: gather the momentum-exchange and capillary partial sums first
 // (false when the surrogate has written the fluid forces)
 template <class S>

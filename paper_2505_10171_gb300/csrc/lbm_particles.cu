@@ -2,10 +2,12 @@
 //   k_mem        momentum-exchange force and torque per particle (Sec. V B)
 //   k_capillary  capillary force and torque from the Lagrangian surface points
 //                (Sec. V E)
-//   k_part_sums  fixed-order sums of the per-block partials of both
-//   k_dem        contacts (normal spring-dashpot, Luding sliding and rolling
-//                friction) and velocity-Verlet update, FP64 (Sec. III): one
-//                thread per contact, then one per particle
+//   k_dem        fixed-order sums of the per-block partials of both, then
+//                contacts (normal spring-dashpot, Luding sliding and rolling
+//                friction) and velocity-Verlet update (Sec. III): one warp per
+//                particle for the sums, one thread per contact, then one per
+//                particle; positions and velocities FP64, contact arithmetic
+//                FP64 in the FP64 mode and FP32 otherwise
 //   k_geom_*     solid map update and refilling of uncovered nodes (Sec. V C)
 // Per-link and per-point arithmetic runs in the storage precision's arithmetic
 // type (double for FP64 storage, float otherwise); every sum over links,
@@ -192,29 +194,6 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
     block_sum6(acc, L.cap_part + ((long long)p * CAP_BLOCKS + blockIdx.x) * 6);
 }
 
-// fluid forces of this step: each particle's block partials of the momentum
-// exchange and capillary kernels summed by one warp, lanes over a fixed
-// block stride and then a fixed shuffle tree (deterministic)
-__global__ void k_part_sums(Lattice L)
-{
-    const int p = blockIdx.x;
-    const int lane = threadIdx.x;
-    double s[12];
-    for (int a = 0; a < 12; a++) s[a] = 0.0;
-    for (int b = lane; b < L.mem_blocks; b += 32)
-        for (int a = 0; a < 6; a++) s[a] += L.mem_part[((long long)p * L.mem_blocks + b) * 6 + a];
-    for (int b = lane; b < CAP_BLOCKS; b += 32)
-        for (int a = 0; a < 6; a++) s[6 + a] += L.cap_part[((long long)p * CAP_BLOCKS + b) * 6 + a];
-    for (int o = 16; o > 0; o >>= 1)
-        for (int a = 0; a < 12; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
-    if (lane == 0) {
-        PartDev &P = L.parts[p];
-        for (int a = 0; a < 3; a++) {
-            P.Feta[a] = s[a]; P.Teta[a] = s[3 + a];
-            P.Fsig[a] = s[6 + a]; P.Tsig[a] = s[9 + a];
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // DEM (Sec. III).  Positions, velocities, spring histories and the Verlet
@@ -340,7 +319,7 @@ __device__ __forceinline__ int pair_index(int i, int j, int np) { return i * np 
 // contact; corrector per particle, adding its contacts in a fixed order
 // (substrate, then partners in increasing index).
 template <class T>
-__global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
+__global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
 {
     const InstDev &I = L.inst[blockIdx.x];
     const int np = I.np;
@@ -351,6 +330,29 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
     __shared__ double xn[3 * DEM_MAXP];
     __shared__ T vp[3 * DEM_MAXP], wp[3 * DEM_MAXP];
     const int tid = threadIdx.x;
+    if (sum_fluid) {
+        // fluid forces of this step: a warp per particle sums the block
+        // partials of the momentum-exchange and capillary kernels, lanes over
+        // a fixed block stride, then a fixed shuffle tree (deterministic)
+        const int lane = tid & 31, wid = tid >> 5;
+        for (int p = wid; p < np; p += DEM_THREADS / 32) {
+            const long long pg = I.part_off + p;
+            double s[12];
+            for (int a = 0; a < 12; a++) s[a] = 0.0;
+            for (int b = lane; b < L.mem_blocks; b += 32)
+                for (int a = 0; a < 6; a++) s[a] += L.mem_part[(pg * L.mem_blocks + b) * 6 + a];
+            for (int b = lane; b < CAP_BLOCKS; b += 32)
+                for (int a = 0; a < 6; a++) s[6 + a] += L.cap_part[(pg * CAP_BLOCKS + b) * 6 + a];
+            for (int o = 16; o > 0; o >>= 1)
+                for (int a = 0; a < 12; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
+            if (lane == 0)
+                for (int a = 0; a < 3; a++) {
+                    P[p].Feta[a] = s[a]; P[p].Teta[a] = s[3 + a];
+                    P[p].Fsig[a] = s[6 + a]; P[p].Tsig[a] = s[9 + a];
+                }
+        }
+        __syncthreads();
+    }
     for (int p = tid; p < np; p += blockDim.x)
         for (int a = 0; a < 3; a++) {
             if (P[p].kin) {
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
                 vp[3 * p + a] = (T)P[p].v[a];
                 wp[3 * p + a] = (T)P[p].w[a];
             } else {
-                const double acc = P[p].Fp[a] / P[p].m, alp = P[p].Tp[a] / P[p].I;
+                const double acc = P[p].Fp[a] * P[p].inv_m, alp = P[p].Tp[a] * P[p].inv_I;
                 xn[3 * p + a] = P[p].x[a] + P[p].v[a] + 0.5 * acc;
                 vp[3 * p + a] = (T)(P[p].v[a] + acc);
                 wp[3 * p + a] = (T)(P[p].w[a] + alp);
@@ -427,8 +429,8 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L)
         }
         if (!Q_.kin)
             for (int a = 0; a < 3; a++) {
-                Q_.v[a] += 0.5 * (Q_.Fp[a] + F[a]) / Q_.m;
-                Q_.w[a] += 0.5 * (Q_.Tp[a] + Tq[a]) / Q_.I;
+                Q_.v[a] += 0.5 * (Q_.Fp[a] + F[a]) * Q_.inv_m;
+                Q_.w[a] += 0.5 * (Q_.Tp[a] + Tq[a]) * Q_.inv_I;
             }
         const T wm[3] = {(T)(0.5 * (wold[0] + Q_.w[0])), (T)(0.5 * (wold[1] + Q_.w[1])),
                          (T)(0.5 * (wold[2] + Q_.w[2]))};
@@ -555,20 +557,38 @@ __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int
         if (!(fli[n] & FRESH_BIT)) continue;
         R sF = 0, sG = 0;
         int nf = 0;
-        for (int hop = 1; hop <= 2 && nf == 0; hop++)
+        for (int hop = 1; hop <= 2 && nf == 0; hop++) {
+            // the qualifying neighbours (fluid, not fresh) first, so that the
+            // population loads below are independent of one another
+            int nbr[Q - 1];
+            bool ok[Q - 1];
+#pragma unroll
             for (int i = 1; i < Q; i++) {
                 int X = ((x + hop * cx(i)) % I.nx + I.nx) % I.nx;
                 int Y = ((y + hop * cy(i)) % I.ny + I.ny) % I.ny;
                 int Z = ((z + hop * cz(i)) % I.nz + I.nz) % I.nz;
-                const int m = (Z * I.ny + Y) * I.nx + X;
-                uint8_t fm = fli[m];
-                if ((fm & OWNER_MASK) != OWN_FLUID || (fm & FRESH_BIT)) continue;
+                nbr[i - 1] = (Z * I.ny + Y) * I.nx + X;
+            }
+#pragma unroll
+            for (int i = 0; i < Q - 1; i++) {
+                const uint8_t fm = fli[nbr[i]];
+                ok[i] = (fm & OWNER_MASK) == OWN_FLUID && !(fm & FRESH_BIT);
+            }
+#pragma unroll 2
+            for (int i = 0; i < Q - 1; i++) {
+                if (!ok[i]) continue;
+                const int m = nbr[i];
+                R aF = 0, aG = 0;
+#pragma unroll
                 for (int j = 0; j < Q; j++) {
-                    sF += wgt<R>(j) * (R(1) + Store<S>::ld(pop + j * N + m));
-                    sG += wgt<R>(j) * Store<S>::ld(pop + (Q + j) * N + m);
+                    aF += wgt<R>(j) * (R(1) + Store<S>::ld(pop + j * N + m));
+                    aG += wgt<R>(j) * Store<S>::ld(pop + (Q + j) * N + m);
                 }
+                sF += aF;
+                sG += aG;
                 nf++;
             }
+        }
         // mean rho/rho0 and (rho^a - rho^b)/rho0 of the neighbours
         R rr, rd;
         if (nf > 0) { rr = sF / nf; rd = sG / nf; }
@@ -645,32 +665,47 @@ void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Ma
     using R = typename Store<S>::real;
     if (L.n_parts == 0) return;
     mk(STAGE_DEM, 0);
-    if (sum_fluid) {
-        k_part_sums<<<L.n_parts, 32, 0, st>>>(L);
-        *launches += 1;
-    }
-    k_dem<R><<<L.n_inst, DEM_THREADS, 0, st>>>(L);
+    k_dem<R><<<L.n_inst, DEM_THREADS, 0, st>>>(L, sum_fluid ? 1 : 0);
     mk(STAGE_DEM, 1);
+    *launches += 1;
+}
+
+void launch_geom_owner(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk)
+{
+    if (L.n_parts == 0) return;
+    // region sides: owner/refill cover the solid of the last two positions,
+    // the boundary pass one more node around
+    mk(STAGE_GEOM_OWNER, 0);
+    k_geom_owner<<<dim3(L.geom_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, L.geom_side);
+    mk(STAGE_GEOM_OWNER, 1);
+    *launches += 1;
+}
+
+void launch_geom_bound(const Lattice &L, cudaStream_t st, long long *launches, const Marker &mk)
+{
+    if (L.n_parts == 0) return;
+    mk(STAGE_GEOM_BOUND, 0);
+    k_geom_bound<<<dim3(L.geom_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, L.geom_side + 2);
+    mk(STAGE_GEOM_BOUND, 1);
+    *launches += 1;
+}
+
+template <class S>
+void launch_refill(const Lattice &L, int nxt, cudaStream_t st, long long *launches, const Marker &mk)
+{
+    if (L.n_parts == 0) return;
+    mk(STAGE_REFILL, 0);
+    k_refill<S><<<dim3(L.geom_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, nxt, L.geom_side);
+    mk(STAGE_REFILL, 1);
     *launches += 1;
 }
 
 template <class S>
 void launch_geometry(const Lattice &L, int nxt, cudaStream_t st, long long *launches, const Marker &mk)
 {
-    if (L.n_parts == 0) return;
-    // region sides: owner/refill cover the solid of the last two positions,
-    // the boundary pass one more node around
-    const int side = L.geom_side;
-    mk(STAGE_GEOM_OWNER, 0);
-    k_geom_owner<<<dim3(L.geom_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, side);
-    mk(STAGE_GEOM_OWNER, 1);
-    mk(STAGE_GEOM_BOUND, 0);
-    k_geom_bound<<<dim3(L.geom_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, side + 2);
-    mk(STAGE_GEOM_BOUND, 1);
-    mk(STAGE_REFILL, 0);
-    k_refill<S><<<dim3(L.geom_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, nxt, side);
-    mk(STAGE_REFILL, 1);
-    *launches += 3;
+    launch_geom_owner(L, st, launches, mk);
+    launch_geom_bound(L, st, launches, mk);
+    launch_refill<S>(L, nxt, st, launches, mk);
 }
 
 void launch_mark_particles(const Lattice &L, cudaStream_t st)
@@ -693,7 +728,8 @@ void launch_boundary_full(const Lattice &L, int inst, long long N, cudaStream_t 
     template void launch_momentum_exchange<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &); \
     template void launch_capillary<S>(const Lattice &, cudaStream_t, long long *, const Marker &);           \
     template void launch_geometry<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &);     \
-    template void launch_dem<S>(const Lattice &, cudaStream_t, long long *, const Marker &, bool);
+    template void launch_dem<S>(const Lattice &, cudaStream_t, long long *, const Marker &, bool);       \
+    template void launch_refill<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &);
 INST(double)
 INST(float)
 INST(__half)
