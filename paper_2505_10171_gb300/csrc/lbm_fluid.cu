@@ -67,6 +67,7 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     Nbr nb;
     nb.init(x, y, z, I.nx, I.ny, I.nz);
     R v = phi_fluid<S>(nb, in, (int)I.N);
+    keep(v);
     if ((fl & OWNER_MASK) != OWN_FLUID) return;
     if (fl & BOUND_BIT) v = phi_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, n, fl, x, y, z);
     ((R *)L.phi)[g] = v;
@@ -210,6 +211,8 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     R F[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) F[i] = Store<S>::ld(in + i * N + nb.at(-cx(i), -cy(i), -cz(i)));
+#pragma unroll
+    for (int i = 0; i < Q; i++) keep(F[i]);
     R *U = I.store_u ? (R *)L.u + I.node_off : nullptr;
     if ((fl & OWNER_MASK) != OWN_FLUID) {
         if (U) { U[n] = 0; U[L.Ntot + n] = 0; U[2 * L.Ntot + n] = 0; }

@@ -157,6 +157,13 @@ struct Lattice {
     unsigned *status;
 };
 
+// materialise a value here: the loads it depends on must be issued before
+// any branch that follows, so the compiler cannot sink them into the one path
+// that uses them (which would put the node's flag load and the population
+// loads in series: two dependent DRAM round trips instead of one)
+__device__ __forceinline__ void keep(float &v) { asm volatile("" : "+f"(v)); }
+__device__ __forceinline__ void keep(double &v) { asm volatile("" : "+d"(v)); }
+
 // streamed populations are read through the read-only path (measured on this
 // GPU: as fast as plain loads, faster than evict-first streaming loads)
 template <class T>
@@ -526,6 +533,13 @@ __device__ __forceinline__ void for_item_nodes(const Lattice &L, F &&f)
     const int j = threadIdx.x;
     if (j >= it.cnt) return;
     const InstDev &I = L.inst[it.k];
+    if (it.nrows == 1) {
+        // one row or row segment per CTA: y and z are the same for every
+        // thread, which lets the neighbour-row offsets be computed once per CTA
+        const int x = it.x0 + j;
+        f(I, (it.z * I.ny + it.y0) * I.nx + x, x, it.y0, it.z);
+        return;
+    }
     int x, y;
     item_node(it, I.nx, j, &x, &y);
     f(I, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
