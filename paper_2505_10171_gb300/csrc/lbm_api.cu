@@ -65,6 +65,8 @@ struct lbm_ctx {
     // static solid nodes next to non-static ones (built before the first step)
     long long *static_list = nullptr;
     long long n_static = 0;
+    long long *static_bfl = nullptr;  // non-static nodes next to static solids
+    long long n_static_bfl = 0;
     bool static_ready = false;
     // learned force surrogate
     Mlp mlp;
@@ -132,6 +134,8 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.n_items = c->fz.rows;
     L.static_list = c->static_list;
     L.n_static = c->n_static;
+    L.static_bfl = c->static_bfl;
+    L.n_static_bfl = c->n_static_bfl;
     L.flags = c->flags;
     L.pop[0] = c->pop[0];
     L.pop[1] = c->pop[1];
@@ -612,6 +616,7 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->gmag);
     cudaFree(ctx->kap);
     cudaFree(ctx->static_list);
+    cudaFree(ctx->static_bfl);
     cudaFree(ctx->speed_d);
     cudaFree(ctx->speed_part);
     mlp_free(ctx->mlp);
@@ -1041,24 +1046,30 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     if (!ctx) return LBM_ERR_ARG;
     if (nsteps < 0) return fail(ctx, LBM_ERR_ARG, "nsteps < 0");
     if (!ctx->static_ready) {
-        // the static solid boundary list: count, allocate, fill
+        // the static boundary lists: count, allocate, fill (mode 0: static
+        // solid nodes next to non-static ones; mode 1: non-static nodes next to
+        // static solids)
         Lattice L = make_lattice(ctx);
-        unsigned long long *cnt = nullptr, h = 0;
+        unsigned long long *cnt = nullptr;
         CU(cudaMalloc((void **)&cnt, sizeof(unsigned long long)));
-        CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream));
-        launch_static_bound(L, nullptr, cnt, ctx->stream);
-        CU(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
-        CU(cudaStreamSynchronize(ctx->stream));
-        if (h > 0) {
-            CU(cudaMalloc((void **)&ctx->static_list, sizeof(long long) * h));
+        long long **lists[2] = {&ctx->static_list, &ctx->static_bfl};
+        long long *counts[2] = {&ctx->n_static, &ctx->n_static_bfl};
+        for (int mode = 0; mode < 2; mode++) {
+            unsigned long long h = 0;
             CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream));
-            L.static_list = ctx->static_list;
-            launch_static_bound(L, ctx->static_list, cnt, ctx->stream);
+            launch_static_bound(L, nullptr, cnt, mode, ctx->stream);
+            CU(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
             CU(cudaStreamSynchronize(ctx->stream));
+            if (h > 0) {
+                CU(cudaMalloc((void **)lists[mode], sizeof(long long) * h));
+                CU(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), ctx->stream));
+                launch_static_bound(L, *lists[mode], cnt, mode, ctx->stream);
+                CU(cudaStreamSynchronize(ctx->stream));
+            }
+            *counts[mode] = (long long)h;
         }
         CU(cudaGetLastError());
         cudaFree(cnt);
-        ctx->n_static = (long long)h;
         ctx->static_ready = true;
         drop_graph(ctx);
     }

@@ -54,22 +54,29 @@ namespace lbmg {
     reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);                                              \
     const int n = (z * I.ny + y) * I.nx + x;
 
-template <class S>
+// order parameter of a fluid node.  full = false (the bulk kernel): the plain
+// pull of every node; at nodes next to a solid this pulls solid populations
+// and the boundary pass (k_phi_bound) rewrites the value.  Keeping the
+// bounce-back code out of the bulk kernel keeps its loads in flight (with it
+// compiled in, the kernel ran 75% longer).
+template <class S, bool full>
 __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
 {
     using R = typename Store<S>::real;
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
     const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
-    // the sums of a node without solid neighbours are formed before the flag
-    // is tested (every neighbour address is valid), so that the 38 loads travel
-    // with the flag load instead of after it
     Nbr nb;
     nb.init(x, y, z, I.nx, I.ny, I.nz);
     R v = phi_fluid<S>(nb, in, (int)I.N);
     keep(v);
     if ((fl & OWNER_MASK) != OWN_FLUID) return;
-    if (fl & BOUND_BIT) v = phi_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, n, fl, x, y, z);
+    if (full && (fl & BOUND_BIT)) {
+        GlobalNbr gnb;
+        gnb.nb = nb;
+        gnb.fli = L.flags + I.node_off;
+        v = node_phi<S>(I, L.parts, gnb, in, (int)I.N, n, fl, x, y, z);
+    }
     ((R *)L.phi)[g] = v;
 }
 
@@ -114,7 +121,7 @@ __device__ __forceinline__ void grad_body(const Lattice &L, const InstDev &I, in
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
 {
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S, false>(L, I, cur, n, x, y, z); });
 }
 
 // instance of global node g (binary search over the node offsets)
@@ -132,10 +139,10 @@ __device__ __forceinline__ int inst_of_node(const Lattice &L, long long g)
 // static solid nodes with a neighbour that is not static solid: the only
 // static nodes the solid-phi fill can reach.  count pass (list == null) or
 // fill pass; the order of the list does not matter.
-__global__ void k_static_bound(Lattice L, long long *list, unsigned long long *count)
+__global__ void k_static_bound(Lattice L, long long *list, unsigned long long *count, int mode)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= L.Ntot || (L.flags[g] & OWNER_MASK) != OWN_WALL) return;
+    if (g >= L.Ntot || ((L.flags[g] & OWNER_MASK) == OWN_WALL) != (mode == 0)) return;
     const InstDev &I = L.inst[inst_of_node(L, g)];
     const int n = (int)(g - I.node_off);
     const int x = n % I.nx, y = (n / I.nx) % I.ny, z = n / (I.nx * I.ny);
@@ -144,7 +151,7 @@ __global__ void k_static_bound(Lattice L, long long *list, unsigned long long *c
     const uint8_t *fli = L.flags + I.node_off;
     bool hit = false;
 #pragma unroll
-    for (int i = 1; i < Q; i++) hit |= (fli[nb.at(cx(i), cy(i), cz(i))] & OWNER_MASK) != OWN_WALL;
+    for (int i = 1; i < Q; i++) hit |= ((fli[nb.at(cx(i), cy(i), cz(i))] & OWNER_MASK) == OWN_WALL) != (mode == 0);
     if (!hit) return;
     const unsigned long long k = atomicAdd(count, 1ull);
     if (list) list[k] = g;
@@ -163,17 +170,82 @@ __global__ void k_solidphi_list(Lattice L)
     solidphi_body<R>(L, I, n, x, y, z);
 }
 
-void launch_static_bound(const Lattice &L, long long *list, unsigned long long *count, cudaStream_t st)
+void launch_static_bound(const Lattice &L, long long *list, unsigned long long *count, int mode, cudaStream_t st)
 {
-    k_static_bound<<<(unsigned)((L.Ntot + 255) / 256), 256, 0, st>>>(L, list, count);
+    k_static_bound<<<(unsigned)((L.Ntot + 255) / 256), 256, 0, st>>>(L, list, count, mode);
 }
 
+
+// node of the boundary passes: blockIdx.y < n_parts: the cube of side
+// cap_side around that particle; blockIdx.y == n_parts: the static list of
+// nodes next to static solids.  Returns false for threads without a node.
+__device__ __forceinline__ bool bound_node(const Lattice &L, const InstDev **Ip, int *n, int *x, int *y, int *z)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((int)blockIdx.y < L.n_parts) {
+        const PartDev &P0 = L.parts[blockIdx.y];
+        const InstDev &I = L.inst[P0.inst];
+        Region reg;
+        reg.init(P0.x, L.cap_side, I.nx, I.ny, I.nz);
+        if (t >= reg.count()) return false;
+        reg.coord(t, I.nx, I.ny, I.nz, x, y, z);
+        *n = (*z * I.ny + *y) * I.nx + *x;
+        *Ip = &I;
+        return true;
+    }
+    if (t >= L.n_static_bfl) return false;
+    const long long g = L.static_bfl[t];
+    const InstDev &I = L.inst[inst_of_node(L, g)];
+    *n = (int)(g - I.node_off);
+    *x = *n % I.nx;
+    *y = (*n / I.nx) % I.ny;
+    *z = *n / (I.nx * I.ny);
+    *Ip = &I;
+    return true;
+}
+
+// the boundary passes: fluid nodes next to a solid, with the bounce-back
+// pull (Sec. V A); a node reached twice (cube and list) is written twice
+// with the same value
+template <class S>
+__global__ void __launch_bounds__(PART_THREADS) k_phi_bound(Lattice L, int cur)
+{
+    using R = typename Store<S>::real;
+    const InstDev *I;
+    int n, x, y, z;
+    if (!bound_node(L, &I, &n, &x, &y, &z)) return;
+    const long long g = I->node_off + n;
+    const uint8_t fl = L.flags[g];
+    if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
+    const S *in = (const S *)L.pop[cur] + NPOP * I->node_off;
+    ((R *)L.phi)[g] = phi_node_cold<S>(I, L.parts, L.flags + I->node_off, in, n, fl, x, y, z);
+}
+
+template <class S>
+__global__ void __launch_bounds__(PART_THREADS) k_collide_bound(Lattice L, int cur)
+{
+    using R = typename Store<S>::real;
+    const InstDev *I;
+    int n, x, y, z;
+    if (!bound_node(L, &I, &n, &x, &y, &z)) return;
+    const long long g = I->node_off + n;
+    const uint8_t fl = L.flags[g];
+    if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
+    const S *in = (const S *)L.pop[cur] + NPOP * I->node_off;
+    S *out = (S *)L.pop[cur ^ 1] + NPOP * I->node_off;
+    const R *Nn = (const R *)L.grad + I->node_off;
+    const long long Nt = L.Ntot;
+    R *U = I->store_u ? (R *)L.u + I->node_off : nullptr;
+    collide_node_cold<S>(I, L.parts, L.flags + I->node_off, in, out, n, fl, x, y, z, ((const R *)L.phi)[g], Nn[n],
+                         Nn[Nt + n], Nn[2 * Nt + n], ((const R *)L.gmag)[g], ((const R *)L.kap)[g], U, L.Ntot,
+                         L.status);
+}
 
 template <class S>
 __global__ void __launch_bounds__(PART_THREADS) k_phi_region(Lattice L, int cur, int side)
 {
     LBM_REGION_PROLOGUE
-    phi_body<S>(L, I, cur, n, x, y, z);
+    phi_body<S, true>(L, I, cur, n, x, y, z);
 }
 
 template <class R>
@@ -218,15 +290,13 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
         if (U) { U[n] = 0; U[L.Ntot + n] = 0; U[2 * L.Ntot + n] = 0; }
         return;
     }
-    if (fl & BOUND_BIT) {
-        collide_node_cold<S>(&I, L.parts, L.flags + I.node_off, in, out, n, fl, x, y, z, phi, nn[0], nn[1], nn[2], m,
-                             kap, U, L.Ntot, L.status);
-        return;
-    }
+    // nodes next to a solid: placeholder values here (solid populations were
+    // pulled), rewritten by the boundary pass k_collide_bound, which also does
+    // their stability check
     FluidPar<R> P;
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, (fl & BOUND_BIT) ? nullptr : L.status);
 }
 
 template <class S>
@@ -468,9 +538,17 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     // staged form where every instance's rows are whole 16-byte units, plain otherwise
     const bool staged = fz.form == FORM_STAGED && fz.st_items > 0;
     const dim3 grid((unsigned)fz.rows);  // one CTA per row-strip work item
+    // boundary passes: particle cubes and the static list of nodes next to walls
+    const unsigned bx = (unsigned)std::max<long long>(L.n_parts > 0 ? L.cap_blocks : 0, (L.n_static_bfl + 255) / 256);
+    const dim3 bgrid(std::max(bx, 1u), (unsigned)L.n_parts + 1);
     mk(STAGE_PHI, 0);
-    if (staged) launch_staged_phi<S>(L, cur, fz, st);
-    else k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+    if (staged) {
+        launch_staged_phi<S>(L, cur, fz, st);
+    } else {
+        k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+        k_phi_bound<S><<<bgrid, PART_THREADS, 0, st>>>(L, cur);
+        *launches += 1;
+    }
     mk(STAGE_PHI, 1);
     // phi of solid nodes next to fluid: the listed static nodes and the
     // particle cubes (every particle node lies within R_p + 1 of its centre)
@@ -489,8 +567,13 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     mk(STAGE_GRAD, 1);
     after_grad();
     mk(STAGE_COLLIDE, 0);
-    if (staged) launch_staged_collide<S>(L, cur, fz, st);
-    else k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+    if (staged) {
+        launch_staged_collide<S>(L, cur, fz, st);
+    } else {
+        k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+        k_collide_bound<S><<<bgrid, PART_THREADS, 0, st>>>(L, cur);
+        *launches += 1;
+    }
     mk(STAGE_COLLIDE, 1);
     *launches += 3;
 }

@@ -134,6 +134,8 @@ struct Lattice {
     long long n_items;   // row-strip work items of all instances
     const long long *static_list;  // static solid nodes next to non-static ones (global node index)
     long long n_static;
+    const long long *static_bfl;   // non-static nodes next to static solid ones
+    long long n_static_bfl;
     uint8_t *flags;
     void *pop[2];
     void *phi;           // [Ntot] real
@@ -694,8 +696,10 @@ template <class S>
 void launch_mass_sums(const Lattice &L, int cur, int inst, long long N, double *partial, int nblk, double *out,
                       cudaStream_t st);
 void launch_boundary_full(const Lattice &L, int inst, long long N, cudaStream_t st);
-// count (list == null) or fill the static solid boundary list
-void launch_static_bound(const Lattice &L, long long *list, unsigned long long *count, cudaStream_t st);
+// count (list == null) or fill a static boundary list: mode 0 static solid
+// nodes with a non-static neighbour, mode 1 non-static nodes with a static
+// solid neighbour
+void launch_static_bound(const Lattice &L, long long *list, unsigned long long *count, int mode, cudaStream_t st);
 void launch_mark_particles(const Lattice &L, cudaStream_t st);
 
 }  // namespace lbmg

@@ -149,7 +149,7 @@ __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<
         if (cz(i)) jz += w * cz(i) * F[i];
     }
     const R rr = R(1) + sF;  // rho / rho0
-    if (!(rr > R(0)) || !(phi == phi)) atomicOr(status, ST_UNSTABLE);
+    if (status && (!(rr > R(0)) || !(phi == phi))) atomicOr(status, ST_UNSTABLE);
     // force density: CSF -1/2 sigma kappa grad(phi) plus phase-weighted body forces
     const R hs = R(-0.5) * P.sigma * kap;
     const R pa = R(0.5) * (R(1) + phi), pb = R(0.5) * (R(1) - phi);
