@@ -40,7 +40,7 @@ struct lbm_ctx {
     bool own_stream = false;
     // side stream of the step: particle forces run beside the fluid kernels
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_grad = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_grad = nullptr, ev_join = nullptr, ev_a = nullptr, ev_b = nullptr;
     cudaGraphExec_t graph = nullptr;
     long long graph_launches = 0;
     long long last_launches = 0;
@@ -469,7 +469,11 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
                 launch_capillary<S>(*q->L, q->c->side, q->launches, *q->mk);
                 cudaEventRecord(q->c->ev_join, q->c->side);
             };
-            launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz, hook);
+            SideLane lane;
+            lane.side = c->side;
+            lane.a = c->ev_a;
+            lane.b = c->ev_b;
+            launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz, hook, lane);
             cudaStreamWaitEvent(c->stream, c->ev_join, 0);
         } else {
             launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz);
@@ -640,6 +644,8 @@ void lbm_destroy(lbm_ctx *ctx)
     if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_grad) cudaEventDestroy(ctx->ev_grad);
     if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_a) cudaEventDestroy(ctx->ev_a);
+    if (ctx->ev_b) cudaEventDestroy(ctx->ev_b);
     delete ctx;
 }
 
@@ -734,7 +740,9 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_b, cudaEventDisableTiming) != cudaSuccess) {
         lbm_destroy(ctx);
         return LBM_ERR_CUDA;
     }

@@ -55,10 +55,10 @@ namespace lbmg {
     const int n = (z * I.ny + y) * I.nx + x;
 
 // order parameter of a fluid node.  full = false (the bulk kernel): the plain
-// pull of every node; at nodes next to a solid this pulls solid populations
-// and the boundary pass (k_phi_bound) rewrites the value.  Keeping the
-// bounce-back code out of the bulk kernel keeps its loads in flight (with it
-// compiled in, the kernel ran 75% longer).
+// pull, for nodes none of whose neighbours is solid; the boundary pass
+// (k_phi_bound) does the others.  Keeping the bounce-back code out of the bulk
+// kernel keeps its loads in flight (with it compiled in, the kernel ran 75%
+// longer).
 template <class S, bool full>
 __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
 {
@@ -71,7 +71,8 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     R v = phi_fluid<S>(nb, in, (int)I.N);
     keep(v);
     if ((fl & OWNER_MASK) != OWN_FLUID) return;
-    if (full && (fl & BOUND_BIT)) {
+    if (fl & BOUND_BIT) {
+        if (!full) return;  // the boundary pass writes this node
         GlobalNbr gnb;
         gnb.nb = nb;
         gnb.fli = L.flags + I.node_off;
@@ -218,7 +219,17 @@ __global__ void __launch_bounds__(PART_THREADS) k_phi_bound(Lattice L, int cur)
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
     const S *in = (const S *)L.pop[cur] + NPOP * I->node_off;
-    ((R *)L.phi)[g] = phi_node_cold<S>(I, L.parts, L.flags + I->node_off, in, n, fl, x, y, z);
+    GlobalNbr nb;
+    nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
+    nb.fli = L.flags + I->node_off;
+    R F[Q], G[Q], sF = 0, sG = 0;
+    gather_all<S>(*I, L.parts, nb, in, (int)I->N, n, F, G, x, y, z);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        sF += wgt<R>(i) * F[i];
+        sG += wgt<R>(i) * G[i];
+    }
+    ((R *)L.phi)[g] = sG / (R(1) + sF);
 }
 
 template <class S>
@@ -236,8 +247,17 @@ __global__ void __launch_bounds__(PART_THREADS) k_collide_bound(Lattice L, int c
     const R *Nn = (const R *)L.grad + I->node_off;
     const long long Nt = L.Ntot;
     R *U = I->store_u ? (R *)L.u + I->node_off : nullptr;
-    collide_node_cold<S>(I, L.parts, L.flags + I->node_off, in, out, n, fl, x, y, z, ((const R *)L.phi)[g], Nn[n],
-                         Nn[Nt + n], Nn[2 * Nt + n], ((const R *)L.gmag)[g], ((const R *)L.kap)[g], U, L.Ntot,
+    GlobalNbr nb;
+    nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
+    nb.fli = L.flags + I->node_off;
+    R F[Q];
+    gather_all<S>(*I, L.parts, nb, in, (int)I->N, n, F, (R *)nullptr, x, y, z);
+    FluidPar<R> P;
+    load_par(*I, P);
+    const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
+    const R m = ((const R *)L.gmag)[g];
+    const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
+    collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, nn, ((const R *)L.kap)[g], out, (int)I->N, n, U, L.Ntot,
                          L.status);
 }
 
@@ -290,13 +310,12 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
         if (U) { U[n] = 0; U[L.Ntot + n] = 0; U[2 * L.Ntot + n] = 0; }
         return;
     }
-    // nodes next to a solid: placeholder values here (solid populations were
-    // pulled), rewritten by the boundary pass k_collide_bound, which also does
-    // their stability check
+    // nodes next to a solid belong to the boundary pass k_collide_bound
+    if (fl & BOUND_BIT) return;
     FluidPar<R> P;
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, (fl & BOUND_BIT) ? nullptr : L.status);
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
 }
 
 template <class S>
@@ -512,7 +531,7 @@ int fused_tile_y(int tile) { return tile == 1 ? 8 : 16; }
 
 template <class S>
 void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
-                       const FluidLaunch &fz, const Hook &after_grad)
+                       const FluidLaunch &fz, const Hook &after_grad, const SideLane &lane)
 {
     using R = typename Store<S>::real;
     if (fz.form == FORM_FUSED) {
@@ -541,14 +560,24 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     // boundary passes: particle cubes and the static list of nodes next to walls
     const unsigned bx = (unsigned)std::max<long long>(L.n_parts > 0 ? L.cap_blocks : 0, (L.n_static_bfl + 255) / 256);
     const dim3 bgrid(std::max(bx, 1u), (unsigned)L.n_parts + 1);
-    mk(STAGE_PHI, 0);
-    if (staged) {
-        launch_staged_phi<S>(L, cur, fz, st);
-    } else {
-        k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
-        k_phi_bound<S><<<bgrid, PART_THREADS, 0, st>>>(L, cur);
+    // boundary pass beside (side lane) or after the bulk kernel
+    auto bound_pass = [&](auto kernel, auto &&bulk) {
+        if (lane.side) {
+            cudaEventRecord(lane.a, st);
+            cudaStreamWaitEvent(lane.side, lane.a, 0);
+            kernel<<<bgrid, PART_THREADS, 0, lane.side>>>(L, cur);
+            cudaEventRecord(lane.b, lane.side);
+            bulk();
+            cudaStreamWaitEvent(st, lane.b, 0);
+        } else {
+            bulk();
+            kernel<<<bgrid, PART_THREADS, 0, st>>>(L, cur);
+        }
         *launches += 1;
-    }
+    };
+    mk(STAGE_PHI, 0);
+    if (staged) launch_staged_phi<S>(L, cur, fz, st);
+    else bound_pass(k_phi_bound<S>, [&] { k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
     mk(STAGE_PHI, 1);
     // phi of solid nodes next to fluid: the listed static nodes and the
     // particle cubes (every particle node lies within R_p + 1 of its centre)
@@ -567,13 +596,8 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     mk(STAGE_GRAD, 1);
     after_grad();
     mk(STAGE_COLLIDE, 0);
-    if (staged) {
-        launch_staged_collide<S>(L, cur, fz, st);
-    } else {
-        k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
-        k_collide_bound<S><<<bgrid, PART_THREADS, 0, st>>>(L, cur);
-        *launches += 1;
-    }
+    if (staged) launch_staged_collide<S>(L, cur, fz, st);
+    else bound_pass(k_collide_bound<S>, [&] { k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
     mk(STAGE_COLLIDE, 1);
     *launches += 3;
 }
@@ -581,7 +605,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
 
 #define INST(S)                                                                                                   \
     template void launch_fluid_step<S>(const Lattice &, int, cudaStream_t, long long *, const Marker &,            \
-                                       const FluidLaunch &, const Hook &);
+                                       const FluidLaunch &, const Hook &, const SideLane &);
 INST(double)
 INST(float)
 INST(__half)

@@ -392,6 +392,51 @@ __device__ __forceinline__ void gather_F(const InstDev &I, const PartDev *parts,
     }
 }
 
+// gather / gather_F for the boundary passes: the same values, with every
+// flag and population load issued before any is used (one dependent round
+// trip instead of one per link); G is skipped when null
+template <class S, class A>
+__device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *parts, const A &nbr,
+                                           const S *__restrict__ in, int N, int n, typename Store<S>::real *F,
+                                           typename Store<S>::real *G, int x, int y, int z)
+{
+    using R = typename Store<S>::real;
+    int own[Q];
+    R pF[Q], oF[Q], pG[Q], oG[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
+        own[i] = nbr.own(-cx(i), -cy(i), -cz(i));
+        pF[i] = Store<S>::ld(in + i * N + s);
+        oF[i] = Store<S>::ld(in + i * N + n);
+        if (G) {
+            pG[i] = Store<S>::ld(in + (Q + i) * N + s);
+            oG[i] = Store<S>::ld(in + (Q + i) * N + n);
+        }
+    }
+    R sF = 0, sG = 0;
+#pragma unroll
+    for (int j = 0; j < Q; j++) {
+        sF += wgt<R>(j) * oF[j];
+        if (G) sG += wgt<R>(j) * oG[j];
+    }
+    const R rr = R(1) + sF, rd = sG;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        if (own[i] == OWN_FLUID) {
+            F[i] = pF[i];
+            if (G) G[i] = pG[i];
+            continue;
+        }
+        double uw[3], lev[3];
+        surface_velocity(I, parts, own[i], x - 0.5 * cx(i), y - 0.5 * cy(i), z - 0.5 * cz(i), uw, lev);
+        const R cu = (R)(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
+        const int ib = opp(i);
+        F[i] = oF[ib] + R(6) * rr * cu;
+        if (G) G[i] = oG[ib] + R(6) * rd * cu;
+    }
+}
+
 // order parameter of a fluid node none of whose neighbours is solid
 template <class S, class A>
 __device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const S *__restrict__ in, int N)
@@ -590,6 +635,13 @@ struct Hook {
     }
 };
 
+// a second stream with two events: the plain form runs its boundary passes
+// there, beside the bulk kernels (they write disjoint nodes)
+struct SideLane {
+    cudaStream_t side = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
 // host-side kernel launchers (defined in the .cu files)
 enum { FORM_STAGED = 0, FORM_FUSED = 1, FORM_PLAIN = 2 };
 struct FluidLaunch {
@@ -626,7 +678,7 @@ template <class S>
 void launch_fused_form(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
 template <class S>
 void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
-                       const FluidLaunch &fz, const Hook &after_grad = Hook());
+                       const FluidLaunch &fz, const Hook &after_grad = Hook(), const SideLane &lane = SideLane());
 int fused_tile_x(int tile);
 int fused_tile_y(int tile);
 template <class S>
