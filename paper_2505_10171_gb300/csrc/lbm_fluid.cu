@@ -209,7 +209,7 @@ __device__ __forceinline__ bool bound_node(const Lattice &L, const InstDev **Ip,
 // pull (Sec. V A); a node reached twice (cube and list) is written twice
 // with the same value
 template <class S>
-__global__ void __launch_bounds__(PART_THREADS) k_phi_bound(Lattice L, int cur)
+__global__ void __launch_bounds__(PART_THREADS, 2) k_phi_bound(Lattice L, int cur)
 {
     using R = typename Store<S>::real;
     const InstDev *I;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_phi_bound(Lattice L, int cur)
 }
 
 template <class S>
-__global__ void __launch_bounds__(PART_THREADS) k_collide_bound(Lattice L, int cur)
+__global__ void __launch_bounds__(PART_THREADS, 2) k_collide_bound(Lattice L, int cur)
 {
     using R = typename Store<S>::real;
     const InstDev *I;

@@ -244,22 +244,28 @@ __device__ __forceinline__ double frsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
 
 // velocity of the solid owning a node at the point xw (Sec. V A)
-__device__ __forceinline__ void surface_velocity(const InstDev &I, const PartDev *parts, int owner,
-                                                 double xw, double yw, double zw, double *u, double *lev)
+template <class R>
+__device__ __forceinline__ void surface_velocity(const InstDev &I, const PartDev *parts, int owner, R xw, R yw, R zw,
+                                                 R *u)
 {
+    // in R: double in the FP64 mode, float (with the float particle centres)
+    // otherwise; the link midpoints are half-integers, exact in either
     if (owner == OWN_WALL) {
-        u[0] = I.wall_u[0]; u[1] = I.wall_u[1]; u[2] = I.wall_u[2];
-        lev[0] = lev[1] = lev[2] = 0.0;
+        u[0] = (R)I.wall_u[0]; u[1] = (R)I.wall_u[1]; u[2] = (R)I.wall_u[2];
         return;
     }
     const PartDev &P = parts[I.part_off + owner - 2];
-    double d0 = min_image(xw - P.x[0], I.nx);
-    double d1 = min_image(yw - P.x[1], I.ny);
-    double d2 = min_image(zw - P.x[2], I.nz);
-    u[0] = P.v[0] + (P.w[1] * d2 - P.w[2] * d1);
-    u[1] = P.v[1] + (P.w[2] * d0 - P.w[0] * d2);
-    u[2] = P.v[2] + (P.w[0] * d1 - P.w[1] * d0);
-    lev[0] = d0; lev[1] = d1; lev[2] = d2;
+    R d0, d1, d2;
+    if (sizeof(R) == 8) {
+        d0 = (R)min_image(xw - P.x[0], I.nx); d1 = (R)min_image(yw - P.x[1], I.ny); d2 = (R)min_image(zw - P.x[2], I.nz);
+    } else {
+        d0 = (R)min_image_f((float)xw - P.xf[0], I.nx); d1 = (R)min_image_f((float)yw - P.xf[1], I.ny);
+        d2 = (R)min_image_f((float)zw - P.xf[2], I.nz);
+    }
+    const R w0 = (R)P.w[0], w1 = (R)P.w[1], w2 = (R)P.w[2];
+    u[0] = (R)P.v[0] + (w1 * d2 - w2 * d1);
+    u[1] = (R)P.v[1] + (w2 * d0 - w0 * d2);
+    u[2] = (R)P.v[2] + (w0 * d1 - w1 * d0);
 }
 
 // cube of side `side` (clamped to the domain) centred on a particle's node
@@ -346,9 +352,9 @@ __device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, c
             rd = sG;
             have_rho = true;
         }
-        double uw[3], lev[3];
-        surface_velocity(I, parts, own, x - 0.5 * cx(i), y - 0.5 * cy(i), z - 0.5 * cz(i), uw, lev);
-        const R cu = (R)(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
+        R uw[3];
+        surface_velocity<R>(I, parts, own, x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
+        const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
         const int ib = opp(i);
         F[i] = Store<S>::ld(in + ib * N + n) + R(6) * rr * cu;
         G[i] = Store<S>::ld(in + (Q + ib) * N + n) + R(6) * rd * cu;
@@ -385,9 +391,9 @@ __device__ __forceinline__ void gather_F(const InstDev &I, const PartDev *parts,
             rr = R(1) + sF;
             have_rho = true;
         }
-        double uw[3], lev[3];
-        surface_velocity(I, parts, own, x - 0.5 * cx(i), y - 0.5 * cy(i), z - 0.5 * cz(i), uw, lev);
-        const R cu = (R)(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
+        R uw[3];
+        surface_velocity<R>(I, parts, own, x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
+        const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
         F[i] = Store<S>::ld(in + opp(i) * N + n) + R(6) * rr * cu;
     }
 }
@@ -428,9 +434,9 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
             if (G) G[i] = pG[i];
             continue;
         }
-        double uw[3], lev[3];
-        surface_velocity(I, parts, own[i], x - 0.5 * cx(i), y - 0.5 * cy(i), z - 0.5 * cz(i), uw, lev);
-        const R cu = (R)(cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2]);
+        R uw[3];
+        surface_velocity<R>(I, parts, own[i], x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
+        const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
         const int ib = opp(i);
         F[i] = oF[ib] + R(6) * rr * cu;
         if (G) G[i] = oG[ib] + R(6) * rd * cu;
