@@ -560,8 +560,9 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     // boundary passes: particle cubes and the static list of nodes next to walls
     const unsigned bx = (unsigned)std::max<long long>(L.n_parts > 0 ? L.cap_blocks : 0, (L.n_static_bfl + 255) / 256);
     const dim3 bgrid(std::max(bx, 1u), (unsigned)L.n_parts + 1);
-    // boundary pass beside (side lane) or after the bulk kernel
-    auto bound_pass = [&](auto kernel, auto &&bulk) {
+    // boundary pass beside (side lane) or after the bulk kernel; profiling
+    // (no side lane) times the two separately
+    auto bound_pass = [&](auto kernel, int bstage, int stage, auto &&bulk) {
         if (lane.side) {
             cudaEventRecord(lane.a, st);
             cudaStreamWaitEvent(lane.side, lane.a, 0);
@@ -570,15 +571,22 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
             bulk();
             cudaStreamWaitEvent(st, lane.b, 0);
         } else {
+            mk(stage, 0);
             bulk();
+            mk(stage, 1);
+            mk(bstage, 0);
             kernel<<<bgrid, PART_THREADS, 0, st>>>(L, cur);
+            mk(bstage, 1);
         }
         *launches += 1;
     };
-    mk(STAGE_PHI, 0);
-    if (staged) launch_staged_phi<S>(L, cur, fz, st);
-    else bound_pass(k_phi_bound<S>, [&] { k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
-    mk(STAGE_PHI, 1);
+    if (staged) {
+        mk(STAGE_PHI, 0);
+        launch_staged_phi<S>(L, cur, fz, st);
+        mk(STAGE_PHI, 1);
+    } else {
+        bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] { k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
+    }
     // phi of solid nodes next to fluid: the listed static nodes and the
     // particle cubes (every particle node lies within R_p + 1 of its centre)
     mk(STAGE_SOLIDPHI, 0);
@@ -595,10 +603,14 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     k_gradcurv<R><<<(unsigned)fz.gc_items, GC_TX * GC_TY, 0, st>>>(L);
     mk(STAGE_GRAD, 1);
     after_grad();
-    mk(STAGE_COLLIDE, 0);
-    if (staged) launch_staged_collide<S>(L, cur, fz, st);
-    else bound_pass(k_collide_bound<S>, [&] { k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
-    mk(STAGE_COLLIDE, 1);
+    if (staged) {
+        mk(STAGE_COLLIDE, 0);
+        launch_staged_collide<S>(L, cur, fz, st);
+        mk(STAGE_COLLIDE, 1);
+    } else {
+        bound_pass(k_collide_bound<S>, STAGE_COLLIDE_BOUND, STAGE_COLLIDE,
+                   [&] { k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
+    }
     *launches += 3;
 }
 

@@ -617,7 +617,7 @@ int persistent_grid(K kernel, size_t smem, int cap)
 enum Stage {
     STAGE_PHI = 0, STAGE_SOLIDPHI, STAGE_GRAD, STAGE_COLLIDE, STAGE_MEM, STAGE_CAPILLARY, STAGE_DEM,
     STAGE_GEOM_OWNER, STAGE_GEOM_BOUND, STAGE_REFILL, STAGE_FUSED, STAGE_REGION, STAGE_CURV, STAGE_SURROGATE,
-    N_STAGES
+    STAGE_PHI_BOUND, STAGE_COLLIDE_BOUND, N_STAGES
 };
 
 // optional per-kernel marker: called right before and right after each launch

@@ -79,7 +79,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
 STAGES = ["phi", "solid_phi", "grad_wetting", "collide", "momentum_exchange", "capillary", "dem", "geom_owner",
-          "geom_boundary", "refill", "fused", "particle_region", "curvature", "surrogate"]
+          "geom_boundary", "refill", "fused", "particle_region", "curvature", "surrogate", "phi_boundary",
+          "collide_boundary"]
 # fluid launch forms of lbm_set_fluid_kernel
 FORM_STAGED, FORM_FUSED, FORM_PLAIN = 0, 1, 2
 
