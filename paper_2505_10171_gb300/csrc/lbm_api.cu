@@ -469,18 +469,34 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
                 launch_capillary<S>(*q->L, q->c->side, q->launches, *q->mk);
                 cudaEventRecord(q->c->ev_join, q->c->side);
             };
+            // the DEM needs the fluid forces of the step and must see the
+            // particle state the collision's boundary pass reads: it follows
+            // that pass on the side stream, beside the bulk collision
             SideLane lane;
             lane.side = c->side;
             lane.a = c->ev_a;
             lane.b = c->ev_b;
+            lane.after_collide_bound.self = &h2;
+            lane.after_collide_bound.fn = [](void *p) {
+                Ctx2 *q = (Ctx2 *)p;
+                launch_dem<S>(*q->L, q->c->side, q->launches, *q->mk, true);
+                cudaEventRecord(q->c->ev_join, q->c->side);
+            };
+            const bool plain = c->fz.form == FORM_PLAIN || c->fz.st_items == 0;
             launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz, hook, lane);
-            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            if (!plain) {
+                // staged form: no boundary passes on the side lane; DEM after the join
+                cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+                launch_dem<S>(L, c->stream, launches, mk, true);
+            } else {
+                cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            }
         } else {
             launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz);
             if (sur) launch_surrogate_forces<S>(L, c->mlp, c->feat, c->stream, launches, mk);
             else launch_particle_forces<S>(L, cur, c->stream, launches, mk);
+            launch_dem<S>(L, c->stream, launches, mk, !sur);
         }
-        launch_dem<S>(L, c->stream, launches, mk, !sur);
         // geometry: owners first; then boundary bits (side stream) beside the
         // refill of uncovered nodes (they touch disjoint data)
         if (!c->profile && L.n_parts > 0) {
@@ -737,7 +753,12 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         }
         ctx->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // the side stream carries the small particle kernels that run beside the
+    // bulk fluid kernels: at the highest priority their CTAs are dispatched as
+    // soon as bulk CTAs retire instead of after the whole bulk grid
+    int prio_least = 0, prio_greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
@@ -1097,7 +1118,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
                 enqueue_step(ctx, &l);
                 cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
                 if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-                e = cudaGraphInstantiate(&ctx->graph, g, 0);
+                // kernel nodes keep the priority of the stream they were captured from
+                e = cudaGraphInstantiate(&ctx->graph, g, cudaGraphInstantiateFlagUseNodePriority);
                 cudaGraphDestroy(g);
                 if (e != cudaSuccess) return fail(ctx, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
                 ctx->graph_launches = l;

@@ -182,9 +182,12 @@ void launch_static_bound(const Lattice &L, long long *list, unsigned long long *
 // nodes next to static solids.  Returns false for threads without a node.
 __device__ __forceinline__ bool bound_node(const Lattice &L, const InstDev **Ip, int *n, int *x, int *y, int *z)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if ((int)blockIdx.y < L.n_parts) {
-        const PartDev &P0 = L.parts[blockIdx.y];
+    // one flat grid: cap_blocks CTAs per particle cube, then the static list
+    const long long cube_ctas = (long long)L.n_parts * L.cap_blocks;
+    const long long b = blockIdx.x;
+    if (b < cube_ctas) {
+        const long long t = (b % L.cap_blocks) * blockDim.x + threadIdx.x;
+        const PartDev &P0 = L.parts[b / L.cap_blocks];
         const InstDev &I = L.inst[P0.inst];
         Region reg;
         reg.init(P0.x, L.cap_side, I.nx, I.ny, I.nz);
@@ -194,6 +197,7 @@ __device__ __forceinline__ bool bound_node(const Lattice &L, const InstDev **Ip,
         *Ip = &I;
         return true;
     }
+    const long long t = (b - cube_ctas) * blockDim.x + threadIdx.x;
     if (t >= L.n_static_bfl) return false;
     const long long g = L.static_bfl[t];
     const InstDev &I = L.inst[inst_of_node(L, g)];
@@ -558,8 +562,8 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     const bool staged = fz.form == FORM_STAGED && fz.st_items > 0;
     const dim3 grid((unsigned)fz.rows);  // one CTA per row-strip work item
     // boundary passes: particle cubes and the static list of nodes next to walls
-    const unsigned bx = (unsigned)std::max<long long>(L.n_parts > 0 ? L.cap_blocks : 0, (L.n_static_bfl + 255) / 256);
-    const dim3 bgrid(std::max(bx, 1u), (unsigned)L.n_parts + 1);
+    const long long bctas = (long long)L.n_parts * L.cap_blocks + (L.n_static_bfl + PART_THREADS - 1) / PART_THREADS;
+    const dim3 bgrid((unsigned)std::max(bctas, 1LL));
     // boundary pass beside (side lane) or after the bulk kernel; profiling
     // (no side lane) times the two separately
     auto bound_pass = [&](auto kernel, int bstage, int stage, auto &&bulk) {
@@ -568,6 +572,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
             cudaStreamWaitEvent(lane.side, lane.a, 0);
             kernel<<<bgrid, PART_THREADS, 0, lane.side>>>(L, cur);
             cudaEventRecord(lane.b, lane.side);
+            if (stage == STAGE_COLLIDE) lane.after_collide_bound();
             bulk();
             cudaStreamWaitEvent(st, lane.b, 0);
         } else {

@@ -646,6 +646,7 @@ struct Hook {
 struct SideLane {
     cudaStream_t side = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
+    Hook after_collide_bound;  // more side-stream work after the collision's boundary pass
 };
 
 // host-side kernel launchers (defined in the .cu files)

@@ -538,76 +538,101 @@ __global__ void k_boundary_full(Lattice L, int inst)
 // f^{a,b} = feq(rho^{a,b}, u_p + w_p x (x - x_p)), rho^{a,b} the mean over the
 // 18 moving-direction neighbours that are fluid and not fresh (two hops out if
 // none; ambient (0, rho0) if still none).
+//
+// Few nodes are uncovered per step (about the swept surface area), so the
+// kernel is a scan of the flags plus, per fresh node, one warp working on it:
+// lane i-1 takes neighbour i and issues its 38 population loads at once, the
+// sums meet in a shuffle reduction and lane i writes direction i.
+template <class R>
+__device__ __forceinline__ R warp_sum(R v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 template <class S>
-__global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int side)
+__device__ void refill_node(const InstDev &I, const PartDev *parts, S *pop, const uint8_t *fli, int x, int y, int z,
+                            int lane)
 {
     using R = typename Store<S>::real;
-    const PartDev &P0 = L.parts[blockIdx.y];
-    const InstDev &I = L.inst[P0.inst];
-    Region reg;
-    reg.init(P0.x, side, I.nx, I.ny, I.nz);
     const int N = (int)I.N;
-    S *pop = (S *)L.pop[nxt] + NPOP * I.node_off;
-    const uint8_t *fli = L.flags + I.node_off;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < reg.count();
-         t += (long long)gridDim.x * blockDim.x) {
-        int x, y, z;
-        reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
-        const int n = (z * I.ny + y) * I.nx + x;
-        if (!(fli[n] & FRESH_BIT)) continue;
-        R sF = 0, sG = 0;
-        int nf = 0;
-        for (int hop = 1; hop <= 2 && nf == 0; hop++) {
-            // the qualifying neighbours (fluid, not fresh) first, so that the
-            // population loads below are independent of one another
-            int nbr[Q - 1];
-            bool ok[Q - 1];
-#pragma unroll
-            for (int i = 1; i < Q; i++) {
-                int X = ((x + hop * cx(i)) % I.nx + I.nx) % I.nx;
-                int Y = ((y + hop * cy(i)) % I.ny + I.ny) % I.ny;
-                int Z = ((z + hop * cz(i)) % I.nz + I.nz) % I.nz;
-                nbr[i - 1] = (Z * I.ny + Y) * I.nx + X;
-            }
-#pragma unroll
-            for (int i = 0; i < Q - 1; i++) {
-                const uint8_t fm = fli[nbr[i]];
-                ok[i] = (fm & OWNER_MASK) == OWN_FLUID && !(fm & FRESH_BIT);
-            }
-#pragma unroll 2
-            for (int i = 0; i < Q - 1; i++) {
-                if (!ok[i]) continue;
-                const int m = nbr[i];
-                R aF = 0, aG = 0;
+    R sF = 0, sG = 0;
+    int nf = 0;
+    for (int hop = 1; hop <= 2 && nf == 0; hop++) {
+        R aF = 0, aG = 0;
+        int ok = 0;
+        if (lane < Q - 1) {
+            const int i = lane + 1;
+            const int X = ((x + hop * cx(i)) % I.nx + I.nx) % I.nx;
+            const int Y = ((y + hop * cy(i)) % I.ny + I.ny) % I.ny;
+            const int Z = ((z + hop * cz(i)) % I.nz + I.nz) % I.nz;
+            const int m = (Z * I.ny + Y) * I.nx + X;
+            const uint8_t fm = fli[m];
+            if ((fm & OWNER_MASK) == OWN_FLUID && !(fm & FRESH_BIT)) {
+                ok = 1;
 #pragma unroll
                 for (int j = 0; j < Q; j++) {
                     aF += wgt<R>(j) * (R(1) + Store<S>::ld(pop + j * N + m));
                     aG += wgt<R>(j) * Store<S>::ld(pop + (Q + j) * N + m);
                 }
-                sF += aF;
-                sG += aG;
-                nf++;
             }
         }
-        // mean rho/rho0 and (rho^a - rho^b)/rho0 of the neighbours
-        R rr, rd;
-        if (nf > 0) { rr = sF / nf; rd = sG / nf; }
-        else { rr = R(1); rd = R(-1); }
-        const int prev = particle_owner(I, L.parts, x, y, z, 1);
-        const PartDev &P = L.parts[I.part_off + (prev >= 2 ? prev - 2 : 0)];
-        R c[3];
-        centre(P, c);
-        const R d0 = min_image_r<R>(x - c[0], I.nx), d1 = min_image_r<R>(y - c[1], I.ny),
-                d2 = min_image_r<R>(z - c[2], I.nz);
-        const R w[3] = {(R)P.w[0], (R)P.w[1], (R)P.w[2]};
-        const R u[3] = {(R)P.v[0] + w[1] * d2 - w[2] * d1, (R)P.v[1] + w[2] * d0 - w[0] * d2,
-                        (R)P.v[2] + w[0] * d1 - w[1] * d0};
-        const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        for (int i = 0; i < Q; i++) {
-            const R cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
-            const R e = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
-            Store<S>::st(pop + i * N + n, rr * e - R(1));
-            Store<S>::st(pop + (Q + i) * N + n, rd * e);
+        sF = warp_sum(aF);
+        sG = warp_sum(aG);
+        nf = __reduce_add_sync(0xffffffffu, ok);
+    }
+    // mean rho/rho0 and (rho^a - rho^b)/rho0 of the neighbours
+    R rr, rd;
+    if (nf > 0) { rr = sF / nf; rd = sG / nf; }
+    else { rr = R(1); rd = R(-1); }
+    if (lane >= Q) return;
+    const int prev = particle_owner(I, parts, x, y, z, 1);
+    const PartDev &P = parts[I.part_off + (prev >= 2 ? prev - 2 : 0)];
+    R c[3];
+    centre(P, c);
+    const R d0 = min_image_r<R>(x - c[0], I.nx), d1 = min_image_r<R>(y - c[1], I.ny),
+            d2 = min_image_r<R>(z - c[2], I.nz);
+    const R w[3] = {(R)P.w[0], (R)P.w[1], (R)P.w[2]};
+    const R u[3] = {(R)P.v[0] + w[1] * d2 - w[2] * d1, (R)P.v[1] + w[2] * d0 - w[0] * d2,
+                    (R)P.v[2] + w[0] * d1 - w[1] * d0};
+    const R uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const int i = lane;
+    const int n = (z * I.ny + y) * I.nx + x;
+    const R cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
+    const R e = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+    Store<S>::st(pop + i * N + n, rr * e - R(1));
+    Store<S>::st(pop + (Q + i) * N + n, rd * e);
+}
+
+template <class S>
+__global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int side)
+{
+    const PartDev &P0 = L.parts[blockIdx.y];
+    const InstDev &I = L.inst[P0.inst];
+    Region reg;
+    reg.init(P0.x, side, I.nx, I.ny, I.nz);
+    S *pop = (S *)L.pop[nxt] + NPOP * I.node_off;
+    const uint8_t *fli = L.flags + I.node_off;
+    const int lane = threadIdx.x & 31;
+    const long long count = reg.count();
+    // warp-uniform trip count: every lane takes part in the ballots
+    for (long long t0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < count;
+         t0 += (long long)gridDim.x * blockDim.x) {
+        const long long t = t0 + lane;
+        int x = 0, y = 0, z = 0;
+        bool fresh = false;
+        if (t < count) {
+            reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
+            fresh = (fli[(z * I.ny + y) * I.nx + x] & FRESH_BIT) != 0;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, fresh);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int X = __shfl_sync(0xffffffffu, x, src), Y = __shfl_sync(0xffffffffu, y, src),
+                      Z = __shfl_sync(0xffffffffu, z, src);
+            refill_node<S>(I, L.parts, pop, fli, X, Y, Z, lane);
         }
     }
 }
