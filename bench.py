@@ -29,19 +29,20 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and % of HBM roofline at 1 GB300 (FP32 vs FP16-storage vs batched) at stated error"
 UNIT = "MLUPS"
 WORKLOAD = "drop R=40 sliding over a 150 deg wall + 8 spheres R_p=8, 256x128x128 (4.19M nodes), coupled LBM-DEM step"
-# algorithmic bytes per lattice update of the fluid update: read + write of
-# 2 x 19 populations
-ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
-DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}
+# element bytes of the total (F) and colour (G) populations; algorithmic bytes
+# per lattice update of the fluid update: read + write of 19 F and 19 G
+ELEM = {"fp64": (8, 8), "fp32": (4, 4), "fp16": (2, 2), "bf16": (2, 2), "mixed": (2, 4)}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math",
+         "mixed": "f16(F)+f32(G)-storage/f32-math"}
 
 
 def algorithmic_bytes_per_node(stage, prec):
     """Bytes a kernel must move per node: the order-parameter pass reads the 38
     streamed populations and writes phi; the collision reads the 19 streamed
     total populations and phi and writes all 38 populations."""
-    e = ELEM[prec]
+    ef, eg = ELEM[prec]
     r = 8 if prec == "fp64" else 4
-    return {"collide": 57 * e + r, "phi": 38 * e + r}.get(stage, 0)
+    return {"collide": 38 * ef + 19 * eg + r, "phi": 19 * (ef + eg) + r}.get(stage, 0)
 
 
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
@@ -208,7 +209,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=300)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "mixed", "fp64"], default="fp32")
     ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit and batched extra measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline sample")
     args = ap.parse_args()
@@ -275,7 +276,7 @@ def main():
     dom_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
     dom_bytes = algorithmic_bytes_per_node(dom, args.precision) * N
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
-    step_bytes = 76 * ELEM[args.precision] * N
+    step_bytes = 38 * sum(ELEM[args.precision]) * N
     roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=hbm, unit="GB/s",
                     frac=(achieved / hbm) if achieved else None,
                     traffic=NCU_TRAFFIC.get((dom, args.precision)), peak_source=peak_src,
@@ -331,10 +332,10 @@ def e2e_measure(torch, lbm, W, args, stream):
 
 
 def extra_measure(torch, lbm, W, args, stream, N):
-    """FP16/BF16 offset storage on the same workload, and the batched sweep."""
+    """FP16/BF16/mixed offset storage on the same workload, and the batched sweep."""
     out = {}
     K = max(50, args.steps // 4)
-    for prec in ("fp16", "bf16"):
+    for prec in ("fp16", "bf16", "mixed"):
         w = W.cfg2()
         ctx = build_context(lbm, w, prec, stream.cuda_stream)
         ctx.lbm_init_fields(w["phi"])
@@ -345,7 +346,8 @@ def extra_measure(torch, lbm, W, args, stream, N):
         col = prof["collide"]
         cms = col["ms"] / max(1, col["launches"])
         out[prec] = dict(value=N * K / (ms_g * 1e-3) / 1e6, value_profiled=N * K / (ms * 1e-3) / 1e6,
-                         collide_ms=cms, collide_gbs=(57 * 2 + 4) * N / (cms * 1e-3) / 1e9, steps=K)
+                         collide_ms=cms, collide_gbs=algorithmic_bytes_per_node("collide", prec) * N / (cms * 1e-3) / 1e9,
+                         steps=K)
     ws = W.cfg4()
     params = [dict(w["params"], store_velocity=0) for w in ws]
     ctx = lbm.Context(params, "fp16", stream=stream.cuda_stream)

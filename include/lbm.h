@@ -64,13 +64,18 @@ typedef enum {
 
 /* Population storage.  FP64 and FP32 store f_i/(w_i rho0) - 1 and
  * (f^a_i - f^b_i)/(w_i rho0); the 16-bit forms store the same offsets in
- * half or bfloat16 with FP32 collision arithmetic.  Particle sums, the DEM and
- * mass sums are FP64 in every form. */
+ * half or bfloat16 with FP32 collision arithmetic.  The mixed form stores the
+ * total offsets in half and the colour offsets in FP32 (114 bytes per node
+ * and copy instead of 152): the order parameter, whose rounding noise the
+ * interface forces amplify into the velocity, keeps FP32 accuracy.  It runs
+ * the plain launch form only.  Particle
+ * sums, the DEM and mass sums are FP64 in every form. */
 typedef enum {
     LBM_FP64 = 0,
     LBM_FP32 = 1,
     LBM_FP16_OFFSET = 2,
-    LBM_BF16_OFFSET = 3
+    LBM_BF16_OFFSET = 3,
+    LBM_F16_F32_OFFSET = 4
 } lbm_precision;
 
 /* Physical parameters of one instance (lattice units, dt = dx = 1).

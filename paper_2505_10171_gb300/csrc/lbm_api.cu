@@ -23,6 +23,8 @@ struct lbm_ctx {
     long long Ntot = 0;
     int cta_cap = 0;  // CTAs per SM of the persistent staged kernels at most (0: occupancy)
     size_t elem = 8, real_sz = 8;
+    size_t pop_node_bytes = 0;  // population bytes per node (both halves)
+    size_t pop_bytes = 0;       // bytes of one population buffer (all instances)
     uint8_t *flags = nullptr;
     void *pop[2] = {nullptr, nullptr};
     void *phi = nullptr, *grad = nullptr, *gmag = nullptr, *kap = nullptr, *u = nullptr;
@@ -104,7 +106,7 @@ static void plan_launch(lbm_ctx *c)
     plan_fused(c);
     c->fz.gc_items = plan_gradcurv(c->inst_h);
     const bool aligned = plan_rows(c->inst_h, c->elem, &c->fz.rows);
-    c->fz.st_items = aligned ? c->fz.rows : 0;
+    c->fz.st_items = aligned && c->prec != LBM_F16_F32_OFFSET ? c->fz.rows : 0;
     dispatch_grids(c);
 }
 
@@ -185,15 +187,15 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
     using R = typename Store<S>::real;
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
-    S *pop = (S *)L.pop[cur] + NPOP * I.node_off;
+    const Pop<S> pop(L.pop[cur], I);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if (pops) {
             for (int a = 0; a < Q; a++) {
                 int i = map.dev[a];
                 double w = wgt<double>(i) * I.rho0;
                 double fa = pops[(long long)a * N + n], fb = pops[(long long)(Q + a) * N + n];
-                Store<S>::st(pop + (long long)i * N + n, (R)((fa + fb) / w - 1.0));
-                Store<S>::st(pop + (long long)(Q + i) * N + n, (R)((fa - fb) / w));
+                pop.setF(i, (int)n, (R)((fa + fb) / w - 1.0));
+                pop.setG(i, (int)n, (R)((fa - fb) / w));
             }
             continue;
         }
@@ -206,8 +208,8 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
             double cu = cx(i) * uu[0] + cy(i) * uu[1] + cz(i) * uu[2];
             double e = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
             // f^{a,b} = feq(rho (1 +- phi)/2, u): total rho e w, colour rho phi e w
-            Store<S>::st(pop + (long long)i * N + n, (R)(rr * e - 1.0));
-            Store<S>::st(pop + (long long)(Q + i) * N + n, (R)(rr * ph * e));
+            pop.setF(i, (int)n, (R)(rr * e - 1.0));
+            pop.setG(i, (int)n, (R)(rr * ph * e));
         }
         if (I.store_u) {
             R *U = (R *)L.u;
@@ -223,7 +225,7 @@ __global__ void k_read(Lattice L, int cur, int inst, unsigned mask, double *out,
     using R = typename Store<S>::real;
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
-    const S *pop = (const S *)L.pop[cur] + NPOP * I.node_off;
+    const Pop<S> pop(L.pop[cur], I);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         const uint8_t f = L.flags[I.node_off + n];
         const bool fluid = (f & OWNER_MASK) == OWN_FLUID;
@@ -231,8 +233,8 @@ __global__ void k_read(Lattice L, int cur, int inst, unsigned mask, double *out,
         if (fluid)
             for (int i = 0; i < Q; i++) {
                 double w = wgt<double>(i) * I.rho0;
-                double Fv = (double)Store<S>::ld(pop + (long long)i * N + n);
-                double Gv = (double)Store<S>::ld(pop + (long long)(Q + i) * N + n);
+                double Fv = (double)pop.F(i, (int)n);
+                double Gv = (double)pop.G(i, (int)n);
                 ra += 0.5 * w * (1.0 + Fv + Gv);
                 rb += 0.5 * w * (1.0 + Fv - Gv);
             }
@@ -249,8 +251,8 @@ __global__ void k_read(Lattice L, int cur, int inst, unsigned mask, double *out,
             for (int a = 0; a < Q; a++) {
                 int i = map.dev[a];
                 double w = wgt<double>(i) * I.rho0;
-                double Fv = fluid ? (double)Store<S>::ld(pop + (long long)i * N + n) : 0.0;
-                double Gv = fluid ? (double)Store<S>::ld(pop + (long long)(Q + i) * N + n) : 0.0;
+                double Fv = fluid ? (double)pop.F(i, (int)n) : 0.0;
+                double Gv = fluid ? (double)pop.G(i, (int)n) : 0.0;
                 out[off + (long long)a * N + n] = fluid ? 0.5 * w * (1.0 + Fv + Gv) : 0.0;
                 out[off + (long long)(Q + a) * N + n] = fluid ? 0.5 * w * (1.0 + Fv - Gv) : 0.0;
             }
@@ -267,14 +269,14 @@ __global__ void k_mass_partial(Lattice L, int cur, int inst, double *part)
 {
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
-    const S *pop = (const S *)L.pop[cur] + NPOP * I.node_off;
+    const Pop<S> pop(L.pop[cur], I);
     double sa = 0.0, sb = 0.0;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
         for (int i = 0; i < Q; i++) {
             double w = wgt<double>(i) * I.rho0;
-            double Fv = (double)Store<S>::ld(pop + (long long)i * N + n);
-            double Gv = (double)Store<S>::ld(pop + (long long)(Q + i) * N + n);
+            double Fv = (double)pop.F(i, (int)n);
+            double Gv = (double)pop.G(i, (int)n);
             sa += 0.5 * w * (1.0 + Fv + Gv);
             sb += 0.5 * w * (1.0 + Fv - Gv);
         }
@@ -314,16 +316,16 @@ __global__ void k_speed_partial(Lattice L, int cur, int inst, double *part)
 {
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
-    const S *pop = (const S *)L.pop[cur] + NPOP * I.node_off;
+    const Pop<S> pop(L.pop[cur], I);
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
         double sF = 0.0, sG = 0.0, j[3] = {0.0, 0.0, 0.0};
         for (int i = 0; i < Q; i++) {
             const double w = wgt<double>(i);
-            const double Fv = (double)Store<S>::ld(pop + (long long)i * N + n);
+            const double Fv = (double)pop.F(i, (int)n);
             sF += w * Fv;
-            sG += w * (double)Store<S>::ld(pop + (long long)(Q + i) * N + n);
+            sG += w * (double)pop.G(i, (int)n);
             j[0] += w * cx(i) * Fv;
             j[1] += w * cy(i) * Fv;
             j[2] += w * cz(i) * Fv;
@@ -403,6 +405,7 @@ static void dispatch(lbm_precision p, F &&f)
     case LBM_FP32: f((float *)nullptr); break;
     case LBM_FP16_OFFSET: f((__half *)nullptr); break;
     case LBM_BF16_OFFSET: f((__nv_bfloat16 *)nullptr); break;
+    case LBM_F16_F32_OFFSET: f((MixedF16F32 *)nullptr); break;
     }
 }
 
@@ -410,7 +413,7 @@ static void dispatch_grids(lbm_ctx *c)
 {
     dispatch(c->prec, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
-        staged_grids<S>(c->fz.st_grid_phi, c->fz.st_grid_collide, c->cta_cap);
+        if constexpr (!is_mixed<S>) staged_grids<S>(c->fz.st_grid_phi, c->fz.st_grid_collide, c->cta_cap);
     });
 }
 
@@ -670,16 +673,21 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
     if (!params || n_instances < 1) return LBM_ERR_ARG;
-    if (prec < LBM_FP64 || prec > LBM_BF16_OFFSET) return LBM_ERR_UNSUPPORTED;
+    if (prec < LBM_FP64 || prec > LBM_F16_F32_OFFSET) return LBM_ERR_UNSUPPORTED;
     lbm_ctx *ctx = new lbm_ctx();
     ctx->prec = prec;
     ctx->n_inst = n_instances;
     ctx->P.assign(params, params + n_instances);
-    ctx->elem = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2);
+    ctx->elem = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 || prec == LBM_F16_F32_OFFSET ? 4 : 2);
+    dispatch(prec, [&](auto *tag) {
+        using S = std::remove_pointer_t<decltype(tag)>;
+        ctx->pop_node_bytes = Pop<S>::node_bytes;
+    });
     ctx->real_sz = prec == LBM_FP64 ? 8 : 4;
     ctx->diag_step.assign(n_instances, -1);
     lbm_status st;
     long long node_off = 0;
+    long long pop_off = 0;
     bool any_u = false;
     for (int k = 0; k < n_instances; k++) {
         const lbm_params &p = params[k];
@@ -694,6 +702,11 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.nx = p.nx; I.ny = p.ny; I.nz = p.nz;
         I.N = (long long)p.nx * p.ny * p.nz;
         I.node_off = node_off;
+        // mixed form: stride padded to 8 nodes keeps both halves of every
+        // instance block 16-byte aligned; the other forms keep stride N
+        I.pstride = (int)(prec == LBM_F16_F32_OFFSET ? (I.N + 7) / 8 * 8 : I.N);
+        I.pop_off = pop_off;
+        pop_off += (long long)I.pstride * (long long)ctx->pop_node_bytes;
         I.wall_z0 = p.wall_z0;
         I.store_u = p.store_velocity ? 1 : 0;
         any_u |= I.store_u != 0;
@@ -743,6 +756,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         node_off += I.N;
     }
     ctx->Ntot = node_off;
+    ctx->pop_bytes = (size_t)pop_off;
     plan_launch(ctx);
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
@@ -778,8 +792,8 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     };
     const size_t Nt = (size_t)ctx->Ntot;
     if ((st = alloc((void **)&ctx->inst_d, sizeof(InstDev) * n_instances)) ||
-        (st = alloc((void **)&ctx->flags, Nt + FLAG_PAD)) || (st = alloc(&ctx->pop[0], NPOP * Nt * ctx->elem)) ||
-        (st = alloc(&ctx->pop[1], NPOP * Nt * ctx->elem)) || (st = alloc(&ctx->phi, Nt * ctx->real_sz)) ||
+        (st = alloc((void **)&ctx->flags, Nt + FLAG_PAD)) || (st = alloc(&ctx->pop[0], ctx->pop_bytes)) ||
+        (st = alloc(&ctx->pop[1], ctx->pop_bytes)) || (st = alloc(&ctx->phi, Nt * ctx->real_sz)) ||
         (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc(&ctx->gmag, Nt * ctx->real_sz)) || (st = alloc(&ctx->kap, Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
         (st = alloc((void **)&ctx->diag_d, sizeof(double) * 2 * n_instances)) ||
         (st = alloc((void **)&ctx->diag_part, sizeof(double) * 2 * DIAG_BLOCKS)) ||
@@ -1271,6 +1285,8 @@ lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
     if (form < FORM_STAGED || form > FORM_PLAIN || tile < 0 || tile > max_tile || zchunk < 0)
         return fail(ctx, LBM_ERR_ARG,
                     "form must be 0 (staged, tile 0..2), 1 (fused, tile 0..1) or 2 (plain, tile 0); zchunk >= 0");
+    if (ctx->prec == LBM_F16_F32_OFFSET && form != FORM_PLAIN)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "the mixed FP16/FP32 storage runs the plain form only");
     CU(cudaStreamSynchronize(ctx->stream));
     // the device table is authoritative (the drop-speed control writes it)
     CU(cudaMemcpy(ctx->inst_h.data(), ctx->inst_d, sizeof(InstDev) * ctx->n_inst, cudaMemcpyDeviceToHost));
@@ -1557,6 +1573,7 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *m
     lbm_status st = LBM_OK;
     for (int k = 0; k < 6 && st == LBM_OK; k++) {
         if (ms_per_step) ms_per_step[k] = -1.0;
+        if (ctx->prec == LBM_F16_F32_OFFSET && cand[k][0] != FORM_PLAIN) continue;
         if ((st = lbm_set_fluid_kernel(ctx, cand[k][0], cand[k][1], 0)) != LBM_OK) break;
         if (lbm_fluid_form_in_use(ctx) != cand[k][0]) continue;  // staged form not available here
         if ((st = lbm_step(ctx, 2)) != LBM_OK) break;            // capture and warm up

@@ -65,10 +65,10 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     using R = typename Store<S>::real;
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
-    const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
+    const Pop<S> in(L.pop[cur], I);
     Nbr nb;
     nb.init(x, y, z, I.nx, I.ny, I.nz);
-    R v = phi_fluid<S>(nb, in, (int)I.N);
+    R v = phi_fluid<S>(nb, in);
     keep(v);
     if ((fl & OWNER_MASK) != OWN_FLUID) return;
     if (fl & BOUND_BIT) {
@@ -76,7 +76,7 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
         GlobalNbr gnb;
         gnb.nb = nb;
         gnb.fli = L.flags + I.node_off;
-        v = node_phi<S>(I, L.parts, gnb, in, (int)I.N, n, fl, x, y, z);
+        v = node_phi<S>(I, L.parts, gnb, in, n, fl, x, y, z);
     }
     ((R *)L.phi)[g] = v;
 }
@@ -222,12 +222,12 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_phi_bound(Lattice L, int cu
     const long long g = I->node_off + n;
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
-    const S *in = (const S *)L.pop[cur] + NPOP * I->node_off;
+    const Pop<S> in(L.pop[cur], *I);
     GlobalNbr nb;
     nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
     nb.fli = L.flags + I->node_off;
     R F[Q], G[Q], sF = 0, sG = 0;
-    gather_all<S>(*I, L.parts, nb, in, (int)I->N, n, F, G, x, y, z);
+    gather_all<S>(*I, L.parts, nb, in, n, F, G, x, y, z);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         sF += wgt<R>(i) * F[i];
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_collide_bound(Lattice L, in
     const long long g = I->node_off + n;
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
-    const S *in = (const S *)L.pop[cur] + NPOP * I->node_off;
-    S *out = (S *)L.pop[cur ^ 1] + NPOP * I->node_off;
+    const Pop<S> in(L.pop[cur], *I);
+    const Pop<S> out(L.pop[cur ^ 1], *I);
     const R *Nn = (const R *)L.grad + I->node_off;
     const long long Nt = L.Ntot;
     R *U = I->store_u ? (R *)L.u + I->node_off : nullptr;
@@ -255,13 +255,13 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_collide_bound(Lattice L, in
     nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
     nb.fli = L.flags + I->node_off;
     R F[Q];
-    gather_all<S>(*I, L.parts, nb, in, (int)I->N, n, F, (R *)nullptr, x, y, z);
+    gather_all<S>(*I, L.parts, nb, in, n, F, (R *)nullptr, x, y, z);
     FluidPar<R> P;
     load_par(*I, P);
     const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
     const R m = ((const R *)L.gmag)[g];
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, nn, ((const R *)L.kap)[g], out, (int)I->N, n, U, L.Ntot,
+    collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, nn, ((const R *)L.kap)[g], out, n, U, L.Ntot,
                          L.status);
 }
 
@@ -290,10 +290,9 @@ template <class S>
 __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
 {
     using R = typename Store<S>::real;
-    const int N = (int)I.N;
     const long long g = I.node_off + n;
-    const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
-    S *out = (S *)L.pop[cur ^ 1] + NPOP * I.node_off;
+    const Pop<S> in(L.pop[cur], I);
+    const Pop<S> out(L.pop[cur ^ 1], I);
     // every load of an interior fluid node is issued before the flag is tested
     const uint8_t fl = L.flags[g];
     const R *Nn = (const R *)L.grad + I.node_off;
@@ -306,7 +305,7 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     nb.init(x, y, z, I.nx, I.ny, I.nz);
     R F[Q];
 #pragma unroll
-    for (int i = 0; i < Q; i++) F[i] = Store<S>::ld(in + i * N + nb.at(-cx(i), -cy(i), -cz(i)));
+    for (int i = 0; i < Q; i++) F[i] = in.F(i, nb.at(-cx(i), -cy(i), -cz(i)));
 #pragma unroll
     for (int i = 0; i < Q; i++) keep(F[i]);
     R *U = I.store_u ? (R *)L.u + I.node_off : nullptr;
@@ -319,7 +318,7 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     FluidPar<R> P;
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, U, L.Ntot, L.status);
 }
 
 template <class S>
@@ -538,7 +537,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
                        const FluidLaunch &fz, const Hook &after_grad, const SideLane &lane)
 {
     using R = typename Store<S>::real;
-    if (fz.form == FORM_FUSED) {
+    if (fz.form == FORM_FUSED && !is_mixed<S>) {
         if (L.n_parts > 0) {
             // phi and grad(phi) around the particles, for the capillary force:
             // corners of the surface points lie within R_p + 2 of the centre,
@@ -553,13 +552,13 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
             *launches += 3;
         }
         mk(STAGE_FUSED, 0);
-        launch_fused_form<S>(L, cur, fz, st);
+        if constexpr (!is_mixed<S>) launch_fused_form<S>(L, cur, fz, st);
         mk(STAGE_FUSED, 1);
         *launches += 1;
         return;
     }
     // staged form where every instance's rows are whole 16-byte units, plain otherwise
-    const bool staged = fz.form == FORM_STAGED && fz.st_items > 0;
+    const bool staged = fz.form == FORM_STAGED && fz.st_items > 0 && !is_mixed<S>;
     const dim3 grid((unsigned)fz.rows);  // one CTA per row-strip work item
     // boundary passes: particle cubes and the static list of nodes next to walls
     const long long bctas = (long long)L.n_parts * L.cap_blocks + (L.n_static_bfl + PART_THREADS - 1) / PART_THREADS;
@@ -587,7 +586,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     };
     if (staged) {
         mk(STAGE_PHI, 0);
-        launch_staged_phi<S>(L, cur, fz, st);
+        if constexpr (!is_mixed<S>) launch_staged_phi<S>(L, cur, fz, st);
         mk(STAGE_PHI, 1);
     } else {
         bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] { k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
@@ -610,7 +609,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     after_grad();
     if (staged) {
         mk(STAGE_COLLIDE, 0);
-        launch_staged_collide<S>(L, cur, fz, st);
+        if constexpr (!is_mixed<S>) launch_staged_collide<S>(L, cur, fz, st);
         mk(STAGE_COLLIDE, 1);
     } else {
         bound_pass(k_collide_bound<S>, STAGE_COLLIDE_BOUND, STAGE_COLLIDE,
@@ -627,6 +626,7 @@ INST(double)
 INST(float)
 INST(__half)
 INST(__nv_bfloat16)
+INST(MixedF16F32)
 #undef INST
 
 }  // namespace lbmg

@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(TX *TY, 2) k_fused(Lattice L, int cur)
     const int z1 = min(z0 + I.zc, I.nz);
     const int nx = I.nx, ny = I.ny, nz = I.nz;
     const int N = (int)I.N;
-    const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
-    S *out = (S *)L.pop[cur ^ 1] + NPOP * I.node_off;
+    const Pop<S> in(L.pop[cur], I);
+    const Pop<S> out(L.pop[cur ^ 1], I);
     const uint8_t *fli = L.flags + I.node_off;
     R *U = I.store_u ? (R *)L.u + I.node_off : nullptr;
     FluidPar<R> P;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(TX *TY, 2) k_fused(Lattice L, int cur)
                     GlobalNbr nb;
                     nb.nb.init(X, Y, Z, nx, ny, nz);
                     nb.fli = fli;
-                    ph = node_phi<S>(I, L.parts, nb, in, N, n, fl, X, Y, Z);
+                    ph = node_phi<S>(I, L.parts, nb, in, n, fl, X, Y, Z);
                 }
                 phiS[s * RN + r] = ph;
             }
@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(TX *TY, 2) k_fused(Lattice L, int cur)
                 };
                 const R kap = curvature<R>(nf);
                 R F[Q];
-                gather_F<S>(I, L.parts, nb, in, N, n, fl, F, gx, gy, Z);
-                collide_store_phi<S>(P, F, phiS[s0 * RN + r], gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+                gather_F<S>(I, L.parts, nb, in, n, fl, F, gx, gy, Z);
+                collide_store_phi<S>(P, F, phiS[s0 * RN + r], gr, nn, kap, out, n, U, L.Ntot, L.status);
             }
         }
         __syncthreads();

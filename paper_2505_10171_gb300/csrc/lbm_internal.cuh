@@ -60,6 +60,8 @@ struct InstDev {
     int nx, ny, nz, np;
     long long N;         // nodes of the instance
     long long node_off;  // first node in the per-node arrays
+    long long pop_off;   // byte offset of the instance's population block
+    int pstride;         // population stride (N; padded to a multiple of 8 in the mixed form)
     int part_off;        // first particle of the instance
     int hist_off;        // first pair-history record of the instance
     int crec_off;        // first DEM contact record of the instance
@@ -205,6 +207,56 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// mixed storage: the total offsets F in FP16 and the colour offsets G in FP32.
+// The colour offsets carry the order parameter, whose rounding noise the
+// interface forces amplify into the velocity; the total offsets are small
+// (|F_i| ~ 3|u| away from walls) and tolerate half precision.
+struct MixedF16F32 {};
+template <>
+struct Store<MixedF16F32> {
+    using real = float;
+};
+
+// element types of the two halves of the population storage
+template <class S>
+struct PopTypes {
+    using F = S;
+    using G = S;
+};
+template <>
+struct PopTypes<MixedF16F32> {
+    using F = __half;
+    using G = float;
+};
+template <class S>
+constexpr bool is_mixed = false;
+template <>
+constexpr bool is_mixed<MixedF16F32> = true;
+
+// populations of one instance: F_i (i < 19, i-major, stride pstride) at the
+// start of the instance's block, G_i after them; instance blocks follow one
+// another in node order.  pstride = N (Q (sizeof F + sizeof G) bytes per node)
+// except in the mixed form, where it is rounded up to a multiple of 8 so that
+// the FP32 half starts 16-byte aligned
+template <class S>
+struct Pop {
+    using FT = typename PopTypes<S>::F;
+    using GT = typename PopTypes<S>::G;
+    using R = typename Store<S>::real;
+    static constexpr size_t node_bytes = Q * (sizeof(FT) + sizeof(GT));
+    FT *f;  // the G block starts Q N F-elements later (derived, not stored: one pointer fewer in registers)
+    int N;  // stride between directions (the instance's pstride)
+    __host__ __device__ __forceinline__ Pop(const void *base, const InstDev &I)
+        : f((FT *)((char *)base + I.pop_off)), N(I.pstride)
+    {
+    }
+    __device__ __forceinline__ GT *g() const { return (GT *)(f + Q * N); }
+    __device__ __forceinline__ R F(int i, int m) const { return Store<FT>::ld(f + i * N + m); }
+    __device__ __forceinline__ R G(int i, int m) const { return Store<GT>::ld(g() + i * N + m); }
+    __device__ __forceinline__ void setF(int i, int m, R v) const { Store<FT>::st(f + i * N + m, v); }
+    __device__ __forceinline__ void setG(int i, int m, R v) const { Store<GT>::st(g() + i * N + m, v); }
+};
+
 // minimum-image displacement on a periodic axis of n nodes (|d| < 3n/2): the
 // same value as d - n floor(d/n + 1/2) without a double-precision division
 __host__ __device__ __forceinline__ double min_image(double d, int n)
@@ -317,7 +369,7 @@ struct GlobalNbr {
 // A is the neighbourhood accessor (global flags, or a shared-memory copy).
 template <class S, class A>
 __device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, const A &nbr,
-                                       const S *__restrict__ in, int N, int n, uint8_t fl,
+                                       const Pop<S> &in, int n, uint8_t fl,
                                        typename Store<S>::real *F, typename Store<S>::real *G, int x, int y, int z)
 {
     using R = typename Store<S>::real;
@@ -325,8 +377,8 @@ __device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, c
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-            F[i] = Store<S>::ld(in + i * N + s);
-            G[i] = Store<S>::ld(in + (Q + i) * N + s);
+            F[i] = in.F(i, s);
+            G[i] = in.G(i, s);
         }
         return;
     }
@@ -337,16 +389,16 @@ __device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, c
         const int own = nbr.own(-cx(i), -cy(i), -cz(i));
         if (own == OWN_FLUID) {
             const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-            F[i] = Store<S>::ld(in + i * N + s);
-            G[i] = Store<S>::ld(in + (Q + i) * N + s);
+            F[i] = in.F(i, s);
+            G[i] = in.G(i, s);
             continue;
         }
         if (!have_rho) {
             R sF = 0, sG = 0;
 #pragma unroll
             for (int j = 0; j < Q; j++) {
-                sF += wgt<R>(j) * Store<S>::ld(in + j * N + n);
-                sG += wgt<R>(j) * Store<S>::ld(in + (Q + j) * N + n);
+                sF += wgt<R>(j) * in.F(j, n);
+                sG += wgt<R>(j) * in.G(j, n);
             }
             rr = R(1) + sF;
             rd = sG;
@@ -356,8 +408,8 @@ __device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, c
         surface_velocity<R>(I, parts, own, x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
         const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
         const int ib = opp(i);
-        F[i] = Store<S>::ld(in + ib * N + n) + R(6) * rr * cu;
-        G[i] = Store<S>::ld(in + (Q + ib) * N + n) + R(6) * rd * cu;
+        F[i] = in.F(ib, n) + R(6) * rr * cu;
+        G[i] = in.G(ib, n) + R(6) * rd * cu;
     }
 }
 
@@ -366,13 +418,13 @@ __device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, c
 // the order parameter, which the order-parameter kernel has already stored
 template <class S, class A>
 __device__ __forceinline__ void gather_F(const InstDev &I, const PartDev *parts, const A &nbr,
-                                         const S *__restrict__ in, int N, int n, uint8_t fl,
+                                         const Pop<S> &in, int n, uint8_t fl,
                                          typename Store<S>::real *F, int x, int y, int z)
 {
     using R = typename Store<S>::real;
     if (!(fl & BOUND_BIT)) {
 #pragma unroll
-        for (int i = 0; i < Q; i++) F[i] = Store<S>::ld(in + i * N + nbr.idx(-cx(i), -cy(i), -cz(i)));
+        for (int i = 0; i < Q; i++) F[i] = in.F(i, nbr.idx(-cx(i), -cy(i), -cz(i)));
         return;
     }
     bool have_rho = false;
@@ -381,20 +433,20 @@ __device__ __forceinline__ void gather_F(const InstDev &I, const PartDev *parts,
     for (int i = 0; i < Q; i++) {
         const int own = nbr.own(-cx(i), -cy(i), -cz(i));
         if (own == OWN_FLUID) {
-            F[i] = Store<S>::ld(in + i * N + nbr.idx(-cx(i), -cy(i), -cz(i)));
+            F[i] = in.F(i, nbr.idx(-cx(i), -cy(i), -cz(i)));
             continue;
         }
         if (!have_rho) {
             R sF = 0;
 #pragma unroll
-            for (int j = 0; j < Q; j++) sF += wgt<R>(j) * Store<S>::ld(in + j * N + n);
+            for (int j = 0; j < Q; j++) sF += wgt<R>(j) * in.F(j, n);
             rr = R(1) + sF;
             have_rho = true;
         }
         R uw[3];
         surface_velocity<R>(I, parts, own, x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
         const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
-        F[i] = Store<S>::ld(in + opp(i) * N + n) + R(6) * rr * cu;
+        F[i] = in.F(opp(i), n) + R(6) * rr * cu;
     }
 }
 
@@ -403,7 +455,7 @@ __device__ __forceinline__ void gather_F(const InstDev &I, const PartDev *parts,
 // trip instead of one per link); G is skipped when null
 template <class S, class A>
 __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *parts, const A &nbr,
-                                           const S *__restrict__ in, int N, int n, typename Store<S>::real *F,
+                                           const Pop<S> &in, int n, typename Store<S>::real *F,
                                            typename Store<S>::real *G, int x, int y, int z)
 {
     using R = typename Store<S>::real;
@@ -413,11 +465,11 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
     for (int i = 0; i < Q; i++) {
         const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
         own[i] = nbr.own(-cx(i), -cy(i), -cz(i));
-        pF[i] = Store<S>::ld(in + i * N + s);
-        oF[i] = Store<S>::ld(in + i * N + n);
+        pF[i] = in.F(i, s);
+        oF[i] = in.F(i, n);
         if (G) {
-            pG[i] = Store<S>::ld(in + (Q + i) * N + s);
-            oG[i] = Store<S>::ld(in + (Q + i) * N + n);
+            pG[i] = in.G(i, s);
+            oG[i] = in.G(i, n);
         }
     }
     R sF = 0, sG = 0;
@@ -445,15 +497,15 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
 
 // order parameter of a fluid node none of whose neighbours is solid
 template <class S, class A>
-__device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const S *__restrict__ in, int N)
+__device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const Pop<S> &in)
 {
     using R = typename Store<S>::real;
     R sF = 0, sG = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-        sF += wgt<R>(i) * Store<S>::ld(in + i * N + s);
-        sG += wgt<R>(i) * Store<S>::ld(in + (Q + i) * N + s);
+        sF += wgt<R>(i) * in.F(i, s);
+        sG += wgt<R>(i) * in.G(i, s);
     }
     return sG / (R(1) + sF);
 }
@@ -462,14 +514,14 @@ __device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const
 // collision's, without keeping the 38 values
 template <class S, class A>
 __device__ __forceinline__ typename Store<S>::real node_phi(const InstDev &I, const PartDev *parts, const A &nbr,
-                                                            const S *__restrict__ in, int N, int n, uint8_t fl,
+                                                            const Pop<S> &in, int n, uint8_t fl,
                                                             int x, int y, int z)
 {
     using R = typename Store<S>::real;
-    if (!(fl & BOUND_BIT)) return phi_fluid<S>(nbr, in, N);
+    if (!(fl & BOUND_BIT)) return phi_fluid<S>(nbr, in);
     R sF = 0, sG = 0;
     R F[Q], G[Q];
-    gather<S>(I, parts, nbr, in, N, n, fl, F, G, x, y, z);
+    gather<S>(I, parts, nbr, in, n, fl, F, G, x, y, z);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         sF += wgt<R>(i) * F[i];

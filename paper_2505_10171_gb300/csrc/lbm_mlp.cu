@@ -595,6 +595,7 @@ INST(double)
 INST(float)
 INST(__half)
 INST(__nv_bfloat16)
+INST(MixedF16F32)
 #undef INST
 
 }  // namespace lbmg

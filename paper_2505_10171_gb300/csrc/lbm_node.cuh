@@ -135,10 +135,15 @@ template <class S>
 __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<S>::real> &P,
                                                   const typename Store<S>::real *F, typename Store<S>::real phi,
                                                   const typename Store<S>::real *g, const typename Store<S>::real *nn,
-                                                  typename Store<S>::real kap, S *__restrict__ out, int N, int n,
+                                                  typename Store<S>::real kap, const Pop<S> &out, int n,
                                                   typename Store<S>::real *U, long long Ustride, unsigned *status)
 {
     using R = typename Store<S>::real;
+    using FT = typename Pop<S>::FT;
+    using GT = typename Pop<S>::GT;
+    const int N = out.N;
+    FT *const of = out.f + n;    // F_0 of this node; F_i at of + i N
+    GT *const og = out.g() + n;  // G_0 likewise
     R sF = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -176,8 +181,8 @@ __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<
         const R feq0 = sF + rr * (R(-1.5) * uu);
         const R fb0 = R(-3) * uF * P.ir0;
         const R Fs = F[0] - om * (F[0] - feq0) + cpe * fb0;
-        Store<S>::st(out + n, Fs);
-        Store<S>::st(out + Q * N + n, phi * (R(1) + Fs));
+        Store<FT>::st(of, Fs);
+        Store<GT>::st(og, phi * (R(1) + Fs));
     }
     // opposite pairs (i, i+9): the paper's S relaxes every even non-conserved
     // moment with omega and every odd one with omega', i.e. the MRT operator is
@@ -201,10 +206,10 @@ __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<
         const R inv_len = csq(i) == 1 ? R(1) : R(0.70710678118654752440);
         const R cn = (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]) * inv_len;
         const R rec = bq * cn;
-        Store<S>::st(out + i * N + n, Fi);
-        Store<S>::st(out + ib * N + n, Fib);
-        Store<S>::st(out + (Q + i) * N + n, phi * (R(1) + Fi) + rec);
-        Store<S>::st(out + (Q + ib) * N + n, phi * (R(1) + Fib) - rec);
+        Store<FT>::st(of + i * N, Fi);
+        Store<FT>::st(of + ib * N, Fib);
+        Store<GT>::st(og + i * N, phi * (R(1) + Fi) + rec);
+        Store<GT>::st(og + ib * N, phi * (R(1) + Fib) - rec);
     }
 }
 
@@ -243,19 +248,19 @@ __device__ __forceinline__ R reg_normal(const R *g, R eps2, R *nn)
 // kernels' hot loops
 template <class S>
 __device__ __noinline__ typename Store<S>::real phi_node_cold(const InstDev *Ip, const PartDev *parts,
-                                                              const uint8_t *fli, const S *in, int n, uint8_t fl,
+                                                              const uint8_t *fli, const Pop<S> &in, int n, uint8_t fl,
                                                               int x, int y, int z)
 {
     const InstDev &I = *Ip;
     GlobalNbr nb;
     nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
     nb.fli = fli;
-    return node_phi<S>(I, parts, nb, in, (int)I.N, n, fl, x, y, z);
+    return node_phi<S>(I, parts, nb, in, n, fl, x, y, z);
 }
 
 template <class S>
 __device__ __noinline__ void collide_node_cold(const InstDev *Ip, const PartDev *parts, const uint8_t *fli,
-                                               const S *in, S *out, int n, uint8_t fl, int x, int y, int z,
+                                               const Pop<S> &in, const Pop<S> &out, int n, uint8_t fl, int x, int y, int z,
                                                typename Store<S>::real phi, typename Store<S>::real n0,
                                                typename Store<S>::real n1, typename Store<S>::real n2,
                                                typename Store<S>::real m, typename Store<S>::real kap,
@@ -271,8 +276,8 @@ __device__ __noinline__ void collide_node_cold(const InstDev *Ip, const PartDev 
     const R nn[3] = {n0, n1, n2};
     const R gr[3] = {n0 * m, n1 * m, n2 * m};
     R F[Q];
-    gather_F<S>(I, parts, nb, in, (int)I.N, n, fl, F, x, y, z);
-    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, (int)I.N, n, U, Ntot, status);
+    gather_F<S>(I, parts, nb, in, n, fl, F, x, y, z);
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, U, Ntot, status);
 }
 
 }  // namespace lbmg

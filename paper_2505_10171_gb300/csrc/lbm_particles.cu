@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
         const uint8_t *fli = L.flags + I.node_off;
         const uint8_t fl = fli[n];
         if ((fl & OWNER_MASK) == OWN_FLUID && (fl & BOUND_BIT)) {
-            const S *in = (const S *)L.pop[cur] + NPOP * I.node_off;
+            const Pop<S> in(L.pop[cur], I);
             Nbr nb;
             nb.init(x, y, z, I.nx, I.ny, I.nz);
             const int mine = 2 + P.local;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
                 if ((fli[nb.at(-cx(i), -cy(i), -cz(i))] & OWNER_MASK) != mine) continue;
                 if (rr < R(0)) {
                     R sF = 0;
-                    for (int j = 0; j < Q; j++) sF += wgt<R>(j) * Store<S>::ld(in + j * N + n);
+                    for (int j = 0; j < Q; j++) sF += wgt<R>(j) * in.F(j, n);
                     rr = R(1) + sF;
                 }
                 const R lev[3] = {min_image_r<R>(x - R(0.5) * cx(i) - c[0], I.nx),
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
                                  v[2] + (w[0] * lev[1] - w[1] * lev[0])};
                 const int ib = opp(i);
                 const R wt = wgt<R>(i) * wr0;
-                const R Fo = Store<S>::ld(in + ib * N + n);
+                const R Fo = in.F(ib, n);
                 const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
                 const R fout = wt * (R(1) + Fo);
                 const R fin = wt * (R(1) + Fo + R(6) * rr * cu);
@@ -552,11 +552,10 @@ __device__ __forceinline__ R warp_sum(R v)
 }
 
 template <class S>
-__device__ void refill_node(const InstDev &I, const PartDev *parts, S *pop, const uint8_t *fli, int x, int y, int z,
-                            int lane)
+__device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S> &pop, const uint8_t *fli, int x, int y,
+                            int z, int lane)
 {
     using R = typename Store<S>::real;
-    const int N = (int)I.N;
     R sF = 0, sG = 0;
     int nf = 0;
     for (int hop = 1; hop <= 2 && nf == 0; hop++) {
@@ -573,8 +572,8 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, S *pop, cons
                 ok = 1;
 #pragma unroll
                 for (int j = 0; j < Q; j++) {
-                    aF += wgt<R>(j) * (R(1) + Store<S>::ld(pop + j * N + m));
-                    aG += wgt<R>(j) * Store<S>::ld(pop + (Q + j) * N + m);
+                    aF += wgt<R>(j) * (R(1) + pop.F(j, m));
+                    aG += wgt<R>(j) * pop.G(j, m);
                 }
             }
         }
@@ -601,8 +600,8 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, S *pop, cons
     const int n = (z * I.ny + y) * I.nx + x;
     const R cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
     const R e = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
-    Store<S>::st(pop + i * N + n, rr * e - R(1));
-    Store<S>::st(pop + (Q + i) * N + n, rd * e);
+    pop.setF(i, n, rr * e - R(1));
+    pop.setG(i, n, rd * e);
 }
 
 template <class S>
@@ -612,7 +611,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int
     const InstDev &I = L.inst[P0.inst];
     Region reg;
     reg.init(P0.x, side, I.nx, I.ny, I.nz);
-    S *pop = (S *)L.pop[nxt] + NPOP * I.node_off;
+    const Pop<S> pop(L.pop[nxt], I);
     const uint8_t *fli = L.flags + I.node_off;
     const int lane = threadIdx.x & 31;
     const long long count = reg.count();
@@ -759,6 +758,7 @@ INST(double)
 INST(float)
 INST(__half)
 INST(__nv_bfloat16)
+INST(MixedF16F32)
 #undef INST
 
 }  // namespace lbmg

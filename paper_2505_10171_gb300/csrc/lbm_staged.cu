@@ -300,8 +300,8 @@ __global__ void __launch_bounds__(ST_THREADS, MINB) k_phi_staged(Lattice L, int 
     const void *pop_in = L.pop[cur];
     auto body = [&](const StItem &it, const unsigned char *stg) {
         const InstDev &I = L.inst[it.k];
-        const int nx = I.nx, ny = I.ny, nz = I.nz, N = (int)I.N;
-        const S *in = (const S *)pop_in + NPOP * I.node_off;
+        const int nx = I.nx, ny = I.ny, nz = I.nz;
+        const Pop<S> in(pop_in, I);
         const S *sp = (const S *)stg;
         const long long g0 = item_node0(I, it);
         const uint8_t *sf = stg + Ly::POP + (g0 & 15);
@@ -343,9 +343,9 @@ __global__ void __launch_bounds__(ST_THREADS, MINB) k_collide_staged(Lattice L, 
     const void *pop_in = L.pop[cur];
     auto body = [&](const StItem &it, const unsigned char *stg) {
         const InstDev &I = L.inst[it.k];
-        const int nx = I.nx, ny = I.ny, nz = I.nz, N = (int)I.N;
-        const S *in = (const S *)pop_in + NPOP * I.node_off;
-        S *out = (S *)L.pop[cur ^ 1] + NPOP * I.node_off;
+        const int nx = I.nx, ny = I.ny, nz = I.nz;
+        const Pop<S> in(pop_in, I);
+        const Pop<S> out(L.pop[cur ^ 1], I);
         const S *sp = (const S *)stg;
         const R *se = (const R *)(stg + Ly::POP);
         const long long g0 = item_node0(I, it);
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(ST_THREADS, MINB) k_collide_staged(Lattice L, 
                 const int o = cx(i) == 1 ? b.bm : (cx(i) == -1 ? b.bp : b.b0);
                 F[i] = Store<S>::lds(sp + i * Ly::BUFW + o);
             }
-            collide_store_phi<S>(P, F, phi, gr, nn, kap, out, N, n, U, L.Ntot, L.status);
+            collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, U, L.Ntot, L.status);
         }
     };
     if constexpr (ASYNC) st_pipeline_async<S, true, MINB>(L, pop_in, n_items, body);

@@ -21,7 +21,8 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_UNSTABLE,
     LBM_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_OOM", "LBM_ERR_CUDA", "LBM_ERR_STATE", "LBM_ERR_UNSTABLE",
                 "LBM_ERR_TIMEOUT", "LBM_ERR_UNSUPPORTED"]
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+# "mixed": total offsets F in half, colour offsets G in FP32
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "mixed": 4}
 FIELD_RHO_A, FIELD_RHO_B, FIELD_PHI, FIELD_U, FIELD_POPS, FIELD_OWNER = 1, 2, 4, 8, 16, 32
 PARTICLE_RECORD = 32
 MAX_PARTICLES = 61

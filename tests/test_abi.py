@@ -81,3 +81,12 @@ def test_create_without_gpu_fails_cleanly(libpath):
         pass
     with pytest.raises(lbm.LbmError):
         lbm.Context(dict(nx=4, ny=4, nz=4), "fp64")
+
+
+def test_precision_codes_match_header():
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef enum \{([^}]*)\}\s*lbm_precision;", src).group(1)
+    enum = {k: int(v) for k, v in re.findall(r"(LBM_[A-Z0-9_]+)\s*=\s*(\d+)", body)}
+    names = {"fp64": "LBM_FP64", "fp32": "LBM_FP32", "fp16": "LBM_FP16_OFFSET", "bf16": "LBM_BF16_OFFSET",
+             "mixed": "LBM_F16_F32_OFFSET"}
+    assert {k: enum[v] for k, v in names.items()} == lbm.PRECISIONS

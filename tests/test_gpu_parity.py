@@ -126,6 +126,35 @@ def test_16bit_offset_cfg1(cfg1_oracle, prec):
     assert errs["F"] <= (5e-2 if prec == "fp16" else 5e-1)
 
 
+def test_mixed_storage_cfg1_meets_reduced_bar(cfg1_oracle):
+    """Total offsets in half and colour offsets in FP32: every field and the
+    per-particle force within the 2e-3 bar of reduced-precision storage."""
+    w, o = cfg1_oracle
+    g = run_gpu(w, w["steps"], "mixed")
+    fl = common_fluid(g, o)
+    rg = g["fields"]["rho_a"] + g["fields"]["rho_b"]
+    ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
+    errs = dict(rho=rel_l2(rg[fl], ro[fl]), phi=rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]),
+                u=rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]), F=force_error(g, o))
+    print("mixed", errs)
+    for k, v in errs.items():
+        assert v <= HALF_TOL, (k, v)
+
+
+def test_mixed_storage_runs_the_plain_form_only():
+    from paper_2505_10171_gb300 import lbm
+    w = W.cfg1()
+    c = gpu_ctx(w, "mixed")
+    with pytest.raises(lbm.LbmError):
+        c.lbm_set_fluid_kernel(lbm.FORM_STAGED, 0, 0)
+    with pytest.raises(lbm.LbmError):
+        c.lbm_set_fluid_kernel(lbm.FORM_FUSED, 0, 0)
+    c.lbm_set_fluid_kernel(lbm.FORM_PLAIN, 0, 0)
+    assert c.lbm_fluid_form_in_use() == lbm.FORM_PLAIN
+    c.lbm_step(4)
+    c.close()
+
+
 def test_fp64_fluid_only_sliding_wall():
     w = W.cfg1()
     w["particles"] = []
@@ -197,6 +226,39 @@ def test_batched_instances_match_single_runs(sizes, form):
         assert np.array_equal(c.lbm_particle_forces(k), single["parts"])
         o = run_oracle(w, 30)
         assert_fp64_parity(single, o)
+
+
+def test_mixed_storage_odd_instances_match_single_runs():
+    """Mixed storage pads each instance's population stride to 8 nodes: three
+    instances with odd node counts in one context equal separate runs bit for
+    bit and the oracle within the reduced-precision bar."""
+    from paper_2505_10171_gb300 import lbm
+    ws = []
+    for k, (nx, ny, nz, R) in enumerate(((33, 29, 17, 6.0), (25, 21, 19, 5.0), (41, 23, 15, 6.0))):
+        assert (nx * ny * nz) % 2 == 1
+        p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=80.0 + 15 * k, nu_a=1 / 6,
+                 nu_b=1 / 30, mu_s=0.2, store_velocity=1)
+        phi = W.drop_phi(nx, ny, nz, (nx / 3, ny / 2, 0.5), R)
+        parts = [dict(x=(nx / 3 + R + 6.0, ny / 2, 4.5), R=3.0, theta_deg=90.0, rho_p=W.PARTICLE_DENSITY)]
+        ws.append(dict(params=p, phi=phi, particles=parts))
+    c = lbm.Context([w["params"] for w in ws], "mixed")
+    for k, w in enumerate(ws):
+        c.lbm_add_particles(w["particles"], inst=k)
+        c.lbm_init_fields(w["phi"], inst=k)
+    c.lbm_step(30)
+    for k, w in enumerate(ws):
+        single = run_gpu(w, 30, "mixed")
+        fa, fb = c.pops(k)
+        assert np.array_equal(fa, single["fa"]) and np.array_equal(fb, single["fb"])
+        assert np.array_equal(c.lbm_particle_forces(k), single["parts"])
+        o = run_oracle(w, 30)
+        fl = common_fluid(single, o)
+        rg = single["fields"]["rho_a"] + single["fields"]["rho_b"]
+        ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
+        assert rel_l2(rg[fl], ro[fl]) <= HALF_TOL
+        assert rel_l2(single["fields"]["phi"][fl], o["fields"]["phi"][fl]) <= HALF_TOL
+        assert rel_l2(single["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= HALF_TOL
+    c.close()
 
 
 def test_fp32_deterministic():
