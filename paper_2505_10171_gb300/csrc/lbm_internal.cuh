@@ -545,8 +545,10 @@ __device__ __forceinline__ void wetting_rotate(R *g, const R *ns, R cth, R sth)
     R ca = ns[0] * st[0] + ns[1] * st[1] + ns[2] * st[2];
     ca = ca > R(1) ? R(1) : (ca < R(-1) ? R(-1) : ca);
     // cos and sin of the angle alpha* between n* and n_s: the FP64 path takes
-    // acos / sin / cos as the oracle does; single precision uses cos alpha* and
-    // sqrt(1 - cos^2) (alpha* in [0, pi]), which needs no transcendental calls
+    // acos / sin / cos as the oracle does; single precision uses the dot and
+    // the norm of the cross product (alpha* in [0, pi]), which need no
+    // transcendental calls and keep sin alpha* to relative precision where
+    // sqrt(1 - cos^2) would lose it (cos alpha* near +-1)
     R sa, cal;
     if (sizeof(R) == 8) {
         const R al = acos(ca);
@@ -554,7 +556,9 @@ __device__ __forceinline__ void wetting_rotate(R *g, const R *ns, R cth, R sth)
         cal = cos(al);
     } else {
         cal = ca;
-        sa = sqrt(R(1) - ca * ca);
+        const R x0 = ns[1] * st[2] - ns[2] * st[1], x1 = ns[2] * st[0] - ns[0] * st[2],
+                x2 = ns[0] * st[1] - ns[1] * st[0];
+        sa = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
     }
     if (sa < R(1e-4)) return;  // contact-line direction undefined (n* parallel to n_s)
     R ap1 = cth - sth * cal / sa, ap2 = sth / sa;

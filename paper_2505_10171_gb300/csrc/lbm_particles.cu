@@ -57,11 +57,9 @@ __device__ __forceinline__ R min_image_r(R d, int n)
 template <class S>
 __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
 {
-    using R = typename Store<S>::real;
     const int p = blockIdx.y;
     const PartDev &P = L.parts[p];
     const InstDev &I = L.inst[P.inst];
-    const int N = (int)I.N;
     Region reg;
     reg.init(P.x, P.mem_side, I.nx, I.ny, I.nz);
     double acc[6] = {0, 0, 0, 0, 0, 0};
@@ -73,42 +71,42 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
         const uint8_t *fli = L.flags + I.node_off;
         const uint8_t fl = fli[n];
         if ((fl & OWNER_MASK) == OWN_FLUID && (fl & BOUND_BIT)) {
+            // link arithmetic in FP64 whatever the storage: each link carries
+            // the rest part 2 w_i rho0 c_i, which cancels over the closed
+            // surface, so single-precision rounding of w (1 + F) would swamp
+            // the offsets F the force is made of (a few hundred links per sphere)
             const Pop<S> in(L.pop[cur], I);
             Nbr nb;
             nb.init(x, y, z, I.nx, I.ny, I.nz);
             const int mine = 2 + P.local;
-            R rr = -1;
-            R c[3], v[3], w[3];
-            centre(P, c);
-            for (int a = 0; a < 3; a++) { v[a] = (R)P.v[a]; w[a] = (R)P.w[a]; }
-            const R wr0 = (R)I.rho0;
+            double rr = -1;
             for (int i = 1; i < Q; i++) {
                 if ((fli[nb.at(-cx(i), -cy(i), -cz(i))] & OWNER_MASK) != mine) continue;
-                if (rr < R(0)) {
-                    R sF = 0;
-                    for (int j = 0; j < Q; j++) sF += wgt<R>(j) * in.F(j, n);
-                    rr = R(1) + sF;
+                if (rr < 0.0) {
+                    double sF = 0;
+                    for (int j = 0; j < Q; j++) sF += wgt<double>(j) * (double)in.F(j, n);
+                    rr = 1.0 + sF;
                 }
-                const R lev[3] = {min_image_r<R>(x - R(0.5) * cx(i) - c[0], I.nx),
-                                  min_image_r<R>(y - R(0.5) * cy(i) - c[1], I.ny),
-                                  min_image_r<R>(z - R(0.5) * cz(i) - c[2], I.nz)};
-                const R uw[3] = {v[0] + (w[1] * lev[2] - w[2] * lev[1]), v[1] + (w[2] * lev[0] - w[0] * lev[2]),
-                                 v[2] + (w[0] * lev[1] - w[1] * lev[0])};
+                const double lev[3] = {min_image(x - 0.5 * cx(i) - P.x[0], I.nx), min_image(y - 0.5 * cy(i) - P.x[1], I.ny),
+                                       min_image(z - 0.5 * cz(i) - P.x[2], I.nz)};
+                const double uw[3] = {P.v[0] + (P.w[1] * lev[2] - P.w[2] * lev[1]),
+                                      P.v[1] + (P.w[2] * lev[0] - P.w[0] * lev[2]),
+                                      P.v[2] + (P.w[0] * lev[1] - P.w[1] * lev[0])};
                 const int ib = opp(i);
-                const R wt = wgt<R>(i) * wr0;
-                const R Fo = in.F(ib, n);
-                const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
-                const R fout = wt * (R(1) + Fo);
-                const R fin = wt * (R(1) + Fo + R(6) * rr * cu);
-                const R ci[3] = {(R)cx(i), (R)cy(i), (R)cz(i)};
-                R dp[3];
+                const double wt = wgt<double>(i) * I.rho0;
+                const double Fo = (double)in.F(ib, n);
+                const double cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
+                const double fout = wt * (1.0 + Fo);
+                const double fin = wt * (1.0 + Fo + 6.0 * rr * cu);
+                const double ci[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
+                double dp[3];
                 for (int a = 0; a < 3; a++) dp[a] = (-ci[a] - uw[a]) * fout - (ci[a] - uw[a]) * fin;
-                acc[0] += (double)dp[0];
-                acc[1] += (double)dp[1];
-                acc[2] += (double)dp[2];
-                acc[3] += (double)(lev[1] * dp[2] - lev[2] * dp[1]);
-                acc[4] += (double)(lev[2] * dp[0] - lev[0] * dp[2]);
-                acc[5] += (double)(lev[0] * dp[1] - lev[1] * dp[0]);
+                acc[0] += dp[0];
+                acc[1] += dp[1];
+                acc[2] += dp[2];
+                acc[3] += lev[1] * dp[2] - lev[2] * dp[1];
+                acc[4] += lev[2] * dp[0] - lev[0] * dp[2];
+                acc[5] += lev[0] * dp[1] - lev[1] * dp[0];
             }
         }
     }
