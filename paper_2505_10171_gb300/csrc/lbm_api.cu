@@ -1066,12 +1066,12 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     ctx->parts_d = nullptr;
     ctx->mem_part = ctx->cap_part = ctx->hist = ctx->crec = nullptr;
     CU(cudaMalloc((void **)&ctx->parts_d, sizeof(PartDev) * np));
-    CU(cudaMalloc((void **)&ctx->mem_part, sizeof(double) * 6 * np * ctx->mem_blocks));
+    CU(cudaMalloc((void **)&ctx->mem_part, sizeof(double) * MEM_PART * np * ctx->mem_blocks));
     CU(cudaMalloc((void **)&ctx->cap_part, sizeof(double) * 6 * np * CAP_BLOCKS));
     CU(cudaMalloc((void **)&ctx->hist, sizeof(double) * 6 * std::max(hist, 1)));
     CU(cudaMalloc((void **)&ctx->crec, sizeof(double) * 12 * std::max(crec, 1)));
     CU(cudaMemsetAsync(ctx->hist, 0, sizeof(double) * 6 * std::max(hist, 1), ctx->stream));
-    CU(cudaMemsetAsync(ctx->mem_part, 0, sizeof(double) * 6 * np * ctx->mem_blocks, ctx->stream));
+    CU(cudaMemsetAsync(ctx->mem_part, 0, sizeof(double) * MEM_PART * np * ctx->mem_blocks, ctx->stream));
     CU(cudaMemsetAsync(ctx->cap_part, 0, sizeof(double) * 6 * np * CAP_BLOCKS, ctx->stream));
     CU(cudaMemcpyAsync(ctx->parts_d, all.data(), sizeof(PartDev) * np, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,

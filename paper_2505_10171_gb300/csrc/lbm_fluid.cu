@@ -565,11 +565,28 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     const dim3 bgrid((unsigned)std::max(bctas, 1LL));
     // boundary pass beside (side lane) or after the bulk kernel; profiling
     // (no side lane) times the two separately
+    // phi of solid nodes next to fluid: the listed static nodes and the
+    // particle cubes (every particle node lies within R_p + 1 of its centre).
+    // It reads phi only at fluid nodes next to a solid, which the boundary
+    // pass writes, so beside the bulk kernel it follows that pass on the side lane
+    bool fill_done = false;
+    auto fill_solid_phi = [&](cudaStream_t s) {
+        if (L.n_static > 0) {
+            k_solidphi_list<R><<<(unsigned)((L.n_static + 255) / 256), 256, 0, s>>>(L);
+            *launches += 1;
+        }
+        if (L.n_parts > 0) {
+            k_solidphi_region<R><<<dim3(L.cap_blocks, L.n_parts), PART_THREADS, 0, s>>>(L, L.cap_side - 2);
+            *launches += 1;
+        }
+        fill_done = true;
+    };
     auto bound_pass = [&](auto kernel, int bstage, int stage, auto &&bulk) {
         if (lane.side) {
             cudaEventRecord(lane.a, st);
             cudaStreamWaitEvent(lane.side, lane.a, 0);
             kernel<<<bgrid, PART_THREADS, 0, lane.side>>>(L, cur);
+            if (stage == STAGE_PHI) fill_solid_phi(lane.side);
             cudaEventRecord(lane.b, lane.side);
             if (stage == STAGE_COLLIDE) lane.after_collide_bound();
             bulk();
@@ -591,18 +608,11 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     } else {
         bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] { k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
     }
-    // phi of solid nodes next to fluid: the listed static nodes and the
-    // particle cubes (every particle node lies within R_p + 1 of its centre)
-    mk(STAGE_SOLIDPHI, 0);
-    if (L.n_static > 0) {
-        k_solidphi_list<R><<<(unsigned)((L.n_static + 255) / 256), 256, 0, st>>>(L);
-        *launches += 1;
+    if (!fill_done) {
+        mk(STAGE_SOLIDPHI, 0);
+        fill_solid_phi(st);
+        mk(STAGE_SOLIDPHI, 1);
     }
-    if (L.n_parts > 0) {
-        k_solidphi_region<R><<<dim3(L.cap_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, L.cap_side - 2);
-        *launches += 1;
-    }
-    mk(STAGE_SOLIDPHI, 1);
     mk(STAGE_GRAD, 0);
     k_gradcurv<R><<<(unsigned)fz.gc_items, GC_TX * GC_TY, 0, st>>>(L);
     mk(STAGE_GRAD, 1);

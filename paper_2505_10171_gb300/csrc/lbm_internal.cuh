@@ -54,6 +54,9 @@ constexpr int CAP_POINTS = 90 * 180;  // Sec. V E: 2 deg x 2 deg Lagrangian poin
 constexpr int CAP_THREADS = 256;
 constexpr int CAP_BLOCKS = (CAP_POINTS + CAP_THREADS - 1) / CAP_THREADS;
 constexpr int PART_THREADS = 256;
+// doubles per block partial of the momentum exchange: force and torque of the
+// small part, then the integer sums K and 2M of the rest part
+constexpr int MEM_PART = 12;
 constexpr int GEOM_MARGIN = 3;  // lattice units a particle may move per step, < this
 
 struct InstDev {
@@ -153,7 +156,7 @@ struct Lattice {
     int geom_side;       // side of the cube the geometry kernels cover
     int cap_side;        // side of the cube of phi around a particle for the capillary force
     int cap_blocks;      // blocks per particle covering that cube
-    double *mem_part;    // [n_parts][mem_blocks][6]
+    double *mem_part;    // [n_parts][mem_blocks][MEM_PART]
     double *cap_part;    // [n_parts][CAP_BLOCKS][6]
     const double *cap_pts;  // [CAP_POINTS][4]: unit normal (3) and sin(alpha) of each surface point
     double *hist;        // contact springs: per instance np*(np+1) records of 6

@@ -20,9 +20,10 @@
 namespace lbmg {
 
 // deterministic block sum of 6 doubles; thread 0 writes them to out
-__device__ __forceinline__ void block_sum6(double *v, double *out)
+template <class T>
+__device__ __forceinline__ void block_sum6(T *v, double *out)
 {
-    __shared__ double sm[PART_THREADS / 32][6];
+    __shared__ T sm[PART_THREADS / 32][6];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int a = 0; a < 6; a++)
@@ -32,11 +33,12 @@ __device__ __forceinline__ void block_sum6(double *v, double *out)
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int a = 0; a < 6; a++) {
-            double s = 0.0;
+            T s = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sm[w][a];
-            out[a] = s;
+            out[a] = (double)s;
         }
     }
+    __syncthreads();  // sm is reused by a second call
 }
 
 // particle centre in the arithmetic type R (single-precision copy for float)
@@ -54,15 +56,28 @@ __device__ __forceinline__ R min_image_r(R d, int n)
 // fluid node x into particle p, force on p = (c_out - u_w) f_out - (c_in - u_w) f_in
 // with f_out = f*_ibar(x) leaving towards the solid and f_in = f_i(x) bounced
 // back; torque lever from the centre to the link midpoint.
+//
+// With f_out = w rho0 (1 + F), f_in = w rho0 (1 + F + 6 rr c.u_w) the link
+// term is -2 w rho0 c (the rest part, order 0.1, cancelling over the closed
+// surface) plus w rho0 (-c (2F + 6 rr c.u_w) + u_w 6 rr c.u_w) (order 1e-4).
+// Rounding the sum in single precision would swamp the offsets, and FP64
+// arithmetic per link is slow on this GPU, so the rest part is kept exactly in
+// integers: with k = 36 w in {1, 2} and the lever d - delta, d the half-integer
+// offset of the link midpoint from the integer point xr = floor(x_p), delta =
+// x_p - xr, its force is -(rho0/18) K and its torque -(rho0/18) (M - delta x K)
+// with K = sum k c and M = sum k d x c. The block partials hold the small
+// part's force and torque, K and 2M; the DEM kernel assembles them in FP64.
 template <class S>
 __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
 {
+    using R = typename Store<S>::real;
     const int p = blockIdx.y;
     const PartDev &P = L.parts[p];
     const InstDev &I = L.inst[P.inst];
     Region reg;
     reg.init(P.x, P.mem_side, I.nx, I.ny, I.nz);
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    R acc[6] = {0, 0, 0, 0, 0, 0};
+    int kin[6] = {0, 0, 0, 0, 0, 0};  // K, then 2M
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < reg.count()) {
         int x, y, z;
@@ -71,46 +86,68 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
         const uint8_t *fli = L.flags + I.node_off;
         const uint8_t fl = fli[n];
         if ((fl & OWNER_MASK) == OWN_FLUID && (fl & BOUND_BIT)) {
-            // link arithmetic in FP64 whatever the storage: each link carries
-            // the rest part 2 w_i rho0 c_i, which cancels over the closed
-            // surface, so single-precision rounding of w (1 + F) would swamp
-            // the offsets F the force is made of (a few hundred links per sphere)
             const Pop<S> in(L.pop[cur], I);
             Nbr nb;
             nb.init(x, y, z, I.nx, I.ny, I.nz);
             const int mine = 2 + P.local;
-            double rr = -1;
+            // twice the node's offset from xr, minimum image (|.| < n)
+            const int xr[3] = {(int)floor(P.x[0]), (int)floor(P.x[1]), (int)floor(P.x[2])};
+            const int per[3] = {I.nx, I.ny, I.nz};
+            const int pos[3] = {x, y, z};
+            int D0[3];
+            for (int a = 0; a < 3; a++) {
+                int d = 2 * (pos[a] - xr[a]);
+                d += d >= per[a] ? -2 * per[a] : (d < -per[a] ? 2 * per[a] : 0);
+                D0[a] = d;
+            }
+            R rr = -1;
+            R c[3], v[3], w[3];
+            centre(P, c);
+            for (int a = 0; a < 3; a++) { v[a] = (R)P.v[a]; w[a] = (R)P.w[a]; }
+            const R r0 = (R)I.rho0;
             for (int i = 1; i < Q; i++) {
                 if ((fli[nb.at(-cx(i), -cy(i), -cz(i))] & OWNER_MASK) != mine) continue;
-                if (rr < 0.0) {
-                    double sF = 0;
-                    for (int j = 0; j < Q; j++) sF += wgt<double>(j) * (double)in.F(j, n);
-                    rr = 1.0 + sF;
+                if (rr < R(0)) {
+                    R sF = 0;
+                    for (int j = 0; j < Q; j++) sF += wgt<R>(j) * in.F(j, n);
+                    rr = R(1) + sF;
                 }
-                const double lev[3] = {min_image(x - 0.5 * cx(i) - P.x[0], I.nx), min_image(y - 0.5 * cy(i) - P.x[1], I.ny),
-                                       min_image(z - 0.5 * cz(i) - P.x[2], I.nz)};
-                const double uw[3] = {P.v[0] + (P.w[1] * lev[2] - P.w[2] * lev[1]),
-                                      P.v[1] + (P.w[2] * lev[0] - P.w[0] * lev[2]),
-                                      P.v[2] + (P.w[0] * lev[1] - P.w[1] * lev[0])};
-                const int ib = opp(i);
-                const double wt = wgt<double>(i) * I.rho0;
-                const double Fo = (double)in.F(ib, n);
-                const double cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
-                const double fout = wt * (1.0 + Fo);
-                const double fin = wt * (1.0 + Fo + 6.0 * rr * cu);
-                const double ci[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
-                double dp[3];
-                for (int a = 0; a < 3; a++) dp[a] = (-ci[a] - uw[a]) * fout - (ci[a] - uw[a]) * fin;
+                const int ci[3] = {cx(i), cy(i), cz(i)};
+                const R lev[3] = {min_image_r<R>(x - R(0.5) * ci[0] - c[0], I.nx),
+                                  min_image_r<R>(y - R(0.5) * ci[1] - c[1], I.ny),
+                                  min_image_r<R>(z - R(0.5) * ci[2] - c[2], I.nz)};
+                const R uw[3] = {v[0] + (w[1] * lev[2] - w[2] * lev[1]), v[1] + (w[2] * lev[0] - w[0] * lev[2]),
+                                 v[2] + (w[0] * lev[1] - w[1] * lev[0])};
+                const R wt = wgt<R>(i) * r0;
+                const R Fo = in.F(opp(i), n);
+                const R cu = ci[0] * uw[0] + ci[1] * uw[1] + ci[2] * uw[2];
+                const R e = R(6) * rr * cu;
+                const R q = R(2) * Fo + e;
+                R dp[3];
+                for (int a = 0; a < 3; a++) dp[a] = wt * (uw[a] * e - ci[a] * q);
                 acc[0] += dp[0];
                 acc[1] += dp[1];
                 acc[2] += dp[2];
                 acc[3] += lev[1] * dp[2] - lev[2] * dp[1];
                 acc[4] += lev[2] * dp[0] - lev[0] * dp[2];
                 acc[5] += lev[0] * dp[1] - lev[1] * dp[0];
+                // rest part: k c and k (2d) x c, 2d = D0 - c
+                const int k = csq(i) == 1 ? 2 : 1;
+                const int D[3] = {D0[0] - ci[0], D0[1] - ci[1], D0[2] - ci[2]};
+                kin[0] += k * ci[0];
+                kin[1] += k * ci[1];
+                kin[2] += k * ci[2];
+                kin[3] += k * (D[1] * ci[2] - D[2] * ci[1]);
+                kin[4] += k * (D[2] * ci[0] - D[0] * ci[2]);
+                kin[5] += k * (D[0] * ci[1] - D[1] * ci[0]);
             }
         }
     }
-    block_sum6(acc, L.mem_part + ((long long)p * L.mem_blocks + blockIdx.x) * 6);
+    double *out = L.mem_part + ((long long)p * L.mem_blocks + blockIdx.x) * MEM_PART;
+    double accd[6];
+    for (int a = 0; a < 6; a++) accd[a] = (double)acc[a];
+    block_sum6(accd, out);
+    block_sum6(kin, out + 6);
 }
 
 // Sec. V E: dF = C sigma (1 - phi^2) dA (n x n_s) x n at the points
@@ -335,19 +372,33 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
         const int lane = tid & 31, wid = tid >> 5;
         for (int p = wid; p < np; p += DEM_THREADS / 32) {
             const long long pg = I.part_off + p;
-            double s[12];
-            for (int a = 0; a < 12; a++) s[a] = 0.0;
+            double s[18];
+            for (int a = 0; a < 18; a++) s[a] = 0.0;
             for (int b = lane; b < L.mem_blocks; b += 32)
-                for (int a = 0; a < 6; a++) s[a] += L.mem_part[(pg * L.mem_blocks + b) * 6 + a];
+                for (int a = 0; a < MEM_PART; a++) s[a] += L.mem_part[(pg * L.mem_blocks + b) * MEM_PART + a];
             for (int b = lane; b < CAP_BLOCKS; b += 32)
-                for (int a = 0; a < 6; a++) s[6 + a] += L.cap_part[(pg * CAP_BLOCKS + b) * 6 + a];
+                for (int a = 0; a < 6; a++) s[12 + a] += L.cap_part[(pg * CAP_BLOCKS + b) * 6 + a];
             for (int o = 16; o > 0; o >>= 1)
-                for (int a = 0; a < 12; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
-            if (lane == 0)
+                for (int a = 0; a < 18; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
+            if (lane == 0) {
+                // momentum exchange: small part plus the exact rest part
+                // -(rho0/18) K, -(rho0/18) (M - delta x K), M = (2M)/2
+                const double g = -I.rho0 / 18.0;
+                double dl[3], K[3], M[3];
                 for (int a = 0; a < 3; a++) {
-                    P[p].Feta[a] = s[a]; P[p].Teta[a] = s[3 + a];
-                    P[p].Fsig[a] = s[6 + a]; P[p].Tsig[a] = s[9 + a];
+                    dl[a] = P[p].x[a] - floor(P[p].x[a]);
+                    K[a] = s[6 + a];
+                    M[a] = 0.5 * s[9 + a];
                 }
+                const double dK[3] = {dl[1] * K[2] - dl[2] * K[1], dl[2] * K[0] - dl[0] * K[2],
+                                      dl[0] * K[1] - dl[1] * K[0]};
+                for (int a = 0; a < 3; a++) {
+                    P[p].Feta[a] = s[a] + g * K[a];
+                    P[p].Teta[a] = s[3 + a] + g * (M[a] - dK[a]);
+                    P[p].Fsig[a] = s[12 + a];
+                    P[p].Tsig[a] = s[15 + a];
+                }
+            }
         }
         __syncthreads();
     }
