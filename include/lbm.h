@@ -92,7 +92,8 @@ typedef struct {
                                /*    in phi (Sec. IV); must be > 0                         */
     double sigma;              /* interfacial tension (CSF force, Sec. IV)                */
     double beta;               /* recolouring segregation parameter in [0, 1] (Sec. IV)   */
-    double cap_norm;           /* capillary prefactor C of Sec. V E; 0 selects (9/2) k beta */
+    double cap_norm;           /* capillary prefactor C of Sec. V E; 0 selects 3 k beta,    */
+                               /*    k = (1 + sqrt 2)/18 (the printed (9/2) k beta = 1.5x)   */
                                /*    with k = (1 + sqrt 2)/18                               */
     double body_force_a[3];    /* force density on phase a, weighted by (1 + phi)/2       */
     double body_force_b[3];    /* force density on phase b, weighted by (1 - phi)/2       */
@@ -193,6 +194,15 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
  * forcing, recolouring, capillary force, DEM, geometry update and refill).
  * Asynchronous on the context's stream; replays a captured CUDA graph. */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+
+/* Set the velocity v and angular velocity w of particle p of an instance
+ * (lattice units per step).  For a kinematic particle this is its prescribed
+ * motion from the next step on; for a free one its current velocity.  Between
+ * steps only, enqueued on the context stream (no synchronisation); the
+ * captured step graph stays valid.  |v| or |w| R_p above 0.1 (the geometry
+ * update assumes sub-lattice motion per step), a bad index or a null pointer ->
+ * LBM_ERR_ARG. */
+lbm_status lbm_set_particle_motion(lbm_ctx *ctx, int inst, int p, const double *v, const double *w);
 
 /* Per-particle record (LBM_PARTICLE_RECORD doubles each) of an instance after
  * the last step; out holds n_particles records.  Synchronises. */

@@ -117,7 +117,7 @@ def _f64(a):
 DEFAULTS = dict(
     wall_z0=0, wall_velocity=(0.0, 0.0, 0.0), theta_wall_deg=90.0, rho0=1.0,
     nu_a=1.0 / 6.0, nu_b=1.0 / 6.0, sigma=0.01, beta=0.7,
-    cap_norm=4.5 * (1.0 + 2.0 ** 0.5) / 18.0 * 0.7,
+    cap_norm=3.0 * (1.0 + 2.0 ** 0.5) / 18.0 * 0.7,
     body_force_a=(0.0, 0.0, 0.0), body_force_b=(0.0, 0.0, 0.0),
     kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0,
     g_particle=(0.0, 0.0, 0.0), grad_eps=1e-4, wet_phi_max=0.99,
@@ -129,13 +129,17 @@ DEFAULTS = dict(
 def make_params(nx, ny, nz, **kw) -> OrParams:
     """OrParams from keyword arguments; unspecified values take DEFAULTS.
 
-    ``cap_norm`` defaults to the paper's (9/2) k beta with k = (1+sqrt 2)/18
-    and the given beta, unless passed explicitly.
+    ``cap_norm`` defaults to 3 k beta with k = (1+sqrt 2)/18 and the given
+    beta, unless passed explicitly.  Sec. V E prints (9/2) k beta; across a
+    settled planar interface sum (1 - phi^2) = 1/(3 k beta), so 3 k beta gives
+    a line force of sigma per unit contact-line length and (9/2) k beta 1.5
+    sigma, and the detachment benchmark of Sec. V E (Scheludko's maximum force)
+    is met with 3 k beta.
     """
     v = dict(DEFAULTS)
     v.update(kw)
     if "cap_norm" not in kw:
-        v["cap_norm"] = 4.5 * (1.0 + 2.0 ** 0.5) / 18.0 * v["beta"]
+        v["cap_norm"] = 3.0 * (1.0 + 2.0 ** 0.5) / 18.0 * v["beta"]
     p = OrParams()
     p.nx, p.ny, p.nz = nx, ny, nz
     for name, _ in OrParams._fields_:

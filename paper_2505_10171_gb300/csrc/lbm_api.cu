@@ -713,7 +713,12 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.rho0 = p.rho0;
         I.sigma = p.sigma;
         I.beta = p.beta;
-        I.cap_norm = p.cap_norm > 0.0 ? p.cap_norm : 4.5 * (1.0 + std::sqrt(2.0)) / 18.0 * p.beta;
+        // default capillary prefactor C = 3 k beta, k = (1 + sqrt 2)/18: the
+        // settled planar profile has sum (1 - phi^2) = 1/(3 k beta) across the
+        // interface, so a contact line of length L carries sigma L (Sec. V E;
+        // the printed (9/2) k beta gives 1.5 sigma L and overshoots the
+        // detachment benchmark's closed form by the same factor)
+        I.cap_norm = p.cap_norm > 0.0 ? p.cap_norm : 3.0 * (1.0 + std::sqrt(2.0)) / 18.0 * p.beta;
         I.eta_a = p.rho0 * p.nu_a;
         I.eta_b = p.rho0 * p.nu_b;
         for (int a = 0; a < 3; a++) {
@@ -1162,6 +1167,24 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
     }
     ctx->last_launches = launches;
     CU(cudaGetLastError());
+    return LBM_OK;
+}
+
+lbm_status lbm_set_particle_motion(lbm_ctx *ctx, int inst, int p, const double *v, const double *w)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !v || !w) return fail(ctx, LBM_ERR_ARG, "bad instance or null velocity");
+    const InstDev &I = ctx->inst_h[inst];
+    if (p < 0 || p >= I.np) return fail(ctx, LBM_ERR_ARG, "bad particle index");
+    const double R = ctx->parts_h[(size_t)(I.part_off + p)].R;
+    const double vv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    const double ww = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (!(vv <= 0.1) || !(ww * R <= 0.1)) return fail(ctx, LBM_ERR_ARG, "particle speed above 0.1 lattice units per step");
+    static_assert(offsetof(PartDev, w) == offsetof(PartDev, v) + 3 * sizeof(double), "v and w adjacent");
+    double vw[6] = {v[0], v[1], v[2], w[0], w[1], w[2]};
+    // pageable source: staged before the call returns
+    CU(cudaMemcpyAsync((char *)(ctx->parts_d + I.part_off + p) + offsetof(PartDev, v), vw, sizeof vw,
+                       cudaMemcpyHostToDevice, ctx->stream));
     return LBM_OK;
 }
 

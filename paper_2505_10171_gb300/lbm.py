@@ -75,7 +75,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
            "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
-           "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune"]
+           "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
     L.lbm_add_particles.argtypes = [vp, i, i, P(lbm_particle)]
     L.lbm_step.argtypes = [vp, i]
     L.lbm_particle_forces.argtypes = [vp, i, d]
+    L.lbm_set_particle_motion.argtypes = [vp, i, i, d, d]
     L.lbm_read_fields.argtypes = [vp, i, ct.c_uint, d]
     L.lbm_read_fields_device.argtypes = [vp, i, ct.c_uint, vp]
     L.lbm_num_particles.argtypes = [vp, i]
@@ -259,6 +260,13 @@ class Context:
 
     def lbm_step(self, n=1):
         self._check(self.L.lbm_step(self.h, int(n)))
+
+    def lbm_set_particle_motion(self, p, v, w=(0.0, 0.0, 0.0), inst=0):
+        """Velocity and angular velocity of particle p (prescribed motion of a
+        kinematic particle), applied from the next step on."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        self._check(self.L.lbm_set_particle_motion(self.h, inst, int(p), _dp(v), _dp(w)))
 
     def lbm_particle_forces(self, inst=0, out=None):
         n = self.num_particles(inst)

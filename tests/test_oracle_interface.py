@@ -24,7 +24,7 @@ def test_planar_interface_integral_and_profile():
     """At rest, a planar interface settles where, for every x,
     (phi(x+1) - phi(x))/6 = beta k [1 - (phi(x+1)^2 + phi(x)^2)/2], hence
     sum_x (1 - phi^2) = 1/(3 k beta) across one interface; this is the quantity
-    the capillary prefactor (9/2) k beta is built on (Sec. V E)."""
+    the capillary prefactor of Sec. V E is built on."""
     for beta in (0.7, 0.99):
         ph = planar(beta)
         half = len(ph) // 2
@@ -133,3 +133,16 @@ def test_sessile_contact_angle():
     assert abs(meas[120.0] - 120.0) / 120.0 < gold["typical"]
     assert abs(meas[90.0] - 90.0) / 90.0 < gold["typical"]
     assert meas[60.0] < meas[90.0] < meas[120.0]
+
+
+def test_default_capillary_prefactor_gives_sigma_per_unit_line():
+    """The default prefactor C = 3 k beta turns the settled planar profile's
+    sum (1 - phi^2) into exactly one: a straight contact line of length L
+    across the interface carries sigma L (the line-integral form of Sec. V E);
+    the printed (9/2) k beta would carry 1.5 sigma L."""
+    for beta in (0.7, 0.99):
+        ph = planar(beta)
+        s1 = (1 - ph[:len(ph) // 2] ** 2).sum()
+        C = O.make_params(8, 8, 8, beta=beta).cap_norm
+        assert abs(C * s1 - 1.0) < 1e-7
+        assert abs(4.5 * K * beta * s1 - 1.5) < 1e-7
