@@ -11,6 +11,12 @@ interface meets it at the prescribed angle; its height gives the measured
 angle, cos(theta_mes) = (z_i - z_c) / R_p with z_i the far-field interface
 height (contact angle measured in phase a, which lies below).
 
+Particle migration in a tube (Sec. V B, the Segre-Silberberg benchmark, in
+the body-force-driven periodic form of the 64 x 64 x 1024 configuration): a
+neutrally buoyant sphere released off-axis in Poiseuille flow drifts
+sideways; the lateral (radial) momentum-exchange force and the radial
+position l / R_t are sampled over time.
+
 Detachment set-up (the paper gives R_p = 25, v_p = 0.01 and theta_p from 30 to 150 deg;
 the rest is this module's choice): a periodic box of 6 R_p x 6 R_p x 12 R_p
 (rounded up to multiples of 8), no substrate, a layer of phase a (the
@@ -134,3 +140,39 @@ def wetting_equilibrium(theta_deg, R_p=25, steps=None, sample_every=100, precisi
     c = (zi_far - zc[-1]) / R_p
     theta_mes = math.degrees(math.acos(max(-1.0, min(1.0, c))))
     return dict(theta_deg=theta_deg, R_p=R_p, t=np.asarray(t), z_c=zc, z_i=zi_far, theta_mes=theta_mes)
+
+
+def tube_migration(nz=1024, steps=50000, sample_every=500, precision="fp32", stream=None):
+    """The tube workload (radius 31 about (31.5, 31.5), periodic along z, body
+    force for a centreline speed of 0.02, sphere R_p = 6 released at
+    l = 0.3 R_t with the local flow speed).  Returns the sampled times, the
+    radial position l / R_t, the radial and axial momentum-exchange forces and
+    the axial flow speed on the tube axis far from the sphere at the end."""
+    w = W.cfg3(nz=nz)
+    Rt, c0 = 31.0, 31.5
+    ctx = lbm.Context(dict(w["params"], store_velocity=1), precision, stream=stream)
+    try:
+        ctx.lbm_set_solid_mask(w["mask"])
+        ctx.lbm_add_particles(w["particles"])
+        ctx.lbm_init_fields(w["phi"], None, w["u"])
+        t, l, fr, fz = [], [], [], []
+        done = 0
+        while done < steps:
+            k = min(sample_every, steps - done)
+            ctx.lbm_step(k)
+            done += k
+            rec = ctx.lbm_particle_forces()[0]
+            d = np.array([rec[18] - c0, rec[19] - c0])
+            r = float(np.hypot(*d))
+            e = d / max(r, 1e-12)
+            t.append(done)
+            l.append(r / Rt)
+            fr.append(float(rec[0] * e[0] + rec[1] * e[1]))
+            fz.append(float(rec[2]))
+        zp = rec[20]
+        u = ctx.lbm_read_fields(lbm.FIELD_U).reshape(3, nz, 64, 64)
+        zf = int((zp + nz / 2) % nz)  # the plane farthest from the sphere
+        u_axis = float(u[2, zf, 31:33, 31:33].mean())
+    finally:
+        ctx.close()
+    return dict(t=np.asarray(t), l=np.asarray(l), F_r=np.asarray(fr), F_z=np.asarray(fz), u_axis=u_axis)

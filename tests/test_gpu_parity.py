@@ -277,6 +277,22 @@ def test_full_size_cfg2_one_step_fp32():
     assert_reduced_parity(g, o, FP32_TOL)
 
 
+def test_full_size_cfg2_one_step_mixed():
+    """The same in the mixed storage form, against the reduced-precision bar."""
+    w = W.cfg2()
+    o = run_oracle(w, 1)
+    g = run_gpu(w, 1, "mixed")
+    assert_reduced_parity(g, o, HALF_TOL)
+
+
+def test_full_size_tube_one_step_fp32():
+    """The 64x64x1024 tube workload at full size: one FP32 step against the oracle."""
+    w = W.cfg3()
+    o = run_oracle(w, 1)
+    g = run_gpu(w, 1, "fp32")
+    assert_reduced_parity(g, o, FP32_TOL)
+
+
 def test_unstable_state_is_reported():
     """A NaN planted in the host-side initial field is caught by the device
     status word and reported as LBM_ERR_UNSTABLE by the next read."""
