@@ -237,8 +237,11 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
 
 /* Fluid-update launch form (all forms compute the same update).
  * form = 2 (default), plain: five kernels per step (order parameter, solid
- *   phi, gradient + wetting + normal, curvature, collision), one thread per
- *   node with direct loads; tile must be 0.
+ *   phi, gradient + wetting + normal, curvature, collision), direct loads.
+ *   tile 0: with 16-bit total offsets (FP16, BF16, mixed) and an even nx in
+ *   every instance the bulk collision takes two nodes of a row per thread
+ *   (pair loads and stores), one node per thread otherwise; tile 1: one node
+ *   per thread always.
  * form = 0, staged: the same five kernels, but the two that stream the
  *   populations are persistent and bring each strip of x-rows into a ring of
  *   shared-memory stages with asynchronous copies.  tile selects the variant:
@@ -250,16 +253,17 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
  *   tile (0: 16x16, 1: 32x8); zchunk is the number of z-planes per work item
  *   (0: automatic, 32).
  * Staged and plain agree bit for bit; fused agrees bit for bit in FP32 and to
- * rounding (FMA contraction) in FP64.  Invalid form, tile or zchunk -> LBM_ERR_ARG.
+ * rounding (FMA contraction) in FP64.  Invalid form, tile or zchunk -> LBM_ERR_ARG;
+ * a form other than plain with the mixed storage -> LBM_ERR_UNSUPPORTED.
  * Invalidates the step graph. */
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk);
 
 /* Autotuner: steps the simulation `steps` times (>= 2) in each available
  * launch form and variant -- plain; staged tiles 0, 1, 2 (when available);
- * fused tiles 0, 1 -- timing each with CUDA events on the context stream,
+ * fused tiles 0, 1; plain tile 1 -- timing each with CUDA events on the context stream,
  * and keeps the fastest.  The simulation advances by all the trial steps (every
  * form computes the same update).  *form and *tile receive the choice;
- * ms_per_step (may be NULL) receives 6 times in the order above, -1 for a
+ * ms_per_step (may be NULL) receives 7 times in the order above, -1 for a
  * form that is not available.  Synchronises. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step);
 

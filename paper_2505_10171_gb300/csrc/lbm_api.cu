@@ -59,7 +59,7 @@ struct lbm_ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
     // fluid launch form: plain (default), staged or fused z-marching
-    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}};
+    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}, false};
     int zc_request = 0;  // z-planes per fused work item, 0: automatic
     // drop-speed control: per instance integral (3) and last U_a (3); block partials
     double *speed_d = nullptr;
@@ -107,6 +107,10 @@ static void plan_launch(lbm_ctx *c)
     c->fz.gc_items = plan_gradcurv(c->inst_h);
     const bool aligned = plan_rows(c->inst_h, c->elem, &c->fz.rows);
     c->fz.st_items = aligned && c->prec != LBM_F16_F32_OFFSET ? c->fz.rows : 0;
+    // node-pair bulk collision (plain form, tile 0) when every row has an even length
+    bool even = true;
+    for (const auto &I : c->inst_h) even = even && I.nx % 2 == 0;
+    c->fz.pair = even && c->fz.form == FORM_PLAIN && c->fz.tile == 0;
     dispatch_grids(c);
 }
 
@@ -1304,10 +1308,10 @@ long long lbm_last_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->last_lau
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
 {
     if (!ctx) return LBM_ERR_ARG;
-    const int max_tile = form == FORM_STAGED ? 2 : (form == FORM_FUSED ? 1 : 0);
+    const int max_tile = form == FORM_STAGED ? 2 : 1;
     if (form < FORM_STAGED || form > FORM_PLAIN || tile < 0 || tile > max_tile || zchunk < 0)
         return fail(ctx, LBM_ERR_ARG,
-                    "form must be 0 (staged, tile 0..2), 1 (fused, tile 0..1) or 2 (plain, tile 0); zchunk >= 0");
+                    "form must be 0 (staged, tile 0..2), 1 (fused, tile 0..1) or 2 (plain, tile 0..1); zchunk >= 0");
     if (ctx->prec == LBM_F16_F32_OFFSET && form != FORM_PLAIN)
         return fail(ctx, LBM_ERR_UNSUPPORTED, "the mixed FP16/FP32 storage runs the plain form only");
     CU(cudaStreamSynchronize(ctx->stream));
@@ -1586,15 +1590,15 @@ lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out)
 lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step)
 {
     if (!ctx || !form || !tile || steps < 2) return fail(ctx, LBM_ERR_ARG, "autotune needs steps >= 2 and outputs");
-    const int cand[6][2] = {{FORM_PLAIN, 0}, {FORM_STAGED, 0}, {FORM_STAGED, 1}, {FORM_STAGED, 2}, {FORM_FUSED, 0},
-                            {FORM_FUSED, 1}};
+    const int cand[7][2] = {{FORM_PLAIN, 0}, {FORM_STAGED, 0}, {FORM_STAGED, 1}, {FORM_STAGED, 2}, {FORM_FUSED, 0},
+                            {FORM_FUSED, 1}, {FORM_PLAIN, 1}};
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best = -1.0;
     int bf = FORM_PLAIN, bt = 0;
     lbm_status st = LBM_OK;
-    for (int k = 0; k < 6 && st == LBM_OK; k++) {
+    for (int k = 0; k < 7 && st == LBM_OK; k++) {
         if (ms_per_step) ms_per_step[k] = -1.0;
         if (ctx->prec == LBM_F16_F32_OFFSET && cand[k][0] != FORM_PLAIN) continue;
         if ((st = lbm_set_fluid_kernel(ctx, cand[k][0], cand[k][1], 0)) != LBM_OK) break;

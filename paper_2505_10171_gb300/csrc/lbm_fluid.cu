@@ -321,6 +321,122 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, U, L.Ntot, L.status);
 }
 
+// Node pairs (x even, x + 1) of one row per thread, for 16-bit total offsets:
+// the pulls along directions with c_x = 0 are one 32-bit load of the pair,
+// every output a pair store (half2, bfloat162 or float2), which halves the
+// per-node load, store, conversion and address instructions.  Each node's
+// arithmetic is that of collide_store_phi; a node of the pair that the bulk
+// kernel skips (solid, next to a solid) is computed but not written.
+template <class S>
+__device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
+{
+    using R = typename Store<S>::real;
+    using FT = typename Pop<S>::FT;
+    using GT = typename Pop<S>::GT;
+    static_assert(sizeof(FT) == 2 && sizeof(R) == 4, "pair kernel: 16-bit total offsets, FP32 arithmetic");
+    const long long g = I.node_off + n;  // even
+    const Pop<S> in(L.pop[cur], I);
+    const Pop<S> out(L.pop[cur ^ 1], I);
+    const int N = in.N;
+    const uint8_t fl0 = L.flags[g], fl1 = L.flags[g + 1];
+    const R *Nn = (const R *)L.grad + I.node_off;
+    const long long Nt = L.Ntot;
+    const float2 n0 = *reinterpret_cast<const float2 *>(Nn + n);
+    const float2 n1 = *reinterpret_cast<const float2 *>(Nn + Nt + n);
+    const float2 n2 = *reinterpret_cast<const float2 *>(Nn + 2 * Nt + n);
+    const float2 mv = *reinterpret_cast<const float2 *>((const R *)L.gmag + g);
+    const float2 kv = *reinterpret_cast<const float2 *>((const R *)L.kap + g);
+    const float2 pv = *reinterpret_cast<const float2 *>((const R *)L.phi + g);
+    Nbr nb;
+    nb.init(x, y, z, I.nx, I.ny, I.nz);
+    const int xp2 = x + 2 == I.nx ? 0 : x + 2;
+    R F0[Q], F1[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const FT *row = in.f + i * N + nb.ZO[1 - cz(i)] + nb.YO[1 - cy(i)];
+        if (cx(i) == 0) {
+            ld_pair(row + x, F0[i], F1[i]);
+        } else if (cx(i) == 1) {
+            F0[i] = Store<FT>::ld(row + nb.X[0]);
+            F1[i] = Store<FT>::ld(row + x);
+        } else {
+            F0[i] = Store<FT>::ld(row + x + 1);
+            F1[i] = Store<FT>::ld(row + xp2);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        keep(F0[i]);
+        keep(F1[i]);
+    }
+    const bool fluid0 = (fl0 & OWNER_MASK) == OWN_FLUID, fluid1 = (fl1 & OWNER_MASK) == OWN_FLUID;
+    const bool a0 = fluid0 && !(fl0 & BOUND_BIT), a1 = fluid1 && !(fl1 & BOUND_BIT);
+    R *U = I.store_u ? (R *)L.u + I.node_off : nullptr;
+    if (U) {
+        if (!fluid0) { U[n] = 0; U[Nt + n] = 0; U[2 * Nt + n] = 0; }
+        if (!fluid1) { U[n + 1] = 0; U[Nt + n + 1] = 0; U[2 * Nt + n + 1] = 0; }
+    }
+    if (!a0 && !a1) return;
+    FluidPar<R> P;
+    load_par(I, P);
+    const R nnA[3] = {n0.x, n1.x, n2.x}, nnB[3] = {n0.y, n1.y, n2.y};
+    const R grA[3] = {nnA[0] * mv.x, nnA[1] * mv.x, nnA[2] * mv.x};
+    const R grB[3] = {nnB[0] * mv.y, nnB[1] * mv.y, nnB[2] * mv.y};
+    const R phA = pv.x, phB = pv.y;
+    const CollideState<R> cA = collide_state(P, F0, phA, grA, kv.x);
+    const CollideState<R> cB = collide_state(P, F1, phB, grB, kv.y);
+    if ((a0 && (!(cA.rr > R(0)) || !(phA == phA))) || (a1 && (!(cB.rr > R(0)) || !(phB == phB))))
+        atomicOr(L.status, ST_UNSTABLE);
+    if (U) {
+        if (a0) { U[n] = cA.ux; U[Nt + n] = cA.uy; U[2 * Nt + n] = cA.uz; }
+        if (a1) { U[n + 1] = cB.ux; U[Nt + n + 1] = cB.uy; U[2 * Nt + n + 1] = cB.uz; }
+    }
+    FT *const of = out.f + n;
+    GT *const og = out.g() + n;
+    const bool both = a0 && a1;
+    auto put = [&](auto *p, R v0, R v1) {
+        using T = std::remove_pointer_t<decltype(p)>;
+        if (both) {
+            st_pair(p, v0, v1);
+        } else if (a0) {
+            Store<T>::st(p, v0);
+        } else {
+            Store<T>::st(p + 1, v1);
+        }
+    };
+    {
+        const R FsA = collide_rest(P, cA, F0[0]), FsB = collide_rest(P, cB, F1[0]);
+        put(of, FsA, FsB);
+        put(og, phA * (R(1) + FsA), phB * (R(1) + FsB));
+    }
+    PairLoop<R>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value, ib = i + 9;
+        R FiA, FibA, recA, FiB, FibB, recB;
+        collide_pair<R, i>(P, cA, nnA, F0[i], F0[ib], FiA, FibA, recA);
+        collide_pair<R, i>(P, cB, nnB, F1[i], F1[ib], FiB, FibB, recB);
+        put(of + i * N, FiA, FiB);
+        put(of + ib * N, FibA, FibB);
+        put(og + i * N, phA * (R(1) + FiA) + recA, phB * (R(1) + FiB) + recB);
+        put(og + ib * N, phA * (R(1) + FibA) - recA, phB * (R(1) + FibB) - recB);
+    });
+}
+
+#ifndef LBM_COLLIDE2_MINB
+#define LBM_COLLIDE2_MINB 5
+#endif
+template <class S>
+__global__ void __launch_bounds__(ROW_NODES / 2, LBM_COLLIDE2_MINB) k_collide2(Lattice L, int cur)
+{
+    StItem it;
+    st_item(L, blockIdx.x, it);
+    const int j = 2 * (int)threadIdx.x;
+    if (j >= it.cnt) return;
+    const InstDev &I = L.inst[it.k];
+    int x, y;
+    item_node(it, I.nx, j, &x, &y);
+    collide_body2<S>(L, I, cur, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
+}
+
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_collide(Lattice L, int cur)
 {
@@ -622,8 +738,15 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         if constexpr (!is_mixed<S>) launch_staged_collide<S>(L, cur, fz, st);
         mk(STAGE_COLLIDE, 1);
     } else {
-        bound_pass(k_collide_bound<S>, STAGE_COLLIDE_BOUND, STAGE_COLLIDE,
-                   [&] { k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
+        bound_pass(k_collide_bound<S>, STAGE_COLLIDE_BOUND, STAGE_COLLIDE, [&] {
+            if constexpr (sizeof(typename PopTypes<S>::F) == 2) {
+                if (fz.pair) {
+                    k_collide2<S><<<grid, ROW_NODES / 2, 0, st>>>(L, cur);
+                    return;
+                }
+            }
+            k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+        });
     }
     *launches += 3;
 }

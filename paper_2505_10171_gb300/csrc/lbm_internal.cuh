@@ -260,6 +260,30 @@ struct Pop {
     __device__ __forceinline__ void setG(int i, int m, R v) const { Store<GT>::st(g() + i * N + m, v); }
 };
 
+// two consecutive 16-bit values of a node pair (x even) as one 32-bit access,
+// and the pair store of two reals
+__device__ __forceinline__ void ld_pair(const __half *p, float &a, float &b)
+{
+    const __half2 v = __ldg(reinterpret_cast<const __half2 *>(p));
+    a = __low2float(v);
+    b = __high2float(v);
+}
+__device__ __forceinline__ void ld_pair(const __nv_bfloat16 *p, float &a, float &b)
+{
+    const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
+    a = __low2float(v);
+    b = __high2float(v);
+}
+__device__ __forceinline__ void st_pair(__half *p, float a, float b)
+{
+    *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+}
+__device__ __forceinline__ void st_pair(__nv_bfloat16 *p, float a, float b)
+{
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
+}
+__device__ __forceinline__ void st_pair(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+
 // minimum-image displacement on a periodic axis of n nodes (|d| < 3n/2): the
 // same value as d - n floor(d/n + 1/2) without a double-precision division
 __host__ __device__ __forceinline__ double min_image(double d, int n)
@@ -719,6 +743,7 @@ struct FluidLaunch {
     long long st_items; // the same when the staged form is available, else 0
     // persistent grids of the staged kernels, per variant (see lbm_staged.cu)
     int st_grid_phi[3], st_grid_collide[3];
+    bool pair;          // every instance has an even nx: node-pair kernels for 16-bit total offsets
 };
 // staged kernels: threads per CTA and nodes per work item at most
 constexpr int ST_THREADS = 256;

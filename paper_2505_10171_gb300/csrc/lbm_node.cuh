@@ -3,6 +3,8 @@
 // arithmetic: solid-node phi, wetting normal, grad(phi), collision + recolouring
 // + write, curvature and the regularised normal.
 #pragma once
+
+#include <type_traits>
 #include "lbm_internal.cuh"
 
 namespace lbmg {
@@ -126,11 +128,107 @@ __device__ __forceinline__ void grad_node(const InstDev &I, const PartDev *parts
     grad_wet<R>(I, parts, nbr, phi_here, fl, wet_max, x, y, z, gr);
 }
 
-// force, velocity, MRT (two-relaxation-time form) with Guo forcing,
-// recolouring and the write of node n.  F: streamed total offsets; phi: the
-// order parameter after streaming (stored by the order-parameter pass: the
-// colour offsets enter the update only through it); g: corrected grad(phi) of
-// the node; nn: its regularised normal; kap: curvature.
+// the node's state before the per-direction updates of the collision
+template <class R>
+struct CollideState {
+    R sF, rr, ux, uy, uz, Fx, Fy, Fz, om, omp, uu, uF, cpe, cpo, bq;
+};
+
+template <class R>
+__device__ __forceinline__ CollideState<R> collide_state(const FluidPar<R> &P, const R *F, R phi, const R *g, R kap)
+{
+    CollideState<R> c;
+    R sF = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const R w = wgt<R>(i);
+        sF += w * F[i];
+        if (cx(i)) jx += w * cx(i) * F[i];
+        if (cy(i)) jy += w * cy(i) * F[i];
+        if (cz(i)) jz += w * cz(i) * F[i];
+    }
+    c.sF = sF;
+    c.rr = R(1) + sF;  // rho / rho0
+    // force density: CSF -1/2 sigma kappa grad(phi) plus phase-weighted body forces
+    const R hs = R(-0.5) * P.sigma * kap;
+    const R pa = R(0.5) * (R(1) + phi), pb = R(0.5) * (R(1) - phi);
+    c.Fx = hs * g[0] + pa * P.ba[0] + pb * P.bb[0];
+    c.Fy = hs * g[1] + pa * P.ba[1] + pb * P.bb[1];
+    c.Fz = hs * g[2] + pa * P.ba[2] + pb * P.bb[2];
+    // velocity: rho u = sum c f + F/2
+    const R rho = P.rho0 * c.rr;
+    const R irho = frcp(rho);
+    c.ux = (P.rho0 * jx + R(0.5) * c.Fx) * irho;
+    c.uy = (P.rho0 * jy + R(0.5) * c.Fy) * irho;
+    c.uz = (P.rho0 * jz + R(0.5) * c.Fz) * irho;
+    // relaxation rates: harmonic-mean viscosity, tau = eta/(rho cs2) + 1/2
+    const R inv_eta = (R(1) + phi) * P.h_ia + (R(1) - phi) * P.h_ib;
+    const R tau = R(3) * frcp(inv_eta * rho) + R(0.5);
+    c.om = frcp(tau);
+    c.omp = R(8) * (R(2) - c.om) * frcp(R(8) - c.om);
+    c.uu = c.ux * c.ux + c.uy * c.uy + c.uz * c.uz;
+    c.uF = c.ux * c.Fx + c.uy * c.Fy + c.uz * c.Fz;
+    c.cpe = R(1) - R(0.5) * c.om;
+    c.cpo = R(1) - R(0.5) * c.omp;
+    c.bq = R(0.5) * P.beta * c.rr * (R(1) - phi * phi);
+    return c;
+}
+
+// post-collision rest population
+template <class R>
+__device__ __forceinline__ R collide_rest(const FluidPar<R> &P, const CollideState<R> &c, R F0)
+{
+    const R feq0 = c.sF + c.rr * (R(-1.5) * c.uu);
+    const R fb0 = R(-3) * c.uF * P.ir0;
+    return F0 - c.om * (F0 - feq0) + c.cpe * fb0;
+}
+
+// opposite pair (i, i+9): the paper's S relaxes every even non-conserved
+// moment with omega and every odd one with omega', i.e. the MRT operator is
+// exactly the two-relaxation-time operator on the pair's even/odd parts.
+// Returns F*_i, F*_ib and the recolouring term beta/2 (rho/rho0)(1 - phi^2)
+// c_i.n/|c_i| (G* = phi (1 + F*) +- rec).
+template <class R, int i>
+__device__ __forceinline__ void collide_pair(const FluidPar<R> &P, const CollideState<R> &c, const R *nn, R Fi_in,
+                                             R Fib_in, R &Fi, R &Fib, R &rec)
+{
+    const R cu = cx(i) * c.ux + cy(i) * c.uy + cz(i) * c.uz;
+    const R cF = cx(i) * c.Fx + cy(i) * c.Fy + cz(i) * c.Fz;
+    const R eqp = c.sF + c.rr * (R(4.5) * cu * cu - R(1.5) * c.uu);
+    const R eqm = c.rr * R(3) * cu;
+    const R fbp = (R(9) * cu * cF - R(3) * c.uF) * P.ir0;
+    const R fbm = R(3) * cF * P.ir0;
+    const R fp = R(0.5) * (Fi_in + Fib_in);
+    const R fm = R(0.5) * (Fi_in - Fib_in);
+    const R dp = -c.om * (fp - eqp) + c.cpe * fbp;
+    const R dm = -c.omp * (fm - eqm) + c.cpo * fbm;
+    Fi = Fi_in + dp + dm;
+    Fib = Fib_in + dp - dm;
+    const R inv_len = csq(i) == 1 ? R(1) : R(0.70710678118654752440);
+    const R cn = (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]) * inv_len;
+    rec = c.bq * cn;
+}
+
+template <class R, int i = 1>
+struct PairLoop {
+    template <class Fn>
+    __device__ __forceinline__ static void run(Fn &&f)
+    {
+        f(std::integral_constant<int, i>());
+        PairLoop<R, i + 1>::run(f);
+    }
+};
+template <class R>
+struct PairLoop<R, 10> {
+    template <class Fn>
+    __device__ __forceinline__ static void run(Fn &&) {}
+};
+
+// force, velocity, MRT (two-relaxation-time form) with Guo forcing (Sec. IV),
+// recolouring and the write of node n.  F: streamed total offsets; phi: the order parameter after
+// streaming (stored by the order-parameter pass: the colour offsets enter the
+// update only through it); g: corrected grad(phi) of the node; nn: its
+// regularised normal; kap: curvature.
 template <class S>
 __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<S>::real> &P,
                                                   const typename Store<S>::real *F, typename Store<S>::real phi,
@@ -144,75 +242,24 @@ __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<
     const int N = out.N;
     FT *const of = out.f + n;    // F_0 of this node; F_i at of + i N
     GT *const og = out.g() + n;  // G_0 likewise
-    R sF = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const R w = wgt<R>(i);
-        sF += w * F[i];
-        if (cx(i)) jx += w * cx(i) * F[i];
-        if (cy(i)) jy += w * cy(i) * F[i];
-        if (cz(i)) jz += w * cz(i) * F[i];
-    }
-    const R rr = R(1) + sF;  // rho / rho0
-    if (status && (!(rr > R(0)) || !(phi == phi))) atomicOr(status, ST_UNSTABLE);
-    // force density: CSF -1/2 sigma kappa grad(phi) plus phase-weighted body forces
-    const R hs = R(-0.5) * P.sigma * kap;
-    const R pa = R(0.5) * (R(1) + phi), pb = R(0.5) * (R(1) - phi);
-    const R Fx = hs * g[0] + pa * P.ba[0] + pb * P.bb[0];
-    const R Fy = hs * g[1] + pa * P.ba[1] + pb * P.bb[1];
-    const R Fz = hs * g[2] + pa * P.ba[2] + pb * P.bb[2];
-    // velocity: rho u = sum c f + F/2
-    const R rho = P.rho0 * rr;
-    const R irho = frcp(rho);
-    const R ux = (P.rho0 * jx + R(0.5) * Fx) * irho;
-    const R uy = (P.rho0 * jy + R(0.5) * Fy) * irho;
-    const R uz = (P.rho0 * jz + R(0.5) * Fz) * irho;
-    if (U) { U[n] = ux; U[Ustride + n] = uy; U[2 * Ustride + n] = uz; }
-    // relaxation rates: harmonic-mean viscosity, tau = eta/(rho cs2) + 1/2
-    const R inv_eta = (R(1) + phi) * P.h_ia + (R(1) - phi) * P.h_ib;
-    const R tau = R(3) * frcp(inv_eta * rho) + R(0.5);
-    const R om = frcp(tau);
-    const R omp = R(8) * (R(2) - om) * frcp(R(8) - om);
-    const R uu = ux * ux + uy * uy + uz * uz;
-    const R uF = ux * Fx + uy * Fy + uz * Fz;
-    const R cpe = R(1) - R(0.5) * om, cpo = R(1) - R(0.5) * omp;
-    const R bq = R(0.5) * P.beta * rr * (R(1) - phi * phi);
+    const CollideState<R> c = collide_state(P, F, phi, g, kap);
+    if (status && (!(c.rr > R(0)) || !(phi == phi))) atomicOr(status, ST_UNSTABLE);
+    if (U) { U[n] = c.ux; U[Ustride + n] = c.uy; U[2 * Ustride + n] = c.uz; }
     {
-        const R feq0 = sF + rr * (R(-1.5) * uu);
-        const R fb0 = R(-3) * uF * P.ir0;
-        const R Fs = F[0] - om * (F[0] - feq0) + cpe * fb0;
+        const R Fs = collide_rest(P, c, F[0]);
         Store<FT>::st(of, Fs);
         Store<GT>::st(og, phi * (R(1) + Fs));
     }
-    // opposite pairs (i, i+9): the paper's S relaxes every even non-conserved
-    // moment with omega and every odd one with omega', i.e. the MRT operator is
-    // exactly the two-relaxation-time operator on the pair's even/odd parts
-#pragma unroll
-    for (int i = 1; i <= 9; i++) {
-        const int ib = i + 9;
-        const R cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-        const R cF = cx(i) * Fx + cy(i) * Fy + cz(i) * Fz;
-        const R eqp = sF + rr * (R(4.5) * cu * cu - R(1.5) * uu);
-        const R eqm = rr * R(3) * cu;
-        const R fbp = (R(9) * cu * cF - R(3) * uF) * P.ir0;
-        const R fbm = R(3) * cF * P.ir0;
-        const R fp = R(0.5) * (F[i] + F[ib]);
-        const R fm = R(0.5) * (F[i] - F[ib]);
-        const R dp = -om * (fp - eqp) + cpe * fbp;
-        const R dm = -omp * (fm - eqm) + cpo * fbm;
-        const R Fi = F[i] + dp + dm;
-        const R Fib = F[ib] + dp - dm;
-        // recolouring: G* = phi (1 + F*) + beta/2 (rho/rho0)(1 - phi^2) c.n/|c|
-        const R inv_len = csq(i) == 1 ? R(1) : R(0.70710678118654752440);
-        const R cn = (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]) * inv_len;
-        const R rec = bq * cn;
+    PairLoop<R>::run([&](auto ic) {
+        constexpr int i = decltype(ic)::value, ib = i + 9;
+        R Fi, Fib, rec;
+        collide_pair<R, i>(P, c, nn, F[i], F[ib], Fi, Fib, rec);
         Store<FT>::st(of + i * N, Fi);
         Store<FT>::st(of + ib * N, Fib);
         Store<GT>::st(og + i * N, phi * (R(1) + Fi) + rec);
         Store<GT>::st(og + ib * N, phi * (R(1) + Fib) - rec);
-    }
+    });
 }
-
 
 // curvature kappa = 3 sum_i w_i c_i . n(x + c_i), taken over opposite pairs as
 // w_i c_i . (n(x + c_i) - n(x - c_i)) so that only the components along c_i

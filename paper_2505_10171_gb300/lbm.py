@@ -310,9 +310,10 @@ class Context:
         return {name: dict(launches=int(out[2 * k]), ms=float(out[2 * k + 1])) for k, name in enumerate(STAGES)}
 
     def lbm_autotune(self, steps=20):
-        """(form, tile) chosen and the per-candidate ms/step (plain, staged 0-2, fused 0-1; -1 unavailable)."""
+        """(form, tile) chosen and the per-candidate ms/step (plain, staged 0-2, fused 0-1, plain 1;
+        -1 unavailable)."""
         f, t = ct.c_int(), ct.c_int()
-        ms = np.zeros(6)
+        ms = np.zeros(7)
         self._check(self.L.lbm_autotune(self.h, int(steps), ct.byref(f), ct.byref(t), _dp(ms)))
         return (f.value, t.value), ms
 

@@ -357,14 +357,16 @@ def _forms_workload(nx, ny, nz):
 
 
 @pytest.mark.parametrize("shape", FORM_SHAPES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16", "mixed"])
 def test_launch_forms_agree(prec, shape):
-    """The staged form (all three variants) gives the bits of the plain form; the
-    z-marching fused form (both tiles, several z-chunk sizes, ragged tiles and
-    chunks) the same bits in FP32 and agrees to rounding in FP64."""
+    """Reference: the plain form with one node per thread.  The plain form's
+    node-pair collision (16-bit total offsets, even nx) and the staged form
+    (all three variants) give its bits; the z-marching fused form (both tiles,
+    several z-chunk sizes, ragged tiles and chunks) the same bits in FP32 and
+    agrees to rounding in FP64."""
     from paper_2505_10171_gb300 import lbm
     w = _forms_workload(*shape)
-    aligned = shape[0] % (16 // {"fp64": 8, "fp32": 4, "fp16": 2}[prec]) == 0
+    aligned = shape[0] % (16 // {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "mixed": 2}[prec]) == 0
 
     def run(form, tile=0, zc=0):
         c = gpu_ctx(w, prec)
@@ -376,14 +378,19 @@ def test_launch_forms_agree(prec, shape):
         c.close()
         return used, out
 
-    used, ref = run(lbm.FORM_PLAIN)
+    used, ref = run(lbm.FORM_PLAIN, 1)
     assert used == lbm.FORM_PLAIN
+    used, got = run(lbm.FORM_PLAIN, 0)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b), "node pairs"
+    if prec == "mixed":
+        return
     for tile in (0, 1, 2):
         used, got = run(lbm.FORM_STAGED, tile)
         assert used == (lbm.FORM_STAGED if aligned else lbm.FORM_PLAIN)
         for a, b in zip(ref, got):
             assert np.array_equal(a, b), ("staged", tile)
-    if prec == "fp16":
+    if prec in ("fp16", "bf16"):
         return
     for tile, zc in ((0, 0), (1, 5), (0, 7), (1, 27), (0, 1)):
         used, got = run(lbm.FORM_FUSED, tile, zc)
@@ -419,22 +426,22 @@ def test_fp64_drop_speed_control_matches_oracle():
 
 
 def test_autotune_picks_a_form_and_keeps_the_trajectory():
-    """The autotuner times all six launch forms/variants (8 steps each here)
+    """The autotuner times all seven launch forms/variants (8 steps each here)
     and keeps the fastest; since every form gives the same FP32 bits, the state
-    afterwards equals 48 plain steps."""
+    afterwards equals 56 plain steps."""
     from paper_2505_10171_gb300 import lbm
     w = _forms_workload(48, 24, 20)
     c = gpu_ctx(w, "fp32")
     (form, tile), ms = c.lbm_autotune(6)
     assert np.all(ms > 0.0), ms
-    assert c.lbm_fluid_form_in_use() == form and ms[[0, 1, 2, 3, 4, 5].index(
-        {(2, 0): 0, (0, 0): 1, (0, 1): 2, (0, 2): 3, (1, 0): 4, (1, 1): 5}[(form, tile)])] == ms.min()
+    assert c.lbm_fluid_form_in_use() == form and ms[
+        {(2, 0): 0, (0, 0): 1, (0, 1): 2, (0, 2): 3, (1, 0): 4, (1, 1): 5, (2, 1): 6}[(form, tile)]] == ms.min()
     fa, fb = c.pops()
     parts = c.lbm_particle_forces()
     c.close()
     c = gpu_ctx(w, "fp32")
     c.lbm_set_fluid_kernel(lbm.FORM_PLAIN)
-    c.lbm_step(48)
+    c.lbm_step(56)
     ra, rb = c.pops()
     assert np.array_equal(fa, ra) and np.array_equal(fb, rb)
     assert np.array_equal(parts, c.lbm_particle_forces())
