@@ -252,8 +252,9 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
  * form = 1, fused: one z-marching kernel per step; tile selects its column
  *   tile (0: 16x16, 1: 32x8); zchunk is the number of z-planes per work item
  *   (0: automatic, 32).
- * Staged and plain agree bit for bit; fused agrees bit for bit in FP32 and to
- * rounding (FMA contraction) in FP64.  Invalid form, tile or zchunk -> LBM_ERR_ARG;
+ * Staged and plain (tile 1) agree bit for bit; fused agrees bit for bit in
+ * FP32 and to rounding (FMA contraction) in FP64; the node-pair collision of
+ * plain tile 0 agrees with tile 1 to the rounding of the storage type.  Invalid form, tile or zchunk -> LBM_ERR_ARG;
  * a form other than plain with the mixed storage -> LBM_ERR_UNSUPPORTED.
  * Invalidates the step graph. */
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk);

@@ -325,8 +325,10 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
 // the pulls along directions with c_x = 0 are one 32-bit load of the pair,
 // every output a pair store (half2, bfloat162 or float2), which halves the
 // per-node load, store, conversion and address instructions.  Each node's
-// arithmetic is that of collide_store_phi; a node of the pair that the bulk
-// kernel skips (solid, next to a solid) is computed but not written.
+// arithmetic is that of collide_store_phi (the same expressions; the code
+// generator may fuse a different set of multiply-adds, so the results agree
+// to rounding); a node of the pair that the bulk kernel skips (solid, next to
+// a solid) is computed but not written.
 template <class S>
 __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
 {

@@ -79,11 +79,23 @@ def place_spheres(rng, n, R, Rc, x_range, y_range, z, min_spacing, max_tries=100
     return out
 
 
+def resting_damping(R_p, rho_p=PARTICLE_DENSITY):
+    """Normal contact damping at half the critical value for a sphere resting
+    on the wall.  Undamped, a sphere released at first contact overshoots its
+    rest overlap by as much again; with the weight 10 sigma R_p and k_n = 2.5 an
+    R_p = 8 sphere then covers the fluid nodes between itself and the wall,
+    and the momentum exchange on its open surface (the rest pressure on the
+    top, none underneath) pushes it into the substrate."""
+    m = rho_p * 4.0 / 3.0 * math.pi * R_p ** 3
+    return 0.5 * 2.0 * math.sqrt(COMMON["kn"] * m)
+
+
 def cfg2(seed=20251, n_spheres=8):
     """256x128x128 resolved run: drop R=40 driven along x over a 150 deg wall
     (body force on the drop, PI-controlled every 100 steps towards a drop speed
     of 5e-3), eight spheres R_p=8 with contact angles uniform in [30, 90] deg,
-    drop:ambient kinematic viscosities 1/6 : 1/60."""
+    drop:ambient kinematic viscosities 1/6 : 1/60, normal contact damping at
+    half the critical value."""
     nx, ny, nz = 256, 128, 128
     R_p, Rc = 8.0, 9.0
     rng = np.random.default_rng(seed)
@@ -93,6 +105,7 @@ def cfg2(seed=20251, n_spheres=8):
     sigma = COMMON["sigma"]
     params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, wall_velocity=(0.0, 0.0, 0.0),
                   theta_wall_deg=150.0, nu_a=1.0 / 6.0, nu_b=1.0 / 60.0, mu_s=0.3, mu_r=0.05,
+                  gn=resting_damping(R_p),
                   body_force_a=(2.0e-6, 0.0, 0.0), g_particle=(0.0, 0.0, -10.0 * sigma * R_p),
                   drop_speed_control=1, drop_speed_target=(5.0e-3, 0.0, 0.0), drop_speed_interval=100)
     phi = drop_phi(nx, ny, nz, (48.0, 64.0, 0.5), 40.0)
@@ -141,7 +154,7 @@ def cfg4(seed=4242, n_instances=96):
         R_p = Rd / 5.0
         sigma = COMMON["sigma"]
         params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=90.0,
-                      nu_a=1.0 / 6.0, nu_b=1.0 / 60.0, mu_s=mu_s, mu_r=mu_r,
+                      nu_a=1.0 / 6.0, nu_b=1.0 / 60.0, mu_s=mu_s, mu_r=mu_r, gn=resting_damping(R_p),
                       body_force_a=(U * 4e-4, 0.0, 0.0), g_particle=(0.0, 0.0, -10.0 * sigma * R_p),
                       drop_speed_control=1, drop_speed_target=(U, 0.0, 0.0), drop_speed_interval=100)
         xd = 1.2 * Rd

