@@ -122,6 +122,7 @@ __device__ __forceinline__ void grad_body(const Lattice &L, const InstDev &I, in
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
 {
+    pdl_trigger();  // the gradient pass may be scheduled as this grid drains
     for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S, false>(L, I, cur, n, x, y, z); });
 }
 
@@ -431,6 +432,7 @@ __global__ void __launch_bounds__(ROW_NODES / 2, LBM_COLLIDE2_MINB) k_collide2(L
 {
     StItem it;
     st_item(L, blockIdx.x, it);
+    pdl_wait();  // the gradient pass's normals, |grad phi| and curvature
     const int j = 2 * (int)threadIdx.x;
     if (j >= it.cnt) return;
     const InstDev &I = L.inst[it.k];
@@ -442,7 +444,10 @@ __global__ void __launch_bounds__(ROW_NODES / 2, LBM_COLLIDE2_MINB) k_collide2(L
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_collide(Lattice L, int cur)
 {
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { collide_body<S>(L, I, cur, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) {
+        pdl_wait();  // the gradient pass's normals, |grad phi| and curvature
+        collide_body<S>(L, I, cur, n, x, y, z);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -534,6 +539,8 @@ __global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : 4) k_gradcu
         const int r = tid + q * NT;
         roff[q] = r < PN ? wrap_any(y0 - 2 + r / PW, ny) * nx + wrap_any(x0 - 2 + r % PW, nx) : -1;
     }
+    pdl_trigger();  // the collision may be scheduled as this grid drains
+    pdl_wait();     // phi of the order-parameter pass
     R pv[PER];
     uint8_t fv[PER];
     auto fetch = [&](int j) {
@@ -650,6 +657,24 @@ long long plan_gradcurv(std::vector<InstDev> &inst)
 int fused_tile_x(int tile) { return tile == 1 ? 32 : 16; }
 int fused_tile_y(int tile) { return tile == 1 ? 8 : 16; }
 
+// launch with programmatic stream serialisation: the kernel may be scheduled
+// while its predecessor in the stream drains (it calls pdl_wait first)
+template <class... P, class... A>
+static void launch_after(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t st, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <class S>
 void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
                        const FluidLaunch &fz, const Hook &after_grad, const SideLane &lane)
@@ -732,7 +757,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         mk(STAGE_SOLIDPHI, 1);
     }
     mk(STAGE_GRAD, 0);
-    k_gradcurv<R><<<(unsigned)fz.gc_items, GC_TX * GC_TY, 0, st>>>(L);
+    launch_after(k_gradcurv<R>, dim3((unsigned)fz.gc_items), dim3(GC_TX * GC_TY), st, L);
     mk(STAGE_GRAD, 1);
     after_grad();
     if (staged) {
@@ -743,11 +768,11 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         bound_pass(k_collide_bound<S>, STAGE_COLLIDE_BOUND, STAGE_COLLIDE, [&] {
             if constexpr (sizeof(typename PopTypes<S>::F) == 2) {
                 if (fz.pair) {
-                    k_collide2<S><<<grid, ROW_NODES / 2, 0, st>>>(L, cur);
+                    launch_after(k_collide2<S>, grid, dim3(ROW_NODES / 2), st, L, cur);
                     return;
                 }
             }
-            k_collide<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+            launch_after(k_collide<S>, grid, dim3(ROW_NODES), st, L, cur);
         });
     }
     *launches += 3;

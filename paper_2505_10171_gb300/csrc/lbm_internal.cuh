@@ -171,6 +171,15 @@ struct Lattice {
 __device__ __forceinline__ void keep(float &v) { asm volatile("" : "+f"(v)); }
 __device__ __forceinline__ void keep(double &v) { asm volatile("" : "+d"(v)); }
 
+// programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may start while its predecessor in the stream drains; it must
+// wait here before touching anything the predecessor writes or reads.  A
+// predecessor signals early that its dependent may be scheduled (all of its
+// CTAs have started by then, so the dependent cannot take their places).
+// Both are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // streamed populations are read through the read-only path (measured on this
 // GPU: as fast as plain loads, faster than evict-first streaming loads)
 template <class T>
