@@ -457,6 +457,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
         // buffer), the capillary force only phi, n and |grad phi| once the
         // gradient pass is done.  Profiling keeps one stream (per-kernel events).
         const bool fork = !sur && !c->profile && L.n_parts > 0 && c->fz.form != FORM_FUSED;
+        bool owner_done = false;  // owners updated on the side stream
         if (fork) {
             cudaEventRecord(c->ev_fork, c->stream);
             cudaStreamWaitEvent(c->side, c->ev_fork, 0);
@@ -487,9 +488,16 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
             lane.after_collide_bound.fn = [](void *p) {
                 Ctx2 *q = (Ctx2 *)p;
                 launch_dem<S>(*q->L, q->c->side, q->launches, *q->mk, true);
+                // the new owners beside the bulk collision: the nodes whose
+                // owner changes are solid or next to a solid before and after,
+                // which the bulk collision skips either way; with a stored
+                // velocity it would zero that of newly covered nodes, so then
+                // the owners follow the collision
+                if (!q->c->u) launch_geom_owner(*q->L, q->c->side, q->launches, *q->mk);
                 cudaEventRecord(q->c->ev_join, q->c->side);
             };
             const bool plain = c->fz.form == FORM_PLAIN || c->fz.st_items == 0;
+            owner_done = plain && !c->u;
             launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz, hook, lane);
             if (!plain) {
                 // staged form: no boundary passes on the side lane; DEM after the join
@@ -507,7 +515,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
         // geometry: owners first; then boundary bits (side stream) beside the
         // refill of uncovered nodes (they touch disjoint data)
         if (!c->profile && L.n_parts > 0) {
-            launch_geom_owner(L, c->stream, launches, mk);
+            if (!owner_done) launch_geom_owner(L, c->stream, launches, mk);
             cudaEventRecord(c->ev_fork, c->stream);
             cudaStreamWaitEvent(c->side, c->ev_fork, 0);
             launch_geom_bound(L, c->side, launches, mk);
