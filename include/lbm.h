@@ -239,9 +239,9 @@ lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
  * form = 2 (default), plain: five kernels per step (order parameter, solid
  *   phi, gradient + wetting + normal, curvature, collision), direct loads.
  *   tile 0: with 16-bit total offsets (FP16, BF16, mixed) and an even nx in
- *   every instance the bulk collision takes two nodes of a row per thread
- *   (pair loads and stores), one node per thread otherwise; tile 1: one node
- *   per thread always.
+ *   every instance the bulk order-parameter and collision kernels take two
+ *   nodes of a row per thread (pair loads and stores), one node per thread
+ *   otherwise; tile 1: one node per thread always.
  * form = 0, staged: the same five kernels, but the two that stream the
  *   populations are persistent and bring each strip of x-rows into a ring of
  *   shared-memory stages with asynchronous copies.  tile selects the variant:

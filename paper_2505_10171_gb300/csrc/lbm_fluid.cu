@@ -81,6 +81,58 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     ((R *)L.phi)[g] = v;
 }
 
+// the order parameter of a node pair (x even, x + 1) per thread, for 16-bit
+// total offsets: pulls along c_x = 0 as one pair load (32-bit, or 64-bit for
+// FP32 colour offsets), the two phi in one pair store; each node's sums are
+// those of phi_fluid
+template <class S>
+__device__ __forceinline__ void phi_body2(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
+{
+    using R = typename Store<S>::real;
+    using FT = typename Pop<S>::FT;
+    using GT = typename Pop<S>::GT;
+    const long long g = I.node_off + n;  // even
+    const uint8_t fl0 = L.flags[g], fl1 = L.flags[g + 1];
+    const Pop<S> in(L.pop[cur], I);
+    const int N = in.N;
+    Nbr nb;
+    nb.init(x, y, z, I.nx, I.ny, I.nz);
+    const int xp2 = x + 2 == I.nx ? 0 : x + 2;
+    R sF0 = 0, sG0 = 0, sF1 = 0, sG1 = 0;
+    auto pull = [&](auto *row, int i, R &a, R &b) {
+        using T = std::remove_cv_t<std::remove_pointer_t<decltype(row)>>;
+        if (cx(i) == 0) {
+            ld_pair(row + x, a, b);
+        } else if (cx(i) == 1) {
+            a = Store<T>::ld(row + nb.X[0]);
+            b = Store<T>::ld(row + x);
+        } else {
+            a = Store<T>::ld(row + x + 1);
+            b = Store<T>::ld(row + xp2);
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int ro = i * N + nb.ZO[1 - cz(i)] + nb.YO[1 - cy(i)];
+        R F0, F1, G0, G1;
+        pull((const FT *)in.f + ro, i, F0, F1);
+        pull((const GT *)in.g() + ro, i, G0, G1);
+        sF0 += wgt<R>(i) * F0;
+        sG0 += wgt<R>(i) * G0;
+        sF1 += wgt<R>(i) * F1;
+        sG1 += wgt<R>(i) * G1;
+    }
+    R v0 = sG0 / (R(1) + sF0), v1 = sG1 / (R(1) + sF1);
+    keep(v0);
+    keep(v1);
+    const bool a0 = (fl0 & OWNER_MASK) == OWN_FLUID && !(fl0 & BOUND_BIT);
+    const bool a1 = (fl1 & OWNER_MASK) == OWN_FLUID && !(fl1 & BOUND_BIT);
+    R *ph = (R *)L.phi + g;
+    if (a0 && a1) st_pair(ph, v0, v1);
+    else if (a0) ph[0] = v0;
+    else if (a1) ph[1] = v1;
+}
+
 template <class R>
 __device__ __forceinline__ void solidphi_body(const Lattice &L, const InstDev &I, int n, int x, int y, int z)
 {
@@ -124,6 +176,23 @@ __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) 
 {
     pdl_trigger();  // the gradient pass may be scheduled as this grid drains
     for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S, false>(L, I, cur, n, x, y, z); });
+}
+
+#ifndef LBM_PHI2_MINB
+#define LBM_PHI2_MINB 8
+#endif
+template <class S>
+__global__ void __launch_bounds__(ROW_NODES / 2, LBM_PHI2_MINB) k_phi2(Lattice L, int cur)
+{
+    pdl_trigger();  // the gradient pass may be scheduled as this grid drains
+    StItem it;
+    st_item(L, blockIdx.x, it);
+    const int j = 2 * (int)threadIdx.x;
+    if (j >= it.cnt) return;
+    const InstDev &I = L.inst[it.k];
+    int x, y;
+    item_node(it, I.nx, j, &x, &y);
+    phi_body2<S>(L, I, cur, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
 }
 
 // instance of global node g (binary search over the node offsets)
@@ -749,7 +818,15 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         if constexpr (!is_mixed<S>) launch_staged_phi<S>(L, cur, fz, st);
         mk(STAGE_PHI, 1);
     } else {
-        bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] { k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
+        bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] {
+            if constexpr (sizeof(typename PopTypes<S>::F) == 2) {
+                if (fz.pair) {
+                    k_phi2<S><<<grid, ROW_NODES / 2, 0, st>>>(L, cur);
+                    return;
+                }
+            }
+            k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+        });
     }
     if (!fill_done) {
         mk(STAGE_SOLIDPHI, 0);

@@ -283,6 +283,12 @@ __device__ __forceinline__ void ld_pair(const __nv_bfloat16 *p, float &a, float 
     a = __low2float(v);
     b = __high2float(v);
 }
+__device__ __forceinline__ void ld_pair(const float *p, float &a, float &b)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    a = v.x;
+    b = v.y;
+}
 __device__ __forceinline__ void st_pair(__half *p, float a, float b)
 {
     *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
