@@ -407,14 +407,16 @@ def test_launch_forms_agree(prec, shape):
     used, ref = run(lbm.FORM_PLAIN, 1)
     assert used == lbm.FORM_PLAIN
     used, got = run(lbm.FORM_PLAIN, 0)
-    # 25 steps from one FP32 rounding difference per value at most: within a
-    # few units of the stored type's last place (half 2^-11, bfloat16 2^-8)
+    # 25 steps from one FP32 rounding difference per value at most: the
+    # populations within a few units of the stored type's last place (half
+    # 2^-11, bfloat16 2^-8), the particle forces and the velocity (small
+    # differences of populations) within a few tens
     ulp = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "mixed": 2.0 ** -11}.get(prec, 0.0)
-    for a, b in zip(ref, got):
+    for a, b, k in zip(ref, got, (8, 8, 64, 64)):
         if ulp == 0.0:
             assert np.array_equal(a, b), "node pairs"
         else:
-            assert rel_l2(a, b) <= 8 * ulp, ("node pairs", rel_l2(a, b))
+            assert rel_l2(a, b) <= k * ulp, ("node pairs", rel_l2(a, b))
     if prec == "mixed":
         return
     for tile in (0, 1, 2):
