@@ -96,7 +96,8 @@ def detachment(theta_deg, R_p=25, v_p=0.01, equil_steps=None, rise=5.0, sample_e
 
 def interface_height(phi_col):
     """Height of the upper zero crossing of phi along one z column (linear
-    interpolation between the two nodes around it)."""
+    interpolation between the two nodes around it: exact for a crossing at a
+    node or midway, within 0.03 lattice units for a tanh of width 2.5)."""
     ph = np.asarray(phi_col)
     k = int(np.argmax(ph))
     while k + 1 < len(ph) and ph[k + 1] > 0.0:

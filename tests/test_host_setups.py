@@ -1,0 +1,77 @@
+"""Host-side set-up code of the benchmarks and the surrogate campaign (no GPU):
+geometry of the detachment and wetting benchmarks, the interface-height
+helper, and the resolved / coarse campaign set-ups."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2505_10171_gb300 import surrogate_study as SS
+from paper_2505_10171_gb300 import validation as V
+from paper_2505_10171_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("theta", [30.0, 90.0, 150.0])
+def test_detachment_setup_geometry(theta):
+    """The sphere sits at the flat-interface equilibrium height (contact angle
+    measured in the liquid below); the liquid layer's order parameter crosses
+    zero at z_i = 4 R_p; the pull of 5 R_p stays inside the box."""
+    R = 10
+    p, phi, part = V.detachment_setup(theta, R)
+    nz = p["nz"]
+    col = phi.reshape(nz, p["ny"], p["nx"])[:, 0, 0]
+    zi = V.interface_height(col)
+    assert abs(zi - 4.0 * R) < 1e-9
+    assert abs(part["x"][2] - (4.0 * R - R * math.cos(math.radians(theta)))) < 1e-12
+    assert part["x"][2] + 5.0 * R + R < nz
+    assert part["kinematic"] == 1 and p["wall_z0"] == 0
+
+
+def test_interface_height_of_a_tanh_profile():
+    """Linear interpolation of the zero crossing is exact for an odd profile
+    crossing at a node or midway between two, and within 0.03 of the true
+    crossing for a tanh of width 2.5 elsewhere (0.07 deg of measured angle at
+    R_p = 25)."""
+    z = np.arange(100, dtype=np.float64)
+    for z0, tol in ((40.0, 1e-12), (40.5, 1e-12), (40.25, 0.03), (61.8, 0.03)):
+        col = np.tanh(2.0 * np.minimum(z - 5.0, z0 - z) / W.INTERFACE_WIDTH)
+        assert abs(V.interface_height(col) - z0) <= tol
+
+
+@pytest.mark.parametrize("seed", [1, 7, 101])
+def test_campaign_setups_scale_consistently(seed):
+    """The coarse set-up is the resolved one at 3/8: box, drop, sphere centres
+    in x and y; every sphere keeps a fluid node between itself and the wall
+    (delta_R = 1 unscaled, centre R_p + 1.5 above the wall plane) and clear of
+    the others by more than the contact distance; sigma, the drop speed and
+    the shell scale as the campaign states."""
+    f, c = SS.resolved(seed), SS.coarse(seed)
+    s = SS.SCALE
+    pf, pc = f["params"], c["params"]
+    assert (pc["nx"], pc["ny"], pc["nz"]) == (96, 48, 48)
+    assert abs(pc["sigma"] - pf["sigma"] * s) < 1e-15
+    assert abs(pc["drop_speed_target"][0] - pf["drop_speed_target"][0] * s) < 1e-15
+    assert pc["delta_R"] == pf["delta_R"] == 1.0
+    assert abs(pc["surrogate_shell_gap"] - 2.0) < 1e-12 and abs(pf["surrogate_shell_gap"] - 2.0 / s) < 1e-12
+    for qf, qc in zip(f["particles"], c["particles"]):
+        assert abs(qc["x"][0] - qf["x"][0] * s) < 1e-12 and abs(qc["x"][1] - qf["x"][1] * s) < 1e-12
+        for q, p in ((qf, pf), (qc, pc)):
+            assert abs(q["x"][2] - (0.5 + q["R"] + 1.0)) < 1e-12
+            # the node plane z = 1 below the centre stays fluid
+            assert q["x"][2] - 1.0 > q["R"]
+    for ws, p in ((f, pf), (c, pc)):
+        xs = np.array([q["x"] for q in ws["particles"]])
+        Rc = ws["particles"][0]["R"] + p["delta_R"]
+        d = np.linalg.norm(xs[:, None, :2] - xs[None, :, :2], axis=-1) + np.eye(len(xs)) * 1e9
+        assert d.min() > 2.0 * Rc
+    # damping below the critical value the DEM check accepts
+    for ws, p in ((f, pf), (c, pc)):
+        R = ws["particles"][0]["R"]
+        m = W.PARTICLE_DENSITY * 4.0 / 3.0 * math.pi * R ** 3
+        assert 0.0 < p["gn"] < 2.0 * math.sqrt(p["kn"] * m)
+
+
+def test_resting_damping_is_half_critical():
+    for R in (3.0, 8.0):
+        m = W.PARTICLE_DENSITY * 4.0 / 3.0 * math.pi * R ** 3
+        assert abs(W.resting_damping(R) - math.sqrt(W.COMMON["kn"] * m)) < 1e-12
