@@ -90,3 +90,32 @@ def test_precision_codes_match_header():
     names = {"fp64": "LBM_FP64", "fp32": "LBM_FP32", "fp16": "LBM_FP16_OFFSET", "bf16": "LBM_BF16_OFFSET",
              "mixed": "LBM_F16_F32_OFFSET"}
     assert {k: enum[v] for k, v in names.items()} == lbm.PRECISIONS
+
+
+BASE = dict(nx=8, ny=8, nz=8)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(nx=0), dict(ny=-3), dict(nx=1024, ny=1024, nz=64),          # sizes; 38 N >= 2^31
+    dict(wall_z0=1, nz=2),                                            # a substrate needs 3 planes
+    dict(nu_a=0.0), dict(nu_b=float("nan")), dict(rho0=-1.0),
+    dict(beta=1.5), dict(sigma=-0.01), dict(theta_wall_deg=180.0),
+    dict(wall_velocity=(float("inf"), 0.0, 0.0)), dict(kn=-1.0), dict(mu_r=-0.1),
+    dict(cap_norm=-1.0), dict(grad_eps=-1e-4), dict(surrogate_shell_gap=-1.0),
+    dict(drop_speed_control=8), dict(drop_speed_interval=-1),
+])
+def test_create_rejects_invalid_parameters(libpath, bad):
+    """Parameters are checked before any device call: an invalid one gives
+    LBM_ERR_ARG on any machine, with or without a GPU."""
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Context(dict(BASE, **bad), "fp32")
+    assert e.value.status == 1  # LBM_ERR_ARG
+
+
+def test_create_rejects_an_unknown_precision(libpath):
+    L = lbm.load()
+    arr = (lbm.lbm_params * 1)(lbm.make_params(**BASE))
+    h = ct.c_void_p()
+    assert L.lbm_create(arr, 1, 9, None, ct.byref(h)) == 7  # LBM_ERR_UNSUPPORTED
+    assert L.lbm_create(arr, 0, 1, None, ct.byref(h)) == 1  # no instances: LBM_ERR_ARG
+    assert not h.value
