@@ -15,10 +15,14 @@
  * carry the same label as the list of readings kept with the design notes
  * (c1 ... c31).
  *
- * Parity pins: see tests/test_oracle_*.py.  Everything here is pinned by at
- * least one closed form, invariant or brute-force check, except the whole
- * coupled step, which has no closed form ("parity unpinned" beyond its
- * component pins).
+ * Parity pins: see tests/test_oracle_*.py.  Every function here is pinned by
+ * at least one closed form, invariant or brute-force check.  The whole
+ * coupled step has no single closed form; it is pinned through whole-step
+ * behaviour: the exact Poiseuille profile between halfway walls, a uniform
+ * flow over a moving wall that stays steady, component mass conservation of a
+ * drop on a sliding wall, the Laplace law of a drop, the sessile contact
+ * angle, the momentum balance between the fluid and a sphere, and the mass
+ * bookkeeping of a sphere that covers and uncovers nodes.
  */
 #include "lbm_oracle.h"
 
