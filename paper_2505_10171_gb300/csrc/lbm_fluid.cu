@@ -549,7 +549,10 @@ struct GcNbr {
 };
 
 template <class R>
-__global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : 4) k_gradcurv(Lattice L)
+#ifndef LBM_GC_MINB
+#define LBM_GC_MINB 4
+#endif
+__global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : LBM_GC_MINB) k_gradcurv(Lattice L)
 {
     constexpr int NT = GC_TX * GC_TY;
     constexpr int PW = GC_TX + 4, PH = GC_TY + 4, PN = PW * PH;  // phi / flag region (2-node halo)
