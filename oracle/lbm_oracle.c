@@ -1067,7 +1067,7 @@ void or_get_phi(const or_sim *s, double *phi)
     memcpy(phi, s->phi, sizeof(double) * s->N);
 }
 
-/* SURVEY c27 reading: the drop is driven by the body force on phase a.
+/* READING c27: the drop is driven by the body force on phase a.
    Every `interval` steps the mass-weighted velocity of phase a over the fluid
    nodes of the current (post-collision) state,
        U_a = sum_x (rho^a / rho) j / sum_x rho^a,  j = sum_i c_i (f^a_i + f^b_i),

@@ -56,7 +56,7 @@ def test_component_mass_conserved_drop_on_sliding_wall():
 
 
 def test_drop_speed_controller_follows_the_pi_recurrence():
-    """SURVEY c27 reading: PI control of the phase-a body force.  In a uniform
+    """Reading c27: PI control of the phase-a body force.  In a uniform
     single-phase periodic box Guo forcing adds exactly f to the momentum per
     node and step, so the measured velocity after step t is U(t) = U(t-1) +
     f(t)/rho0 and the force follows the PI law updated every `iv` steps; the
