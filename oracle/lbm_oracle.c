@@ -22,7 +22,11 @@
  * flow over a moving wall that stays steady, component mass conservation of a
  * drop on a sliding wall, the Laplace law of a drop, the sessile contact
  * angle, the momentum balance between the fluid and a sphere, and the mass
- * bookkeeping of a sphere that covers and uncovers nodes.
+ * bookkeeping of a sphere that covers and uncovers nodes.  The refill values
+ * (one-hop, two-hop and ambient branches), the momentum-exchange torque (an
+ * exact angular-momentum balance with a spinning sphere across the periodic
+ * boundary) and the sphere branch of the wetting normal (the rotated
+ * gradient's angle to the nearest sphere's normal) have pins of their own.
  */
 #include "lbm_oracle.h"
 

@@ -121,3 +121,215 @@ def test_capillary_matches_surface_integral():
     assert Fb[2] < 0  # the drop below pulls the particle down along the line of centres
     assert abs(F[2] / Fb[2] - 1) < 0.05
     assert np.abs(F[:2]).max() < 1e-12 and np.abs(T).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Pins of the refill values, the momentum-exchange torque and the sphere branch
+# of the wetting normal.  Each one recomputes the quantity from the paper's
+# definition with this file's own lattice arithmetic (velocities and weights
+# from |c|^2, pinned in test_oracle_lattice.py) and the oracle's state.
+# ---------------------------------------------------------------------------
+def _lat():
+    c, w, _ = O.lattice()
+    return c, w
+
+
+def _feq(rho, u, c, w):
+    """Second-order equilibrium of Sec. V C: w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2)."""
+    cu = c @ u
+    return w * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * (u @ u))
+
+
+def _nbr(n3, z, y, x, d):
+    nx, ny, nz = n3
+    return (((z + d[2]) % nz) * ny + (y + d[1]) % ny) * nx + (x + d[0]) % nx
+
+
+def _refill_expected(s, own0, c, w, xp, vp, wp):
+    """Sec. V C refill of every node that the particle uncovered in the last
+    step: f^{a,b}_eq(rho_bar^{a,b}, u_p + w_p x (x - x_p)), rho_bar the mean
+    density over the moving-direction neighbours that are fluid and were not
+    fresh (two hops along the same directions if there is none, the ambient
+    state (0, rho0) if there is still none; reading c16)."""
+    n3 = (s.nx, s.ny, s.nz)
+    own1 = s.owner()
+    fa, fb = s.pops()
+    fresh = (own0 >= 2) & (own1 == 0)
+    out, branch = [], []
+    for g in np.nonzero(fresh)[0]:
+        z, y, x = g // (s.nx * s.ny), (g // s.nx) % s.ny, g % s.nx
+        for hop in (1, 2):
+            src = [q for q in (_nbr(n3, z, y, x, hop * c[i]) for i in range(1, 19)) if own1[q] == 0 and not fresh[q]]
+            if src:
+                break
+        if src:
+            ra = np.mean([fa[:, q].sum() for q in src])
+            rb = np.mean([fb[:, q].sum() for q in src])
+            branch.append(hop)
+        else:
+            ra, rb = 0.0, s.params.rho0
+            branch.append(0)
+        d = np.array([x, y, z], float) - xp
+        d -= np.array(n3) * np.round(d / np.array(n3))
+        u = vp + np.cross(wp, d)
+        out.append((g, _feq(ra, u, c, w), _feq(rb, u, c, w)))
+    return out, branch, fa, fb
+
+
+def test_refill_values_from_the_neighbour_mean():
+    """Sec. V C: a fast kinematic sphere over a fluid of random density and order
+    parameter; every uncovered node holds f_eq of the mean over its fluid,
+    non-fresh neighbours (N_f of them, not 18) at the rigid-body velocity of its
+    own position, including nodes that need the two-hop fallback."""
+    c, w = _lat()
+    n = 22
+    rng = np.random.default_rng(11)
+    s = O.OracleSim(n, n, n, sigma=0.01)
+    s.init_fields(rng.uniform(-0.9, 0.9, n ** 3), rng.uniform(0.9, 1.1, n ** 3))
+    vp, wp = np.array([2.2, 0.4, 0.1]), np.array([0.01, -0.02, 0.015])
+    s.add_particle((6.3, 11.2, 10.7), 4.3, v=vp, w=wp, kinematic=True)
+    seen = set()
+    checked = 0
+    for _ in range(3):
+        own0 = s.owner().copy()
+        s.step(1)
+        xp = s.particles()[0][18:21]
+        exp, branch, fa, fb = _refill_expected(s, own0, c, w, xp, vp, wp)
+        seen |= set(branch)
+        for g, ea, eb in exp:
+            # at |u| ~ 2 the polynomial's terms reach ~10 and cancel: 1e-13 absolute
+            assert np.abs(fa[:, g] - ea).max() < 1e-13 and np.abs(fb[:, g] - eb).max() < 1e-13
+            checked += 1
+    assert checked > 100 and {1, 2} <= seen
+
+
+def test_refill_ambient_without_fluid_neighbours():
+    """Reading c16's last fallback: a sphere in a cavity that holds no fluid at
+    all leaves behind nodes with no fluid within two hops; they take
+    f_eq(0, u) for phase a and f_eq(rho0, u) for phase b."""
+    c, w = _lat()
+    n = 20
+    xp0, R = np.array([9.4, 10.1, 9.8]), 4.2
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    inside = (x - xp0[0]) ** 2 + (y - xp0[1]) ** 2 + (z - xp0[2]) ** 2 < R * R
+    s = O.OracleSim(n, n, n, sigma=0.0, rho0=1.3)
+    s.set_static_solid(~inside)
+    s.init_fields(np.ones(n ** 3))
+    vp, wp = np.array([1.1, -0.3, 0.2]), np.array([0.0, 0.02, -0.01])
+    s.add_particle(xp0, R, v=vp, w=wp, kinematic=True)
+    own0 = s.owner().copy()
+    s.step(1)
+    exp, branch, fa, fb = _refill_expected(s, own0, c, w, s.particles()[0][18:21], vp, wp)
+    assert len(exp) > 10 and set(branch) == {0}
+    for g, ea, eb in exp:
+        assert np.abs(fa[:, g]).max() == 0.0
+        assert np.abs(fb[:, g] - eb).max() < 1e-15
+
+
+def test_torque_balances_fluid_angular_momentum():
+    """Sec. V B: a kinematically spinning sphere that straddles the periodic
+    boundary, in fluid that starts at rest.  Per link the fluid gains
+    (x - x_p) x c_i (f_in + f_out) and the particle receives
+    (x_w - x_p) x [(c_out - u_w) f_out - (c_in - u_w) f_in], x_w the link
+    midpoint; since c_i x c_i = 0 the two differ only by
+    (x_w - x_p) x u_w (f_in - f_out), f_in - f_out = 6 w_i rho c_i.u_w.  So
+    T_eta = -dL_fluid + sum_links (x_w - x_p) x u_w 6 w_i rho c_i.u_w, with the
+    fluid's angular momentum L about x_p (minimum image) before and after the
+    step.  The disturbance reaches no far periodic boundary within the steps
+    checked, so L has no boundary flux."""
+    c, w = _lat()
+    n = 26
+    s = O.OracleSim(n, n, n, sigma=0.0)
+    s.init_fields(-np.ones(n ** 3))
+    xp, R = np.array([1.3, 12.7, 11.9]), 4.6
+    om = np.array([0.004, -0.007, 0.011])
+    s.add_particle(xp, R, w=om, kinematic=True)
+    z, y, x = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    pos = np.stack([x.ravel(), y.ravel(), z.ravel()]).astype(float)
+
+    def mi(d):
+        return d - n * np.round(d / n)
+
+    r = mi(pos - xp[:, None])
+
+    def ang(own):
+        fa, fb = s.pops()
+        f = fa + fb
+        m = own == 0
+        return np.cross(r[:, m].T, (c.T @ f)[:, m].T).sum(0), f.sum(0)
+
+    def link_term(own, rho, lever_at_node=False):
+        C = np.zeros(3)
+        for i in range(1, 19):
+            src = ((((z - c[i, 2]) % n) * n + (y - c[i, 1]) % n) * n + (x - c[i, 0]) % n).ravel()
+            idx = np.nonzero((own == 0) & (own[src] >= 2))[0]
+            lev = mi(pos[:, idx] - 0.5 * c[i][:, None] - xp[:, None])
+            uw = np.cross(om, lev.T).T
+            d = 6.0 * w[i] * rho[idx] * (c[i] @ uw)
+            C += (np.cross((r[:, idx] if lever_at_node else lev).T, uw.T) * d[:, None]).sum(0)
+        return C
+
+    s.step(1)
+    for _ in range(4):
+        own = s.owner()
+        L0, rho = ang(own)
+        C = link_term(own, rho)
+        s.step(1)
+        assert (s.owner() == own).all()
+        L1, _ = ang(own)
+        T = s.particles()[0][3:6]
+        assert np.abs(T).max() > 1.0
+        assert np.abs(T - (C - (L1 - L0))).max() < 1e-12 * np.abs(T).max()
+        # the lever at the node instead of the link midpoint would miss by far more
+        assert np.abs(link_term(own, rho, True) - C).max() > 1e-6
+
+
+def test_sphere_wetting_normal_geometry():
+    """Sec. V D with reading c11/c12 on spheres: two spheres of different contact
+    angle across a flat diffuse interface, 0.7 lu apart.  At every fluid node
+    next to a particle with |phi| < 0.99, -grad(phi) after the wetting step has
+    the magnitude of the plain stencil gradient and the direction
+    cos(theta_p) n_s + sin(theta_p) e, where n_s = (x - x_p)/|x - x_p| of the
+    nearest sphere surface, theta_p that sphere's angle and e the unit part of
+    n* = -g/|g| normal to n_s (the candidate on n*'s side).  Every other node
+    keeps the plain gradient."""
+    n = 36
+    zc = np.arange(n, dtype=float)
+    phi = np.broadcast_to(np.tanh(0.55 * (17.3 - zc))[:, None, None], (n, n, n)).reshape(-1)
+    sph = [((11.4, 17.2, 18.1), 6.3, 40.0), ((24.3, 18.4, 16.9), 6.0, 125.0)]
+    grads = []
+    for wet in (0.99, 0.0):
+        s = O.OracleSim(n, n, n, sigma=0.01, wet_phi_max=wet)
+        s.init_fields(phi)
+        for xp, R, th in sph:
+            s.add_particle(xp, R, theta_deg=th, kinematic=True)
+        ph, g = s.eval_interface()
+        grads.append(g)
+        own = s.owner()
+    g1, g0 = grads
+    c, _ = _lat()
+    n3 = (n, n, n)
+    rotated = nearest_used = 0
+    for gi in np.nonzero(own == 0)[0]:
+        z, y, x = gi // (n * n), (gi // n) % n, gi % n
+        owners = {own[_nbr(n3, z, y, x, c[i])] for i in range(1, 19)} - {0}
+        if not owners or abs(ph[gi]) >= 0.99:
+            assert np.array_equal(g1[:, gi], g0[:, gi])
+            continue
+        dist = []
+        for o in sorted(owners):
+            xp, R, th = sph[o - 2]
+            d = np.array([x, y, z], float) - np.array(xp)
+            dist.append((np.linalg.norm(d) - R, o - 2, d / np.linalg.norm(d), math.radians(th)))
+        _, p, ns, th = min(dist)
+        nearest_used += len(owners) > 1
+        gm = np.linalg.norm(g0[:, gi])
+        nst = -g0[:, gi] / gm
+        e = nst - (nst @ ns) * ns
+        if np.linalg.norm(e) < 1e-3:
+            continue
+        e /= np.linalg.norm(e)
+        expect = -gm * (math.cos(th) * ns + math.sin(th) * e)
+        assert np.abs(g1[:, gi] - expect).max() < 1e-12 * max(gm, 1e-3)
+        rotated += 1
+    assert rotated > 100 and nearest_used > 0
