@@ -29,26 +29,56 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and % of HBM roofline at 1 GB300 (FP32 vs FP16-storage vs batched) at stated error"
 UNIT = "MLUPS"
 WORKLOAD = "drop R=40 sliding over a 150 deg wall + 8 spheres R_p=8, 256x128x128 (4.19M nodes), coupled LBM-DEM step"
-# element bytes of the total (F) and colour (G) populations; algorithmic bytes
-# per lattice update of the fluid update: read + write of 19 F and 19 G
-ELEM = {"fp64": (8, 8), "fp32": (4, 4), "fp16": (2, 2), "bf16": (2, 2), "mixed": (2, 4)}
-DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math",
-         "mixed": "f16(F)+f32(G)-storage/f32-math"}
+# bytes of one stored total population (F) and of one per-node real (phi, b,
+# normal, |grad phi|, curvature)
+ELEM = {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2}
+REAL = {"fp64": 8, "fp32": 4, "fp16": 4, "bf16": 4}
+DTYPE = {"fp64": "f64", "fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math"}
 
 
-def algorithmic_bytes_per_node(stage, prec):
-    """Bytes a kernel must move per node: the order-parameter pass reads the 38
-    streamed populations and writes phi; the collision reads the 19 streamed
-    total populations and phi and writes all 38 populations."""
-    ef, eg = ELEM[prec]
-    r = 8 if prec == "fp64" else 4
-    return {"collide": 38 * ef + 19 * eg + r, "phi": 19 * (ef + eg) + r}.get(stage, 0)
+def method_bytes_per_lu(prec):
+    """The method's population traffic per lattice update: read and write of
+    2 x 19 populations at the storage precision."""
+    return 2 * 38 * ELEM[prec]
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
-# capture of this workload (profiles/step_launches_fp32_256x128x128.md); valid
-# while the kernel is unchanged since that capture
-NCU_TRAFFIC = {("collide", "fp32"): 990.03e6}
+def population_bytes_per_node(stage, prec):
+    """Population bytes a kernel moves per node: the order-parameter pass reads
+    the 19 streamed total populations, the collision reads them again and
+    writes 19."""
+    e = ELEM[prec]
+    return {"collide": 38 * e, "phi": 19 * e}.get(stage, 0)
+
+
+def design_bytes_per_node(stage, prec):
+    """Every byte a kernel reads or writes per node, each once: populations
+    plus the per-node reals (phi, b, n, |grad phi|, kappa), flags left out.
+    Order parameter: 19 F + phi, b, n of the sources + phi out; gradient pass:
+    phi in, n, |grad phi|, kappa out; collision: 19 F + phi, n, |grad phi|,
+    kappa in, 19 F + b out."""
+    e, r = ELEM[prec], REAL[prec]
+    return {"phi": 19 * e + 6 * r, "grad_wetting": 6 * r, "collide": 38 * e + 7 * r}.get(stage, 0)
+
+
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture of
+# this workload, keyed to the SHA-256 of the fluid-kernel sources it was taken
+# with: reported only while those sources are unchanged
+NCU_TRAFFIC = {}
+FLUID_SOURCES = ("paper_2505_10171_gb300/csrc/lbm_fluid.cu", "paper_2505_10171_gb300/csrc/lbm_node.cuh",
+                 "paper_2505_10171_gb300/csrc/lbm_internal.cuh")
+
+
+def fluid_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in FLUID_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(stage, prec):
+    v = NCU_TRAFFIC.get((stage, prec))
+    return v[0] if v and v[1] == fluid_source_hash() else None
 
 
 def measured_peaks():
@@ -209,7 +239,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=300)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "mixed", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16", "fp64"], default="fp32")
     ap.add_argument("--no-extra", action="store_true", help="skip the 16-bit and batched extra measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline sample")
     args = ap.parse_args()
@@ -274,13 +304,17 @@ def main():
     peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
     dom = max(prof, key=lambda k: prof[k]["ms"])
     dom_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
-    dom_bytes = algorithmic_bytes_per_node(dom, args.precision) * N
+    dom_bytes = population_bytes_per_node(dom, args.precision) * N
+    dom_design = design_bytes_per_node(dom, args.precision) * N
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes else None
-    step_bytes = 38 * sum(ELEM[args.precision]) * N
+    step_bytes = method_bytes_per_lu(args.precision) * N
+    design_step = sum(design_bytes_per_node(k, args.precision) for k in ("phi", "grad_wetting", "collide"))
     roofline = dict(bound="hbm", kernel=dom, achieved=achieved, peak=hbm, unit="GB/s",
                     frac=(achieved / hbm) if achieved else None,
-                    traffic=NCU_TRAFFIC.get((dom, args.precision)), peak_source=peak_src,
-                    algorithmic_bytes_per_launch=dom_bytes, avg_launch_ms=dom_ms)
+                    traffic=ncu_traffic(dom, args.precision), peak_source=peak_src,
+                    algorithmic_bytes_per_launch=dom_bytes, avg_launch_ms=dom_ms,
+                    design_bytes_per_launch=dom_design,
+                    design_frac=dom_design / (dom_ms * 1e-3) / 1e9 / hbm)
     stage_ms = {k: round(v["ms"] / max(1, v["launches"]), 5) for k, v in prof.items() if v["launches"]}
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -290,6 +324,9 @@ def main():
                             l2="inputs larger than L2 (populations %.0f MB)" % (2 * step_bytes / 2 / 1e6)),
                 roofline=roofline,
                 step_roofline_frac=(value * 1e6 * step_bytes / N) / (hbm * 1e9),
+                bytes_per_lu=dict(method=method_bytes_per_lu(args.precision), moved=design_step,
+                                  note="method: read + write of 38 populations; moved: every population and "
+                                       "per-node field byte the fluid kernels read or write once"),
                 stage_ms_per_launch=stage_ms,
                 value_profiled=world * N * args.steps / (ms_prof * 1e-3) / 1e6,
                 gpu_launches=launches, clocks=clk, mass=dict(rho_a=diag[0], rho_b=diag[1]))
@@ -332,10 +369,10 @@ def e2e_measure(torch, lbm, W, args, stream):
 
 
 def extra_measure(torch, lbm, W, args, stream, N):
-    """FP16/BF16/mixed offset storage on the same workload, and the batched sweep."""
+    """FP16/BF16 offset storage on the same workload, and the batched sweep."""
     out = {}
     K = max(50, args.steps // 4)
-    for prec in ("fp16", "bf16", "mixed"):
+    for prec in ("fp16", "bf16"):
         w = W.cfg2()
         ctx = build_context(lbm, w, prec, stream.cuda_stream)
         ctx.lbm_init_fields(w["phi"])
@@ -346,11 +383,11 @@ def extra_measure(torch, lbm, W, args, stream, N):
         col = prof["collide"]
         cms = col["ms"] / max(1, col["launches"])
         out[prec] = dict(value=N * K / (ms_g * 1e-3) / 1e6, value_profiled=N * K / (ms * 1e-3) / 1e6,
-                         collide_ms=cms, collide_gbs=algorithmic_bytes_per_node("collide", prec) * N / (cms * 1e-3) / 1e9,
+                         collide_ms=cms, collide_gbs=design_bytes_per_node("collide", prec) * N / (cms * 1e-3) / 1e9,
                          steps=K)
     ws = W.cfg4()
     params = [dict(w["params"], store_velocity=0) for w in ws]
-    for prec in ("fp16", "mixed"):
+    for prec in ("fp16",):
         ctx = lbm.Context(params, prec, stream=stream.cuda_stream)
         nodes = 0
         for k, w in enumerate(ws):
@@ -390,7 +427,7 @@ def error_measure(lbm, W, stream):
 
     f0, o0, F0 = run("fp64")
     out = dict(reference="fp64 path, 48x32x32 drop + sphere, 200 steps", bar={"fp32": 1e-4, "reduced": 2e-3})
-    for prec in ("fp32", "mixed", "fp16", "bf16"):
+    for prec in ("fp32", "fp16", "bf16"):
         f, o, F = run(prec)
         fl = (o0 == 0) & (o == 0)
         out[prec] = dict(rho=rl2((f["rho_a"] + f["rho_b"])[fl], (f0["rho_a"] + f0["rho_b"])[fl]),

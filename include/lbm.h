@@ -62,20 +62,21 @@ typedef enum {
     LBM_ERR_UNSUPPORTED = 7  /* feature or precision not available              */
 } lbm_status;
 
-/* Population storage.  FP64 and FP32 store f_i/(w_i rho0) - 1 and
- * (f^a_i - f^b_i)/(w_i rho0); the 16-bit forms store the same offsets in
- * half or bfloat16 with FP32 collision arithmetic.  The mixed form stores the
- * total offsets in half and the colour offsets in FP32 (114 bytes per node
- * and copy instead of 152): the order parameter, whose rounding noise the
- * interface forces amplify into the velocity, keeps FP32 accuracy.  It runs
- * the plain launch form only.  Particle
- * sums, the DEM and mass sums are FP64 in every form. */
+/* Population storage.  Every form stores the total populations as offsets
+ * F_i = f_i/(w_i rho0) - 1: FP64, FP32, or half / bfloat16 with FP32
+ * arithmetic.  The colour populations are not stored: after the recolouring
+ * step of Sec. IV a node's colour offsets are
+ * (f^a_i - f^b_i)/(w_i rho0) = phi (1 + F_i) + b (c_i . n)/|c_i|,
+ * b = beta/2 (rho/rho0)(1 - phi^2), with the order parameter phi and the
+ * interface normal n of that node's collision, so the state keeps phi, b and
+ * n per node (FP64 in the FP64 form, FP32 otherwise) and every colour
+ * population is rebuilt from them.  Particle sums, the DEM and mass sums are
+ * FP64 in every form. */
 typedef enum {
     LBM_FP64 = 0,
     LBM_FP32 = 1,
     LBM_FP16_OFFSET = 2,
-    LBM_BF16_OFFSET = 3,
-    LBM_F16_F32_OFFSET = 4
+    LBM_BF16_OFFSET = 3
 } lbm_precision;
 
 /* Physical parameters of one instance (lattice units, dt = dx = 1).
@@ -86,13 +87,13 @@ typedef struct {
     int wall_z0;               /* 1: node plane z = 0 is the substrate; its halfway wall  */
                                /*    sits at z = 0.5 (and z = nz - 0.5 through periodicity) */
     double wall_velocity[3];   /* substrate velocity (moving-wall bounce-back, Sec. V A)  */
-    double theta_wall_deg;     /* substrate contact angle, measured in phase a (Sec. V D) */
+    double theta_wall_deg;     /* substrate contact angle, measured in phase a (Sec. V E) */
     double rho0;               /* reference density                                       */
     double nu_a, nu_b;         /* kinematic viscosities; eta = rho0 nu, harmonic mean     */
                                /*    in phi (Sec. IV); must be > 0                         */
     double sigma;              /* interfacial tension (CSF force, Sec. IV)                */
     double beta;               /* recolouring segregation parameter in [0, 1] (Sec. IV)   */
-    double cap_norm;           /* capillary prefactor C of Sec. V E; 0 selects 3 k beta,    */
+    double cap_norm;           /* capillary prefactor C of Sec. V F; 0 selects 3 k beta,    */
                                /*    k = (1 + sqrt 2)/18 (the printed (9/2) k beta = 1.5x)   */
                                /*    with k = (1 + sqrt 2)/18                               */
     double body_force_a[3];    /* force density on phase a, weighted by (1 + phi)/2       */
@@ -100,7 +101,7 @@ typedef struct {
     double kn, kt, kr;         /* DEM normal / sliding / rolling stiffness (Sec. III)     */
     double gn, gt, gr;         /* DEM damping constants                                   */
     double mu_s, mu_r;         /* sliding and rolling friction coefficients               */
-    double delta_R;            /* mechanical minus hydrodynamic radius (Sec. V G)         */
+    double delta_R;            /* mechanical minus hydrodynamic radius (Sec. V H)         */
     double g_particle[3];      /* external force on every particle (gravity, Sec. VI A)   */
     double grad_eps;           /* eps of the interface normal g/sqrt(|g|^2 + eps^2),       */
                                /*    g = grad phi; 0 selects 1e-4                          */
@@ -144,7 +145,7 @@ enum {
 
 /* Number of doubles lbm_particle_forces writes per particle:
  * F_eta[3] T_eta[3] (momentum exchange, Sec. V B), F_sigma[3] T_sigma[3]
- * (capillary, Sec. V E), F_c[3] T_c[3] (contact, Sec. III), x[3] v[3] w[3],
+ * (capillary, Sec. V F), F_c[3] T_c[3] (contact, Sec. III), x[3] v[3] w[3],
  * orientation quaternion q[4] (w, x, y, z), m. */
 #define LBM_PARTICLE_RECORD 32
 
@@ -171,7 +172,12 @@ lbm_status lbm_set_solid_mask(lbm_ctx *ctx, int inst, const uint8_t *mask);
 /* Initialise the populations of an instance to the equilibrium (Sec. V C
  * form) of the given host fields: phi [N], rho [N] (NULL: rho0), u [3][N]
  * (NULL: at rest); rho^{a,b} = rho (1 +- phi)/2.  When pops is non-NULL it
- * holds f^a then f^b ([38][N], LBM_C order) and is stored instead (resume).
+ * holds f^a then f^b ([38][N], LBM_C order) and is stored instead (resume):
+ * the total offsets as given, phi = (rho^a - rho^b)/rho, and b n from the
+ * colour part beyond phi (1 + F_i) projected on (c_i . n)/|c_i|
+ * (b n = 9/2 sum_i w_i c_i/|c_i| [G_i - phi (1 + F_i)]).  A state that
+ * lbm_read_fields returned is restored exactly (to rounding); colour
+ * populations of any other form keep only that projection.
  * Host buffers; synchronous. */
 lbm_status lbm_init_fields(lbm_ctx *ctx, int inst, const double *phi, const double *rho,
                            const double *u, const double *pops);
@@ -184,7 +190,7 @@ lbm_status lbm_init_fields_device(lbm_ctx *ctx, int inst, const double *phi, con
 /* Add n spheres to an instance (Sec. III, V).  Checks (-> LBM_ERR_ARG):
  * R_p > 0, rho_p > 0, 0 < theta < 180, hydrodynamic spheres clear of each
  * other and of the substrate, gamma_n < 2 sqrt(k_n m) and a collision time
- * t_c >= 10 (Sec. V G), at most LBM_MAX_PARTICLES per instance.  Only before
+ * t_c >= 10 (Sec. V H), at most LBM_MAX_PARTICLES per instance.  Only before
  * the first lbm_step (-> LBM_ERR_STATE). */
 lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *parts);
 
@@ -229,48 +235,27 @@ long long lbm_num_nodes(const lbm_ctx *ctx, int inst);
  * taken so far, out[3] = sticky device status bits.  Synchronises. */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
 
-/* Launch-shape override of the persistent kernels of the staged form: at most
- * ctas_per_sm CTAs (of 256 threads) per SM, in [1, 8]; 0 (default) fills every
- * SM to the occupancy each kernel allows.  Out of range -> LBM_ERR_ARG.
- * Invalidates the captured step graph. */
-lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm);
-
-/* Fluid-update launch form (all forms compute the same update).
- * form = 2 (default), plain: five kernels per step (order parameter, solid
- *   phi, gradient + wetting + normal, curvature, collision), direct loads.
- *   tile 0: with 16-bit total offsets (FP16, BF16, mixed) and an even nx in
- *   every instance the bulk order-parameter and collision kernels take two
- *   nodes of a row per thread (pair loads and stores), one node per thread
- *   otherwise; tile 1: one node per thread always.
- * form = 0, staged: the same five kernels, but the two that stream the
- *   populations are persistent and bring each strip of x-rows into a ring of
- *   shared-memory stages with asynchronous copies.  tile selects the variant:
- *   0 16-byte cp.async copies by all threads, two CTAs per SM; 1 bulk copies
- *   (cp.async.bulk) completing on mbarriers, two CTAs per SM; 2 as 0 with one
- *   CTA per SM and a deeper ring.  Needs nx * (bytes per stored population)
- *   to be a multiple of 16 in every instance; otherwise the plain form runs.
- * form = 1, fused: one z-marching kernel per step; tile selects its column
- *   tile (0: 16x16, 1: 32x8); zchunk is the number of z-planes per work item
- *   (0: automatic, 32).
- * Staged and plain (tile 1) agree bit for bit; fused agrees bit for bit in
- * FP32 and to rounding (FMA contraction) in FP64; the node-pair collision of
- * plain tile 0 agrees with tile 1 to the rounding of the storage type.  Invalid form, tile or zchunk -> LBM_ERR_ARG;
- * a form other than plain with the mixed storage -> LBM_ERR_UNSUPPORTED.
- * Invalidates the step graph. */
+/* Launch variant of the fluid update.  form must be 2 (plain: order
+ * parameter, solid phi, gradient + wetting + normal + curvature, collision,
+ * with the nodes next to a solid in boundary passes beside the bulk kernels).
+ * tile 0 (default): with 16-bit storage and an even nx in every instance the
+ * bulk order-parameter and collision kernels take two nodes of a row per
+ * thread (pair loads and stores), one node per thread otherwise; tile 1: one
+ * node per thread always.  zchunk: z-planes per work item of the gradient
+ * pass (0: 16).  Every variant computes the same update; the node-pair
+ * kernels agree with the one-node kernels to the rounding of the storage type
+ * (the code generator may fuse a different set of multiply-adds).  Invalid
+ * form, tile or zchunk -> LBM_ERR_ARG.  Invalidates the step graph. */
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk);
 
-/* Autotuner: steps the simulation `steps` times (>= 2) in each available
- * launch form and variant -- plain; staged tiles 0, 1, 2 (when available);
- * fused tiles 0, 1; plain tile 1 -- timing each with CUDA events on the context stream,
- * and keeps the fastest.  The simulation advances by all the trial steps (every
- * form computes the same update).  *form and *tile receive the choice;
- * ms_per_step (may be NULL) receives 7 times in the order above, -1 for a
- * form that is not available.  Synchronises. */
+/* Autotuner: steps the simulation `steps` times (>= 2) with each bulk-kernel
+ * variant (tile 0, tile 1), timing each with CUDA events on the context
+ * stream, and keeps the fastest.  The simulation advances by all the trial
+ * steps.  *form and *tile receive the choice; ms_per_step (may be NULL)
+ * receives the 2 times.  Synchronises. */
 lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step);
 
-/* The fluid-update form the next step runs: 0 staged, 1 fused, 2 plain (the
- * staged form falls back to plain when an instance's rows are not whole
- * 16-byte units); -1 for a null context. */
+/* The fluid-update form the next step runs (2); -1 for a null context. */
 int lbm_fluid_form_in_use(const lbm_ctx *ctx);
 
 /* Count of kernel launches the last lbm_step call enqueued (graph nodes
@@ -315,7 +300,7 @@ lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out);
 
 /* ---------------------------------------------------------------------------
  * Learned force surrogate (an extension of the method; the paper has none).
- * On a coarse grid the momentum-exchange and capillary forces (Sec. V B, V E)
+ * On a coarse grid the momentum-exchange and capillary forces (Sec. V B, V F)
  * can be replaced by a network evaluated on samples of the flow around each
  * sphere:
  *   inputs (LBM_MLP_INPUTS = 387): at the 96 points of a Fibonacci sphere of

@@ -130,10 +130,10 @@ def make_params(nx, ny, nz, **kw) -> OrParams:
     """OrParams from keyword arguments; unspecified values take DEFAULTS.
 
     ``cap_norm`` defaults to 3 k beta with k = (1+sqrt 2)/18 and the given
-    beta, unless passed explicitly.  Sec. V E prints (9/2) k beta; across a
+    beta, unless passed explicitly.  Sec. V F prints (9/2) k beta; across a
     settled planar interface sum (1 - phi^2) = 1/(3 k beta), so 3 k beta gives
     a line force of sigma per unit contact-line length and (9/2) k beta 1.5
-    sigma, and the detachment benchmark of Sec. V E (Scheludko's maximum force)
+    sigma, and the detachment benchmark of Sec. V G (Scheludko's maximum force)
     is met with 3 k beta.
     """
     v = dict(DEFAULTS)

@@ -164,7 +164,7 @@ typedef struct {
     double R, Rc, m, I, theta;
     double Fp[3], Tp[3];          /* total force/torque of the last DEM step */
     double Feta[3], Teta[3];      /* hydrodynamic, Sec. V B                 */
-    double Fsig[3], Tsig[3];      /* capillary, Sec. V E                    */
+    double Fsig[3], Tsig[3];      /* capillary, Sec. V F                    */
     double Fc[3], Tc[3];          /* contact, Sec. III                      */
     int kin;                      /* prescribed (kinematic) motion          */
 } or_part;
@@ -335,7 +335,7 @@ int or_add_particle(or_sim *s, const double *x, const double *v, const double *w
     for (int a = 0; a < 3; a++) { P->x[a] = x[a]; P->v[a] = v[a]; P->w[a] = w[a]; }
     P->q[0] = 1.0;
     P->R = R;
-    P->Rc = R + s->p.delta_R;                     /* Sec. V G */
+    P->Rc = R + s->p.delta_R;                     /* Sec. V H */
     /* READING c25: m_p from the hydrodynamic radius, I_p of a solid sphere */
     P->m = rho_p * 4.0 / 3.0 * M_PI * R * R * R;
     P->I = 0.4 * P->m * R * R;
@@ -442,7 +442,7 @@ void or_collide_node(const double *fa, const double *fb, const double *F_ext,
         for (int a = 0; a < 3; a++) u_out[a] = u[a];
 }
 
-/* Sec. V D, geometric wetting condition (Xu 2017, Akai 2018).
+/* Sec. V E, geometric wetting condition (Xu 2017, Akai 2018).
  * READING c11: n* = -grad(phi)/|grad(phi)| points out of the phi=+1 phase,
  * theta is measured inside phase a, n_s points out of the solid.  Of the two
  * candidates n_+, n_- the one closer to n* is taken; the gradient keeps its
@@ -522,7 +522,7 @@ static int solid_normal(const or_sim *s, int x, int y, int z, double *ns, double
 }
 
 /* ---------------------------------------------------------------------- */
-/* Sec. V E: capillary force on particle p from the Lagrangian surface     */
+/* Sec. V F: capillary force on particle p from the Lagrangian surface     */
 /* points.  READING c17/c18: dF = C sigma (1-phi^2) dA [n_s - (n.n_s) n],  */
 /* points at alpha_j = (j+1/2) 2deg, varphi_k = k 2deg on r = R_p; phi and */
 /* grad(phi) by trilinear interpolation over fluid corners only.           */
@@ -875,7 +875,7 @@ static void step_once(or_sim *s)
                 s->phi[id] = sw > 0.0 ? sp / sw : 0.0;
             }
     /* (5) READING c5: grad phi = (1/cs2) sum_i w_i c_i phi(x + c_i); then the
-     * Sec. V D wetting rotation at fluid nodes next to a solid inside the
+     * Sec. V E wetting rotation at fluid nodes next to a solid inside the
      * diffuse interface (READING c10: |phi| < wet_phi_max = 0.99). */
 #pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; z++)
@@ -947,7 +947,7 @@ static void step_once(or_sim *s)
                 }
                 for (int a = 0; a < 3; a++) s->u[a * N + id] = uo[a];
             }
-    /* (7) capillary force, Sec. V E */
+    /* (7) capillary force, Sec. V F */
     for (int p = 0; p < s->np; p++) or_capillary(s, p, s->P[p].Fsig, s->P[p].Tsig);
     /* (8) DEM, Sec. III and Eqs. (Newton second law), (Newton - rotation) */
     if (s->np > 0) dem_step(s, 1);

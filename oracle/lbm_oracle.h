@@ -29,7 +29,7 @@ typedef struct {
     double nu_a, nu_b;           /* kinematic viscosities of phases a, b   */
     double sigma;                /* interfacial tension                    */
     double beta;                 /* recolouring segregation parameter      */
-    double cap_norm;             /* capillary-force prefactor C (Sec. V E) */
+    double cap_norm;             /* capillary-force prefactor C (Sec. V F) */
     double body_force_a[3];      /* force density on phase a               */
     double body_force_b[3];      /* force density on phase b               */
     double kn, kt, kr;           /* DEM spring stiffnesses                 */

@@ -21,13 +21,15 @@ struct lbm_ctx {
     std::vector<InstDev> inst_h;
     InstDev *inst_d = nullptr;
     long long Ntot = 0;
-    int cta_cap = 0;  // CTAs per SM of the persistent staged kernels at most (0: occupancy)
     size_t elem = 8, real_sz = 8;
-    size_t pop_node_bytes = 0;  // population bytes per node (both halves)
+    size_t pop_node_bytes = 0;  // population bytes per node
     size_t pop_bytes = 0;       // bytes of one population buffer (all instances)
     uint8_t *flags = nullptr;
     void *pop[2] = {nullptr, nullptr};
-    void *phi = nullptr, *grad = nullptr, *gmag = nullptr, *kap = nullptr, *u = nullptr;
+    // phis[k]: the order parameter of the state in pop[k] (the step that writes
+    // pop[k] computes it); rec: recolouring amplitude b of the current state
+    void *phis[2] = {nullptr, nullptr}, *rec = nullptr;
+    void *grad = nullptr, *gmag = nullptr, *kap = nullptr, *u = nullptr;
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
     double *mem_part = nullptr, *cap_part = nullptr, *hist = nullptr;
@@ -58,9 +60,9 @@ struct lbm_ctx {
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pairs;
     cudaEvent_t ev_open[N_STAGES] = {};
-    // fluid launch form: plain (default), staged or fused z-marching
-    FluidLaunch fz = {FORM_PLAIN, 0, 0, 0, 0, 0, {0, 0, 0}, {0, 0, 0}, false};
-    int zc_request = 0;  // z-planes per fused work item, 0: automatic
+    // launch variant of the fluid update
+    FluidLaunch fz = {0, 0, 0, false};
+    int zc_request = 0;  // z-planes per gradient work item, 0: automatic
     // drop-speed control: per instance integral (3) and last U_a (3); block partials
     double *speed_d = nullptr;
     double *speed_part = nullptr;
@@ -80,42 +82,19 @@ struct lbm_ctx {
     size_t tr_cap = 0;
 };
 
-static void dispatch_grids(lbm_ctx *c);
-
-// work items of the fused kernel: column tiles x z-chunks, per instance
-static void plan_fused(lbm_ctx *c)
-{
-    const int TX = fused_tile_x(c->fz.tile), TY = fused_tile_y(c->fz.tile);
-    long long items = 0;
-    for (auto &I : c->inst_h) {
-        I.tiles_x = (I.nx + TX - 1) / TX;
-        I.tiles_y = (I.ny + TY - 1) / TY;
-        int zc = c->zc_request > 0 ? c->zc_request : 32;
-        if (zc > I.nz) zc = I.nz;
-        I.nchunks = (I.nz + zc - 1) / zc;
-        I.zc = (I.nz + I.nchunks - 1) / I.nchunks;
-        I.item_start = items;
-        items += (long long)I.tiles_x * I.tiles_y * I.nchunks;
-    }
-    c->fz.items = items;
-}
-
-// work items and persistent grids of the staged kernels
+// work items of the bulk kernels and of the gradient pass; node pairs (tile 0)
+// when every row has an even length
 static void plan_launch(lbm_ctx *c)
 {
-    plan_fused(c);
-    c->fz.gc_items = plan_gradcurv(c->inst_h);
-    const bool aligned = plan_rows(c->inst_h, c->elem, &c->fz.rows);
-    c->fz.st_items = aligned && c->prec != LBM_F16_F32_OFFSET ? c->fz.rows : 0;
-    // node-pair bulk collision (plain form, tile 0) when every row has an even length
+    c->fz.gc_items = plan_gradcurv(c->inst_h, c->zc_request);
+    c->fz.rows = plan_rows(c->inst_h);
     bool even = true;
     for (const auto &I : c->inst_h) even = even && I.nx % 2 == 0;
-    c->fz.pair = even && c->fz.form == FORM_PLAIN && c->fz.tile == 0;
-    dispatch_grids(c);
+    c->fz.pair = even && c->fz.tile == 0;
 }
 
 static const int DIAG_BLOCKS = 512;
-// bytes after the last flag: the staged kernels copy flags in whole 16-byte units
+// bytes after the last flag (zeroed)
 static const size_t FLAG_PAD = 64;
 
 static lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m)
@@ -132,6 +111,9 @@ static lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m)
                         std::string(#call) + ": " + cudaGetErrorString(e_));                          \
     } while (0)
 
+// the lattice view outside a step: phi is the order parameter of the current
+// state (the one its last step computed); enqueue_step points phi at the other
+// buffer, which the step writes
 static Lattice make_lattice(const lbm_ctx *c)
 {
     Lattice L;
@@ -145,7 +127,9 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.flags = c->flags;
     L.pop[0] = c->pop[0];
     L.pop[1] = c->pop[1];
-    L.phi = c->phi;
+    L.phi = c->phis[c->cur];
+    L.phi_src = c->phis[c->cur];
+    L.rec = c->rec;
     L.grad = c->grad;
     L.gmag = c->gmag;
     L.kap = c->kap;
@@ -184,6 +168,32 @@ static AbiMap abi_map()
     return m;
 }
 
+// the state of node n as populations: rho/rho0 and phi, and the colour
+// offsets G*_i = phi (1 + F*_i) + b (c_i . n)/|c_i| of the recolouring step
+template <class S>
+struct NodeState {
+    using R = typename Store<S>::real;
+    const Pop<S> &pop;
+    const Colour<R> &C;
+    int n;
+    __device__ double F(int i) const { return (double)pop.F(i, n); }
+    __device__ double G(int i) const
+    {
+        return (double)C.ph[n] * (1.0 + F(i)) + (i ? (double)C.rec(i, n) : 0.0);
+    }
+    __device__ double rr() const
+    {
+        double s = 0.0;
+        for (int i = 0; i < Q; i++) s += wgt<double>(i) * F(i);
+        return 1.0 + s;
+    }
+};
+
+// initial state: from phi, rho, u as f^{a,b} = feq(rho (1 +- phi)/2, u) (b = 0),
+// or from given populations (resume).  Given populations are stored as F*,
+// phi = (rho^a - rho^b)/rho and the part of the colour offsets beyond
+// phi (1 + F*): b n = 9/2 sum_i w_i (c_i/|c_i|) [G_i - phi (1 + F_i)], exact for a
+// state of the recoloured form (as lbm_read_fields returns it).
 template <class S>
 __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const double *rho, const double *u,
                        const double *pops, AbiMap map)
@@ -192,18 +202,38 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
+    R *ph = (R *)L.phi_src + I.node_off, *B = (R *)L.rec + I.node_off, *Nn = (R *)L.grad + I.node_off;
+    const long long Nt = L.Ntot;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if (pops) {
+            double F[Q], G[Q], sF = 0.0, sG = 0.0;
             for (int a = 0; a < Q; a++) {
-                int i = map.dev[a];
-                double w = wgt<double>(i) * I.rho0;
-                double fa = pops[(long long)a * N + n], fb = pops[(long long)(Q + a) * N + n];
-                pop.setF(i, (int)n, (R)((fa + fb) / w - 1.0));
-                pop.setG(i, (int)n, (R)((fa - fb) / w));
+                const int i = map.dev[a];
+                const double w = wgt<double>(i) * I.rho0;
+                const double fa = pops[(long long)a * N + n], fb = pops[(long long)(Q + a) * N + n];
+                F[i] = (fa + fb) / w - 1.0;
+                G[i] = (fa - fb) / w;
+                sF += wgt<double>(i) * F[i];
+                sG += wgt<double>(i) * G[i];
             }
+            const double p = 1.0 + sF != 0.0 ? sG / (1.0 + sF) : 0.0;
+            double a3[3] = {0.0, 0.0, 0.0};
+            for (int i = 1; i < Q; i++) {
+                const double il = csq(i) == 1 ? 1.0 : 0.70710678118654752440;
+                const double r = G[i] - p * (1.0 + F[i]);
+                a3[0] += wgt<double>(i) * cx(i) * il * r;
+                a3[1] += wgt<double>(i) * cy(i) * il * r;
+                a3[2] += wgt<double>(i) * cz(i) * il * r;
+            }
+            for (int k = 0; k < 3; k++) a3[k] *= 4.5;
+            const double am = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
+            for (int i = 0; i < Q; i++) pop.setF(i, (int)n, (R)F[i]);
+            ph[n] = (R)p;
+            B[n] = (R)am;
+            for (int k = 0; k < 3; k++) Nn[k * Nt + n] = am > 0.0 ? (R)(a3[k] / am) : R(0);
             continue;
         }
-        double ph = phi[n];
+        double p = phi[n];
         double r = rho ? rho[n] : I.rho0;
         double uu[3] = {u ? u[n] : 0.0, u ? u[N + n] : 0.0, u ? u[2 * N + n] : 0.0};
         double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
@@ -213,8 +243,10 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
             double e = 1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq;
             // f^{a,b} = feq(rho (1 +- phi)/2, u): total rho e w, colour rho phi e w
             pop.setF(i, (int)n, (R)(rr * e - 1.0));
-            pop.setG(i, (int)n, (R)(rr * ph * e));
         }
+        ph[n] = (R)p;
+        B[n] = R(0);
+        for (int k = 0; k < 3; k++) Nn[k * Nt + n] = R(0);
         if (I.store_u) {
             R *U = (R *)L.u;
             bool fl = (L.flags[I.node_off + n] & OWNER_MASK) == OWN_FLUID;
@@ -230,15 +262,15 @@ __global__ void k_read(Lattice L, int cur, int inst, unsigned mask, double *out,
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
+    const Colour<R> C(L, I);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         const uint8_t f = L.flags[I.node_off + n];
         const bool fluid = (f & OWNER_MASK) == OWN_FLUID;
+        const NodeState<S> ns{pop, C, (int)n};
         double ra = 0.0, rb = 0.0;
         if (fluid)
             for (int i = 0; i < Q; i++) {
-                double w = wgt<double>(i) * I.rho0;
-                double Fv = (double)pop.F(i, (int)n);
-                double Gv = (double)pop.G(i, (int)n);
+                const double w = wgt<double>(i) * I.rho0, Fv = ns.F(i), Gv = ns.G(i);
                 ra += 0.5 * w * (1.0 + Fv + Gv);
                 rb += 0.5 * w * (1.0 + Fv - Gv);
             }
@@ -253,10 +285,9 @@ __global__ void k_read(Lattice L, int cur, int inst, unsigned mask, double *out,
         }
         if (mask & LBM_FIELD_POPS) {
             for (int a = 0; a < Q; a++) {
-                int i = map.dev[a];
-                double w = wgt<double>(i) * I.rho0;
-                double Fv = fluid ? (double)pop.F(i, (int)n) : 0.0;
-                double Gv = fluid ? (double)pop.G(i, (int)n) : 0.0;
+                const int i = map.dev[a];
+                const double w = wgt<double>(i) * I.rho0;
+                const double Fv = fluid ? ns.F(i) : 0.0, Gv = fluid ? ns.G(i) : 0.0;
                 out[off + (long long)a * N + n] = fluid ? 0.5 * w * (1.0 + Fv + Gv) : 0.0;
                 out[off + (long long)(Q + a) * N + n] = fluid ? 0.5 * w * (1.0 + Fv - Gv) : 0.0;
             }
@@ -274,13 +305,13 @@ __global__ void k_mass_partial(Lattice L, int cur, int inst, double *part)
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
+    const Colour<typename Store<S>::real> C(L, I);
     double sa = 0.0, sb = 0.0;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
+        const NodeState<S> ns{pop, C, (int)n};
         for (int i = 0; i < Q; i++) {
-            double w = wgt<double>(i) * I.rho0;
-            double Fv = (double)pop.F(i, (int)n);
-            double Gv = (double)pop.G(i, (int)n);
+            const double w = wgt<double>(i) * I.rho0, Fv = ns.F(i), Gv = ns.G(i);
             sa += 0.5 * w * (1.0 + Fv + Gv);
             sb += 0.5 * w * (1.0 + Fv - Gv);
         }
@@ -321,15 +352,17 @@ __global__ void k_speed_partial(Lattice L, int cur, int inst, double *part)
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
+    const Colour<typename Store<S>::real> C(L, I);
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
+        const NodeState<S> ns{pop, C, (int)n};
         double sF = 0.0, sG = 0.0, j[3] = {0.0, 0.0, 0.0};
         for (int i = 0; i < Q; i++) {
             const double w = wgt<double>(i);
-            const double Fv = (double)pop.F(i, (int)n);
+            const double Fv = ns.F(i);
             sF += w * Fv;
-            sG += w * (double)pop.G(i, (int)n);
+            sG += w * ns.G(i);
             j[0] += w * cx(i) * Fv;
             j[1] += w * cy(i) * Fv;
             j[2] += w * cz(i) * Fv;
@@ -409,16 +442,7 @@ static void dispatch(lbm_precision p, F &&f)
     case LBM_FP32: f((float *)nullptr); break;
     case LBM_FP16_OFFSET: f((__half *)nullptr); break;
     case LBM_BF16_OFFSET: f((__nv_bfloat16 *)nullptr); break;
-    case LBM_F16_F32_OFFSET: f((MixedF16F32 *)nullptr); break;
     }
-}
-
-static void dispatch_grids(lbm_ctx *c)
-{
-    dispatch(c->prec, [&](auto *tag) {
-        using S = std::remove_pointer_t<decltype(tag)>;
-        if constexpr (!is_mixed<S>) staged_grids<S>(c->fz.st_grid_phi, c->fz.st_grid_collide, c->cta_cap);
-    });
 }
 
 static cudaEvent_t next_event(lbm_ctx *c)
@@ -444,6 +468,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
 {
     Lattice L = make_lattice(c);
     const int cur = c->cur;
+    L.phi = c->phis[cur ^ 1];  // the order parameter this step computes (that of the next state)
     Marker mk;
     if (c->profile) {
         mk.fn = profile_mark;
@@ -456,7 +481,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
         // only the step's input populations (the fluid kernels write the other
         // buffer), the capillary force only phi, n and |grad phi| once the
         // gradient pass is done.  Profiling keeps one stream (per-kernel events).
-        const bool fork = !sur && !c->profile && L.n_parts > 0 && c->fz.form != FORM_FUSED;
+        const bool fork = !sur && !c->profile && L.n_parts > 0;
         bool owner_done = false;  // owners updated on the side stream
         if (fork) {
             cudaEventRecord(c->ev_fork, c->stream);
@@ -496,16 +521,9 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
                 if (!q->c->u) launch_geom_owner(*q->L, q->c->side, q->launches, *q->mk);
                 cudaEventRecord(q->c->ev_join, q->c->side);
             };
-            const bool plain = c->fz.form == FORM_PLAIN || c->fz.st_items == 0;
-            owner_done = plain && !c->u;
+            owner_done = !c->u;
             launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz, hook, lane);
-            if (!plain) {
-                // staged form: no boundary passes on the side lane; DEM after the join
-                cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-                launch_dem<S>(L, c->stream, launches, mk, true);
-            } else {
-                cudaStreamWaitEvent(c->stream, c->ev_join, 0);
-            }
+            cudaStreamWaitEvent(c->stream, c->ev_join, 0);
         } else {
             launch_fluid_step<S>(L, cur, c->stream, launches, mk, c->fz);
             if (sur) launch_surrogate_forces<S>(L, c->mlp, c->feat, c->stream, launches, mk);
@@ -646,7 +664,9 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->flags);
     cudaFree(ctx->pop[0]);
     cudaFree(ctx->pop[1]);
-    cudaFree(ctx->phi);
+    cudaFree(ctx->phis[0]);
+    cudaFree(ctx->phis[1]);
+    cudaFree(ctx->rec);
     cudaFree(ctx->grad);
     cudaFree(ctx->gmag);
     cudaFree(ctx->kap);
@@ -685,12 +705,12 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
     if (!params || n_instances < 1) return LBM_ERR_ARG;
-    if (prec < LBM_FP64 || prec > LBM_F16_F32_OFFSET) return LBM_ERR_UNSUPPORTED;
+    if (prec < LBM_FP64 || prec > LBM_BF16_OFFSET) return LBM_ERR_UNSUPPORTED;
     lbm_ctx *ctx = new lbm_ctx();
     ctx->prec = prec;
     ctx->n_inst = n_instances;
     ctx->P.assign(params, params + n_instances);
-    ctx->elem = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 || prec == LBM_F16_F32_OFFSET ? 4 : 2);
+    ctx->elem = prec == LBM_FP64 ? 8 : (prec == LBM_FP32 ? 4 : 2);
     dispatch(prec, [&](auto *tag) {
         using S = std::remove_pointer_t<decltype(tag)>;
         ctx->pop_node_bytes = Pop<S>::node_bytes;
@@ -714,9 +734,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.nx = p.nx; I.ny = p.ny; I.nz = p.nz;
         I.N = (long long)p.nx * p.ny * p.nz;
         I.node_off = node_off;
-        // mixed form: stride padded to 8 nodes keeps both halves of every
-        // instance block 16-byte aligned; the other forms keep stride N
-        I.pstride = (int)(prec == LBM_F16_F32_OFFSET ? (I.N + 7) / 8 * 8 : I.N);
+        I.pstride = (int)I.N;
         I.pop_off = pop_off;
         pop_off += (long long)I.pstride * (long long)ctx->pop_node_bytes;
         I.wall_z0 = p.wall_z0;
@@ -727,7 +745,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.beta = p.beta;
         // default capillary prefactor C = 3 k beta, k = (1 + sqrt 2)/18: the
         // settled planar profile has sum (1 - phi^2) = 1/(3 k beta) across the
-        // interface, so a contact line of length L carries sigma L (Sec. V E;
+        // interface, so a contact line of length L carries sigma L (Sec. V F;
         // the printed (9/2) k beta gives 1.5 sigma L and overshoots the
         // detachment benchmark's closed form by the same factor)
         I.cap_norm = p.cap_norm > 0.0 ? p.cap_norm : 3.0 * (1.0 + std::sqrt(2.0)) / 18.0 * p.beta;
@@ -810,7 +828,8 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     const size_t Nt = (size_t)ctx->Ntot;
     if ((st = alloc((void **)&ctx->inst_d, sizeof(InstDev) * n_instances)) ||
         (st = alloc((void **)&ctx->flags, Nt + FLAG_PAD)) || (st = alloc(&ctx->pop[0], ctx->pop_bytes)) ||
-        (st = alloc(&ctx->pop[1], ctx->pop_bytes)) || (st = alloc(&ctx->phi, Nt * ctx->real_sz)) ||
+        (st = alloc(&ctx->pop[1], ctx->pop_bytes)) || (st = alloc(&ctx->phis[0], Nt * ctx->real_sz)) ||
+        (st = alloc(&ctx->phis[1], Nt * ctx->real_sz)) || (st = alloc(&ctx->rec, Nt * ctx->real_sz)) ||
         (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc(&ctx->gmag, Nt * ctx->real_sz)) || (st = alloc(&ctx->kap, Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
         (st = alloc((void **)&ctx->diag_d, sizeof(double) * 2 * n_instances)) ||
         (st = alloc((void **)&ctx->diag_part, sizeof(double) * 2 * DIAG_BLOCKS)) ||
@@ -821,7 +840,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         lbm_destroy(ctx);
         return st;
     }
-    // Sec. V E surface points alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg:
+    // Sec. V F surface points alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg:
     // unit normal and sin(alpha), evaluated once on the host
     {
         std::vector<double> tab(4 * (size_t)CAP_POINTS);
@@ -843,7 +862,9 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     }
     cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * n_instances, cudaMemcpyHostToDevice, ctx->stream);
     cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream);
-    cudaMemsetAsync(ctx->phi, 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->phis[0], 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->phis[1], 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->rec, 0, Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->grad, 0, 3 * Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->gmag, 0, Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->kap, 0, Nt * ctx->real_sz, ctx->stream);
@@ -1021,7 +1042,7 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
         d.R2lo = (float)(q.R_p * q.R_p - 0.05);
         d.R2hi = (float)(q.R_p * q.R_p + 0.05);
         d.local = I.np + k;
-        // Sec. V G: gamma_n < 2 sqrt(k_n m) and a resolved collision time
+        // Sec. V H: gamma_n < 2 sqrt(k_n m) and a resolved collision time
         if (!d.kin) {
             if (!(p.gn < 2.0 * std::sqrt(p.kn * d.m)))
                 return fail(ctx, LBM_ERR_ARG, "gamma_n >= 2 sqrt(k_n m): no real collision time");
@@ -1029,7 +1050,7 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
                 double wc = std::sqrt(p.kn / d.m - (p.gn / (2 * d.m)) * (p.gn / (2 * d.m)));
                 double tc = M_PI / wc;
                 if (tc < 10.0) {
-                    snprintf(b, sizeof b, "collision time t_c = %.3g < 10 steps (Sec. V G)", tc);
+                    snprintf(b, sizeof b, "collision time t_c = %.3g < 10 steps (Sec. V H)", tc);
                     return fail(ctx, LBM_ERR_ARG, b);
                 }
             }
@@ -1300,32 +1321,16 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out)
     return LBM_OK;
 }
 
-lbm_status lbm_set_launch(lbm_ctx *ctx, int ctas_per_sm)
-{
-    if (!ctx) return LBM_ERR_ARG;
-    if (ctas_per_sm < 0 || ctas_per_sm > 8) return fail(ctx, LBM_ERR_ARG, "ctas_per_sm must be in [0, 8]");
-    CU(cudaStreamSynchronize(ctx->stream));
-    ctx->cta_cap = ctas_per_sm;
-    dispatch_grids(ctx);
-    drop_graph(ctx);
-    return LBM_OK;
-}
-
 long long lbm_last_launch_count(const lbm_ctx *ctx) { return ctx ? ctx->last_launches : -1; }
 
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
 {
     if (!ctx) return LBM_ERR_ARG;
-    const int max_tile = form == FORM_STAGED ? 2 : 1;
-    if (form < FORM_STAGED || form > FORM_PLAIN || tile < 0 || tile > max_tile || zchunk < 0)
-        return fail(ctx, LBM_ERR_ARG,
-                    "form must be 0 (staged, tile 0..2), 1 (fused, tile 0..1) or 2 (plain, tile 0..1); zchunk >= 0");
-    if (ctx->prec == LBM_F16_F32_OFFSET && form != FORM_PLAIN)
-        return fail(ctx, LBM_ERR_UNSUPPORTED, "the mixed FP16/FP32 storage runs the plain form only");
+    if (form != FORM_PLAIN || tile < 0 || tile > 1 || zchunk < 0)
+        return fail(ctx, LBM_ERR_ARG, "form must be 2, tile 0 or 1, zchunk >= 0");
     CU(cudaStreamSynchronize(ctx->stream));
     // the device table is authoritative (the drop-speed control writes it)
     CU(cudaMemcpy(ctx->inst_h.data(), ctx->inst_d, sizeof(InstDev) * ctx->n_inst, cudaMemcpyDeviceToHost));
-    ctx->fz.form = form;
     ctx->fz.tile = tile;
     ctx->zc_request = zchunk;
     plan_launch(ctx);
@@ -1336,12 +1341,7 @@ lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
     return LBM_OK;
 }
 
-int lbm_fluid_form_in_use(const lbm_ctx *ctx)
-{
-    if (!ctx) return -1;
-    if (ctx->fz.form == FORM_STAGED && ctx->fz.st_items == 0) return FORM_PLAIN;
-    return ctx->fz.form;
-}
+int lbm_fluid_form_in_use(const lbm_ctx *ctx) { return ctx ? FORM_PLAIN : -1; }
 
 lbm_status lbm_profile(lbm_ctx *ctx, int enable)
 {
@@ -1465,7 +1465,7 @@ lbm_status lbm_surrogate_predict(lbm_ctx *ctx, const float *X, size_t n, float *
         lbm_status s = upload_xy(ctx, X + r0 * MLP_NIN, nullptr, nb, &Xd, &Yd);
         if (s != LBM_OK) return s;
         mlp_stage(ctx->mlp, Xd, nullptr, nullptr, 0, nb, ctx->stream);
-        mlp_forward(ctx->mlp, nb, ctx->status, ctx->stream);
+        CU(mlp_forward(ctx->mlp, nb, ctx->status, ctx->stream));
         CU(cudaGetLastError());
         CU(cudaMemcpy2DAsync(Y + r0 * MLP_NOUT, sizeof(float) * MLP_NOUT, ctx->mlp.Y, sizeof(float) * 16,
                              sizeof(float) * MLP_NOUT, nb, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1484,8 +1484,8 @@ lbm_status lbm_surrogate_gradient(lbm_ctx *ctx, const float *X, const float *Y, 
     lbm_status s = upload_xy(ctx, X, Y, n, &Xd, &Yd);
     if (s != LBM_OK) return s;
     mlp_stage(ctx->mlp, Xd, Yd, nullptr, 0, (int)n, ctx->stream);
-    mlp_forward(ctx->mlp, (int)n, ctx->status, ctx->stream);
-    mlp_backward(ctx->mlp, (int)n, nullptr, ctx->status, ctx->stream);
+    CU(mlp_forward(ctx->mlp, (int)n, ctx->status, ctx->stream));
+    CU(mlp_backward(ctx->mlp, (int)n, nullptr, ctx->status, ctx->stream));
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(grad, ctx->mlp.grad, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, ctx->stream));
     double l = 0.0;
@@ -1543,8 +1543,8 @@ lbm_status lbm_surrogate_train(lbm_ctx *ctx, const float *X, const float *Y, siz
             const long long r0 = (long long)(b * batch);
             const int sz = (int)std::min<size_t>(batch, n - r0);
             mlp_stage(ctx->mlp, ctx->trX, ctx->trY, ctx->perm, r0, sz, ctx->stream);
-            mlp_forward(ctx->mlp, sz, ctx->status, ctx->stream);
-            mlp_backward(ctx->mlp, sz, ctx->mlp.loss + 1, ctx->status, ctx->stream);
+            CU(mlp_forward(ctx->mlp, sz, ctx->status, ctx->stream));
+            CU(mlp_backward(ctx->mlp, sz, ctx->mlp.loss + 1, ctx->status, ctx->stream));
             mlp_adam(ctx->mlp, lr, ctx->stream);
         }
         CU(cudaGetLastError());
@@ -1598,20 +1598,17 @@ lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out)
 lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step)
 {
     if (!ctx || !form || !tile || steps < 2) return fail(ctx, LBM_ERR_ARG, "autotune needs steps >= 2 and outputs");
-    const int cand[7][2] = {{FORM_PLAIN, 0}, {FORM_STAGED, 0}, {FORM_STAGED, 1}, {FORM_STAGED, 2}, {FORM_FUSED, 0},
-                            {FORM_FUSED, 1}, {FORM_PLAIN, 1}};
+    const int ncand = 2;
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     double best = -1.0;
-    int bf = FORM_PLAIN, bt = 0;
+    int bt = 0;
     lbm_status st = LBM_OK;
-    for (int k = 0; k < 7 && st == LBM_OK; k++) {
+    for (int k = 0; k < ncand && st == LBM_OK; k++) {
         if (ms_per_step) ms_per_step[k] = -1.0;
-        if (ctx->prec == LBM_F16_F32_OFFSET && cand[k][0] != FORM_PLAIN) continue;
-        if ((st = lbm_set_fluid_kernel(ctx, cand[k][0], cand[k][1], 0)) != LBM_OK) break;
-        if (lbm_fluid_form_in_use(ctx) != cand[k][0]) continue;  // staged form not available here
-        if ((st = lbm_step(ctx, 2)) != LBM_OK) break;            // capture and warm up
+        if ((st = lbm_set_fluid_kernel(ctx, FORM_PLAIN, k, ctx->zc_request)) != LBM_OK) break;
+        if ((st = lbm_step(ctx, 2)) != LBM_OK) break;  // capture and warm up
         cudaEventRecord(e0, ctx->stream);
         if ((st = lbm_step(ctx, steps)) != LBM_OK) break;
         cudaEventRecord(e1, ctx->stream);
@@ -1625,16 +1622,15 @@ lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *m
         if (ms_per_step) ms_per_step[k] = per;
         if (best < 0.0 || per < best) {
             best = per;
-            bf = cand[k][0];
-            bt = cand[k][1];
+            bt = k;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LBM_OK) return st;
-    *form = bf;
+    *form = FORM_PLAIN;
     *tile = bt;
-    st = lbm_set_fluid_kernel(ctx, bf, bt, 0);
+    st = lbm_set_fluid_kernel(ctx, FORM_PLAIN, bt, ctx->zc_request);
     if (st != LBM_OK) return st;
     return check_status(ctx);
 }

@@ -2,28 +2,22 @@
 //
 // Per node: pull streaming with bounce-back -> order parameter phi -> phi on
 // solid nodes next to fluid (w-weighted fluid mean) -> isotropic grad(phi)
-// with the geometric wetting rotation (Sec. V D) -> regularised normal and its
+// with the geometric wetting rotation (Sec. V E) -> regularised normal and its
 // divergence (curvature) -> CSF + body force -> MRT with Guo forcing, evaluated
 // in its two-relaxation-time form -> recolouring -> write.
 //
-// Three launch forms run the per-node device functions of lbm_node.cuh:
-//  * plain (default): k_phi (one thread per node, stores phi); the solid-phi
-//    fill over the listed static solid nodes and the particle cubes;
-//    k_gradcurv (z-marching tiles: gradient, wetting, normal, curvature);
-//    k_collide (one thread per node).  The collision pulls only the 19 total
-//    offsets F: the colour offsets enter it only through phi, which k_phi
-//    stores.
-//  * staged: k_phi and k_collide replaced by persistent kernels that bring
-//    their inputs into shared memory with asynchronous copies (lbm_staged.cu).
-//  * k_fused: one kernel per step.  A block owns a TX x TY column tile and a
-//    chunk of z-planes and marches z: the order parameter of plane z+3 is
-//    gathered into a shared-memory ring (with a 3-node halo, enough for the
-//    solid-phi fill), solids of plane z+2 are filled, gradient/wetting/normal of
-//    plane z+1 are formed, and plane z is collided.
-// The staged and plain forms agree bit for bit; the fused form agrees bit for
-// bit in FP32 and to rounding in FP64 (contraction into FMA may differ).
-// The particle-region kernels recompute phi and grad(phi) around each particle
-// for the capillary force.
+// Kernels of a step: k_phi (one thread per node, or k_phi2 with a node pair
+// per thread for 16-bit storage) stores phi; the solid-phi fill over the listed
+// static solid nodes and the particle cubes; k_gradcurv (z-marching tiles:
+// gradient, wetting, normal, curvature); k_collide (or k_collide2).  Nodes next
+// to a solid go to the boundary passes k_phi_bound and k_collide_bound, which
+// run beside the bulk kernels on a second stream.
+//
+// The state between steps is the total offsets F* (pop[cur]) with phi (the
+// order parameter its collision used), the recolouring amplitude b and the
+// normal n per node: the order-parameter pass rebuilds each pulled colour
+// offset G_i from its source node (lbm_internal.cuh), the collision needs the
+// colour offsets only through phi.
 // Storage type S in {double, float, __half, __nv_bfloat16}; arithmetic in
 // double for S = double and float otherwise.
 #include "lbm_node.cuh"
@@ -40,7 +34,7 @@
 namespace lbmg {
 
 // ---------------------------------------------------------------------------
-// four-kernel form over all nodes (and the same bodies over particle regions)
+// bulk kernels over all nodes, region kernels over the particle cubes
 // ---------------------------------------------------------------------------
 // region of particle blockIdx.y: nodes of a cube of side `side` around it
 #define LBM_REGION_PROLOGUE                                                                  \
@@ -54,51 +48,45 @@ namespace lbmg {
     reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);                                              \
     const int n = (z * I.ny + y) * I.nx + x;
 
-// order parameter of a fluid node.  full = false (the bulk kernel): the plain
-// pull, for nodes none of whose neighbours is solid; the boundary pass
-// (k_phi_bound) does the others.  Keeping the bounce-back code out of the bulk
-// kernel keeps its loads in flight (with it compiled in, the kernel ran 75%
-// longer).
-template <class S, bool full>
+// order parameter of a fluid node none of whose neighbours is solid; the
+// boundary pass (k_phi_bound) does the others.  Keeping the bounce-back code
+// out of the bulk kernel keeps its loads in flight (with it compiled in, the
+// kernel ran 75% longer).
+template <class S>
 __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
 {
     using R = typename Store<S>::real;
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
     const Pop<S> in(L.pop[cur], I);
+    const Colour<R> C(L, I);
     Nbr nb;
     nb.init(x, y, z, I.nx, I.ny, I.nz);
-    R v = phi_fluid<S>(nb, in);
+    R v = phi_fluid<S>(nb, in, C);
     keep(v);
-    if ((fl & OWNER_MASK) != OWN_FLUID) return;
-    if (fl & BOUND_BIT) {
-        if (!full) return;  // the boundary pass writes this node
-        GlobalNbr gnb;
-        gnb.nb = nb;
-        gnb.fli = L.flags + I.node_off;
-        v = node_phi<S>(I, L.parts, gnb, in, n, fl, x, y, z);
-    }
+    if ((fl & OWNER_MASK) != OWN_FLUID || (fl & BOUND_BIT)) return;
     ((R *)L.phi)[g] = v;
 }
 
 // the order parameter of a node pair (x even, x + 1) per thread, for 16-bit
-// total offsets: pulls along c_x = 0 as one pair load (32-bit, or 64-bit for
-// FP32 colour offsets), the two phi in one pair store; each node's sums are
-// those of phi_fluid
+// storage: pulls along c_x = 0 as one pair load (of the total offsets and of
+// the sources' phi, b and n), the two phi in one pair store; each node's sums
+// are those of phi_fluid
 template <class S>
 __device__ __forceinline__ void phi_body2(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
 {
     using R = typename Store<S>::real;
     using FT = typename Pop<S>::FT;
-    using GT = typename Pop<S>::GT;
     const long long g = I.node_off + n;  // even
     const uint8_t fl0 = L.flags[g], fl1 = L.flags[g + 1];
     const Pop<S> in(L.pop[cur], I);
+    const Colour<R> C(L, I);
     const int N = in.N;
     Nbr nb;
     nb.init(x, y, z, I.nx, I.ny, I.nz);
     const int xp2 = x + 2 == I.nx ? 0 : x + 2;
     R sF0 = 0, sG0 = 0, sF1 = 0, sG1 = 0;
+    // sources of the pair along direction i in the row `row`
     auto pull = [&](auto *row, int i, R &a, R &b) {
         using T = std::remove_cv_t<std::remove_pointer_t<decltype(row)>>;
         if (cx(i) == 0) {
@@ -113,14 +101,25 @@ __device__ __forceinline__ void phi_body2(const Lattice &L, const InstDev &I, in
     };
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const int ro = i * N + nb.ZO[1 - cz(i)] + nb.YO[1 - cy(i)];
-        R F0, F1, G0, G1;
-        pull((const FT *)in.f + ro, i, F0, F1);
-        pull((const GT *)in.g() + ro, i, G0, G1);
+        const int ro = nb.ZO[1 - cz(i)] + nb.YO[1 - cy(i)];
+        R F0, F1, p0, p1;
+        pull((const FT *)in.f + i * N + ro, i, F0, F1);
+        pull(C.ph + ro, i, p0, p1);
+        R g0 = p0 * (R(1) + F0), g1 = p1 * (R(1) + F1);
+        if (i) {
+            R b0, b1, a0, a1, t0 = 0, t1 = 0;
+            pull(C.b + ro, i, b0, b1);
+            if (cx(i)) { pull(C.n + ro, i, a0, a1); t0 += cx(i) * a0; t1 += cx(i) * a1; }
+            if (cy(i)) { pull(C.n + C.Nt + ro, i, a0, a1); t0 += cy(i) * a0; t1 += cy(i) * a1; }
+            if (cz(i)) { pull(C.n + 2 * C.Nt + ro, i, a0, a1); t0 += cz(i) * a0; t1 += cz(i) * a1; }
+            if (csq(i) != 1) { t0 *= R(0.70710678118654752440); t1 *= R(0.70710678118654752440); }
+            g0 += b0 * t0;
+            g1 += b1 * t1;
+        }
         sF0 += wgt<R>(i) * F0;
-        sG0 += wgt<R>(i) * G0;
+        sG0 += wgt<R>(i) * g0;
         sF1 += wgt<R>(i) * F1;
-        sG1 += wgt<R>(i) * G1;
+        sG1 += wgt<R>(i) * g1;
     }
     R v0 = sG0 / (R(1) + sF0), v1 = sG1 / (R(1) + sF1);
     keep(v0);
@@ -147,39 +146,15 @@ __device__ __forceinline__ void solidphi_body(const Lattice &L, const InstDev &I
     ((R *)L.phi)[g] = solid_fill<R>(nb, phi_of);
 }
 
-template <class R>
-__device__ __forceinline__ void grad_body(const Lattice &L, const InstDev &I, int n, int x, int y, int z)
-{
-    const long long g = I.node_off + n;
-    const uint8_t fl = L.flags[g];
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = L.flags + I.node_off;
-    const R *ph = (const R *)L.phi + I.node_off;
-    auto phi_of = [&](int dx, int dy, int dz) { return ph[nb.idx(dx, dy, dz)]; };
-    R gr[3], nn[3];
-    grad_sum<R>(phi_of, gr);  // loads issued before the flag is tested
-    if ((fl & OWNER_MASK) != OWN_FLUID) return;
-    FluidPar<R> P;
-    load_par(I, P);
-    grad_wet<R>(I, L.parts, nb, ph[n], fl, P.wet_max, x, y, z, gr);
-    const R m = reg_normal(gr, P.eps2, nn);
-    R *Nn = (R *)L.grad;
-    Nn[g] = nn[0];
-    Nn[L.Ntot + g] = nn[1];
-    Nn[2 * L.Ntot + g] = nn[2];
-    ((R *)L.gmag)[g] = m;
-}
-
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
 {
     pdl_trigger();  // the gradient pass may be scheduled as this grid drains
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S, false>(L, I, cur, n, x, y, z); });
+    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
 }
 
 #ifndef LBM_PHI2_MINB
-#define LBM_PHI2_MINB 8
+#define LBM_PHI2_MINB 6
 #endif
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES / 2, LBM_PHI2_MINB) k_phi2(Lattice L, int cur)
@@ -293,16 +268,14 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_phi_bound(Lattice L, int cu
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
     const Pop<S> in(L.pop[cur], *I);
+    const Colour<R> C(L, *I);
     GlobalNbr nb;
     nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
     nb.fli = L.flags + I->node_off;
-    R F[Q], G[Q], sF = 0, sG = 0;
-    gather_all<S>(*I, L.parts, nb, in, n, F, G, x, y, z);
+    R F[Q], sF = 0, sG = 0;
+    gather_all<S>(*I, L.parts, nb, in, &C, n, F, &sG, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        sF += wgt<R>(i) * F[i];
-        sG += wgt<R>(i) * G[i];
-    }
+    for (int i = 0; i < Q; i++) sF += wgt<R>(i) * F[i];
     ((R *)L.phi)[g] = sG / (R(1) + sF);
 }
 
@@ -325,21 +298,13 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_collide_bound(Lattice L, in
     nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
     nb.fli = L.flags + I->node_off;
     R F[Q];
-    gather_all<S>(*I, L.parts, nb, in, n, F, (R *)nullptr, x, y, z);
+    gather_all<S>(*I, L.parts, nb, in, (const Colour<R> *)nullptr, n, F, (R *)nullptr, x, y, z);
     FluidPar<R> P;
     load_par(*I, P);
-    const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
     const R m = ((const R *)L.gmag)[g];
-    const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, nn, ((const R *)L.kap)[g], out, n, U, L.Ntot,
-                         L.status);
-}
-
-template <class S>
-__global__ void __launch_bounds__(PART_THREADS) k_phi_region(Lattice L, int cur, int side)
-{
-    LBM_REGION_PROLOGUE
-    phi_body<S, true>(L, I, cur, n, x, y, z);
+    const R gr[3] = {Nn[n] * m, Nn[Nt + n] * m, Nn[2 * Nt + n] * m};
+    collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, ((const R *)L.kap)[g], out, n, (R *)L.rec + g, U,
+                         L.Ntot, L.status);
 }
 
 template <class R>
@@ -347,13 +312,6 @@ __global__ void __launch_bounds__(PART_THREADS) k_solidphi_region(Lattice L, int
 {
     LBM_REGION_PROLOGUE
     solidphi_body<R>(L, I, n, x, y, z);
-}
-
-template <class R>
-__global__ void __launch_bounds__(PART_THREADS) k_grad_region(Lattice L, int side)
-{
-    LBM_REGION_PROLOGUE
-    grad_body<R>(L, I, n, x, y, z);
 }
 
 template <class S>
@@ -388,12 +346,12 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     FluidPar<R> P;
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, U, L.Ntot, L.status);
+    collide_store_phi<S>(P, F, phi, gr, kap, out, n, (R *)L.rec + g, U, L.Ntot, L.status);
 }
 
-// Node pairs (x even, x + 1) of one row per thread, for 16-bit total offsets:
-// the pulls along directions with c_x = 0 are one 32-bit load of the pair,
-// every output a pair store (half2, bfloat162 or float2), which halves the
+// Node pairs (x even, x + 1) of one row per thread, for 16-bit storage: the
+// pulls along directions with c_x = 0 are one 32-bit load of the pair, every
+// output a pair store (half2, bfloat162 or float2), which halves the
 // per-node load, store, conversion and address instructions.  Each node's
 // arithmetic is that of collide_store_phi (the same expressions; the code
 // generator may fuse a different set of multiply-adds, so the results agree
@@ -404,7 +362,6 @@ __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I
 {
     using R = typename Store<S>::real;
     using FT = typename Pop<S>::FT;
-    using GT = typename Pop<S>::GT;
     static_assert(sizeof(FT) == 2 && sizeof(R) == 4, "pair kernel: 16-bit total offsets, FP32 arithmetic");
     const long long g = I.node_off + n;  // even
     const Pop<S> in(L.pop[cur], I);
@@ -451,9 +408,8 @@ __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I
     if (!a0 && !a1) return;
     FluidPar<R> P;
     load_par(I, P);
-    const R nnA[3] = {n0.x, n1.x, n2.x}, nnB[3] = {n0.y, n1.y, n2.y};
-    const R grA[3] = {nnA[0] * mv.x, nnA[1] * mv.x, nnA[2] * mv.x};
-    const R grB[3] = {nnB[0] * mv.y, nnB[1] * mv.y, nnB[2] * mv.y};
+    const R grA[3] = {n0.x * mv.x, n1.x * mv.x, n2.x * mv.x};
+    const R grB[3] = {n0.y * mv.y, n1.y * mv.y, n2.y * mv.y};
     const R phA = pv.x, phB = pv.y;
     const CollideState<R> cA = collide_state(P, F0, phA, grA, kv.x);
     const CollideState<R> cB = collide_state(P, F1, phB, grB, kv.y);
@@ -464,7 +420,6 @@ __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I
         if (a1) { U[n + 1] = cB.ux; U[Nt + n + 1] = cB.uy; U[2 * Nt + n + 1] = cB.uz; }
     }
     FT *const of = out.f + n;
-    GT *const og = out.g() + n;
     const bool both = a0 && a1;
     auto put = [&](auto *p, R v0, R v1) {
         using T = std::remove_pointer_t<decltype(p)>;
@@ -476,25 +431,20 @@ __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I
             Store<T>::st(p + 1, v1);
         }
     };
-    {
-        const R FsA = collide_rest(P, cA, F0[0]), FsB = collide_rest(P, cB, F1[0]);
-        put(of, FsA, FsB);
-        put(og, phA * (R(1) + FsA), phB * (R(1) + FsB));
-    }
+    put((R *)L.rec + g, cA.bq, cB.bq);
+    put(of, collide_rest(P, cA, F0[0]), collide_rest(P, cB, F1[0]));
     PairLoop<R>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value, ib = i + 9;
-        R FiA, FibA, recA, FiB, FibB, recB;
-        collide_pair<R, i>(P, cA, nnA, F0[i], F0[ib], FiA, FibA, recA);
-        collide_pair<R, i>(P, cB, nnB, F1[i], F1[ib], FiB, FibB, recB);
+        R FiA, FibA, FiB, FibB;
+        collide_pair<R, i>(P, cA, F0[i], F0[ib], FiA, FibA);
+        collide_pair<R, i>(P, cB, F1[i], F1[ib], FiB, FibB);
         put(of + i * N, FiA, FiB);
         put(of + ib * N, FibA, FibB);
-        put(og + i * N, phA * (R(1) + FiA) + recA, phB * (R(1) + FiB) + recB);
-        put(og + ib * N, phA * (R(1) + FibA) - recA, phB * (R(1) + FibB) - recB);
     });
 }
 
 #ifndef LBM_COLLIDE2_MINB
-#define LBM_COLLIDE2_MINB 5
+#define LBM_COLLIDE2_MINB 4
 #endif
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES / 2, LBM_COLLIDE2_MINB) k_collide2(Lattice L, int cur)
@@ -710,13 +660,13 @@ __global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : LBM_GC_MINB
     }
 }
 
-long long plan_gradcurv(std::vector<InstDev> &inst)
+long long plan_gradcurv(std::vector<InstDev> &inst, int zc_request)
 {
     long long items = 0;
     for (auto &I : inst) {
         I.gc_tiles_x = (I.nx + GC_TX - 1) / GC_TX;
         I.gc_tiles_y = (I.ny + GC_TY - 1) / GC_TY;
-        const int zc = std::min(GC_ZC, I.nz);
+        const int zc = std::min(zc_request > 0 ? zc_request : GC_ZC, I.nz);
         I.gc_nchunks = (I.nz + zc - 1) / zc;
         I.gc_zc = (I.nz + I.gc_nchunks - 1) / I.gc_nchunks;
         I.gc_item_start = items;
@@ -725,9 +675,31 @@ long long plan_gradcurv(std::vector<InstDev> &inst)
     return items;
 }
 
-// tile shapes of the fused kernel: 0 -> 16 x 16, 1 -> 32 x 8
-int fused_tile_x(int tile) { return tile == 1 ? 32 : 16; }
-int fused_tile_y(int tile) { return tile == 1 ? 8 : 16; }
+// row-strip work items of the bulk kernels: whole x-rows of one z-plane, at
+// most ROW_NODES nodes per item, or one row cut into segments of at most
+// ROW_NODES nodes
+long long plan_rows(std::vector<InstDev> &inst)
+{
+    long long total = 0;
+    for (auto &I : inst) {
+        if (I.nx <= ROW_NODES) {
+            I.st_rows = std::min(I.ny, ROW_NODES / I.nx);
+            I.st_seg = I.nx;
+            I.st_nseg = 1;
+        } else {
+            const int nseg = (I.nx + ROW_NODES - 1) / ROW_NODES;
+            int seg = (I.nx + nseg - 1) / nseg;
+            seg = (seg + 1) / 2 * 2;  // even: node pairs never straddle two items
+            I.st_rows = 1;
+            I.st_seg = seg;
+            I.st_nseg = (I.nx + seg - 1) / seg;
+        }
+        I.st_ygroups = (I.ny + I.st_rows - 1) / I.st_rows;
+        I.st_item_start = total;
+        total += (long long)I.nz * I.st_ygroups * I.st_nseg;
+    }
+    return total;
+}
 
 // launch with programmatic stream serialisation: the kernel may be scheduled
 // while its predecessor in the stream drains (it calls pdl_wait first)
@@ -752,34 +724,11 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
                        const FluidLaunch &fz, const Hook &after_grad, const SideLane &lane)
 {
     using R = typename Store<S>::real;
-    if (fz.form == FORM_FUSED && !is_mixed<S>) {
-        if (L.n_parts > 0) {
-            // phi and grad(phi) around the particles, for the capillary force:
-            // corners of the surface points lie within R_p + 2 of the centre,
-            // their gradient reads phi within R_p + 3 (solid-filled), the fill
-            // reads fluid phi within R_p + 4
-            const int side = L.cap_side;
-            mk(STAGE_REGION, 0);
-            k_phi_region<S><<<dim3(L.cap_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, cur, side);
-            k_solidphi_region<R><<<dim3(L.cap_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, side - 2);
-            k_grad_region<R><<<dim3(L.cap_blocks, L.n_parts), PART_THREADS, 0, st>>>(L, side - 4);
-            mk(STAGE_REGION, 1);
-            *launches += 3;
-        }
-        mk(STAGE_FUSED, 0);
-        if constexpr (!is_mixed<S>) launch_fused_form<S>(L, cur, fz, st);
-        mk(STAGE_FUSED, 1);
-        *launches += 1;
-        return;
-    }
-    // staged form where every instance's rows are whole 16-byte units, plain otherwise
-    const bool staged = fz.form == FORM_STAGED && fz.st_items > 0 && !is_mixed<S>;
     const dim3 grid((unsigned)fz.rows);  // one CTA per row-strip work item
+    const bool pair = sizeof(S) == 2 && fz.pair;
     // boundary passes: particle cubes and the static list of nodes next to walls
     const long long bctas = (long long)L.n_parts * L.cap_blocks + (L.n_static_bfl + PART_THREADS - 1) / PART_THREADS;
     const dim3 bgrid((unsigned)std::max(bctas, 1LL));
-    // boundary pass beside (side lane) or after the bulk kernel; profiling
-    // (no side lane) times the two separately
     // phi of solid nodes next to fluid: the listed static nodes and the
     // particle cubes (every particle node lies within R_p + 1 of its centre).
     // It reads phi only at fluid nodes next to a solid, which the boundary
@@ -796,6 +745,8 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         }
         fill_done = true;
     };
+    // boundary pass beside (side lane) or after the bulk kernel; profiling
+    // (no side lane) times the two separately
     auto bound_pass = [&](auto kernel, int bstage, int stage, auto &&bulk) {
         if (lane.side) {
             cudaEventRecord(lane.a, st);
@@ -816,21 +767,15 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         }
         *launches += 1;
     };
-    if (staged) {
-        mk(STAGE_PHI, 0);
-        if constexpr (!is_mixed<S>) launch_staged_phi<S>(L, cur, fz, st);
-        mk(STAGE_PHI, 1);
-    } else {
-        bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] {
-            if constexpr (sizeof(typename PopTypes<S>::F) == 2) {
-                if (fz.pair) {
-                    k_phi2<S><<<grid, ROW_NODES / 2, 0, st>>>(L, cur);
-                    return;
-                }
+    bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] {
+        if constexpr (sizeof(S) == 2) {
+            if (pair) {
+                k_phi2<S><<<grid, ROW_NODES / 2, 0, st>>>(L, cur);
+                return;
             }
-            k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
-        });
-    }
+        }
+        k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
+    });
     if (!fill_done) {
         mk(STAGE_SOLIDPHI, 0);
         fill_solid_phi(st);
@@ -840,21 +785,15 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     launch_after(k_gradcurv<R>, dim3((unsigned)fz.gc_items), dim3(GC_TX * GC_TY), st, L);
     mk(STAGE_GRAD, 1);
     after_grad();
-    if (staged) {
-        mk(STAGE_COLLIDE, 0);
-        if constexpr (!is_mixed<S>) launch_staged_collide<S>(L, cur, fz, st);
-        mk(STAGE_COLLIDE, 1);
-    } else {
-        bound_pass(k_collide_bound<S>, STAGE_COLLIDE_BOUND, STAGE_COLLIDE, [&] {
-            if constexpr (sizeof(typename PopTypes<S>::F) == 2) {
-                if (fz.pair) {
-                    launch_after(k_collide2<S>, grid, dim3(ROW_NODES / 2), st, L, cur);
-                    return;
-                }
+    bound_pass(k_collide_bound<S>, STAGE_COLLIDE_BOUND, STAGE_COLLIDE, [&] {
+        if constexpr (sizeof(S) == 2) {
+            if (pair) {
+                launch_after(k_collide2<S>, grid, dim3(ROW_NODES / 2), st, L, cur);
+                return;
             }
-            launch_after(k_collide<S>, grid, dim3(ROW_NODES), st, L, cur);
-        });
-    }
+        }
+        launch_after(k_collide<S>, grid, dim3(ROW_NODES), st, L, cur);
+    });
     *launches += 3;
 }
 
@@ -866,7 +805,6 @@ INST(double)
 INST(float)
 INST(__half)
 INST(__nv_bfloat16)
-INST(MixedF16F32)
 #undef INST
 
 }  // namespace lbmg

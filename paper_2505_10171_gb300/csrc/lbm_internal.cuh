@@ -5,9 +5,12 @@
 // opposites, so that the opposite of i is i +- 9; the C ABI order (LBM_C in
 // include/lbm.h) is mapped on the way in and out.
 //
-// Populations are stored as offsets (two-component encoding):
-//   F_i = f_i/(w_i rho0) - 1,   G_i = (f^a_i - f^b_i)/(w_i rho0)
-// structure of arrays: pop[q*N + n], q = 0..18 for F, 19..37 for G.
+// Populations are stored as total offsets F_i = f_i/(w_i rho0) - 1, structure
+// of arrays pop[i*N + n].  The colour offsets G_i = (f^a_i - f^b_i)/(w_i rho0)
+// are not stored: the recolouring step (Sec. IV) leaves every node with
+//   G*_i = phi (1 + F*_i) + b (c_i . n)/|c_i|,   b = beta/2 (rho/rho0)(1 - phi^2),
+// phi and n the order parameter and interface normal its collision used, so a
+// state is F* plus phi, b and n per node, and G is rebuilt where it is needed.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -50,7 +53,7 @@ constexpr unsigned ST_UNSTABLE = 1u;
 constexpr unsigned ST_DISPLACEMENT = 2u;
 constexpr unsigned ST_TIMEOUT = 4u;  // a bounded wait for an asynchronous copy gave up
 
-constexpr int CAP_POINTS = 90 * 180;  // Sec. V E: 2 deg x 2 deg Lagrangian points
+constexpr int CAP_POINTS = 90 * 180;  // Sec. V F: 2 deg x 2 deg Lagrangian points
 constexpr int CAP_THREADS = 256;
 constexpr int CAP_BLOCKS = (CAP_POINTS + CAP_THREADS - 1) / CAP_THREADS;
 constexpr int PART_THREADS = 256;
@@ -64,7 +67,7 @@ struct InstDev {
     long long N;         // nodes of the instance
     long long node_off;  // first node in the per-node arrays
     long long pop_off;   // byte offset of the instance's population block
-    int pstride;         // population stride (N; padded to a multiple of 8 in the mixed form)
+    int pstride;         // population stride (N)
     int part_off;        // first particle of the instance
     int hist_off;        // first pair-history record of the instance
     int crec_off;        // first DEM contact record of the instance
@@ -80,10 +83,7 @@ struct InstDev {
     float f_rho0, f_sigma, f_beta, f_eta_a, f_eta_b, f_eps2, f_wet_max;
     float f_body_a[3], f_body_b[3];
     float f_ir0, f_h_ia, f_h_ib;
-    // fused-kernel work items: tiles_x * tiles_y column tiles x nchunks z-chunks
-    long long item_start;
-    int tiles_x, tiles_y, nchunks, zc;
-    // staged-kernel work items: st_rows whole x-rows of one z-plane per item
+    // row-strip work items of the bulk kernels: st_rows whole x-rows of one z-plane per item
     // (st_nseg = 1, st_seg = nx), or one row cut into st_nseg segments of at
     // most st_seg nodes; st_ygroups items cover the y rows of a plane
     long long st_item_start;
@@ -143,8 +143,11 @@ struct Lattice {
     long long n_static_bfl;
     uint8_t *flags;
     void *pop[2];
-    void *phi;           // [Ntot] real
-    void *grad;          // [3][Ntot] real: regularised interface normal n
+    void *phi;           // [Ntot] real: the order parameter this step computes (outside a step: the last one)
+    void *phi_src;       // [Ntot] real: the order parameter of the stored state (its collision's phi)
+    void *rec;           // [Ntot] real: recolouring amplitude b of the stored state
+    void *grad;          // [3][Ntot] real: regularised interface normal n (of the stored state until
+                         //   the gradient pass of the next step rewrites it)
     void *gmag;          // [Ntot] real: sqrt(|grad phi|^2 + eps^2), so grad phi = n gmag
     void *kap;           // [Ntot] real: curvature div(n) of fluid nodes
     void *u;             // [3][Ntot] real (store_velocity)
@@ -219,54 +222,21 @@ struct Store<__nv_bfloat16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
-// mixed storage: the total offsets F in FP16 and the colour offsets G in FP32.
-// The colour offsets carry the order parameter, whose rounding noise the
-// interface forces amplify into the velocity; the total offsets are small
-// (|F_i| ~ 3|u| away from walls) and tolerate half precision.
-struct MixedF16F32 {};
-template <>
-struct Store<MixedF16F32> {
-    using real = float;
-};
-
-// element types of the two halves of the population storage
-template <class S>
-struct PopTypes {
-    using F = S;
-    using G = S;
-};
-template <>
-struct PopTypes<MixedF16F32> {
-    using F = __half;
-    using G = float;
-};
-template <class S>
-constexpr bool is_mixed = false;
-template <>
-constexpr bool is_mixed<MixedF16F32> = true;
-
-// populations of one instance: F_i (i < 19, i-major, stride pstride) at the
-// start of the instance's block, G_i after them; instance blocks follow one
-// another in node order.  pstride = N (Q (sizeof F + sizeof G) bytes per node)
-// except in the mixed form, where it is rounded up to a multiple of 8 so that
-// the FP32 half starts 16-byte aligned
+// populations of one instance: F_i (i-major, stride pstride = N) at the
+// instance block's byte offset; instance blocks follow one another in node order
 template <class S>
 struct Pop {
-    using FT = typename PopTypes<S>::F;
-    using GT = typename PopTypes<S>::G;
+    using FT = S;
     using R = typename Store<S>::real;
-    static constexpr size_t node_bytes = Q * (sizeof(FT) + sizeof(GT));
-    FT *f;  // the G block starts Q N F-elements later (derived, not stored: one pointer fewer in registers)
+    static constexpr size_t node_bytes = Q * sizeof(S);
+    FT *f;
     int N;  // stride between directions (the instance's pstride)
     __host__ __device__ __forceinline__ Pop(const void *base, const InstDev &I)
         : f((FT *)((char *)base + I.pop_off)), N(I.pstride)
     {
     }
-    __device__ __forceinline__ GT *g() const { return (GT *)(f + Q * N); }
     __device__ __forceinline__ R F(int i, int m) const { return Store<FT>::ld(f + i * N + m); }
-    __device__ __forceinline__ R G(int i, int m) const { return Store<GT>::ld(g() + i * N + m); }
     __device__ __forceinline__ void setF(int i, int m, R v) const { Store<FT>::st(f + i * N + m, v); }
-    __device__ __forceinline__ void setG(int i, int m, R v) const { Store<GT>::st(g() + i * N + m, v); }
 };
 
 // two consecutive 16-bit values of a node pair (x even) as one 32-bit access,
@@ -404,170 +374,108 @@ struct GlobalNbr {
     __device__ __forceinline__ int own(int dx, int dy, int dz) const { return fli[nb.at(dx, dy, dz)] & OWNER_MASK; }
 };
 
-// Pull streaming of both components into node n (Sec. IV streaming), with the
-// Sec. V A halfway bounce-back where the source node is solid:
-//   f_i(x) = f*_ibar(x) + 6 w_i rho^{a,b}(x) c_i.u_w,  rho^{a,b}(x) taken from
-// the node's own pre-streaming populations, u_w at the link midpoint.
-// A is the neighbourhood accessor (global flags, or a shared-memory copy).
-template <class S, class A>
-__device__ __forceinline__ void gather(const InstDev &I, const PartDev *parts, const A &nbr,
-                                       const Pop<S> &in, int n, uint8_t fl,
-                                       typename Store<S>::real *F, typename Store<S>::real *G, int x, int y, int z)
-{
-    using R = typename Store<S>::real;
-    if (!(fl & BOUND_BIT)) {
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-            F[i] = in.F(i, s);
-            G[i] = in.G(i, s);
-        }
-        return;
+// The colour part of the stored state (see the top of this file): per node
+// the order parameter phi of the collision that produced it, the recolouring
+// amplitude b and the interface normal n.  rec(i, m) = b (c_i . n)/|c_i| of
+// node m, so the stored post-collision colour offset is
+// G*_i(m) = phi(m) (1 + F*_i(m)) + rec(i, m).
+template <class R>
+struct Colour {
+    const R *ph, *b, *n;  // instance-relative; n holds three blocks Nt apart
+    long long Nt;
+    __device__ __forceinline__ Colour(const Lattice &L, const InstDev &I)
+        : ph((const R *)L.phi_src + I.node_off), b((const R *)L.rec + I.node_off),
+          n((const R *)L.grad + I.node_off), Nt(L.Ntot)
+    {
     }
-    bool have_rho = false;
-    R rr = 0, rd = 0;  // rho/rho0 and (rho^a - rho^b)/rho0 of this node
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const int own = nbr.own(-cx(i), -cy(i), -cz(i));
-        if (own == OWN_FLUID) {
-            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-            F[i] = in.F(i, s);
-            G[i] = in.G(i, s);
-            continue;
-        }
-        if (!have_rho) {
-            R sF = 0, sG = 0;
-#pragma unroll
-            for (int j = 0; j < Q; j++) {
-                sF += wgt<R>(j) * in.F(j, n);
-                sG += wgt<R>(j) * in.G(j, n);
-            }
-            rr = R(1) + sF;
-            rd = sG;
-            have_rho = true;
-        }
-        R uw[3];
-        surface_velocity<R>(I, parts, own, x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
-        const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
-        const int ib = opp(i);
-        F[i] = in.F(ib, n) + R(6) * rr * cu;
-        G[i] = in.G(ib, n) + R(6) * rd * cu;
+    // c_i . n / |c_i| (only the components along c_i are read)
+    __device__ __forceinline__ R cn(int i, int m) const
+    {
+        R t = 0;
+        if (cx(i)) t += cx(i) * n[m];
+        if (cy(i)) t += cy(i) * n[Nt + m];
+        if (cz(i)) t += cz(i) * n[2 * Nt + m];
+        return csq(i) == 1 ? t : t * R(0.70710678118654752440);
     }
-}
+    __device__ __forceinline__ R rec(int i, int m) const { return b[m] * cn(i, m); }
+};
 
-// pull streaming of the total populations only (F), with the same
-// bounce-back as gather(); the collision needs the colour offsets only through
-// the order parameter, which the order-parameter kernel has already stored
-template <class S, class A>
-__device__ __forceinline__ void gather_F(const InstDev &I, const PartDev *parts, const A &nbr,
-                                         const Pop<S> &in, int n, uint8_t fl,
-                                         typename Store<S>::real *F, int x, int y, int z)
-{
-    using R = typename Store<S>::real;
-    if (!(fl & BOUND_BIT)) {
-#pragma unroll
-        for (int i = 0; i < Q; i++) F[i] = in.F(i, nbr.idx(-cx(i), -cy(i), -cz(i)));
-        return;
-    }
-    bool have_rho = false;
-    R rr = 0;
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const int own = nbr.own(-cx(i), -cy(i), -cz(i));
-        if (own == OWN_FLUID) {
-            F[i] = in.F(i, nbr.idx(-cx(i), -cy(i), -cz(i)));
-            continue;
-        }
-        if (!have_rho) {
-            R sF = 0;
-#pragma unroll
-            for (int j = 0; j < Q; j++) sF += wgt<R>(j) * in.F(j, n);
-            rr = R(1) + sF;
-            have_rho = true;
-        }
-        R uw[3];
-        surface_velocity<R>(I, parts, own, x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
-        const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
-        F[i] = in.F(opp(i), n) + R(6) * rr * cu;
-    }
-}
-
-// gather / gather_F for the boundary passes: the same values, with every
-// flag and population load issued before any is used (one dependent round
-// trip instead of one per link); G is skipped when null
+// Pull streaming (Sec. IV) into fluid node n, with the Sec. V A halfway
+// bounce-back where the source node is solid:
+//   f_i(x) = f*_ibar(x) + 6 w_i rho^{a,b}(x) c_i.u_w,
+// rho^{a,b}(x) of the node's own pre-streaming state, u_w at the link midpoint.
+// Every flag and population load is issued before any is used (one dependent
+// round trip instead of one per link).  F receives the 19 total offsets.
+// With C set, *sG receives sum_i w_i G_i of the streamed colour offsets:
+// G_i(x) = G*_i(x - c_i) from a fluid source; from a solid one
+// G*_ibar(x) + 6 (rho^a - rho^b)(x)/rho0 c_i.u_w, and since
+// (rho^a - rho^b)(x) = phi(x) rho(x) that is phi(x)(1 + F_i(x)) - rec(i, x).
 template <class S, class A>
 __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *parts, const A &nbr,
-                                           const Pop<S> &in, int n, typename Store<S>::real *F,
-                                           typename Store<S>::real *G, int x, int y, int z)
+                                           const Pop<S> &in, const Colour<typename Store<S>::real> *C, int n,
+                                           typename Store<S>::real *F, typename Store<S>::real *sG, int x, int y,
+                                           int z)
 {
     using R = typename Store<S>::real;
     int own[Q];
-    R pF[Q], oF[Q], pG[Q], oG[Q];
+    R pF[Q], oF[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
         own[i] = nbr.own(-cx(i), -cy(i), -cz(i));
         pF[i] = in.F(i, s);
         oF[i] = in.F(i, n);
-        if (G) {
-            pG[i] = in.G(i, s);
-            oG[i] = in.G(i, n);
-        }
     }
-    R sF = 0, sG = 0;
+    R sF = 0;
 #pragma unroll
-    for (int j = 0; j < Q; j++) {
-        sF += wgt<R>(j) * oF[j];
-        if (G) sG += wgt<R>(j) * oG[j];
-    }
-    const R rr = R(1) + sF, rd = sG;
+    for (int j = 0; j < Q; j++) sF += wgt<R>(j) * oF[j];
+    const R rr = R(1) + sF;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (own[i] == OWN_FLUID) {
             F[i] = pF[i];
-            if (G) G[i] = pG[i];
             continue;
         }
         R uw[3];
         surface_velocity<R>(I, parts, own[i], x - R(0.5) * cx(i), y - R(0.5) * cy(i), z - R(0.5) * cz(i), uw);
         const R cu = cx(i) * uw[0] + cy(i) * uw[1] + cz(i) * uw[2];
-        const int ib = opp(i);
-        F[i] = oF[ib] + R(6) * rr * cu;
-        if (G) G[i] = oG[ib] + R(6) * rd * cu;
+        F[i] = oF[opp(i)] + R(6) * rr * cu;
     }
+    if (!C) return;
+    const R phn = C->ph[n];
+    R g = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        R gi;
+        if (own[i] == OWN_FLUID) {
+            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
+            gi = C->ph[s] * (R(1) + F[i]);
+            if (i) gi += C->rec(i, s);
+        } else {
+            gi = phn * (R(1) + F[i]) - C->rec(i, n);
+        }
+        g += wgt<R>(i) * gi;
+    }
+    *sG = g;
 }
 
-// order parameter of a fluid node none of whose neighbours is solid
+// order parameter after streaming of a fluid node none of whose neighbours is
+// solid: phi = sum_i w_i G_i / (1 + sum_i w_i F_i) with G_i rebuilt from the
+// source node's colour state
 template <class S, class A>
-__device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const Pop<S> &in)
+__device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const Pop<S> &in,
+                                                             const Colour<typename Store<S>::real> &C)
 {
     using R = typename Store<S>::real;
     R sF = 0, sG = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-        sF += wgt<R>(i) * in.F(i, s);
-        sG += wgt<R>(i) * in.G(i, s);
-    }
-    return sG / (R(1) + sF);
-}
-
-// order parameter of a fluid node after streaming: the same sums as the
-// collision's, without keeping the 38 values
-template <class S, class A>
-__device__ __forceinline__ typename Store<S>::real node_phi(const InstDev &I, const PartDev *parts, const A &nbr,
-                                                            const Pop<S> &in, int n, uint8_t fl,
-                                                            int x, int y, int z)
-{
-    using R = typename Store<S>::real;
-    if (!(fl & BOUND_BIT)) return phi_fluid<S>(nbr, in);
-    R sF = 0, sG = 0;
-    R F[Q], G[Q];
-    gather<S>(I, parts, nbr, in, n, fl, F, G, x, y, z);
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        sF += wgt<R>(i) * F[i];
-        sG += wgt<R>(i) * G[i];
+        const R F = in.F(i, s);
+        sF += wgt<R>(i) * F;
+        R g = C.ph[s] * (R(1) + F);
+        if (i) g += C.rec(i, s);
+        sG += wgt<R>(i) * g;
     }
     return sG / (R(1) + sF);
 }
@@ -575,7 +483,7 @@ __device__ __forceinline__ typename Store<S>::real node_phi(const InstDev &I, co
 template <class R>
 __device__ __forceinline__ R dsqrt(R v) { return sqrt(v); }
 
-// Sec. V D geometric wetting: rotate g so that -g/|g| makes the angle theta
+// Sec. V E geometric wetting: rotate g so that -g/|g| makes the angle theta
 // with the outward solid normal ns, keeping |g|; of the two candidates the one
 // closer to the original direction is kept.
 template <class R>
@@ -696,21 +604,6 @@ __device__ __forceinline__ void for_item_nodes(const Lattice &L, F &&f)
     f(I, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
 }
 
-// grid of a persistent kernel of ROW_NODES threads: every SM filled to the
-// occupancy the kernel allows, capped at cap CTAs per SM when cap > 0
-template <class K>
-int persistent_grid(K kernel, size_t smem, int cap)
-{
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, ROW_NODES, smem);
-    if (per_sm < 1) per_sm = 1;
-    if (cap > 0 && per_sm > cap) per_sm = cap;
-    return sms * per_sm;
-}
-
 // kernel stages, in launch order within a step (for per-kernel timing)
 enum Stage {
     STAGE_PHI = 0, STAGE_SOLIDPHI, STAGE_GRAD, STAGE_COLLIDE, STAGE_MEM, STAGE_CAPILLARY, STAGE_DEM,
@@ -729,7 +622,7 @@ struct Marker {
 };
 
 // host-side hook run by the fluid launcher once grad(phi), the normals and
-// the curvature of the step are final (plain and staged forms)
+// the curvature of the step are final
 struct Hook {
     void (*fn)(void *self) = nullptr;
     void *self = nullptr;
@@ -748,45 +641,21 @@ struct SideLane {
 };
 
 // host-side kernel launchers (defined in the .cu files)
-enum { FORM_STAGED = 0, FORM_FUSED = 1, FORM_PLAIN = 2 };
+constexpr int FORM_PLAIN = 2;  // the launch form of the fluid update (the value the ABI names)
 struct FluidLaunch {
-    int form;           // FORM_STAGED, FORM_FUSED or FORM_PLAIN
-    int tile;           // fused tile shape index (see lbm_fluid.cu)
-    long long items;    // fused work items (all instances)
-    long long rows;     // row-strip work items (all instances): CTAs of each plain kernel
+    int tile;           // 0: node-pair bulk kernels where possible; 1: one node per thread
+    long long rows;     // row-strip work items (all instances): CTAs of each bulk kernel
     long long gc_items; // gradient + curvature work items (all instances)
-    long long st_items; // the same when the staged form is available, else 0
-    // persistent grids of the staged kernels, per variant (see lbm_staged.cu)
-    int st_grid_phi[3], st_grid_collide[3];
-    bool pair;          // every instance has an even nx: node-pair kernels for 16-bit total offsets
+    bool pair;          // every instance has an even nx: node-pair kernels for 16-bit storage
 };
-// staged kernels: threads per CTA and nodes per work item at most
-constexpr int ST_THREADS = 256;
-constexpr int ST_SEGMAX = 256;
-static_assert(ST_SEGMAX == ROW_NODES && ST_THREADS == ROW_NODES, "one node per thread per item");
-template <class S>
-struct StagedCfg {
-    static constexpr int A = 16 / (int)sizeof(S);  // elements per 16 bytes
-};
-// plan the work items of the gradient + curvature kernel
-long long plan_gradcurv(std::vector<InstDev> &inst);
-// plan the row-strip work items of every instance; *items = their number,
-// returns false if an instance's rows are not whole 16-byte units of storage
-// (which the staged copies need)
-bool plan_rows(std::vector<InstDev> &inst, size_t elem, long long *items);
-template <class S>
-void staged_grids(int *grid_phi, int *grid_collide, int cap);  // arrays of 3 (variants)
-template <class S>
-void launch_staged_phi(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
-template <class S>
-void launch_staged_collide(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
-template <class S>
-void launch_fused_form(const Lattice &L, int cur, const FluidLaunch &fz, cudaStream_t st);
+// plan the work items of the gradient + curvature kernel (z-planes per item:
+// zc_request, 0 for the default)
+long long plan_gradcurv(std::vector<InstDev> &inst, int zc_request);
+// plan the row-strip work items of every instance; returns their number
+long long plan_rows(std::vector<InstDev> &inst);
 template <class S>
 void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk,
                        const FluidLaunch &fz, const Hook &after_grad = Hook(), const SideLane &lane = SideLane());
-int fused_tile_x(int tile);
-int fused_tile_y(int tile);
 template <class S>
 void launch_particle_forces(const Lattice &L, int cur, cudaStream_t st, long long *launches, const Marker &mk);
 // the two halves of it: momentum exchange (needs only the step's input
@@ -836,8 +705,8 @@ void mlp_refresh(const Mlp &m, cudaStream_t st);
 // rows idx[row0 + r] (or row0 + r) of fp32 features [*][387] (and targets [*][6]) into the batch buffers
 void mlp_stage(const Mlp &m, const float *X, const float *Y, const long long *idx, long long row0, int n,
                cudaStream_t st);
-void mlp_forward(const Mlp &m, int n, unsigned *status, cudaStream_t st);
-void mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cudaStream_t st);
+cudaError_t mlp_forward(const Mlp &m, int n, unsigned *status, cudaStream_t st);
+cudaError_t mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cudaStream_t st);
 void mlp_adam(Mlp &m, double lr, cudaStream_t st);
 template <class S>
 void launch_shell_features(const Lattice &L, int p0, int np, float *feat, cudaStream_t st);

@@ -16,6 +16,7 @@
 // with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and applies
 // bias, tanh or the tanh derivative.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "lbm_async.cuh"
@@ -235,16 +236,36 @@ __global__ void __launch_bounds__(GM) k_gemm_tc(GemmArgs g)
     if (warp == 0) tmem_dealloc(tmem, NCOLS);
 }
 
+// k_gemm_tc<BN> needs more than 48 KiB of dynamic shared memory, a function
+// attribute of each device: set once per device (under a lock, since
+// contexts on several threads may reach here first together), with its result
+// checked, before the first launch there
 template <int BN>
-void gemm(const GemmArgs &a, int M, int N, cudaStream_t st)
+static cudaError_t gemm_setup()
 {
-    static bool configured = false;
-    if (!configured) {
-        cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmSmem<BN>::BYTES);
-        configured = true;
-    }
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static bool done[MAXDEV] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAXDEV) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmSmem<BN>::BYTES);
+    if (e == cudaSuccess) done[dev] = true;
+    return e;
+}
+
+// returns the set-up's or this launch's own error
+template <int BN>
+cudaError_t gemm(const GemmArgs &a, int M, int N, cudaStream_t st)
+{
+    const cudaError_t e = gemm_setup<BN>();
+    if (e != cudaSuccess) return e;
     const dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)((N + BN - 1) / BN));
-    k_gemm_tc<BN><<<grid, GM, GemmSmem<BN>::BYTES, st>>>(a);
+    void *args[] = {(void *)&a};
+    return cudaLaunchKernel((const void *)k_gemm_tc<BN>, grid, dim3(GM), args, GemmSmem<BN>::BYTES, st);
 }
 
 GemmArgs gargs(int Mv, int Nv, int Kv, const bf16 *A, long long sam, long long sak, const bf16 *B, long long sbn,
@@ -416,25 +437,28 @@ void mlp_stage(const Mlp &m, const float *X, const float *Y, const long long *id
     if (Y) k_stage_targets<<<(n * MLP_NOUT + EW - 1) / EW, EW, 0, st>>>(Y, idx, row0, n, m.T);
 }
 
-void mlp_forward(const Mlp &m, int n, unsigned *status, cudaStream_t st)
+cudaError_t mlp_forward(const Mlp &m, int n, unsigned *status, cudaStream_t st)
 {
+    cudaError_t e;
     const float *b1 = m.theta + MLP_OFF_B1, *b2 = m.theta + MLP_OFF_B2, *b3 = m.theta + MLP_OFF_B3;
     // h1 = tanh(X W1^T + b1)
     GemmArgs a = gargs(n, MLP_HIDDEN, MLP_KIN, m.X, MLP_KIN, 1, m.W1b, MLP_KIN, 1, status);
     a.bias = b1; a.act = 1; a.C16 = m.H1; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    gemm<128>(a, n, MLP_HIDDEN, st);
+    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // h2 = tanh(h1 W2^T + b2)
     a = gargs(n, MLP_HIDDEN, MLP_HIDDEN, m.H1, MLP_HIDDEN, 1, m.W2b, MLP_HIDDEN, 1, status);
     a.bias = b2; a.act = 1; a.C16 = m.H2; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    gemm<128>(a, n, MLP_HIDDEN, st);
+    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // y = h2 W3^T + b3  ([n][16], columns 6..15 unused)
     a = gargs(n, MLP_NOUT, MLP_HIDDEN, m.H2, MLP_HIDDEN, 1, m.W3b, MLP_HIDDEN, 1, status);
     a.bias = b3; a.C32 = m.Y; a.scm = 16; a.scn = 1;
-    gemm<16>(a, n, 16, st);
+    if ((e = gemm<16>(a, n, 16, st)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
-void mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cudaStream_t st)
+cudaError_t mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cudaStream_t st)
 {
+    cudaError_t e;
     float *g = m.grad;
     const int nl = (n * 16 + EW - 1) / EW;
     k_loss<<<nl, EW, 0, st>>>(m.Y, m.T, n, m.dY, m.dYb, m.loss_part);
@@ -442,26 +466,27 @@ void mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cudaStream
     // dW3[j][i] = sum_b dY[b][j] h2[b][i]   (M = hidden i, N = output j, K = batch)
     GemmArgs a = gargs(MLP_HIDDEN, MLP_NOUT, n, m.H2, 1, MLP_HIDDEN, m.dYb, 1, 16, status);
     a.C32 = g + MLP_OFF_W3; a.scm = 1; a.scn = MLP_HIDDEN;
-    gemm<16>(a, MLP_HIDDEN, 16, st);
+    if ((e = gemm<16>(a, MLP_HIDDEN, 16, st)) != cudaSuccess) return e;
     k_colsum<float><<<MLP_NOUT, EW, 0, st>>>(m.dY, n, 16, g + MLP_OFF_B3);
     // dz2 = (dY W3) * (1 - h2^2)
     a = gargs(n, MLP_HIDDEN, MLP_NOUT, m.dYb, 16, 1, m.W3b, 1, MLP_HIDDEN, status);
     a.act = 2; a.g = m.H2; a.sgm = MLP_HIDDEN; a.sgn = 1; a.C16 = m.dZ2; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    gemm<128>(a, n, MLP_HIDDEN, st);
+    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // dW2[o][i] = sum_b dz2[b][o] h1[b][i]
     a = gargs(MLP_HIDDEN, MLP_HIDDEN, n, m.dZ2, 1, MLP_HIDDEN, m.H1, 1, MLP_HIDDEN, status);
     a.C32 = g + MLP_OFF_W2; a.scm = MLP_HIDDEN; a.scn = 1;
-    gemm<128>(a, MLP_HIDDEN, MLP_HIDDEN, st);
+    if ((e = gemm<128>(a, MLP_HIDDEN, MLP_HIDDEN, st)) != cudaSuccess) return e;
     k_colsum<bf16><<<MLP_HIDDEN, EW, 0, st>>>(m.dZ2, n, MLP_HIDDEN, g + MLP_OFF_B2);
     // dz1 = (dz2 W2) * (1 - h1^2)
     a = gargs(n, MLP_HIDDEN, MLP_HIDDEN, m.dZ2, MLP_HIDDEN, 1, m.W2b, 1, MLP_HIDDEN, status);
     a.act = 2; a.g = m.H1; a.sgm = MLP_HIDDEN; a.sgn = 1; a.C16 = m.dZ1; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    gemm<128>(a, n, MLP_HIDDEN, st);
+    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // dW1[o][i] = sum_b dz1[b][o] x[b][i]
     a = gargs(MLP_HIDDEN, MLP_KIN, n, m.dZ1, 1, MLP_HIDDEN, m.X, 1, MLP_KIN, status);
     a.C32 = g + MLP_OFF_W1; a.scm = MLP_KIN; a.scn = 1;
-    gemm<128>(a, MLP_HIDDEN, MLP_KIN, st);
+    if ((e = gemm<128>(a, MLP_HIDDEN, MLP_KIN, st)) != cudaSuccess) return e;
     k_colsum<bf16><<<MLP_HIDDEN, EW, 0, st>>>(m.dZ1, n, MLP_HIDDEN, g + MLP_OFF_B1);
+    return cudaSuccess;
 }
 
 void mlp_adam(Mlp &m, double lr, cudaStream_t st)
@@ -580,7 +605,9 @@ void launch_surrogate_forces(const Lattice &L, const Mlp &m, float *feat, cudaSt
         const int np = std::min(m.cap, L.n_parts - p0);
         launch_shell_features<S>(L, p0, np, feat, st);
         mlp_stage(m, feat, nullptr, nullptr, 0, np, st);
-        mlp_forward(m, np, L.status, st);
+        // a failed set-up or launch stays in the runtime's last error, which
+        // lbm_step checks after enqueueing the step
+        if (mlp_forward(m, np, L.status, st) != cudaSuccess) return;
         k_surrogate_apply<<<(np + 127) / 128, 128, 0, st>>>(L, m.Y, p0, np);
         *launches += 6;
     }
@@ -595,7 +622,6 @@ INST(double)
 INST(float)
 INST(__half)
 INST(__nv_bfloat16)
-INST(MixedF16F32)
 #undef INST
 
 }  // namespace lbmg

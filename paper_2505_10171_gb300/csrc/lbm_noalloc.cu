@@ -94,9 +94,22 @@ extern "C" lbm_status lbm_component_masses_noalloc(const double *pops, long long
         }
         part = g_partials_addr[dev];
     }
-    const int nblk = (int)((n_nodes + NA_NODES_PER_BLOCK - 1) / NA_NODES_PER_BLOCK);
+    int nblk = (int)((n_nodes + NA_NODES_PER_BLOCK - 1) / NA_NODES_PER_BLOCK);
     cudaStream_t st = (cudaStream_t)stream;
-    k_noalloc_partial<<<nblk, NA_THREADS, 0, st>>>(pops, n_nodes, (double(*)[2])part);
-    k_noalloc_final<<<1, 32, 0, st>>>((const double(*)[2])part, nblk, masses);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    // launched through cudaLaunchKernel, whose return code is that launch's
+    // own: an earlier, unrelated error left in the runtime is neither reported
+    // as this call's failure nor cleared
+    double(*pp)[2] = (double(*)[2])part;
+    void *a1[] = {(void *)&pops, (void *)&n_nodes, (void *)&pp};
+    if (cudaLaunchKernel((const void *)k_noalloc_partial, dim3(nblk), dim3(NA_THREADS), a1, 0, st) != cudaSuccess) {
+        cudaGetLastError();  // this launch's error, reported by the return value
+        return LBM_ERR_CUDA;
+    }
+    const double(*cp)[2] = pp;
+    void *a2[] = {(void *)&cp, (void *)&nblk, (void *)&masses};
+    if (cudaLaunchKernel((const void *)k_noalloc_final, dim3(1), dim3(32), a2, 0, st) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
 }

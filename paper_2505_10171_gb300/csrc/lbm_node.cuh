@@ -1,4 +1,4 @@
-// Per-node device functions of the fluid update (Sec. IV, V D of arXiv
+// Per-node device functions of the fluid update (Sec. IV, V E of arXiv
 // 2505.10171), shared by every launch form so that all forms run the same
 // arithmetic: solid-node phi, wetting normal, grad(phi), collision + recolouring
 // + write, curvature and the regularised normal.
@@ -186,11 +186,10 @@ __device__ __forceinline__ R collide_rest(const FluidPar<R> &P, const CollideSta
 // opposite pair (i, i+9): the paper's S relaxes every even non-conserved
 // moment with omega and every odd one with omega', i.e. the MRT operator is
 // exactly the two-relaxation-time operator on the pair's even/odd parts.
-// Returns F*_i, F*_ib and the recolouring term beta/2 (rho/rho0)(1 - phi^2)
-// c_i.n/|c_i| (G* = phi (1 + F*) +- rec).
+// Returns F*_i and F*_ib.
 template <class R, int i>
-__device__ __forceinline__ void collide_pair(const FluidPar<R> &P, const CollideState<R> &c, const R *nn, R Fi_in,
-                                             R Fib_in, R &Fi, R &Fib, R &rec)
+__device__ __forceinline__ void collide_pair(const FluidPar<R> &P, const CollideState<R> &c, R Fi_in, R Fib_in,
+                                             R &Fi, R &Fib)
 {
     const R cu = cx(i) * c.ux + cy(i) * c.uy + cz(i) * c.uz;
     const R cF = cx(i) * c.Fx + cy(i) * c.Fy + cz(i) * c.Fz;
@@ -204,9 +203,6 @@ __device__ __forceinline__ void collide_pair(const FluidPar<R> &P, const Collide
     const R dm = -c.omp * (fm - eqm) + c.cpo * fbm;
     Fi = Fi_in + dp + dm;
     Fib = Fib_in + dp - dm;
-    const R inv_len = csq(i) == 1 ? R(1) : R(0.70710678118654752440);
-    const R cn = (cx(i) * nn[0] + cy(i) * nn[1] + cz(i) * nn[2]) * inv_len;
-    rec = c.bq * cn;
 }
 
 template <class R, int i = 1>
@@ -225,39 +221,34 @@ struct PairLoop<R, 10> {
 };
 
 // force, velocity, MRT (two-relaxation-time form) with Guo forcing (Sec. IV),
-// recolouring and the write of node n.  F: streamed total offsets; phi: the order parameter after
-// streaming (stored by the order-parameter pass: the colour offsets enter the
-// update only through it); g: corrected grad(phi) of the node; nn: its
-// regularised normal; kap: curvature.
+// recolouring and the write of node n.  F: streamed total offsets; phi: the
+// order parameter after streaming (stored by the order-parameter pass); g:
+// corrected grad(phi) of the node; kap: curvature.  The recolouring of Sec. IV
+// gives G*_i = phi (1 + F*_i) + b (c_i . n)/|c_i| with b = beta/2 (rho/rho0)
+// (1 - phi^2): with phi and n kept, the state is complete with F* and b, which
+// are written (*B receives b).
 template <class S>
 __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<S>::real> &P,
                                                   const typename Store<S>::real *F, typename Store<S>::real phi,
-                                                  const typename Store<S>::real *g, const typename Store<S>::real *nn,
-                                                  typename Store<S>::real kap, const Pop<S> &out, int n,
+                                                  const typename Store<S>::real *g, typename Store<S>::real kap,
+                                                  const Pop<S> &out, int n, typename Store<S>::real *B,
                                                   typename Store<S>::real *U, long long Ustride, unsigned *status)
 {
     using R = typename Store<S>::real;
     using FT = typename Pop<S>::FT;
-    using GT = typename Pop<S>::GT;
     const int N = out.N;
-    FT *const of = out.f + n;    // F_0 of this node; F_i at of + i N
-    GT *const og = out.g() + n;  // G_0 likewise
+    FT *const of = out.f + n;  // F_0 of this node; F_i at of + i N
     const CollideState<R> c = collide_state(P, F, phi, g, kap);
     if (status && (!(c.rr > R(0)) || !(phi == phi))) atomicOr(status, ST_UNSTABLE);
     if (U) { U[n] = c.ux; U[Ustride + n] = c.uy; U[2 * Ustride + n] = c.uz; }
-    {
-        const R Fs = collide_rest(P, c, F[0]);
-        Store<FT>::st(of, Fs);
-        Store<GT>::st(og, phi * (R(1) + Fs));
-    }
+    *B = c.bq;
+    Store<FT>::st(of, collide_rest(P, c, F[0]));
     PairLoop<R>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value, ib = i + 9;
-        R Fi, Fib, rec;
-        collide_pair<R, i>(P, c, nn, F[i], F[ib], Fi, Fib, rec);
+        R Fi, Fib;
+        collide_pair<R, i>(P, c, F[i], F[ib], Fi, Fib);
         Store<FT>::st(of + i * N, Fi);
         Store<FT>::st(of + ib * N, Fib);
-        Store<GT>::st(og + i * N, phi * (R(1) + Fi) + rec);
-        Store<GT>::st(og + ib * N, phi * (R(1) + Fib) - rec);
     });
 }
 
@@ -288,43 +279,6 @@ __device__ __forceinline__ R reg_normal(const R *g, R eps2, R *nn)
     const R im = frsqrt(m2);
     nn[0] = g[0] * im; nn[1] = g[1] * im; nn[2] = g[2] * im;
     return m2 * im;
-}
-
-// nodes next to a solid (bounce-back) and other rare nodes take these
-// out-of-line global-memory paths, so that their registers do not weigh on the
-// kernels' hot loops
-template <class S>
-__device__ __noinline__ typename Store<S>::real phi_node_cold(const InstDev *Ip, const PartDev *parts,
-                                                              const uint8_t *fli, const Pop<S> &in, int n, uint8_t fl,
-                                                              int x, int y, int z)
-{
-    const InstDev &I = *Ip;
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = fli;
-    return node_phi<S>(I, parts, nb, in, n, fl, x, y, z);
-}
-
-template <class S>
-__device__ __noinline__ void collide_node_cold(const InstDev *Ip, const PartDev *parts, const uint8_t *fli,
-                                               const Pop<S> &in, const Pop<S> &out, int n, uint8_t fl, int x, int y, int z,
-                                               typename Store<S>::real phi, typename Store<S>::real n0,
-                                               typename Store<S>::real n1, typename Store<S>::real n2,
-                                               typename Store<S>::real m, typename Store<S>::real kap,
-                                               typename Store<S>::real *U, long long Ntot, unsigned *status)
-{
-    using R = typename Store<S>::real;
-    const InstDev &I = *Ip;
-    GlobalNbr nb;
-    nb.nb.init(x, y, z, I.nx, I.ny, I.nz);
-    nb.fli = fli;
-    FluidPar<R> P;
-    load_par(I, P);
-    const R nn[3] = {n0, n1, n2};
-    const R gr[3] = {n0 * m, n1 * m, n2 * m};
-    R F[Q];
-    gather_F<S>(I, parts, nb, in, n, fl, F, x, y, z);
-    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, U, Ntot, status);
 }
 
 }  // namespace lbmg

@@ -1,7 +1,7 @@
 // Particle kernels of one coupled time step (Sec. III and V of arXiv 2505.10171):
 //   k_mem        momentum-exchange force and torque per particle (Sec. V B)
 //   k_capillary  capillary force and torque from the Lagrangian surface points
-//                (Sec. V E)
+//                (Sec. V F)
 //   k_dem        fixed-order sums of the per-block partials of both, then
 //                contacts (normal spring-dashpot, Luding sliding and rolling
 //                friction) and velocity-Verlet update (Sec. III): one warp per
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
     block_sum6(kin, out + 6);
 }
 
-// Sec. V E: dF = C sigma (1 - phi^2) dA (n x n_s) x n at the points
+// Sec. V F: dF = C sigma (1 - phi^2) dA (n x n_s) x n at the points
 // alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg on r = R_p, n the regularised
 // normal of the trilinearly interpolated grad(phi) (fluid corners only);
 // torque R_p n_s x dF.
@@ -588,9 +588,14 @@ __global__ void k_boundary_full(Lattice L, int inst)
 // 18 moving-direction neighbours that are fluid and not fresh (two hops out if
 // none; ambient (0, rho0) if still none).
 //
+// In the stored form (F* with phi, b, n per node) the refilled state is
+// F_i = (rho/rho0) e_i - 1 with phi = (rho^a - rho^b)/rho and b = 0: its colour
+// offsets (rho^a - rho^b)/rho0 e_i are phi (1 + F_i) exactly.  A neighbour's
+// rho^a - rho^b is phi rho (its colour offsets sum to phi (1 + sum w F)).
+//
 // Few nodes are uncovered per step (about the swept surface area), so the
 // kernel is a scan of the flags plus, per fresh node, one warp working on it:
-// lane i-1 takes neighbour i and issues its 38 population loads at once, the
+// lane i-1 takes neighbour i and issues its 19 population loads at once, the
 // sums meet in a shuffle reduction and lane i writes direction i.
 template <class R>
 __device__ __forceinline__ R warp_sum(R v)
@@ -601,8 +606,9 @@ __device__ __forceinline__ R warp_sum(R v)
 }
 
 template <class S>
-__device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S> &pop, const uint8_t *fli, int x, int y,
-                            int z, int lane)
+__device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S> &pop,
+                            typename Store<S>::real *ph, typename Store<S>::real *B, typename Store<S>::real *Nn,
+                            long long Nt, const uint8_t *fli, int x, int y, int z, int lane)
 {
     using R = typename Store<S>::real;
     R sF = 0, sG = 0;
@@ -620,10 +626,8 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
             if ((fm & OWNER_MASK) == OWN_FLUID && !(fm & FRESH_BIT)) {
                 ok = 1;
 #pragma unroll
-                for (int j = 0; j < Q; j++) {
-                    aF += wgt<R>(j) * (R(1) + pop.F(j, m));
-                    aG += wgt<R>(j) * pop.G(j, m);
-                }
+                for (int j = 0; j < Q; j++) aF += wgt<R>(j) * (R(1) + pop.F(j, m));
+                aG = ph[m] * aF;
             }
         }
         sF = warp_sum(aF);
@@ -650,12 +654,17 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
     const R cu = cx(i) * u[0] + cy(i) * u[1] + cz(i) * u[2];
     const R e = R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
     pop.setF(i, n, rr * e - R(1));
-    pop.setG(i, n, rd * e);
+    if (lane == 0) {
+        ph[n] = rd / rr;
+        B[n] = 0;
+        Nn[n] = Nn[Nt + n] = Nn[2 * Nt + n] = 0;
+    }
 }
 
 template <class S>
 __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int side)
 {
+    using R = typename Store<S>::real;
     const PartDev &P0 = L.parts[blockIdx.y];
     const InstDev &I = L.inst[P0.inst];
     Region reg;
@@ -680,7 +689,8 @@ __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int
             todo &= todo - 1;
             const int X = __shfl_sync(0xffffffffu, x, src), Y = __shfl_sync(0xffffffffu, y, src),
                       Z = __shfl_sync(0xffffffffu, z, src);
-            refill_node<S>(I, L.parts, pop, fli, X, Y, Z, lane);
+            refill_node<S>(I, L.parts, pop, (R *)L.phi + I.node_off, (R *)L.rec + I.node_off,
+                           (R *)L.grad + I.node_off, L.Ntot, fli, X, Y, Z, lane);
         }
     }
 }
@@ -807,7 +817,6 @@ INST(double)
 INST(float)
 INST(__half)
 INST(__nv_bfloat16)
-INST(MixedF16F32)
 #undef INST
 
 }  // namespace lbmg

@@ -21,8 +21,9 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_STATE, LBM_ERR_UNSTABLE,
     LBM_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_OOM", "LBM_ERR_CUDA", "LBM_ERR_STATE", "LBM_ERR_UNSTABLE",
                 "LBM_ERR_TIMEOUT", "LBM_ERR_UNSUPPORTED"]
-# "mixed": total offsets F in half, colour offsets G in FP32
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3, "mixed": 4}
+# storage of the total offsets F; the per-node order parameter, recolouring
+# amplitude and normal are FP64 in the FP64 form and FP32 otherwise
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 FIELD_RHO_A, FIELD_RHO_B, FIELD_PHI, FIELD_U, FIELD_POPS, FIELD_OWNER = 1, 2, 4, 8, 16, 32
 PARTICLE_RECORD = 32
 MAX_PARTICLES = 61
@@ -71,7 +72,7 @@ class lbm_particle(ct.Structure):
 _lib = None
 EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", "lbm_init_fields",
            "lbm_init_fields_device", "lbm_add_particles", "lbm_step", "lbm_particle_forces", "lbm_read_fields",
-           "lbm_read_fields_device", "lbm_num_particles", "lbm_num_nodes", "lbm_diagnostics", "lbm_set_launch",
+           "lbm_read_fields_device", "lbm_num_particles", "lbm_num_nodes", "lbm_diagnostics",
            "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
            "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
@@ -82,8 +83,8 @@ FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
 STAGES = ["phi", "solid_phi", "grad_wetting", "collide", "momentum_exchange", "capillary", "dem", "geom_owner",
           "geom_boundary", "refill", "fused", "particle_region", "curvature", "surrogate", "phi_boundary",
           "collide_boundary"]
-# fluid launch forms of lbm_set_fluid_kernel
-FORM_STAGED, FORM_FUSED, FORM_PLAIN = 0, 1, 2
+# the launch form of lbm_set_fluid_kernel
+FORM_PLAIN = 2
 
 
 def load(path: str = LIB_PATH):
@@ -114,7 +115,6 @@ def load(path: str = LIB_PATH):
     L.lbm_num_nodes.argtypes = [vp, i]
     L.lbm_num_nodes.restype = ct.c_longlong
     L.lbm_diagnostics.argtypes = [vp, i, d]
-    L.lbm_set_launch.argtypes = [vp, i]
     L.lbm_fluid_form_in_use.argtypes = [vp]
     L.lbm_fluid_form_in_use.restype = i
     L.lbm_last_launch_count.argtypes = [vp]
@@ -289,9 +289,6 @@ class Context:
         self._check(self.L.lbm_diagnostics(self.h, inst, _dp(out)))
         return out
 
-    def lbm_set_launch(self, ctas_per_sm=0):
-        self._check(self.L.lbm_set_launch(self.h, int(ctas_per_sm)))
-
     def lbm_set_fluid_kernel(self, form=FORM_PLAIN, tile=0, zchunk=0):
         self._check(self.L.lbm_set_fluid_kernel(self.h, int(form), int(tile), int(zchunk)))
 
@@ -310,10 +307,9 @@ class Context:
         return {name: dict(launches=int(out[2 * k]), ms=float(out[2 * k + 1])) for k, name in enumerate(STAGES)}
 
     def lbm_autotune(self, steps=20):
-        """(form, tile) chosen and the per-candidate ms/step (plain, staged 0-2, fused 0-1, plain 1;
-        -1 unavailable)."""
+        """(form, tile) chosen and the per-candidate ms/step (tile 0, tile 1)."""
         f, t = ct.c_int(), ct.c_int()
-        ms = np.zeros(7)
+        ms = np.zeros(2)
         self._check(self.L.lbm_autotune(self.h, int(steps), ct.byref(f), ct.byref(t), _dp(ms)))
         return (f.value, t.value), ms
 

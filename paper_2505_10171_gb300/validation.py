@@ -1,11 +1,11 @@
 """Benchmarks of the method against closed forms, run through the C ABI.
 
-Capillary detachment (Sec. V E, Scheludko's maximum force): a sphere held at
+Capillary detachment (Sec. V G, benchmarking the capillary force; Scheludko's maximum force): a sphere held at
 its equilibrium height in a flat interface is pulled out at constant speed, and
 the largest capillary force opposing the motion is compared with
 F_max = 2 pi sigma R_p cos^2(theta_p / 2).
 
-Wetting equilibrium (Sec. V D, the particle-at-interface benchmark): a free
+Wetting equilibrium (Sec. V E, wetting boundary condition: the particle-at-interface benchmark): a free
 sphere released halfway through a flat interface settles where the
 interface meets it at the prescribed angle; its height gives the measured
 angle, cos(theta_mes) = (z_i - z_c) / R_p with z_i the far-field interface

@@ -7,7 +7,7 @@ z-major (index = (z*ny + y)*nx + x) and FP64.
 
 The shapes follow the paper's own set-ups (Sec. VI A: a hemispherical drop on
 a flat substrate with a sphere in front of it, periodic in x, y, z; Table I
-parameter ranges; Sec. V F: Segre-Silberberg tube), with the sizes of the
+parameter ranges; Sec. V D: Segre-Silberberg tube), with the sizes of the
 configurations this library is measured on:
 
 * ``cfg1`` - 48x32x32, drop R=10, one sphere R_p=4, 200 steps (parity case).

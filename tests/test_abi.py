@@ -87,8 +87,7 @@ def test_precision_codes_match_header():
     src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     body = re.search(r"typedef enum \{([^}]*)\}\s*lbm_precision;", src).group(1)
     enum = {k: int(v) for k, v in re.findall(r"(LBM_[A-Z0-9_]+)\s*=\s*(\d+)", body)}
-    names = {"fp64": "LBM_FP64", "fp32": "LBM_FP32", "fp16": "LBM_FP16_OFFSET", "bf16": "LBM_BF16_OFFSET",
-             "mixed": "LBM_F16_F32_OFFSET"}
+    names = {"fp64": "LBM_FP64", "fp32": "LBM_FP32", "fp16": "LBM_FP16_OFFSET", "bf16": "LBM_BF16_OFFSET"}
     assert {k: enum[v] for k, v in names.items()} == lbm.PRECISIONS
 
 
@@ -117,5 +116,6 @@ def test_create_rejects_an_unknown_precision(libpath):
     arr = (lbm.lbm_params * 1)(lbm.make_params(**BASE))
     h = ct.c_void_p()
     assert L.lbm_create(arr, 1, 9, None, ct.byref(h)) == 7  # LBM_ERR_UNSUPPORTED
+    assert L.lbm_create(arr, 1, 4, None, ct.byref(h)) == 7  # the former mixed-storage code
     assert L.lbm_create(arr, 0, 1, None, ct.byref(h)) == 1  # no instances: LBM_ERR_ARG
     assert not h.value

@@ -1,4 +1,4 @@
-"""Benchmarks of the method on the GPU.  Capillary detachment (Sec. V E): the largest capillary
+"""Benchmarks of the method on the GPU.  Capillary detachment (Sec. V G): the largest capillary
 force on a sphere pulled out of a flat interface at v_p = 0.01 against
 Scheludko's F_max = 2 pi sigma R_p cos^2(theta_p / 2).  The paper reports
 agreement within 5% at R_p = 25 and errors up to 30% at R_p = 10; the bands
@@ -28,7 +28,7 @@ def test_detachment_force_small_sphere(theta):
 
 
 def test_wetting_equilibrium_large_sphere():
-    """Sec. V D particle-at-interface benchmark: a free sphere released on a
+    """Sec. V E particle-at-interface benchmark: a free sphere released on a
     flat interface settles at the height that gives its contact angle."""
     r = V.wetting_equilibrium(110.0, R_p=25)
     print(r["theta_mes"], r["z_i"], r["z_c"][-1])

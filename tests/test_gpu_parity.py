@@ -106,50 +106,44 @@ def test_fp32_cfg1(cfg1_oracle):
     assert_reduced_parity(run_gpu(w, w["steps"], "fp32"), o, FP32_TOL)
 
 
+def reduced_errors(g, o):
+    fl = common_fluid(g, o)
+    rg = g["fields"]["rho_a"] + g["fields"]["rho_b"]
+    ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
+    return dict(rho=rel_l2(rg[fl], ro[fl]), phi=rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]),
+                u=rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]), F=force_error(g, o))
+
+
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_16bit_offset_cfg1(cfg1_oracle, prec):
+    """16-bit total offsets (the colour part rebuilt from the FP32 per-node
+    order parameter, amplitude and normal): every field and the per-particle
+    force within the 2e-3 bar of reduced-precision storage after 200 steps."""
     w, o = cfg1_oracle
-    g = run_gpu(w, w["steps"], prec)
-    fl = common_fluid(g, o)
-    rg = g["fields"]["rho_a"] + g["fields"]["rho_b"]
-    ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
-    errs = dict(rho=rel_l2(rg[fl], ro[fl]), phi=rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]),
-                u=rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]), F=force_error(g, o))
+    errs = reduced_errors(run_gpu(w, w["steps"], prec), o)
     print(prec, errs)
-    # density and order parameter meet the 2e-3 bar of 16-bit storage; the
-    # velocity and particle force do not yet (half keeps ~2e-6 absolute on the
-    # momentum offsets at |u| ~ 1e-3, bfloat16 only 8 bits): bounded loosely here
-    # and listed as open in the design notes
-    assert errs["rho"] <= HALF_TOL
-    assert errs["phi"] <= (HALF_TOL if prec == "fp16" else 2e-2)
-    assert errs["u"] <= (1e-2 if prec == "fp16" else 1e-1)
-    assert errs["F"] <= (5e-2 if prec == "fp16" else 5e-1)
-
-
-def test_mixed_storage_cfg1_meets_reduced_bar(cfg1_oracle):
-    """Total offsets in half and colour offsets in FP32: every field and the
-    per-particle force within the 2e-3 bar of reduced-precision storage."""
-    w, o = cfg1_oracle
-    g = run_gpu(w, w["steps"], "mixed")
-    fl = common_fluid(g, o)
-    rg = g["fields"]["rho_a"] + g["fields"]["rho_b"]
-    ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
-    errs = dict(rho=rel_l2(rg[fl], ro[fl]), phi=rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]),
-                u=rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]), F=force_error(g, o))
-    print("mixed", errs)
+    if prec == "bf16":
+        # bfloat16 keeps 8 significant bits: the velocity part of the offsets
+        # (|F_i| ~ 3|u|) is held to ~2^-9 relative, which the velocity and the
+        # particle force inherit; density and order parameter meet the bar
+        for k in ("rho", "phi"):
+            assert errs[k] <= HALF_TOL, (k, errs[k])
+        over = {k: round(float(v), 6) for k, v in errs.items() if v > HALF_TOL}
+        if over:
+            pytest.xfail(f"bfloat16 storage above the 2e-3 bar: {over}")
+        return
     for k, v in errs.items():
         assert v <= HALF_TOL, (k, v)
 
 
-def test_mixed_storage_runs_the_plain_form_only():
+def test_only_the_plain_form_exists():
     from paper_2505_10171_gb300 import lbm
-    w = W.cfg1()
-    c = gpu_ctx(w, "mixed")
-    with pytest.raises(lbm.LbmError):
-        c.lbm_set_fluid_kernel(lbm.FORM_STAGED, 0, 0)
-    with pytest.raises(lbm.LbmError):
-        c.lbm_set_fluid_kernel(lbm.FORM_FUSED, 0, 0)
-    c.lbm_set_fluid_kernel(lbm.FORM_PLAIN, 0, 0)
+    c = gpu_ctx(W.cfg1(), "fp16")
+    for form in (0, 1, 3):
+        with pytest.raises(lbm.LbmError) as e:
+            c.lbm_set_fluid_kernel(form, 0, 0)
+        assert e.value.status == lbm.LBM_ERR_ARG
+    c.lbm_set_fluid_kernel(lbm.FORM_PLAIN, 1, 8)
     assert c.lbm_fluid_form_in_use() == lbm.FORM_PLAIN
     c.lbm_step(4)
     c.close()
@@ -190,7 +184,7 @@ def test_fp64_kinematic_sphere_refill():
     assert_fp64_parity(run_gpu(w, 50, "fp64"), o)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_stored_velocity_does_not_change_the_update(prec):
     """Without a stored velocity the owner update runs beside the bulk
     collision; with one it follows it.  A fast prescribed sphere (nodes covered
@@ -221,11 +215,11 @@ def test_fp64_static_tube_mask():
     assert_fp64_parity(run_gpu(w, 20, "fp64"), o)
 
 
-@pytest.mark.parametrize("sizes,form", [
-    (((40, 24, 20, 7.0), (33, 29, 17, 6.0), (24, 24, 24, 5.0)), 2),  # nx = 33: plain form
-    (((48, 24, 20, 7.0), (40, 29, 17, 6.0), (24, 24, 24, 5.0)), 0),  # staged, 5/6/10 rows per item
+@pytest.mark.parametrize("sizes,zchunk", [
+    (((40, 24, 20, 7.0), (33, 29, 17, 6.0), (24, 24, 24, 5.0)), 0),
+    (((48, 24, 20, 7.0), (40, 29, 17, 6.0), (24, 24, 24, 5.0)), 7),  # ragged gradient chunks
 ])
-def test_batched_instances_match_single_runs(sizes, form):
+def test_batched_instances_match_single_runs(sizes, zchunk):
     """Three uneven instances stepped in one context equal three separate runs
     bit for bit, and the oracle within the FP64 bar."""
     from paper_2505_10171_gb300 import lbm
@@ -237,8 +231,7 @@ def test_batched_instances_match_single_runs(sizes, form):
         parts = [dict(x=(nx / 3 + R + 6.0, ny / 2, 4.5), R=3.0, theta_deg=90.0, rho_p=W.PARTICLE_DENSITY)]
         ws.append(dict(params=p, phi=phi, particles=parts))
     c = lbm.Context([w["params"] for w in ws], "fp64")
-    c.lbm_set_fluid_kernel(form)  # the single runs below use the default (plain) form
-    assert c.lbm_fluid_form_in_use() == form
+    c.lbm_set_fluid_kernel(lbm.FORM_PLAIN, 0, zchunk)  # the single runs below use the defaults
     for k, w in enumerate(ws):
         c.lbm_add_particles(w["particles"], inst=k)
         c.lbm_init_fields(w["phi"], inst=k)
@@ -252,10 +245,10 @@ def test_batched_instances_match_single_runs(sizes, form):
         assert_fp64_parity(single, o)
 
 
-def test_mixed_storage_odd_instances_match_single_runs():
-    """Mixed storage pads each instance's population stride to 8 nodes: three
-    instances with odd node counts in one context equal separate runs bit for
-    bit and the oracle within the reduced-precision bar."""
+def test_16bit_odd_instances_match_single_runs():
+    """Three instances with odd node counts (one node per thread: the node-pair
+    kernels need even rows) in FP16 storage in one context equal separate runs
+    bit for bit and the oracle within the reduced-precision bar."""
     from paper_2505_10171_gb300 import lbm
     ws = []
     for k, (nx, ny, nz, R) in enumerate(((33, 29, 17, 6.0), (25, 21, 19, 5.0), (41, 23, 15, 6.0))):
@@ -265,23 +258,19 @@ def test_mixed_storage_odd_instances_match_single_runs():
         phi = W.drop_phi(nx, ny, nz, (nx / 3, ny / 2, 0.5), R)
         parts = [dict(x=(nx / 3 + R + 6.0, ny / 2, 4.5), R=3.0, theta_deg=90.0, rho_p=W.PARTICLE_DENSITY)]
         ws.append(dict(params=p, phi=phi, particles=parts))
-    c = lbm.Context([w["params"] for w in ws], "mixed")
+    c = lbm.Context([w["params"] for w in ws], "fp16")
     for k, w in enumerate(ws):
         c.lbm_add_particles(w["particles"], inst=k)
         c.lbm_init_fields(w["phi"], inst=k)
     c.lbm_step(30)
     for k, w in enumerate(ws):
-        single = run_gpu(w, 30, "mixed")
+        single = run_gpu(w, 30, "fp16")
         fa, fb = c.pops(k)
         assert np.array_equal(fa, single["fa"]) and np.array_equal(fb, single["fb"])
         assert np.array_equal(c.lbm_particle_forces(k), single["parts"])
-        o = run_oracle(w, 30)
-        fl = common_fluid(single, o)
-        rg = single["fields"]["rho_a"] + single["fields"]["rho_b"]
-        ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
-        assert rel_l2(rg[fl], ro[fl]) <= HALF_TOL
-        assert rel_l2(single["fields"]["phi"][fl], o["fields"]["phi"][fl]) <= HALF_TOL
-        assert rel_l2(single["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= HALF_TOL
+        errs = reduced_errors(single, run_oracle(w, 30))
+        for name in ("rho", "phi", "u"):
+            assert errs[name] <= HALF_TOL, (name, errs[name])
     c.close()
 
 
@@ -301,11 +290,11 @@ def test_full_size_cfg2_one_step_fp32():
     assert_reduced_parity(g, o, FP32_TOL)
 
 
-def test_full_size_cfg2_one_step_mixed():
-    """The same in the mixed storage form, against the reduced-precision bar."""
+def test_full_size_cfg2_one_step_fp16():
+    """The same in FP16 storage, against the reduced-precision bar."""
     w = W.cfg2()
     o = run_oracle(w, 1)
-    g = run_gpu(w, 1, "mixed")
+    g = run_gpu(w, 1, "fp16")
     assert_reduced_parity(g, o, HALF_TOL)
 
 
@@ -333,12 +322,10 @@ def test_full_size_batched_sweep_one_step_fp16():
         fl = common_fluid(g, o)
         rg = g["fields"]["rho_a"] + g["fields"]["rho_b"]
         ro = o["fields"]["rho_a"] + o["fields"]["rho_b"]
-        # the bounds of the 16-bit cfg1 test: rho and phi at the 2e-3 bar,
-        # velocity and particle force at FP16's documented 1e-2 / 5e-2
         assert rel_l2(rg[fl], ro[fl]) <= HALF_TOL
         assert rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]) <= HALF_TOL
-        assert rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= 1e-2
-        assert force_error(g, o) <= 5e-2
+        assert rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= HALF_TOL
+        assert force_error(g, o) <= HALF_TOL
 
 
 def test_full_size_tube_one_step_fp32():
@@ -398,8 +385,8 @@ def test_2d_slab_domain_matches_oracle():
     assert_fp64_parity(run_gpu(w, 100, "fp64"), o)
 
 
-# 45: rows not whole 16-byte units (plain form only); 48: five whole rows per
-# staged item with y-wrapped sources; 264: rows cut into two staged segments
+# 45: odd rows (one node per thread); 48: five whole rows per work item with
+# y-wrapped sources; 264: rows cut into two segments
 FORM_SHAPES = [(45, 21, 27), (48, 21, 27), (264, 16, 13)]
 
 
@@ -413,59 +400,42 @@ def _forms_workload(nx, ny, nz):
 
 
 @pytest.mark.parametrize("shape", FORM_SHAPES)
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16", "mixed"])
-def test_launch_forms_agree(prec, shape):
-    """Reference: the plain form with one node per thread.  The staged form
-    (all three variants) gives its bits; the plain form's node-pair collision
-    (16-bit total offsets, even nx) runs the same per-node expressions but the
-    code generator may fuse a different set of multiply-adds in it, so it
-    agrees to the rounding of the storage type; the z-marching fused form
-    (both tiles, several z-chunk sizes, ragged tiles and chunks) gives the same
-    bits in FP32 and agrees to rounding in FP64."""
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_launch_variants_agree(prec, shape):
+    """Reference: one node per thread (tile 1), 16-plane gradient chunks.  The
+    gradient pass gives the same bits for any z-chunk (ragged chunks
+    included).  The node-pair kernels (tile 0: 16-bit storage, even nx) run
+    the same per-node expressions, but the code generator may fuse a different
+    set of multiply-adds in them, so they agree to the rounding of the storage
+    type; elsewhere tile 0 is tile 1."""
     from paper_2505_10171_gb300 import lbm
     w = _forms_workload(*shape)
-    aligned = shape[0] % (16 // {"fp64": 8, "fp32": 4, "fp16": 2, "bf16": 2, "mixed": 2}[prec]) == 0
 
-    def run(form, tile=0, zc=0):
+    def run(tile, zc=0):
         c = gpu_ctx(w, prec)
-        c.lbm_set_fluid_kernel(form, tile, zc)
-        used = c.lbm_fluid_form_in_use()
+        c.lbm_set_fluid_kernel(lbm.FORM_PLAIN, tile, zc)
         c.lbm_step(25)
         fa, fb = c.pops()
         out = (fa, fb, c.lbm_particle_forces(), c.fields()["u"])
         c.close()
-        return used, out
+        return out
 
-    used, ref = run(lbm.FORM_PLAIN, 1)
-    assert used == lbm.FORM_PLAIN
-    used, got = run(lbm.FORM_PLAIN, 0)
+    ref = run(1)
+    for zc in (1, 5, 27):
+        for a, b in zip(ref, run(1, zc)):
+            assert np.array_equal(a, b), ("z-chunk", zc)
+    got = run(0)
     # 25 steps from one FP32 rounding difference per value at most: the
     # populations within a few units of the stored type's last place (half
     # 2^-11, bfloat16 2^-8), the particle forces and the velocity (small
     # differences of populations) within a few tens
-    ulp = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8, "mixed": 2.0 ** -11}.get(prec, 0.0)
+    ulp = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}.get(prec, 0.0) if shape[0] % 2 == 0 else 0.0
     for a, b, k in zip(ref, got, (8, 8, 64, 64)):
         if ulp == 0.0:
             assert np.array_equal(a, b), "node pairs"
         else:
             assert rel_l2(a, b) <= k * ulp, ("node pairs", rel_l2(a, b))
-    if prec == "mixed":
-        return
-    for tile in (0, 1, 2):
-        used, got = run(lbm.FORM_STAGED, tile)
-        assert used == (lbm.FORM_STAGED if aligned else lbm.FORM_PLAIN)
-        for a, b in zip(ref, got):
-            assert np.array_equal(a, b), ("staged", tile)
-    if prec in ("fp16", "bf16"):
-        return
-    for tile, zc in ((0, 0), (1, 5), (0, 7), (1, 27), (0, 1)):
-        used, got = run(lbm.FORM_FUSED, tile, zc)
-        assert used == lbm.FORM_FUSED
-        for a, b in zip(ref, got):
-            if prec == "fp32":
-                assert np.array_equal(a, b), ("fused", tile, zc)
-            else:  # FMA contraction may differ between the two kernels
-                assert np.abs(a - b).max() <= 1e-13 * max(1.0, np.abs(a).max()), ("fused", tile, zc)
+
 
 def test_fp64_drop_speed_control_matches_oracle():
     """Drop-speed control (PI on the phase-a body force, x component, every 10
@@ -491,24 +461,44 @@ def test_fp64_drop_speed_control_matches_oracle():
     assert_fp64_parity(run_gpu(w, 65, "fp64"), o)
 
 
-def test_autotune_picks_a_form_and_keeps_the_trajectory():
-    """The autotuner times all seven launch forms/variants (8 steps each here)
-    and keeps the fastest; since every form gives the same FP32 bits, the state
-    afterwards equals 56 plain steps."""
+def test_autotune_picks_a_variant_and_keeps_the_trajectory():
+    """The autotuner times both bulk-kernel variants (8 steps each here) and
+    keeps the fastest; in FP32 both give the same bits, so the state afterwards
+    equals 16 steps of the default."""
     from paper_2505_10171_gb300 import lbm
     w = _forms_workload(48, 24, 20)
     c = gpu_ctx(w, "fp32")
     (form, tile), ms = c.lbm_autotune(6)
     assert np.all(ms > 0.0), ms
-    assert c.lbm_fluid_form_in_use() == form and ms[
-        {(2, 0): 0, (0, 0): 1, (0, 1): 2, (0, 2): 3, (1, 0): 4, (1, 1): 5, (2, 1): 6}[(form, tile)]] == ms.min()
+    assert form == lbm.FORM_PLAIN and ms[tile] == ms.min()
     fa, fb = c.pops()
     parts = c.lbm_particle_forces()
     c.close()
     c = gpu_ctx(w, "fp32")
-    c.lbm_set_fluid_kernel(lbm.FORM_PLAIN)
-    c.lbm_step(56)
+    c.lbm_step(16)
     ra, rb = c.pops()
     assert np.array_equal(fa, ra) and np.array_equal(fb, rb)
     assert np.array_equal(parts, c.lbm_particle_forces())
     c.close()
+
+
+def test_resume_from_read_populations():
+    """lbm_read_fields(POPS) then lbm_init_fields(pops) in a new context
+    (fluid only): the colour part is recovered from the populations and the
+    continued run equals the uninterrupted one to rounding (FP64)."""
+    w = W.cfg1()
+    w["particles"] = []
+    c = gpu_ctx(w, "fp64")
+    c.lbm_step(40)
+    fa, fb = c.pops()
+    c.lbm_step(30)
+    ref_a, ref_b = c.pops()
+    c.close()
+    r = gpu_ctx(w, "fp64")
+    r.lbm_init_fields(None, pops=np.concatenate([fa, fb]))
+    ga, gb = r.pops()
+    assert np.abs(ga - fa).max() <= 1e-15 and np.abs(gb - fb).max() <= 1e-15
+    r.lbm_step(30)
+    ga, gb = r.pops()
+    r.close()
+    assert max(np.abs(ga - ref_a).max(), np.abs(gb - ref_b).max()) <= 1e-13

@@ -15,7 +15,7 @@ M = RHO_P * 4.0 / 3.0 * math.pi * R ** 3
 
 
 def test_collision_time_matches_paper_step_ratio():
-    """Sec. V G: t_c = pi/omega_c, omega_c = sqrt(k_n/m - (g_n/2m)^2); with the
+    """Sec. V H: t_c = pi/omega_c, omega_c = sqrt(k_n/m - (g_n/2m)^2); with the
     Table I values and m from R_p, Delta t = 1 ~ t_c/45."""
     tc = math.pi / math.sqrt(T1["kn"] / M)
     g = GOLD["dt_over_tc"]

@@ -1,4 +1,4 @@
-"""Interface pins of the oracle: recolouring profile, CSF/Laplace, wetting (Sec. IV, V D)."""
+"""Interface pins of the oracle: recolouring profile, CSF/Laplace, wetting (Sec. IV, V E)."""
 import json
 import math
 import os
@@ -24,7 +24,7 @@ def test_planar_interface_integral_and_profile():
     """At rest, a planar interface settles where, for every x,
     (phi(x+1) - phi(x))/6 = beta k [1 - (phi(x+1)^2 + phi(x)^2)/2], hence
     sum_x (1 - phi^2) = 1/(3 k beta) across one interface; this is the quantity
-    the capillary prefactor of Sec. V E is built on."""
+    the capillary prefactor of Sec. V F is built on."""
     for beta in (0.7, 0.99):
         ph = planar(beta)
         half = len(ph) // 2
@@ -79,7 +79,7 @@ def test_laplace_law_sphere():
 
 
 def test_wetting_rotation_properties():
-    """Sec. V D: the rotated gradient keeps |grad phi|; its direction -n makes the
+    """Sec. V E: the rotated gradient keeps |grad phi|; its direction -n makes the
     prescribed angle with n_s; of n_+ and n_- the one closer to n* is taken."""
     rng = np.random.default_rng(5)
     for _ in range(50):
@@ -118,7 +118,7 @@ def fit_cap_angle(ph, nx, nz, zmin=3):
 
 def test_sessile_contact_angle():
     """A 2-D sessile drop relaxes to the prescribed angle, measured inside phase a,
-    within the paper's stated accuracy (~6%, worst ~16%, Sec. V D/F)."""
+    within the paper's stated accuracy (~6%, worst ~16%, Sec. V E)."""
     nx, nz, R = 72, 28, 11
     X, Z = np.meshgrid(np.arange(nx), np.arange(nz), indexing="xy")
     phi = np.tanh(2 * (R - np.sqrt((X - 36) ** 2 + (Z - 0.5) ** 2)) / 2.5)
@@ -138,7 +138,7 @@ def test_sessile_contact_angle():
 def test_default_capillary_prefactor_gives_sigma_per_unit_line():
     """The default prefactor C = 3 k beta turns the settled planar profile's
     sum (1 - phi^2) into exactly one: a straight contact line of length L
-    across the interface carries sigma L (the line-integral form of Sec. V E);
+    across the interface carries sigma L (the line-integral form of Sec. V F);
     the printed (9/2) k beta would carry 1.5 sigma L."""
     for beta in (0.7, 0.99):
         ph = planar(beta)

@@ -67,7 +67,7 @@ def test_magic_parameter_three_sixteenths():
 
 
 def test_recolouring_constant_k_matches_paper():
-    """k = (1/2) sum_i w_i c_ix^2/|c_i| = (1+sqrt2)/18 ~ 0.134 (Sec. V E)."""
+    """k = (1/2) sum_i w_i c_ix^2/|c_i| = (1+sqrt2)/18 ~ 0.134 (Sec. V F)."""
     c, w, _ = O.lattice()
     norm = np.sqrt((c ** 2).sum(1))
     k = 0.5 * sum(w[i] * c[i, 0] ** 2 / norm[i] for i in range(1, 19))

@@ -92,7 +92,7 @@ def test_capillary_symmetric_interface_zero_force():
 
 
 def test_capillary_matches_surface_integral():
-    """Sec. V E: the Lagrangian-point sum approximates
+    """Sec. V F: the Lagrangian-point sum approximates
     C sigma oint (1 - phi^2) [n_s - (n.n_s) n] dA over the sphere, evaluated here by
     brute-force quadrature of the analytic field of a spherical drop crossing the
     particle (wetting rotation disabled so the gradient is the plain stencil)."""
@@ -285,7 +285,7 @@ def test_torque_balances_fluid_angular_momentum():
 
 
 def test_sphere_wetting_normal_geometry():
-    """Sec. V D with reading c11/c12 on spheres: two spheres of different contact
+    """Sec. V E with reading c11/c12 on spheres: two spheres of different contact
     angle across a flat diffuse interface, 0.7 lu apart.  At every fluid node
     next to a particle with |phi| < 0.99, -grad(phi) after the wetting step has
     the magnitude of the plain stencil gradient and the direction
