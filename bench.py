@@ -144,10 +144,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
-def oracle_sample(budget_s=15.0, steps_cap=None):
-    """Time the FP64 CPU oracle on a sub-box of the workload (host cores)."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def omp_threads(n):
+    """Threads of the oracle's OpenMP loops from now on (its libgomp is the
+    process's); returns the count set, or None if libgomp is not loadable."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+        return int(n)
+    except OSError:
+        return None
+
+
+def oracle_sample(budget_s=15.0, steps_cap=None, threads=None):
+    """Time the FP64 CPU oracle on a sub-box of the workload (host cores; all
+    of them, or `threads`)."""
     import oracle as O
     from paper_2505_10171_gb300 import workloads as W
+    O.lib()
+    cores = omp_threads(threads if threads else os.cpu_count()) or os.cpu_count()
     for dims in ((128, 128, 48), (96, 96, 40), (64, 64, 32)):
         w = W.cfg2_crop(*dims)
         s = O.from_workload(w)
@@ -163,7 +195,7 @@ def oracle_sample(budget_s=15.0, steps_cap=None):
     s.step(n)
     dt = time.perf_counter() - t0
     N = dims[0] * dims[1] * dims[2]
-    cores = os.cpu_count()
+    omp_threads(os.cpu_count())
     return dict(value=N * n / dt / 1e6, unit=UNIT, cores=cores, kind="oracle",
                 sample=f"{n} steps of a {dims[0]}x{dims[1]}x{dims[2]} sub-box of the workload "
                        f"({len(w['particles'])} spheres), FP64 C oracle, OpenMP on {cores} threads",
@@ -253,9 +285,10 @@ def main():
         return
 
     # CPU baseline first (no process forked after the GPU is touched)
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample()
+        cpu1 = oracle_sample(budget_s=10.0, threads=1)
 
     import torch
     torch.cuda.set_device(local)
@@ -332,6 +365,9 @@ def main():
                 gpu_launches=launches, clocks=clk, mass=dict(rho_a=diag[0], rho_b=diag[1]))
     if cpu:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        line["cpu_baseline"]["cpu_model"] = cpu_model()
+        if cpu1:
+            line["cpu_baseline"]["single_thread"] = {k: cpu1[k] for k in ("value", "unit", "cores", "sample")}
 
     if rank == 0:
         line["e2e"] = e2e_measure(torch, lbm, W, args, stream)

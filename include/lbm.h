@@ -58,7 +58,7 @@ typedef enum {
     LBM_ERR_CUDA = 3,        /* CUDA runtime error                              */
     LBM_ERR_STATE = 4,       /* call not valid in the current state             */
     LBM_ERR_UNSTABLE = 5,    /* non-finite/non-positive density seen on device  */
-    LBM_ERR_TIMEOUT = 6,     /* a bounded device wait gave up (staged copies)   */
+    LBM_ERR_TIMEOUT = 6,     /* a bounded device wait gave up (tensor-core GEMM) */
     LBM_ERR_UNSUPPORTED = 7  /* feature or precision not available              */
 } lbm_status;
 
@@ -235,16 +235,16 @@ long long lbm_num_nodes(const lbm_ctx *ctx, int inst);
  * taken so far, out[3] = sticky device status bits.  Synchronises. */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
 
-/* Launch variant of the fluid update.  form must be 2 (plain: order
+/* Launch shape of the fluid update.  form must be 2 (plain: order
  * parameter, solid phi, gradient + wetting + normal + curvature, collision,
  * with the nodes next to a solid in boundary passes beside the bulk kernels).
  * tile 0 (default): with 16-bit storage and an even nx in every instance the
- * bulk order-parameter and collision kernels take two nodes of a row per
- * thread (pair loads and stores), one node per thread otherwise; tile 1: one
- * node per thread always.  zchunk: z-planes per work item of the gradient
- * pass (0: 16).  Every variant computes the same update; the node-pair
- * kernels agree with the one-node kernels to the rounding of the storage type
- * (the code generator may fuse a different set of multiply-adds).  Invalid
+ * bulk collision takes two nodes of a row per thread (pair loads and stores),
+ * one node per thread otherwise; tile 1: one node per thread always.
+ * zchunk: z-planes per work item of the gradient pass (0: 16).  Every shape
+ * computes the same update; the node-pair collision agrees with the one-node
+ * collision to the rounding of the storage type (the code generator may fuse
+ * a different set of multiply-adds), the z-chunk gives the same bits.  Invalid
  * form, tile or zchunk -> LBM_ERR_ARG.  Invalidates the step graph. */
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk);
 
@@ -292,6 +292,19 @@ lbm_status lbm_profile_read(lbm_ctx *ctx, double *out, int max_stages);
  * the one array, so calls that overlap on the GPU race.  Asynchronous; returns
  * LBM_ERR_CUDA if the lookup or a launch fails. */
 lbm_status lbm_component_masses_noalloc(const double *pops, long long n_nodes, double *masses, void *stream);
+
+/* Host-side fault injection, for testing the failure path of the bounded
+ * device waits without a device fault.  fault = LBM_FAULT_GEMM_NO_COMMIT: every
+ * tensor-core GEMM of the surrogate network on this context (predict,
+ * gradient, train, the surrogate force model in a step) issues no MMA and
+ * never signals its commit barrier, so its bounded wait on that barrier
+ * (shortened to about a millisecond) finds nothing arriving, gives up, frees
+ * its tensor memory and sets the sticky device status; the next synchronising
+ * call returns LBM_ERR_TIMEOUT (outputs of the failed call are undefined).
+ * LBM_FAULT_NONE switches it off.  The sticky status stays: create a new
+ * context to continue.  Unknown fault -> LBM_ERR_ARG.  Synchronises. */
+enum { LBM_FAULT_NONE = 0, LBM_FAULT_GEMM_NO_COMMIT = 1 };
+lbm_status lbm_inject_fault(lbm_ctx *ctx, int fault);
 
 /* Drop-speed control state of an instance: out[0..2] the body force on phase
  * a now, out[3..5] U_a at the last update (zeros before the first).

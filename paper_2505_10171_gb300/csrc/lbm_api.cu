@@ -26,9 +26,10 @@ struct lbm_ctx {
     size_t pop_bytes = 0;       // bytes of one population buffer (all instances)
     uint8_t *flags = nullptr;
     void *pop[2] = {nullptr, nullptr};
-    // phis[k]: the order parameter of the state in pop[k] (the step that writes
-    // pop[k] computes it); rec: recolouring amplitude b of the current state
-    void *phis[2] = {nullptr, nullptr}, *rec = nullptr;
+    // phi: the order parameter of the last step; col: the colour record
+    // (phi, b n) of the current state, one per node
+    void *phi = nullptr, *col = nullptr;
+    size_t col_sz = 32;  // bytes of one colour record
     void *grad = nullptr, *gmag = nullptr, *kap = nullptr, *u = nullptr;
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
@@ -111,9 +112,6 @@ static lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m)
                         std::string(#call) + ": " + cudaGetErrorString(e_));                          \
     } while (0)
 
-// the lattice view outside a step: phi is the order parameter of the current
-// state (the one its last step computed); enqueue_step points phi at the other
-// buffer, which the step writes
 static Lattice make_lattice(const lbm_ctx *c)
 {
     Lattice L;
@@ -127,9 +125,8 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.flags = c->flags;
     L.pop[0] = c->pop[0];
     L.pop[1] = c->pop[1];
-    L.phi = c->phis[c->cur];
-    L.phi_src = c->phis[c->cur];
-    L.rec = c->rec;
+    L.phi = c->phi;
+    L.col = c->col;
     L.grad = c->grad;
     L.gmag = c->gmag;
     L.kap = c->kap;
@@ -179,7 +176,8 @@ struct NodeState {
     __device__ double F(int i) const { return (double)pop.F(i, n); }
     __device__ double G(int i) const
     {
-        return (double)C.ph[n] * (1.0 + F(i)) + (i ? (double)C.rec(i, n) : 0.0);
+        const ColRec<R> c = C.at(n);
+        return (double)c.p * (1.0 + F(i)) + (i ? (double)col_rec(i, c) : 0.0);
     }
     __device__ double rr() const
     {
@@ -202,8 +200,8 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
-    R *ph = (R *)L.phi_src + I.node_off, *B = (R *)L.rec + I.node_off, *Nn = (R *)L.grad + I.node_off;
-    const long long Nt = L.Ntot;
+    R *ph = (R *)L.phi + I.node_off;
+    ColRec<R> *col = (ColRec<R> *)L.col + I.node_off;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if (pops) {
             double F[Q], G[Q], sF = 0.0, sG = 0.0;
@@ -226,11 +224,9 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
                 a3[2] += wgt<double>(i) * cz(i) * il * r;
             }
             for (int k = 0; k < 3; k++) a3[k] *= 4.5;
-            const double am = sqrt(a3[0] * a3[0] + a3[1] * a3[1] + a3[2] * a3[2]);
             for (int i = 0; i < Q; i++) pop.setF(i, (int)n, (R)F[i]);
             ph[n] = (R)p;
-            B[n] = (R)am;
-            for (int k = 0; k < 3; k++) Nn[k * Nt + n] = am > 0.0 ? (R)(a3[k] / am) : R(0);
+            col[n] = ColRec<R>{(R)p, (R)a3[0], (R)a3[1], (R)a3[2]};
             continue;
         }
         double p = phi[n];
@@ -245,8 +241,7 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
             pop.setF(i, (int)n, (R)(rr * e - 1.0));
         }
         ph[n] = (R)p;
-        B[n] = R(0);
-        for (int k = 0; k < 3; k++) Nn[k * Nt + n] = R(0);
+        col[n] = ColRec<R>{(R)p, R(0), R(0), R(0)};
         if (I.store_u) {
             R *U = (R *)L.u;
             bool fl = (L.flags[I.node_off + n] & OWNER_MASK) == OWN_FLUID;
@@ -468,7 +463,6 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
 {
     Lattice L = make_lattice(c);
     const int cur = c->cur;
-    L.phi = c->phis[cur ^ 1];  // the order parameter this step computes (that of the next state)
     Marker mk;
     if (c->profile) {
         mk.fn = profile_mark;
@@ -664,9 +658,8 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->flags);
     cudaFree(ctx->pop[0]);
     cudaFree(ctx->pop[1]);
-    cudaFree(ctx->phis[0]);
-    cudaFree(ctx->phis[1]);
-    cudaFree(ctx->rec);
+    cudaFree(ctx->phi);
+    cudaFree(ctx->col);
     cudaFree(ctx->grad);
     cudaFree(ctx->gmag);
     cudaFree(ctx->kap);
@@ -716,6 +709,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         ctx->pop_node_bytes = Pop<S>::node_bytes;
     });
     ctx->real_sz = prec == LBM_FP64 ? 8 : 4;
+    ctx->col_sz = 4 * ctx->real_sz;
     ctx->diag_step.assign(n_instances, -1);
     lbm_status st;
     long long node_off = 0;
@@ -828,8 +822,8 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     const size_t Nt = (size_t)ctx->Ntot;
     if ((st = alloc((void **)&ctx->inst_d, sizeof(InstDev) * n_instances)) ||
         (st = alloc((void **)&ctx->flags, Nt + FLAG_PAD)) || (st = alloc(&ctx->pop[0], ctx->pop_bytes)) ||
-        (st = alloc(&ctx->pop[1], ctx->pop_bytes)) || (st = alloc(&ctx->phis[0], Nt * ctx->real_sz)) ||
-        (st = alloc(&ctx->phis[1], Nt * ctx->real_sz)) || (st = alloc(&ctx->rec, Nt * ctx->real_sz)) ||
+        (st = alloc(&ctx->pop[1], ctx->pop_bytes)) || (st = alloc(&ctx->phi, Nt * ctx->real_sz)) ||
+        (st = alloc(&ctx->col, Nt * ctx->col_sz)) ||
         (st = alloc(&ctx->grad, 3 * Nt * ctx->real_sz)) || (st = alloc(&ctx->gmag, Nt * ctx->real_sz)) || (st = alloc(&ctx->kap, Nt * ctx->real_sz)) || (st = alloc((void **)&ctx->status, sizeof(unsigned))) ||
         (st = alloc((void **)&ctx->diag_d, sizeof(double) * 2 * n_instances)) ||
         (st = alloc((void **)&ctx->diag_part, sizeof(double) * 2 * DIAG_BLOCKS)) ||
@@ -862,9 +856,8 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     }
     cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * n_instances, cudaMemcpyHostToDevice, ctx->stream);
     cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream);
-    cudaMemsetAsync(ctx->phis[0], 0, Nt * ctx->real_sz, ctx->stream);
-    cudaMemsetAsync(ctx->phis[1], 0, Nt * ctx->real_sz, ctx->stream);
-    cudaMemsetAsync(ctx->rec, 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->phi, 0, Nt * ctx->real_sz, ctx->stream);
+    cudaMemsetAsync(ctx->col, 0, Nt * ctx->col_sz, ctx->stream);
     cudaMemsetAsync(ctx->grad, 0, 3 * Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->gmag, 0, Nt * ctx->real_sz, ctx->stream);
     cudaMemsetAsync(ctx->kap, 0, Nt * ctx->real_sz, ctx->stream);
@@ -1578,6 +1571,17 @@ lbm_status lbm_surrogate_features(lbm_ctx *ctx, int inst, float *out)
         CU(cudaStreamSynchronize(ctx->stream));
     }
     return check_status(ctx);
+}
+
+lbm_status lbm_inject_fault(lbm_ctx *ctx, int fault)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (fault != LBM_FAULT_NONE && fault != LBM_FAULT_GEMM_NO_COMMIT)
+        return fail(ctx, LBM_ERR_ARG, "unknown fault");
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->mlp.fault_no_commit = fault == LBM_FAULT_GEMM_NO_COMMIT;
+    drop_graph(ctx);
+    return LBM_OK;
 }
 
 lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out)

@@ -1,5 +1,5 @@
-// Shared-memory barriers and bulk asynchronous copies (PTX), shared by the
-// staged fluid kernels and the tensor-core GEMM of the surrogate network.
+// Shared-memory barriers and bulk asynchronous copies (PTX) of the
+// tensor-core GEMM of the surrogate network.
 // Every wait is bounded (about one second) so that a kernel can report a
 // missing arrival instead of hanging.
 #pragma once
@@ -37,12 +37,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, unsigned parity)
 
 constexpr long long WAIT_CYCLES = 1ll << 31;  // about one second at 2 GHz
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, unsigned parity, long long limit = WAIT_CYCLES)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 

@@ -6,26 +6,33 @@
 // divergence (curvature) -> CSF + body force -> MRT with Guo forcing, evaluated
 // in its two-relaxation-time form -> recolouring -> write.
 //
-// Kernels of a step: k_phi (one thread per node, or k_phi2 with a node pair
-// per thread for 16-bit storage) stores phi; the solid-phi fill over the listed
+// Kernels of a step: k_phi (one thread per node over row strips) stores phi;
+// the solid-phi fill over the listed
 // static solid nodes and the particle cubes; k_gradcurv (z-marching tiles:
 // gradient, wetting, normal, curvature); k_collide (or k_collide2).  Nodes next
 // to a solid go to the boundary passes k_phi_bound and k_collide_bound, which
 // run beside the bulk kernels on a second stream.
 //
-// The state between steps is the total offsets F* (pop[cur]) with phi (the
-// order parameter its collision used), the recolouring amplitude b and the
-// normal n per node: the order-parameter pass rebuilds each pulled colour
-// offset G_i from its source node (lbm_internal.cuh), the collision needs the
-// colour offsets only through phi.
+// The state between steps is the total offsets F* (pop[cur]) with one colour
+// record per node: phi (the order parameter its collision used) and b n (the
+// recolouring amplitude times the normal).  The order-parameter pass rebuilds
+// each pulled colour offset G_i from its source node's record
+// (lbm_internal.cuh); the collision needs the colour offsets only through phi.
 // Storage type S in {double, float, __half, __nv_bfloat16}; arithmetic in
 // double for S = double and float otherwise.
 #include "lbm_node.cuh"
 
 // CTAs of 256 threads per SM the single-precision order-parameter and
-// collision kernels are compiled for (register budget 65536 / (256 x this))
+// collision kernels are compiled for (register budget 65536 / (256 x this)).
+// The order-parameter pass holds 19 pulled offsets and 19 four-value colour
+// records per node: with FP32 offsets 3 CTAs (85 registers) measured faster
+// than 4 (106 against 115 us per 256x128x128 launch), with 16-bit offsets 4
+// (91 against 125 us)
 #ifndef LBM_PHI_MINB
 #define LBM_PHI_MINB 4
+#endif
+#ifndef LBM_PHI_MINB_F32
+#define LBM_PHI_MINB_F32 3
 #endif
 #ifndef LBM_COLLIDE_MINB
 #define LBM_COLLIDE_MINB 4
@@ -68,70 +75,6 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     ((R *)L.phi)[g] = v;
 }
 
-// the order parameter of a node pair (x even, x + 1) per thread, for 16-bit
-// storage: pulls along c_x = 0 as one pair load (of the total offsets and of
-// the sources' phi, b and n), the two phi in one pair store; each node's sums
-// are those of phi_fluid
-template <class S>
-__device__ __forceinline__ void phi_body2(const Lattice &L, const InstDev &I, int cur, int n, int x, int y, int z)
-{
-    using R = typename Store<S>::real;
-    using FT = typename Pop<S>::FT;
-    const long long g = I.node_off + n;  // even
-    const uint8_t fl0 = L.flags[g], fl1 = L.flags[g + 1];
-    const Pop<S> in(L.pop[cur], I);
-    const Colour<R> C(L, I);
-    const int N = in.N;
-    Nbr nb;
-    nb.init(x, y, z, I.nx, I.ny, I.nz);
-    const int xp2 = x + 2 == I.nx ? 0 : x + 2;
-    R sF0 = 0, sG0 = 0, sF1 = 0, sG1 = 0;
-    // sources of the pair along direction i in the row `row`
-    auto pull = [&](auto *row, int i, R &a, R &b) {
-        using T = std::remove_cv_t<std::remove_pointer_t<decltype(row)>>;
-        if (cx(i) == 0) {
-            ld_pair(row + x, a, b);
-        } else if (cx(i) == 1) {
-            a = Store<T>::ld(row + nb.X[0]);
-            b = Store<T>::ld(row + x);
-        } else {
-            a = Store<T>::ld(row + x + 1);
-            b = Store<T>::ld(row + xp2);
-        }
-    };
-#pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const int ro = nb.ZO[1 - cz(i)] + nb.YO[1 - cy(i)];
-        R F0, F1, p0, p1;
-        pull((const FT *)in.f + i * N + ro, i, F0, F1);
-        pull(C.ph + ro, i, p0, p1);
-        R g0 = p0 * (R(1) + F0), g1 = p1 * (R(1) + F1);
-        if (i) {
-            R b0, b1, a0, a1, t0 = 0, t1 = 0;
-            pull(C.b + ro, i, b0, b1);
-            if (cx(i)) { pull(C.n + ro, i, a0, a1); t0 += cx(i) * a0; t1 += cx(i) * a1; }
-            if (cy(i)) { pull(C.n + C.Nt + ro, i, a0, a1); t0 += cy(i) * a0; t1 += cy(i) * a1; }
-            if (cz(i)) { pull(C.n + 2 * C.Nt + ro, i, a0, a1); t0 += cz(i) * a0; t1 += cz(i) * a1; }
-            if (csq(i) != 1) { t0 *= R(0.70710678118654752440); t1 *= R(0.70710678118654752440); }
-            g0 += b0 * t0;
-            g1 += b1 * t1;
-        }
-        sF0 += wgt<R>(i) * F0;
-        sG0 += wgt<R>(i) * g0;
-        sF1 += wgt<R>(i) * F1;
-        sG1 += wgt<R>(i) * g1;
-    }
-    R v0 = sG0 / (R(1) + sF0), v1 = sG1 / (R(1) + sF1);
-    keep(v0);
-    keep(v1);
-    const bool a0 = (fl0 & OWNER_MASK) == OWN_FLUID && !(fl0 & BOUND_BIT);
-    const bool a1 = (fl1 & OWNER_MASK) == OWN_FLUID && !(fl1 & BOUND_BIT);
-    R *ph = (R *)L.phi + g;
-    if (a0 && a1) st_pair(ph, v0, v1);
-    else if (a0) ph[0] = v0;
-    else if (a1) ph[1] = v1;
-}
-
 template <class R>
 __device__ __forceinline__ void solidphi_body(const Lattice &L, const InstDev &I, int n, int x, int y, int z)
 {
@@ -147,27 +90,11 @@ __device__ __forceinline__ void solidphi_body(const Lattice &L, const InstDev &I
 }
 
 template <class S>
-__global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_PHI_MINB) k_phi(Lattice L, int cur)
+__global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? LBM_PHI_MINB_F32 : LBM_PHI_MINB))
+    k_phi(Lattice L, int cur)
 {
     pdl_trigger();  // the gradient pass may be scheduled as this grid drains
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
-}
-
-#ifndef LBM_PHI2_MINB
-#define LBM_PHI2_MINB 6
-#endif
-template <class S>
-__global__ void __launch_bounds__(ROW_NODES / 2, LBM_PHI2_MINB) k_phi2(Lattice L, int cur)
-{
-    pdl_trigger();  // the gradient pass may be scheduled as this grid drains
-    StItem it;
-    st_item(L, blockIdx.x, it);
-    const int j = 2 * (int)threadIdx.x;
-    if (j >= it.cnt) return;
-    const InstDev &I = L.inst[it.k];
-    int x, y;
-    item_node(it, I.nx, j, &x, &y);
-    phi_body2<S>(L, I, cur, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
+    for_item_nodes(L, blockIdx.x, [&](const InstDev &I, int n, int x, int y, int z) { phi_body<S>(L, I, cur, n, x, y, z); });
 }
 
 // instance of global node g (binary search over the node offsets)
@@ -303,8 +230,9 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_collide_bound(Lattice L, in
     load_par(*I, P);
     const R m = ((const R *)L.gmag)[g];
     const R gr[3] = {Nn[n] * m, Nn[Nt + n] * m, Nn[2 * Nt + n] * m};
-    collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, ((const R *)L.kap)[g], out, n, (R *)L.rec + g, U,
-                         L.Ntot, L.status);
+    const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
+    collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, nn, ((const R *)L.kap)[g], out, n,
+                         (ColRec<R> *)L.col + g, U, L.Ntot, L.status);
 }
 
 template <class R>
@@ -346,7 +274,7 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     FluidPar<R> P;
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, phi, gr, kap, out, n, (R *)L.rec + g, U, L.Ntot, L.status);
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, (ColRec<R> *)L.col + g, U, L.Ntot, L.status);
 }
 
 // Node pairs (x even, x + 1) of one row per thread, for 16-bit storage: the
@@ -431,7 +359,11 @@ __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I
             Store<T>::st(p + 1, v1);
         }
     };
-    put((R *)L.rec + g, cA.bq, cB.bq);
+    {
+        ColRec<R> *cr = (ColRec<R> *)L.col + g;
+        if (a0) cr[0] = ColRec<R>{phA, cA.bq * n0.x, cA.bq * n1.x, cA.bq * n2.x};
+        if (a1) cr[1] = ColRec<R>{phB, cB.bq * n0.y, cB.bq * n1.y, cB.bq * n2.y};
+    }
     put(of, collide_rest(P, cA, F0[0]), collide_rest(P, cB, F1[0]));
     PairLoop<R>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value, ib = i + 9;
@@ -456,14 +388,14 @@ __global__ void __launch_bounds__(ROW_NODES / 2, LBM_COLLIDE2_MINB) k_collide2(L
     if (j >= it.cnt) return;
     const InstDev &I = L.inst[it.k];
     int x, y;
-    item_node(it, I.nx, j, &x, &y);
+    item_node(I, it, j, &x, &y);
     collide_body2<S>(L, I, cur, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
 }
 
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MINB) k_collide(Lattice L, int cur)
 {
-    for_item_nodes(L, [&](const InstDev &I, int n, int x, int y, int z) {
+    for_item_nodes(L, blockIdx.x, [&](const InstDev &I, int n, int x, int y, int z) {
         pdl_wait();  // the gradient pass's normals, |grad phi| and curvature
         collide_body<S>(L, I, cur, n, x, y, z);
     });
@@ -481,8 +413,12 @@ __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MI
 // of the fused kernel.
 constexpr int GC_TX = 32, GC_TY = 8, GC_ZC = 16;
 
+// a mod n in [0, n): the in-range and one-period cases without a division
 __device__ __forceinline__ int wrap_any(int a, int n)
 {
+    if (a >= 0 && a < n) return a;
+    if (a < 0 && a >= -n) return a + n;
+    if (a >= n && a < 2 * n) return a - n;
     a %= n;
     return a < 0 ? a + n : a;
 }
@@ -525,9 +461,10 @@ __global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : LBM_GC_MINB
     }
     const InstDev &I = L.inst[k];
     const int loc = (int)(item - I.gc_item_start);
-    const int chunk = loc % I.gc_nchunks;
-    const int t2 = loc / I.gc_nchunks;
-    const int x0 = (t2 % I.gc_tiles_x) * GC_TX, y0 = (t2 / I.gc_tiles_x) * GC_TY;
+    const int t2 = I.fd_nchunks.div(loc);
+    const int chunk = loc - t2 * I.gc_nchunks;
+    const int ty = I.fd_tiles_x.div(t2);
+    const int x0 = (t2 - ty * I.gc_tiles_x) * GC_TX, y0 = ty * GC_TY;
     const int z0 = chunk * I.gc_zc, z1 = min(z0 + I.gc_zc, I.nz);
     const int nx = I.nx, ny = I.ny, nz = I.nz;
     const long long off = I.node_off, Nt = L.Ntot;
@@ -669,6 +606,8 @@ long long plan_gradcurv(std::vector<InstDev> &inst, int zc_request)
         const int zc = std::min(zc_request > 0 ? zc_request : GC_ZC, I.nz);
         I.gc_nchunks = (I.nz + zc - 1) / zc;
         I.gc_zc = (I.nz + I.gc_nchunks - 1) / I.gc_nchunks;
+        I.fd_nchunks.set(I.gc_nchunks);
+        I.fd_tiles_x.set(I.gc_tiles_x);
         I.gc_item_start = items;
         items += (long long)I.gc_tiles_x * I.gc_tiles_y * I.gc_nchunks;
     }
@@ -695,6 +634,9 @@ long long plan_rows(std::vector<InstDev> &inst)
             I.st_nseg = (I.nx + seg - 1) / seg;
         }
         I.st_ygroups = (I.ny + I.st_rows - 1) / I.st_rows;
+        I.fd_plane.set(I.st_ygroups * I.st_nseg);
+        I.fd_nseg.set(I.st_nseg);
+        I.fd_nx.set(I.nx);
         I.st_item_start = total;
         total += (long long)I.nz * I.st_ygroups * I.st_nseg;
     }
@@ -767,15 +709,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         }
         *launches += 1;
     };
-    bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] {
-        if constexpr (sizeof(S) == 2) {
-            if (pair) {
-                k_phi2<S><<<grid, ROW_NODES / 2, 0, st>>>(L, cur);
-                return;
-            }
-        }
-        k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur);
-    });
+    bound_pass(k_phi_bound<S>, STAGE_PHI_BOUND, STAGE_PHI, [&] { k_phi<S><<<grid, ROW_NODES, 0, st>>>(L, cur); });
     if (!fill_done) {
         mk(STAGE_SOLIDPHI, 0);
         fill_solid_phi(st);

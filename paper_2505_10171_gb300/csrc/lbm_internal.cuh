@@ -10,7 +10,8 @@
 // are not stored: the recolouring step (Sec. IV) leaves every node with
 //   G*_i = phi (1 + F*_i) + b (c_i . n)/|c_i|,   b = beta/2 (rho/rho0)(1 - phi^2),
 // phi and n the order parameter and interface normal its collision used, so a
-// state is F* plus phi, b and n per node, and G is rebuilt where it is needed.
+// state is F* plus one record (phi, a = b n) per node, and G is rebuilt where
+// it is needed: G*_i = phi (1 + F*_i) + (c_i . a)/|c_i|.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -62,6 +63,24 @@ constexpr int PART_THREADS = 256;
 constexpr int MEM_PART = 12;
 constexpr int GEOM_MARGIN = 3;  // lattice units a particle may move per step, < this
 
+// division by an integer fixed when the work items are planned (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// q = (mulhi(n, m) + n) >> l with l = ceil(log2 d), m = floor(2^32 (2^l - d)/d) + 1,
+// exact for 0 <= n < 2^31 and 1 <= d < 2^31 (n + mulhi stays below 2^32); a
+// handful of instructions instead of the runtime divide sequence
+struct FastDiv {
+    unsigned d, m;
+    int l;
+    void set(unsigned d_)
+    {
+        d = d_ ? d_ : 1;
+        l = 0;
+        while ((1ull << l) < d) l++;
+        m = (unsigned)((((unsigned long long)1 << 32) * ((1ull << l) - d)) / d + 1);
+    }
+    __device__ __forceinline__ int div(int n) const { return (int)((__umulhi((unsigned)n, m) + (unsigned)n) >> l); }
+};
+
 struct InstDev {
     int nx, ny, nz, np;
     long long N;         // nodes of the instance
@@ -88,12 +107,14 @@ struct InstDev {
     // most st_seg nodes; st_ygroups items cover the y rows of a plane
     long long st_item_start;
     int st_rows, st_seg, st_nseg, st_ygroups;
+    FastDiv fd_plane, fd_nseg, fd_nx;  // st_ygroups st_nseg, st_nseg, nx
     // surrogate inputs: shell gap, velocity and radius scales
     double sh_gap, sh_uref, sh_rref;
     // gradient + curvature work items: gc_tiles_x * gc_tiles_y column tiles x
     // gc_nchunks z-chunks of gc_zc planes
     long long gc_item_start;
     int gc_tiles_x, gc_tiles_y, gc_nchunks, gc_zc;
+    FastDiv fd_nchunks, fd_tiles_x;  // gc_nchunks, gc_tiles_x
     // drop-speed control (body force on phase a): component mask, interval,
     // target velocity, PI gains, base force
     int sp_mask, sp_interval;
@@ -143,11 +164,9 @@ struct Lattice {
     long long n_static_bfl;
     uint8_t *flags;
     void *pop[2];
-    void *phi;           // [Ntot] real: the order parameter this step computes (outside a step: the last one)
-    void *phi_src;       // [Ntot] real: the order parameter of the stored state (its collision's phi)
-    void *rec;           // [Ntot] real: recolouring amplitude b of the stored state
-    void *grad;          // [3][Ntot] real: regularised interface normal n (of the stored state until
-                         //   the gradient pass of the next step rewrites it)
+    void *phi;           // [Ntot] real: the order parameter of the step (outside a step: of the last one)
+    void *col;           // [Ntot] ColRec<real>: colour record (phi, b n) of the stored state
+    void *grad;          // [3][Ntot] real: regularised interface normal n
     void *gmag;          // [Ntot] real: sqrt(|grad phi|^2 + eps^2), so grad phi = n gmag
     void *kap;           // [Ntot] real: curvature div(n) of fluid nodes
     void *u;             // [3][Ntot] real (store_velocity)
@@ -374,30 +393,35 @@ struct GlobalNbr {
     __device__ __forceinline__ int own(int dx, int dy, int dz) const { return fli[nb.at(dx, dy, dz)] & OWNER_MASK; }
 };
 
-// The colour part of the stored state (see the top of this file): per node
-// the order parameter phi of the collision that produced it, the recolouring
-// amplitude b and the interface normal n.  rec(i, m) = b (c_i . n)/|c_i| of
-// node m, so the stored post-collision colour offset is
-// G*_i(m) = phi(m) (1 + F*_i(m)) + rec(i, m).
+// The colour record of a node of the stored state (see the top of this
+// file): the order parameter phi of the collision that produced it and
+// a = b n, one 16-byte (FP64: 32-byte) aligned record, so that a pulled source
+// costs one vector load.
+template <class R>
+struct alignas(4 * sizeof(R)) ColRec {
+    R p, a0, a1, a2;
+};
+
+// (c_i . a)/|c_i|: the colour offset G*_i of a record beyond phi (1 + F*_i)
+template <class R>
+__device__ __forceinline__ R col_rec(int i, const ColRec<R> &c)
+{
+    R t = 0;
+    if (cx(i)) t += cx(i) * c.a0;
+    if (cy(i)) t += cy(i) * c.a1;
+    if (cz(i)) t += cz(i) * c.a2;
+    return csq(i) == 1 ? t : t * R(0.70710678118654752440);
+}
+
+// the colour records of an instance
 template <class R>
 struct Colour {
-    const R *ph, *b, *n;  // instance-relative; n holds three blocks Nt apart
-    long long Nt;
+    const ColRec<R> *c;
     __device__ __forceinline__ Colour(const Lattice &L, const InstDev &I)
-        : ph((const R *)L.phi_src + I.node_off), b((const R *)L.rec + I.node_off),
-          n((const R *)L.grad + I.node_off), Nt(L.Ntot)
+        : c((const ColRec<R> *)L.col + I.node_off)
     {
     }
-    // c_i . n / |c_i| (only the components along c_i are read)
-    __device__ __forceinline__ R cn(int i, int m) const
-    {
-        R t = 0;
-        if (cx(i)) t += cx(i) * n[m];
-        if (cy(i)) t += cy(i) * n[Nt + m];
-        if (cz(i)) t += cz(i) * n[2 * Nt + m];
-        return csq(i) == 1 ? t : t * R(0.70710678118654752440);
-    }
-    __device__ __forceinline__ R rec(int i, int m) const { return b[m] * cn(i, m); }
+    __device__ __forceinline__ ColRec<R> at(int m) const { return c[m]; }
 };
 
 // Pull streaming (Sec. IV) into fluid node n, with the Sec. V A halfway
@@ -409,7 +433,7 @@ struct Colour {
 // With C set, *sG receives sum_i w_i G_i of the streamed colour offsets:
 // G_i(x) = G*_i(x - c_i) from a fluid source; from a solid one
 // G*_ibar(x) + 6 (rho^a - rho^b)(x)/rho0 c_i.u_w, and since
-// (rho^a - rho^b)(x) = phi(x) rho(x) that is phi(x)(1 + F_i(x)) - rec(i, x).
+// (rho^a - rho^b)(x) = phi(x) rho(x) that is phi(x)(1 + F_i(x)) - (c_i . a(x))/|c_i|.
 template <class S, class A>
 __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *parts, const A &nbr,
                                            const Pop<S> &in, const Colour<typename Store<S>::real> *C, int n,
@@ -442,17 +466,17 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
         F[i] = oF[opp(i)] + R(6) * rr * cu;
     }
     if (!C) return;
-    const R phn = C->ph[n];
+    const ColRec<R> cn = C->at(n);
     R g = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         R gi;
         if (own[i] == OWN_FLUID) {
-            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-            gi = C->ph[s] * (R(1) + F[i]);
-            if (i) gi += C->rec(i, s);
+            const ColRec<R> cs = C->at(nbr.idx(-cx(i), -cy(i), -cz(i)));
+            gi = cs.p * (R(1) + F[i]);
+            if (i) gi += col_rec(i, cs);
         } else {
-            gi = phn * (R(1) + F[i]) - C->rec(i, n);
+            gi = cn.p * (R(1) + F[i]) - col_rec(i, cn);
         }
         g += wgt<R>(i) * gi;
     }
@@ -472,9 +496,10 @@ __device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const
     for (int i = 0; i < Q; i++) {
         const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
         const R F = in.F(i, s);
+        const ColRec<R> cs = C.at(s);
         sF += wgt<R>(i) * F;
-        R g = C.ph[s] * (R(1) + F);
-        if (i) g += C.rec(i, s);
+        R g = cs.p * (R(1) + F);
+        if (i) g += col_rec(i, cs);
         sG += wgt<R>(i) * g;
     }
     return sG / (R(1) + sF);
@@ -550,9 +575,9 @@ __device__ __forceinline__ void st_item(const Lattice &L, long long item, StItem
     const int loc = (int)(item - I.st_item_start);  // < 2^31: rows of one instance
     const int per_plane = I.st_ygroups * I.st_nseg;
     it.k = lo;
-    it.z = loc / per_plane;
+    it.z = I.fd_plane.div(loc);
     const int r = loc - it.z * per_plane;
-    const int yg = r / I.st_nseg, sg = r - yg * I.st_nseg;
+    const int yg = I.fd_nseg.div(r), sg = r - yg * I.st_nseg;
     it.y0 = yg * I.st_rows;
     it.whole = I.st_nseg == 1;
     it.nrows = min(I.st_rows, I.ny - it.y0);
@@ -570,25 +595,25 @@ __device__ __forceinline__ long long item_node0(const InstDev &I, const StItem &
 }
 
 // node j of a work item
-__device__ __forceinline__ void item_node(const StItem &it, int nx, int j, int *x, int *y)
+__device__ __forceinline__ void item_node(const InstDev &I, const StItem &it, int j, int *x, int *y)
 {
     int r = 0, xx = it.x0 + j;
     if (it.nrows > 1) {
-        r = j / nx;
-        xx = j - r * nx;
+        r = I.fd_nx.div(j);
+        xx = j - r * I.nx;
     }
     *x = xx;
     *y = it.y0 + r;
 }
 
-// one CTA per work item, launched in item order (so that the CTAs in flight
-// cover a contiguous band of rows and the neighbour rows they share stay in
-// L2): f(I, n, x, y, z) for the CTA's nodes
+// the nodes of work item `item` (CTAs launched in item order cover a
+// contiguous band of rows, so the neighbour rows they share stay in L2):
+// f(I, n, x, y, z) for the CTA's nodes
 template <class F>
-__device__ __forceinline__ void for_item_nodes(const Lattice &L, F &&f)
+__device__ __forceinline__ void for_item_nodes(const Lattice &L, long long item, F &&f)
 {
     StItem it;
-    st_item(L, blockIdx.x, it);
+    st_item(L, item, it);
     const int j = threadIdx.x;
     if (j >= it.cnt) return;
     const InstDev &I = L.inst[it.k];
@@ -600,7 +625,7 @@ __device__ __forceinline__ void for_item_nodes(const Lattice &L, F &&f)
         return;
     }
     int x, y;
-    item_node(it, I.nx, j, &x, &y);
+    item_node(I, it, j, &x, &y);
     f(I, (it.z * I.ny + y) * I.nx + x, x, y, it.z);
 }
 
@@ -643,7 +668,7 @@ struct SideLane {
 // host-side kernel launchers (defined in the .cu files)
 constexpr int FORM_PLAIN = 2;  // the launch form of the fluid update (the value the ABI names)
 struct FluidLaunch {
-    int tile;           // 0: node-pair bulk kernels where possible; 1: one node per thread
+    int tile;           // 0: node-pair bulk collision where possible; 1: one node per thread
     long long rows;     // row-strip work items (all instances): CTAs of each bulk kernel
     long long gc_items; // gradient + curvature work items (all instances)
     bool pair;          // every instance has an even nx: node-pair kernels for 16-bit storage
@@ -698,6 +723,7 @@ struct Mlp {
     double *loss_part = nullptr, *loss = nullptr;     // loss[0]: last batch, loss[1]: accumulator
     int cap = 0;
     long long t = 0;  // Adam steps taken
+    bool fault_no_commit = false;  // host-set fault injection (lbm_inject_fault)
 };
 cudaError_t mlp_alloc(Mlp &m, int cap);
 void mlp_free(Mlp &m);

@@ -130,6 +130,8 @@ struct GemmArgs {
     bf16 *C16;
     long long s16m, s16n;
     unsigned *status;
+    int no_mma;            // fault injection: issue no MMA and no commit (the wait finds nothing arriving)
+    long long wait_limit;  // clock cycles a wait on the commit barrier may take
 };
 
 // one chunk of rows r0.. (ROWS of them) and k0..k0+GK into the canonical layout
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(GM) k_gemm_tc(GemmArgs g)
         stage_tile<BN>(g.B, g.sbn, g.sbk, n0, g.Nv, c * GK, g.Kv, Bs);
         fence_async_smem();
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !g.no_mma) {
             tc_fence_after();
 #pragma unroll
             for (int j = 0; j < GK / 16; j++) {
@@ -197,14 +199,16 @@ __global__ void __launch_bounds__(GM) k_gemm_tc(GemmArgs g)
             }
             tc_commit(bar);
         }
-        ok = mbar_wait_bounded(bar, (unsigned)(c & 1));
+        ok = mbar_wait_bounded(bar, (unsigned)(c & 1), g.wait_limit);
         if (__syncthreads_or(!ok)) break;
         tc_fence_after();
     }
     if (!ok) {
         if (tid == 0) {
             atomicOr(g.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, (unsigned)(c & 1));  // the MMAs of the chunk still in flight
+            // the MMAs of the chunk still in flight (none were issued under the
+            // fault injection) must finish before the tensor memory is freed
+            if (!g.no_mma) mbar_wait_bounded(bar, (unsigned)(c & 1));
         }
     } else if (nchunks > 0) {
         const int m = m0 + warp * 32 + lane;
@@ -277,6 +281,17 @@ GemmArgs gargs(int Mv, int Nv, int Kv, const bf16 *A, long long sam, long long s
     a.A = A; a.sam = sam; a.sak = sak;
     a.B = B; a.sbn = sbn; a.sbk = sbk;
     a.status = status;
+    a.wait_limit = WAIT_CYCLES;
+    return a;
+}
+
+// the GEMM arguments under the network's fault-injection setting: with it on,
+// no MMA is issued and the commit barrier is never signalled, so the bounded
+// wait (shortened to about a millisecond) runs out and reports a timeout
+static GemmArgs mode(GemmArgs a, const Mlp &m)
+{
+    a.no_mma = m.fault_no_commit ? 1 : 0;
+    if (a.no_mma) a.wait_limit = 1ll << 21;
     return a;
 }
 
@@ -444,15 +459,15 @@ cudaError_t mlp_forward(const Mlp &m, int n, unsigned *status, cudaStream_t st)
     // h1 = tanh(X W1^T + b1)
     GemmArgs a = gargs(n, MLP_HIDDEN, MLP_KIN, m.X, MLP_KIN, 1, m.W1b, MLP_KIN, 1, status);
     a.bias = b1; a.act = 1; a.C16 = m.H1; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // h2 = tanh(h1 W2^T + b2)
     a = gargs(n, MLP_HIDDEN, MLP_HIDDEN, m.H1, MLP_HIDDEN, 1, m.W2b, MLP_HIDDEN, 1, status);
     a.bias = b2; a.act = 1; a.C16 = m.H2; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // y = h2 W3^T + b3  ([n][16], columns 6..15 unused)
     a = gargs(n, MLP_NOUT, MLP_HIDDEN, m.H2, MLP_HIDDEN, 1, m.W3b, MLP_HIDDEN, 1, status);
     a.bias = b3; a.C32 = m.Y; a.scm = 16; a.scn = 1;
-    if ((e = gemm<16>(a, n, 16, st)) != cudaSuccess) return e;
+    if ((e = gemm<16>(mode(a, m), n, 16, st)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -466,25 +481,25 @@ cudaError_t mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cud
     // dW3[j][i] = sum_b dY[b][j] h2[b][i]   (M = hidden i, N = output j, K = batch)
     GemmArgs a = gargs(MLP_HIDDEN, MLP_NOUT, n, m.H2, 1, MLP_HIDDEN, m.dYb, 1, 16, status);
     a.C32 = g + MLP_OFF_W3; a.scm = 1; a.scn = MLP_HIDDEN;
-    if ((e = gemm<16>(a, MLP_HIDDEN, 16, st)) != cudaSuccess) return e;
+    if ((e = gemm<16>(mode(a, m), MLP_HIDDEN, 16, st)) != cudaSuccess) return e;
     k_colsum<float><<<MLP_NOUT, EW, 0, st>>>(m.dY, n, 16, g + MLP_OFF_B3);
     // dz2 = (dY W3) * (1 - h2^2)
     a = gargs(n, MLP_HIDDEN, MLP_NOUT, m.dYb, 16, 1, m.W3b, 1, MLP_HIDDEN, status);
     a.act = 2; a.g = m.H2; a.sgm = MLP_HIDDEN; a.sgn = 1; a.C16 = m.dZ2; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // dW2[o][i] = sum_b dz2[b][o] h1[b][i]
     a = gargs(MLP_HIDDEN, MLP_HIDDEN, n, m.dZ2, 1, MLP_HIDDEN, m.H1, 1, MLP_HIDDEN, status);
     a.C32 = g + MLP_OFF_W2; a.scm = MLP_HIDDEN; a.scn = 1;
-    if ((e = gemm<128>(a, MLP_HIDDEN, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<128>(mode(a, m), MLP_HIDDEN, MLP_HIDDEN, st)) != cudaSuccess) return e;
     k_colsum<bf16><<<MLP_HIDDEN, EW, 0, st>>>(m.dZ2, n, MLP_HIDDEN, g + MLP_OFF_B2);
     // dz1 = (dz2 W2) * (1 - h1^2)
     a = gargs(n, MLP_HIDDEN, MLP_HIDDEN, m.dZ2, MLP_HIDDEN, 1, m.W2b, 1, MLP_HIDDEN, status);
     a.act = 2; a.g = m.H1; a.sgm = MLP_HIDDEN; a.sgn = 1; a.C16 = m.dZ1; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(a, n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // dW1[o][i] = sum_b dz1[b][o] x[b][i]
     a = gargs(MLP_HIDDEN, MLP_KIN, n, m.dZ1, 1, MLP_HIDDEN, m.X, 1, MLP_KIN, status);
     a.C32 = g + MLP_OFF_W1; a.scm = MLP_KIN; a.scn = 1;
-    if ((e = gemm<128>(a, MLP_HIDDEN, MLP_KIN, st)) != cudaSuccess) return e;
+    if ((e = gemm<128>(mode(a, m), MLP_HIDDEN, MLP_KIN, st)) != cudaSuccess) return e;
     k_colsum<bf16><<<MLP_HIDDEN, EW, 0, st>>>(m.dZ1, n, MLP_HIDDEN, g + MLP_OFF_B1);
     return cudaSuccess;
 }

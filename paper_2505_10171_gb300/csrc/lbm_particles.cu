@@ -588,10 +588,11 @@ __global__ void k_boundary_full(Lattice L, int inst)
 // 18 moving-direction neighbours that are fluid and not fresh (two hops out if
 // none; ambient (0, rho0) if still none).
 //
-// In the stored form (F* with phi, b, n per node) the refilled state is
-// F_i = (rho/rho0) e_i - 1 with phi = (rho^a - rho^b)/rho and b = 0: its colour
-// offsets (rho^a - rho^b)/rho0 e_i are phi (1 + F_i) exactly.  A neighbour's
-// rho^a - rho^b is phi rho (its colour offsets sum to phi (1 + sum w F)).
+// In the stored form (F* and the colour record (phi, b n) per node) the
+// refilled state is F_i = (rho/rho0) e_i - 1 with the record
+// (phi = (rho^a - rho^b)/rho, 0): its colour offsets (rho^a - rho^b)/rho0 e_i
+// are phi (1 + F_i) exactly.  A neighbour's rho^a - rho^b is phi rho (its
+// colour offsets sum to phi (1 + sum w F)).
 //
 // Few nodes are uncovered per step (about the swept surface area), so the
 // kernel is a scan of the flags plus, per fresh node, one warp working on it:
@@ -607,8 +608,8 @@ __device__ __forceinline__ R warp_sum(R v)
 
 template <class S>
 __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S> &pop,
-                            typename Store<S>::real *ph, typename Store<S>::real *B, typename Store<S>::real *Nn,
-                            long long Nt, const uint8_t *fli, int x, int y, int z, int lane)
+                            typename Store<S>::real *ph, ColRec<typename Store<S>::real> *col, const uint8_t *fli,
+                            int x, int y, int z, int lane)
 {
     using R = typename Store<S>::real;
     R sF = 0, sG = 0;
@@ -627,7 +628,7 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
                 ok = 1;
 #pragma unroll
                 for (int j = 0; j < Q; j++) aF += wgt<R>(j) * (R(1) + pop.F(j, m));
-                aG = ph[m] * aF;
+                aG = col[m].p * aF;
             }
         }
         sF = warp_sum(aF);
@@ -656,8 +657,7 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
     pop.setF(i, n, rr * e - R(1));
     if (lane == 0) {
         ph[n] = rd / rr;
-        B[n] = 0;
-        Nn[n] = Nn[Nt + n] = Nn[2 * Nt + n] = 0;
+        col[n] = ColRec<R>{rd / rr, R(0), R(0), R(0)};
     }
 }
 
@@ -689,8 +689,8 @@ __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int
             todo &= todo - 1;
             const int X = __shfl_sync(0xffffffffu, x, src), Y = __shfl_sync(0xffffffffu, y, src),
                       Z = __shfl_sync(0xffffffffu, z, src);
-            refill_node<S>(I, L.parts, pop, (R *)L.phi + I.node_off, (R *)L.rec + I.node_off,
-                           (R *)L.grad + I.node_off, L.Ntot, fli, X, Y, Z, lane);
+            refill_node<S>(I, L.parts, pop, (R *)L.phi + I.node_off, (ColRec<R> *)L.col + I.node_off, fli, X, Y, Z,
+                           lane);
         }
     }
 }

@@ -76,10 +76,12 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_last_launch_count", "lbm_profile", "lbm_profile_read", "lbm_component_masses_noalloc",
            "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
-           "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion"]
+           "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion",
+           "lbm_inject_fault"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
+FAULT_NONE, FAULT_GEMM_NO_COMMIT = 0, 1
 STAGES = ["phi", "solid_phi", "grad_wetting", "collide", "momentum_exchange", "capillary", "dem", "geom_owner",
           "geom_boundary", "refill", "fused", "particle_region", "curvature", "surrogate", "phi_boundary",
           "collide_boundary"]
@@ -134,6 +136,7 @@ def load(path: str = LIB_PATH):
     L.lbm_surrogate_features.argtypes = [vp, i, fp]
     L.lbm_drop_speed_state.argtypes = [vp, i, d]
     L.lbm_autotune.argtypes = [vp, i, P(ct.c_int), P(ct.c_int), d]
+    L.lbm_inject_fault.argtypes = [vp, i]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
                         "lbm_last_launch_count"):
@@ -312,6 +315,9 @@ class Context:
         ms = np.zeros(2)
         self._check(self.L.lbm_autotune(self.h, int(steps), ct.byref(f), ct.byref(t), _dp(ms)))
         return (f.value, t.value), ms
+
+    def lbm_inject_fault(self, fault):
+        self._check(self.L.lbm_inject_fault(self.h, int(fault)))
 
     def lbm_drop_speed_state(self, inst=0):
         out = np.zeros(6)

@@ -144,3 +144,29 @@ def test_coarse_campaign_pipeline():
     assert rec["losses"][-1] < rec["losses"][0]
     for k in ("offline", "plain_coarse", "surrogate_coarse"):
         assert np.all(np.isfinite(table[k]))
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """The failure path of the tensor-core GEMM's bounded wait, with no device
+    fault: under the host-set injection the GEMM issues no MMA and never
+    signals its commit barrier, the wait runs out, the kernel frees its tensor
+    memory and returns, and the call reports LBM_ERR_TIMEOUT.  The GPU stays
+    usable: a fresh context computes the same forward pass as before."""
+    from paper_2505_10171_gb300 import lbm
+    th = M.init_params(8)
+    X = np.random.default_rng(3).normal(size=(150, M.N_IN)).astype(np.float32)
+    c = _host()
+    c.lbm_surrogate_load(th)
+    Y0 = c.lbm_surrogate_predict(X)
+    c.lbm_inject_fault(lbm.FAULT_GEMM_NO_COMMIT)
+    with pytest.raises(lbm.LbmError) as e:
+        c.lbm_surrogate_predict(X)
+    assert e.value.status == lbm.LBM_ERR_TIMEOUT
+    with pytest.raises(lbm.LbmError) as e:
+        c.lbm_inject_fault(7)
+    assert e.value.status == lbm.LBM_ERR_ARG
+    c.close()
+    c = _host()
+    c.lbm_surrogate_load(th)
+    assert np.array_equal(c.lbm_surrogate_predict(X), Y0)
+    c.close()
