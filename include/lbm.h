@@ -248,12 +248,19 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, int inst, double *out);
  * form, tile or zchunk -> LBM_ERR_ARG.  Invalidates the step graph. */
 lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk);
 
-/* Autotuner: steps the simulation `steps` times (>= 2) with each bulk-kernel
- * variant (tile 0, tile 1), timing each with CUDA events on the context
- * stream, and keeps the fastest.  The simulation advances by all the trial
- * steps.  *form and *tile receive the choice; ms_per_step (may be NULL)
- * receives the 2 times.  Synchronises. */
-lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step);
+/* Autotuner of the launch shape, on the context's own instances.  Instances
+ * fall into size classes by nz (<= 64, <= 96, <= 128, larger); for each class
+ * present, the z-planes per work item of the gradient pass are chosen from 8,
+ * 16 and 32 (the other classes held at their current choice), then the
+ * bulk-kernel variant (tile 0, 1).  Each candidate is re-planned, its step
+ * graph captured and warmed up for 2 steps, then timed over `steps` (>= 2)
+ * steps with CUDA events on the context stream; the fastest is kept.  The
+ * simulation advances by all the trial steps (every shape computes the same
+ * update).  *tile receives the variant; zchunks (may be NULL) one z-chunk per
+ * instance; ms_best (may be NULL) the ms per step of the chosen shape.
+ * lbm_set_fluid_kernel afterwards replaces the per-class choice by one
+ * z-chunk for all.  Synchronises. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *tile, int *zchunks, double *ms_best);
 
 /* The fluid-update form the next step runs (2); -1 for a null context. */
 int lbm_fluid_form_in_use(const lbm_ctx *ctx);

@@ -63,7 +63,8 @@ struct lbm_ctx {
     cudaEvent_t ev_open[N_STAGES] = {};
     // launch variant of the fluid update
     FluidLaunch fz = {0, 0, 0, false};
-    int zc_request = 0;  // z-planes per gradient work item, 0: automatic
+    int zc_request = 0;        // z-planes per gradient work item, 0: automatic
+    std::vector<int> zc_inst;  // per instance (the autotuner's size classes), 0: zc_request
     // drop-speed control: per instance integral (3) and last U_a (3); block partials
     double *speed_d = nullptr;
     double *speed_part = nullptr;
@@ -87,7 +88,7 @@ struct lbm_ctx {
 // when every row has an even length
 static void plan_launch(lbm_ctx *c)
 {
-    c->fz.gc_items = plan_gradcurv(c->inst_h, c->zc_request);
+    c->fz.gc_items = plan_gradcurv(c->inst_h, c->zc_request, c->zc_inst);
     c->fz.rows = plan_rows(c->inst_h);
     bool even = true;
     for (const auto &I : c->inst_h) even = even && I.nx % 2 == 0;
@@ -1326,6 +1327,7 @@ lbm_status lbm_set_fluid_kernel(lbm_ctx *ctx, int form, int tile, int zchunk)
     CU(cudaMemcpy(ctx->inst_h.data(), ctx->inst_d, sizeof(InstDev) * ctx->n_inst, cudaMemcpyDeviceToHost));
     ctx->fz.tile = tile;
     ctx->zc_request = zchunk;
+    ctx->zc_inst.clear();
     plan_launch(ctx);
     CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -1599,43 +1601,86 @@ lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out)
     return LBM_OK;
 }
 
-lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *form, int *tile, double *ms_per_step)
+// size class of an instance for the autotuner: its nz in buckets (the
+// gradient pass's z-chunk divides nz)
+static int size_class(int nz) { return nz <= 64 ? 0 : (nz <= 96 ? 1 : (nz <= 128 ? 2 : 3)); }
+
+lbm_status lbm_autotune(lbm_ctx *ctx, int steps, int *tile, int *zchunks, double *ms_best)
 {
-    if (!ctx || !form || !tile || steps < 2) return fail(ctx, LBM_ERR_ARG, "autotune needs steps >= 2 and outputs");
-    const int ncand = 2;
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
-    double best = -1.0;
-    int bt = 0;
+    if (!ctx || !tile || steps < 2) return fail(ctx, LBM_ERR_ARG, "autotune needs steps >= 2 and a tile output");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        cudaGetLastError();
+        return fail(ctx, LBM_ERR_CUDA, "autotune: event creation");
+    }
     lbm_status st = LBM_OK;
-    for (int k = 0; k < ncand && st == LBM_OK; k++) {
-        if (ms_per_step) ms_per_step[k] = -1.0;
-        if ((st = lbm_set_fluid_kernel(ctx, FORM_PLAIN, k, ctx->zc_request)) != LBM_OK) break;
-        if ((st = lbm_step(ctx, 2)) != LBM_OK) break;  // capture and warm up
-        cudaEventRecord(e0, ctx->stream);
-        if ((st = lbm_step(ctx, steps)) != LBM_OK) break;
-        cudaEventRecord(e1, ctx->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            st = fail(ctx, LBM_ERR_CUDA, "autotune: event");
-            break;
+    // ms per step of the current shape (re-planned, captured and warmed up)
+    auto time_shape = [&](double *ms) -> lbm_status {
+        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaMemcpy(ctx->inst_h.data(), ctx->inst_d, sizeof(InstDev) * ctx->n_inst, cudaMemcpyDeviceToHost));
+        plan_launch(ctx);
+        CU(cudaMemcpy(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice));
+        drop_graph(ctx);
+        lbm_status s = lbm_step(ctx, 2);
+        if (s != LBM_OK) return s;
+        CU(cudaEventRecord(e0, ctx->stream));
+        if ((s = lbm_step(ctx, steps)) != LBM_OK) return s;
+        CU(cudaEventRecord(e1, ctx->stream));
+        CU(cudaEventSynchronize(e1));
+        float m = 0.0f;
+        CU(cudaEventElapsedTime(&m, e0, e1));
+        *ms = m / steps;
+        return LBM_OK;
+    };
+    // 1. the gradient pass's z-chunk per size class (coordinate descent over
+    // the classes present, the others held at their current choice)
+    ctx->zc_inst.assign(ctx->n_inst, 0);
+    bool present[4] = {false, false, false, false};
+    for (const auto &I : ctx->inst_h) present[size_class(I.nz)] = true;
+    const int cand[3] = {8, 16, 32};
+    double best = -1.0;
+    for (int c = 0; c < 4 && st == LBM_OK; c++) {
+        if (!present[c]) continue;
+        int bz = 0;
+        double bc = -1.0;
+        for (int z : cand) {
+            for (int k = 0; k < ctx->n_inst; k++)
+                if (size_class(ctx->inst_h[k].nz) == c) ctx->zc_inst[k] = z;
+            double ms = 0.0;
+            if ((st = time_shape(&ms)) != LBM_OK) break;
+            if (bc < 0.0 || ms < bc) {
+                bc = ms;
+                bz = z;
+            }
         }
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        const double per = ms / steps;
-        if (ms_per_step) ms_per_step[k] = per;
-        if (best < 0.0 || per < best) {
-            best = per;
-            bt = k;
+        for (int k = 0; k < ctx->n_inst; k++)
+            if (size_class(ctx->inst_h[k].nz) == c) ctx->zc_inst[k] = bz;
+        best = bc;
+    }
+    // 2. the bulk-kernel variant
+    (void)best;
+    int bt = 0;
+    double bestt = -1.0;
+    for (int t = 0; t < 2 && st == LBM_OK; t++) {
+        ctx->fz.tile = t;
+        double ms = 0.0;
+        if ((st = time_shape(&ms)) != LBM_OK) break;
+        if (bestt < 0.0 || ms < bestt) {
+            bestt = ms;
+            bt = t;
         }
     }
+    ctx->fz.tile = bt;
+    double ms = 0.0;
+    if (st == LBM_OK) st = time_shape(&ms);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != LBM_OK) return st;
-    *form = FORM_PLAIN;
     *tile = bt;
-    st = lbm_set_fluid_kernel(ctx, FORM_PLAIN, bt, ctx->zc_request);
-    if (st != LBM_OK) return st;
+    if (zchunks)
+        for (int k = 0; k < ctx->n_inst; k++) zchunks[k] = ctx->inst_h[k].gc_zc;
+    if (ms_best) *ms_best = ms;
     return check_status(ctx);
 }
 

@@ -597,13 +597,15 @@ __global__ void __launch_bounds__(GC_TX *GC_TY, sizeof(R) == 8 ? 2 : LBM_GC_MINB
     }
 }
 
-long long plan_gradcurv(std::vector<InstDev> &inst, int zc_request)
+long long plan_gradcurv(std::vector<InstDev> &inst, int zc_request, const std::vector<int> &zc_inst)
 {
     long long items = 0;
-    for (auto &I : inst) {
+    for (size_t k = 0; k < inst.size(); k++) {
+        InstDev &I = inst[k];
+        const int req = k < zc_inst.size() && zc_inst[k] > 0 ? zc_inst[k] : zc_request;
         I.gc_tiles_x = (I.nx + GC_TX - 1) / GC_TX;
         I.gc_tiles_y = (I.ny + GC_TY - 1) / GC_TY;
-        const int zc = std::min(zc_request > 0 ? zc_request : GC_ZC, I.nz);
+        const int zc = std::min(req > 0 ? req : GC_ZC, I.nz);
         I.gc_nchunks = (I.nz + zc - 1) / zc;
         I.gc_zc = (I.nz + I.gc_nchunks - 1) / I.gc_nchunks;
         I.fd_nchunks.set(I.gc_nchunks);

@@ -674,8 +674,8 @@ struct FluidLaunch {
     bool pair;          // every instance has an even nx: node-pair kernels for 16-bit storage
 };
 // plan the work items of the gradient + curvature kernel (z-planes per item:
-// zc_request, 0 for the default)
-long long plan_gradcurv(std::vector<InstDev> &inst, int zc_request);
+// zc_inst[k] for instance k where set (> 0), else zc_request, else the default)
+long long plan_gradcurv(std::vector<InstDev> &inst, int zc_request, const std::vector<int> &zc_inst);
 // plan the row-strip work items of every instance; returns their number
 long long plan_rows(std::vector<InstDev> &inst);
 template <class S>

@@ -310,11 +310,12 @@ class Context:
         return {name: dict(launches=int(out[2 * k]), ms=float(out[2 * k + 1])) for k, name in enumerate(STAGES)}
 
     def lbm_autotune(self, steps=20):
-        """(form, tile) chosen and the per-candidate ms/step (tile 0, tile 1)."""
-        f, t = ct.c_int(), ct.c_int()
-        ms = np.zeros(2)
-        self._check(self.L.lbm_autotune(self.h, int(steps), ct.byref(f), ct.byref(t), _dp(ms)))
-        return (f.value, t.value), ms
+        """(tile, z-chunk per instance, ms per step of the chosen shape)."""
+        t = ct.c_int()
+        zc = (ct.c_int * self.n_inst)()
+        ms = np.zeros(1)
+        self._check(self.L.lbm_autotune(self.h, int(steps), ct.byref(t), zc, _dp(ms)))
+        return t.value, list(zc), float(ms[0])
 
     def lbm_inject_fault(self, fault):
         self._check(self.L.lbm_inject_fault(self.h, int(fault)))

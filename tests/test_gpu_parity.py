@@ -73,9 +73,10 @@ def assert_reduced_parity(g, o, tol):
     assert rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]) <= tol
     assert rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= tol
     if len(o["parts"]):
-        # the per-particle force drifts with the particle trajectory (4e-9 at
-        # step 1, 4e-6 at step 200 against forces ~1e-2 in cfg1); bounded at 5x
-        # the field bar and listed as open in the design notes
+        # FP32: the momentum-exchange part meets the bar, the capillary part
+        # (whose surface integral cancels about 14:1 at the contact line) does
+        # not; test_gpu_force_replay.py separates the two on a common
+        # trajectory.  Bounded at 5x the bar (3.3e-4 measured on cfg1)
         assert force_error(g, o) <= 5 * tol
 
 
@@ -461,24 +462,37 @@ def test_fp64_drop_speed_control_matches_oracle():
     assert_fp64_parity(run_gpu(w, 65, "fp64"), o)
 
 
-def test_autotune_picks_a_variant_and_keeps_the_trajectory():
-    """The autotuner times both bulk-kernel variants (8 steps each here) and
-    keeps the fastest; in FP32 both give the same bits, so the state afterwards
-    equals 16 steps of the default."""
+def test_autotune_picks_shapes_per_size_class_and_keeps_the_trajectory():
+    """The autotuner chooses the gradient pass's z-chunk per size class (nz
+    buckets) and the bulk variant, timing each candidate on the context's own
+    instances; in FP32 every shape gives the same bits, so the state afterwards
+    equals the same number of default steps: 3 instances in 3 size classes,
+    3 z-chunks per class + 2 variants + the final shape, 8 steps each."""
     from paper_2505_10171_gb300 import lbm
-    w = _forms_workload(48, 24, 20)
-    c = gpu_ctx(w, "fp32")
-    (form, tile), ms = c.lbm_autotune(6)
-    assert np.all(ms > 0.0), ms
-    assert form == lbm.FORM_PLAIN and ms[tile] == ms.min()
-    fa, fb = c.pops()
-    parts = c.lbm_particle_forces()
+    ws = [_forms_workload(32, 24, nz) for nz in (20, 72, 100)]
+    c = lbm.Context([w["params"] for w in ws], "fp32")
+    for k, w in enumerate(ws):
+        c.lbm_add_particles(w["particles"], inst=k)
+        c.lbm_init_fields(w["phi"], inst=k)
+    tile, zc, ms = c.lbm_autotune(6)
+    assert tile in (0, 1) and ms > 0.0
+
+    def balanced(req, nz):  # chunks of equal size: ceil(nz / ceil(nz / min(req, nz)))
+        z = min(req, nz)
+        return -(-nz // -(-nz // z))
+
+    for k, nz in enumerate((20, 72, 100)):
+        assert zc[k] in {balanced(r, nz) for r in (8, 16, 32)}, (k, zc)
+    got = [c.pops(k) for k in range(3)]
     c.close()
-    c = gpu_ctx(w, "fp32")
-    c.lbm_step(16)
-    ra, rb = c.pops()
-    assert np.array_equal(fa, ra) and np.array_equal(fb, rb)
-    assert np.array_equal(parts, c.lbm_particle_forces())
+    c = lbm.Context([w["params"] for w in ws], "fp32")
+    for k, w in enumerate(ws):
+        c.lbm_add_particles(w["particles"], inst=k)
+        c.lbm_init_fields(w["phi"], inst=k)
+    c.lbm_step((3 * 3 + 2 + 1) * 8)
+    for k in range(3):
+        fa, fb = c.pops(k)
+        assert np.array_equal(fa, got[k][0]) and np.array_equal(fb, got[k][1]), k
     c.close()
 
 
