@@ -373,6 +373,8 @@ def main():
         line["e2e"] = e2e_measure(torch, lbm, W, args, stream)
         if not args.no_extra and world == 1:
             line["extra"] = extra_measure(torch, lbm, W, args, stream, N)
+            for prec in ("fp16", "bf16"):
+                line["extra"][prec]["speedup_over_fp32_step"] = line["extra"][prec]["value"] / value
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -421,23 +423,81 @@ def extra_measure(torch, lbm, W, args, stream, N):
         out[prec] = dict(value=N * K / (ms_g * 1e-3) / 1e6, value_profiled=N * K / (ms * 1e-3) / 1e6,
                          collide_ms=cms, collide_gbs=design_bytes_per_node("collide", prec) * N / (cms * 1e-3) / 1e9,
                          steps=K)
-    ws = W.cfg4()
-    params = [dict(w["params"], store_velocity=0) for w in ws]
-    for prec in ("fp16",):
-        ctx = lbm.Context(params, prec, stream=stream.cuda_stream)
-        nodes = 0
-        for k, w in enumerate(ws):
-            ctx.lbm_add_particles(w["particles"], inst=k)
-            ctx.lbm_init_fields(w["phi"], inst=k)
-            nodes += ctx.num_nodes(k)
-        ctx.lbm_step(args.warmup)
-        Kb = max(20, args.steps // 20)
-        ms_g, _, _ = timed_steps(torch, ctx, stream, Kb, profile=False)
-        ctx.close()
-        out["batched_" + prec] = dict(value=nodes * Kb / (ms_g * 1e-3) / 1e6, unit=UNIT, instances=len(ws),
-                                      nodes=nodes, steps=Kb)
+    out["batched"] = batched_measure(torch, lbm, W, args, stream)
     out["stated_error"] = error_measure(lbm, W, stream)
     return out
+
+
+def batched_measure(torch, lbm, W, args, stream):
+    """The 96-instance sweep of uneven domains: one batched FP16 context with
+    the autotuned launch shape (graph-captured steps), against the same
+    instances stepped one at a time as plain FP32 contexts (the per-instance
+    baseline), both timed with CUDA events over the same number of steps after
+    warm-up.  Accuracy: the smallest and the largest instance after the same
+    steps from the same start, batched FP16 and single FP32 each against a
+    single FP64 run (phi, u over common fluid nodes)."""
+    import numpy as np
+
+    ws = W.cfg4()
+    warm, Kb = 20, max(20, args.steps // 20)
+    params = [dict(w["params"], store_velocity=1) for w in ws]
+
+    def one(k, prec):
+        c = lbm.Context(params[k], prec, stream=stream.cuda_stream)
+        c.lbm_add_particles(ws[k]["particles"])
+        c.lbm_init_fields(ws[k]["phi"])
+        return c
+
+    ctx = lbm.Context(params, "fp16", stream=stream.cuda_stream)
+    nodes = 0
+    for k, w in enumerate(ws):
+        ctx.lbm_add_particles(w["particles"], inst=k)
+        ctx.lbm_init_fields(w["phi"], inst=k)
+        nodes += ctx.num_nodes(k)
+    tile, zc, _ = ctx.lbm_autotune(4)
+    tuned_steps = ctx.lbm_diagnostics()[2]
+    ms_b, _, launches = timed_steps(torch, ctx, stream, Kb, profile=False)
+    steps_b = ctx.lbm_diagnostics()[2]
+    sizes = [ctx.num_nodes(k) for k in range(len(ws))]
+    picks = sorted({int(np.argmin(sizes)), int(np.argmax(sizes))})
+    got16 = {k: (ctx.fields(k), ctx.owner(k)) for k in picks}
+    ctx.close()
+    # per-instance plain FP32 runs, one context at a time
+    total_ms = 0.0
+    for k in range(len(ws)):
+        c = one(k, "fp32")
+        c.lbm_step(warm)
+        ms, _, _ = timed_steps(torch, c, stream, Kb, profile=False)
+        total_ms += ms
+        c.close()
+    acc = {}
+    for k in picks:
+        ref = one(k, "fp64")
+        ref.lbm_step(int(steps_b))
+        f0, o0 = ref.fields(), ref.owner()
+        ref.close()
+        c = one(k, "fp32")
+        c.lbm_step(int(steps_b))
+        f32, o32 = c.fields(), c.owner()
+        c.close()
+        f16, o16 = got16[k]
+
+        def rl2(a, b):
+            return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+        e = {}
+        for name, f, o in (("batched_fp16", f16, o16), ("single_fp32", f32, o32)):
+            fl = (o0 == 0) & (o == 0)
+            e[name] = dict(phi=rl2(f["phi"][fl], f0["phi"][fl]), u=rl2(f["u"][:, fl], f0["u"][:, fl]))
+        acc[f"instance {k} ({sizes[k]} nodes)"] = e
+    value = nodes * Kb / (ms_b * 1e-3) / 1e6
+    base = nodes * Kb / (total_ms * 1e-3) / 1e6
+    return dict(value=value, unit=UNIT, instances=len(ws), nodes=nodes, steps=Kb, launches_per_step=launches / Kb,
+                shape=dict(tile=tile, grad_zchunk_per_instance=sorted(set(zc)), autotune_steps=int(tuned_steps)),
+                per_instance_fp32=dict(value=base, unit=UNIT, note="96 plain FP32 contexts run one after another, "
+                                       "same steps each after %d warm-up steps" % warm),
+                speedup_over_per_instance_fp32=value / base,
+                error_vs_fp64_after_steps=int(steps_b), accuracy=acc)
 
 
 def error_measure(lbm, W, stream):
