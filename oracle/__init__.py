@@ -48,6 +48,7 @@ class OrParams(ct.Structure):
         ("grad_eps", ct.c_double), ("wet_phi_max", ct.c_double),
         ("drop_speed_control", ct.c_int), ("drop_speed_target", ct.c_double * 3),
         ("drop_speed_kp", ct.c_double), ("drop_speed_ki", ct.c_double), ("drop_speed_interval", ct.c_int),
+        ("pressure_z", ct.c_int), ("rho_in", ct.c_double), ("rho_out", ct.c_double),
     ]
 
 
@@ -122,7 +123,7 @@ DEFAULTS = dict(
     kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0,
     g_particle=(0.0, 0.0, 0.0), grad_eps=1e-4, wet_phi_max=0.99,
     drop_speed_control=0, drop_speed_target=(0.0, 0.0, 0.0), drop_speed_kp=0.0, drop_speed_ki=0.0,
-    drop_speed_interval=0,
+    drop_speed_interval=0, pressure_z=0, rho_in=1.0, rho_out=1.0,
 )
 
 
@@ -306,7 +307,7 @@ def omega_of_phi(phi, rho, **kw):
 SIM_KEYS = ("wall_z0", "wall_velocity", "theta_wall_deg", "rho0", "nu_a", "nu_b", "sigma", "beta",
             "body_force_a", "body_force_b", "kn", "kt", "kr", "gn", "gt", "gr", "mu_s", "mu_r", "delta_R",
             "g_particle", "grad_eps", "wet_phi_max", "drop_speed_control", "drop_speed_target", "drop_speed_kp",
-            "drop_speed_ki", "drop_speed_interval")
+            "drop_speed_ki", "drop_speed_interval", "pressure_z", "rho_in", "rho_out")
 
 
 def from_workload(w) -> OracleSim:

@@ -36,6 +36,7 @@
 
 #define FLUID 0
 #define WALL 1
+#define PRESS 63 /* inlet/outlet face of a pressure boundary (Sec. V D); particles are 2 + p, p < 61 */
 
 /* ---------------------------------------------------------------------- */
 /* Sec. IV: D3Q19 velocity set (Krueger et al. 2016).  Weights follow from */
@@ -263,7 +264,13 @@ or_sim *or_create(const or_params *p)
     if (p->wall_z0)
         for (int y = 0; y < s->ny; y++)
             for (int x = 0; x < s->nx; x++) s->stat[lidx(s, x, y, 0)] = 1;
-    for (long i = 0; i < N; i++) s->owner[i] = s->stat[i] ? WALL : FLUID;
+    /* Sec. V D pressure boundaries: the node planes z=0 and z=nz-1 are the
+     * outside of the inlet and outlet faces, which sit halfway, at z=0.5 and
+     * z=nz-1.5; the domain is then not periodic in z for the fluid */
+    if (p->pressure_z)
+        for (int y = 0; y < s->ny; y++)
+            for (int x = 0; x < s->nx; x++) s->stat[lidx(s, x, y, 0)] = s->stat[lidx(s, x, y, s->nz - 1)] = 2;
+    for (long i = 0; i < N; i++) s->owner[i] = s->stat[i] == 2 ? PRESS : (s->stat[i] ? WALL : FLUID);
     return s;
 }
 
@@ -279,6 +286,7 @@ void or_destroy(or_sim *s)
 
 static int solid_owner_of(const or_sim *s, int x, int y, int z)
 {
+    if (s->stat[lidx(s, x, y, z)] == 2) return PRESS;
     if (s->stat[lidx(s, x, y, z)]) return WALL;
     /* READING c15: node x is inside particle p iff |x - x_p|^2 < R_p^2 */
     for (int p = 0; p < s->np; p++) {
@@ -293,7 +301,8 @@ static int solid_owner_of(const or_sim *s, int x, int y, int z)
 
 int or_set_static_solid(or_sim *s, const unsigned char *mask)
 {
-    for (long i = 0; i < s->N; i++) s->stat[i] = mask[i] ? 1 : 0;
+    for (long i = 0; i < s->N; i++)
+        if (s->stat[i] != 2) s->stat[i] = mask[i] ? 1 : 0;
     for (int z = 0; z < s->nz; z++)
         for (int y = 0; y < s->ny; y++)
             for (int x = 0; x < s->nx; x++)
@@ -490,7 +499,7 @@ static int solid_normal(const or_sim *s, int x, int y, int z, double *ns, double
     for (int i = 1; i < OR_Q; i++) {
         long id = nbr(s, x, y, z, OR_C[i][0], OR_C[i][1], OR_C[i][2]);
         int o = s->owner[id];
-        if (o == FLUID) continue;
+        if (o == FLUID || o == PRESS) continue; /* a pressure face carries no contact angle */
         any = 1;
         if (o == WALL) {
             for (int a = 0; a < 3; a++) ws[a] -= OR_W[i] * OR_C[i][a];
@@ -793,7 +802,7 @@ static void step_once(or_sim *s)
             for (int x = 0; x < nx; x++) {
                 long id = lidx(s, x, y, z);
                 if (s->owner[id] != FLUID) continue;
-                double ra = 0.0, rb = 0.0;
+                double ra = 0.0, rb = 0.0, j[3] = {0.0, 0.0, 0.0};
                 int have_rho = 0;
                 for (int i = 0; i < OR_Q; i++) {
                     long sid = nbr(s, x, y, z, -OR_C[i][0], -OR_C[i][1], -OR_C[i][2]);
@@ -804,8 +813,30 @@ static void step_once(or_sim *s)
                         continue;
                     }
                     if (!have_rho) {
-                        for (int k = 0; k < OR_Q; k++) { ra += s->fa[k * N + id]; rb += s->fb[k * N + id]; }
+                        for (int k = 0; k < OR_Q; k++) {
+                            ra += s->fa[k * N + id];
+                            rb += s->fb[k * N + id];
+                            for (int a = 0; a < 3; a++) j[a] += OR_C[k][a] * (s->fa[k * N + id] + s->fb[k * N + id]);
+                        }
                         have_rho = 1;
+                    }
+                    if (o == PRESS) {
+                        /* Sec. V D anti-bounce-back (Krueger et al. 2016):
+                         * f_in(x_b) = -f*_out(x_b)
+                         *   + 2 w_i rho_w [1 + (c_i.u_w)^2/(2 cs^4) - u_w^2/(2 cs^2)],
+                         * p_w = cs^2 rho_w.  READING: rho_w = rho_in on the face
+                         * below the fluid (source plane z=0), rho_out above; u_w
+                         * = j / rho and the colour split rho^{a,b}_w =
+                         * rho_w rho^{a,b} / rho of x_b's own post-collision state. */
+                        const double rw = OR_C[i][2] > 0 ? pp->rho_in : pp->rho_out;
+                        const double rt = ra + rb;
+                        const double uw[3] = {j[0] / rt, j[1] / rt, j[2] / rt};
+                        const double cu = OR_C[i][0] * uw[0] + OR_C[i][1] * uw[1] + OR_C[i][2] * uw[2];
+                        const double e = 1.0 + 4.5 * cu * cu - 1.5 * dot3(uw, uw);
+                        int ib = OR_OPP[i];
+                        s->fas[i * N + id] = -s->fa[ib * N + id] + 2.0 * OR_W[i] * rw * (ra / rt) * e;
+                        s->fbs[i * N + id] = -s->fb[ib * N + id] + 2.0 * OR_W[i] * rw * (rb / rt) * e;
+                        continue;
                     }
                     double xw[3] = {x - 0.5 * OR_C[i][0], y - 0.5 * OR_C[i][1], z - 0.5 * OR_C[i][2]};
                     double uw[3], lev[3];
@@ -837,7 +868,7 @@ static void step_once(or_sim *s)
                     double fout = s->fa[ib * N + id] + s->fb[ib * N + id];
                     double fin = s->fas[i * N + id] + s->fbs[i * N + id];
                     bb_mass += fin - fout;
-                    if (o == WALL) continue;
+                    if (o == WALL || o == PRESS) continue;
                     or_part *P = &s->P[o - 2];
                     double xw[3] = {x - 0.5 * OR_C[i][0], y - 0.5 * OR_C[i][1], z - 0.5 * OR_C[i][2]};
                     double uw[3], lev[3];

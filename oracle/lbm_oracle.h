@@ -43,6 +43,8 @@ typedef struct {
     double drop_speed_target[3]; /* target mean velocity of phase a        */
     double drop_speed_kp, drop_speed_ki;  /* PI gains; both 0: rho0/1000, rho0/(1000*5000) */
     int drop_speed_interval;     /* steps between updates; 0: 100          */
+    int pressure_z;              /* 1: node planes z=0 and z=nz-1 are pressure faces (Sec. V D) */
+    double rho_in, rho_out;      /* density imposed on the face at z=0.5 / z=nz-1.5 */
 } or_params;
 
 typedef struct or_sim or_sim;
