@@ -122,6 +122,17 @@ typedef struct {
     double drop_speed_target[3];
     double drop_speed_kp, drop_speed_ki;
     int drop_speed_interval;
+    /* pressure boundaries (Sec. V D, anti-bounce-back): pressure_z = 1 makes the
+     * node planes z = 0 and z = nz - 1 the outside of an inlet face at z = 0.5
+     * with density rho_in and an outlet face at z = nz - 1.5 with rho_out
+     * (pressure cs^2 rho); the fluid is then not periodic in z.  A link leaving
+     * a boundary node x_b through a face takes
+     * f_in = -f*_out(x_b) + 2 w_i rho_w [1 + (c_i.u_w)^2/(2 cs^4) - u_w^2/(2 cs^2)],
+     * u_w and the colour split of rho_w from x_b's own post-collision state.
+     * The faces carry no contact angle and no momentum-exchange force; keep
+     * particles clear of them.  Needs nz >= 4 and wall_z0 = 0. */
+    int pressure_z;
+    double rho_in, rho_out;
 } lbm_params;
 
 /* One rigid sphere (Sec. III, V).  R_c = R_p + delta_R; m = rho_p 4/3 pi R_p^3;

@@ -612,6 +612,9 @@ static lbm_status validate(lbm_ctx *ctx, const lbm_params &p, int k)
         return bad("negative grad_eps / wet_phi_max / cap_norm / diag_interval");
     if (!(p.surrogate_u_ref >= 0) || !(p.surrogate_r_ref >= 0) || !(p.surrogate_shell_gap >= 0))
         return bad("negative surrogate_u_ref / surrogate_r_ref / surrogate_shell_gap");
+    if (p.pressure_z && (p.wall_z0 || p.nz < 4 || !(p.rho_in > 0.0) || !(p.rho_out > 0.0) ||
+                         !std::isfinite(p.rho_in) || !std::isfinite(p.rho_out)))
+        return bad("pressure faces need nz >= 4, no substrate plane and finite rho_in, rho_out > 0");
     if (p.drop_speed_control < 0 || p.drop_speed_control > 7 || p.drop_speed_interval < 0 ||
         !finite3(p.drop_speed_target) || !std::isfinite(p.drop_speed_kp) || !std::isfinite(p.drop_speed_ki))
         return bad("drop_speed_control must be a mask in [0, 7], drop_speed_interval >= 0, finite gains and target");
@@ -733,6 +736,11 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.pop_off = pop_off;
         pop_off += (long long)I.pstride * (long long)ctx->pop_node_bytes;
         I.wall_z0 = p.wall_z0;
+        I.press = p.pressure_z ? 1 : 0;
+        I.rin = p.rho_in / p.rho0;
+        I.rout = p.rho_out / p.rho0;
+        I.f_rin = (float)I.rin;
+        I.f_rout = (float)I.rout;
         I.store_u = p.store_velocity ? 1 : 0;
         any_u |= I.store_u != 0;
         I.rho0 = p.rho0;
@@ -873,6 +881,9 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         fl.assign((size_t)I.N, OWN_FLUID);
         if (I.wall_z0)
             for (long long n = 0; n < (long long)I.nx * I.ny; n++) fl[(size_t)n] = OWN_WALL;
+        if (I.press)
+            for (long long n = 0; n < (long long)I.nx * I.ny; n++)
+                fl[(size_t)n] = fl[(size_t)(I.N - (long long)I.nx * I.ny + n)] = OWN_PRESS;
         cudaMemcpyAsync(ctx->flags + I.node_off, fl.data(), (size_t)I.N, cudaMemcpyHostToDevice, ctx->stream);
         cudaStreamSynchronize(ctx->stream);
     }
@@ -913,8 +924,10 @@ lbm_status lbm_set_solid_mask(lbm_ctx *ctx, int inst, const uint8_t *mask)
     const InstDev &I = ctx->inst_h[inst];
     std::vector<uint8_t> fl((size_t)I.N);
     for (long long n = 0; n < I.N; n++) {
-        bool wall = I.wall_z0 && n < (long long)I.nx * I.ny;
+        const long long plane = (long long)I.nx * I.ny;
+        bool wall = I.wall_z0 && n < plane;
         fl[(size_t)n] = (wall || mask[n]) ? OWN_WALL : OWN_FLUID;
+        if (I.press && (n < plane || n >= I.N - plane)) fl[(size_t)n] = OWN_PRESS;
     }
     CU(cudaMemcpyAsync(ctx->flags + I.node_off, fl.data(), (size_t)I.N, cudaMemcpyHostToDevice, ctx->stream));
     Lattice L = make_lattice(ctx);

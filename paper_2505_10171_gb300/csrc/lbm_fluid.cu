@@ -115,7 +115,7 @@ __device__ __forceinline__ int inst_of_node(const Lattice &L, long long g)
 __global__ void k_static_bound(Lattice L, long long *list, unsigned long long *count, int mode)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= L.Ntot || ((L.flags[g] & OWNER_MASK) == OWN_WALL) != (mode == 0)) return;
+    if (g >= L.Ntot || own_static(L.flags[g] & OWNER_MASK) != (mode == 0)) return;
     const InstDev &I = L.inst[inst_of_node(L, g)];
     const int n = (int)(g - I.node_off);
     const int x = n % I.nx, y = (n / I.nx) % I.ny, z = n / (I.nx * I.ny);
@@ -124,7 +124,7 @@ __global__ void k_static_bound(Lattice L, long long *list, unsigned long long *c
     const uint8_t *fli = L.flags + I.node_off;
     bool hit = false;
 #pragma unroll
-    for (int i = 1; i < Q; i++) hit |= ((fli[nb.at(cx(i), cy(i), cz(i))] & OWNER_MASK) == OWN_WALL) != (mode == 0);
+    for (int i = 1; i < Q; i++) hit |= own_static(fli[nb.at(cx(i), cy(i), cz(i))] & OWNER_MASK) != (mode == 0);
     if (!hit) return;
     const unsigned long long k = atomicAdd(count, 1ull);
     if (list) list[k] = g;

@@ -48,6 +48,10 @@ constexpr uint8_t FRESH_BIT = 0x40;
 constexpr uint8_t BOUND_BIT = 0x80;
 constexpr uint8_t OWN_FLUID = 0;
 constexpr uint8_t OWN_WALL = 1;
+// outside of an inlet / outlet face of the Sec. V D pressure boundary (the
+// node planes z = 0 and z = nz - 1); particles own 2 .. 62
+constexpr uint8_t OWN_PRESS = 63;
+__host__ __device__ __forceinline__ bool own_static(int o) { return o == OWN_WALL || o == OWN_PRESS; }
 
 // sticky status bits
 constexpr unsigned ST_UNSTABLE = 1u;
@@ -91,6 +95,9 @@ struct InstDev {
     int hist_off;        // first pair-history record of the instance
     int crec_off;        // first DEM contact record of the instance
     int wall_z0, store_u;
+    int press;                 // pressure faces at z = 0.5 and z = nz - 1.5 (Sec. V D)
+    double rin, rout;          // their densities over rho0
+    float f_rin, f_rout;
     double rho0, sigma, beta, cap_norm, eta_a, eta_b;
     double body_a[3], body_b[3], wall_u[3];
     double cos_tw, sin_tw;
@@ -430,6 +437,11 @@ struct Colour {
 // rho^{a,b}(x) of the node's own pre-streaming state, u_w at the link midpoint.
 // Every flag and population load is issued before any is used (one dependent
 // round trip instead of one per link).  F receives the 19 total offsets.
+// A source on a pressure face (Sec. V D) gives the anti-bounce-back value
+//   f_i = -f*_ibar(x) + 2 w_i rho_w [1 + (c_i.u_w)^2/(2 cs^4) - u_w^2/(2 cs^2)],
+// rho_w the face's density (inlet below, outlet above), u_w = j*/rho* of the
+// node's own post-collision state; the colour split of rho_w follows that
+// state's phi, so the colour offset is phi(x)(1 + F_i) + (c_i . a(x))/|c_i|.
 // With C set, *sG receives sum_i w_i G_i of the streamed colour offsets:
 // G_i(x) = G*_i(x - c_i) from a fluid source; from a solid one
 // G*_ibar(x) + 6 (rho^a - rho^b)(x)/rho0 c_i.u_w, and since
@@ -450,14 +462,27 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
         pF[i] = in.F(i, s);
         oF[i] = in.F(i, n);
     }
-    R sF = 0;
+    R sF = 0, jw[3] = {0, 0, 0};
 #pragma unroll
-    for (int j = 0; j < Q; j++) sF += wgt<R>(j) * oF[j];
+    for (int j = 0; j < Q; j++) {
+        sF += wgt<R>(j) * oF[j];
+        if (cx(j)) jw[0] += wgt<R>(j) * cx(j) * oF[j];
+        if (cy(j)) jw[1] += wgt<R>(j) * cy(j) * oF[j];
+        if (cz(j)) jw[2] += wgt<R>(j) * cz(j) * oF[j];
+    }
     const R rr = R(1) + sF;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         if (own[i] == OWN_FLUID) {
             F[i] = pF[i];
+            continue;
+        }
+        if (own[i] == OWN_PRESS) {
+            const R irr = R(1) / rr;
+            const R u0 = jw[0] * irr, u1 = jw[1] * irr, u2 = jw[2] * irr;
+            const R cu = cx(i) * u0 + cy(i) * u1 + cz(i) * u2;
+            const R rw = sizeof(R) == 8 ? (R)(cz(i) > 0 ? I.rin : I.rout) : (R)(cz(i) > 0 ? I.f_rin : I.f_rout);
+            F[i] = R(-2) - oF[opp(i)] + R(2) * rw * (R(1) + R(4.5) * cu * cu - R(1.5) * (u0 * u0 + u1 * u1 + u2 * u2));
             continue;
         }
         R uw[3];
@@ -475,6 +500,8 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
             const ColRec<R> cs = C->at(nbr.idx(-cx(i), -cy(i), -cz(i)));
             gi = cs.p * (R(1) + F[i]);
             if (i) gi += col_rec(i, cs);
+        } else if (own[i] == OWN_PRESS) {
+            gi = cn.p * (R(1) + F[i]) + col_rec(i, cn);
         } else {
             gi = cn.p * (R(1) + F[i]) - col_rec(i, cn);
         }

@@ -44,7 +44,7 @@ __device__ __forceinline__ bool solid_normal(const InstDev &I, const PartDev *pa
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         int own = nbr.own(cx(i), cy(i), cz(i));
-        if (own == OWN_FLUID) continue;
+        if (own == OWN_FLUID || own == OWN_PRESS) continue;  // a pressure face carries no contact angle
         any = true;
         if (own == OWN_WALL) {
             ws[0] -= wgt<R>(i) * cx(i);

@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_geom_owner(Lattice L, int side
         reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
         const long long g = I.node_off + ((long long)z * I.ny + y) * I.nx + x;
         const uint8_t old = L.flags[g];
-        if ((old & OWNER_MASK) == OWN_WALL) continue;
+        if (own_static(old & OWNER_MASK)) continue;
         const int own = particle_owner(I, L.parts, x, y, z, 0);
         const int prev = particle_owner(I, L.parts, x, y, z, 1);
         uint8_t f = (uint8_t)own;
@@ -708,7 +708,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_mark(Lattice L, int side)
         reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
         const long long g = I.node_off + ((long long)z * I.ny + y) * I.nx + x;
         const uint8_t old = L.flags[g];
-        if ((old & OWNER_MASK) == OWN_WALL) continue;
+        if (own_static(old & OWNER_MASK)) continue;
         L.flags[g] = (uint8_t)(particle_owner(I, L.parts, x, y, z, 0) | (old & BOUND_BIT));
     }
 }

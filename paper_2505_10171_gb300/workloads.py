@@ -135,6 +135,37 @@ def cfg3(nz=1024):
                 mask=mask, particles=particles, steps=50000)
 
 
+# the anti-bounce-back faces realise an imposed density drop about this many
+# lattice units inside each face (measured on a pressure-driven channel)
+FACE_SHIFT = 1.6
+
+
+def tube_pressure(R_t=40.0, R_p=12.2, nz=2560, rho=1.05, nu=0.457, v_in=0.0113, l0=0.21, z0=200.0):
+    """Segre-Silberberg tube of Sec. V D at the paper's parameters: tube of
+    radius R_t along z, pressure faces at both ends (anti-bounce-back) with
+    the density drop of Poiseuille flow at mean speed v_in over the effective
+    length, single phase of density rho and viscosity nu, a neutrally buoyant
+    sphere R_p released at l0 R_t from the axis with the local flow speed.
+    The initial flow is the Poiseuille profile."""
+    nx = ny = int(2 * R_t) + 2
+    c = (nx - 1) / 2.0
+    x, y, z = grid(nx, ny, nz)
+    r = np.sqrt((x - c) ** 2 + (y - c) ** 2).reshape(-1)
+    mask = (r > R_t).astype(np.uint8)
+    L_eff = nz - 2 - 2 * FACE_SHIFT
+    drho = 3.0 * 8.0 * rho * nu * v_in / R_t ** 2 * L_eff
+    u = np.zeros((3, nx * ny * nz))
+    u[2] = np.where(r <= R_t, 2.0 * v_in * (1.0 - (r / R_t) ** 2), 0.0)
+    params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=0, rho0=rho, nu_a=nu, nu_b=nu, sigma=0.0,
+                  pressure_z=1, rho_in=rho + drho / 2, rho_out=rho - drho / 2, mu_s=0.0, mu_r=0.0)
+    l = l0 * R_t
+    up = 2.0 * v_in * (1.0 - (l / R_t) ** 2)
+    particles = [dict(x=(c + l, c, z0), R=R_p, rho_p=rho, theta_deg=90.0, v=(0.0, 0.0, up))]
+    return dict(name=f"pressure-driven tube R_t={R_t:g}, sphere R_p={R_p:g}, {nx}x{ny}x{nz}", params=params,
+                phi=np.ones(nx * ny * nz), rho=np.full(nx * ny * nz, rho), u=u, mask=mask, particles=particles,
+                R_t=R_t, centre=c)
+
+
 def ceil8(v):
     return int(math.ceil(v / 8.0) * 8)
 

@@ -48,9 +48,10 @@ def test_struct_layout_matches_header(libpath):
 #include <stddef.h>
 #include "lbm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, g_particle),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, g_particle),
          offsetof(lbm_params, store_velocity), offsetof(lbm_params, diag_interval), sizeof(lbm_particle),
-         offsetof(lbm_particle, theta_deg), offsetof(lbm_particle, kinematic));
+         offsetof(lbm_particle, theta_deg), offsetof(lbm_particle, kinematic), offsetof(lbm_params, pressure_z),
+         offsetof(lbm_params, rho_out));
   return 0; }
 """
     with tempfile.TemporaryDirectory() as d:
@@ -61,7 +62,7 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     P, Pa = lbm.lbm_params, lbm.lbm_particle
     assert vals == [ct.sizeof(P), P.g_particle.offset, P.store_velocity.offset, P.diag_interval.offset,
-                    ct.sizeof(Pa), Pa.theta_deg.offset, Pa.kinematic.offset]
+                    ct.sizeof(Pa), Pa.theta_deg.offset, Pa.kinematic.offset, P.pressure_z.offset, P.rho_out.offset]
 
 
 def test_abi_velocity_order_matches_header():
@@ -102,6 +103,7 @@ BASE = dict(nx=8, ny=8, nz=8)
     dict(wall_velocity=(float("inf"), 0.0, 0.0)), dict(kn=-1.0), dict(mu_r=-0.1),
     dict(cap_norm=-1.0), dict(grad_eps=-1e-4), dict(surrogate_shell_gap=-1.0),
     dict(drop_speed_control=8), dict(drop_speed_interval=-1),
+    dict(pressure_z=1, wall_z0=1), dict(pressure_z=1, rho_in=0.0), dict(pressure_z=1, nz=3),
 ])
 def test_create_rejects_invalid_parameters(libpath, bad):
     """Parameters are checked before any device call: an invalid one gives
