@@ -756,7 +756,9 @@ static void dem_step(or_sim *s, int with_fluid)
         double wm[3] = {0.5 * (wold[0] + P->w[0]), 0.5 * (wold[1] + P->w[1]), 0.5 * (wold[2] + P->w[2])};
         quat_rotate(P->q, wm);
         for (int a = 0; a < 3; a++) {
-            P->x[a] = xn[3 * p + a];
+            /* periodic domain: positions kept in [0, n) */
+            const int per = a == 0 ? s->nx : (a == 1 ? s->ny : s->nz);
+            P->x[a] = xn[3 * p + a] - per * floor(xn[3 * p + a] / per);
             P->Fp[a] = F[a];
             P->Tp[a] = T[a];
         }

@@ -484,9 +484,16 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
         const T wm[3] = {(T)(0.5 * (wold[0] + Q_.w[0])), (T)(0.5 * (wold[1] + Q_.w[1])),
                          (T)(0.5 * (wold[2] + Q_.w[2]))};
         quat_rotate<T>(Q_.q, wm);
+        // the geometry kernels assume a move below the margin: a larger or
+        // non-finite one sets the status and leaves the particle where it was
+        // (the run is reported unstable), so that nothing indexes with it
+        bool ok = true;
+        for (int a = 0; a < 3; a++) ok = ok && fabs(xn[3 * p + a] - Q_.x[a]) < GEOM_MARGIN - 1;
+        if (!ok) atomicOr(L.status, ST_DISPLACEMENT);
+        const int per[3] = {I.nx, I.ny, I.nz};
         for (int a = 0; a < 3; a++) {
-            if (fabs(xn[3 * p + a] - Q_.x[a]) >= GEOM_MARGIN - 1) atomicOr(L.status, ST_DISPLACEMENT);
-            Q_.x[a] = xn[3 * p + a];
+            // periodic domain: positions kept in [0, n)
+            if (ok) Q_.x[a] = xn[3 * p + a] - per[a] * floor(xn[3 * p + a] / per[a]);
             Q_.xf[a] = (float)Q_.x[a];
             Q_.Fp[a] = F[a];
             Q_.Tp[a] = Tq[a];

@@ -216,3 +216,66 @@ def tube_pressure_migration(steps=100000, sample_every=1000, nz=2560, precision=
     finally:
         ctx.close()
     return dict(t=np.asarray(t), l=np.asarray(l), z=np.asarray(zs), u_mean=u_mean, v_in=kw.get("v_in", 0.0113))
+
+
+# outcomes of a drop-particle collision (Sec. VI B/C)
+PUSH_PULL, ENTER_EXIT, CAPTURED_AFTER_ENTERING, NO_CONTACT, LEFT_BEHIND = (
+    "push-pull", "enter-exit", "captured after entering", "no contact", "left behind")
+
+
+def classify_outcome(shell_phi, inside=0.5):
+    """Outcome of one collision from the order parameter sampled on the
+    sphere's shell (rows: samples in time, columns: shell points; phase a,
+    phi > 0, is the drop).  The particle touches the drop when some shell
+    point is in phase a, is inside it when the shell's mean phi exceeds
+    `inside`.  Captured (the particle stays attached to the drop) = touching
+    at the last sample.  push-pull: captured, never inside; enter-exit:
+    inside at some sample, detached at the end; captured after entering;
+    left behind: touched, never inside, detached; no contact: never touched."""
+    s = np.asarray(shell_phi, dtype=float)
+    touch = (s > 0.0).any(axis=1)
+    entered = bool((s.mean(axis=1) > inside).any())
+    captured = bool(touch[-1])
+    if not touch.any():
+        return NO_CONTACT
+    if captured:
+        return CAPTURED_AFTER_ENTERING if entered else PUSH_PULL
+    return ENTER_EXIT if entered else LEFT_BEHIND
+
+
+def capture_map(mus, mu_rs, steps=40000, sample_every=500, precision="fp16", stream=None, **kw):
+    """The friction map of Sec. VI C on the batched sweep: one instance per
+    (mu, mu_r) of workloads.capture_case, all stepped in one context (one
+    launch per kernel per step, graph-captured); every sample_every steps the
+    shell order parameter of each sphere (the surrogate's shell features) and
+    its record are read.  Returns per case mu, mu_r, the outcome, the sphere's
+    x displacement and its rolling ratio omega_y R_p / v_x at the end."""
+    cases = [(m, r) for m in mus for r in mu_rs]
+    ws = [W.capture_case(m, r, **kw) for m, r in cases]
+    # the shell features read the stored collision velocity
+    ctx = lbm.Context([dict(w["params"], store_velocity=1) for w in ws], precision, stream=stream)
+    try:
+        for k, w in enumerate(ws):
+            ctx.lbm_add_particles(w["particles"], inst=k)
+            ctx.lbm_init_fields(w["phi"], inst=k)
+        x0 = [ctx.lbm_particle_forces(k)[0][18] for k in range(len(ws))]
+        shells = [[] for _ in ws]
+        done = 0
+        while done < steps:
+            n = min(sample_every, steps - done)
+            ctx.lbm_step(n)
+            done += n
+            for k in range(len(ws)):
+                f = ctx.lbm_surrogate_features(k)[0]
+                shells[k].append(f[0:4 * 96:4])  # phi at the 96 shell points
+        out = []
+        for k, (m, r) in enumerate(cases):
+            rec = ctx.lbm_particle_forces(k)[0]
+            nx = ws[k]["params"]["nx"]
+            dx = (rec[18] - x0[k] + nx / 2) % nx - nx / 2
+            v, wv = rec[21:24], rec[24:27]
+            out.append(dict(mu=m, mu_r=r, outcome=classify_outcome(shells[k]), dx=float(dx),
+                            rolling=float(wv[1] * ws[k]["particles"][0]["R"] / v[0]) if abs(v[0]) > 1e-9 else 0.0))
+    finally:
+        ctx.close()
+    return out

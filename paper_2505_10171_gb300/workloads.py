@@ -166,6 +166,37 @@ def tube_pressure(R_t=40.0, R_p=12.2, nz=2560, rho=1.05, nu=0.457, v_in=0.0113, 
                 R_t=R_t, centre=c)
 
 
+def capture_case(mu, mu_r, scale=0.5, Bo=1.25, friction_number=5.23, sigma=0.01, offset=0.5):
+    """One drop-particle collision of the friction map of Sec. VI C, its
+    shapes scaled by `scale` from the paper's (400x181x71 lattice, R_p = 10,
+    R_d = 5 R_p): a hemispherical drop (phase a) on the substrate, pushed
+    along x by the force density f_x = Bo sigma / R_d^2 on phase a (the
+    printed Bo = f_x R_d / sigma is not dimensionless for a force per unit
+    volume; with R_d^2 and sigma = 0.01 the total force on the R_d = 50 drop
+    is 1.3, inside Table I's 0.26 - 1.57), and a sphere
+    resting on the substrate ahead of it, `offset` R_p to the side, weight
+    g_p = friction_number sigma R_p (so that mu g_p/(sigma R_p) spans 0 to
+    friction_number as mu goes from 0 to 1), contact angles 90 deg on sphere
+    and substrate, sliding / rolling friction mu, mu_r.  Viscosities of the
+    256x128x128 run (drop 1/6, ambient 1/60), particle density of the
+    workloads, normal contact damping at half the critical value."""
+    nx, ny, nz = int(round(400 * scale)), int(round(181 * scale)), int(round(71 * scale))
+    R_p = 10.0 * scale
+    R_d = 5.0 * R_p
+    f_x = Bo * sigma / R_d ** 2
+    g_p = friction_number * sigma * R_p
+    xd = 1.0 + R_d + 6.0 * scale
+    params = dict(COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=90.0, sigma=sigma, nu_a=1.0 / 6.0,
+                  nu_b=1.0 / 60.0, body_force_a=(f_x, 0.0, 0.0), mu_s=mu, mu_r=mu_r, gn=resting_damping(R_p),
+                  g_particle=(0.0, 0.0, -g_p))
+    phi = drop_phi(nx, ny, nz, (xd, ny / 2.0, 0.5), R_d)
+    zc = 0.5 + R_p + params["delta_R"] - g_p / params["kn"]
+    particles = [dict(x=(xd + R_d + R_p + 3.0, ny / 2.0 + offset * R_p, zc), R=R_p, rho_p=PARTICLE_DENSITY,
+                      theta_deg=90.0)]
+    return dict(name=f"capture case mu={mu:g} mu_r={mu_r:g}", params=params, phi=phi, particles=particles,
+                R_d=R_d, Bo=Bo)
+
+
 def ceil8(v):
     return int(math.ceil(v / 8.0) * 8)
 
