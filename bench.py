@@ -52,12 +52,12 @@ def population_bytes_per_node(stage, prec):
 
 def design_bytes_per_node(stage, prec):
     """Every byte a kernel reads or writes per node, each once: populations
-    plus the per-node reals (phi, b, n, |grad phi|, kappa), flags left out.
-    Order parameter: 19 F + phi, b, n of the sources + phi out; gradient pass:
-    phi in, n, |grad phi|, kappa out; collision: 19 F + phi, n, |grad phi|,
-    kappa in, 19 F + b out."""
+    plus the per-node reals (phi, the colour record of 4 reals, n,
+    |grad phi|, kappa), flags left out.  Order parameter: 19 F + the sources'
+    records + phi out; gradient pass: phi in, n, |grad phi|, kappa out;
+    collision: 19 F + phi, n, |grad phi|, kappa in, 19 F + record out."""
     e, r = ELEM[prec], REAL[prec]
-    return {"phi": 19 * e + 6 * r, "grad_wetting": 6 * r, "collide": 38 * e + 7 * r}.get(stage, 0)
+    return {"phi": 19 * e + 5 * r, "grad_wetting": 6 * r, "collide": 38 * e + 10 * r}.get(stage, 0)
 
 
 # DRAM bytes (read + write) per launch of a kernel from one ncu capture of

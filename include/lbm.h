@@ -133,6 +133,7 @@ typedef struct {
      * particles clear of them.  Needs nz >= 4 and wall_z0 = 0. */
     int pressure_z;
     double rho_in, rho_out;
+    double surrogate_box;      /* surrogate inputs: box filter width (0: none), reading c30 */
 } lbm_params;
 
 /* One rigid sphere (Sec. III, V).  R_c = R_p + delta_R; m = rho_p 4/3 pi R_p^3;

@@ -235,19 +235,39 @@ def interp_fluid(field, fluid, X):
     return acc / wsum
 
 
-def shell_features(phi, u, fluid, xp, vp, wp, R, theta_deg, gap, u_ref, r_ref):
+def shell_features(phi, u, fluid, xp, vp, wp, R, theta_deg, gap, u_ref, r_ref, box=0.0, wall=False):
     """The 387 inputs of one particle: phi, u: [nz][ny][nx] and [3][nz][ny][nx]
     FP64 fields; fluid: boolean [nz][ny][nx]; xp, vp, wp: centre, velocity,
-    angular velocity; R, theta_deg: radius and contact angle."""
+    angular velocity; R, theta_deg: radius and contact angle.  READING c30:
+    with box > 0 each sample is the box filter of width `box` of the fields,
+    taken as the mean of the fluid-corner trilinear values at the 3 x 3 x 3
+    points (offsets -box/3, 0, +box/3 per axis) of the box around the shell
+    point (the midpoint rule of the box average; points whose cell has no
+    fluid corner are left out).  With wall (a solid plane z = 0), a point
+    whose z lies outside [0, nz) is inside that wall or beyond it and is left
+    out too: z is not wrapped across the wall."""
     nz, ny, nx = fluid.shape
     out = np.zeros(N_IN)
     dirs = shell_directions()
     rs = R + gap
+    offs = [np.zeros(3)] if box <= 0.0 else [np.array([i, j, k]) * box / 3.0
+                                              for k in (-1, 0, 1) for j in (-1, 0, 1) for i in (-1, 0, 1)]
     for k, e in enumerate(dirs):
-        X = np.asarray(xp, dtype=np.float64) + rs * e
-        X = np.array([X[0] % nx, X[1] % ny, X[2] % nz])
-        ph = interp_fluid(phi, fluid, X)
-        uu = interp_fluid(u, fluid, X)
+        phs, us = [], []
+        for d in offs:
+            X = np.asarray(xp, dtype=np.float64) + rs * e + d
+            if wall and not 0.0 <= X[2] < nz:
+                continue
+            X = np.array([X[0] % nx, X[1] % ny, X[2] % nz])
+            p_ = interp_fluid(phi, fluid, X)
+            if p_ is None:
+                continue
+            phs.append(p_)
+            us.append(interp_fluid(u, fluid, X))
+        if not phs:
+            continue
+        ph = sum(phs) / len(phs)
+        uu = sum(us) / len(us)
         if ph is None:
             continue
         lever = rs * e

@@ -610,8 +610,9 @@ static lbm_status validate(lbm_ctx *ctx, const lbm_params &p, int k)
         return bad("DEM constants must be >= 0");
     if (p.grad_eps < 0 || p.wet_phi_max < 0 || p.cap_norm < 0 || p.diag_interval < 0)
         return bad("negative grad_eps / wet_phi_max / cap_norm / diag_interval");
-    if (!(p.surrogate_u_ref >= 0) || !(p.surrogate_r_ref >= 0) || !(p.surrogate_shell_gap >= 0))
-        return bad("negative surrogate_u_ref / surrogate_r_ref / surrogate_shell_gap");
+    if (!(p.surrogate_u_ref >= 0) || !(p.surrogate_r_ref >= 0) || !(p.surrogate_shell_gap >= 0) ||
+        !(p.surrogate_box >= 0) || !std::isfinite(p.surrogate_box))
+        return bad("negative surrogate_u_ref / surrogate_r_ref / surrogate_shell_gap / surrogate_box");
     if (p.pressure_z && (p.wall_z0 || p.nz < 4 || !(p.rho_in > 0.0) || !(p.rho_out > 0.0) ||
                          !std::isfinite(p.rho_in) || !std::isfinite(p.rho_out)))
         return bad("pressure faces need nz >= 4, no substrate plane and finite rho_in, rho_out > 0");
@@ -768,6 +769,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.sh_gap = p.surrogate_shell_gap > 0.0 ? p.surrogate_shell_gap : 2.0;
         I.sh_uref = p.surrogate_u_ref > 0.0 ? p.surrogate_u_ref : 1e-3;
         I.sh_rref = p.surrogate_r_ref > 0.0 ? p.surrogate_r_ref : 8.0;
+        I.sh_box = p.surrogate_box;
         I.sp_mask = p.drop_speed_control & 7;
         I.sp_interval = p.drop_speed_interval > 0 ? p.drop_speed_interval : 100;
         I.sp_kp = p.drop_speed_kp;

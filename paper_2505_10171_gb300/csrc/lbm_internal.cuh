@@ -116,7 +116,7 @@ struct InstDev {
     int st_rows, st_seg, st_nseg, st_ygroups;
     FastDiv fd_plane, fd_nseg, fd_nx;  // st_ygroups st_nseg, st_nseg, nx
     // surrogate inputs: shell gap, velocity and radius scales
-    double sh_gap, sh_uref, sh_rref;
+    double sh_gap, sh_uref, sh_rref, sh_box;
     // gradient + curvature work items: gc_tiles_x * gc_tiles_y column tiles x
     // gc_nchunks z-chunks of gc_zc planes
     long long gc_item_start;

@@ -562,15 +562,38 @@ __global__ void __launch_bounds__(128) k_shell(Lattice L, int p0, float *feat)
         const double e[3] = {er * cos(az), er * sin(az), ez};
         const double rs = P.R + I.sh_gap;
         const int n3[3] = {I.nx, I.ny, I.nz};
-        double X[3], lev[3];
-        for (int a = 0; a < 3; a++) {
-            lev[a] = rs * e[a];
-            const double v = P.x[a] + lev[a];
-            X[a] = v - n3[a] * floor(v / n3[a]);
-        }
+        double lev[3];
+        for (int a = 0; a < 3; a++) lev[a] = rs * e[a];
+        // with a box filter (width sh_box) the mean over the 3 x 3 x 3 points
+        // of the box, offsets -w/3, 0, +w/3 per axis, of those whose cell has
+        // a fluid corner (the midpoint rule of the box average); with a wall
+        // at z = 0 a point outside [0, nz) in z lies in or beyond the wall and
+        // is left out (no wrap across the wall)
+        const int nsub = I.sh_box > 0.0 ? 27 : 1;
         double ph = 0.0, u[3] = {0.0, 0.0, 0.0};
+        int used = 0;
+        for (int s = 0; s < nsub; s++) {
+            const double d[3] = {nsub == 1 ? 0.0 : (s % 3 - 1) * I.sh_box / 3.0,
+                                 nsub == 1 ? 0.0 : ((s / 3) % 3 - 1) * I.sh_box / 3.0,
+                                 nsub == 1 ? 0.0 : (s / 9 - 1) * I.sh_box / 3.0};
+            double X[3];
+            bool in_wall = false;
+            for (int a = 0; a < 3; a++) {
+                const double v = P.x[a] + lev[a] + d[a];
+                if (a == 2 && I.wall_z0 && !(v >= 0.0 && v < n3[2])) in_wall = true;
+                X[a] = v - n3[a] * floor(v / n3[a]);
+            }
+            if (in_wall) continue;
+            double p1 = 0.0, u1[3] = {0.0, 0.0, 0.0};
+            if (!interp_fluid<R>(L, I, X, &p1, u1)) continue;
+            ph += p1;
+            for (int a = 0; a < 3; a++) u[a] += u1[a];
+            used++;
+        }
         float o[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (interp_fluid<R>(L, I, X, &ph, u)) {
+        if (used > 0) {
+            ph /= used;
+            for (int a = 0; a < 3; a++) u[a] /= used;
             const double us[3] = {P.v[0] + (P.w[1] * lev[2] - P.w[2] * lev[1]),
                                   P.v[1] + (P.w[2] * lev[0] - P.w[0] * lev[2]),
                                   P.v[2] + (P.w[0] * lev[1] - P.w[1] * lev[0])};

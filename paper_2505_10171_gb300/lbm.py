@@ -59,6 +59,7 @@ class lbm_params(ct.Structure):
         ("drop_speed_control", ct.c_int), ("drop_speed_target", ct.c_double * 3),
         ("drop_speed_kp", ct.c_double), ("drop_speed_ki", ct.c_double), ("drop_speed_interval", ct.c_int),
         ("pressure_z", ct.c_int), ("rho_in", ct.c_double), ("rho_out", ct.c_double),
+        ("surrogate_box", ct.c_double),
     ]
 
 
@@ -153,7 +154,7 @@ PARAM_DEFAULTS = dict(
     grad_eps=0.0, wet_phi_max=0.0, store_velocity=0, diag_interval=0,
     surrogate_u_ref=0.0, surrogate_r_ref=0.0, surrogate_shell_gap=0.0,
     drop_speed_control=0, drop_speed_target=(0.0, 0.0, 0.0), drop_speed_kp=0.0, drop_speed_ki=0.0,
-    drop_speed_interval=0, pressure_z=0, rho_in=1.0, rho_out=1.0,
+    drop_speed_interval=0, pressure_z=0, rho_in=1.0, rho_out=1.0, surrogate_box=0.0,
 )
 
 

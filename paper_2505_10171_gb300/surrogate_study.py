@@ -7,17 +7,27 @@ of each sphere and its resolved fluid force and torque (momentum exchange
 plus capillary), divided by sigma R_p and sigma R_p^2.  The test set-ups are
 the same runs at 3/8 scale (96 x 48 x 48, drop R = 15, R_p = 3, U and sigma
 scaled by 3/8, viscosities kept: diffusive scaling, so that t U / R_p and
-the step count match).  They run twice on the coarse grid, with the plain coarse
-forces and with the surrogate, and both are compared with the resolved runs
-of the same seeds at the same steps.
+the step count match).  They run twice on the coarse grid, with the plain
+coarse forces and with the surrogate, and both are compared with the
+resolved runs of the same seeds at the same steps.
 
-Choices (the paper has no surrogate): the shell lies at R_p + 2 coarse units,
-the resolved samples use the same physical shell (R_p + 16/3 fine units);
-velocities are scaled by each run's drop speed target U and radii by R_p; the
-resolved inputs are taken on the resolved run's own fields by the GPU feature
-kernel (no box filter).
+Choices (the paper has no surrogate): the shell has radius 1.5 R_p on either
+grid; the resolved inputs are box-filtered over one coarse cell (width 8/3
+resolved units, 27-point midpoint rule) so that they see the fields at the
+coarse grid's resolution; velocities are scaled by each run's drop speed
+target U and radii by R_p.  By default the spheres are held at rest on the
+substrate (prescribed motion) while the drop sweeps over them, so that the
+resolved and coarse runs of a seed have the same particle positions at every
+sample and the comparison measures the force model alone; with free=True
+they move under the forces (the surrogate's force then also changes the
+trajectory, and a difference in trajectory shows up as force error).
 """
 from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
 
 import numpy as np
 
@@ -25,21 +35,24 @@ from paper_2505_10171_gb300 import lbm
 from paper_2505_10171_gb300 import workloads as W
 
 SCALE = 3.0 / 8.0
-FINE_U, FINE_RP, SHELL_GAP = 5.0e-3, 8.0, 2.0
+FINE_U, FINE_RP = 5.0e-3, 8.0
+SHELL = 0.5            # shell radius (1 + SHELL) R_p
+BOX = 1.0 / SCALE      # box filter of the resolved inputs: one coarse cell
+# nodes per context: 38 N must stay below 2^31 (population indices are int32)
+MAX_NODES = 50_000_000
 
 
-def _setup(seed, s):
+def _setup(seed, s, free=False):
     """Drop R = 40 s driven along x at 5e-3 s over a 150 deg wall, eight
     spheres R_p = 8 s (contact angles uniform in [30, 90] deg) placed 4 to 50 s
     ahead of the drop front (centres x in [98, 152] s, y in [12, 116] s) at
-    centre spacings of at least 24 s, on a box of
-    256 x 128 x 128 times s.  The contact offset delta_R stays one lattice unit
-    and the spheres rest on the wall with normal damping at half the critical
-    value and a weight of 2 sigma R_p: a sphere must keep a fluid node
-    between itself and the wall, or the momentum exchange on its open surface
-    carries the unbalanced rest pressure (with the weight 10 sigma R_p and no
-    damping of the 256 x 128 x 128 benchmark workload, spheres that overshoot
-    their rest overlap seal against the wall and are pushed into it)."""
+    centre spacings of at least 24 s, on a box of 256 x 128 x 128 times s.
+    The contact offset delta_R stays one lattice unit.  Held spheres
+    (free=False) sit at rest one delta_R above the wall.  Free spheres rest
+    on the wall with normal damping at half the critical value and a weight
+    of 2 sigma R_p: a sphere must keep a fluid node between itself and the
+    wall, or the momentum exchange on its open surface carries the
+    unbalanced rest pressure."""
     rng = np.random.default_rng(seed)
     R8, Rc8 = FINE_RP, FINE_RP + 1.0
     centres = W.place_spheres(rng, 8, R8, Rc8, (98.0, 152.0), (12.0, 116.0), 9.5, 24.0)
@@ -52,21 +65,21 @@ def _setup(seed, s):
                   body_force_a=(2.0e-6 * s, 0.0, 0.0), g_particle=(0.0, 0.0, -2.0 * sigma * R_p),
                   drop_speed_control=1, drop_speed_target=(FINE_U * s, 0.0, 0.0), drop_speed_interval=100,
                   store_velocity=1, surrogate_u_ref=FINE_U * s, surrogate_r_ref=R_p,
-                  surrogate_shell_gap=SHELL_GAP * (s / SCALE))
+                  surrogate_shell_gap=SHELL * R_p, surrogate_box=BOX if s == 1.0 else 0.0)
     phi = W.drop_phi(nx, ny, nz, (48.0 * s, 64.0 * s, 0.5), 40.0 * s)
     particles = [dict(x=(c[0] * s, c[1] * s, 0.5 + R_p + 1.0), R=R_p, rho_p=W.PARTICLE_DENSITY,
-                      theta_deg=float(t)) for c, t in zip(centres, thetas)]
+                      theta_deg=float(t), kinematic=0 if free else 1) for c, t in zip(centres, thetas)]
     return dict(params=params, phi=phi, particles=particles)
 
 
-def resolved(seed):
+def resolved(seed, free=False):
     """The resolved (R_p = 8) set-up of a seed."""
-    return _setup(seed, 1.0)
+    return _setup(seed, 1.0, free)
 
 
-def coarse(seed):
+def coarse(seed, free=False):
     """The same set-up at 3/8 scale (R_p = 3)."""
-    return _setup(seed, SCALE)
+    return _setup(seed, SCALE, free)
 
 
 def _labels(rec, sigma, R_p):
@@ -75,37 +88,48 @@ def _labels(rec, sigma, R_p):
     return np.concatenate([F / (sigma * R_p), T / (sigma * R_p * R_p)], axis=1)
 
 
+def _chunks(ws):
+    """Split the workloads into contexts of at most MAX_NODES nodes, as even
+    in count as the limit allows."""
+    nodes = [w["params"]["nx"] * w["params"]["ny"] * w["params"]["nz"] for w in ws]
+    per = max(1, int(MAX_NODES // max(nodes)))
+    n = math.ceil(len(ws) / per)
+    size = math.ceil(len(ws) / n)
+    return [list(range(i, min(i + size, len(ws)))) for i in range(0, len(ws), size)]
+
+
 def run(ws, steps, every, weights=None, features=True, stream=None):
-    """Step the workloads ws (one context, one instance each) and sample every
-    `every` steps.  Returns per instance the inputs X [samples][387] (when
-    features) and the nondimensional fluid force and torque Y [samples][6],
-    samples ordered by time then sphere.  With weights, the context uses the
-    surrogate for the particle forces."""
-    ctx = lbm.Context([w["params"] for w in ws], "fp32", stream=stream)
-    try:
-        for k, w in enumerate(ws):
-            ctx.lbm_add_particles(w["particles"], inst=k)
-            ctx.lbm_init_fields(w["phi"], inst=k)
-        if weights is not None:
-            ctx.lbm_surrogate_load(weights)
-            ctx.lbm_set_force_model(lbm.FORCE_SURROGATE)
-        X = [[] for _ in ws]
-        Y = [[] for _ in ws]
-        done = 0
-        while done < steps:
-            ctx.lbm_step(every)
-            done += every
-            for k, w in enumerate(ws):
-                p = w["params"]
-                R_p = w["particles"][0]["R"]
-                if features:
-                    X[k].append(ctx.lbm_surrogate_features(k))
-                Y[k].append(_labels(ctx.lbm_particle_forces(k), p["sigma"], R_p))
-    finally:
-        ctx.close()
-    out = []
-    for k in range(len(ws)):
-        out.append(dict(X=np.concatenate(X[k]) if features else None, Y=np.concatenate(Y[k])))
+    """Step the workloads ws (batched, one instance each, in as few contexts
+    as the node limit allows) and sample every `every` steps.  Returns per
+    instance the inputs X [samples][387] (when features) and the
+    nondimensional fluid force and torque Y [samples][6], samples ordered by
+    time then sphere.  With weights, the contexts use the surrogate for the
+    particle forces."""
+    out = [None] * len(ws)
+    for idx in _chunks(ws):
+        part = [ws[i] for i in idx]
+        ctx = lbm.Context([w["params"] for w in part], "fp32", stream=stream)
+        try:
+            for k, w in enumerate(part):
+                ctx.lbm_add_particles(w["particles"], inst=k)
+                ctx.lbm_init_fields(w["phi"], inst=k)
+            if weights is not None:
+                ctx.lbm_surrogate_load(weights)
+                ctx.lbm_set_force_model(lbm.FORCE_SURROGATE)
+            X = [[] for _ in part]
+            Y = [[] for _ in part]
+            done = 0
+            while done < steps:
+                ctx.lbm_step(every)
+                done += every
+                for k, w in enumerate(part):
+                    if features:
+                        X[k].append(ctx.lbm_surrogate_features(k))
+                    Y[k].append(_labels(ctx.lbm_particle_forces(k), w["params"]["sigma"], w["particles"][0]["R"]))
+        finally:
+            ctx.close()
+        for k, i in enumerate(idx):
+            out[i] = dict(X=np.concatenate(X[k]) if features else None, Y=np.concatenate(Y[k]))
     return out
 
 
@@ -115,23 +139,8 @@ def errors(Y, Yref):
             float(np.linalg.norm(Y[:, 3:6] - Yref[:, 3:6], axis=1).mean()))
 
 
-def campaign(train_seeds, test_seeds, steps=16000, every=32, epochs=40, batch=512, lr=1e-3, seed=9,
-             stream=None):
-    """Train on the resolved runs of train_seeds, then compare on test_seeds:
-    the network on the resolved test inputs (offline), and the coarse runs
-    with the plain forces and with the surrogate, all against the resolved
-    test runs.  Returns the error table and the training record."""
-    Xs, Ys = [], []
-    for sd in train_seeds:
-        r = run([resolved(sd)], steps, every, stream=stream)[0]
-        Xs.append(r["X"])
-        Ys.append(r["Y"])
-    X, Y = np.concatenate(Xs), np.concatenate(Ys)
-    ref = [run([resolved(sd)], steps, every, stream=stream)[0] for sd in test_seeds]
-    cws = [coarse(sd) for sd in test_seeds]
-    # the network lives in a context; train it in the plain coarse one's place
-    host = lbm.Context(cws[0]["params"], "fp32", stream=stream)
-    # initial weights: uniform +-1/sqrt(fan-in), zero biases and padding columns
+def init_weights(seed):
+    """Uniform +-1/sqrt(fan-in) weights, zero biases and padding columns."""
     rng = np.random.default_rng(seed)
     th = np.zeros(lbm.MLP_PARAMS, dtype=np.float32)
     o = 0
@@ -144,21 +153,82 @@ def campaign(train_seeds, test_seeds, steps=16000, every=32, epochs=40, batch=51
                 blk[:, 387:] = 0.0
             th[o:o + n] = blk.reshape(-1)
         o += n
-    host.lbm_surrogate_load(th)
-    losses = [host.lbm_surrogate_train(X, Y, 1, batch, lr, seed + e) for e in range(epochs)]
-    weights = host.lbm_surrogate_save()
-    off = []
-    for r in ref:
-        pred = np.concatenate([host.lbm_surrogate_predict(r["X"][i:i + lbm.MLP_MAX_BATCH])
-                               for i in range(0, len(r["X"]), lbm.MLP_MAX_BATCH)])
-        off.append(errors(pred.astype(np.float64), r["Y"]))
-    host.close()
+    return th
+
+
+def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=512, lr=1e-3, seed=9, free=False,
+             stream=None):
+    """Train on the resolved runs of train_seeds, then compare on test_seeds:
+    the network on the resolved test inputs (offline), and the coarse runs
+    with the plain forces and with the surrogate, all against the resolved
+    test runs.  The learning rate halves after half and after three quarters
+    of the epochs.  Returns the error table and the training record."""
+    t0 = time.time()
+    tr = run([resolved(sd, free) for sd in train_seeds], steps, every, stream=stream)
+    X = np.concatenate([r["X"] for r in tr])
+    Y = np.concatenate([r["Y"] for r in tr])
+    del tr
+    t_train_data = time.time() - t0
+    ref = run([resolved(sd, free) for sd in test_seeds], steps, every, stream=stream)
+    t_ref = time.time() - t0 - t_train_data
+    cws = [coarse(sd, free) for sd in test_seeds]
+    # the network lives in a context; a small coarse one hosts it
+    host = lbm.Context(cws[0]["params"], "fp32", stream=stream)
+    try:
+        host.lbm_surrogate_load(init_weights(seed))
+        losses = []
+        t1 = time.time()
+        for e in range(epochs):
+            rate = lr * (0.5 if e >= epochs // 2 else 1.0) * (0.5 if e >= (3 * epochs) // 4 else 1.0)
+            losses.append(host.lbm_surrogate_train(X, Y, 1, batch, rate, seed + e))
+        t_fit = time.time() - t1
+        weights = host.lbm_surrogate_save()
+        pred = [np.concatenate([host.lbm_surrogate_predict(r["X"][i:i + lbm.MLP_MAX_BATCH])
+                                for i in range(0, len(r["X"]), lbm.MLP_MAX_BATCH)]).astype(np.float64)
+                for r in ref]
+    finally:
+        host.close()
+    t2 = time.time()
     plain = run(cws, steps, every, features=False, stream=stream)
     sur = run(cws, steps, every, weights=weights, features=False, stream=stream)
-    table = dict(samples=int(X.shape[0]), label_rms=float(np.sqrt((Y * Y).mean())),
-                 offline=np.mean(off, axis=0).tolist(),
-                 plain_coarse=np.mean([errors(plain[k]["Y"], ref[k]["Y"]) for k in range(len(cws))], axis=0).tolist(),
-                 surrogate_coarse=np.mean([errors(sur[k]["Y"], ref[k]["Y"]) for k in range(len(cws))],
-                                          axis=0).tolist(),
-                 ref_force_mean=float(np.mean([np.linalg.norm(r["Y"][:, 0:3], axis=1).mean() for r in ref])))
+    t_coarse = time.time() - t2
+    Yr = np.concatenate([r["Y"] for r in ref])
+
+    def err(rows):
+        return list(errors(np.concatenate(rows), Yr))
+
+    table = dict(samples=int(X.shape[0]), test_samples=int(Yr.shape[0]), train_seeds=len(train_seeds),
+                 test_seeds=len(test_seeds), steps=steps, every=every, epochs=epochs, free=bool(free),
+                 label_rms=float(np.sqrt((Y * Y).mean())),
+                 ref_force_mean=float(np.linalg.norm(Yr[:, 0:3], axis=1).mean()),
+                 ref_torque_mean=float(np.linalg.norm(Yr[:, 3:6], axis=1).mean()),
+                 offline=err(pred), plain_coarse=err([p["Y"] for p in plain]),
+                 surrogate_coarse=err([p["Y"] for p in sur]),
+                 loss_first=losses[0], loss_last=losses[-1],
+                 seconds=dict(train_data=t_train_data, reference=t_ref, fit=t_fit, coarse_runs=t_coarse))
     return table, dict(losses=losses, weights=weights)
+
+
+def main():
+    ap = argparse.ArgumentParser(description="surrogate training and coarse-grid evaluation campaign")
+    ap.add_argument("--train", type=int, default=25, help="resolved training runs (seeds 1..N)")
+    ap.add_argument("--test", type=int, default=64, help="held-out seeds (1001..) run coarse and resolved")
+    ap.add_argument("--steps", type=int, default=16000)
+    ap.add_argument("--every", type=int, default=16)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--free", action="store_true", help="free spheres instead of held ones")
+    ap.add_argument("--out", default=None, help="write the error table as JSON here")
+    ap.add_argument("--weights", default=None, help="write the trained FP32 weights (.npy) here")
+    a = ap.parse_args()
+    table, rec = campaign(list(range(1, a.train + 1)), list(range(1001, 1001 + a.test)), steps=a.steps,
+                          every=a.every, epochs=a.epochs, free=a.free)
+    table["losses"] = rec["losses"]
+    print(json.dumps(table))
+    if a.out:
+        json.dump(table, open(a.out, "w"), indent=1)
+    if a.weights:
+        np.save(a.weights, rec["weights"])
+
+
+if __name__ == "__main__":
+    main()

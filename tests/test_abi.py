@@ -104,6 +104,7 @@ BASE = dict(nx=8, ny=8, nz=8)
     dict(cap_norm=-1.0), dict(grad_eps=-1e-4), dict(surrogate_shell_gap=-1.0),
     dict(drop_speed_control=8), dict(drop_speed_interval=-1),
     dict(pressure_z=1, wall_z0=1), dict(pressure_z=1, rho_in=0.0), dict(pressure_z=1, nz=3),
+    dict(surrogate_box=-1.0),
 ])
 def test_create_rejects_invalid_parameters(libpath, bad):
     """Parameters are checked before any device call: an invalid one gives

@@ -81,12 +81,13 @@ def test_training_follows_oracle():
     c.close()
 
 
-def test_shell_features_match_oracle():
+@pytest.mark.parametrize("gap,box", [(2.0, 0.0), (2.0, 8.0 / 3.0)])
+def test_shell_features_match_oracle(gap, box):
     """FP64 run of the 48x32x32 drop + sphere case: the 387 inputs of the
     sphere after 20 steps against the oracle's, sampled from the oracle's own
-    fields."""
+    fields, without and with the box filter of reading c30."""
     w = W.cfg1()
-    w["params"] = dict(w["params"], store_velocity=1)
+    w["params"] = dict(w["params"], store_velocity=1, surrogate_shell_gap=gap, surrogate_box=box)
     steps = 20
     o = oracle_sim(w)
     o.step(steps)
@@ -95,7 +96,8 @@ def test_shell_features_match_oracle():
     rec = o.particles()[0]
     fo = M.shell_features(f["phi"].reshape(nz, ny, nx), f["u"].reshape(3, nz, ny, nx),
                           (o.owner() == 0).reshape(nz, ny, nx), rec[18:21], rec[21:24], rec[24:27],
-                          w["particles"][0]["R"], w["particles"][0]["theta_deg"], 2.0, 1e-3, 8.0)
+                          w["particles"][0]["R"], w["particles"][0]["theta_deg"], gap, 1e-3, 8.0, box=box,
+                          wall=bool(w["params"]["wall_z0"]))
     c = gpu_ctx(w, "fp64")
     c.lbm_step(steps)
     fg = c.lbm_surrogate_features()

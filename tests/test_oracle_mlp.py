@@ -140,6 +140,33 @@ def test_shell_features_exact_on_linear_and_rigid_fields():
     assert np.allclose(f[2:384:4], urel[:, 1], atol=1e-11)
     assert np.allclose(f[3:384:4], urel[:, 2], atol=1e-11)
     assert abs(f[384] - 0.5) < 1e-15 and abs(f[385] - math.sqrt(3) / 2) < 1e-15 and f[386] == 5.0 / 8.0
+    # reading c30: the box filter's midpoint rule is exact for a linear field,
+    # so with a box the linear-field features are unchanged
+    fb = M.shell_features(phi, u, fluid, xp, np.zeros(3), w, R, 60.0, gap, 1e-3, 8.0, box=8.0 / 3.0)
+    assert np.allclose(fb, f, rtol=0, atol=1e-13)
+
+
+def test_box_filter_averages_a_quadratic_over_the_box():
+    """On phi = x^2 the box filter of width b at X gives the 3-point midpoint
+    rule's mean, X^2 + 2 (b/3)^2 / 3 (the grid is coarse enough that the
+    trilinear interpolation of x^2 adds (f - f^2) at each sub-point, which
+    the reference sums the same way)."""
+    n = 40
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    phi = (x.astype(float) - 20.0) ** 2
+    u = np.zeros((3, n, n, n))
+    fluid = np.ones(phi.shape, bool)
+    xp, R, gap, b = np.array([20.2, 19.6, 20.4]), 4.0, 2.0, 2.0
+    f = M.shell_features(phi, u, fluid, xp, np.zeros(3), np.zeros(3), R, 90.0, gap, 1e-3, 8.0, box=b)
+    e = M.shell_directions()
+    X = xp + (R + gap) * e
+    want = np.zeros(96)
+    for d in (-b / 3, 0.0, b / 3):
+        xs = X[:, 0] + d - 20.0
+        fr = xs - np.floor(xs)
+        want += xs ** 2 + fr * (1.0 - fr)   # linear interpolation of x^2 between nodes
+    want /= 3.0
+    assert np.allclose(f[0:384:4], want, rtol=0, atol=1e-11)
 
 
 def test_shell_features_skip_solid_corners():
@@ -159,3 +186,30 @@ def test_shell_features_skip_solid_corners():
     seven = np.abs(vals - 7.0) <= 1e-14
     assert np.all(seven | (vals == 0.0))
     assert seven.sum() > 80
+
+
+def test_shell_features_do_not_reach_across_a_wall():
+    """With a solid plane at z = 0 the shell of a sphere resting on it dips
+    below the plane; those points read nothing (zero features), while without
+    the wall they wrap to the top of the periodic box.  Fields: phi = 1 on the
+    lower half of the box, -1 on the upper half, so a wrapped sample would
+    read -1 where the sphere's own side of the wall is +1."""
+    n = 32
+    phi = np.where(np.arange(n)[:, None, None] < n // 2, 1.0, -1.0) * np.ones((n, n, n))
+    u = np.zeros((3, n, n, n))
+    fluid = np.ones((n, n, n), bool)
+    fluid[0] = False  # the wall plane
+    xp, R, gap = np.array([16.0, 16.0, 5.0]), 4.0, 2.0
+    e = M.shell_directions()
+    z = xp[2] + (R + gap) * e[:, 2]
+    below = z < 0.0
+    assert below.sum() >= 3
+    fw = M.shell_features(phi, u, fluid, xp, np.zeros(3), np.zeros(3), R, 90.0, gap, 1e-3, 8.0, wall=True)
+    assert np.all(fw[0:384:4][below] == 0.0)
+    assert np.all(fw[0:384:4][(z >= 1.0) & (z < n // 2 - 1)] == 1.0)
+    fp = M.shell_features(phi, u, fluid, xp, np.zeros(3), np.zeros(3), R, 90.0, gap, 1e-3, 8.0)
+    assert np.all(fp[0:384:4][z < -1.0] == -1.0)  # the periodic reading reaches the far side
+    # with a box filter, sub-points below the plane are left out of the mean
+    fb = M.shell_features(phi, u, fluid, xp, np.zeros(3), np.zeros(3), R, 90.0, gap, 1e-3, 8.0, box=2.0,
+                          wall=True)
+    assert np.all(fb[0:384:4] >= 0.0)
