@@ -134,6 +134,10 @@ typedef struct {
     int pressure_z;
     double rho_in, rho_out;
     double surrogate_box;      /* surrogate inputs: box filter width (0: none), reading c30 */
+    double buoyancy_a[3];      /* buoyancy, reading c28 (Sec. VI A): force per unit volume of a
+                                  particle immersed in phase a, e.g. (0, 0, rho_a g); the
+                                  particle receives (4/3) pi R^3 v buoyancy_a, v its immersed
+                                  volume fraction in phase a (see LBM_PARTICLE_RECORD) */
 } lbm_params;
 
 /* One rigid sphere (Sec. III, V).  R_c = R_p + delta_R; m = rho_p 4/3 pi R_p^3;
@@ -158,8 +162,14 @@ enum {
 /* Number of doubles lbm_particle_forces writes per particle:
  * F_eta[3] T_eta[3] (momentum exchange, Sec. V B), F_sigma[3] T_sigma[3]
  * (capillary, Sec. V F), F_c[3] T_c[3] (contact, Sec. III), x[3] v[3] w[3],
- * orientation quaternion q[4] (w, x, y, z), m. */
-#define LBM_PARTICLE_RECORD 32
+ * orientation quaternion q[4] (w, x, y, z), m, then (reading c28) the
+ * immersed volume fraction v in phase a and the buoyancy F_b[3].  v comes
+ * from the phase-a share a of the capillary force's surface points,
+ * s = (1 + phi)/2 clipped to [0, 1], area-weighted over the points with a
+ * fluid corner: a flat interface at height (2a - 1) R above the centre leaves
+ * v = (1 + t)^2 (2 - t)/4, t = 2a - 1, below it.  Both are those of the last
+ * resolved-force step (0 before the first). */
+#define LBM_PARTICLE_RECORD 36
 
 /* Create a context of n_instances instances; params points to n_instances
  * records (uneven sizes allowed).  stream is a cudaStream_t (NULL: the
@@ -225,6 +235,29 @@ lbm_status lbm_set_particle_motion(lbm_ctx *ctx, int inst, int p, const double *
 /* Per-particle record (LBM_PARTICLE_RECORD doubles each) of an instance after
  * the last step; out holds n_particles records.  Synchronises. */
 lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out);
+
+/* Checkpoint of an instance's particles, for an exact resume with contacts
+ * (the DEM of Sec. III carries state from step to step).  Per particle
+ * LBM_PARTICLE_STATE doubles: x[3] v[3] w[3] q[4] (w, x, y, z), then the total
+ * force and torque of the last DEM step F_prev[3] T_prev[3] (the next
+ * velocity-Verlet step reads them); then the friction-spring histories of
+ * Sec. III B-C: n_particles (n_particles + 1) slots of 6 doubles (sliding
+ * xi[3], rolling xi_r[3]) in the library's order, to be handed back as read.
+ * lbm_particle_state_size gives the total count (-1 for a bad instance). */
+#define LBM_PARTICLE_STATE 19
+long long lbm_particle_state_size(const lbm_ctx *ctx, int inst);
+
+/* Read the checkpoint; n must equal lbm_particle_state_size (-> LBM_ERR_ARG).
+ * Synchronises. */
+lbm_status lbm_get_particle_state(lbm_ctx *ctx, int inst, double *out, size_t n);
+
+/* Restore a checkpoint into a new context before its first step
+ * (-> LBM_ERR_STATE after): the instance must hold the same particles, added
+ * at exactly the checkpoint's positions (the solid map is built from them;
+ * another position -> LBM_ERR_ARG), with the fields restored by
+ * lbm_init_fields from the read populations.  Non-finite values or a speed
+ * above 0.1 -> LBM_ERR_ARG.  Synchronises; invalidates the step graph. */
+lbm_status lbm_set_particle_state(lbm_ctx *ctx, int inst, const double *in, size_t n);
 
 /* Read the fields selected by mask (LBM_FIELD_*) of an instance into host
  * memory, FP64.  Solid nodes read 0 for the density, phi and population
@@ -362,7 +395,9 @@ typedef enum { LBM_FORCE_RESOLVED = 0, LBM_FORCE_SURROGATE = 1 } lbm_force_model
 
 /* Select how the fluid forces on the particles are computed from the next
  * step on.  LBM_FORCE_SURROGATE needs loaded weights and store_velocity in
- * every instance (-> LBM_ERR_STATE).  Invalidates the step graph. */
+ * every instance (-> LBM_ERR_STATE); it replaces the surface sums that the
+ * buoyancy reads, so an instance with a nonzero buoyancy_a refuses it
+ * (-> LBM_ERR_UNSUPPORTED).  Invalidates the step graph. */
 lbm_status lbm_set_force_model(lbm_ctx *ctx, int model);
 
 /* Copy n = LBM_MLP_PARAMS host floats in as the master weights (the BF16

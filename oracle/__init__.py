@@ -49,6 +49,7 @@ class OrParams(ct.Structure):
         ("drop_speed_control", ct.c_int), ("drop_speed_target", ct.c_double * 3),
         ("drop_speed_kp", ct.c_double), ("drop_speed_ki", ct.c_double), ("drop_speed_interval", ct.c_int),
         ("pressure_z", ct.c_int), ("rho_in", ct.c_double), ("rho_out", ct.c_double),
+        ("buoyancy_a", ct.c_double * 3),
     ]
 
 
@@ -101,6 +102,8 @@ def lib():
         L.or_wetting_rotate.argtypes = [P(d), P(d), d]
         L.or_capillary.argtypes = [ct.c_void_p, i, P(d), P(d)]
         L.or_capillary.restype = i
+        L.or_immersed_fraction.argtypes = [ct.c_void_p, i]
+        L.or_immersed_fraction.restype = d
         L.or_eval_interface.argtypes = [ct.c_void_p]
         L.or_get_phi.argtypes = [ct.c_void_p, P(d)]
         _lib = L
@@ -123,7 +126,7 @@ DEFAULTS = dict(
     kn=2.5, kt=1.0, kr=0.5, gn=0.0, gt=0.0, gr=0.0, mu_s=0.0, mu_r=0.0, delta_R=1.0,
     g_particle=(0.0, 0.0, 0.0), grad_eps=1e-4, wet_phi_max=0.99,
     drop_speed_control=0, drop_speed_target=(0.0, 0.0, 0.0), drop_speed_kp=0.0, drop_speed_ki=0.0,
-    drop_speed_interval=0, pressure_z=0, rho_in=1.0, rho_out=1.0,
+    drop_speed_interval=0, pressure_z=0, rho_in=1.0, rho_out=1.0, buoyancy_a=(0.0, 0.0, 0.0),
 )
 
 
@@ -244,7 +247,7 @@ class OracleSim:
 
     def particles(self):
         n = self.num_particles
-        out = np.zeros((max(n, 1), 32))
+        out = np.zeros((max(n, 1), 36))
         self.L.or_get_particles(self.h, _dp(out))
         return out[:n]
 
@@ -264,6 +267,11 @@ class OracleSim:
         F, T = np.zeros(3), np.zeros(3)
         used = self.L.or_capillary(self.h, int(p), _dp(F), _dp(T))
         return F, T, used
+
+    def immersed_fraction(self, p):
+        """Volume fraction of particle p in phase a from the current phi
+        (reading c28)."""
+        return float(self.L.or_immersed_fraction(self.h, int(p)))
 
 
 def lattice():
@@ -307,7 +315,7 @@ def omega_of_phi(phi, rho, **kw):
 SIM_KEYS = ("wall_z0", "wall_velocity", "theta_wall_deg", "rho0", "nu_a", "nu_b", "sigma", "beta",
             "body_force_a", "body_force_b", "kn", "kt", "kr", "gn", "gt", "gr", "mu_s", "mu_r", "delta_R",
             "g_particle", "grad_eps", "wet_phi_max", "drop_speed_control", "drop_speed_target", "drop_speed_kp",
-            "drop_speed_ki", "drop_speed_interval", "pressure_z", "rho_in", "rho_out")
+            "drop_speed_ki", "drop_speed_interval", "pressure_z", "rho_in", "rho_out", "buoyancy_a")
 
 
 def from_workload(w) -> OracleSim:

@@ -26,7 +26,10 @@
  * (one-hop, two-hop and ambient branches), the momentum-exchange torque (an
  * exact angular-momentum balance with a spinning sphere across the periodic
  * boundary) and the sphere branch of the wetting normal (the rotated
- * gradient's angle to the nearest sphere's normal) have pins of their own.
+ * gradient's angle to the nearest sphere's normal) have pins of their own,
+ * and so does the immersed fraction behind the buoyancy (reading c28): the
+ * cap volume cut off by a flat interface, and a neutrally buoyant sphere
+ * that keeps its place.
  */
 #include "lbm_oracle.h"
 
@@ -167,6 +170,7 @@ typedef struct {
     double Feta[3], Teta[3];      /* hydrodynamic, Sec. V B                 */
     double Fsig[3], Tsig[3];      /* capillary, Sec. V F                    */
     double Fc[3], Tc[3];          /* contact, Sec. III                      */
+    double sub, Fb[3];            /* immersed fraction, buoyancy (c28)      */
     int kin;                      /* prescribed (kinematic) motion          */
 } or_part;
 
@@ -594,6 +598,61 @@ int or_capillary(const or_sim *s, int p, double *F, double *T)
 }
 
 /* ---------------------------------------------------------------------- */
+/* READING c28 (Sec. VI A: the particle's effective weight drops by the    */
+/* buoyancy of the drop once it enters it; no mechanism given).  Phase-a   */
+/* share of the sphere surface: s = (1+phi)/2 clipped to [0,1] at the      */
+/* capillary force's surface points, phi trilinear over fluid corners,     */
+/* area-weighted over the points that have a fluid corner: a = sum s dA /  */
+/* sum dA.  By Archimedes' hat-box theorem a spherical zone's area is      */
+/* proportional to its height, so a flat interface at height h = (2a-1) R  */
+/* above the centre cuts off the volume fraction v = (1+t)^2 (2-t)/4,      */
+/* t = h/R, below it.  Returns v (0 when no point has a fluid corner).     */
+/* ---------------------------------------------------------------------- */
+double or_immersed_fraction(const or_sim *s, int p)
+{
+    const or_part *P = &s->P[p];
+    const double da = 2.0 * M_PI / 180.0, dv = 2.0 * M_PI / 180.0;
+    double num = 0.0, den = 0.0;
+    for (int j = 0; j < 90; j++) {
+        double al = (j + 0.5) * da;
+        for (int k = 0; k < 180; k++) {
+            double vp = k * dv;
+            double ns[3] = {sin(al) * cos(vp), sin(al) * sin(vp), cos(al)};
+            double xi[3] = {P->x[0] + P->R * ns[0], P->x[1] + P->R * ns[1], P->x[2] + P->R * ns[2]};
+            double dA = P->R * P->R * sin(al) * da * dv;
+            int b[3];
+            double fr[3];
+            for (int a = 0; a < 3; a++) {
+                double fl = floor(xi[a]);
+                b[a] = (int)fl;
+                fr[a] = xi[a] - fl;
+            }
+            double ws = 0.0, ph = 0.0;
+            for (int cz = 0; cz < 2; cz++)
+                for (int cy = 0; cy < 2; cy++)
+                    for (int cx = 0; cx < 2; cx++) {
+                        long id = lidx(s, wrapi(b[0] + cx, s->nx), wrapi(b[1] + cy, s->ny),
+                                       wrapi(b[2] + cz, s->nz));
+                        if (s->owner[id] != FLUID) continue;
+                        double wgt = (cx ? fr[0] : 1.0 - fr[0]) * (cy ? fr[1] : 1.0 - fr[1]) *
+                                     (cz ? fr[2] : 1.0 - fr[2]);
+                        ws += wgt;
+                        ph += wgt * s->phi[id];
+                    }
+            if (ws <= 0.0) continue;
+            double sa = 0.5 * (1.0 + ph / ws);
+            if (sa < 0.0) sa = 0.0;
+            if (sa > 1.0) sa = 1.0;
+            num += sa * dA;
+            den += dA;
+        }
+    }
+    if (den <= 0.0) return 0.0;
+    double t = 2.0 * (num / den) - 1.0;
+    return (1.0 + t) * (1.0 + t) * (2.0 - t) / 4.0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Sec. III: DEM contact (normal spring-dashpot, Luding sliding and       */
 /* rolling friction) and Verlet integration.                              */
 /* ---------------------------------------------------------------------- */
@@ -743,7 +802,7 @@ static void dem_step(or_sim *s, int with_fluid)
         or_part *P = &s->P[p];
         double F[3], T[3];
         for (int a = 0; a < 3; a++) {
-            F[a] = P->Fc[a] + s->p.g_particle[a] + (with_fluid ? P->Feta[a] + P->Fsig[a] : 0.0);
+            F[a] = P->Fc[a] + s->p.g_particle[a] + (with_fluid ? P->Feta[a] + P->Fsig[a] + P->Fb[a] : 0.0);
             T[a] = P->Tc[a] + (with_fluid ? P->Teta[a] + P->Tsig[a] : 0.0);
         }
         double wold[3] = {P->w[0], P->w[1], P->w[2]};
@@ -982,6 +1041,13 @@ static void step_once(or_sim *s)
             }
     /* (7) capillary force, Sec. V F */
     for (int p = 0; p < s->np; p++) or_capillary(s, p, s->P[p].Fsig, s->P[p].Tsig);
+    /* (7b) buoyancy, READING c28: F_b = (4/3) pi R^3 v b_a */
+    for (int p = 0; p < s->np; p++) {
+        or_part *P = &s->P[p];
+        P->sub = or_immersed_fraction(s, p);
+        const double vol = 4.0 / 3.0 * M_PI * P->R * P->R * P->R;
+        for (int a = 0; a < 3; a++) P->Fb[a] = vol * P->sub * s->p.buoyancy_a[a];
+    }
     /* (8) DEM, Sec. III and Eqs. (Newton second law), (Newton - rotation) */
     if (s->np > 0) dem_step(s, 1);
     /* (9) geometry update and Sec. V C refilling (Caiazzo 2008).
@@ -1202,7 +1268,7 @@ void or_get_particles(const or_sim *s, double *out)
 {
     for (int p = 0; p < s->np; p++) {
         const or_part *P = &s->P[p];
-        double *o = out + 32 * p;
+        double *o = out + 36 * p;
         for (int a = 0; a < 3; a++) {
             o[a] = P->Feta[a]; o[3 + a] = P->Teta[a];
             o[6 + a] = P->Fsig[a]; o[9 + a] = P->Tsig[a];
@@ -1211,6 +1277,8 @@ void or_get_particles(const or_sim *s, double *out)
         }
         for (int a = 0; a < 4; a++) o[27 + a] = P->q[a];
         o[31] = P->m;
+        o[32] = P->sub;
+        for (int a = 0; a < 3; a++) o[33 + a] = P->Fb[a];
     }
 }
 

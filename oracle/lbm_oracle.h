@@ -45,6 +45,7 @@ typedef struct {
     int drop_speed_interval;     /* steps between updates; 0: 100          */
     int pressure_z;              /* 1: node planes z=0 and z=nz-1 are pressure faces (Sec. V D) */
     double rho_in, rho_out;      /* density imposed on the face at z=0.5 / z=nz-1.5 */
+    double buoyancy_a[3];        /* READING c28: force per unit particle volume immersed in phase a */
 } or_params;
 
 typedef struct or_sim or_sim;
@@ -66,8 +67,8 @@ void    or_get_owner(const or_sim *s, unsigned char *owner);
 int     or_num_particles(const or_sim *s);
 /* body force on phase a now and the phase-a velocity of the last controller update */
 void    or_get_speed_control(const or_sim *s, double *out /* [6] */);
-/* per particle 32 doubles: F_eta[3] T_eta[3] F_sig[3] T_sig[3] F_c[3] T_c[3]
-   x[3] v[3] w[3] q[4] m */
+/* per particle 36 doubles: F_eta[3] T_eta[3] F_sig[3] T_sig[3] F_c[3] T_c[3]
+   x[3] v[3] w[3] q[4] m, immersed volume fraction in phase a, buoyancy F_b[3] */
 void    or_get_particles(const or_sim *s, double *out);
 /* per step: [0] bounce-back mass source, [1] refilled mass, [2] covered mass,
    [3] total fluid mass, [4..6] total fluid momentum (post-collision state) */
@@ -82,6 +83,7 @@ void    or_collide_node(const double *fa, const double *fb, const double *F_ext,
 double  or_omega_of_phi(const or_params *p, double phi, double rho);
 void    or_wetting_rotate(double *g, const double *ns, double theta_rad);
 int     or_capillary(const or_sim *s, int p, double *F, double *T);
+double  or_immersed_fraction(const or_sim *s, int p);
 int     or_eval_interface(or_sim *s);
 void    or_get_phi(const or_sim *s, double *phi);
 

@@ -613,6 +613,7 @@ static lbm_status validate(lbm_ctx *ctx, const lbm_params &p, int k)
     if (!(p.surrogate_u_ref >= 0) || !(p.surrogate_r_ref >= 0) || !(p.surrogate_shell_gap >= 0) ||
         !(p.surrogate_box >= 0) || !std::isfinite(p.surrogate_box))
         return bad("negative surrogate_u_ref / surrogate_r_ref / surrogate_shell_gap / surrogate_box");
+    if (!finite3(p.buoyancy_a)) return bad("non-finite buoyancy_a");
     if (p.pressure_z && (p.wall_z0 || p.nz < 4 || !(p.rho_in > 0.0) || !(p.rho_out > 0.0) ||
                          !std::isfinite(p.rho_in) || !std::isfinite(p.rho_out)))
         return bad("pressure faces need nz >= 4, no substrate plane and finite rho_in, rho_out > 0");
@@ -770,6 +771,7 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
         I.sh_uref = p.surrogate_u_ref > 0.0 ? p.surrogate_u_ref : 1e-3;
         I.sh_rref = p.surrogate_r_ref > 0.0 ? p.surrogate_r_ref : 8.0;
         I.sh_box = p.surrogate_box;
+        for (int a = 0; a < 3; a++) I.buoy[a] = p.buoyancy_a[a];
         I.sp_mask = p.drop_speed_control & 7;
         I.sp_interval = p.drop_speed_interval > 0 ? p.drop_speed_interval : 100;
         I.sp_kp = p.drop_speed_kp;
@@ -1114,12 +1116,12 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     ctx->mem_part = ctx->cap_part = ctx->hist = ctx->crec = nullptr;
     CU(cudaMalloc((void **)&ctx->parts_d, sizeof(PartDev) * np));
     CU(cudaMalloc((void **)&ctx->mem_part, sizeof(double) * MEM_PART * np * ctx->mem_blocks));
-    CU(cudaMalloc((void **)&ctx->cap_part, sizeof(double) * 6 * np * CAP_BLOCKS));
+    CU(cudaMalloc((void **)&ctx->cap_part, sizeof(double) * CAP_PART * np * CAP_BLOCKS));
     CU(cudaMalloc((void **)&ctx->hist, sizeof(double) * 6 * std::max(hist, 1)));
     CU(cudaMalloc((void **)&ctx->crec, sizeof(double) * 12 * std::max(crec, 1)));
     CU(cudaMemsetAsync(ctx->hist, 0, sizeof(double) * 6 * std::max(hist, 1), ctx->stream));
     CU(cudaMemsetAsync(ctx->mem_part, 0, sizeof(double) * MEM_PART * np * ctx->mem_blocks, ctx->stream));
-    CU(cudaMemsetAsync(ctx->cap_part, 0, sizeof(double) * 6 * np * CAP_BLOCKS, ctx->stream));
+    CU(cudaMemsetAsync(ctx->cap_part, 0, sizeof(double) * CAP_PART * np * CAP_BLOCKS, ctx->stream));
     CU(cudaMemcpyAsync(ctx->parts_d, all.data(), sizeof(PartDev) * np, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice,
                        ctx->stream));
@@ -1230,6 +1232,80 @@ lbm_status lbm_set_particle_motion(lbm_ctx *ctx, int inst, int p, const double *
     return LBM_OK;
 }
 
+long long lbm_particle_state_size(const lbm_ctx *ctx, int inst)
+{
+    if (!ctx || inst < 0 || inst >= ctx->n_inst) return -1;
+    const long long np = ctx->inst_h[inst].np;
+    return np * LBM_PARTICLE_STATE + np * (np + 1) * 6;
+}
+
+lbm_status lbm_get_particle_state(lbm_ctx *ctx, int inst, double *out, size_t n)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || (!out && n)) return fail(ctx, LBM_ERR_ARG, "bad instance or output");
+    const InstDev &I = ctx->inst_h[inst];
+    if ((long long)n != lbm_particle_state_size(ctx, inst))
+        return fail(ctx, LBM_ERR_ARG, "n must be lbm_particle_state_size");
+    if (I.np == 0) return LBM_OK;
+    std::vector<PartDev> h((size_t)I.np);
+    CU(cudaMemcpyAsync(h.data(), ctx->parts_d + I.part_off, sizeof(PartDev) * I.np, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    double *springs = out + (size_t)I.np * LBM_PARTICLE_STATE;
+    CU(cudaMemcpyAsync(springs, ctx->hist + (size_t)I.hist_off * 6, sizeof(double) * 6 * I.np * (I.np + 1),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    lbm_status s = check_status(ctx);
+    for (int p = 0; p < I.np; p++) {
+        double *o = out + (size_t)LBM_PARTICLE_STATE * p;
+        const PartDev &q = h[(size_t)p];
+        for (int a = 0; a < 3; a++) {
+            o[a] = q.x[a]; o[3 + a] = q.v[a]; o[6 + a] = q.w[a];
+            o[13 + a] = q.Fp[a]; o[16 + a] = q.Tp[a];
+        }
+        for (int a = 0; a < 4; a++) o[9 + a] = q.q[a];
+    }
+    return s;
+}
+
+lbm_status lbm_set_particle_state(lbm_ctx *ctx, int inst, const double *in, size_t n)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || (!in && n)) return fail(ctx, LBM_ERR_ARG, "bad instance or input");
+    const InstDev &I = ctx->inst_h[inst];
+    if ((long long)n != lbm_particle_state_size(ctx, inst))
+        return fail(ctx, LBM_ERR_ARG, "n must be lbm_particle_state_size");
+    if (ctx->stepped) return fail(ctx, LBM_ERR_STATE, "the state is restored before the first step");
+    if (I.np == 0) return LBM_OK;
+    for (size_t k = 0; k < n; k++)
+        if (!std::isfinite(in[k])) return fail(ctx, LBM_ERR_ARG, "non-finite particle state");
+    std::vector<PartDev> h((size_t)I.np);
+    CU(cudaMemcpyAsync(h.data(), ctx->parts_d + I.part_off, sizeof(PartDev) * I.np, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int p = 0; p < I.np; p++) {
+        const double *o = in + (size_t)LBM_PARTICLE_STATE * p;
+        PartDev &q = h[(size_t)p];
+        // the solid map was built from the positions the particles were added
+        // at: the checkpoint must carry the same ones
+        for (int a = 0; a < 3; a++)
+            if (o[a] != q.x[a]) return fail(ctx, LBM_ERR_ARG, "particle added at another position than the state's");
+        const double vv = sqrt(o[3] * o[3] + o[4] * o[4] + o[5] * o[5]);
+        const double ww = sqrt(o[6] * o[6] + o[7] * o[7] + o[8] * o[8]);
+        if (!(vv <= 0.1) || !(ww * q.R <= 0.1)) return fail(ctx, LBM_ERR_ARG, "particle speed above 0.1");
+        for (int a = 0; a < 3; a++) {
+            q.v[a] = o[3 + a]; q.w[a] = o[6 + a];
+            q.Fp[a] = o[13 + a]; q.Tp[a] = o[16 + a];
+        }
+        for (int a = 0; a < 4; a++) q.q[a] = o[9 + a];
+    }
+    CU(cudaMemcpyAsync(ctx->parts_d + I.part_off, h.data(), sizeof(PartDev) * I.np, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaMemcpyAsync(ctx->hist + (size_t)I.hist_off * 6, in + (size_t)I.np * LBM_PARTICLE_STATE,
+                       sizeof(double) * 6 * I.np * (I.np + 1), cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));  // the host copies are pageable and local
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
 lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out)
 {
     if (!ctx) return LBM_ERR_ARG;
@@ -1251,6 +1327,8 @@ lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out)
         }
         for (int a = 0; a < 4; a++) o[27 + a] = q.q[a];
         o[31] = q.m;
+        o[32] = q.sub;
+        for (int a = 0; a < 3; a++) o[33 + a] = q.Fb[a];
     }
     return s;
 }
@@ -1428,8 +1506,11 @@ lbm_status lbm_set_force_model(lbm_ctx *ctx, int model)
         return fail(ctx, LBM_ERR_ARG, "model must be LBM_FORCE_RESOLVED or LBM_FORCE_SURROGATE");
     if (model == LBM_FORCE_SURROGATE) {
         if (!ctx->mlp_loaded) return fail(ctx, LBM_ERR_STATE, "no surrogate weights loaded");
-        for (auto &I : ctx->inst_h)
+        for (auto &I : ctx->inst_h) {
             if (!I.store_u) return fail(ctx, LBM_ERR_STATE, "the surrogate needs store_velocity in every instance");
+            if (I.buoy[0] != 0.0 || I.buoy[1] != 0.0 || I.buoy[2] != 0.0)
+                return fail(ctx, LBM_ERR_UNSUPPORTED, "the buoyancy needs the resolved surface sums");
+        }
     }
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->force_model = model;

@@ -61,6 +61,7 @@ constexpr unsigned ST_TIMEOUT = 4u;  // a bounded wait for an asynchronous copy 
 constexpr int CAP_POINTS = 90 * 180;  // Sec. V F: 2 deg x 2 deg Lagrangian points
 constexpr int CAP_THREADS = 256;
 constexpr int CAP_BLOCKS = (CAP_POINTS + CAP_THREADS - 1) / CAP_THREADS;
+constexpr int CAP_PART = 8;  // per block: F_sig, T_sig, sum s dA, sum dA
 constexpr int PART_THREADS = 256;
 // doubles per block partial of the momentum exchange: force and torque of the
 // small part, then the integer sums K and 2M of the rest part
@@ -104,6 +105,7 @@ struct InstDev {
     double grad_eps, wet_max;
     double kn, kt, kr, gn, gt, gr, mu_s, mu_r, dR;
     double g_part[3];
+    double buoy[3];      // force per unit particle volume immersed in phase a (reading c28)
     // single-precision copies of the fluid parameters (no FP64 conversions in
     // the FP32 and 16-bit kernels)
     float f_rho0, f_sigma, f_beta, f_eta_a, f_eta_b, f_eps2, f_wet_max;
@@ -156,6 +158,7 @@ struct PartDev {
     double inv_m, inv_I;  // 1/m, 1/I
     double Fp[3], Tp[3];
     double Feta[3], Teta[3], Fsig[3], Tsig[3], Fc[3], Tc[3];
+    double sub, Fb[3];    // immersed volume fraction in phase a, buoyancy
     float xf[3], xfo[3];  // single-precision copies of x and x_old
     float R2lo, R2hi;     // |x - x_p|^2 below / above these is inside / outside for sure
     int kin, inst, local, mem_side;
@@ -186,7 +189,7 @@ struct Lattice {
     int cap_side;        // side of the cube of phi around a particle for the capillary force
     int cap_blocks;      // blocks per particle covering that cube
     double *mem_part;    // [n_parts][mem_blocks][MEM_PART]
-    double *cap_part;    // [n_parts][CAP_BLOCKS][6]
+    double *cap_part;    // [n_parts][CAP_BLOCKS][CAP_PART]
     const double *cap_pts;  // [CAP_POINTS][4]: unit normal (3) and sin(alpha) of each surface point
     double *hist;        // contact springs: per instance np*(np+1) records of 6
     double *crec;        // DEM contact forces: per instance np + np(np-1)/2 records of 12

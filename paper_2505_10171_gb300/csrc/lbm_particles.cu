@@ -20,19 +20,19 @@
 namespace lbmg {
 
 // deterministic block sum of 6 doubles; thread 0 writes them to out
-template <class T>
-__device__ __forceinline__ void block_sum6(T *v, double *out)
+template <int K, class T>
+__device__ __forceinline__ void block_sum(T *v, double *out)
 {
-    __shared__ T sm[PART_THREADS / 32][6];
+    __shared__ T sm[PART_THREADS / 32][K];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int a = 0; a < 6; a++)
+    for (int a = 0; a < K; a++)
         for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_down_sync(0xffffffffu, v[a], o);
     if (lane == 0)
-        for (int a = 0; a < 6; a++) sm[wid][a] = v[a];
+        for (int a = 0; a < K; a++) sm[wid][a] = v[a];
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int a = 0; a < 6; a++) {
+        for (int a = 0; a < K; a++) {
             T s = 0;
             for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sm[w][a];
             out[a] = (double)s;
@@ -40,6 +40,9 @@ __device__ __forceinline__ void block_sum6(T *v, double *out)
     }
     __syncthreads();  // sm is reused by a second call
 }
+
+template <class T>
+__device__ __forceinline__ void block_sum6(T *v, double *out) { block_sum<6>(v, out); }
 
 // particle centre in the arithmetic type R (single-precision copy for float)
 __device__ __forceinline__ void centre(const PartDev &P, double *c) { c[0] = P.x[0]; c[1] = P.x[1]; c[2] = P.x[2]; }
@@ -153,14 +156,16 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
 // Sec. V F: dF = C sigma (1 - phi^2) dA (n x n_s) x n at the points
 // alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg on r = R_p, n the regularised
 // normal of the trilinearly interpolated grad(phi) (fluid corners only);
-// torque R_p n_s x dF.
+// torque R_p n_s x dF.  Also the phase-a share of the surface for the
+// buoyancy (reading c28): s = (1 + phi)/2 clipped to [0, 1] and dA, summed
+// over the points with a fluid corner.
 template <class R>
 __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
 {
     const int p = blockIdx.y;
     const PartDev &P = L.parts[p];
     const InstDev &I = L.inst[P.inst];
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    double acc[CAP_PART] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int pt = blockIdx.x * blockDim.x + threadIdx.x;
     if (pt < CAP_POINTS) {
         const double *tp = L.cap_pts + 4 * pt;
@@ -205,6 +210,9 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
                 }
         if (ws > R(0)) {
             const R phv = phs / ws;
+            const R sa = fmin(fmax(R(0.5) * (R(1) + phv), R(0)), R(1));
+            acc[6] = (double)(sa * dA);
+            acc[7] = (double)dA;
             const R g0 = gs[0] / ws, g1 = gs[1] / ws, g2 = gs[2] / ws;
             if (fabs(phv) < R(1)) {
                 const R eps2 = (R)(I.grad_eps * I.grad_eps);
@@ -226,7 +234,7 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
             }
         }
     }
-    block_sum6(acc, L.cap_part + ((long long)p * CAP_BLOCKS + blockIdx.x) * 6);
+    block_sum<CAP_PART>(acc, L.cap_part + ((long long)p * CAP_BLOCKS + blockIdx.x) * CAP_PART);
 }
 
 
@@ -372,14 +380,14 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
         const int lane = tid & 31, wid = tid >> 5;
         for (int p = wid; p < np; p += DEM_THREADS / 32) {
             const long long pg = I.part_off + p;
-            double s[18];
-            for (int a = 0; a < 18; a++) s[a] = 0.0;
+            double s[12 + CAP_PART];
+            for (int a = 0; a < 12 + CAP_PART; a++) s[a] = 0.0;
             for (int b = lane; b < L.mem_blocks; b += 32)
                 for (int a = 0; a < MEM_PART; a++) s[a] += L.mem_part[(pg * L.mem_blocks + b) * MEM_PART + a];
             for (int b = lane; b < CAP_BLOCKS; b += 32)
-                for (int a = 0; a < 6; a++) s[12 + a] += L.cap_part[(pg * CAP_BLOCKS + b) * 6 + a];
+                for (int a = 0; a < CAP_PART; a++) s[12 + a] += L.cap_part[(pg * CAP_BLOCKS + b) * CAP_PART + a];
             for (int o = 16; o > 0; o >>= 1)
-                for (int a = 0; a < 18; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
+                for (int a = 0; a < 12 + CAP_PART; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
             if (lane == 0) {
                 // momentum exchange: small part plus the exact rest part
                 // -(rho0/18) K, -(rho0/18) (M - delta x K), M = (2M)/2
@@ -398,6 +406,18 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
                     P[p].Fsig[a] = s[12 + a];
                     P[p].Tsig[a] = s[15 + a];
                 }
+                // buoyancy (reading c28): a flat interface at height h = (2a - 1) R
+                // above the centre leaves the volume fraction (1 + t)^2 (2 - t)/4,
+                // t = h/R, of the sphere below it (a spherical zone's area is
+                // proportional to its height)
+                double sub = 0.0;
+                if (s[19] > 0.0) {
+                    const double t = 2.0 * (s[18] / s[19]) - 1.0;
+                    sub = (1.0 + t) * (1.0 + t) * (2.0 - t) / 4.0;
+                }
+                const double vol = 4.0 / 3.0 * M_PI * P[p].R * P[p].R * P[p].R;
+                P[p].sub = sub;
+                for (int a = 0; a < 3; a++) P[p].Fb[a] = vol * sub * I.buoy[a];
             }
         }
         __syncthreads();
@@ -470,7 +490,7 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
         for (int a = 0; a < 3; a++) {
             Q_.Fc[a] = Fc[a];
             Q_.Tc[a] = Tc[a];
-            F[a] = Fc[a] + I.g_part[a] + Q_.Feta[a] + Q_.Fsig[a];
+            F[a] = Fc[a] + I.g_part[a] + Q_.Feta[a] + Q_.Fsig[a] + Q_.Fb[a];
             Tq[a] = Tc[a] + Q_.Teta[a] + Q_.Tsig[a];
             wold[a] = Q_.w[a];
             Q_.x_old[a] = Q_.x[a];

@@ -25,7 +25,8 @@ STATUS_NAMES = ["LBM_OK", "LBM_ERR_ARG", "LBM_ERR_OOM", "LBM_ERR_CUDA", "LBM_ERR
 # amplitude and normal are FP64 in the FP64 form and FP32 otherwise
 PRECISIONS = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 FIELD_RHO_A, FIELD_RHO_B, FIELD_PHI, FIELD_U, FIELD_POPS, FIELD_OWNER = 1, 2, 4, 8, 16, 32
-PARTICLE_RECORD = 32
+PARTICLE_RECORD = 36
+PARTICLE_STATE = 19
 MAX_PARTICLES = 61
 # velocity order of population arrays at the ABI (LBM_C)
 LBM_C = np.array([[0, 0, 0], [1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 0],
@@ -60,6 +61,7 @@ class lbm_params(ct.Structure):
         ("drop_speed_kp", ct.c_double), ("drop_speed_ki", ct.c_double), ("drop_speed_interval", ct.c_int),
         ("pressure_z", ct.c_int), ("rho_in", ct.c_double), ("rho_out", ct.c_double),
         ("surrogate_box", ct.c_double),
+        ("buoyancy_a", ct.c_double * 3),
     ]
 
 
@@ -79,7 +81,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
            "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion",
-           "lbm_inject_fault"]
+           "lbm_inject_fault", "lbm_particle_state_size", "lbm_get_particle_state", "lbm_set_particle_state"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -123,6 +125,8 @@ def load(path: str = LIB_PATH):
     L.lbm_fluid_form_in_use.restype = i
     L.lbm_last_launch_count.argtypes = [vp]
     L.lbm_last_launch_count.restype = ct.c_longlong
+    L.lbm_particle_state_size.argtypes = [vp, i]
+    L.lbm_particle_state_size.restype = ct.c_longlong
     L.lbm_profile.argtypes = [vp, i]
     L.lbm_profile_read.argtypes = [vp, d, i]
     L.lbm_component_masses_noalloc.argtypes = [vp, ct.c_longlong, vp, vp]
@@ -139,9 +143,11 @@ def load(path: str = LIB_PATH):
     L.lbm_drop_speed_state.argtypes = [vp, i, d]
     L.lbm_autotune.argtypes = [vp, i, P(ct.c_int), P(ct.c_int), d]
     L.lbm_inject_fault.argtypes = [vp, i]
+    L.lbm_get_particle_state.argtypes = [vp, i, d, ct.c_size_t]
+    L.lbm_set_particle_state.argtypes = [vp, i, d, ct.c_size_t]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
-                        "lbm_last_launch_count"):
+                        "lbm_last_launch_count", "lbm_particle_state_size"):
             getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -155,6 +161,7 @@ PARAM_DEFAULTS = dict(
     surrogate_u_ref=0.0, surrogate_r_ref=0.0, surrogate_shell_gap=0.0,
     drop_speed_control=0, drop_speed_target=(0.0, 0.0, 0.0), drop_speed_kp=0.0, drop_speed_ki=0.0,
     drop_speed_interval=0, pressure_z=0, rho_in=1.0, rho_out=1.0, surrogate_box=0.0,
+    buoyancy_a=(0.0, 0.0, 0.0),
 )
 
 
@@ -278,6 +285,20 @@ class Context:
         out = np.zeros((max(n, 1), PARTICLE_RECORD)) if out is None else out
         self._check(self.L.lbm_particle_forces(self.h, inst, _dp(out)))
         return out[:n]
+
+    def lbm_get_particle_state(self, inst=0):
+        """The particles' checkpoint (include/lbm.h): LBM_PARTICLE_STATE
+        doubles per particle, then the friction-spring histories."""
+        n = int(self.L.lbm_particle_state_size(self.h, inst))
+        if n < 0:
+            raise LbmError(1, "bad instance")
+        out = np.zeros(max(n, 1))
+        self._check(self.L.lbm_get_particle_state(self.h, inst, _dp(out), ct.c_size_t(n)))
+        return out[:n]
+
+    def lbm_set_particle_state(self, state, inst=0):
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        self._check(self.L.lbm_set_particle_state(self.h, inst, _dp(st), ct.c_size_t(st.size)))
 
     def lbm_read_fields(self, mask, inst=0, out=None):
         N = self.num_nodes(inst)

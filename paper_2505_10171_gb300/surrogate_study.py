@@ -2,25 +2,32 @@
 grids, through the C ABI.
 
 Resolved runs of a 256 x 128 x 128 drop-sphere set-up (R_p = 8, see
-_setup) give the training samples: every `every` steps, the 387 shell inputs
-of each sphere and its resolved fluid force and torque (momentum exchange
-plus capillary), divided by sigma R_p and sigma R_p^2.  The test set-ups are
-the same runs at 3/8 scale (96 x 48 x 48, drop R = 15, R_p = 3, U and sigma
-scaled by 3/8, viscosities kept: diffusive scaling, so that t U / R_p and
-the step count match).  They run twice on the coarse grid, with the plain
-coarse forces and with the surrogate, and both are compared with the
-resolved runs of the same seeds at the same steps.
+_setup) give the labels: every `every` steps, each sphere's resolved fluid
+force and torque (momentum exchange plus capillary), divided by sigma R_p and
+sigma R_p^2.  The coarse set-ups are the same runs at 3/8 scale (96 x 48 x 48,
+drop R = 15, R_p = 3, U and sigma scaled by 3/8, viscosities kept: diffusive
+scaling, so that t U / R_p and the step count match).  Held-out seeds run on
+the coarse grid with the plain coarse forces and with the surrogate, and both
+are compared with the resolved runs of the same seeds at the same steps.
 
 Choices (the paper has no surrogate): the shell has radius 1.5 R_p on either
-grid; the resolved inputs are box-filtered over one coarse cell (width 8/3
-resolved units, 27-point midpoint rule) so that they see the fields at the
-coarse grid's resolution; velocities are scaled by each run's drop speed
-target U and radii by R_p.  By default the spheres are held at rest on the
-substrate (prescribed motion) while the drop sweeps over them, so that the
-resolved and coarse runs of a seed have the same particle positions at every
-sample and the comparison measures the force model alone; with free=True
-they move under the forces (the surrogate's force then also changes the
-trajectory, and a difference in trajectory shows up as force error).
+grid; velocities are scaled by each run's drop speed target U and radii by
+R_p.  The network's inputs come from one of two sources:
+  inputs="coarse" (default): the shells of the coarse run of the same seed at
+    the same step, paired with the resolved labels, so that training and use
+    see the same grid;
+  inputs="box": the resolved run's own shells, box-filtered over one coarse
+    cell (width 8/3 resolved units, 27-point midpoint rule), the reading that
+    restricts resolved fields to the coarse resolution.  Measured at 8
+    training and 8 held-out seeds, the network fitted this way is accurate on
+    resolved inputs but worse than the plain coarse method on coarse ones: the
+    coarse grid's interface is 8/3 times wider in physical units and its
+    near-sphere flow differs, which a box filter of the resolved fields does
+    not reproduce.
+The spheres are held at rest on the substrate (prescribed motion) while the
+drop sweeps over them, so that the resolved and coarse runs of a seed have
+the same particle positions at every sample: the comparison measures the
+force model alone, and the pairing of inputs and labels is exact in geometry.
 """
 from __future__ import annotations
 
@@ -42,7 +49,7 @@ BOX = 1.0 / SCALE      # box filter of the resolved inputs: one coarse cell
 MAX_NODES = 50_000_000
 
 
-def _setup(seed, s, free=False):
+def _setup(seed, s, free=False, box=0.0):
     """Drop R = 40 s driven along x at 5e-3 s over a 150 deg wall, eight
     spheres R_p = 8 s (contact angles uniform in [30, 90] deg) placed 4 to 50 s
     ahead of the drop front (centres x in [98, 152] s, y in [12, 116] s) at
@@ -65,16 +72,16 @@ def _setup(seed, s, free=False):
                   body_force_a=(2.0e-6 * s, 0.0, 0.0), g_particle=(0.0, 0.0, -2.0 * sigma * R_p),
                   drop_speed_control=1, drop_speed_target=(FINE_U * s, 0.0, 0.0), drop_speed_interval=100,
                   store_velocity=1, surrogate_u_ref=FINE_U * s, surrogate_r_ref=R_p,
-                  surrogate_shell_gap=SHELL * R_p, surrogate_box=BOX if s == 1.0 else 0.0)
+                  surrogate_shell_gap=SHELL * R_p, surrogate_box=box)
     phi = W.drop_phi(nx, ny, nz, (48.0 * s, 64.0 * s, 0.5), 40.0 * s)
     particles = [dict(x=(c[0] * s, c[1] * s, 0.5 + R_p + 1.0), R=R_p, rho_p=W.PARTICLE_DENSITY,
                       theta_deg=float(t), kinematic=0 if free else 1) for c, t in zip(centres, thetas)]
     return dict(params=params, phi=phi, particles=particles)
 
 
-def resolved(seed, free=False):
-    """The resolved (R_p = 8) set-up of a seed."""
-    return _setup(seed, 1.0, free)
+def resolved(seed, free=False, box=BOX):
+    """The resolved (R_p = 8) set-up of a seed (shell inputs box-filtered)."""
+    return _setup(seed, 1.0, free, box)
 
 
 def coarse(seed, free=False):
@@ -157,21 +164,34 @@ def init_weights(seed):
 
 
 def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=512, lr=1e-3, seed=9, free=False,
-             stream=None):
-    """Train on the resolved runs of train_seeds, then compare on test_seeds:
-    the network on the resolved test inputs (offline), and the coarse runs
-    with the plain forces and with the surrogate, all against the resolved
-    test runs.  The learning rate halves after half and after three quarters
-    of the epochs.  Returns the error table and the training record."""
+             inputs="coarse", stream=None):
+    """Train on train_seeds (labels from their resolved runs, inputs as
+    `inputs` says), then compare on test_seeds: the network offline on the
+    test inputs, and the coarse runs with the plain forces and with the
+    surrogate in the loop, all against the resolved test runs.  The learning
+    rate halves after half and after three quarters of the epochs.  Returns
+    the error table and the training record."""
+    if inputs not in ("coarse", "box"):
+        raise ValueError("inputs must be 'coarse' or 'box'")
+    box = inputs == "box"
     t0 = time.time()
-    tr = run([resolved(sd, free) for sd in train_seeds], steps, every, stream=stream)
-    X = np.concatenate([r["X"] for r in tr])
+    tr = run([resolved(sd, free) for sd in train_seeds], steps, every, features=box, stream=stream)
     Y = np.concatenate([r["Y"] for r in tr])
+    if box:
+        X = np.concatenate([r["X"] for r in tr])
+    else:
+        trc = run([coarse(sd, free) for sd in train_seeds], steps, every, stream=stream)
+        X = np.concatenate([r["X"] for r in trc])
+        del trc
     del tr
     t_train_data = time.time() - t0
-    ref = run([resolved(sd, free) for sd in test_seeds], steps, every, stream=stream)
+    ref = run([resolved(sd, free) for sd in test_seeds], steps, every, features=box, stream=stream)
     t_ref = time.time() - t0 - t_train_data
     cws = [coarse(sd, free) for sd in test_seeds]
+    t2 = time.time()
+    plain = run(cws, steps, every, stream=stream)
+    t_plain = time.time() - t2
+    test_X = [r["X"] for r in (ref if box else plain)]
     # the network lives in a context; a small coarse one hosts it
     host = lbm.Context(cws[0]["params"], "fp32", stream=stream)
     try:
@@ -183,29 +203,29 @@ def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=51
             losses.append(host.lbm_surrogate_train(X, Y, 1, batch, rate, seed + e))
         t_fit = time.time() - t1
         weights = host.lbm_surrogate_save()
-        pred = [np.concatenate([host.lbm_surrogate_predict(r["X"][i:i + lbm.MLP_MAX_BATCH])
-                                for i in range(0, len(r["X"]), lbm.MLP_MAX_BATCH)]).astype(np.float64)
-                for r in ref]
+        pred = [np.concatenate([host.lbm_surrogate_predict(x[i:i + lbm.MLP_MAX_BATCH])
+                                for i in range(0, len(x), lbm.MLP_MAX_BATCH)]).astype(np.float64)
+                for x in test_X]
     finally:
         host.close()
-    t2 = time.time()
-    plain = run(cws, steps, every, features=False, stream=stream)
+    t3 = time.time()
     sur = run(cws, steps, every, weights=weights, features=False, stream=stream)
-    t_coarse = time.time() - t2
+    t_sur = time.time() - t3
     Yr = np.concatenate([r["Y"] for r in ref])
 
     def err(rows):
         return list(errors(np.concatenate(rows), Yr))
 
-    table = dict(samples=int(X.shape[0]), test_samples=int(Yr.shape[0]), train_seeds=len(train_seeds),
-                 test_seeds=len(test_seeds), steps=steps, every=every, epochs=epochs, free=bool(free),
-                 label_rms=float(np.sqrt((Y * Y).mean())),
+    table = dict(inputs=inputs, samples=int(X.shape[0]), test_samples=int(Yr.shape[0]),
+                 train_seeds=len(train_seeds), test_seeds=len(test_seeds), steps=steps, every=every,
+                 epochs=epochs, free=bool(free), label_rms=float(np.sqrt((Y * Y).mean())),
                  ref_force_mean=float(np.linalg.norm(Yr[:, 0:3], axis=1).mean()),
                  ref_torque_mean=float(np.linalg.norm(Yr[:, 3:6], axis=1).mean()),
                  offline=err(pred), plain_coarse=err([p["Y"] for p in plain]),
                  surrogate_coarse=err([p["Y"] for p in sur]),
                  loss_first=losses[0], loss_last=losses[-1],
-                 seconds=dict(train_data=t_train_data, reference=t_ref, fit=t_fit, coarse_runs=t_coarse))
+                 seconds=dict(train_data=t_train_data, reference=t_ref, fit=t_fit, plain_coarse=t_plain,
+                              surrogate_coarse=t_sur))
     return table, dict(losses=losses, weights=weights)
 
 
@@ -217,11 +237,13 @@ def main():
     ap.add_argument("--every", type=int, default=16)
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--free", action="store_true", help="free spheres instead of held ones")
+    ap.add_argument("--inputs", choices=("coarse", "box"), default="coarse",
+                    help="network inputs: coarse-run shells, or box-filtered resolved shells")
     ap.add_argument("--out", default=None, help="write the error table as JSON here")
     ap.add_argument("--weights", default=None, help="write the trained FP32 weights (.npy) here")
     a = ap.parse_args()
     table, rec = campaign(list(range(1, a.train + 1)), list(range(1001, 1001 + a.test)), steps=a.steps,
-                          every=a.every, epochs=a.epochs, free=a.free)
+                          every=a.every, epochs=a.epochs, free=a.free, inputs=a.inputs)
     table["losses"] = rec["losses"]
     print(json.dumps(table))
     if a.out:

@@ -48,10 +48,10 @@ def test_struct_layout_matches_header(libpath):
 #include <stddef.h>
 #include "lbm.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(lbm_params), offsetof(lbm_params, g_particle),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %d\n", sizeof(lbm_params), offsetof(lbm_params, g_particle),
          offsetof(lbm_params, store_velocity), offsetof(lbm_params, diag_interval), sizeof(lbm_particle),
          offsetof(lbm_particle, theta_deg), offsetof(lbm_particle, kinematic), offsetof(lbm_params, pressure_z),
-         offsetof(lbm_params, rho_out));
+         offsetof(lbm_params, rho_out), offsetof(lbm_params, buoyancy_a), LBM_PARTICLE_RECORD);
   return 0; }
 """
     with tempfile.TemporaryDirectory() as d:
@@ -62,7 +62,8 @@ int main(void) {
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     P, Pa = lbm.lbm_params, lbm.lbm_particle
     assert vals == [ct.sizeof(P), P.g_particle.offset, P.store_velocity.offset, P.diag_interval.offset,
-                    ct.sizeof(Pa), Pa.theta_deg.offset, Pa.kinematic.offset, P.pressure_z.offset, P.rho_out.offset]
+                    ct.sizeof(Pa), Pa.theta_deg.offset, Pa.kinematic.offset, P.pressure_z.offset, P.rho_out.offset,
+                    P.buoyancy_a.offset, lbm.PARTICLE_RECORD]
 
 
 def test_abi_velocity_order_matches_header():
@@ -104,7 +105,7 @@ BASE = dict(nx=8, ny=8, nz=8)
     dict(cap_norm=-1.0), dict(grad_eps=-1e-4), dict(surrogate_shell_gap=-1.0),
     dict(drop_speed_control=8), dict(drop_speed_interval=-1),
     dict(pressure_z=1, wall_z0=1), dict(pressure_z=1, rho_in=0.0), dict(pressure_z=1, nz=3),
-    dict(surrogate_box=-1.0),
+    dict(surrogate_box=-1.0), dict(buoyancy_a=(0.0, 0.0, float("nan"))),
 ])
 def test_create_rejects_invalid_parameters(libpath, bad):
     """Parameters are checked before any device call: an invalid one gives

@@ -547,3 +547,60 @@ def test_fp64_pressure_tube_with_sphere_matches_oracle():
     o = run_oracle(w, 60)
     assert o["parts"][0][20] > 16.0  # it moved downstream
     assert_fp64_parity(run_gpu(w, 60, "fp64"), o)
+
+
+def test_resume_with_contacts_from_particle_checkpoint():
+    """A sphere pressed onto the sliding substrate (its friction springs are
+    loaded) next to a drop: after 60 steps the populations and the particle
+    checkpoint (state and spring histories) are read, a new context is built
+    from them, and the continued run equals the uninterrupted one to rounding
+    (FP64).  Restoring everything but the springs does not."""
+    w = W.cfg1()
+    w["params"] = dict(w["params"], g_particle=(0.0, 0.0, -0.01))
+    c = gpu_ctx(w, "fp64")
+    c.lbm_step(60)
+    fa, fb = c.pops()
+    st = c.lbm_get_particle_state()
+    c.lbm_step(40)
+    ref_a, ref_b = c.pops()
+    ref = c.lbm_particle_forces()[0]
+    c.close()
+    from paper_2505_10171_gb300 import lbm
+    assert st.size == lbm.PARTICLE_STATE + 2 * 6
+    assert np.abs(st[lbm.PARTICLE_STATE:]).max() > 0.0  # the substrate spring is loaded
+    out = {}
+    for keep in (True, False):
+        w2 = dict(w, particles=[dict(w["particles"][0], x=tuple(st[0:3]))])
+        r = gpu_ctx(w2, "fp64")
+        r.lbm_init_fields(None, pops=np.concatenate([fa, fb]))
+        s2 = st.copy()
+        if not keep:
+            s2[lbm.PARTICLE_STATE:] = 0.0
+        r.lbm_set_particle_state(s2)
+        r.lbm_step(40)
+        out[keep] = (r.pops(), r.lbm_particle_forces()[0])
+        r.close()
+    (ga, gb), rg = out[True]
+    assert max(np.abs(ga - ref_a).max(), np.abs(gb - ref_b).max()) <= 1e-12
+    assert np.abs(rg[12:27] - ref[12:27]).max() <= 1e-13
+    rh = out[False][1]
+    assert np.abs(rh[12:18] - ref[12:18]).max() > 1e-9  # the contact force depends on the springs
+
+
+def test_particle_checkpoint_is_checked():
+    w = W.cfg1()
+    c = gpu_ctx(w, "fp64")
+    st = c.lbm_get_particle_state()
+    from paper_2505_10171_gb300 import lbm
+    bad = st.copy()
+    bad[0] += 0.25  # another position than the one the particle was added at
+    with pytest.raises(lbm.LbmError):
+        c.lbm_set_particle_state(bad)
+    with pytest.raises(lbm.LbmError):
+        c.lbm_set_particle_state(st[:-1])
+    c.lbm_set_particle_state(st)
+    c.lbm_step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        c.lbm_set_particle_state(st)  # after the first step
+    assert e.value.status == 4  # LBM_ERR_STATE
+    c.close()

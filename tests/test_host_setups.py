@@ -44,7 +44,8 @@ def test_campaign_setups_scale_consistently(seed):
     in x and y; every sphere keeps a fluid node between itself and the wall
     (delta_R = 1 unscaled, centre R_p + 1.5 above the wall plane) and clear of
     the others by more than the contact distance; sigma, the drop speed and
-    the shell scale as the campaign states."""
+    the shell (radius 1.5 R_p on either grid) scale as the campaign states;
+    only the resolved inputs are box-filtered, over one coarse cell."""
     f, c = SS.resolved(seed), SS.coarse(seed)
     s = SS.SCALE
     pf, pc = f["params"], c["params"]
@@ -52,7 +53,10 @@ def test_campaign_setups_scale_consistently(seed):
     assert abs(pc["sigma"] - pf["sigma"] * s) < 1e-15
     assert abs(pc["drop_speed_target"][0] - pf["drop_speed_target"][0] * s) < 1e-15
     assert pc["delta_R"] == pf["delta_R"] == 1.0
-    assert abs(pc["surrogate_shell_gap"] - 2.0) < 1e-12 and abs(pf["surrogate_shell_gap"] - 2.0 / s) < 1e-12
+    Rf, Rc_ = f["particles"][0]["R"], c["particles"][0]["R"]
+    assert abs(pc["surrogate_shell_gap"] - 0.5 * Rc_) < 1e-12 and abs(pf["surrogate_shell_gap"] - 0.5 * Rf) < 1e-12
+    assert pc["surrogate_box"] == 0.0 and abs(pf["surrogate_box"] - 1.0 / s) < 1e-12
+    assert all(q["kinematic"] == 1 for q in f["particles"] + c["particles"])  # held spheres
     for qf, qc in zip(f["particles"], c["particles"]):
         assert abs(qc["x"][0] - qf["x"][0] * s) < 1e-12 and abs(qc["x"][1] - qf["x"][1] * s) < 1e-12
         for q, p in ((qf, pf), (qc, pc)):
