@@ -279,3 +279,38 @@ def capture_map(mus, mu_rs, steps=40000, sample_every=500, precision="fp16", str
     finally:
         ctx.close()
     return out
+
+
+def main():
+    """Command line: run one of the long set-ups and write its record (JSON)."""
+    import argparse
+    import json
+    import sys
+    import time
+    ap = argparse.ArgumentParser(description="long validation runs of the method, through the C ABI")
+    sub = ap.add_subparsers(dest="case", required=True)
+    t = sub.add_parser("tube-pressure", help="Segre-Silberberg tube with pressure faces (Sec. V B, V D)")
+    t.add_argument("--steps", type=int, default=116000)
+    t.add_argument("--every", type=int, default=2000)
+    m = sub.add_parser("friction-map", help="collision outcomes over (mu, mu_r) (Sec. VI C)")
+    m.add_argument("--steps", type=int, default=40000)
+    m.add_argument("--every", type=int, default=1000)
+    m.add_argument("--grid", default="0,0.2,0.4,0.6,0.8,1.0", help="values of mu and of mu_r")
+    ap.add_argument("--out", required=True, help="JSON record to write")
+    a = ap.parse_args()
+    t0 = time.time()
+    if a.case == "tube-pressure":
+        r = tube_pressure_migration(steps=a.steps, sample_every=a.every)
+        rec = dict(t=[int(v) for v in r["t"]], l_over_Rt=[round(float(v), 5) for v in r["l"]],
+                   axial_position=[round(float(v), 2) for v in r["z"]], u_mean_far=r["u_mean"], v_in=r["v_in"])
+    else:
+        grid = [float(v) for v in a.grid.split(",")]
+        rec = dict(cases=capture_map(grid, grid, steps=a.steps, sample_every=a.every))
+    rec["seconds"] = time.time() - t0
+    rec["command"] = "python -m paper_2505_10171_gb300.validation " + " ".join(sys.argv[1:])
+    json.dump(rec, open(a.out, "w"), indent=1)
+    print(json.dumps(rec)[:2000])
+
+
+if __name__ == "__main__":
+    main()
