@@ -60,10 +60,12 @@ def design_bytes_per_node(stage, prec):
     return {"phi": 19 * e + 5 * r, "grad_wetting": 6 * r, "collide": 38 * e + 10 * r}.get(stage, 0)
 
 
-# DRAM bytes (read + write) per launch of a kernel from one ncu capture of
-# this workload, keyed to the SHA-256 of the fluid-kernel sources it was taken
-# with: reported only while those sources are unchanged
-NCU_TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
+# kernel, from one ncu --set full capture of the 256x128x64 crop of the
+# workload (python -m paper_2505_10171_gb300.profile_case fp32), scaled by
+# the node count to the 256x128x128 launch (traffic grows with the nodes);
+# valid only for the fluid-kernel sources it was taken on (their hash)
+NCU_TRAFFIC = {("collide", "fp32"): (2 * 349711104, "42ac16d839a2606d")}
 FLUID_SOURCES = ("paper_2505_10171_gb300/csrc/lbm_fluid.cu", "paper_2505_10171_gb300/csrc/lbm_node.cuh",
                  "paper_2505_10171_gb300/csrc/lbm_internal.cuh")
 
