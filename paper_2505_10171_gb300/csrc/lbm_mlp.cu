@@ -10,11 +10,14 @@
 // 128 threads per 128-row by BN-column tile.  Per 64-wide chunk of k the CTA
 // writes A (128 x 64) and B (BN x 64) into shared memory in the canonical
 // K-major layout without swizzle (8-row x 16-byte core matrices: along k
-// LBO apart, along rows 128 bytes apart), thread 0 issues four
-// tcgen05.mma.kind::f16 (K = 16 each) and commits them to an mbarrier that
-// every thread waits on (bounded).  The epilogue reads the FP32 accumulator
-// with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows) and applies
-// bias, tanh or the tanh derivative.
+// LBO apart, along rows 128 bytes apart), with 16-byte loads where the operand
+// is contiguous along k or along its rows; thread 0 issues four
+// tcgen05.mma.kind::f16 (K = 16 each) and commits them to the stage's
+// mbarrier.  Two stages: the chunk after is staged while the tensor core
+// works on the one before, and a stage is refilled only once the commit of the
+// chunk that read it has arrived (bounded waits).  The epilogue reads the FP32
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = tile rows)
+// and applies bias, tanh or the tanh derivative.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -99,21 +102,24 @@ __host__ __device__ constexpr uint32_t idesc_bf16()
 
 constexpr int GM = 128;  // tile rows (TMEM lanes)
 constexpr int GK = 64;   // k per staged chunk
+#ifndef LBM_GEMM_BN
+#define LBM_GEMM_BN 64
+#endif
+constexpr int BNH = LBM_GEMM_BN;  // column tile of the GEMMs with 128 or more columns
 
-// shared memory: barrier and TMEM slot, then A and B regions.  Each region is
-// larger than its tile so that even reading the core-matrix strides the
-// other way round (rows LBO apart, k 128 bytes apart) stays inside it.
+// shared memory: two barriers and the TMEM slot, then two stages of A and B.
+// A stage holds exactly its tile: the four MMAs of a chunk read core matrices
+// 2j LBO + {0, LBO} + 16 row groups x 128 bytes, j < 4, i.e. 8 LBO bytes.
 template <int BN>
 struct GemmSmem {
     static constexpr int HEAD = 128;
     static constexpr int A_LBO = GM / 8 * 128;  // bytes between core matrices along k
     static constexpr int B_LBO = BN / 8 * 128;
-    // tile: 2 ROWS GK bytes; read the other way round, slice j = 0..3 reaches
-    // 2j LBO + (ROWS/8 - 1) LBO + 2 x 128 bytes: 43 KB for 128 rows
-    static constexpr int A_BYTES = 48 * 1024;
-    static constexpr int B_BYTES = BN >= 64 ? 48 * 1024 : 4096;
-    static constexpr int BYTES = HEAD + A_BYTES + B_BYTES;
+    static constexpr int A_STAGE = GM * GK * 2;
+    static constexpr int B_STAGE = BN * GK * 2;
+    static constexpr int BYTES = HEAD + 2 * (A_STAGE + B_STAGE);
 };
+static_assert(GemmSmem<128>::BYTES <= 227 * 1024, "two stages fit in shared memory");
 
 struct GemmArgs {
     int Mv, Nv, Kv;  // valid extents
@@ -134,25 +140,70 @@ struct GemmArgs {
     long long wait_limit;  // clock cycles a wait on the commit barrier may take
 };
 
-// one chunk of rows r0.. (ROWS of them) and k0..k0+GK into the canonical layout
+// one chunk of rows r0.. (ROWS of them) and k0..k0+GK into the canonical
+// layout.  vec: 1 = the operand is contiguous along k (sk = 1), 2 = along its
+// rows (sr = 1), both with 16-byte aligned runs of 8 (checked by the caller):
+// runs of 8 elements wholly inside the valid extents move as one 16-byte load;
+// the rest element by element, zero outside the extents.
 template <int ROWS>
 __device__ __forceinline__ void stage_tile(const bf16 *P, long long sr, long long sk, int r0, int rv, int k0, int kv,
-                                           unsigned char *dst)
+                                           int vec, unsigned char *dst)
 {
-    for (int i = threadIdx.x; i < ROWS * GK; i += GM) {
-        int r, k;
-        if (sk == 1) {
-            r = i / GK;
-            k = i % GK;
-        } else {
-            k = i / ROWS;
-            r = i % ROWS;
+    auto at = [&](int r, int k) {
+        return (bf16 *)(dst + ((k >> 3) * (ROWS / 8) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+    };
+    auto scalar8 = [&](int r, int k, int dr, int dk) {
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int gr = r0 + r + e * dr, gk = k0 + k + e * dk;
+            bf16 v = __float2bfloat16_rn(0.0f);
+            if (gr < rv && gk < kv) v = P[(long long)gr * sr + (long long)gk * sk];
+            *at(r + e * dr, k + e * dk) = v;
         }
-        const int gr = r0 + r, gk = k0 + k;
-        bf16 v = __float2bfloat16_rn(0.0f);
-        if (gr < rv && gk < kv) v = P[(long long)gr * sr + (long long)gk * sk];
-        *(bf16 *)(dst + ((k >> 3) * (ROWS / 8) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2) = v;
+    };
+    if (vec == 1) {
+        // one core-matrix row (8 k values, 16 bytes) per vector
+        for (int i = threadIdx.x; i < ROWS * (GK / 8); i += GM) {
+            const int r = i / (GK / 8), k = (i % (GK / 8)) * 8;
+            const int gr = r0 + r, gk = k0 + k;
+            if (gr < rv && gk + 8 <= kv)
+                *(uint4 *)at(r, k) = *(const uint4 *)(P + (long long)gr * sr + gk);
+            else
+                scalar8(r, k, 0, 1);
+        }
+    } else if (vec == 2) {
+        // 8 rows at one k: a core-matrix column (consecutive threads take
+        // consecutive k, whose 2-byte stores share 32-bit words)
+        for (int i = threadIdx.x; i < (ROWS / 8) * GK; i += GM) {
+            const int r = (i / GK) * 8, k = i % GK;
+            const int gr = r0 + r, gk = k0 + k;
+            if (gr + 8 <= rv && gk < kv) {
+                const uint4 w = *(const uint4 *)(P + gr + (long long)gk * sk);
+                const bf16 *h = (const bf16 *)&w;
+#pragma unroll
+                for (int e = 0; e < 8; e++) *at(r + e, k) = h[e];
+            } else {
+                scalar8(r, k, 1, 0);
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < ROWS * GK; i += GM) {
+            const int r = i / GK, k = i % GK;
+            const int gr = r0 + r, gk = k0 + k;
+            bf16 v = __float2bfloat16_rn(0.0f);
+            if (gr < rv && gk < kv) v = P[(long long)gr * sr + (long long)gk * sk];
+            *at(r, k) = v;
+        }
     }
+}
+
+// which staging path an operand takes (the same for every thread of the grid)
+__device__ __forceinline__ int vec_mode(const bf16 *P, long long sr, long long sk)
+{
+    if (((uintptr_t)P & 15) != 0) return 0;
+    if (sk == 1 && sr % 8 == 0) return 1;
+    if (sr == 1 && sk % 8 == 0) return 2;
+    return 0;
 }
 
 template <int BN>
@@ -160,10 +211,11 @@ __global__ void __launch_bounds__(GM) k_gemm_tc(GemmArgs g)
 {
     using Sm = GemmSmem<BN>;
     extern __shared__ __align__(1024) unsigned char gsm[];
-    unsigned char *As = gsm + Sm::HEAD;
-    unsigned char *Bs = As + Sm::A_BYTES;
-    const uint32_t bar = smem_addr(gsm);
-    const uint32_t slot = smem_addr(gsm + 8);
+    // stage st: A at As0 + st A_STAGE, B at Bs0 + st B_STAGE, barrier bar0 + 8 st
+    unsigned char *const As0 = gsm + Sm::HEAD;
+    unsigned char *const Bs0 = gsm + Sm::HEAD + 2 * Sm::A_STAGE;
+    const uint32_t bar0 = smem_addr(gsm);
+    const uint32_t slot = smem_addr(gsm + 16);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.x * GM, n0 = blockIdx.y * BN;
     constexpr uint32_t NCOLS = BN < 32 ? 32 : BN;
@@ -173,20 +225,34 @@ __global__ void __launch_bounds__(GM) k_gemm_tc(GemmArgs g)
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(bar, 1);
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
         mbar_fence_init();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *(volatile uint32_t *)(gsm + 8);
+    const uint32_t tmem = *(volatile uint32_t *)(gsm + 16);
+    const int va = vec_mode(g.A, g.sam, g.sak), vb = vec_mode(g.B, g.sbn, g.sbk);
 
+    // chunk c uses stage c & 1 and commits to that stage's barrier, whose
+    // phases complete in chunk order, the one of chunk c having parity
+    // (c >> 1) & 1, and at most one of its phases is ever pending
     const int nchunks = (g.Kv + GK - 1) / GK;
     bool ok = true;
-    int c = 0;
-    for (; c < nchunks; c++) {
-        stage_tile<GM>(g.A, g.sam, g.sak, m0, g.Mv, c * GK, g.Kv, As);
-        stage_tile<BN>(g.B, g.sbn, g.sbk, n0, g.Nv, c * GK, g.Kv, Bs);
+    int last = -1;  // last chunk whose MMAs were committed
+    for (int c = 0; c < nchunks; c++) {
+        const int st = c & 1;
+        if (c >= 2) {
+            // the MMAs of chunk c - 2 read this stage
+            ok = mbar_wait_bounded(bar0 + 8 * st, (unsigned)(((c - 2) >> 1) & 1), g.wait_limit);
+            if (__syncthreads_or(!ok)) break;
+            tc_fence_after();
+        }
+        unsigned char *const As = As0 + st * Sm::A_STAGE;
+        unsigned char *const Bs = Bs0 + st * Sm::B_STAGE;
+        stage_tile<GM>(g.A, g.sam, g.sak, m0, g.Mv, c * GK, g.Kv, va, As);
+        stage_tile<BN>(g.B, g.sbn, g.sbk, n0, g.Nv, c * GK, g.Kv, vb, Bs);
         fence_async_smem();
         __syncthreads();
         if (tid == 0 && !g.no_mma) {
@@ -197,18 +263,23 @@ __global__ void __launch_bounds__(GM) k_gemm_tc(GemmArgs g)
                 const uint64_t bd = smem_desc(smem_addr(Bs) + j * 2 * Sm::B_LBO, Sm::B_LBO, 128);
                 tc_mma_bf16(tmem, ad, bd, idesc_bf16<BN>(), (c > 0 || j > 0) ? 1u : 0u);
             }
-            tc_commit(bar);
+            tc_commit(bar0 + 8 * st);
         }
-        ok = mbar_wait_bounded(bar, (unsigned)(c & 1), g.wait_limit);
-        if (__syncthreads_or(!ok)) break;
+        last = c;
+    }
+    // a commit covers every MMA this thread issued before it: the last one's
+    // arrival means the accumulator is complete
+    if (ok && last >= 0) {
+        ok = mbar_wait_bounded(bar0 + 8 * (last & 1), (unsigned)((last >> 1) & 1), g.wait_limit);
+        ok = !__syncthreads_or(!ok);
         tc_fence_after();
     }
     if (!ok) {
         if (tid == 0) {
             atomicOr(g.status, ST_TIMEOUT);
-            // the MMAs of the chunk still in flight (none were issued under the
-            // fault injection) must finish before the tensor memory is freed
-            if (!g.no_mma) mbar_wait_bounded(bar, (unsigned)(c & 1));
+            // MMAs still in flight (none are issued under the fault injection)
+            // must finish before the tensor memory is freed
+            if (!g.no_mma && last >= 0) mbar_wait_bounded(bar0 + 8 * (last & 1), (unsigned)((last >> 1) & 1));
         }
     } else if (nchunks > 0) {
         const int m = m0 + warp * 32 + lane;
@@ -459,11 +530,11 @@ cudaError_t mlp_forward(const Mlp &m, int n, unsigned *status, cudaStream_t st)
     // h1 = tanh(X W1^T + b1)
     GemmArgs a = gargs(n, MLP_HIDDEN, MLP_KIN, m.X, MLP_KIN, 1, m.W1b, MLP_KIN, 1, status);
     a.bias = b1; a.act = 1; a.C16 = m.H1; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<BNH>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // h2 = tanh(h1 W2^T + b2)
     a = gargs(n, MLP_HIDDEN, MLP_HIDDEN, m.H1, MLP_HIDDEN, 1, m.W2b, MLP_HIDDEN, 1, status);
     a.bias = b2; a.act = 1; a.C16 = m.H2; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<BNH>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // y = h2 W3^T + b3  ([n][16], columns 6..15 unused)
     a = gargs(n, MLP_NOUT, MLP_HIDDEN, m.H2, MLP_HIDDEN, 1, m.W3b, MLP_HIDDEN, 1, status);
     a.bias = b3; a.C32 = m.Y; a.scm = 16; a.scn = 1;
@@ -486,20 +557,20 @@ cudaError_t mlp_backward(const Mlp &m, int n, double *acc, unsigned *status, cud
     // dz2 = (dY W3) * (1 - h2^2)
     a = gargs(n, MLP_HIDDEN, MLP_NOUT, m.dYb, 16, 1, m.W3b, 1, MLP_HIDDEN, status);
     a.act = 2; a.g = m.H2; a.sgm = MLP_HIDDEN; a.sgn = 1; a.C16 = m.dZ2; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<BNH>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // dW2[o][i] = sum_b dz2[b][o] h1[b][i]
     a = gargs(MLP_HIDDEN, MLP_HIDDEN, n, m.dZ2, 1, MLP_HIDDEN, m.H1, 1, MLP_HIDDEN, status);
     a.C32 = g + MLP_OFF_W2; a.scm = MLP_HIDDEN; a.scn = 1;
-    if ((e = gemm<128>(mode(a, m), MLP_HIDDEN, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<BNH>(mode(a, m), MLP_HIDDEN, MLP_HIDDEN, st)) != cudaSuccess) return e;
     k_colsum<bf16><<<MLP_HIDDEN, EW, 0, st>>>(m.dZ2, n, MLP_HIDDEN, g + MLP_OFF_B2);
     // dz1 = (dz2 W2) * (1 - h1^2)
     a = gargs(n, MLP_HIDDEN, MLP_HIDDEN, m.dZ2, MLP_HIDDEN, 1, m.W2b, 1, MLP_HIDDEN, status);
     a.act = 2; a.g = m.H1; a.sgm = MLP_HIDDEN; a.sgn = 1; a.C16 = m.dZ1; a.s16m = MLP_HIDDEN; a.s16n = 1;
-    if ((e = gemm<128>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
+    if ((e = gemm<BNH>(mode(a, m), n, MLP_HIDDEN, st)) != cudaSuccess) return e;
     // dW1[o][i] = sum_b dz1[b][o] x[b][i]
     a = gargs(MLP_HIDDEN, MLP_KIN, n, m.dZ1, 1, MLP_HIDDEN, m.X, 1, MLP_KIN, status);
     a.C32 = g + MLP_OFF_W1; a.scm = MLP_KIN; a.scn = 1;
-    if ((e = gemm<128>(mode(a, m), MLP_HIDDEN, MLP_KIN, st)) != cudaSuccess) return e;
+    if ((e = gemm<BNH>(mode(a, m), MLP_HIDDEN, MLP_KIN, st)) != cudaSuccess) return e;
     k_colsum<bf16><<<MLP_HIDDEN, EW, 0, st>>>(m.dZ1, n, MLP_HIDDEN, g + MLP_OFF_B1);
     return cudaSuccess;
 }
