@@ -29,7 +29,7 @@ struct lbm_ctx {
     // phi: the order parameter of the last step; col: the colour record
     // (phi, b n) of the current state, one per node
     void *phi = nullptr, *col = nullptr;
-    size_t col_sz = 32;  // bytes of one colour record
+    size_t col_sz = 32;  // bytes of one node's colour record (four reals, one array each)
     void *grad = nullptr, *gmag = nullptr, *kap = nullptr, *u = nullptr;
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
@@ -202,7 +202,7 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
     R *ph = (R *)L.phi + I.node_off;
-    ColRec<R> *col = (ColRec<R> *)L.col + I.node_off;
+    const ColSlot<R> col = col_slot<R>(L, I.node_off);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if (pops) {
             double F[Q], G[Q], sF = 0.0, sG = 0.0;
@@ -227,7 +227,7 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
             for (int k = 0; k < 3; k++) a3[k] *= 4.5;
             for (int i = 0; i < Q; i++) pop.setF(i, (int)n, (R)F[i]);
             ph[n] = (R)p;
-            col[n] = ColRec<R>{(R)p, (R)a3[0], (R)a3[1], (R)a3[2]};
+            ColSlot<R>{col.p + n, col.Nt}.set(ColRec<R>{(R)p, (R)a3[0], (R)a3[1], (R)a3[2]});
             continue;
         }
         double p = phi[n];
@@ -242,7 +242,7 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
             pop.setF(i, (int)n, (R)(rr * e - 1.0));
         }
         ph[n] = (R)p;
-        col[n] = ColRec<R>{(R)p, R(0), R(0), R(0)};
+        ColSlot<R>{col.p + n, col.Nt}.set(ColRec<R>{(R)p, R(0), R(0), R(0)});
         if (I.store_u) {
             R *U = (R *)L.u;
             bool fl = (L.flags[I.node_off + n] & OWNER_MASK) == OWN_FLUID;

@@ -175,7 +175,7 @@ struct Lattice {
     uint8_t *flags;
     void *pop[2];
     void *phi;           // [Ntot] real: the order parameter of the step (outside a step: of the last one)
-    void *col;           // [Ntot] ColRec<real>: colour record (phi, b n) of the stored state
+    void *col;           // [4][Ntot] real: colour records (phi, b n) of the stored state
     void *grad;          // [3][Ntot] real: regularised interface normal n
     void *gmag;          // [Ntot] real: sqrt(|grad phi|^2 + eps^2), so grad phi = n gmag
     void *kap;           // [Ntot] real: curvature div(n) of fluid nodes
@@ -405,10 +405,10 @@ struct GlobalNbr {
 
 // The colour record of a node of the stored state (see the top of this
 // file): the order parameter phi of the collision that produced it and
-// a = b n, one 16-byte (FP64: 32-byte) aligned record, so that a pulled source
-// costs one vector load.
+// a = b n.  Stored as four arrays of Ntot reals (phi, a0, a1, a2), so that a
+// pulled source loads phi and only the components of a its direction needs.
 template <class R>
-struct alignas(4 * sizeof(R)) ColRec {
+struct ColRec {
     R p, a0, a1, a2;
 };
 
@@ -423,16 +423,51 @@ __device__ __forceinline__ R col_rec(int i, const ColRec<R> &c)
     return csq(i) == 1 ? t : t * R(0.70710678118654752440);
 }
 
-// the colour records of an instance
+// one node's record slot: p[0], p[Nt], p[2 Nt], p[3 Nt]
+template <class R>
+struct ColSlot {
+    R *p;
+    long long Nt;
+    __device__ __forceinline__ void set(const ColRec<R> &c) const
+    {
+        p[0] = c.p;
+        p[Nt] = c.a0;
+        p[2 * Nt] = c.a1;
+        p[3 * Nt] = c.a2;
+    }
+};
+
+// the colour records of an instance (read side)
 template <class R>
 struct Colour {
-    const ColRec<R> *c;
+    const R *b;
+    long long Nt;
     __device__ __forceinline__ Colour(const Lattice &L, const InstDev &I)
-        : c((const ColRec<R> *)L.col + I.node_off)
+        : b((const R *)L.col + I.node_off), Nt(L.Ntot)
     {
     }
-    __device__ __forceinline__ ColRec<R> at(int m) const { return c[m]; }
+    __device__ __forceinline__ ColRec<R> at(int m) const
+    {
+        return ColRec<R>{b[m], b[Nt + m], b[2 * Nt + m], b[3 * Nt + m]};
+    }
+    __device__ __forceinline__ R phi(int m) const { return b[m]; }
+    // col_rec(i, at(m)) from the components direction i touches
+    __device__ __forceinline__ R proj(int i, int m) const
+    {
+        R t = 0;
+        if (cx(i)) t += cx(i) * b[Nt + m];
+        if (cy(i)) t += cy(i) * b[2 * Nt + m];
+        if (cz(i)) t += cz(i) * b[3 * Nt + m];
+        return csq(i) == 1 ? t : t * R(0.70710678118654752440);
+    }
 };
+
+// the record slot of global node g
+template <class R>
+__device__ __forceinline__ ColSlot<R> col_slot(const Lattice &L, long long g)
+{
+    return ColSlot<R>{(R *)L.col + g, L.Ntot};
+}
 
 // Pull streaming (Sec. IV) into fluid node n, with the Sec. V A halfway
 // bounce-back where the source node is solid:
@@ -526,10 +561,9 @@ __device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const
     for (int i = 0; i < Q; i++) {
         const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
         const R F = in.F(i, s);
-        const ColRec<R> cs = C.at(s);
         sF += wgt<R>(i) * F;
-        R g = cs.p * (R(1) + F);
-        if (i) g += col_rec(i, cs);
+        R g = C.phi(s) * (R(1) + F);
+        if (i) g += C.proj(i, s);
         sG += wgt<R>(i) * g;
     }
     return sG / (R(1) + sF);

@@ -226,13 +226,13 @@ struct PairLoop<R, 10> {
 // corrected grad(phi) of the node; nn: its regularised normal; kap: curvature.
 // The recolouring of Sec. IV gives G*_i = phi (1 + F*_i) + b (c_i . n)/|c_i|
 // with b = beta/2 (rho/rho0)(1 - phi^2): the state is complete with F* and
-// the colour record (phi, b n), which are written (*C).
+// the colour record (phi, b n), which are written (C).
 template <class S>
 __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<S>::real> &P,
                                                   const typename Store<S>::real *F, typename Store<S>::real phi,
                                                   const typename Store<S>::real *g, const typename Store<S>::real *nn,
                                                   typename Store<S>::real kap, const Pop<S> &out, int n,
-                                                  ColRec<typename Store<S>::real> *C, typename Store<S>::real *U,
+                                                  const ColSlot<typename Store<S>::real> &C, typename Store<S>::real *U,
                                                   long long Ustride, unsigned *status)
 {
     using R = typename Store<S>::real;
@@ -242,7 +242,7 @@ __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<
     const CollideState<R> c = collide_state(P, F, phi, g, kap);
     if (status && (!(c.rr > R(0)) || !(phi == phi))) atomicOr(status, ST_UNSTABLE);
     if (U) { U[n] = c.ux; U[Ustride + n] = c.uy; U[2 * Ustride + n] = c.uz; }
-    *C = ColRec<R>{phi, c.bq * nn[0], c.bq * nn[1], c.bq * nn[2]};
+    C.set(ColRec<R>{phi, c.bq * nn[0], c.bq * nn[1], c.bq * nn[2]});
     Store<FT>::st(of, collide_rest(P, c, F[0]));
     PairLoop<R>::run([&](auto ic) {
         constexpr int i = decltype(ic)::value, ib = i + 9;

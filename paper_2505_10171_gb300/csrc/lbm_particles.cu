@@ -341,7 +341,7 @@ __device__ void quat_rotate(double *q, const T *w)
 }
 
 constexpr int DEM_MAXP = 61;
-constexpr int DEM_THREADS = 64;
+constexpr int DEM_THREADS = 256;  // a warp per particle for the fluid sums of up to 8 particles at once
 
 // pair index c in [0, np(np-1)/2) -> (i, j), i < j, lexicographic
 __device__ __forceinline__ void pair_of(int c, int np, int *i, int *j)
@@ -635,7 +635,7 @@ __device__ __forceinline__ R warp_sum(R v)
 
 template <class S>
 __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S> &pop,
-                            typename Store<S>::real *ph, ColRec<typename Store<S>::real> *col, const uint8_t *fli,
+                            typename Store<S>::real *ph, ColSlot<typename Store<S>::real> col, const uint8_t *fli,
                             int x, int y, int z, int lane)
 {
     using R = typename Store<S>::real;
@@ -655,7 +655,7 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
                 ok = 1;
 #pragma unroll
                 for (int j = 0; j < Q; j++) aF += wgt<R>(j) * (R(1) + pop.F(j, m));
-                aG = col[m].p * aF;
+                aG = col.p[m] * aF;
             }
         }
         sF = warp_sum(aF);
@@ -684,7 +684,7 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
     pop.setF(i, n, rr * e - R(1));
     if (lane == 0) {
         ph[n] = rd / rr;
-        col[n] = ColRec<R>{rd / rr, R(0), R(0), R(0)};
+        ColSlot<R>{col.p + n, col.Nt}.set(ColRec<R>{rd / rr, R(0), R(0), R(0)});
     }
 }
 
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int
             todo &= todo - 1;
             const int X = __shfl_sync(0xffffffffu, x, src), Y = __shfl_sync(0xffffffffu, y, src),
                       Z = __shfl_sync(0xffffffffu, z, src);
-            refill_node<S>(I, L.parts, pop, (R *)L.phi + I.node_off, (ColRec<R> *)L.col + I.node_off, fli, X, Y, Z,
+            refill_node<S>(I, L.parts, pop, (R *)L.phi + I.node_off, col_slot<R>(L, I.node_off), fli, X, Y, Z,
                            lane);
         }
     }
