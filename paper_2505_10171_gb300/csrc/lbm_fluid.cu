@@ -35,6 +35,10 @@
 #ifndef LBM_PHI_MINB_F32
 #define LBM_PHI_MINB_F32 4
 #endif
+// CTAs per SM of the boundary passes, which run beside the bulk kernels
+#ifndef LBM_BOUND_MINB
+#define LBM_BOUND_MINB 2
+#endif
 #ifndef LBM_COLLIDE_MINB
 #define LBM_COLLIDE_MINB 4
 #endif
@@ -186,7 +190,7 @@ __device__ __forceinline__ bool bound_node(const Lattice &L, const InstDev **Ip,
 // pull (Sec. V A); a node reached twice (cube and list) is written twice
 // with the same value
 template <class S>
-__global__ void __launch_bounds__(PART_THREADS, 2) k_phi_bound(Lattice L, int cur)
+__global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_phi_bound(Lattice L, int cur)
 {
     using R = typename Store<S>::real;
     const InstDev *I;
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(PART_THREADS, 2) k_phi_bound(Lattice L, int cu
 }
 
 template <class S>
-__global__ void __launch_bounds__(PART_THREADS, 2) k_collide_bound(Lattice L, int cur)
+__global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_collide_bound(Lattice L, int cur)
 {
     using R = typename Store<S>::real;
     const InstDev *I;

@@ -535,9 +535,9 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
     for (int i = 0; i < Q; i++) {
         R gi;
         if (own[i] == OWN_FLUID) {
-            const ColRec<R> cs = C->at(nbr.idx(-cx(i), -cy(i), -cz(i)));
-            gi = cs.p * (R(1) + F[i]);
-            if (i) gi += col_rec(i, cs);
+            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
+            gi = C->phi(s) * (R(1) + F[i]);
+            if (i) gi += C->proj(i, s);
         } else if (own[i] == OWN_PRESS) {
             gi = cn.p * (R(1) + F[i]) + col_rec(i, cn);
         } else {
