@@ -168,7 +168,8 @@ enum {
  * s = (1 + phi)/2 clipped to [0, 1], area-weighted over the points with a
  * fluid corner: a flat interface at height (2a - 1) R above the centre leaves
  * v = (1 + t)^2 (2 - t)/4, t = 2a - 1, below it.  Both are those of the last
- * resolved-force step (0 before the first). */
+ * resolved-force step (0 before the first), and are computed only in contexts
+ * where some instance has a nonzero buoyancy_a (0 otherwise). */
 #define LBM_PARTICLE_RECORD 36
 
 /* Create a context of n_instances instances; params points to n_instances

@@ -1041,8 +1041,10 @@ static void step_once(or_sim *s)
             }
     /* (7) capillary force, Sec. V F */
     for (int p = 0; p < s->np; p++) or_capillary(s, p, s->P[p].Fsig, s->P[p].Tsig);
-    /* (7b) buoyancy, READING c28: F_b = (4/3) pi R^3 v b_a */
-    for (int p = 0; p < s->np; p++) {
+    /* (7b) buoyancy, READING c28: F_b = (4/3) pi R^3 v b_a (v reported only
+     * where the buoyancy is on; with b_a = 0 both stay 0) */
+    const int buoy_on = s->p.buoyancy_a[0] != 0.0 || s->p.buoyancy_a[1] != 0.0 || s->p.buoyancy_a[2] != 0.0;
+    for (int p = 0; buoy_on && p < s->np; p++) {
         or_part *P = &s->P[p];
         P->sub = or_immersed_fraction(s, p);
         const double vol = 4.0 / 3.0 * M_PI * P->R * P->R * P->R;

@@ -68,7 +68,8 @@ int     or_num_particles(const or_sim *s);
 /* body force on phase a now and the phase-a velocity of the last controller update */
 void    or_get_speed_control(const or_sim *s, double *out /* [6] */);
 /* per particle 36 doubles: F_eta[3] T_eta[3] F_sig[3] T_sig[3] F_c[3] T_c[3]
-   x[3] v[3] w[3] q[4] m, immersed volume fraction in phase a, buoyancy F_b[3] */
+   x[3] v[3] w[3] q[4] m, immersed volume fraction in phase a, buoyancy F_b[3]
+   (the last two 0 while buoyancy_a is zero) */
 void    or_get_particles(const or_sim *s, double *out);
 /* per step: [0] bounce-back mass source, [1] refilled mass, [2] covered mass,
    [3] total fluid mass, [4..6] total fluid momentum (post-collision state) */

@@ -29,7 +29,7 @@ struct lbm_ctx {
     // phi: the order parameter of the last step; col: the colour record
     // (phi, b n) of the current state, one per node
     void *phi = nullptr, *col = nullptr;
-    size_t col_sz = 32;  // bytes of one node's colour record (four reals, one array each)
+    size_t col_sz = 32;  // bytes of one colour record
     void *grad = nullptr, *gmag = nullptr, *kap = nullptr, *u = nullptr;
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
@@ -119,6 +119,9 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.inst = c->inst_d;
     L.n_inst = c->n_inst;
     L.n_items = c->fz.rows;
+    L.buoyancy = 0;
+    for (const auto &I : c->inst_h)
+        if (I.buoy[0] != 0.0 || I.buoy[1] != 0.0 || I.buoy[2] != 0.0) L.buoyancy = 1;
     L.static_list = c->static_list;
     L.n_static = c->n_static;
     L.static_bfl = c->static_bfl;
@@ -172,7 +175,7 @@ template <class S>
 struct NodeState {
     using R = typename Store<S>::real;
     const Pop<S> &pop;
-    const Colour<R> &C;
+    const ColourOf<S> &C;
     int n;
     __device__ double F(int i) const { return (double)pop.F(i, n); }
     __device__ double G(int i) const
@@ -202,7 +205,7 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
     R *ph = (R *)L.phi + I.node_off;
-    const ColSlot<R> col = col_slot<R>(L, I.node_off);
+    const ColSlotOf<S> col = col_slot<S>(L, I.node_off);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if (pops) {
             double F[Q], G[Q], sF = 0.0, sG = 0.0;
@@ -227,7 +230,7 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
             for (int k = 0; k < 3; k++) a3[k] *= 4.5;
             for (int i = 0; i < Q; i++) pop.setF(i, (int)n, (R)F[i]);
             ph[n] = (R)p;
-            ColSlot<R>{col.p + n, col.Nt}.set(ColRec<R>{(R)p, (R)a3[0], (R)a3[1], (R)a3[2]});
+            col.shifted(n).set(ColRec<R>{(R)p, (R)a3[0], (R)a3[1], (R)a3[2]});
             continue;
         }
         double p = phi[n];
@@ -242,7 +245,7 @@ __global__ void k_init(Lattice L, int cur, int inst, const double *phi, const do
             pop.setF(i, (int)n, (R)(rr * e - 1.0));
         }
         ph[n] = (R)p;
-        ColSlot<R>{col.p + n, col.Nt}.set(ColRec<R>{(R)p, R(0), R(0), R(0)});
+        col.shifted(n).set(ColRec<R>{(R)p, R(0), R(0), R(0)});
         if (I.store_u) {
             R *U = (R *)L.u;
             bool fl = (L.flags[I.node_off + n] & OWNER_MASK) == OWN_FLUID;
@@ -258,7 +261,7 @@ __global__ void k_read(Lattice L, int cur, int inst, unsigned mask, double *out,
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
-    const Colour<R> C(L, I);
+    const ColourOf<S> C(L, I);
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         const uint8_t f = L.flags[I.node_off + n];
         const bool fluid = (f & OWNER_MASK) == OWN_FLUID;
@@ -301,7 +304,7 @@ __global__ void k_mass_partial(Lattice L, int cur, int inst, double *part)
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
-    const Colour<typename Store<S>::real> C(L, I);
+    const ColourOf<S> C(L, I);
     double sa = 0.0, sb = 0.0;
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
@@ -348,7 +351,7 @@ __global__ void k_speed_partial(Lattice L, int cur, int inst, double *part)
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
-    const Colour<typename Store<S>::real> C(L, I);
+    const ColourOf<S> C(L, I);
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;

@@ -24,16 +24,15 @@
 
 // CTAs of 256 threads per SM the single-precision order-parameter and
 // collision kernels are compiled for (register budget 65536 / (256 x this)).
-// The order-parameter pass holds 19 pulled offsets and, per source, phi and
-// the one or two components of its colour record that its direction needs
-// (the records are four arrays).  Measured per 256x128x128 launch: FP32
-// offsets 97 us at 4 CTAs, 107 at 3, 114 at 2; 16-bit offsets 93 us at 4,
-// 103 at 3
+// The order-parameter pass holds 19 pulled offsets and 19 four-value colour
+// records per node: with FP32 offsets 3 CTAs (85 registers) measured faster
+// than 4 (106 against 115 us per 256x128x128 launch), with 16-bit offsets 4
+// (91 against 125 us)
 #ifndef LBM_PHI_MINB
 #define LBM_PHI_MINB 4
 #endif
 #ifndef LBM_PHI_MINB_F32
-#define LBM_PHI_MINB_F32 4
+#define LBM_PHI_MINB_F32 3
 #endif
 // CTAs per SM of the boundary passes, which run beside the bulk kernels
 #ifndef LBM_BOUND_MINB
@@ -71,7 +70,7 @@ __device__ __forceinline__ void phi_body(const Lattice &L, const InstDev &I, int
     const long long g = I.node_off + n;
     const uint8_t fl = L.flags[g];
     const Pop<S> in(L.pop[cur], I);
-    const Colour<R> C(L, I);
+    const ColourOf<S> C(L, I);
     Nbr nb;
     nb.init(x, y, z, I.nx, I.ny, I.nz);
     R v = phi_fluid<S>(nb, in, C);
@@ -200,7 +199,7 @@ __global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_phi_bound(Latt
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
     const Pop<S> in(L.pop[cur], *I);
-    const Colour<R> C(L, *I);
+    const ColourOf<S> C(L, *I);
     GlobalNbr nb;
     nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
     nb.fli = L.flags + I->node_off;
@@ -230,14 +229,14 @@ __global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_collide_bound(
     nb.nb.init(x, y, z, I->nx, I->ny, I->nz);
     nb.fli = L.flags + I->node_off;
     R F[Q];
-    gather_all<S>(*I, L.parts, nb, in, (const Colour<R> *)nullptr, n, F, (R *)nullptr, x, y, z);
+    gather_all<S>(*I, L.parts, nb, in, (const ColourOf<S> *)nullptr, n, F, (R *)nullptr, x, y, z);
     FluidPar<R> P;
     load_par(*I, P);
     const R m = ((const R *)L.gmag)[g];
     const R gr[3] = {Nn[n] * m, Nn[Nt + n] * m, Nn[2 * Nt + n] * m};
     const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
     collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, nn, ((const R *)L.kap)[g], out, n,
-                         col_slot<R>(L, g), U, L.Ntot, L.status);
+                         col_slot<S>(L, g), U, L.Ntot, L.status);
 }
 
 template <class R>
@@ -279,7 +278,7 @@ __device__ __forceinline__ void collide_body(const Lattice &L, const InstDev &I,
     FluidPar<R> P;
     load_par(I, P);
     const R gr[3] = {nn[0] * m, nn[1] * m, nn[2] * m};
-    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, col_slot<R>(L, g), U, L.Ntot, L.status);
+    collide_store_phi<S>(P, F, phi, gr, nn, kap, out, n, col_slot<S>(L, g), U, L.Ntot, L.status);
 }
 
 // Node pairs (x even, x + 1) of one row per thread, for 16-bit storage: the
@@ -365,8 +364,8 @@ __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I
         }
     };
     {
-        if (a0) col_slot<R>(L, g).set(ColRec<R>{phA, cA.bq * n0.x, cA.bq * n1.x, cA.bq * n2.x});
-        if (a1) col_slot<R>(L, g + 1).set(ColRec<R>{phB, cB.bq * n0.y, cB.bq * n1.y, cB.bq * n2.y});
+        if (a0) col_slot<S>(L, g).set(ColRec<R>{phA, cA.bq * n0.x, cA.bq * n1.x, cA.bq * n2.x});
+        if (a1) col_slot<S>(L, g + 1).set(ColRec<R>{phB, cB.bq * n0.y, cB.bq * n1.y, cB.bq * n2.y});
     }
     put(of, collide_rest(P, cA, F0[0]), collide_rest(P, cB, F1[0]));
     PairLoop<R>::run([&](auto ic) {

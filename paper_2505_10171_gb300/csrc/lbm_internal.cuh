@@ -168,6 +168,7 @@ struct Lattice {
     const InstDev *inst;
     int n_inst;
     long long n_items;   // row-strip work items of all instances
+    int buoyancy;        // some instance has a nonzero buoyancy_a: the immersed fractions are summed
     const long long *static_list;  // static solid nodes next to non-static ones (global node index)
     long long n_static;
     const long long *static_bfl;   // non-static nodes next to static solid ones
@@ -175,7 +176,7 @@ struct Lattice {
     uint8_t *flags;
     void *pop[2];
     void *phi;           // [Ntot] real: the order parameter of the step (outside a step: of the last one)
-    void *col;           // [4][Ntot] real: colour records (phi, b n) of the stored state
+    void *col;           // [Ntot] ColRec<real>: colour record (phi, b n) of the stored state
     void *grad;          // [3][Ntot] real: regularised interface normal n
     void *gmag;          // [Ntot] real: sqrt(|grad phi|^2 + eps^2), so grad phi = n gmag
     void *kap;           // [Ntot] real: curvature div(n) of fluid nodes
@@ -405,10 +406,10 @@ struct GlobalNbr {
 
 // The colour record of a node of the stored state (see the top of this
 // file): the order parameter phi of the collision that produced it and
-// a = b n.  Stored as four arrays of Ntot reals (phi, a0, a1, a2), so that a
-// pulled source loads phi and only the components of a its direction needs.
+// a = b n, one 16-byte (FP64: 32-byte) aligned record, so that a pulled source
+// costs one vector load.
 template <class R>
-struct ColRec {
+struct alignas(4 * sizeof(R)) ColRec {
     R p, a0, a1, a2;
 };
 
@@ -423,50 +424,46 @@ __device__ __forceinline__ R col_rec(int i, const ColRec<R> &c)
     return csq(i) == 1 ? t : t * R(0.70710678118654752440);
 }
 
-// one node's record slot: p[0], p[Nt], p[2 Nt], p[3 Nt]
+// one node's record slot (write side)
 template <class R>
 struct ColSlot {
-    R *p;
-    long long Nt;
-    __device__ __forceinline__ void set(const ColRec<R> &c) const
-    {
-        p[0] = c.p;
-        p[Nt] = c.a0;
-        p[2 * Nt] = c.a1;
-        p[3 * Nt] = c.a2;
-    }
+    ColRec<R> *p;
+    __device__ __forceinline__ void set(const ColRec<R> &c) const { *p = c; }
+    // the slot n nodes further on
+    __device__ __forceinline__ ColSlot shifted(long long n) const { return ColSlot{p + n}; }
+    // phi of the record n nodes further on
+    __device__ __forceinline__ R phi(long long n) const { return p[n].p; }
 };
 
 // the colour records of an instance (read side)
 template <class R>
 struct Colour {
-    const R *b;
-    long long Nt;
+    const ColRec<R> *c;
     __device__ __forceinline__ Colour(const Lattice &L, const InstDev &I)
-        : b((const R *)L.col + I.node_off), Nt(L.Ntot)
+        : c((const ColRec<R> *)L.col + I.node_off)
     {
     }
-    __device__ __forceinline__ ColRec<R> at(int m) const
+    __device__ __forceinline__ ColRec<R> at(int m) const { return c[m]; }
+    // G*_i = phi (1 + F*_i) + (c_i . a)/|c_i| of the record at m
+    __device__ __forceinline__ R G(int i, int m, R F) const
     {
-        return ColRec<R>{b[m], b[Nt + m], b[2 * Nt + m], b[3 * Nt + m]};
-    }
-    __device__ __forceinline__ R phi(int m) const { return b[m]; }
-    // col_rec(i, at(m)) from the components direction i touches
-    __device__ __forceinline__ R proj(int i, int m) const
-    {
-        R t = 0;
-        if (cx(i)) t += cx(i) * b[Nt + m];
-        if (cy(i)) t += cy(i) * b[2 * Nt + m];
-        if (cz(i)) t += cz(i) * b[3 * Nt + m];
-        return csq(i) == 1 ? t : t * R(0.70710678118654752440);
+        const ColRec<R> r = c[m];
+        R g = r.p * (R(1) + F);
+        if (i) g += col_rec(i, r);
+        return g;
     }
 };
 
+template <class S>
+using ColourOf = Colour<typename Store<S>::real>;
+template <class S>
+using ColSlotOf = ColSlot<typename Store<S>::real>;
+
 // the record slot of global node g
-template <class R>
-__device__ __forceinline__ ColSlot<R> col_slot(const Lattice &L, long long g)
+template <class S>
+__device__ __forceinline__ ColSlotOf<S> col_slot(const Lattice &L, long long g)
 {
-    return ColSlot<R>{(R *)L.col + g, L.Ntot};
+    return ColSlotOf<S>{(ColRec<typename Store<S>::real> *)L.col + g};
 }
 
 // Pull streaming (Sec. IV) into fluid node n, with the Sec. V A halfway
@@ -486,7 +483,7 @@ __device__ __forceinline__ ColSlot<R> col_slot(const Lattice &L, long long g)
 // (rho^a - rho^b)(x) = phi(x) rho(x) that is phi(x)(1 + F_i(x)) - (c_i . a(x))/|c_i|.
 template <class S, class A>
 __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *parts, const A &nbr,
-                                           const Pop<S> &in, const Colour<typename Store<S>::real> *C, int n,
+                                           const Pop<S> &in, const ColourOf<S> *C, int n,
                                            typename Store<S>::real *F, typename Store<S>::real *sG, int x, int y,
                                            int z)
 {
@@ -535,9 +532,7 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
     for (int i = 0; i < Q; i++) {
         R gi;
         if (own[i] == OWN_FLUID) {
-            const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
-            gi = C->phi(s) * (R(1) + F[i]);
-            if (i) gi += C->proj(i, s);
+            gi = C->G(i, nbr.idx(-cx(i), -cy(i), -cz(i)), F[i]);
         } else if (own[i] == OWN_PRESS) {
             gi = cn.p * (R(1) + F[i]) + col_rec(i, cn);
         } else {
@@ -553,7 +548,7 @@ __device__ __forceinline__ void gather_all(const InstDev &I, const PartDev *part
 // source node's colour state
 template <class S, class A>
 __device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const Pop<S> &in,
-                                                             const Colour<typename Store<S>::real> &C)
+                                                             const ColourOf<S> &C)
 {
     using R = typename Store<S>::real;
     R sF = 0, sG = 0;
@@ -561,9 +556,10 @@ __device__ __forceinline__ typename Store<S>::real phi_fluid(const A &nbr, const
     for (int i = 0; i < Q; i++) {
         const int s = nbr.idx(-cx(i), -cy(i), -cz(i));
         const R F = in.F(i, s);
+        const ColRec<R> cs = C.at(s);
         sF += wgt<R>(i) * F;
-        R g = C.phi(s) * (R(1) + F);
-        if (i) g += C.proj(i, s);
+        R g = cs.p * (R(1) + F);
+        if (i) g += col_rec(i, cs);
         sG += wgt<R>(i) * g;
     }
     return sG / (R(1) + sF);

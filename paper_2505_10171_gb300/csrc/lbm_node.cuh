@@ -232,7 +232,7 @@ __device__ __forceinline__ void collide_store_phi(const FluidPar<typename Store<
                                                   const typename Store<S>::real *F, typename Store<S>::real phi,
                                                   const typename Store<S>::real *g, const typename Store<S>::real *nn,
                                                   typename Store<S>::real kap, const Pop<S> &out, int n,
-                                                  const ColSlot<typename Store<S>::real> &C, typename Store<S>::real *U,
+                                                  const ColSlotOf<S> &C, typename Store<S>::real *U,
                                                   long long Ustride, unsigned *status)
 {
     using R = typename Store<S>::real;

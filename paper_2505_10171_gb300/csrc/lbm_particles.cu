@@ -156,10 +156,10 @@ __global__ void __launch_bounds__(PART_THREADS) k_mem(Lattice L, int cur)
 // Sec. V F: dF = C sigma (1 - phi^2) dA (n x n_s) x n at the points
 // alpha_j = (j + 1/2) 2 deg, varphi_k = k 2 deg on r = R_p, n the regularised
 // normal of the trilinearly interpolated grad(phi) (fluid corners only);
-// torque R_p n_s x dF.  Also the phase-a share of the surface for the
-// buoyancy (reading c28): s = (1 + phi)/2 clipped to [0, 1] and dA, summed
+// torque R_p n_s x dF.  With BUOY also the phase-a share of the surface for
+// the buoyancy (reading c28): s = (1 + phi)/2 clipped to [0, 1] and dA, summed
 // over the points with a fluid corner.
-template <class R>
+template <class R, bool BUOY>
 __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
 {
     const int p = blockIdx.y;
@@ -210,9 +210,11 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
                 }
         if (ws > R(0)) {
             const R phv = phs / ws;
-            const R sa = fmin(fmax(R(0.5) * (R(1) + phv), R(0)), R(1));
-            acc[6] = (double)(sa * dA);
-            acc[7] = (double)dA;
+            if (BUOY) {
+                const R sa = fmin(fmax(R(0.5) * (R(1) + phv), R(0)), R(1));
+                acc[6] = (double)(sa * dA);
+                acc[7] = (double)dA;
+            }
             const R g0 = gs[0] / ws, g1 = gs[1] / ws, g2 = gs[2] / ws;
             if (fabs(phv) < R(1)) {
                 const R eps2 = (R)(I.grad_eps * I.grad_eps);
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(CAP_THREADS) k_capillary(Lattice L)
             }
         }
     }
-    block_sum<CAP_PART>(acc, L.cap_part + ((long long)p * CAP_BLOCKS + blockIdx.x) * CAP_PART);
+    block_sum<BUOY ? 8 : 6>(acc, L.cap_part + ((long long)p * CAP_BLOCKS + blockIdx.x) * CAP_PART);
 }
 
 
@@ -361,7 +363,7 @@ __device__ __forceinline__ int pair_index(int i, int j, int np) { return i * np 
 // forces one thread per contact (substrate contacts, then pairs), kept per
 // contact; corrector per particle, adding its contacts in a fixed order
 // (substrate, then partners in increasing index).
-template <class T>
+template <class T, bool BUOY>
 __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
 {
     const InstDev &I = L.inst[blockIdx.x];
@@ -380,14 +382,15 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
         const int lane = tid & 31, wid = tid >> 5;
         for (int p = wid; p < np; p += DEM_THREADS / 32) {
             const long long pg = I.part_off + p;
-            double s[12 + CAP_PART];
-            for (int a = 0; a < 12 + CAP_PART; a++) s[a] = 0.0;
+            constexpr int NC = BUOY ? CAP_PART : 6;  // capillary partials used
+            double s[12 + NC];
+            for (int a = 0; a < 12 + NC; a++) s[a] = 0.0;
             for (int b = lane; b < L.mem_blocks; b += 32)
                 for (int a = 0; a < MEM_PART; a++) s[a] += L.mem_part[(pg * L.mem_blocks + b) * MEM_PART + a];
             for (int b = lane; b < CAP_BLOCKS; b += 32)
-                for (int a = 0; a < CAP_PART; a++) s[12 + a] += L.cap_part[(pg * CAP_BLOCKS + b) * CAP_PART + a];
+                for (int a = 0; a < NC; a++) s[12 + a] += L.cap_part[(pg * CAP_BLOCKS + b) * CAP_PART + a];
             for (int o = 16; o > 0; o >>= 1)
-                for (int a = 0; a < 12 + CAP_PART; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
+                for (int a = 0; a < 12 + NC; a++) s[a] += __shfl_down_sync(0xffffffffu, s[a], o);
             if (lane == 0) {
                 // momentum exchange: small part plus the exact rest part
                 // -(rho0/18) K, -(rho0/18) (M - delta x K), M = (2M)/2
@@ -410,14 +413,16 @@ __global__ void __launch_bounds__(DEM_THREADS) k_dem(Lattice L, int sum_fluid)
                 // above the centre leaves the volume fraction (1 + t)^2 (2 - t)/4,
                 // t = h/R, of the sphere below it (a spherical zone's area is
                 // proportional to its height)
-                double sub = 0.0;
-                if (s[19] > 0.0) {
-                    const double t = 2.0 * (s[18] / s[19]) - 1.0;
-                    sub = (1.0 + t) * (1.0 + t) * (2.0 - t) / 4.0;
+                if constexpr (BUOY) {
+                    double sub = 0.0;
+                    if (s[19] > 0.0) {
+                        const double t = 2.0 * (s[18] / s[19]) - 1.0;
+                        sub = (1.0 + t) * (1.0 + t) * (2.0 - t) / 4.0;
+                    }
+                    const double vol = 4.0 / 3.0 * M_PI * P[p].R * P[p].R * P[p].R;
+                    P[p].sub = sub;
+                    for (int a = 0; a < 3; a++) P[p].Fb[a] = vol * sub * I.buoy[a];
                 }
-                const double vol = 4.0 / 3.0 * M_PI * P[p].R * P[p].R * P[p].R;
-                P[p].sub = sub;
-                for (int a = 0; a < 3; a++) P[p].Fb[a] = vol * sub * I.buoy[a];
             }
         }
         __syncthreads();
@@ -635,7 +640,7 @@ __device__ __forceinline__ R warp_sum(R v)
 
 template <class S>
 __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S> &pop,
-                            typename Store<S>::real *ph, ColSlot<typename Store<S>::real> col, const uint8_t *fli,
+                            typename Store<S>::real *ph, ColSlotOf<S> col, const uint8_t *fli,
                             int x, int y, int z, int lane)
 {
     using R = typename Store<S>::real;
@@ -655,7 +660,7 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
                 ok = 1;
 #pragma unroll
                 for (int j = 0; j < Q; j++) aF += wgt<R>(j) * (R(1) + pop.F(j, m));
-                aG = col.p[m] * aF;
+                aG = col.phi(m) * aF;
             }
         }
         sF = warp_sum(aF);
@@ -684,7 +689,7 @@ __device__ void refill_node(const InstDev &I, const PartDev *parts, const Pop<S>
     pop.setF(i, n, rr * e - R(1));
     if (lane == 0) {
         ph[n] = rd / rr;
-        ColSlot<R>{col.p + n, col.Nt}.set(ColRec<R>{rd / rr, R(0), R(0), R(0)});
+        col.shifted(n).set(ColRec<R>{rd / rr, R(0), R(0), R(0)});
     }
 }
 
@@ -716,7 +721,7 @@ __global__ void __launch_bounds__(PART_THREADS) k_refill(Lattice L, int nxt, int
             todo &= todo - 1;
             const int X = __shfl_sync(0xffffffffu, x, src), Y = __shfl_sync(0xffffffffu, y, src),
                       Z = __shfl_sync(0xffffffffu, z, src);
-            refill_node<S>(I, L.parts, pop, (R *)L.phi + I.node_off, col_slot<R>(L, I.node_off), fli, X, Y, Z,
+            refill_node<S>(I, L.parts, pop, (R *)L.phi + I.node_off, col_slot<S>(L, I.node_off), fli, X, Y, Z,
                            lane);
         }
     }
@@ -757,7 +762,10 @@ void launch_capillary(const Lattice &L, cudaStream_t st, long long *launches, co
     using R = typename Store<S>::real;
     if (L.n_parts == 0) return;
     mk(STAGE_CAPILLARY, 0);
-    k_capillary<R><<<dim3(CAP_BLOCKS, L.n_parts), CAP_THREADS, 0, st>>>(L);
+    if (L.buoyancy)
+        k_capillary<R, true><<<dim3(CAP_BLOCKS, L.n_parts), CAP_THREADS, 0, st>>>(L);
+    else
+        k_capillary<R, false><<<dim3(CAP_BLOCKS, L.n_parts), CAP_THREADS, 0, st>>>(L);
     mk(STAGE_CAPILLARY, 1);
     *launches += 1;
 }
@@ -775,7 +783,10 @@ void launch_dem(const Lattice &L, cudaStream_t st, long long *launches, const Ma
     using R = typename Store<S>::real;
     if (L.n_parts == 0) return;
     mk(STAGE_DEM, 0);
-    k_dem<R><<<L.n_inst, DEM_THREADS, 0, st>>>(L, sum_fluid ? 1 : 0);
+    if (L.buoyancy)
+        k_dem<R, true><<<L.n_inst, DEM_THREADS, 0, st>>>(L, sum_fluid ? 1 : 0);
+    else
+        k_dem<R, false><<<L.n_inst, DEM_THREADS, 0, st>>>(L, sum_fluid ? 1 : 0);
     mk(STAGE_DEM, 1);
     *launches += 1;
 }
