@@ -42,6 +42,20 @@ def test_buoyancy_matches_oracle_fp64():
     assert np.abs(rg[18:27] - ro[18:27]).max() <= 1e-12
 
 
+@pytest.mark.parametrize("prec,tol", [("fp16", 2e-3), ("bf16", 2e-3)])
+def test_buoyancy_16bit(prec, tol):
+    w = immersed_case()
+    o = oracle_sim(w)
+    o.step(60)
+    ro = o.particles()[0]
+    c = gpu_ctx(w, prec)
+    c.lbm_step(60)
+    rg = c.lbm_particle_forces()[0]
+    c.close()
+    assert abs(rg[32] - ro[32]) <= tol
+    assert np.abs(rg[33:36] - ro[33:36]).max() <= tol * np.abs(ro[33:36]).max()
+
+
 def test_buoyancy_fp32_and_surrogate_guard():
     w = immersed_case()
     steps = 60

@@ -608,3 +608,55 @@ def test_particle_checkpoint_is_checked():
         c.lbm_set_particle_state(st)  # after the first step
     assert e.value.status == 4  # LBM_ERR_STATE
     c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", FP32_TOL), ("fp16", HALF_TOL)])
+def test_pressure_faces_channel_reduced_precision(prec, tol):
+    """The pressure-driven two-phase channel of the FP64 test in FP32 and FP16
+    storage, against the oracle at the stated bars."""
+    nx, ny, nz = 6, 20, 36
+    mask = np.zeros((nz, ny, nx), np.uint8)
+    mask[:, 0, :] = 1
+    mask[:, ny - 1, :] = 1
+    yy = np.arange(ny, dtype=float)
+    phi = np.broadcast_to(np.tanh(2.0 * (yy - 8.3) / 2.5)[None, :, None], (nz, ny, nx)).reshape(-1)
+    p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=0, nu_a=1 / 6, nu_b=1 / 12, pressure_z=1, rho_in=1.004,
+             rho_out=0.996, sigma=0.01)
+    w = dict(params=p, phi=phi.copy(), mask=mask.reshape(-1), particles=[])
+    o = run_oracle(w, 150)
+    assert_reduced_parity(run_gpu(w, 150, prec), o, tol)
+
+
+def test_particle_checkpoint_of_a_batched_instance():
+    """The checkpoint of instance 1 of a two-instance context restores into
+    instance 1 of a new one: the continued run equals the uninterrupted one
+    (FP64), and instance 0 is untouched by it."""
+    from paper_2505_10171_gb300 import lbm
+    w0 = W.cfg1()
+    w1 = W.cfg1()
+    w1["params"] = dict(w1["params"], g_particle=(0.0, 0.0, -0.01))
+    w1["particles"] = [dict(w1["particles"][0], x=(31.0, 15.0, 5.5))]
+
+    def make(ws, particles1=None):
+        c = lbm.Context([dict(w["params"], store_velocity=1) for w in ws], "fp64")
+        for k, w in enumerate(ws):
+            c.lbm_add_particles(particles1 if (k == 1 and particles1) else w["particles"], inst=k)
+            c.lbm_init_fields(w["phi"], inst=k)
+        return c
+
+    c = make([w0, w1])
+    c.lbm_step(50)
+    pops = [np.concatenate(c.pops(k)) for k in range(2)]
+    st = c.lbm_get_particle_state(1)
+    c.lbm_step(30)
+    ref = [c.lbm_particle_forces(k)[0] for k in range(2)]
+    c.close()
+    r = make([w0, w1], particles1=[dict(w1["particles"][0], x=tuple(st[0:3]))])
+    # instance 0 restarts from its own populations; its particle keeps its initial state
+    for k in range(2):
+        r.lbm_init_fields(None, pops=pops[k], inst=k)
+    r.lbm_set_particle_state(st, inst=1)
+    r.lbm_step(30)
+    got = r.lbm_particle_forces(1)[0]
+    r.close()
+    assert np.abs(got[12:27] - ref[1][12:27]).max() <= 1e-13
