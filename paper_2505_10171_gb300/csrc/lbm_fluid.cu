@@ -414,10 +414,7 @@ __global__ void __launch_bounds__(ROW_NODES, sizeof(S) == 8 ? 1 : LBM_COLLIDE_MI
 // ring.  Each phi value is read from L2/HBM about 1.7 times, the normal once
 // per CTA; the per-node arithmetic is that of grad_body and the curvature
 // of the fused kernel.
-#ifndef LBM_GC_TY
-#define LBM_GC_TY 8
-#endif
-constexpr int GC_TX = 32, GC_TY = LBM_GC_TY, GC_ZC = 16;
+constexpr int GC_TX = 32, GC_TY = 8, GC_ZC = 16;
 
 // a mod n in [0, n): the in-range and one-period cases without a division
 __device__ __forceinline__ int wrap_any(int a, int n)
