@@ -270,6 +270,32 @@ def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=51
     return table, dict(losses=losses, weights=weights)
 
 
+def evaluate(weights, test_seeds, steps=16000, every=16, free=False, win=64, stream=None):
+    """Run trained weights on test_seeds without training: the resolved
+    runs, and the coarse runs with the plain forces and with the surrogate in
+    the loop; the error table as campaign() reports it (no offline column)."""
+    n_sph = 8
+    t0 = time.time()
+    ref = run([resolved(sd, free) for sd in test_seeds], steps, every, features=False, stream=stream)
+    cws = [coarse(sd, free) for sd in test_seeds]
+    plain = run(cws, steps, every, stream=stream)
+    sur = run(cws, steps, every, weights=weights, features=False, stream=stream)
+    series = dict(plain_coarse=[p["Y"] for p in plain], surrogate_coarse=[p["Y"] for p in sur])
+    touch = np.concatenate([touching(p["X"]) for p in plain])
+    table = dict(test_samples=int(len(touch)), touching_fraction=float(touch.mean()), test_seeds=len(test_seeds),
+                 steps=steps, every=every, smooth_window=win, free=bool(free))
+    for tag, w_ in (("raw", 1), ("smoothed", win)):
+        Yr = np.concatenate([smooth(r["Y"], n_sph, w_) for r in ref])
+        table[f"ref_force_mean_{tag}"] = float(np.linalg.norm(Yr[:, 0:3], axis=1).mean())
+        table[f"ref_force_mean_touching_{tag}"] = float(np.linalg.norm(Yr[touch, 0:3], axis=1).mean())
+        for name, rows in series.items():
+            Ys = np.concatenate([smooth(y, n_sph, w_) for y in rows])
+            table[f"{name}_{tag}"] = list(errors(Ys, Yr))
+            table[f"{name}_touching_{tag}"] = list(errors(Ys, Yr, touch))
+    table["seconds"] = time.time() - t0
+    return table
+
+
 def main():
     ap = argparse.ArgumentParser(description="surrogate training and coarse-grid evaluation campaign")
     ap.add_argument("--train", type=int, default=25, help="resolved training runs (seeds 1..N)")
@@ -283,7 +309,17 @@ def main():
     ap.add_argument("--smooth", type=int, default=64, help="moving-average window in samples")
     ap.add_argument("--out", default=None, help="write the error table as JSON here")
     ap.add_argument("--weights", default=None, help="write the trained FP32 weights (.npy) here")
+    ap.add_argument("--evaluate", default=None, help="evaluate these weights (.npy) instead of training")
     a = ap.parse_args()
+    if a.evaluate:
+        table = evaluate(np.load(a.evaluate), list(range(1001, 1001 + a.test)), steps=a.steps, every=a.every,
+                         free=a.free, win=a.smooth)
+        table["weights"] = a.evaluate
+        table["command"] = "python -m paper_2505_10171_gb300.surrogate_study " + " ".join(sys.argv[1:])
+        print(json.dumps(table))
+        if a.out:
+            json.dump(table, open(a.out, "w"), indent=1)
+        return
     table, rec = campaign(list(range(1, a.train + 1)), list(range(1001, 1001 + a.test)), steps=a.steps,
                           every=a.every, epochs=a.epochs, free=a.free, inputs=a.inputs, win=a.smooth)
     table["losses"] = rec["losses"]
