@@ -62,7 +62,7 @@ BOX = 1.0 / SCALE      # box filter of the resolved inputs: one coarse cell
 MAX_NODES = 50_000_000
 
 
-def _setup(seed, s, free=False, box=0.0):
+def _setup(seed, s, free=False, box=0.0, moving=False):
     """Drop R = 40 s driven along x at 5e-3 s over a 150 deg wall, eight
     spheres R_p = 8 s (contact angles uniform in [30, 90] deg) placed 4 to 50 s
     ahead of the drop front (centres x in [98, 152] s, y in [12, 116] s) at
@@ -72,11 +72,16 @@ def _setup(seed, s, free=False, box=0.0):
     on the wall with normal damping at half the critical value and a weight
     of 2 sigma R_p: a sphere must keep a fluid node between itself and the
     wall, or the momentum exchange on its open surface carries the
-    unbalanced rest pressure."""
+    unbalanced rest pressure.  Moving (held spheres only): all spheres of the
+    seed glide along the substrate with one prescribed velocity, x component
+    uniform in [-U, U], y component uniform in [-U/3, U/3] (U the drop speed
+    target), rolling without slip on odd seeds, so that the network also sees
+    spheres that move relative to the fluid."""
     rng = np.random.default_rng(seed)
     R8, Rc8 = FINE_RP, FINE_RP + 1.0
     centres = W.place_spheres(rng, 8, R8, Rc8, (98.0, 152.0), (12.0, 116.0), 9.5, 24.0)
     thetas = rng.uniform(30.0, 90.0, size=8)
+    glide = np.array([rng.uniform(-1.0, 1.0), rng.uniform(-1.0 / 3.0, 1.0 / 3.0), 0.0]) * FINE_U * s
     nx, ny, nz = int(round(256 * s)), int(round(128 * s)), int(round(128 * s))
     sigma, R_p = W.COMMON["sigma"] * s, R8 * s
     gn = W.resting_damping(R_p)
@@ -89,17 +94,23 @@ def _setup(seed, s, free=False, box=0.0):
     phi = W.drop_phi(nx, ny, nz, (48.0 * s, 64.0 * s, 0.5), 40.0 * s)
     particles = [dict(x=(c[0] * s, c[1] * s, 0.5 + R_p + 1.0), R=R_p, rho_p=W.PARTICLE_DENSITY,
                       theta_deg=float(t), kinematic=0 if free else 1) for c, t in zip(centres, thetas)]
+    if moving and not free:
+        roll = seed % 2 == 1
+        w = (-glide[1] / R_p, glide[0] / R_p, 0.0) if roll else (0.0, 0.0, 0.0)
+        for q in particles:
+            q["v"] = tuple(float(v) for v in glide)
+            q["w"] = tuple(float(v) for v in w)
     return dict(params=params, phi=phi, particles=particles)
 
 
-def resolved(seed, free=False, box=BOX):
+def resolved(seed, free=False, box=BOX, moving=False):
     """The resolved (R_p = 8) set-up of a seed (shell inputs box-filtered)."""
-    return _setup(seed, 1.0, free, box)
+    return _setup(seed, 1.0, free, box, moving)
 
 
-def coarse(seed, free=False):
+def coarse(seed, free=False, moving=False):
     """The same set-up at 3/8 scale (R_p = 3)."""
-    return _setup(seed, SCALE, free)
+    return _setup(seed, SCALE, free, moving=moving)
 
 
 def _labels(rec, sigma, R_p):
@@ -201,7 +212,7 @@ def init_weights(seed):
 
 
 def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=512, lr=1e-3, seed=9, free=False,
-             inputs="coarse", win=64, stream=None):
+             inputs="coarse", win=64, moving=False, stream=None):
     """Train on train_seeds (labels: their resolved runs' forces through the
     moving average over `win` samples; inputs as `inputs` says), then compare
     on test_seeds: the network offline on the test inputs, and the coarse runs
@@ -215,12 +226,12 @@ def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=51
     box = inputs == "box"
     n_sph = 8
     t0 = time.time()
-    tr = run([resolved(sd, free) for sd in train_seeds], steps, every, features=box, stream=stream)
+    tr = run([resolved(sd, free, moving=moving) for sd in train_seeds], steps, every, features=box, stream=stream)
     Y = np.concatenate([smooth(r["Y"], n_sph, win) for r in tr])
     if box:
         X = np.concatenate([r["X"] for r in tr])
     else:
-        trc = run([coarse(sd, free) for sd in train_seeds], steps, every, stream=stream)
+        trc = run([coarse(sd, free, moving=moving) for sd in train_seeds], steps, every, stream=stream)
         X = np.concatenate([r["X"] for r in trc])
         del trc
     del tr
@@ -253,7 +264,7 @@ def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=51
     t_sur = time.time() - t3
     series = dict(offline=pred, plain_coarse=[p["Y"] for p in plain], surrogate_coarse=[p["Y"] for p in sur])
     touch = np.concatenate([touching(p["X"]) for p in plain])
-    table = dict(inputs=inputs, samples=int(X.shape[0]), test_samples=int(len(touch)),
+    table = dict(inputs=inputs, moving_training=bool(moving), samples=int(X.shape[0]), test_samples=int(len(touch)),
                  touching_fraction=float(touch.mean()), train_seeds=len(train_seeds), test_seeds=len(test_seeds),
                  steps=steps, every=every, smooth_window=win, epochs=epochs, free=bool(free),
                  label_rms=float(np.sqrt((Y * Y).mean())), loss_first=losses[0], loss_last=losses[-1])
@@ -307,6 +318,7 @@ def main():
     ap.add_argument("--inputs", choices=("coarse", "box"), default="coarse",
                     help="network inputs: coarse-run shells, or box-filtered resolved shells")
     ap.add_argument("--smooth", type=int, default=64, help="moving-average window in samples")
+    ap.add_argument("--moving", action="store_true", help="train on spheres gliding on prescribed paths")
     ap.add_argument("--out", default=None, help="write the error table as JSON here")
     ap.add_argument("--weights", default=None, help="write the trained FP32 weights (.npy) here")
     ap.add_argument("--evaluate", default=None, help="evaluate these weights (.npy) instead of training")
@@ -321,7 +333,8 @@ def main():
             json.dump(table, open(a.out, "w"), indent=1)
         return
     table, rec = campaign(list(range(1, a.train + 1)), list(range(1001, 1001 + a.test)), steps=a.steps,
-                          every=a.every, epochs=a.epochs, free=a.free, inputs=a.inputs, win=a.smooth)
+                          every=a.every, epochs=a.epochs, free=a.free, inputs=a.inputs, win=a.smooth,
+                          moving=a.moving)
     table["losses"] = rec["losses"]
     table["command"] = "python -m paper_2505_10171_gb300.surrogate_study " + " ".join(sys.argv[1:])
     print(json.dumps(table))
