@@ -125,8 +125,13 @@ def _chunks(ws):
     nodes = [w["params"]["nx"] * w["params"]["ny"] * w["params"]["nz"] for w in ws]
     per = max(1, int(MAX_NODES // max(nodes)))
     n = math.ceil(len(ws) / per)
-    size = math.ceil(len(ws) / n)
-    return [list(range(i, min(i + size, len(ws)))) for i in range(0, len(ws), size)]
+    base, extra = divmod(len(ws), n)
+    out, i = [], 0
+    for k in range(n):
+        size = base + (1 if k < extra else 0)
+        out.append(list(range(i, i + size)))
+        i += size
+    return out
 
 
 def run(ws, steps, every, weights=None, features=True, stream=None):

@@ -79,3 +79,56 @@ def test_resting_damping_is_half_critical():
     for R in (3.0, 8.0):
         m = W.PARTICLE_DENSITY * 4.0 / 3.0 * math.pi * R ** 3
         assert abs(W.resting_damping(R) - math.sqrt(W.COMMON["kn"] * m)) < 1e-12
+
+
+def test_campaign_smoothing_and_contact_helpers():
+    """The moving average keeps a constant series, averages a linear one to
+    itself away from the ends, works per sphere, and shortens its window at
+    the ends; touching() flags samples whose shell reaches phase a."""
+    T, n = 40, 3
+    t = np.arange(T, dtype=float)
+    Y = np.stack([np.stack([t * (k + 1), np.full(T, 2.0 + k)], axis=1) for k in range(n)], axis=1).reshape(T * n, 2)
+    S = SS.smooth(Y, n, 8).reshape(T, n, 2)
+    assert np.allclose(S[:, :, 1], 2.0 + np.arange(n))
+    # a centred window over 8 samples of a linear series: the mean of t-4 .. t+3
+    assert np.allclose(S[10:30, 1, 0], 2.0 * (t[10:30] - 0.5))
+    assert np.isclose(S[0, 0, 0], np.mean(t[0:4]))
+    assert SS.smooth(Y, n, 1) is Y
+    X = np.zeros((3, 387))
+    X[0, 0:384:4] = -1.0
+    X[1, 0:384:4] = -1.0
+    X[1, 40] = 0.2
+    X[2, 0:384:4] = 0.9
+    assert SS.touching(X).tolist() == [False, True, True]
+
+
+def test_campaign_contexts_stay_under_the_node_limit():
+    ws = [SS.resolved(s) for s in range(1, 26)]
+    chunks = SS._chunks(ws)
+    assert sorted(i for c in chunks for i in c) == list(range(25))
+    for c in chunks:
+        assert sum(ws[i]["params"]["nx"] * ws[i]["params"]["ny"] * ws[i]["params"]["nz"] for i in c) <= SS.MAX_NODES
+        assert 38 * SS.MAX_NODES < 2 ** 31
+    assert max(len(c) for c in chunks) - min(len(c) for c in chunks) <= 1
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_moving_training_spheres_glide_together(seed):
+    """Prescribed glide: one velocity for all spheres of a seed, along the
+    substrate, scaled with the grid (the angular velocity is the same on both
+    grids), rolling without slip on odd seeds; held spheres otherwise."""
+    f, c = SS.resolved(seed, moving=True), SS.coarse(seed, moving=True)
+    vf = {q["v"] for q in f["particles"]}
+    assert len(vf) == 1
+    v = np.array(f["particles"][0]["v"])
+    assert v[2] == 0.0 and abs(v[0]) <= SS.FINE_U and abs(v[1]) <= SS.FINE_U / 3
+    assert np.allclose(np.array(c["particles"][0]["v"]), v * SS.SCALE)
+    assert np.allclose(c["particles"][0]["w"], f["particles"][0]["w"])
+    w = np.array(f["particles"][0]["w"])
+    if seed % 2:
+        R = f["particles"][0]["R"]
+        assert np.allclose(w, [-v[1] / R, v[0] / R, 0.0])
+    else:
+        assert np.all(w == 0.0)
+    assert all(q["kinematic"] == 1 for q in f["particles"])
+    assert "v" not in SS.resolved(seed)["particles"][0]
