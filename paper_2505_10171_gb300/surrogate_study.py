@@ -276,7 +276,7 @@ def campaign(train_seeds, test_seeds, steps=16000, every=16, epochs=40, batch=51
     for tag, w_ in (("raw", 1), ("smoothed", win)):
         Yr = np.concatenate([smooth(r["Y"], n_sph, w_) for r in ref])
         table[f"ref_force_mean_{tag}"] = float(np.linalg.norm(Yr[:, 0:3], axis=1).mean())
-        table[f"ref_force_mean_touching_{tag}"] = float(np.linalg.norm(Yr[touch, 0:3], axis=1).mean())
+        table[f"ref_force_mean_touching_{tag}"] = (float(np.linalg.norm(Yr[touch, 0:3], axis=1).mean()) if touch.any() else float("nan"))
         for name, rows in series.items():
             Ys = np.concatenate([smooth(y, n_sph, w_) for y in rows])
             table[f"{name}_{tag}"] = list(errors(Ys, Yr))
@@ -303,7 +303,7 @@ def evaluate(weights, test_seeds, steps=16000, every=16, free=False, win=64, str
     for tag, w_ in (("raw", 1), ("smoothed", win)):
         Yr = np.concatenate([smooth(r["Y"], n_sph, w_) for r in ref])
         table[f"ref_force_mean_{tag}"] = float(np.linalg.norm(Yr[:, 0:3], axis=1).mean())
-        table[f"ref_force_mean_touching_{tag}"] = float(np.linalg.norm(Yr[touch, 0:3], axis=1).mean())
+        table[f"ref_force_mean_touching_{tag}"] = (float(np.linalg.norm(Yr[touch, 0:3], axis=1).mean()) if touch.any() else float("nan"))
         for name, rows in series.items():
             Ys = np.concatenate([smooth(y, n_sph, w_) for y in rows])
             table[f"{name}_{tag}"] = list(errors(Ys, Yr))
