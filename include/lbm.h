@@ -359,6 +359,19 @@ lbm_status lbm_component_masses_noalloc(const double *pops, long long n_nodes, d
 enum { LBM_FAULT_NONE = 0, LBM_FAULT_GEMM_NO_COMMIT = 1 };
 lbm_status lbm_inject_fault(lbm_ctx *ctx, int fault);
 
+/* Run state of a context, for an exact resume beside the populations
+ * (lbm_read_fields / lbm_init_fields) and the particle checkpoint:
+ * out[0] = steps taken (the drop-speed control and the diagnostics are
+ * scheduled on it), then per instance 9 doubles: the body force on phase a
+ * now [3], the drop-speed control's error integral [3] and the phase-a
+ * velocity at its last update [3] (the PI law of lbm_params).
+ * lbm_run_state_size gives 1 + 9 n_instances (-1 for a null context).
+ * Get synchronises; set is valid before the first step only (-> LBM_ERR_STATE),
+ * checks n and finiteness (-> LBM_ERR_ARG) and invalidates the step graph. */
+long long lbm_run_state_size(const lbm_ctx *ctx);
+lbm_status lbm_get_run_state(lbm_ctx *ctx, double *out, size_t n);
+lbm_status lbm_set_run_state(lbm_ctx *ctx, const double *in, size_t n);
+
 /* Drop-speed control state of an instance: out[0..2] the body force on phase
  * a now, out[3..5] U_a at the last update (zeros before the first).
  * Synchronises. */

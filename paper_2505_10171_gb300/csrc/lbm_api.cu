@@ -1686,6 +1686,57 @@ lbm_status lbm_inject_fault(lbm_ctx *ctx, int fault)
     return LBM_OK;
 }
 
+long long lbm_run_state_size(const lbm_ctx *ctx) { return ctx ? 1 + 9LL * ctx->n_inst : -1; }
+
+lbm_status lbm_get_run_state(lbm_ctx *ctx, double *out, size_t n)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!out || (long long)n != lbm_run_state_size(ctx)) return fail(ctx, LBM_ERR_ARG, "n must be lbm_run_state_size");
+    CU(cudaStreamSynchronize(ctx->stream));
+    std::vector<InstDev> h((size_t)ctx->n_inst);
+    CU(cudaMemcpy(h.data(), ctx->inst_d, sizeof(InstDev) * ctx->n_inst, cudaMemcpyDeviceToHost));
+    std::vector<double> sp(6 * (size_t)ctx->n_inst);
+    CU(cudaMemcpy(sp.data(), ctx->speed_d, sizeof(double) * sp.size(), cudaMemcpyDeviceToHost));
+    out[0] = (double)ctx->steps;
+    for (int k = 0; k < ctx->n_inst; k++) {
+        double *o = out + 1 + 9 * k;
+        for (int a = 0; a < 3; a++) {
+            o[a] = h[(size_t)k].body_a[a];
+            o[3 + a] = sp[6 * (size_t)k + a];
+            o[6 + a] = sp[6 * (size_t)k + 3 + a];
+        }
+    }
+    return check_status(ctx);
+}
+
+lbm_status lbm_set_run_state(lbm_ctx *ctx, const double *in, size_t n)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (!in || (long long)n != lbm_run_state_size(ctx)) return fail(ctx, LBM_ERR_ARG, "n must be lbm_run_state_size");
+    if (ctx->stepped) return fail(ctx, LBM_ERR_STATE, "the run state is restored before the first step");
+    for (size_t k = 0; k < n; k++)
+        if (!std::isfinite(in[k])) return fail(ctx, LBM_ERR_ARG, "non-finite run state");
+    if (!(in[0] >= 0.0) || in[0] != std::floor(in[0]) || in[0] > 9.0e15)
+        return fail(ctx, LBM_ERR_ARG, "steps taken must be a non-negative integer");
+    std::vector<double> sp(6 * (size_t)ctx->n_inst);
+    for (int k = 0; k < ctx->n_inst; k++) {
+        const double *o = in + 1 + 9 * k;
+        InstDev &I = ctx->inst_h[(size_t)k];
+        for (int a = 0; a < 3; a++) {
+            I.body_a[a] = o[a];
+            I.f_body_a[a] = (float)o[a];
+            sp[6 * (size_t)k + a] = o[3 + a];
+            sp[6 * (size_t)k + 3 + a] = o[6 + a];
+        }
+    }
+    CU(cudaStreamSynchronize(ctx->stream));
+    CU(cudaMemcpy(ctx->inst_d, ctx->inst_h.data(), sizeof(InstDev) * ctx->n_inst, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->speed_d, sp.data(), sizeof(double) * sp.size(), cudaMemcpyHostToDevice));
+    ctx->steps = (long long)in[0];
+    drop_graph(ctx);
+    return LBM_OK;
+}
+
 lbm_status lbm_drop_speed_state(lbm_ctx *ctx, int inst, double *out)
 {
     if (!ctx || !out || inst < 0 || inst >= ctx->n_inst) return fail(ctx, LBM_ERR_ARG, "bad instance or output");

@@ -81,7 +81,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_set_fluid_kernel", "lbm_fluid_form_in_use", "lbm_set_force_model", "lbm_surrogate_load",
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
            "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion",
-           "lbm_inject_fault", "lbm_particle_state_size", "lbm_get_particle_state", "lbm_set_particle_state"]
+           "lbm_inject_fault", "lbm_particle_state_size", "lbm_get_particle_state", "lbm_set_particle_state",
+           "lbm_run_state_size", "lbm_get_run_state", "lbm_set_run_state"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -127,6 +128,8 @@ def load(path: str = LIB_PATH):
     L.lbm_last_launch_count.restype = ct.c_longlong
     L.lbm_particle_state_size.argtypes = [vp, i]
     L.lbm_particle_state_size.restype = ct.c_longlong
+    L.lbm_run_state_size.argtypes = [vp]
+    L.lbm_run_state_size.restype = ct.c_longlong
     L.lbm_profile.argtypes = [vp, i]
     L.lbm_profile_read.argtypes = [vp, d, i]
     L.lbm_component_masses_noalloc.argtypes = [vp, ct.c_longlong, vp, vp]
@@ -144,10 +147,12 @@ def load(path: str = LIB_PATH):
     L.lbm_autotune.argtypes = [vp, i, P(ct.c_int), P(ct.c_int), d]
     L.lbm_inject_fault.argtypes = [vp, i]
     L.lbm_get_particle_state.argtypes = [vp, i, d, ct.c_size_t]
+    L.lbm_get_run_state.argtypes = [vp, d, ct.c_size_t]
+    L.lbm_set_run_state.argtypes = [vp, d, ct.c_size_t]
     L.lbm_set_particle_state.argtypes = [vp, i, d, ct.c_size_t]
     for name in EXPORTS:
         if name not in ("lbm_destroy", "lbm_last_error", "lbm_num_particles", "lbm_num_nodes",
-                        "lbm_last_launch_count", "lbm_particle_state_size"):
+                        "lbm_last_launch_count", "lbm_particle_state_size", "lbm_run_state_size"):
             getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -299,6 +304,18 @@ class Context:
     def lbm_set_particle_state(self, state, inst=0):
         st = np.ascontiguousarray(state, dtype=np.float64)
         self._check(self.L.lbm_set_particle_state(self.h, inst, _dp(st), ct.c_size_t(st.size)))
+
+    def lbm_get_run_state(self):
+        """Steps taken, then per instance the phase-a body force, the
+        drop-speed control's error integral and last measured velocity."""
+        n = int(self.L.lbm_run_state_size(self.h))
+        out = np.zeros(n)
+        self._check(self.L.lbm_get_run_state(self.h, _dp(out), ct.c_size_t(n)))
+        return out
+
+    def lbm_set_run_state(self, state):
+        st = np.ascontiguousarray(state, dtype=np.float64)
+        self._check(self.L.lbm_set_run_state(self.h, _dp(st), ct.c_size_t(st.size)))
 
     def lbm_read_fields(self, mask, inst=0, out=None):
         N = self.num_nodes(inst)

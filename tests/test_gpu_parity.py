@@ -660,3 +660,53 @@ def test_particle_checkpoint_of_a_batched_instance():
     got = r.lbm_particle_forces(1)[0]
     r.close()
     assert np.abs(got[12:27] - ref[1][12:27]).max() <= 1e-13
+
+
+def test_resume_under_drop_speed_control():
+    """The 64x64x32 sub-box of the benchmark workload, with its drop-speed
+    control (updates every 50 steps here) and its sphere: after 120 steps the
+    populations, the particle checkpoint and the run state (steps taken, body
+    force, the control's integral and last velocity) are read; a new context
+    built from them continues to step 300 equal to the uninterrupted run to
+    rounding (FP64).  Without the run state the body force and the control's
+    schedule differ and so does the run."""
+    from paper_2505_10171_gb300 import lbm
+    w = W.cfg2_crop()
+    w["params"] = dict(w["params"], drop_speed_interval=50)
+    assert w["params"]["drop_speed_control"]
+    c = gpu_ctx(w, "fp64")
+    c.lbm_step(120)
+    fa, fb = c.pops()
+    pst = c.lbm_get_particle_state()
+    rst = c.lbm_get_run_state()
+    c.lbm_step(180)
+    ref_a, ref_b = c.pops()
+    ref_run = c.lbm_get_run_state()
+    c.close()
+    assert rst[0] == 120 and ref_run[0] == 300
+    assert np.abs(rst[1:4] - np.asarray(w["params"]["body_force_a"])).max() > 0  # the control acted
+    out = {}
+    for keep in (True, False):
+        parts = [dict(p, x=tuple(pst[lbm.PARTICLE_STATE * k:lbm.PARTICLE_STATE * k + 3]))
+                 for k, p in enumerate(w["particles"])]
+        r = gpu_ctx(dict(w, particles=parts), "fp64")
+        r.lbm_init_fields(None, pops=np.concatenate([fa, fb]))
+        r.lbm_set_particle_state(pst)
+        if keep:
+            r.lbm_set_run_state(rst)
+        r.lbm_step(180)
+        out[keep] = (r.pops(), r.lbm_get_run_state())
+        r.close()
+    (ga, gb), run = out[True]
+    assert max(np.abs(ga - ref_a).max(), np.abs(gb - ref_b).max()) <= 1e-12
+    assert np.abs(run - ref_run).max() <= 1e-12 * max(1.0, np.abs(ref_run).max())
+    (ha, hb), _ = out[False]
+    assert max(np.abs(ha - ref_a).max(), np.abs(hb - ref_b).max()) > 1e-9
+    bad = gpu_ctx(w, "fp64")
+    with pytest.raises(lbm.LbmError):
+        bad.lbm_set_run_state(rst[:-1])
+    bad.lbm_step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        bad.lbm_set_run_state(rst)  # after the first step
+    assert e.value.status == 4
+    bad.close()
