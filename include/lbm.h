@@ -237,6 +237,14 @@ lbm_status lbm_set_particle_motion(lbm_ctx *ctx, int inst, int p, const double *
  * the last step; out holds n_particles records.  Synchronises. */
 lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out);
 
+/* As lbm_particle_forces, enqueued on the context's stream without
+ * synchronising: the records are packed on the device and copied to out,
+ * which should be page-locked host memory for the copy to overlap (the
+ * values are valid once the stream has reached the copy, e.g. after the next
+ * synchronising call).  Lets a caller read every step's forces without
+ * stalling the device.  Bad instance or null out -> LBM_ERR_ARG. */
+lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out);
+
 /* Checkpoint of an instance's particles, for an exact resume with contacts
  * (the DEM of Sec. III carries state from step to step).  Per particle
  * LBM_PARTICLE_STATE doubles: x[3] v[3] w[3] q[4] (w, x, y, z), then the total

@@ -48,6 +48,9 @@ struct lbm_ctx {
     cudaEvent_t ev_fork = nullptr, ev_grad = nullptr, ev_join = nullptr, ev_a = nullptr, ev_b = nullptr;
     cudaGraphExec_t graph = nullptr;
     long long graph_launches = 0;
+    cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // one step from buffer 0 / from buffer 1
+    long long graph1_launches[2] = {0, 0};
+    double *rec_d = nullptr;  // packed particle records of lbm_particle_forces_async
     long long last_launches = 0;
     double *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -648,6 +651,30 @@ static void drop_graph(lbm_ctx *c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
+    for (int k = 0; k < 2; k++) {
+        if (c->graph1[k]) cudaGraphExecDestroy(c->graph1[k]);
+        c->graph1[k] = nullptr;
+    }
+}
+
+// the records of lbm_particle_forces, packed on the device (one thread per
+// particle of the instance)
+__global__ void k_pack_records(const PartDev *parts, int np, double *out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const PartDev &q = parts[p];
+    double *o = out + (size_t)LBM_PARTICLE_RECORD * p;
+    for (int a = 0; a < 3; a++) {
+        o[a] = q.Feta[a]; o[3 + a] = q.Teta[a];
+        o[6 + a] = q.Fsig[a]; o[9 + a] = q.Tsig[a];
+        o[12 + a] = q.Fc[a]; o[15 + a] = q.Tc[a];
+        o[18 + a] = q.x[a]; o[21 + a] = q.v[a]; o[24 + a] = q.w[a];
+    }
+    for (int a = 0; a < 4; a++) o[27 + a] = q.q[a];
+    o[31] = q.m;
+    o[32] = q.sub;
+    for (int a = 0; a < 3; a++) o[33 + a] = q.Fb[a];
 }
 
 // ---------------------------------------------------------------------------
@@ -675,6 +702,7 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->static_list);
     cudaFree(ctx->static_bfl);
     cudaFree(ctx->speed_d);
+    cudaFree(ctx->rec_d);
     cudaFree(ctx->speed_part);
     mlp_free(ctx->mlp);
     cudaFree(ctx->feat);
@@ -1112,6 +1140,8 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     const size_t np = all.size();
     CU(cudaStreamSynchronize(ctx->stream));
     cudaFree(ctx->parts_d);
+    cudaFree(ctx->rec_d);
+    ctx->rec_d = nullptr;
     cudaFree(ctx->mem_part);
     cudaFree(ctx->cap_part);
     cudaFree(ctx->hist);
@@ -1202,7 +1232,31 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps)
                 launches += 2 * ctx->n_inst;
             }
         } else {
-            enqueue_step(ctx, &launches);
+            // a single step: replayed from its own graph (one per buffer
+            // parity), eagerly while profiling
+            if (ctx->profile) {
+                enqueue_step(ctx, &launches);
+            } else {
+                const int c0 = ctx->cur;
+                if (!ctx->graph1[c0]) {
+                    cudaGraph_t g;
+                    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                    long long l = 0;
+                    enqueue_step(ctx, &l);  // flips ctx->cur, as the replayed step will
+                    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+                    if (e != cudaSuccess)
+                        return fail(ctx, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+                    e = cudaGraphInstantiate(&ctx->graph1[c0], g, cudaGraphInstantiateFlagUseNodePriority);
+                    cudaGraphDestroy(g);
+                    if (e != cudaSuccess)
+                        return fail(ctx, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+                    ctx->graph1_launches[c0] = l;
+                } else {
+                    ctx->cur ^= 1;
+                }
+                CU(cudaGraphLaunch(ctx->graph1[c0], ctx->stream));
+                launches += ctx->graph1_launches[c0];
+            }
             nsteps -= 1;
             ctx->steps += 1;
             take_speed(ctx, &launches);
@@ -1307,6 +1361,25 @@ lbm_status lbm_set_particle_state(lbm_ctx *ctx, int inst, const double *in, size
                        sizeof(double) * 6 * I.np * (I.np + 1), cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));  // the host copies are pageable and local
     drop_graph(ctx);
+    return LBM_OK;
+}
+
+lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    if (inst < 0 || inst >= ctx->n_inst || !out) return fail(ctx, LBM_ERR_ARG, "bad instance or output");
+    const InstDev &I = ctx->inst_h[inst];
+    if (I.np == 0) return LBM_OK;
+    if (!ctx->rec_d) {
+        // records of every particle of the context, allocated on first use
+        CU(cudaStreamSynchronize(ctx->stream));
+        CU(cudaMalloc((void **)&ctx->rec_d, sizeof(double) * LBM_PARTICLE_RECORD * ctx->parts_h.size()));
+    }
+    double *dst = ctx->rec_d + (size_t)LBM_PARTICLE_RECORD * I.part_off;
+    k_pack_records<<<(I.np + 63) / 64, 64, 0, ctx->stream>>>(ctx->parts_d + I.part_off, I.np, dst);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(out, dst, sizeof(double) * LBM_PARTICLE_RECORD * I.np, cudaMemcpyDeviceToHost,
+                       ctx->stream));
     return LBM_OK;
 }
 

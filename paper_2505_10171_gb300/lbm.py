@@ -82,7 +82,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
            "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion",
            "lbm_inject_fault", "lbm_particle_state_size", "lbm_get_particle_state", "lbm_set_particle_state",
-           "lbm_run_state_size", "lbm_get_run_state", "lbm_set_run_state"]
+           "lbm_run_state_size", "lbm_get_run_state", "lbm_set_run_state", "lbm_particle_forces_async"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
     L.lbm_add_particles.argtypes = [vp, i, i, P(lbm_particle)]
     L.lbm_step.argtypes = [vp, i]
     L.lbm_particle_forces.argtypes = [vp, i, d]
+    L.lbm_particle_forces_async.argtypes = [vp, i, d]
     L.lbm_set_particle_motion.argtypes = [vp, i, i, d, d]
     L.lbm_read_fields.argtypes = [vp, i, ct.c_uint, d]
     L.lbm_read_fields_device.argtypes = [vp, i, ct.c_uint, vp]
@@ -316,6 +317,15 @@ class Context:
     def lbm_set_run_state(self, state):
         st = np.ascontiguousarray(state, dtype=np.float64)
         self._check(self.L.lbm_set_run_state(self.h, _dp(st), ct.c_size_t(st.size)))
+
+    def lbm_particle_forces_async(self, out, inst=0):
+        """Enqueue the read of the particle records into out (a float64 array of
+        at least n_particles x PARTICLE_RECORD, page-locked for the copy to
+        overlap); valid after the next synchronisation."""
+        n = self.num_particles(inst)
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < n * PARTICLE_RECORD:
+            raise ValueError("out must be a C-contiguous float64 array of n_particles x PARTICLE_RECORD")
+        self._check(self.L.lbm_particle_forces_async(self.h, inst, _dp(out)))
 
     def lbm_read_fields(self, mask, inst=0, out=None):
         N = self.num_nodes(inst)

@@ -710,3 +710,29 @@ def test_resume_under_drop_speed_control():
         bad.lbm_set_run_state(rst)  # after the first step
     assert e.value.status == 4
     bad.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_step_calls_equal_bulk_steps(prec):
+    """lbm_step(1) replays a captured one-step graph (one per buffer parity);
+    40 single-step calls give the same bits as one call of 40 steps, and the
+    records read asynchronously each step equal the synchronous read."""
+    w = W.cfg1()
+    a = gpu_ctx(w, prec)
+    a.lbm_step(40)
+    fa, fb = a.pops()
+    ra = a.lbm_particle_forces()
+    a.close()
+    b = gpu_ctx(w, prec)
+    from paper_2505_10171_gb300 import lbm
+    recs = np.zeros((40, lbm.PARTICLE_RECORD))
+    for k in range(40):
+        b.lbm_step(1)
+        b.lbm_particle_forces_async(recs[k])
+    gb_a, gb_b = b.pops()  # synchronises
+    rb = b.lbm_particle_forces()
+    b.close()
+    assert np.array_equal(fa, gb_a) and np.array_equal(fb, gb_b)
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(recs[-1], rb[0])
+    assert not np.array_equal(recs[0], recs[-1])
