@@ -217,11 +217,13 @@ lbm_status lbm_init_fields_device(lbm_ctx *ctx, int inst, const double *phi, con
  * the first lbm_step (-> LBM_ERR_STATE). */
 lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *parts);
 
-/* Advance every instance by nsteps coupled time steps (Sec. IV-V and Fig. 5
- * order: streaming with bounce-back, momentum exchange, order parameter,
- * gradient with wetting, curvature and CSF force, MRT collision with Guo
- * forcing, recolouring, capillary force, DEM, geometry update and refill).
- * Asynchronous on the context's stream; replays a captured CUDA graph. */
+/* Advance every instance by nsteps coupled time steps (Sec. IV-V, in the order
+ * of the paper's flow chart of the coupled algorithm, Fig. 4): streaming with
+ * bounce-back, momentum exchange, order parameter, gradient with wetting,
+ * curvature and CSF force, MRT collision with Guo forcing, recolouring,
+ * capillary force, DEM, geometry update and refill.  Asynchronous on the
+ * context's stream; replays a captured CUDA graph (of two steps, or of one
+ * step for a single-step call). */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
 
 /* Set the velocity v and angular velocity w of particle p of an instance

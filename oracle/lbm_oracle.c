@@ -842,9 +842,10 @@ int or_dem_only_step(or_sim *s, int n, double *traj)
 }
 
 /* ---------------------------------------------------------------------- */
-/* one coupled time step (READING c26: the order of Fig. 5 is taken as     */
-/* stream+bounce-back+momentum exchange, moments, gradient+wetting,        */
-/* curvature, force, MRT+Guo, recolour, capillary force, DEM, refill)      */
+/* one coupled time step (READING c26: the order of the flow chart of the */
+/* coupled algorithm, Fig. 4, is taken as stream + bounce-back + momentum */
+/* exchange, moments, gradient + wetting, curvature, force, MRT + Guo,     */
+/* recolour, capillary force, DEM, refill)                                 */
 /* ---------------------------------------------------------------------- */
 static void step_once(or_sim *s)
 {
