@@ -34,6 +34,9 @@ struct lbm_ctx {
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
     double *mem_part = nullptr, *cap_part = nullptr, *hist = nullptr;
+    long long *pbl = nullptr;              // boundary-pass list of particle nodes
+    unsigned long long *pbl_n = nullptr;
+    int n_sm = 1;
     double *cap_pts = nullptr;  // Lagrangian surface-point table
     double *crec = nullptr;     // DEM contact records
     unsigned *status = nullptr;
@@ -145,6 +148,12 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.geom_blocks = c->geom_blocks;
     L.geom_side = c->geom_side;
     L.cap_side = c->cap_side;
+    L.pbl = c->pbl;
+    L.pbl_n = c->pbl_n;
+#ifndef LBM_BOUND_CTAS_PER_SM
+#define LBM_BOUND_CTAS_PER_SM 2
+#endif
+    L.bound_ctas = LBM_BOUND_CTAS_PER_SM * c->n_sm;
     L.cap_blocks = c->cap_blocks;
     L.mem_part = c->mem_part;
     L.cap_part = c->cap_part;
@@ -703,6 +712,8 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->static_bfl);
     cudaFree(ctx->speed_d);
     cudaFree(ctx->rec_d);
+    cudaFree(ctx->pbl);
+    cudaFree(ctx->pbl_n);
     cudaFree(ctx->speed_part);
     mlp_free(ctx->mlp);
     cudaFree(ctx->feat);
@@ -844,6 +855,12 @@ lbm_status lbm_create(const lbm_params *params, int n_instances, lbm_precision p
     // bulk fluid kernels: at the highest priority their CTAs are dispatched as
     // soon as bulk CTAs retire instead of after the whole bulk grid (at the
     // lowest priority the 256x128x128 step measured 452 against 390 us)
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && sms > 0)
+            ctx->n_sm = sms;
+    }
     int prio_least = 0, prio_greatest = 0;
     cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
@@ -1142,6 +1159,8 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     cudaFree(ctx->parts_d);
     cudaFree(ctx->rec_d);
     ctx->rec_d = nullptr;
+    cudaFree(ctx->pbl);
+    ctx->pbl = nullptr;
     cudaFree(ctx->mem_part);
     cudaFree(ctx->cap_part);
     cudaFree(ctx->hist);
@@ -1149,6 +1168,9 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     ctx->parts_d = nullptr;
     ctx->mem_part = ctx->cap_part = ctx->hist = ctx->crec = nullptr;
     CU(cudaMalloc((void **)&ctx->parts_d, sizeof(PartDev) * np));
+    // every node of every particle's cube can be listed once per cube
+    CU(cudaMalloc((void **)&ctx->pbl, sizeof(long long) * np * (size_t)ctx->cap_blocks * PART_THREADS));
+    if (!ctx->pbl_n) CU(cudaMalloc((void **)&ctx->pbl_n, sizeof(unsigned long long)));
     CU(cudaMalloc((void **)&ctx->mem_part, sizeof(double) * MEM_PART * np * ctx->mem_blocks));
     CU(cudaMalloc((void **)&ctx->cap_part, sizeof(double) * CAP_PART * np * CAP_BLOCKS));
     CU(cudaMalloc((void **)&ctx->hist, sizeof(double) * 6 * std::max(hist, 1)));

@@ -153,48 +153,59 @@ void launch_static_bound(const Lattice &L, long long *list, unsigned long long *
 }
 
 
-// node of the boundary passes: blockIdx.y < n_parts: the cube of side
-// cap_side around that particle; blockIdx.y == n_parts: the static list of
-// nodes next to static solids.  Returns false for threads without a node.
-__device__ __forceinline__ bool bound_node(const Lattice &L, const InstDev **Ip, int *n, int *x, int *y, int *z)
+// the fluid nodes next to a solid inside the particle cubes (cubes of side
+// cap_side around each particle, cap_blocks CTAs each), appended to L.pbl
+// with one atomic per warp: the particle part of the boundary passes' work
+// list, rebuilt at the start of every step (the flags do not change within
+// a step).  Order within the list does not matter; a node in two cubes is
+// listed twice and written twice with the same value.
+__global__ void __launch_bounds__(PART_THREADS) k_bound_list(Lattice L)
 {
-    // one flat grid: cap_blocks CTAs per particle cube, then the static list
-    const long long cube_ctas = (long long)L.n_parts * L.cap_blocks;
     const long long b = blockIdx.x;
-    if (b < cube_ctas) {
-        const long long t = (b % L.cap_blocks) * blockDim.x + threadIdx.x;
-        const PartDev &P0 = L.parts[b / L.cap_blocks];
-        const InstDev &I = L.inst[P0.inst];
-        Region reg;
-        reg.init(P0.x, L.cap_side, I.nx, I.ny, I.nz);
-        if (t >= reg.count()) return false;
-        reg.coord(t, I.nx, I.ny, I.nz, x, y, z);
-        *n = (*z * I.ny + *y) * I.nx + *x;
-        *Ip = &I;
-        return true;
+    const long long t = (b % L.cap_blocks) * blockDim.x + threadIdx.x;
+    const PartDev &P0 = L.parts[b / L.cap_blocks];
+    const InstDev &I = L.inst[P0.inst];
+    Region reg;
+    reg.init(P0.x, L.cap_side, I.nx, I.ny, I.nz);
+    bool take = false;
+    long long g = 0;
+    if (t < reg.count()) {
+        int x, y, z;
+        reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
+        g = I.node_off + ((long long)z * I.ny + y) * I.nx + x;
+        const uint8_t fl = L.flags[g];
+        take = (fl & OWNER_MASK) == OWN_FLUID && (fl & BOUND_BIT);
     }
-    const long long t = (b - cube_ctas) * blockDim.x + threadIdx.x;
-    if (t >= L.n_static_bfl) return false;
-    const long long g = L.static_bfl[t];
+    const unsigned m = __ballot_sync(0xffffffffu, take);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(L.pbl_n, (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (take) L.pbl[base + __popc(m & ((1u << lane) - 1u))] = g;
+}
+
+// work item t of the boundary passes: the listed particle nodes, then the
+// static list of nodes next to static solids
+__device__ __forceinline__ void bound_item(const Lattice &L, long long npb, long long t, const InstDev **Ip, int *n,
+                                           int *x, int *y, int *z)
+{
+    const long long g = t < npb ? L.pbl[t] : L.static_bfl[t - npb];
     const InstDev &I = L.inst[inst_of_node(L, g)];
     *n = (int)(g - I.node_off);
     *x = *n % I.nx;
     *y = (*n / I.nx) % I.ny;
     *z = *n / (I.nx * I.ny);
     *Ip = &I;
-    return true;
 }
 
 // the boundary passes: fluid nodes next to a solid, with the bounce-back
-// pull (Sec. V A); a node reached twice (cube and list) is written twice
-// with the same value
+// pull (Sec. V A), grid-stride over the work list; a node listed twice (two
+// cubes, or a cube and the static list) is written twice with the same value
 template <class S>
-__global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_phi_bound(Lattice L, int cur)
+__device__ __forceinline__ void phi_bound_node(const Lattice &L, int cur, const InstDev *I, int n, int x, int y, int z)
 {
     using R = typename Store<S>::real;
-    const InstDev *I;
-    int n, x, y, z;
-    if (!bound_node(L, &I, &n, &x, &y, &z)) return;
     const long long g = I->node_off + n;
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
@@ -211,12 +222,24 @@ __global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_phi_bound(Latt
 }
 
 template <class S>
-__global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_collide_bound(Lattice L, int cur)
+__global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_phi_bound(Lattice L, int cur)
+{
+    const long long npb = L.pbl_n ? (long long)*L.pbl_n : 0;
+    const long long total = npb + L.n_static_bfl;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const InstDev *I;
+        int n, x, y, z;
+        bound_item(L, npb, t, &I, &n, &x, &y, &z);
+        phi_bound_node<S>(L, cur, I, n, x, y, z);
+    }
+}
+
+template <class S>
+__device__ __forceinline__ void collide_bound_node(const Lattice &L, int cur, const InstDev *I, int n, int x, int y,
+                                                   int z)
 {
     using R = typename Store<S>::real;
-    const InstDev *I;
-    int n, x, y, z;
-    if (!bound_node(L, &I, &n, &x, &y, &z)) return;
     const long long g = I->node_off + n;
     const uint8_t fl = L.flags[g];
     if ((fl & OWNER_MASK) != OWN_FLUID || !(fl & BOUND_BIT)) return;
@@ -237,6 +260,20 @@ __global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_collide_bound(
     const R nn[3] = {Nn[n], Nn[Nt + n], Nn[2 * Nt + n]};
     collide_store_phi<S>(P, F, ((const R *)L.phi)[g], gr, nn, ((const R *)L.kap)[g], out, n,
                          col_slot<S>(L, g), U, L.Ntot, L.status);
+}
+
+template <class S>
+__global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_collide_bound(Lattice L, int cur)
+{
+    const long long npb = L.pbl_n ? (long long)*L.pbl_n : 0;
+    const long long total = npb + L.n_static_bfl;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const InstDev *I;
+        int n, x, y, z;
+        bound_item(L, npb, t, &I, &n, &x, &y, &z);
+        collide_bound_node<S>(L, cur, I, n, x, y, z);
+    }
 }
 
 template <class R>
@@ -673,9 +710,15 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     using R = typename Store<S>::real;
     const dim3 grid((unsigned)fz.rows);  // one CTA per row-strip work item
     const bool pair = sizeof(S) == 2 && fz.pair;
-    // boundary passes: particle cubes and the static list of nodes next to walls
-    const long long bctas = (long long)L.n_parts * L.cap_blocks + (L.n_static_bfl + PART_THREADS - 1) / PART_THREADS;
-    const dim3 bgrid((unsigned)std::max(bctas, 1LL));
+    // boundary passes: grid-stride over the listed particle nodes and the
+    // static list of nodes next to walls
+    const dim3 bgrid((unsigned)std::max(L.bound_ctas, 1));
+    auto list_bound = [&](cudaStream_t s) {
+        if (L.n_parts == 0) return;
+        cudaMemsetAsync(L.pbl_n, 0, sizeof(unsigned long long), s);
+        k_bound_list<<<(unsigned)((long long)L.n_parts * L.cap_blocks), PART_THREADS, 0, s>>>(L);
+        *launches += 1;
+    };
     // phi of solid nodes next to fluid: the listed static nodes and the
     // particle cubes (every particle node lies within R_p + 1 of its centre).
     // It reads phi only at fluid nodes next to a solid, which the boundary
@@ -698,6 +741,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         if (lane.side) {
             cudaEventRecord(lane.a, st);
             cudaStreamWaitEvent(lane.side, lane.a, 0);
+            if (stage == STAGE_PHI) list_bound(lane.side);
             kernel<<<bgrid, PART_THREADS, 0, lane.side>>>(L, cur);
             if (stage == STAGE_PHI) fill_solid_phi(lane.side);
             cudaEventRecord(lane.b, lane.side);
@@ -709,6 +753,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
             bulk();
             mk(stage, 1);
             mk(bstage, 0);
+            if (stage == STAGE_PHI) list_bound(st);
             kernel<<<bgrid, PART_THREADS, 0, st>>>(L, cur);
             mk(bstage, 1);
         }

@@ -188,6 +188,9 @@ struct Lattice {
     int geom_blocks;     // blocks per particle of the geometry kernels
     int geom_side;       // side of the cube the geometry kernels cover
     int cap_side;        // side of the cube of phi around a particle for the capillary force
+    long long *pbl;              // fluid nodes next to a solid inside the particle cubes (global index), this step
+    unsigned long long *pbl_n;   // their number
+    int bound_ctas;              // CTAs of the grid-stride boundary passes
     int cap_blocks;      // blocks per particle covering that cube
     double *mem_part;    // [n_parts][mem_blocks][MEM_PART]
     double *cap_part;    // [n_parts][CAP_BLOCKS][CAP_PART]
