@@ -34,8 +34,8 @@ struct lbm_ctx {
     std::vector<PartDev> parts_h;
     PartDev *parts_d = nullptr;
     double *mem_part = nullptr, *cap_part = nullptr, *hist = nullptr;
-    long long *pbl = nullptr;              // boundary-pass list of particle nodes
-    unsigned long long *pbl_n = nullptr;
+    long long *pbl = nullptr, *psl = nullptr;  // lists of particle-adjacent fluid / solid nodes
+    unsigned long long *pbl_n = nullptr, *psl_n = nullptr;
     int n_sm = 1;
     double *cap_pts = nullptr;  // Lagrangian surface-point table
     double *crec = nullptr;     // DEM contact records
@@ -150,6 +150,8 @@ static Lattice make_lattice(const lbm_ctx *c)
     L.cap_side = c->cap_side;
     L.pbl = c->pbl;
     L.pbl_n = c->pbl_n;
+    L.psl = c->psl;
+    L.psl_n = c->psl_n;
 #ifndef LBM_BOUND_CTAS_PER_SM
 #define LBM_BOUND_CTAS_PER_SM 2
 #endif
@@ -714,6 +716,8 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->rec_d);
     cudaFree(ctx->pbl);
     cudaFree(ctx->pbl_n);
+    cudaFree(ctx->psl);
+    cudaFree(ctx->psl_n);
     cudaFree(ctx->speed_part);
     mlp_free(ctx->mlp);
     cudaFree(ctx->feat);
@@ -1160,7 +1164,8 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     cudaFree(ctx->rec_d);
     ctx->rec_d = nullptr;
     cudaFree(ctx->pbl);
-    ctx->pbl = nullptr;
+    cudaFree(ctx->psl);
+    ctx->pbl = ctx->psl = nullptr;
     cudaFree(ctx->mem_part);
     cudaFree(ctx->cap_part);
     cudaFree(ctx->hist);
@@ -1170,7 +1175,9 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     CU(cudaMalloc((void **)&ctx->parts_d, sizeof(PartDev) * np));
     // every node of every particle's cube can be listed once per cube
     CU(cudaMalloc((void **)&ctx->pbl, sizeof(long long) * np * (size_t)ctx->cap_blocks * PART_THREADS));
+    CU(cudaMalloc((void **)&ctx->psl, sizeof(long long) * np * (size_t)ctx->cap_blocks * PART_THREADS));
     if (!ctx->pbl_n) CU(cudaMalloc((void **)&ctx->pbl_n, sizeof(unsigned long long)));
+    if (!ctx->psl_n) CU(cudaMalloc((void **)&ctx->psl_n, sizeof(unsigned long long)));
     CU(cudaMalloc((void **)&ctx->mem_part, sizeof(double) * MEM_PART * np * ctx->mem_blocks));
     CU(cudaMalloc((void **)&ctx->cap_part, sizeof(double) * CAP_PART * np * CAP_BLOCKS));
     CU(cudaMalloc((void **)&ctx->hist, sizeof(double) * 6 * std::max(hist, 1)));

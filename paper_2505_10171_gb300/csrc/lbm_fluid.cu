@@ -45,20 +45,8 @@
 namespace lbmg {
 
 // ---------------------------------------------------------------------------
-// bulk kernels over all nodes, region kernels over the particle cubes
+// bulk kernels over all nodes, list kernels over the nodes next to solids
 // ---------------------------------------------------------------------------
-// region of particle blockIdx.y: nodes of a cube of side `side` around it
-#define LBM_REGION_PROLOGUE                                                                  \
-    const PartDev &P0 = L.parts[blockIdx.y];                                                 \
-    const InstDev &I = L.inst[P0.inst];                                                      \
-    Region reg;                                                                              \
-    reg.init(P0.x, side, I.nx, I.ny, I.nz);                                                  \
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;                   \
-    if (t >= reg.count()) return;                                                            \
-    int x, y, z;                                                                             \
-    reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);                                              \
-    const int n = (z * I.ny + y) * I.nx + x;
-
 // order parameter of a fluid node none of whose neighbours is solid; the
 // boundary pass (k_phi_bound) does the others.  Keeping the bounce-back code
 // out of the bulk kernel keeps its loads in flight (with it compiled in, the
@@ -157,7 +145,8 @@ void launch_static_bound(const Lattice &L, long long *list, unsigned long long *
 // cap_side around each particle, cap_blocks CTAs each), appended to L.pbl
 // with one atomic per warp: the particle part of the boundary passes' work
 // list, rebuilt at the start of every step (the flags do not change within
-// a step).  Order within the list does not matter; a node in two cubes is
+// a step); likewise the solid nodes next to fluid, for the solid-phi fill,
+// to L.psl.  Order within a list does not matter; a node in two cubes is
 // listed twice and written twice with the same value.
 __global__ void __launch_bounds__(PART_THREADS) k_bound_list(Lattice L)
 {
@@ -167,22 +156,28 @@ __global__ void __launch_bounds__(PART_THREADS) k_bound_list(Lattice L)
     const InstDev &I = L.inst[P0.inst];
     Region reg;
     reg.init(P0.x, L.cap_side, I.nx, I.ny, I.nz);
-    bool take = false;
+    bool fluid = false, solid = false;
     long long g = 0;
     if (t < reg.count()) {
         int x, y, z;
         reg.coord(t, I.nx, I.ny, I.nz, &x, &y, &z);
         g = I.node_off + ((long long)z * I.ny + y) * I.nx + x;
         const uint8_t fl = L.flags[g];
-        take = (fl & OWNER_MASK) == OWN_FLUID && (fl & BOUND_BIT);
+        fluid = (fl & OWNER_MASK) == OWN_FLUID && (fl & BOUND_BIT);
+        solid = (fl & OWNER_MASK) != OWN_FLUID && (fl & BOUND_BIT);
     }
-    const unsigned m = __ballot_sync(0xffffffffu, take);
-    if (!m) return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(L.pbl_n, (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (take) L.pbl[base + __popc(m & ((1u << lane) - 1u))] = g;
+    const int lane = threadIdx.x & 31;
+    auto append = [&](bool take, long long *list, unsigned long long *count) {
+        const unsigned m = __ballot_sync(0xffffffffu, take);
+        if (!m) return;
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (take) list[base + __popc(m & ((1u << lane) - 1u))] = g;
+    };
+    append(fluid, L.pbl, L.pbl_n);
+    append(solid, L.psl, L.psl_n);
 }
 
 // work item t of the boundary passes: the listed particle nodes, then the
@@ -276,11 +271,18 @@ __global__ void __launch_bounds__(PART_THREADS, LBM_BOUND_MINB) k_collide_bound(
     }
 }
 
+// solid-phi fill of the listed particle-surface solid nodes, grid-stride
 template <class R>
-__global__ void __launch_bounds__(PART_THREADS) k_solidphi_region(Lattice L, int side)
+__global__ void __launch_bounds__(PART_THREADS) k_solidphi_plist(Lattice L)
 {
-    LBM_REGION_PROLOGUE
-    solidphi_body<R>(L, I, n, x, y, z);
+    const long long nps = (long long)*L.psl_n;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nps;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long g = L.psl[t];
+        const InstDev &I = L.inst[inst_of_node(L, g)];
+        const int n = (int)(g - I.node_off);
+        solidphi_body<R>(L, I, n, n % I.nx, (n / I.nx) % I.ny, n / (I.nx * I.ny));
+    }
 }
 
 template <class S>
@@ -716,6 +718,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
     auto list_bound = [&](cudaStream_t s) {
         if (L.n_parts == 0) return;
         cudaMemsetAsync(L.pbl_n, 0, sizeof(unsigned long long), s);
+        cudaMemsetAsync(L.psl_n, 0, sizeof(unsigned long long), s);
         k_bound_list<<<(unsigned)((long long)L.n_parts * L.cap_blocks), PART_THREADS, 0, s>>>(L);
         *launches += 1;
     };
@@ -730,7 +733,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
             *launches += 1;
         }
         if (L.n_parts > 0) {
-            k_solidphi_region<R><<<dim3(L.cap_blocks, L.n_parts), PART_THREADS, 0, s>>>(L, L.cap_side - 2);
+            k_solidphi_plist<R><<<(unsigned)std::max(L.bound_ctas / 2, 1), PART_THREADS, 0, s>>>(L);
             *launches += 1;
         }
         fill_done = true;

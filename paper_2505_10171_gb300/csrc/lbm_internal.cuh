@@ -190,6 +190,8 @@ struct Lattice {
     int cap_side;        // side of the cube of phi around a particle for the capillary force
     long long *pbl;              // fluid nodes next to a solid inside the particle cubes (global index), this step
     unsigned long long *pbl_n;   // their number
+    long long *psl;              // solid nodes next to fluid inside the particle cubes, this step
+    unsigned long long *psl_n;   // their number
     int bound_ctas;              // CTAs of the grid-stride boundary passes
     int cap_blocks;      // blocks per particle covering that cube
     double *mem_part;    // [n_parts][mem_blocks][MEM_PART]
