@@ -356,34 +356,44 @@ __global__ void k_mass_final(const double *part, int nblk, double *out)
     }
 }
 
-// drop-speed control: FP64 sums over the fluid nodes of sum (rho^a/rho) j and
+// drop-speed control: sums over the fluid nodes of sum (rho^a/rho) j and
 // sum rho^a (per block), then one thread per instance applies the PI law to
-// the body force on phase a in the device instance table
+// the body force on phase a in the device instance table.  Each node's moments
+// are formed in the storage's arithmetic type (FP64 for FP64 storage, FP32
+// otherwise: the populations carry no more than that) and only the four
+// per-node products are accumulated in FP64, which keeps the sweep off the
+// slow FP64 pipe for the 16-bit and FP32 forms.
 template <class S>
 __global__ void k_speed_partial(Lattice L, int cur, int inst, double *part)
 {
+    using R = typename Store<S>::real;
     const InstDev &I = L.inst[inst];
     const long long N = I.N;
     const Pop<S> pop(L.pop[cur], I);
     const ColourOf<S> C(L, I);
+    const R rho0 = (R)I.rho0;
     double s[4] = {0.0, 0.0, 0.0, 0.0};
     for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
         if ((L.flags[I.node_off + n] & OWNER_MASK) != OWN_FLUID) continue;
-        const NodeState<S> ns{pop, C, (int)n};
-        double sF = 0.0, sG = 0.0, j[3] = {0.0, 0.0, 0.0};
+        const int m = (int)n;
+        const ColRec<R> c = C.at(m);
+        R sF = 0, sG = 0, j0 = 0, j1 = 0, j2 = 0;
         for (int i = 0; i < Q; i++) {
-            const double w = wgt<double>(i);
-            const double Fv = ns.F(i);
+            const R w = wgt<R>(i);
+            const R Fv = pop.F(i, m);
             sF += w * Fv;
-            sG += w * ns.G(i);
-            j[0] += w * cx(i) * Fv;
-            j[1] += w * cy(i) * Fv;
-            j[2] += w * cz(i) * Fv;
+            sG += w * (c.p * (R(1) + Fv) + (i ? col_rec(i, c) : R(0)));
+            if (cx(i)) j0 += w * cx(i) * Fv;
+            if (cy(i)) j1 += w * cy(i) * Fv;
+            if (cz(i)) j2 += w * cz(i) * Fv;
         }
-        const double rr = 1.0 + sF;             // rho / rho0
-        const double ra = 0.5 * (rr + sG);      // rho^a / rho0
-        for (int a = 0; a < 3; a++) s[a] += ra / rr * I.rho0 * j[a];
-        s[3] += ra * I.rho0;
+        const R rr = R(1) + sF;                 // rho / rho0
+        const R ra = R(0.5) * (rr + sG);        // rho^a / rho0
+        const R k = ra / rr * rho0;
+        s[0] += (double)(k * j0);
+        s[1] += (double)(k * j1);
+        s[2] += (double)(k * j2);
+        s[3] += (double)(ra * rho0);
     }
     __shared__ double sh[4][256];
     for (int a = 0; a < 4; a++) sh[a][threadIdx.x] = s[a];
@@ -397,16 +407,27 @@ __global__ void k_speed_partial(Lattice L, int cur, int inst, double *part)
         for (int a = 0; a < 4; a++) part[4 * blockIdx.x + a] = sh[a][0];
 }
 
-// state[0..2]: integral of the error, state[3..5]: U_a at the last update
+// state[0..2]: integral of the error, state[3..5]: U_a at the last update.
+// One CTA of SPEED_THREADS sums the per-block partials (strided, then a tree
+// in shared memory); thread 0 applies the law.
+static const int SPEED_THREADS = 256;
 __global__ void k_speed_update(Lattice L, int inst, const double *part, int nblk, double *state)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double sh[4][SPEED_THREADS];
     double s[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = 0; b < nblk; b++)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
         for (int a = 0; a < 4; a++) s[a] += part[4 * b + a];
+    for (int a = 0; a < 4; a++) sh[a][threadIdx.x] = s[a];
+    __syncthreads();
+    for (int k = SPEED_THREADS / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k)
+            for (int a = 0; a < 4; a++) sh[a][threadIdx.x] += sh[a][threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
     InstDev &I = ((InstDev *)L.inst)[inst];
     for (int a = 0; a < 3; a++) {
-        const double U = s[3] > 0.0 ? s[a] / s[3] : 0.0;
+        const double U = sh[3][0] > 0.0 ? sh[a][0] / sh[3][0] : 0.0;
         state[3 + a] = U;
         if (!(I.sp_mask & (1 << a))) continue;
         const double e = I.sp_target[a] - U;
@@ -582,7 +603,7 @@ static void take_speed(lbm_ctx *ctx, long long *launches)
             using S = std::remove_pointer_t<decltype(tag)>;
             k_speed_partial<S><<<DIAG_BLOCKS, 256, 0, ctx->stream>>>(L, ctx->cur, k, ctx->speed_part);
         });
-        k_speed_update<<<1, 32, 0, ctx->stream>>>(L, k, ctx->speed_part, DIAG_BLOCKS, ctx->speed_d + 6 * k);
+        k_speed_update<<<1, SPEED_THREADS, 0, ctx->stream>>>(L, k, ctx->speed_part, DIAG_BLOCKS, ctx->speed_d + 6 * k);
         *launches += 2;
     }
 }

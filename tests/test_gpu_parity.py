@@ -442,28 +442,37 @@ def test_launch_variants_agree(prec, shape):
             assert rel_l2(a, b) <= k * ulp, ("node pairs", rel_l2(a, b))
 
 
-def test_fp64_drop_speed_control_matches_oracle():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_drop_speed_control_matches_oracle(prec):
     """Drop-speed control (PI on the phase-a body force, x component, every 10
     steps) on a sessile drop: the controlled force, the measured phase-a
     velocity and the populations after 65 steps (6 updates, one between the
-    two steps of a captured pair) against the oracle."""
+    two steps of a captured pair) against the oracle.  FP32 storage: the
+    velocity within the FP32 field bar (1e-4 of its size) and the force within
+    what that velocity error drives through the PI law over the 6 updates."""
     nx, ny, nz = 40, 24, 20
+    kp, ki, every = 1e-2, 5e-5, 10
     p = dict(W.COMMON, nx=nx, ny=ny, nz=nz, wall_z0=1, theta_wall_deg=100.0, nu_a=1 / 6, nu_b=1 / 30,
              body_force_a=(1e-6, 0.0, 0.0), drop_speed_control=1, drop_speed_target=(2e-3, 0.0, 0.0),
-             drop_speed_kp=1e-2, drop_speed_ki=5e-5, drop_speed_interval=10)
+             drop_speed_kp=kp, drop_speed_ki=ki, drop_speed_interval=every)
     w = dict(params=p, phi=W.drop_phi(nx, ny, nz, (14.0, 12.0, 0.5), 7.0), particles=[])
-    o = run_oracle(w, 65)
     sim = oracle_sim(w)
     sim.step(65)
     fo, uo = sim.speed_control()
-    c = gpu_ctx(w, "fp64")
+    c = gpu_ctx(w, prec)
     c.lbm_step(65)
     fg, ug = c.lbm_drop_speed_state()
     c.close()
-    assert abs(fg[0] - fo[0]) <= 1e-12 * abs(fo[0]) and fg[1] == 0.0 and fg[2] == 0.0
-    assert np.all(np.abs(ug - uo) <= 1e-13)
     assert fo[0] != 1e-6  # the controller acted
-    assert_fp64_parity(run_gpu(w, 65, "fp64"), o)
+    assert fg[1] == 0.0 and fg[2] == 0.0
+    if prec == "fp64":
+        assert abs(fg[0] - fo[0]) <= 1e-12 * abs(fo[0])
+        assert np.all(np.abs(ug - uo) <= 1e-13)
+        assert_fp64_parity(run_gpu(w, 65, "fp64"), o=run_oracle(w, 65))
+    else:
+        tol_u = 1e-4 * np.abs(uo).max()
+        assert np.all(np.abs(ug - uo) <= tol_u), (ug, uo)
+        assert abs(fg[0] - fo[0]) <= (kp + 6 * every * ki) * tol_u, (fg[0], fo[0])
 
 
 def test_autotune_picks_shapes_per_size_class_and_keeps_the_trajectory():
@@ -736,3 +745,4 @@ def test_single_step_calls_equal_bulk_steps(prec):
     assert np.array_equal(ra, rb)
     assert np.array_equal(recs[-1], rb[0])
     assert not np.array_equal(recs[0], recs[-1])
+
