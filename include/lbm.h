@@ -240,11 +240,13 @@ lbm_status lbm_set_particle_motion(lbm_ctx *ctx, int inst, int p, const double *
 lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out);
 
 /* As lbm_particle_forces, enqueued on the context's stream without
- * synchronising: the records are packed on the device and copied to out,
- * which should be page-locked host memory for the copy to overlap (the
- * values are valid once the stream has reached the copy, e.g. after the next
- * synchronising call).  Lets a caller read every step's forces without
- * stalling the device.  Bad instance or null out -> LBM_ERR_ARG. */
+ * synchronising.  If the device can address out (page-locked host memory,
+ * which unified addressing maps, or device / managed memory), one packing
+ * kernel writes the records there directly; otherwise (pageable host memory)
+ * they are packed on the device and copied to out.  The values are valid once
+ * the stream has passed that point, e.g. after the next synchronising call.
+ * Lets a caller read every step's forces without stalling the device.  Bad
+ * instance or null out -> LBM_ERR_ARG. */
 lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out);
 
 /* Checkpoint of an instance's particles, for an exact resume with contacts

@@ -1425,6 +1425,18 @@ lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out)
         CU(cudaStreamSynchronize(ctx->stream));
         CU(cudaMalloc((void **)&ctx->rec_d, sizeof(double) * LBM_PARTICLE_RECORD * ctx->parts_h.size()));
     }
+    // a buffer the device can address (page-locked host memory, which unified
+    // addressing maps, or device / managed memory) is written by the packing
+    // kernel itself: no separate copy in the stream
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.devicePointer &&
+        (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
+        k_pack_records<<<(I.np + 63) / 64, 64, 0, ctx->stream>>>(ctx->parts_d + I.part_off, I.np,
+                                                                 (double *)pa.devicePointer);
+        CU(cudaGetLastError());
+        return LBM_OK;
+    }
+    cudaGetLastError();  // an unregistered pointer is not an error here
     double *dst = ctx->rec_d + (size_t)LBM_PARTICLE_RECORD * I.part_off;
     k_pack_records<<<(I.np + 63) / 64, 64, 0, ctx->stream>>>(ctx->parts_d + I.part_off, I.np, dst);
     CU(cudaGetLastError());

@@ -320,8 +320,9 @@ class Context:
 
     def lbm_particle_forces_async(self, out, inst=0):
         """Enqueue the read of the particle records into out (a float64 array of
-        at least n_particles x PARTICLE_RECORD, page-locked for the copy to
-        overlap); valid after the next synchronisation."""
+        at least n_particles x PARTICLE_RECORD; page-locked memory is written by
+        the device directly, pageable memory through a copy); valid after the
+        next synchronisation."""
         n = self.num_particles(inst)
         if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < n * PARTICLE_RECORD:
             raise ValueError("out must be a C-contiguous float64 array of n_particles x PARTICLE_RECORD")

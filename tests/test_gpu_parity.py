@@ -725,7 +725,10 @@ def test_resume_under_drop_speed_control():
 def test_single_step_calls_equal_bulk_steps(prec):
     """lbm_step(1) replays a captured one-step graph (one per buffer parity);
     40 single-step calls give the same bits as one call of 40 steps, and the
-    records read asynchronously each step equal the synchronous read."""
+    records read asynchronously each step equal the synchronous read, into
+    pageable memory (packed and copied), page-locked host memory and device
+    memory (both written by the packing kernel directly)."""
+    import torch
     w = W.cfg1()
     a = gpu_ctx(w, prec)
     a.lbm_step(40)
@@ -735,9 +738,15 @@ def test_single_step_calls_equal_bulk_steps(prec):
     b = gpu_ctx(w, prec)
     from paper_2505_10171_gb300 import lbm
     recs = np.zeros((40, lbm.PARTICLE_RECORD))
+    pinned = torch.zeros((40, lbm.PARTICLE_RECORD), dtype=torch.float64).pin_memory()
+    recp = pinned.numpy()
+    dev = torch.zeros((40, lbm.PARTICLE_RECORD), dtype=torch.float64, device="cuda")
     for k in range(40):
         b.lbm_step(1)
         b.lbm_particle_forces_async(recs[k])
+        b.lbm_particle_forces_async(recp[k])
+        dptr = lbm.ct.cast(lbm.ct.c_void_p(dev[k].data_ptr()), lbm.ct.POINTER(lbm.ct.c_double))
+        b._check(b.L.lbm_particle_forces_async(b.h, 0, dptr))
     gb_a, gb_b = b.pops()  # synchronises
     rb = b.lbm_particle_forces()
     b.close()
@@ -745,4 +754,6 @@ def test_single_step_calls_equal_bulk_steps(prec):
     assert np.array_equal(ra, rb)
     assert np.array_equal(recs[-1], rb[0])
     assert not np.array_equal(recs[0], recs[-1])
+    assert np.array_equal(recp, recs)
+    assert np.array_equal(dev.cpu().numpy(), recs)
 
