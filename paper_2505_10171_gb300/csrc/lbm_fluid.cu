@@ -417,8 +417,12 @@ __device__ __forceinline__ void collide_body2(const Lattice &L, const InstDev &I
     });
 }
 
+// CTAs of 128 threads per SM the node-pair collision is compiled for: 6 (80
+// registers, 60 bytes spilled) measured faster than 4 (128 registers, no
+// spill), 5, 7 and 8 (105, 102, 100 and 109 against 96 us per 256x128x128
+// launch): the pulls of more node pairs in flight outweigh the spill traffic
 #ifndef LBM_COLLIDE2_MINB
-#define LBM_COLLIDE2_MINB 4
+#define LBM_COLLIDE2_MINB 6
 #endif
 template <class S>
 __global__ void __launch_bounds__(ROW_NODES / 2, LBM_COLLIDE2_MINB) k_collide2(Lattice L, int cur)
