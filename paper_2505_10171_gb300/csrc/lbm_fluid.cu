@@ -38,8 +38,11 @@
 #ifndef LBM_BOUND_MINB
 #define LBM_BOUND_MINB 2
 #endif
+// CTAs of 256 threads per SM of the one-node collision: 5 (48 registers, no
+// spill) measured faster than 4 (64 registers) and 6 (40, spilling): 123
+// against 127 and 148 us per FP32 256x128x128 launch
 #ifndef LBM_COLLIDE_MINB
-#define LBM_COLLIDE_MINB 4
+#define LBM_COLLIDE_MINB 5
 #endif
 
 namespace lbmg {
