@@ -384,10 +384,10 @@ def main():
 
 def e2e_measure(torch, lbm, W, args, stream):
     """The same metric through the C ABI with host buffers: pinned-host upload of
-    the initial order parameter, K single-step calls each followed by a
-    device-to-host read of that step's per-particle force records into pinned
-    host memory (enqueued, not waited on), and a final synchronising host read
-    of phi, which the timed region includes."""
+    the initial order parameter, K single-step calls, every step's per-particle
+    records written into a page-locked host ring by the step itself
+    (lbm_set_record_ring, one slot per step), and a final synchronising host
+    read of phi, which the timed region includes."""
     import numpy as np
     w = W.cfg2()
     N = 256 * 128 * 128
@@ -395,22 +395,23 @@ def e2e_measure(torch, lbm, W, args, stream):
     phi_h = torch.from_numpy(w["phi"]).pin_memory().numpy()
     out_h = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
     K = args.steps
-    rec_h = torch.empty((K, nparts * lbm.PARTICLE_RECORD), dtype=torch.float64).pin_memory().numpy()
+    rec_h = torch.zeros((K, nparts * lbm.PARTICLE_RECORD), dtype=torch.float64).pin_memory().numpy()
     ctx = build_context(lbm, w, args.precision, stream.cuda_stream)
     ctx.lbm_init_fields(phi_h)
+    ctx.lbm_set_record_ring(rec_h)  # before the graphs are captured
     ctx.lbm_step(args.warmup)
     for k in range(2):  # both single-step graphs captured before the timed region
         ctx.lbm_step(1)
     torch.cuda.synchronize()
+    rec_h[:] = np.nan  # every slot must be written again by the timed steps
     t0 = time.perf_counter()
     ctx.lbm_init_fields(phi_h)
     for k in range(K):
         ctx.lbm_step(1)
-        ctx.lbm_particle_forces_async(rec_h[k])
     ctx.lbm_read_fields(lbm.FIELD_PHI, out=out_h)
     dt = time.perf_counter() - t0
     if not np.isfinite(rec_h).all():
-        raise RuntimeError("non-finite particle records in the end-to-end run")
+        raise RuntimeError("particle records missing or non-finite in the end-to-end run")
     ctx.close()
     return dict(value=N * K / dt / 1e6, unit=UNIT, h2d_bytes_per_step=8 * N / K,
                 d2h_bytes_per_step=8 * lbm.PARTICLE_RECORD * nparts + 8 * N / K)

@@ -249,6 +249,21 @@ lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out);
  * instance or null out -> LBM_ERR_ARG. */
 lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out);
 
+/* Record ring: from the next step on, every step writes the records of all
+ * particles of the context (instances in order, LBM_PARTICLE_RECORD doubles
+ * each, the layout of lbm_particle_forces) into slot k mod slots of ring, k
+ * counting the steps since this call (from 0).  The records are packed on the
+ * device inside the step, right after the DEM (Sec. III) has updated the
+ * particles, on the stream that runs the particle kernels: no launch and no
+ * copy of the caller's.  ring must be page-locked host, device or managed
+ * memory (the device writes it) of slots x n_particles_total x
+ * LBM_PARTICLE_RECORD doubles, kept alive while set; a slot is valid once the
+ * context's stream has passed its step (e.g. after the next synchronising
+ * call).  ring NULL stops the recording; adding particles stops it too.
+ * slots < 1, no particles, or memory the device cannot address ->
+ * LBM_ERR_ARG.  Synchronises; invalidates the step graph. */
+lbm_status lbm_set_record_ring(lbm_ctx *ctx, double *ring, int slots);
+
 /* Checkpoint of an instance's particles, for an exact resume with contacts
  * (the DEM of Sec. III carries state from step to step).  Per particle
  * LBM_PARTICLE_STATE doubles: x[3] v[3] w[3] q[4] (w, x, y, z), then the total

@@ -54,6 +54,11 @@ struct lbm_ctx {
     cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // one step from buffer 0 / from buffer 1
     long long graph1_launches[2] = {0, 0};
     double *rec_d = nullptr;  // packed particle records of lbm_particle_forces_async
+    // record ring (lbm_set_record_ring): device address of the caller's
+    // buffer, its slot count, and the device-side count of steps written
+    double *ring = nullptr;
+    int ring_slots = 0;
+    long long *ring_ctr = nullptr;
     long long last_launches = 0;
     double *scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -498,6 +503,8 @@ static void profile_mark(void *self, int stage, int after)
     else c->ev_pairs.push_back({stage, {c->ev_open[stage], e}});
 }
 
+static void enqueue_ring(const lbm_ctx *c, cudaStream_t st, long long *launches);
+
 static void enqueue_step(lbm_ctx *c, long long *launches)
 {
     Lattice L = make_lattice(c);
@@ -546,6 +553,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
             lane.after_collide_bound.fn = [](void *p) {
                 Ctx2 *q = (Ctx2 *)p;
                 launch_dem<S>(*q->L, q->c->side, q->launches, *q->mk, true);
+                enqueue_ring(q->c, q->c->side, q->launches);
                 // the new owners beside the bulk collision: the nodes whose
                 // owner changes are solid or next to a solid before and after,
                 // which the bulk collision skips either way; with a stored
@@ -562,6 +570,7 @@ static void enqueue_step(lbm_ctx *c, long long *launches)
             if (sur) launch_surrogate_forces<S>(L, c->mlp, c->feat, c->stream, launches, mk);
             else launch_particle_forces<S>(L, cur, c->stream, launches, mk);
             launch_dem<S>(L, c->stream, launches, mk, !sur);
+            enqueue_ring(c, c->stream, launches);
         }
         // geometry: owners first; then boundary bits (side stream) beside the
         // refill of uncovered nodes (they touch disjoint data)
@@ -691,12 +700,8 @@ static void drop_graph(lbm_ctx *c)
 
 // the records of lbm_particle_forces, packed on the device (one thread per
 // particle of the instance)
-__global__ void k_pack_records(const PartDev *parts, int np, double *out)
+__device__ __forceinline__ void pack_record(const PartDev &q, double *o)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= np) return;
-    const PartDev &q = parts[p];
-    double *o = out + (size_t)LBM_PARTICLE_RECORD * p;
     for (int a = 0; a < 3; a++) {
         o[a] = q.Feta[a]; o[3 + a] = q.Teta[a];
         o[6 + a] = q.Fsig[a]; o[9 + a] = q.Tsig[a];
@@ -707,6 +712,33 @@ __global__ void k_pack_records(const PartDev *parts, int np, double *out)
     o[31] = q.m;
     o[32] = q.sub;
     for (int a = 0; a < 3; a++) o[33 + a] = q.Fb[a];
+}
+
+__global__ void k_pack_records(const PartDev *parts, int np, double *out)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    pack_record(parts[p], out + (size_t)LBM_PARTICLE_RECORD * p);
+}
+
+// the records of every particle of the context into slot (*ctr mod slots) of
+// the record ring, then *ctr + 1 (one CTA)
+__global__ void k_pack_ring(const PartDev *parts, int np, double *ring, int slots, long long *ctr)
+{
+    const long long k = *ctr;
+    double *slot = ring + (size_t)(k % slots) * LBM_PARTICLE_RECORD * np;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) pack_record(parts[p], slot + (size_t)LBM_PARTICLE_RECORD * p);
+    __syncthreads();
+    if (threadIdx.x == 0) *ctr = k + 1;
+}
+
+// the step's particle records into the record ring, if one is set; the
+// particle state is final once the DEM has run
+static void enqueue_ring(const lbm_ctx *c, cudaStream_t st, long long *launches)
+{
+    if (!c->ring || c->parts_h.empty()) return;
+    k_pack_ring<<<1, 64, 0, st>>>(c->parts_d, (int)c->parts_h.size(), c->ring, c->ring_slots, c->ring_ctr);
+    *launches += 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -735,6 +767,7 @@ void lbm_destroy(lbm_ctx *ctx)
     cudaFree(ctx->static_bfl);
     cudaFree(ctx->speed_d);
     cudaFree(ctx->rec_d);
+    cudaFree(ctx->ring_ctr);
     cudaFree(ctx->pbl);
     cudaFree(ctx->pbl_n);
     cudaFree(ctx->psl);
@@ -1184,6 +1217,7 @@ lbm_status lbm_add_particles(lbm_ctx *ctx, int inst, int n, const lbm_particle *
     cudaFree(ctx->parts_d);
     cudaFree(ctx->rec_d);
     ctx->rec_d = nullptr;
+    ctx->ring = nullptr;  // a ring slot holds every particle: set it again
     cudaFree(ctx->pbl);
     cudaFree(ctx->psl);
     ctx->pbl = ctx->psl = nullptr;
@@ -1442,6 +1476,32 @@ lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out)
     CU(cudaGetLastError());
     CU(cudaMemcpyAsync(out, dst, sizeof(double) * LBM_PARTICLE_RECORD * I.np, cudaMemcpyDeviceToHost,
                        ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_record_ring(lbm_ctx *ctx, double *ring, int slots)
+{
+    if (!ctx) return LBM_ERR_ARG;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (!ring) {
+        ctx->ring = nullptr;
+        drop_graph(ctx);
+        return LBM_OK;
+    }
+    if (slots < 1) return fail(ctx, LBM_ERR_ARG, "slots < 1");
+    if (ctx->parts_h.empty()) return fail(ctx, LBM_ERR_ARG, "no particles to record");
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, ring) != cudaSuccess || !pa.devicePointer ||
+        !(pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(ctx, LBM_ERR_ARG, "the ring must be page-locked host, device or managed memory");
+    }
+    if (!ctx->ring_ctr) CU(cudaMalloc((void **)&ctx->ring_ctr, sizeof(long long)));
+    CU(cudaMemsetAsync(ctx->ring_ctr, 0, sizeof(long long), ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->ring = (double *)pa.devicePointer;
+    ctx->ring_slots = slots;
+    drop_graph(ctx);
     return LBM_OK;
 }
 

@@ -82,7 +82,8 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_surrogate_save", "lbm_surrogate_predict", "lbm_surrogate_gradient", "lbm_surrogate_train",
            "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion",
            "lbm_inject_fault", "lbm_particle_state_size", "lbm_get_particle_state", "lbm_set_particle_state",
-           "lbm_run_state_size", "lbm_get_run_state", "lbm_set_run_state", "lbm_particle_forces_async"]
+           "lbm_run_state_size", "lbm_get_run_state", "lbm_set_run_state", "lbm_particle_forces_async",
+           "lbm_set_record_ring"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -115,6 +116,7 @@ def load(path: str = LIB_PATH):
     L.lbm_step.argtypes = [vp, i]
     L.lbm_particle_forces.argtypes = [vp, i, d]
     L.lbm_particle_forces_async.argtypes = [vp, i, d]
+    L.lbm_set_record_ring.argtypes = [vp, vp, i]
     L.lbm_set_particle_motion.argtypes = [vp, i, i, d, d]
     L.lbm_read_fields.argtypes = [vp, i, ct.c_uint, d]
     L.lbm_read_fields_device.argtypes = [vp, i, ct.c_uint, vp]
@@ -327,6 +329,26 @@ class Context:
         if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < n * PARTICLE_RECORD:
             raise ValueError("out must be a C-contiguous float64 array of n_particles x PARTICLE_RECORD")
         self._check(self.L.lbm_particle_forces_async(self.h, inst, _dp(out)))
+
+    def lbm_set_record_ring(self, ring):
+        """Record every step's particle records (all instances) into ring, a
+        float64 array of slots x n_particles_total x PARTICLE_RECORD in
+        page-locked host memory (or a device tensor's pointer given as an int
+        with its slot count: (ptr, slots)); step k since the call goes to slot
+        k mod slots.  None stops the recording."""
+        if ring is None:
+            self._ring = None
+            self._check(self.L.lbm_set_record_ring(self.h, None, 0))
+            return
+        if isinstance(ring, tuple):
+            ptr, slots = ring
+            self._check(self.L.lbm_set_record_ring(self.h, ct.c_void_p(int(ptr)), int(slots)))
+            self._ring = ring
+            return
+        if ring.dtype != np.float64 or not ring.flags.c_contiguous or ring.ndim < 2:
+            raise ValueError("ring must be a C-contiguous float64 array of slots x records")
+        self._check(self.L.lbm_set_record_ring(self.h, ring.ctypes.data_as(ct.c_void_p), int(ring.shape[0])))
+        self._ring = ring
 
     def lbm_read_fields(self, mask, inst=0, out=None):
         N = self.num_nodes(inst)

@@ -757,3 +757,44 @@ def test_single_step_calls_equal_bulk_steps(prec):
     assert np.array_equal(recp, recs)
     assert np.array_equal(dev.cpu().numpy(), recs)
 
+
+
+@pytest.mark.parametrize("where", ["pinned", "device"])
+def test_record_ring_holds_every_steps_records(where):
+    """lbm_set_record_ring: 20 steps in one call (two-step graphs) leave the
+    records of steps 12..19 in slots k mod 8, equal to the synchronous reads
+    after each of 20 single steps of a second context (FP32 is bitwise
+    reproducible); the ring is written inside the captured step, in page-locked
+    host or device memory.  Pageable memory and zero slots are refused; a ring
+    set to None is no longer written."""
+    import torch
+    from paper_2505_10171_gb300 import lbm
+    w = W.cfg1()
+    a = gpu_ctx(w, "fp32", store_velocity=False)
+    ref = []
+    for k in range(20):
+        a.lbm_step(1)
+        ref.append(a.lbm_particle_forces().reshape(-1).copy())
+    a.close()
+    b = gpu_ctx(w, "fp32", store_velocity=False)
+    n = b.num_particles() * lbm.PARTICLE_RECORD
+    if where == "pinned":
+        t = torch.zeros((8, n), dtype=torch.float64).pin_memory()
+        b.lbm_set_record_ring(t.numpy())
+    else:
+        t = torch.zeros((8, n), dtype=torch.float64, device="cuda")
+        b.lbm_set_record_ring((t.data_ptr(), 8))
+    b.lbm_step(20)
+    b.pops()  # synchronises
+    got = t.cpu().numpy().copy()
+    for k in range(12, 20):
+        assert np.array_equal(got[k % 8], ref[k]), k
+    b.lbm_set_record_ring(None)
+    b.lbm_step(3)
+    b.pops()
+    assert np.array_equal(t.cpu().numpy(), got)
+    with pytest.raises(lbm.LbmError):
+        b.lbm_set_record_ring(np.zeros((4, n)))
+    with pytest.raises(lbm.LbmError):
+        b.lbm_set_record_ring((t.data_ptr(), 0))
+    b.close()
