@@ -434,6 +434,12 @@ def extra_measure(torch, lbm, W, args, stream, N):
         out[prec] = dict(value=N * K / (ms_g * 1e-3) / 1e6, value_profiled=N * K / (ms * 1e-3) / 1e6,
                          collide_ms=cms, collide_gbs=design_bytes_per_node("collide", prec) * N / (cms * 1e-3) / 1e9,
                          steps=K)
+    # the non-tensor arithmetic ceiling of the 16-bit modes (their collision
+    # is issue-bound): measured FP32 FMA throughput against the nominal rate
+    # (152 SMs x 128 FP32 lanes x 2 FLOP x the maximum SM clock)
+    fma = lbm.lbm_fp32_fma_peak()
+    nominal = 152 * 128 * 2 * 2.07e9 / 1e12
+    out["alu"] = dict(fp32_fma_peak_tflops=fma, unit="TFLOP/s", nominal_tflops=nominal, frac_of_nominal=fma / nominal)
     out["batched"] = batched_measure(torch, lbm, W, args, stream)
     out["stated_error"] = error_measure(lbm, W, stream)
     return out

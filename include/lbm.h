@@ -264,6 +264,15 @@ lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out);
  * LBM_ERR_ARG.  Synchronises; invalidates the step graph. */
 lbm_status lbm_set_record_ring(lbm_ctx *ctx, double *ring, int slots);
 
+/* Measured FP32 multiply-add throughput of the current device in TFLOP/s
+ * (2 FLOP per FMA): the non-tensor arithmetic ceiling of the 16-bit storage
+ * modes, whose collision is held by instruction issue rather than by DRAM.
+ * Eight CTAs of 256 threads per SM, eight independent chains per thread, the
+ * best of five timed launches after a warm-up (about 2 ms each).  The paper
+ * has no counterpart.  Null tflops -> LBM_ERR_ARG (no device call); a CUDA
+ * failure -> LBM_ERR_CUDA.  Synchronises. */
+lbm_status lbm_fp32_fma_peak(double *tflops);
+
 /* Checkpoint of an instance's particles, for an exact resume with contacts
  * (the DEM of Sec. III carries state from step to step).  Per particle
  * LBM_PARTICLE_STATE doubles: x[3] v[3] w[3] q[4] (w, x, y, z), then the total

@@ -83,7 +83,7 @@ EXPORTS = ["lbm_create", "lbm_destroy", "lbm_last_error", "lbm_set_solid_mask", 
            "lbm_surrogate_features", "lbm_drop_speed_state", "lbm_autotune", "lbm_set_particle_motion",
            "lbm_inject_fault", "lbm_particle_state_size", "lbm_get_particle_state", "lbm_set_particle_state",
            "lbm_run_state_size", "lbm_get_run_state", "lbm_set_run_state", "lbm_particle_forces_async",
-           "lbm_set_record_ring"]
+           "lbm_set_record_ring", "lbm_fp32_fma_peak"]
 # learned force surrogate (include/lbm.h)
 MLP_INPUTS, MLP_OUTPUTS, MLP_PARAMS, MLP_MAX_BATCH = 387, 6, 68614, 4096
 FORCE_RESOLVED, FORCE_SURROGATE = 0, 1
@@ -117,6 +117,7 @@ def load(path: str = LIB_PATH):
     L.lbm_particle_forces.argtypes = [vp, i, d]
     L.lbm_particle_forces_async.argtypes = [vp, i, d]
     L.lbm_set_record_ring.argtypes = [vp, vp, i]
+    L.lbm_fp32_fma_peak.argtypes = [d]
     L.lbm_set_particle_motion.argtypes = [vp, i, i, d, d]
     L.lbm_read_fields.argtypes = [vp, i, ct.c_uint, d]
     L.lbm_read_fields_device.argtypes = [vp, i, ct.c_uint, vp]
@@ -196,6 +197,15 @@ def lbm_component_masses_noalloc(pops_ptr, n_nodes, masses_ptr, stream=0):
                                              ct.c_void_p(stream or 0))
     if st != LBM_OK:
         raise LbmError(st, "lbm_component_masses_noalloc failed")
+
+
+def lbm_fp32_fma_peak():
+    """Measured FP32 multiply-add throughput of the current device, TFLOP/s."""
+    out = ct.c_double(0.0)
+    st = load().lbm_fp32_fma_peak(ct.byref(out))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_fp32_fma_peak failed")
+    return out.value
 
 
 def _dp(a):

@@ -19,7 +19,7 @@ HEADER = os.path.join(ROOT, "include", "lbm.h")
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -123,3 +123,9 @@ def test_create_rejects_an_unknown_precision(libpath):
     assert L.lbm_create(arr, 1, 4, None, ct.byref(h)) == 7  # the former mixed-storage code
     assert L.lbm_create(arr, 0, 1, None, ct.byref(h)) == 1  # no instances: LBM_ERR_ARG
     assert not h.value
+
+
+def test_fma_peak_rejects_a_null_output():
+    """The FMA microbenchmark checks its argument before touching a device."""
+    from paper_2505_10171_gb300 import lbm
+    assert lbm.load().lbm_fp32_fma_peak(None) == 1  # LBM_ERR_ARG
