@@ -241,8 +241,8 @@ lbm_status lbm_particle_forces(lbm_ctx *ctx, int inst, double *out);
 
 /* As lbm_particle_forces, enqueued on the context's stream without
  * synchronising.  If the device can address out (page-locked host memory,
- * which unified addressing maps, or device / managed memory), one packing
- * kernel writes the records there directly; otherwise (pageable host memory)
+ * which unified addressing maps, managed memory, or this device's memory),
+ * one packing kernel writes the records there directly; otherwise (pageable host memory)
  * they are packed on the device and copied to out.  The values are valid once
  * the stream has passed that point, e.g. after the next synchronising call.
  * Lets a caller read every step's forces without stalling the device.  Bad
@@ -255,8 +255,8 @@ lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out);
  * counting the steps since this call (from 0).  The records are packed on the
  * device inside the step, right after the DEM (Sec. III) has updated the
  * particles, on the stream that runs the particle kernels: no launch and no
- * copy of the caller's.  ring must be page-locked host, device or managed
- * memory (the device writes it) of slots x n_particles_total x
+ * copy of the caller's.  ring must be page-locked host, managed or this
+ * device's memory (the device writes it) of slots x n_particles_total x
  * LBM_PARTICLE_RECORD doubles, kept alive while set; a slot is valid once the
  * context's stream has passed its step (e.g. after the next synchronising
  * call).  ring NULL stops the recording; adding particles stops it too.

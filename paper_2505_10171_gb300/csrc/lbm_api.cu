@@ -505,6 +505,24 @@ static void profile_mark(void *self, int stage, int after)
 
 static void enqueue_ring(const lbm_ctx *c, cudaStream_t st, long long *launches);
 
+// the device address of a caller buffer this context's device can write:
+// page-locked host memory (mapped under unified addressing), managed memory,
+// or device memory of this device; null otherwise (pageable host memory,
+// another device's memory)
+static void *device_addressable(const void *p)
+{
+    cudaPointerAttributes pa;
+    int dev = -1;
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();  // an unregistered pointer is not an error here
+        return nullptr;
+    }
+    if (!pa.devicePointer) return nullptr;
+    if (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeManaged) return pa.devicePointer;
+    if (pa.type == cudaMemoryTypeDevice && pa.device == dev) return pa.devicePointer;
+    return nullptr;
+}
+
 static void enqueue_step(lbm_ctx *c, long long *launches)
 {
     Lattice L = make_lattice(c);
@@ -1462,15 +1480,11 @@ lbm_status lbm_particle_forces_async(lbm_ctx *ctx, int inst, double *out)
     // a buffer the device can address (page-locked host memory, which unified
     // addressing maps, or device / managed memory) is written by the packing
     // kernel itself: no separate copy in the stream
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.devicePointer &&
-        (pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
-        k_pack_records<<<(I.np + 63) / 64, 64, 0, ctx->stream>>>(ctx->parts_d + I.part_off, I.np,
-                                                                 (double *)pa.devicePointer);
+    if (void *d = device_addressable(out)) {
+        k_pack_records<<<(I.np + 63) / 64, 64, 0, ctx->stream>>>(ctx->parts_d + I.part_off, I.np, (double *)d);
         CU(cudaGetLastError());
         return LBM_OK;
     }
-    cudaGetLastError();  // an unregistered pointer is not an error here
     double *dst = ctx->rec_d + (size_t)LBM_PARTICLE_RECORD * I.part_off;
     k_pack_records<<<(I.np + 63) / 64, 64, 0, ctx->stream>>>(ctx->parts_d + I.part_off, I.np, dst);
     CU(cudaGetLastError());
@@ -1490,16 +1504,12 @@ lbm_status lbm_set_record_ring(lbm_ctx *ctx, double *ring, int slots)
     }
     if (slots < 1) return fail(ctx, LBM_ERR_ARG, "slots < 1");
     if (ctx->parts_h.empty()) return fail(ctx, LBM_ERR_ARG, "no particles to record");
-    cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, ring) != cudaSuccess || !pa.devicePointer ||
-        !(pa.type == cudaMemoryTypeHost || pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
-        cudaGetLastError();
-        return fail(ctx, LBM_ERR_ARG, "the ring must be page-locked host, device or managed memory");
-    }
+    void *d = device_addressable(ring);
+    if (!d) return fail(ctx, LBM_ERR_ARG, "the ring must be page-locked host, managed or this device's memory");
     if (!ctx->ring_ctr) CU(cudaMalloc((void **)&ctx->ring_ctr, sizeof(long long)));
     CU(cudaMemsetAsync(ctx->ring_ctr, 0, sizeof(long long), ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
-    ctx->ring = (double *)pa.devicePointer;
+    ctx->ring = (double *)d;
     ctx->ring_slots = slots;
     drop_graph(ctx);
     return LBM_OK;
