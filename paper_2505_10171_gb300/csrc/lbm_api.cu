@@ -106,7 +106,9 @@ static void plan_launch(lbm_ctx *c)
     c->fz.pair = even && c->fz.tile == 0;
 }
 
-static const int DIAG_BLOCKS = 512;
+// CTAs of 256 threads of the node sweeps of the diagnostics and of the
+// drop-speed control (8 per SM of a 152-SM GB300)
+static const int DIAG_BLOCKS = 1216;
 // bytes after the last flag (zeroed)
 static const size_t FLAG_PAD = 64;
 
@@ -351,13 +353,30 @@ __global__ void k_mass_partial(Lattice L, int cur, int inst, double *part)
     }
 }
 
+// the per-block partials summed by one CTA of MASS_THREADS (strided, then a
+// tree in shared memory)
+static const int MASS_THREADS = 256;
 __global__ void k_mass_final(const double *part, int nblk, double *out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int i = 0; i < nblk; i++) { a += part[2 * i]; b += part[2 * i + 1]; }
-        out[0] = a;
-        out[1] = b;
+    __shared__ double sh[2][MASS_THREADS];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        a += part[2 * i];
+        b += part[2 * i + 1];
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int k = MASS_THREADS / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + k];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0];
+        out[1] = sh[1][0];
     }
 }
 
@@ -466,7 +485,7 @@ void launch_mass_sums(const Lattice &L, int cur, int inst, long long N, double *
 {
     (void)N;
     k_mass_partial<S><<<nblk, 256, 0, st>>>(L, cur, inst, partial);
-    k_mass_final<<<1, 32, 0, st>>>(partial, nblk, out);
+    k_mass_final<<<1, MASS_THREADS, 0, st>>>(partial, nblk, out);
 }
 }  // namespace lbmg
 
