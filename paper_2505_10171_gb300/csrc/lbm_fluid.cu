@@ -7,8 +7,8 @@
 // in its two-relaxation-time form -> recolouring -> write.
 //
 // Kernels of a step: k_phi (one thread per node over row strips) stores phi;
-// the solid-phi fill over the listed
-// static solid nodes and the particle cubes; k_gradcurv (z-marching tiles:
+// the solid-phi fill over the listed static solid nodes and the step's list
+// of particle-surface solid nodes; k_gradcurv (z-marching tiles:
 // gradient, wetting, normal, curvature); k_collide (or k_collide2).  Nodes next
 // to a solid go to the boundary passes k_phi_bound and k_collide_bound, which
 // run beside the bulk kernels on a second stream.
@@ -730,7 +730,7 @@ void launch_fluid_step(const Lattice &L, int cur, cudaStream_t st, long long *la
         *launches += 1;
     };
     // phi of solid nodes next to fluid: the listed static nodes and the
-    // particle cubes (every particle node lies within R_p + 1 of its centre).
+    // particle-surface solid nodes the step's list scan found in the cubes.
     // It reads phi only at fluid nodes next to a solid, which the boundary
     // pass writes, so beside the bulk kernel it follows that pass on the side lane
     bool fill_done = false;
