@@ -798,3 +798,25 @@ def test_record_ring_holds_every_steps_records(where):
     with pytest.raises(lbm.LbmError):
         b.lbm_set_record_ring((t.data_ptr(), 0))
     b.close()
+
+
+def test_record_ring_of_a_batched_context():
+    """Two instances with a sphere each: a ring slot holds instance 0's
+    records, then instance 1's, equal to the synchronous per-instance reads
+    after the same step."""
+    import torch
+    from paper_2505_10171_gb300 import lbm
+    ws = [W.cfg1(), W.cfg2_crop(40, 40, 24)]
+    c = lbm.Context([dict(w["params"], store_velocity=0) for w in ws], "fp32")
+    for k, w in enumerate(ws):
+        c.lbm_add_particles(w["particles"], inst=k)
+        c.lbm_init_fields(w["phi"], inst=k)
+    n0, n1 = c.num_particles(0), c.num_particles(1)
+    assert n0 >= 1 and n1 >= 1
+    t = torch.zeros((4, (n0 + n1) * lbm.PARTICLE_RECORD), dtype=torch.float64).pin_memory()
+    c.lbm_set_record_ring(t.numpy())
+    c.lbm_step(7)  # slots 0..3 hold steps 4, 5, 6 and 3
+    r0, r1 = c.lbm_particle_forces(0).reshape(-1), c.lbm_particle_forces(1).reshape(-1)
+    last = t.numpy()[6 % 4]
+    assert np.array_equal(last[:r0.size], r0) and np.array_equal(last[r0.size:], r1)
+    c.close()
